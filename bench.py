@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Benchmark: forward + backward throughput of the Gaussian Mesh Renderer hot
+path (mesh-to-Gaussian conversion, EWA projection, tile binning and sorting,
+alpha compositing, and the backward to vertices and face colours/opacity).
+
+Metric: Mpixel-views/s = (pixels over all views) / (fwd + bwd time) / 1e6 for
+one step, where a step renders every view of the workload, computes the L2
+loss against fixed target images and runs the full backward. The headline
+value is the batched form (all views in one call, captured in a CUDA graph);
+the per-view form (one call per view) is reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmr|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the path is not sharded); value = pixels of all ranks / slowest rank.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gmr_inputs as gi  # noqa: E402
+
+METRIC = "fwd+bwd Mpixel-views/s and ms/iter, batched vs per-view, at ≤1e-5 img err"
+UNIT = "Mpixel-views/s"
+DEFAULT_WORKLOAD = "icosphere5_sin_8x512"
+WORKLOADS = {
+    "icosphere5_sin_8x512": gi.scene_ring,
+    "icosphere3_1x128": gi.scene_single_view,
+    "icosphere6_noise_64xuneven": gi.scene_fibonacci_uneven,
+    "icosphere8_perlin_16x1024": gi.scene_large,
+}
+
+# FP32 peak of the CUDA cores: 148 SMs x 128 lanes x 2 (FMA) x 2.032 GHz.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# Algorithmic FP32 operations (FMA = 2) per evaluated (pixel, Gaussian) pair
+# and per contributing pair, counted from the compositing formulas.
+FLOPS_EVAL = 13
+FLOPS_FWD_CONTRIB = 10
+FLOPS_BWD_CONTRIB = 59
+# DRAM bytes per launch measured by ncu for the dominant kernel on the
+# default workload (profiles/raster_bwd_icosphere5_sin_8x512.md); None when
+# the kernel has changed since the capture.
+NCU_TRAFFIC = {}
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clock, power and clock-event reasons through NVML."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
+
+    def __init__(self, device_index, period=0.1):
+        self.samples = []
+        self.period = period
+        self.ok = False
+        self._stop = threading.Event()
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = None
+            try:
+                import torch
+
+                uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+                self.h = pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid) if not uuid.startswith("GPU") else uuid)
+            except Exception:
+                self.h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception as e:  # no NVML: report no clocks
+            log(f"clock sampling unavailable: {e}")
+
+    def _run(self):
+        nv = self.nv
+        while not self._stop.is_set():
+            try:
+                t = time.perf_counter()
+                mhz = nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
+                try:
+                    rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                except Exception:
+                    rs = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
+                pw = nv.nvmlDeviceGetPowerUsage(self.h) / 1000.0
+                self.samples.append((t, mhz, rs, pw))
+            except Exception:
+                pass
+            self._stop.wait(self.period)
+
+    def start(self):
+        if self.ok:
+            self.th = threading.Thread(target=self._run, daemon=True)
+            self.th.start()
+
+    def stop(self):
+        if self.ok:
+            self._stop.set()
+            self.th.join()
+
+    def summary(self, t0, t1):
+        if not self.ok or not self.samples:
+            return None
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = "timed"
+        if len(inside) < 3:
+            inside = self.samples
+            window = "warmup+timed"
+        reasons = set()
+        for s in inside:
+            for bit, name in self.REASONS.items():
+                if s[2] & bit and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+                "power_w_max": max(s[3] for s in inside)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_sample_time(scene, n_pix, seed=0):
+    """Oracle fwd + bwd on n_pix random pixels of the workload; seconds."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    off = oracle.pixel_offsets(scene.cams)
+    pix = []
+    for _ in range(n_pix):
+        c = int(rng.integers(len(scene.cams)))
+        pix.append((c, int(rng.integers(int(scene.cams[c]["width"]))), int(rng.integers(int(scene.cams[c]["height"])))))
+    pix = np.array(pix, dtype=np.int32)
+    t0 = time.perf_counter()
+    r = oracle.render(scene, pixels=pix, bands=None)
+    g = 2.0 * (r["rgb"] - 0.5)
+    oracle.backward(scene, g, pixels=pix)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(scene, target_seconds):
+    oracle_sample_time(scene, 4)  # build + warm
+    t_small = oracle_sample_time(scene, 32)
+    per_px = max(t_small / 32, 1e-6)
+    n = int(max(64, min(200000, target_seconds / per_px)))
+    t = oracle_sample_time(scene, n, seed=1)
+    return {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
+                      f"(single thread), {t:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    scene = WORKLOADS[args.workload]()
+    n_pix = args.ref_pixels
+    for _ in range(args.warmup):
+        oracle_sample_time(scene, max(8, n_pix // 8))
+    ts = [oracle_sample_time(scene, n_pix, seed=k + 1) for k in range(args.steps)]
+    total = sum(ts)
+    value = n_pix * args.steps / total / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "step": f"oracle fwd+bwd on {n_pix} random pixels"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{n_pix} random pixels per step, FP64 brute force, single thread"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gmr(args, ws, rank, local):
+    import torch
+
+    from paper_2602_14493_b300 import Renderer, camera_array
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene = WORKLOADS[args.workload]()
+    C, F = len(scene.cams), len(scene.faces)
+    n_pix = scene.n_pixels
+
+    v = torch.from_numpy(scene.verts).to(dev)
+    f = torch.from_numpy(scene.faces).to(dev)
+    c = torch.from_numpy(scene.rgb).to(dev)
+    o = torch.from_numpy(scene.opacity).to(dev)
+    cams = camera_array(scene.cams)
+
+    r = Renderer(tile=args.tile, batch=args.batch, profile=True)
+    # target: render of the jittered mesh
+    vt = torch.from_numpy(scene.extra["target_verts"]).to(dev)
+    target, _ = r.forward(vt, f, c, o, cams, want_t=False)
+    target = target.clone()
+    img, _ = r.forward(v, f, c, o, cams, want_t=False)
+    torch.cuda.synchronize()
+    P = r.stats()["n_pairs"]
+    r.reserve(F, C, n_pix, int(P * 1.3) + 4096)
+    r.set_config(sync_check=False)
+    stream = torch.cuda.Stream(dev)
+    img = torch.empty((n_pix, 3), device=dev)
+    grad = torch.empty_like(img)
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    dv, dc, do = torch.empty_like(v), torch.empty_like(c), torch.empty_like(o)
+
+    def step(s):
+        r.forward(v, f, c, o, cams, images=img, want_t=False, stream=s)
+        r.l2_loss(img, target, grad, loss, stream=s)
+        r.backward(grad, dv, dc, do, stream=s)
+
+    with torch.cuda.stream(stream):
+        step(stream)
+    stream.synchronize()
+    l0 = r.stats()["launches"]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step(stream)
+    launches_per_step = r.stats()["launches"] - l0
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    st = r.stats()
+    if r.device_status() != 0:
+        raise RuntimeError("device status bits set during warm-up")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_acc = {}
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+        times = r.stage_times(stream)
+        for name, ms in times.items():
+            if ms is not None:
+                stage_acc.setdefault(name, []).append(ms)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t_wall1 = time.perf_counter()
+    sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    total_s_max = max_over_ranks(total_s, ws)
+    value = ws * n_pix * args.steps / total_s_max / 1e6
+    ms_per_step = 1e3 * total_s_max / args.steps
+    status = r.device_status()
+
+    # per-view form: one call per view (eager, same workspace)
+    pv_steps = max(3, min(args.steps, 30))
+    cams_k = [camera_array(scene.cams[k:k + 1]) for k in range(C)]
+    with torch.cuda.stream(stream):
+        off = np.concatenate([[0], np.cumsum([int(cm.width) * int(cm.height) for cm in cams])])
+
+        def per_view_step():
+            for k in range(C):
+                sl = slice(int(off[k]), int(off[k + 1]))
+                r.forward(v, f, c, o, cams_k[k], images=img[sl], want_t=False, stream=stream)
+                r.l2_loss(img[sl], target[sl], grad[sl], loss, stream=stream)
+                r.backward(grad[sl], dv, dc, do, accumulate=(k > 0), stream=stream)
+
+        for _ in range(2):
+            per_view_step()
+        stream.synchronize()
+        pv_ev = []
+        for _ in range(pv_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            per_view_step()
+            b.record(stream)
+            flush.zero_()
+            pv_ev.append((a, b))
+        stream.synchronize()
+        pv_ms = statistics.mean(a.elapsed_time(b) for a, b in pv_ev)
+        # batched, eager (no graph)
+        be_ev = []
+        for _ in range(pv_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(stream)
+            b.record(stream)
+            flush.zero_()
+            be_ev.append((a, b))
+        stream.synchronize()
+        be_ms = statistics.mean(a.elapsed_time(b) for a, b in be_ev)
+
+    # end to end through the public API with host buffers
+    h_v = torch.from_numpy(scene.verts).pin_memory()
+    h_f = torch.from_numpy(scene.faces).pin_memory()
+    h_c = torch.from_numpy(scene.rgb).pin_memory()
+    h_o = torch.from_numpy(scene.opacity).pin_memory()
+    h_t = target.cpu().pin_memory()
+    h_loss = torch.empty((), dtype=torch.float64).pin_memory()
+    h_dv, h_dc, h_do = (torch.empty(x.shape, dtype=torch.float32).pin_memory() for x in (v, c, o))
+    d_v, d_f, d_c, d_o, d_t = (torch.empty_like(x, device=dev) for x in (h_v, h_f, h_c, h_o, h_t))
+    h2d = sum(x.numel() * x.element_size() for x in (h_v, h_f, h_c, h_o, h_t))
+    d2h = sum(x.numel() * x.element_size() for x in (h_loss, h_dv, h_dc, h_do))
+    e2e_steps = max(3, min(args.steps, 30))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for d, h in ((d_v, h_v), (d_f, h_f), (d_c, h_c), (d_o, h_o), (d_t, h_t)):
+                d.copy_(h, non_blocking=True)
+            r.forward(d_v, d_f, d_c, d_o, cams, images=img, want_t=False, stream=stream)
+            r.l2_loss(img, d_t, grad, loss, stream=stream)
+            r.backward(grad, dv, dc, do, stream=stream)
+            for h, d in ((h_loss, loss), (h_dv, dv), (h_dc, dc), (h_do, do)):
+                h.copy_(d, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(e2e_s, ws)
+
+    if rank != 0:
+        return
+    stats = r.stats()
+    peaks, peak_kind = measured_peaks()
+    stage_ms = {k: statistics.mean(vs) for k, vs in stage_acc.items()}
+    kern = {k: vv for k, vv in stage_ms.items() if k != "loss"}
+    if kern:
+        dom = max(kern, key=kern.get)
+        roof = roofline_for(dom, stage_ms[dom], stats, scene, peaks, peak_kind, args)
+    else:
+        roof = None
+        log("no stage times were recorded")
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
+                   "form": "batched, one call for all views, CUDA graph", "tile": args.tile,
+                   "batch": args.batch, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "per_view": {"value": n_pix / (pv_ms / 1e3) / 1e6, "ms_per_step": pv_ms, "form": "one call per view, eager"},
+        "batched_eager": {"value": n_pix / (be_ms / 1e3) / 1e6, "ms_per_step": be_ms},
+        "stages_ms": {k: round(vv, 5) for k, vv in stage_ms.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * n_pix / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
+        "gpu_launches": launches_per_step * args.steps,
+        "launches_per_step": launches_per_step,
+        "clocks": sampler.summary(t_wall0, t_wall1),
+        "counters": {"pairs": stats["n_pairs"], "evals_fwd": stats["evals_fwd"], "evals_bwd": stats["evals_bwd"],
+                     "contribs": stats["contribs"]},
+        "device_status": status,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
+    """Roofline entry of the dominant kernel from its live event time."""
+    E_f, E_b, K = stats["evals_fwd"], stats["evals_bwd"], stats["contribs"]
+    if stage in ("raster_fwd", "raster_bwd"):
+        flops = (FLOPS_EVAL * E_f + FLOPS_FWD_CONTRIB * K) if stage == "raster_fwd" else \
+                (FLOPS_EVAL * E_b + FLOPS_BWD_CONTRIB * K)
+        ach = flops / (ms / 1e3) / 1e12
+        return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((stage, args.workload)),
+                "peak_source": "FP32 CUDA-core peak from unit counts and max clock (148 SM x 128 x 2 x 2.032 GHz)",
+                "ms": ms}
+    # memory-bound stages: algorithmic bytes
+    R = stats["n_records"]
+    P = stats["n_pairs"]
+    byts = {"project": R * 64 + len(scene.faces) * 28, "sort_records": R * 8 * 2 * 4,
+            "scan": R * 12, "emit": P * 8 + R * 16, "sort_pairs": P * 8 * 2 * 2, "ranges": P * 4,
+            "project_bwd": R * 32 + len(scene.faces) * 52}.get(stage, 0)
+    ach = byts / (ms / 1e3) / 1e9
+    pk = peaks["hbm_gbs"]
+    return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+            "traffic": NCU_TRAFFIC.get((stage, args.workload)), "peak_source": peak_kind, "ms": ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gmr", choices=["gmr", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-pixels", type=int, default=256)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_gmr(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

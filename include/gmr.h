@@ -1,0 +1,249 @@
+/*
+ * gmr.h -- C ABI of the Gaussian Mesh Renderer hot path (CUDA, sm_103a).
+ *
+ * The library turns every triangle of a mesh into one planar 3D Gaussian
+ * (paper Sec. 2.2, Eq. 3-16) and renders those Gaussians with 3DGS-style tile
+ * rasterization (Sec. 2.1): EWA projection to the image plane, binning into
+ * screen tiles sorted by (tile, depth, face index), and front-to-back alpha
+ * compositing. The backward pass returns dL/d(vertex positions) and
+ * dL/d(per-face or per-vertex colour, per-face opacity) from dL/d(image).
+ *
+ * Conventions for every entry point
+ *  - Array arguments are DEVICE pointers unless stated otherwise, contiguous,
+ *    FP32 (or int32 for indices), owned by the caller and never freed or
+ *    retained by the library beyond what is stated.
+ *  - Work is enqueued asynchronously on the given stream; outputs are valid
+ *    once that stream reaches the call's end. A NULL stream is the legacy
+ *    default stream.
+ *  - Errors found on the host are returned at once and nothing is enqueued.
+ *    Errors found on the device (face index out of range, pair buffer too
+ *    small) set bits of a device status word that gmr_get_device_status()
+ *    returns; no kernel traps, asserts or spins without bound.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Images are packed view after view; view c occupies pixels
+ *    [off[c], off[c+1]) of the packed buffer (see gmr_image_offsets), rows
+ *    top to bottom, 3 floats (RGB) per pixel.
+ */
+#ifndef GMR_H_
+#define GMR_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GMR_API __attribute__((visibility("default")))
+#else
+#define GMR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t / CUstream. */
+typedef struct CUstream_st* gmr_stream;
+
+typedef enum {
+  GMR_OK = 0,
+  GMR_ERR_INVALID_ARG = 1, /* bad pointer, size, configuration or face index */
+  GMR_ERR_CUDA = 2,        /* a CUDA runtime call failed; see gmr_last_error */
+  GMR_ERR_OOM = 3,         /* device allocation of the workspace failed */
+  GMR_ERR_CAPACITY = 4,    /* a workspace buffer was too small (no-sync mode) */
+  GMR_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+  GMR_ERR_STATE = 6        /* call order: e.g. backward without a forward */
+} gmr_status;
+
+/* Device status bits reported by gmr_get_device_status. */
+#define GMR_DEV_BAD_FACE_INDEX 1u /* a face referenced a vertex outside [0, V) */
+#define GMR_DEV_PAIR_OVERFLOW 2u  /* more (tile, Gaussian) pairs than capacity */
+
+/* Sec. 2.2: which 3D covariance a facet becomes. */
+typedef enum {
+  GMR_COV_AREA = 0,     /* Eq. 13: area-matched scales kappa*lambda, s_z = 1e-6 */
+  GMR_COV_EMBED_RAW = 1 /* Eq. 15 literally: Sigma2D embedded, zero normal variance */
+} gmr_cov_mode;
+
+/* Sec. 2.2, colour assignment. */
+typedef enum {
+  GMR_COLOR_PER_FACE = 0,  /* rgb is F x 3 */
+  GMR_COLOR_PER_VERTEX = 1 /* rgb is V x 3; face colour = mean of its 3 vertices (Eq. 16) */
+} gmr_color_mode;
+
+/* Pinhole camera (76 bytes, no padding). World-to-camera rotation R
+ * (row-major) and translation t: x_cam = R x + t; OpenCV axes (x right, y
+ * down, z forward); pixel (px, py) has its centre at (px + 0.5, py + 0.5);
+ * u = fx * x/z + cx, v = fy * y/z + cy. Faces whose centroid depth is not
+ * above znear are culled. */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float znear;
+} gmr_camera;
+
+/* Renderer configuration. Compositing constants are those of the standard
+ * 3DGS rasterizer the paper renders with (Sec. 2.1): alpha = min(0.99,
+ * o * G), Gaussians with alpha < 1/255 are skipped, a pixel stops before the
+ * Gaussian that would take its transmittance below 1e-4, and a 0.3 px^2
+ * low-pass term is added to every projected covariance. */
+typedef struct {
+  int32_t tile;       /* tile edge in pixels: 16 or 32 */
+  int32_t batch;      /* Gaussians staged per shared-memory batch: 64, 128 or 256 */
+  int32_t cov_mode;   /* gmr_cov_mode */
+  int32_t color_mode; /* gmr_color_mode */
+  float bg[3];        /* background colour added as T_final * bg */
+  int32_t flags;      /* GMR_FLAG_* */
+} gmr_config;
+
+/* With this flag the forward reads the pair count back to the host once
+ * (one stream synchronisation) and grows the pair buffers when needed.
+ * Without it the forward never synchronises (it may be captured in a CUDA
+ * graph) and an undersized buffer sets GMR_DEV_PAIR_OVERFLOW instead. */
+#define GMR_FLAG_SYNC_CHECK 1
+
+/* With this flag every stage of the forward and backward is bracketed by
+ * CUDA events on the call's stream (also inside a captured graph), and
+ * gmr_get_stage_times returns their durations. */
+#define GMR_FLAG_PROFILE 2
+
+/* Stages timed under GMR_FLAG_PROFILE (paper step in brackets). */
+typedef enum {
+  GMR_STAGE_PROJECT = 0,      /* face colours + conversion fused with EWA projection (Sec. 2.2, 2.1) */
+  GMR_STAGE_SORT_RECORDS = 1, /* Gaussians by depth key */
+  GMR_STAGE_SCAN = 2,         /* tiles per Gaussian -> pair offsets */
+  GMR_STAGE_EMIT = 3,         /* (tile, Gaussian) pairs */
+  GMR_STAGE_SORT_PAIRS = 4,   /* pairs by tile id */
+  GMR_STAGE_RANGES = 5,       /* per-tile [start, end) */
+  GMR_STAGE_RASTER_FWD = 6,   /* front-to-back compositing */
+  GMR_STAGE_LOSS = 7,         /* gmr_l2_loss */
+  GMR_STAGE_RASTER_BWD = 8,   /* compositing backward */
+  GMR_STAGE_PROJECT_BWD = 9,  /* projection + conversion backward, vertex scatter */
+  GMR_NUM_STAGES = 10
+} gmr_stage;
+
+typedef struct gmr_ctx gmr_ctx;
+
+/* Counters of the last forward/backward (host copies; see gmr_get_stats). */
+typedef struct {
+  int64_t n_records;     /* views x faces */
+  int64_t n_pairs;       /* (tile, Gaussian) pairs of the last forward */
+  int64_t n_tiles;       /* tiles over all views */
+  int64_t n_pixels;      /* pixels over all views */
+  int64_t evals_fwd;     /* (pixel, Gaussian) evaluations, last forward */
+  int64_t evals_bwd;     /* (pixel, Gaussian) evaluations, last backward */
+  int64_t contribs;      /* (pixel, Gaussian) pairs that contributed, last forward */
+  int64_t launches;      /* kernels launched by this context since creation */
+  int64_t pair_capacity; /* current pair buffer capacity */
+} gmr_stats;
+
+/* Fills *cfg with the defaults: tile 16, batch 256, GMR_COV_AREA,
+ * GMR_COLOR_PER_FACE, black background, GMR_FLAG_SYNC_CHECK. */
+GMR_API gmr_status gmr_config_default(gmr_config* cfg);
+
+/* Creates a context on the current CUDA device. The context owns its
+ * workspace (device memory, grown on demand outside stream capture) and the
+ * forward state that gmr_render_bwd consumes. cfg may be NULL (defaults). */
+GMR_API gmr_status gmr_create(const gmr_config* cfg, gmr_ctx** out);
+
+/* Frees the context and its workspace. The caller must make sure no work
+ * using the context is still running. */
+GMR_API gmr_status gmr_destroy(gmr_ctx* ctx);
+
+/* Replaces the configuration (validated). Invalidates the forward state. */
+GMR_API gmr_status gmr_set_config(gmr_ctx* ctx, const gmr_config* cfg);
+
+/* Message of the last host-side error of this context ("" if none). */
+GMR_API const char* gmr_last_error(const gmr_ctx* ctx);
+
+/* Name of a status code. */
+GMR_API const char* gmr_status_string(gmr_status s);
+
+/* Packed image layout: offsets[c] = first pixel of view c, offsets[C] =
+ * total pixels. cams and offsets are HOST arrays. */
+GMR_API gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t* offsets);
+
+/* Pre-sizes the workspace for up to max_faces faces, max_views views,
+ * max_pixels total pixels and max_pairs (tile, Gaussian) pairs, so that
+ * later calls within these limits allocate nothing (needed before stream
+ * capture). */
+GMR_API gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels,
+                       int64_t max_pairs);
+
+/* Mesh-to-Gaussian conversion alone (Sec. 2.2, Eq. 3-16).
+ *  verts   V x 3, faces F x 3 (int32 vertex indices in [0, V)),
+ *  rgb     F x 3 (per-face mode) or V x 3 (per-vertex mode, Eq. 16),
+ *  opacity F per-face opacities, or NULL for 1 (the paper's o = 1);
+ *          values are clamped to [0, 1].
+ * Outputs (any may be NULL): means F x 3 (centroid, Eq. 3-4), cov F x 6
+ * (xx, xy, xz, yy, yz, zz of Eq. 13 or Eq. 15 per cov_mode), face_rgb F x 3
+ * (Eq. 16), face_opacity F. Faces with an index outside [0, V) set
+ * GMR_DEV_BAD_FACE_INDEX and get zero outputs. */
+GMR_API gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                       const float* rgb, const float* opacity, float* means, float* cov, float* face_rgb,
+                       float* face_opacity, gmr_stream stream);
+
+/* Forward render of C views (Sec. 2.1-2.2): conversion fused with EWA
+ * projection, binning, sorting by (tile, depth, face), compositing.
+ *  cams     HOST array of C cameras (copied; under stream capture they must
+ *           equal those of the previous call on this context).
+ *  images   packed RGB output, offsets[C] x 3 floats.
+ *  t_final  packed final transmittance, offsets[C] floats, or NULL.
+ * verts, faces, rgb and opacity must stay valid and unchanged until the
+ * matching gmr_render_bwd has been enqueued. C = 1 in a loop is the
+ * per-view form; one call with all views is the batched form. */
+GMR_API gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                          const float* rgb, const float* opacity, const gmr_camera* cams, int32_t C,
+                          float* images, float* t_final, gmr_stream stream);
+
+/* Backward of the last forward on this context. The per-pixel compositing is
+ * recomputed back to front from the stored final transmittance and last
+ * contributor; no per-pixel lists are kept.
+ *  dL_dimages    packed, same layout as images.
+ *  dL_dverts     V x 3 (may be NULL).
+ *  dL_drgb       shape of rgb (may be NULL).
+ *  dL_dopacity   F (may be NULL; ignored when the forward had opacity NULL).
+ *  accumulate    0: outputs are overwritten; 1: gradients are added to them.
+ */
+GMR_API gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dverts, float* dL_drgb,
+                          float* dL_dopacity, int32_t accumulate, gmr_stream stream);
+
+/* Squared-error loss sum((img - target)^2) over n floats and its gradient
+ * 2 (img - target). loss is a device double (overwritten); dL_dimg may
+ * alias neither input. Deterministic (fixed reduction order). */
+GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int64_t n, float* dL_dimg,
+                       double* loss, gmr_stream stream);
+
+/* Synchronises the stream, returns and clears the device status bits
+ * (GMR_DEV_*) accumulated since the last call. */
+GMR_API gmr_status gmr_get_device_status(gmr_ctx* ctx, gmr_stream stream, uint32_t* status);
+
+/* Synchronises the stream and returns the counters. */
+GMR_API gmr_status gmr_get_stats(gmr_ctx* ctx, gmr_stream stream, gmr_stats* out);
+
+/* Synchronises the stream and writes, for each gmr_stage, the duration in
+ * milliseconds between its two events as last recorded (eagerly or by a
+ * replayed graph captured under GMR_FLAG_PROFILE); -1 for a stage that never
+ * ran under profiling. ms has GMR_NUM_STAGES entries. */
+GMR_API gmr_status gmr_get_stage_times(gmr_ctx* ctx, gmr_stream stream, float* ms);
+
+/* Introspection of the last forward, for tests (device outputs, copied on
+ * the stream):
+ *  depth_bits  C*F   FP32 depth key bits per (view, face), view-major
+ *  rects       C*F*4 inclusive tile rectangle (x0, x1, y0, y1); x0 > x1 when
+ *                    the Gaussian is culled or off-screen
+ *  tile_ids, face_ids  n_pairs sorted pairs (cap entries available)
+ *  ranges      n_tiles*2 [start, end) per global tile
+ *  rec_u       C*F*4 image-plane mean as (x_hi, y_hi, x_lo, y_lo), the mean
+ *                    being x_hi + x_lo (float pair)
+ *  rec_conic   C*F*4 (a, b, c, 0) of the conic Sigma'^-1 = [[a, b], [b, c]]
+ *  n_last      n_pixels  list position + 1 of the last contributor
+ * Any pointer may be NULL. n_pairs (host) receives the pair count. */
+GMR_API gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* rects, uint32_t* tile_ids,
+                                   uint32_t* face_ids, int64_t cap, uint32_t* ranges, float* rec_u,
+                                   float* rec_conic, uint32_t* n_last, int64_t* n_pairs, gmr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMR_H_ */

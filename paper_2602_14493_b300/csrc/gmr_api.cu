@@ -1,0 +1,621 @@
+// C ABI entry points (include/gmr.h): context, workspace, argument checks and
+// the order of the kernels of one forward / backward.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gmr_internal.cuh"
+
+using gmr::Counters;
+using gmr::ViewInfo;
+using gmr::Workspace;
+
+struct gmr_ctx {
+  gmr_config cfg;
+  int device = 0;
+  Workspace ws;
+  std::string err;
+  int64_t launches = 0;
+  // cameras of the last upload
+  std::vector<gmr_camera> cams;
+  std::vector<ViewInfo> views;
+  ViewInfo* views_pinned = nullptr;
+  int32_t views_pinned_cap = 0;
+  cudaEvent_t upload_done = nullptr;
+  Counters* counters_pinned = nullptr;
+  // stage events (GMR_FLAG_PROFILE)
+  cudaEvent_t stage_ev[2 * GMR_NUM_STAGES] = {};
+  uint32_t stage_mask = 0;
+  // forward state consumed by the backward
+  bool fwd_valid = false;
+  const float* verts = nullptr;
+  const int32_t* faces = nullptr;
+  const float* rgb = nullptr;
+  const float* opacity = nullptr;
+  int32_t V = 0, F = 0, C = 0;
+  int64_t n_tiles = 0, n_pixels = 0;
+  int pair_buf = 0, rec_buf = 0;
+  gmr_config fwd_cfg;
+};
+
+namespace {
+
+gmr_status fail(gmr_ctx* ctx, gmr_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+gmr_status cuda_fail(gmr_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, GMR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GMR_CUDA(ctx, call)                                      \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+  } while (0)
+
+bool valid_config(const gmr_config* c, std::string* why) {
+  if (c->tile != 16 && c->tile != 32) { *why = "tile must be 16 or 32"; return false; }
+  if (c->batch != 64 && c->batch != 128 && c->batch != 256) { *why = "batch must be 64, 128 or 256"; return false; }
+  if (c->cov_mode != GMR_COV_AREA && c->cov_mode != GMR_COV_EMBED_RAW) { *why = "bad cov_mode"; return false; }
+  if (c->color_mode != GMR_COLOR_PER_FACE && c->color_mode != GMR_COLOR_PER_VERTEX) {
+    *why = "bad color_mode";
+    return false;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->bg[k])) { *why = "background must be finite"; return false; }
+  return true;
+}
+
+// Grow a device buffer to at least `need` elements (geometric growth).
+template <class T>
+gmr_status grow(gmr_ctx* ctx, T** ptr, int64_t* cap, int64_t need, bool capturing, const char* what) {
+  if (need <= *cap) return GMR_OK;
+  if (capturing)
+    return fail(ctx, GMR_ERR_STATE,
+                std::string("workspace '") + what + "' must grow during stream capture; call gmr_reserve first");
+  int64_t ncap = need + need / 4 + 1024;
+  T* p = nullptr;
+  cudaError_t e = cudaMalloc((void**)&p, (size_t)ncap * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, GMR_ERR_OOM, std::string("cudaMalloc of workspace '") + what + "' failed");
+  }
+  if (*ptr) cudaFree(*ptr);
+  *ptr = p;
+  *cap = ncap;
+  return GMR_OK;
+}
+
+// Capacity groups: records (2 ping-pong arrays share one capacity).
+gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_records) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "record workspace must grow during stream capture; call gmr_reserve");
+  int64_t c0 = w.cap_records;
+  int64_t cap;
+  gmr_status s;
+#define G(field, T)                                              \
+  cap = c0;                                                      \
+  s = grow<T>(ctx, &w.field, &cap, n, false, #field);            \
+  if (s != GMR_OK) return s;
+  G(rec_u, float4);
+  G(rec_q, float4);
+  G(rec_rect, uint2);
+  G(rec_ntiles, uint32_t);
+  G(rec_key[0], uint32_t);
+  G(rec_key[1], uint32_t);
+  G(rec_id[0], uint32_t);
+  G(rec_id[1], uint32_t);
+  G(rec_off, uint32_t);
+#undef G
+  int64_t gcap = 2 * c0;
+  s = grow<float4>(ctx, &w.rec_grad, &gcap, 2 * n, false, "rec_grad");
+  if (s != GMR_OK) return s;
+  w.cap_records = cap;
+  return GMR_OK;
+}
+
+gmr_status ensure_scratch(gmr_ctx* ctx, int64_t n_items, bool capturing) {
+  Workspace& w = ctx->ws;
+  int64_t ncounts = gmr::radix_counts_needed(n_items);
+  gmr_status s = grow<uint32_t>(ctx, &w.radix_counts, &w.cap_counts, ncounts, capturing, "radix_counts");
+  if (s != GMR_OK) return s;
+  int64_t nscan = std::max(gmr::scan_block_sums_needed(n_items), gmr::scan_block_sums_needed(ncounts));
+  return grow<uint32_t>(ctx, &w.scan_tmp, &w.cap_scan, nscan, capturing, "scan_tmp");
+}
+
+gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_pairs) return GMR_OK;
+  if (n >= (int64_t)0x7fffffff) return fail(ctx, GMR_ERR_CAPACITY, "more than 2^31 - 1 (tile, Gaussian) pairs");
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "pair workspace must grow during stream capture; call gmr_reserve");
+  int64_t c0 = w.cap_pairs, cap;
+  gmr_status s;
+  for (int b = 0; b < 2; ++b) {
+    cap = c0;
+    if ((s = grow<uint32_t>(ctx, &w.pair_tile[b], &cap, n, false, "pair_tile")) != GMR_OK) return s;
+    cap = c0;
+    if ((s = grow<uint32_t>(ctx, &w.pair_face[b], &cap, n, false, "pair_face")) != GMR_OK) return s;
+  }
+  w.cap_pairs = cap;
+  return ensure_scratch(ctx, std::max(cap, w.cap_records), false);
+}
+
+// face_col and face_grad share one capacity.
+gmr_status ensure_faces(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_faces) return GMR_OK;
+  int64_t c0 = w.cap_faces, cap = c0;
+  gmr_status s = grow<float4>(ctx, &w.face_col, &cap, n, capturing, "face_col");
+  if (s != GMR_OK) return s;
+  int64_t cap2 = c0;
+  s = grow<float4>(ctx, &w.face_grad, &cap2, n, capturing, "face_grad");
+  if (s != GMR_OK) return s;
+  w.cap_faces = std::min(cap, cap2);
+  return GMR_OK;
+}
+
+gmr_status ensure_views(gmr_ctx* ctx, int32_t C, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (C <= w.cap_views) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "view table must grow during stream capture");
+  int64_t cap = w.cap_views;
+  gmr_status s = grow<ViewInfo>(ctx, &w.views, &cap, C, false, "views");
+  if (s != GMR_OK) return s;
+  w.cap_views = (int32_t)cap;
+  if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
+  ctx->views_pinned = nullptr;
+  cudaError_t e = cudaMallocHost((void**)&ctx->views_pinned, (size_t)cap * sizeof(ViewInfo));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost(views)");
+  ctx->views_pinned_cap = (int32_t)cap;
+  return GMR_OK;
+}
+
+// Brackets one stage with events when profiling is on.
+struct StageTimer {
+  gmr_ctx* ctx;
+  int stage;
+  cudaStream_t s;
+  bool on;
+  unsigned flags;
+  StageTimer(gmr_ctx* c, int st, cudaStream_t strm, const gmr_config& cfg)
+      : ctx(c), stage(st), s(strm), on((cfg.flags & GMR_FLAG_PROFILE) && c->stage_ev[0] != nullptr), flags(0) {
+    if (!on) return;
+    // under stream capture the records must become event-record nodes of the
+    // graph (external events), not capture-internal dependencies
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags(ctx->stage_ev[2 * stage], s, flags);
+  }
+  ~StageTimer() {
+    if (on) {
+      cudaEventRecordWithFlags(ctx->stage_ev[2 * stage + 1], s, flags);
+      ctx->stage_mask |= 1u << stage;
+    }
+  }
+};
+
+int bits_for(int64_t n) {
+  int b = 0;
+  while (b < 63 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+bool same_cams(const std::vector<gmr_camera>& a, const gmr_camera* b, int32_t C) {
+  return (int32_t)a.size() == C && std::memcmp(a.data(), b, sizeof(gmr_camera) * (size_t)C) == 0;
+}
+
+gmr_status check_cams(gmr_ctx* ctx, const gmr_camera* cams, int32_t C) {
+  for (int32_t c = 0; c < C; ++c) {
+    const gmr_camera& k = cams[c];
+    if (k.width <= 0 || k.height <= 0 || k.width > (1 << 20) || k.height > (1 << 20))
+      return fail(ctx, GMR_ERR_INVALID_ARG, "camera " + std::to_string(c) + ": bad image size");
+    const float* f = &k.R[0];
+    for (int q = 0; q < 16; ++q)
+      if (!std::isfinite(f[q])) return fail(ctx, GMR_ERR_INVALID_ARG, "camera " + std::to_string(c) + ": non-finite");
+    if (!std::isfinite(k.znear)) return fail(ctx, GMR_ERR_INVALID_ARG, "camera znear non-finite");
+  }
+  return GMR_OK;
+}
+
+// Builds the view table (tile and pixel bases) for the configured tile size.
+void build_views(gmr_ctx* ctx, const gmr_camera* cams, int32_t C, int64_t* n_tiles, int64_t* n_pixels) {
+  ctx->views.resize(C);
+  int64_t tb = 0, pb = 0;
+  int ts = ctx->cfg.tile;
+  for (int32_t c = 0; c < C; ++c) {
+    ViewInfo& v = ctx->views[c];
+    std::memcpy(v.R, cams[c].R, sizeof(v.R));
+    std::memcpy(v.t, cams[c].t, sizeof(v.t));
+    v.fx = cams[c].fx; v.fy = cams[c].fy; v.cx = cams[c].cx; v.cy = cams[c].cy; v.znear = cams[c].znear;
+    v.W = cams[c].width; v.H = cams[c].height;
+    v.tiles_x = (v.W + ts - 1) / ts;
+    v.tiles_y = (v.H + ts - 1) / ts;
+    v.tile_base = (int32_t)tb;
+    v.pix_base = pb;
+    tb += (int64_t)v.tiles_x * v.tiles_y;
+    pb += (int64_t)v.W * v.H;
+  }
+  *n_tiles = tb;
+  *n_pixels = pb;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gmr_status_string(gmr_status s) {
+  switch (s) {
+    case GMR_OK: return "GMR_OK";
+    case GMR_ERR_INVALID_ARG: return "GMR_ERR_INVALID_ARG";
+    case GMR_ERR_CUDA: return "GMR_ERR_CUDA";
+    case GMR_ERR_OOM: return "GMR_ERR_OOM";
+    case GMR_ERR_CAPACITY: return "GMR_ERR_CAPACITY";
+    case GMR_ERR_TIMEOUT: return "GMR_ERR_TIMEOUT";
+    case GMR_ERR_STATE: return "GMR_ERR_STATE";
+  }
+  return "GMR_UNKNOWN";
+}
+
+gmr_status gmr_config_default(gmr_config* cfg) {
+  if (!cfg) return GMR_ERR_INVALID_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->tile = 16;
+  cfg->batch = 256;
+  cfg->cov_mode = GMR_COV_AREA;
+  cfg->color_mode = GMR_COLOR_PER_FACE;
+  cfg->flags = GMR_FLAG_SYNC_CHECK;
+  return GMR_OK;
+}
+
+gmr_status gmr_create(const gmr_config* cfg, gmr_ctx** out) {
+  if (!out) return GMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  gmr_config c;
+  if (cfg) c = *cfg; else gmr_config_default(&c);
+  std::string why;
+  if (!valid_config(&c, &why)) return GMR_ERR_INVALID_ARG;
+  gmr_ctx* ctx = new gmr_ctx();
+  ctx->cfg = c;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->ws.counters, sizeof(Counters));
+  if (e == cudaSuccess) e = cudaMemset(ctx->ws.counters, 0, sizeof(Counters));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->counters_pinned, sizeof(Counters));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->upload_done, cudaEventDisableTiming);
+  for (int k = 0; k < 2 * GMR_NUM_STAGES && e == cudaSuccess; ++k) e = cudaEventCreate(&ctx->stage_ev[k]);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    gmr_destroy(ctx);
+    return GMR_ERR_CUDA;
+  }
+  *out = ctx;
+  return GMR_OK;
+}
+
+gmr_status gmr_destroy(gmr_ctx* ctx) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  Workspace& w = ctx->ws;
+  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key[0], w.rec_key[1], w.rec_id[0],
+                  w.rec_id[1], w.rec_off, w.rec_grad, w.face_col, w.face_grad, w.pix_T, w.pix_last,
+                  w.tile_range, w.pair_tile[0], w.pair_tile[1], w.pair_face[0], w.pair_face[1], w.scan_tmp,
+                  w.radix_counts, w.loss_part, w.views, w.counters};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
+  if (ctx->counters_pinned) cudaFreeHost(ctx->counters_pinned);
+  if (ctx->upload_done) cudaEventDestroy(ctx->upload_done);
+  for (int k = 0; k < 2 * GMR_NUM_STAGES; ++k)
+    if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
+  delete ctx;
+  return GMR_OK;
+}
+
+gmr_status gmr_set_config(gmr_ctx* ctx, const gmr_config* cfg) {
+  if (!ctx || !cfg) return fail(ctx, GMR_ERR_INVALID_ARG, "null argument");
+  std::string why;
+  if (!valid_config(cfg, &why)) return fail(ctx, GMR_ERR_INVALID_ARG, why);
+  ctx->cfg = *cfg;
+  ctx->fwd_valid = false;
+  ctx->cams.clear();  // tile bases depend on the tile size
+  return GMR_OK;
+}
+
+const char* gmr_last_error(const gmr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t* offsets) {
+  if (!cams || !offsets || C < 0) return GMR_ERR_INVALID_ARG;
+  int64_t p = 0;
+  for (int32_t c = 0; c < C; ++c) {
+    offsets[c] = p;
+    p += (int64_t)cams[c].width * cams[c].height;
+  }
+  offsets[C] = p;
+  return GMR_OK;
+}
+
+gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels, int64_t max_pairs) {
+  if (!ctx || max_faces < 0 || max_views < 0 || max_pixels < 0 || max_pairs < 0)
+    return fail(ctx, GMR_ERR_INVALID_ARG, "bad reserve sizes");
+  gmr_status s;
+  if ((s = ensure_records(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK) return s;
+  if ((s = ensure_faces(ctx, max_faces, false)) != GMR_OK) return s;
+  int64_t pc = ctx->ws.cap_pixels, pc2 = ctx->ws.cap_pixels;
+  if ((s = grow<float>(ctx, &ctx->ws.pix_T, &pc, max_pixels, false, "pix_T")) != GMR_OK) return s;
+  if ((s = grow<uint32_t>(ctx, &ctx->ws.pix_last, &pc2, max_pixels, false, "pix_last")) != GMR_OK) return s;
+  ctx->ws.cap_pixels = std::min(pc, pc2);
+  // tiles: at most one per 16x16 block plus one ragged tile per row/column and view
+  int64_t mt = max_pixels / 256 + 2 * (int64_t)max_views * 1024 + 16;
+  if ((s = grow<uint2>(ctx, &ctx->ws.tile_range, &ctx->ws.cap_tiles, mt, false, "tile_range")) != GMR_OK) return s;
+  if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
+  if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;
+  if ((s = ensure_scratch(ctx, std::max(ctx->ws.cap_pairs, ctx->ws.cap_records), false)) != GMR_OK) return s;
+  int64_t lp = gmr::l2_loss_partials_needed(3 * max_pixels);
+  return grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, lp, false, "loss_part");
+}
+
+gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                       const float* rgb, const float* opacity, float* means, float* cov, float* face_rgb,
+                       float* face_opacity, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (V < 0 || F < 0) return fail(ctx, GMR_ERR_INVALID_ARG, "negative size");
+  if (F > 0 && (!verts || !faces || V == 0)) return fail(ctx, GMR_ERR_INVALID_ARG, "null verts/faces");
+  if (face_rgb && !rgb && F > 0) return fail(ctx, GMR_ERR_INVALID_ARG, "face_rgb requested without rgb");
+  cudaStream_t s = (cudaStream_t)stream;
+  GMR_CUDA(ctx, gmr::launch_convert(verts, V, faces, F, rgb, opacity, ctx->cfg.cov_mode, ctx->cfg.color_mode, means,
+                                    cov, face_rgb, face_opacity, ctx->ws.counters, s, &ctx->launches));
+  return GMR_OK;
+}
+
+gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                          const float* rgb, const float* opacity, const gmr_camera* cams, int32_t C, float* images,
+                          float* t_final, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  ctx->fwd_valid = false;
+  if (V < 0 || F < 0) return fail(ctx, GMR_ERR_INVALID_ARG, "negative size");
+  if (C < 1 || C > gmr::kMaxViews) return fail(ctx, GMR_ERR_INVALID_ARG, "C must be in [1, 65535]");
+  if (!cams || !images) return fail(ctx, GMR_ERR_INVALID_ARG, "null cams or images");
+  if (F > 0 && (!verts || !faces || !rgb || V == 0)) return fail(ctx, GMR_ERR_INVALID_ARG, "null mesh input");
+  if ((int64_t)F * C >= (int64_t)0x7fffffff) return fail(ctx, GMR_ERR_INVALID_ARG, "views x faces >= 2^31");
+  gmr_status st = check_cams(ctx, cams, C);
+  if (st != GMR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+  const bool capturing = cap_status != cudaStreamCaptureStatusNone;
+  const gmr_config& cfg = ctx->cfg;
+  Workspace& w = ctx->ws;
+
+  // view table
+  const bool cams_same = same_cams(ctx->cams, cams, C);
+  if (!cams_same && capturing)
+    return fail(ctx, GMR_ERR_STATE, "cameras differ from the previous call during stream capture");
+  int64_t n_tiles, n_pixels;
+  build_views(ctx, cams, C, &n_tiles, &n_pixels);
+  if (n_tiles >= (int64_t)0x7fffffff) return fail(ctx, GMR_ERR_INVALID_ARG, "too many tiles");
+  const int64_t n_rec = (int64_t)F * C;
+
+  // workspace
+  if ((st = ensure_views(ctx, C, capturing)) != GMR_OK) return st;
+  if ((st = ensure_records(ctx, n_rec, capturing)) != GMR_OK) return st;
+  if ((st = ensure_faces(ctx, F, capturing)) != GMR_OK) return st;
+  {
+    int64_t pc = w.cap_pixels, pc2 = w.cap_pixels;
+    if ((st = grow<float>(ctx, &w.pix_T, &pc, n_pixels, capturing, "pix_T")) != GMR_OK) return st;
+    if ((st = grow<uint32_t>(ctx, &w.pix_last, &pc2, n_pixels, capturing, "pix_last")) != GMR_OK) return st;
+    w.cap_pixels = std::min(pc, pc2);
+  }
+  if ((st = grow<uint2>(ctx, &w.tile_range, &w.cap_tiles, n_tiles, capturing, "tile_range")) != GMR_OK) return st;
+  if ((st = ensure_scratch(ctx, std::max(n_rec, w.cap_pairs), capturing)) != GMR_OK) return st;
+
+  if (!cams_same) {
+    GMR_CUDA(ctx, cudaEventSynchronize(ctx->upload_done));
+    std::memcpy(ctx->views_pinned, ctx->views.data(), sizeof(ViewInfo) * (size_t)C);
+    GMR_CUDA(ctx, cudaMemcpyAsync(w.views, ctx->views_pinned, sizeof(ViewInfo) * (size_t)C, cudaMemcpyHostToDevice, s));
+    GMR_CUDA(ctx, cudaEventRecord(ctx->upload_done, s));
+    ctx->cams.assign(cams, cams + C);
+  }
+
+  // counters: pair total and forward evaluation counts
+  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->n_pairs, 0, sizeof(uint32_t), s));
+  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_fwd, 0, sizeof(unsigned long long), s));
+  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->contribs, 0, sizeof(unsigned long long), s));
+
+  // S1/S2: per-face attributes, then conversion + projection per (view, face)
+  {
+    StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
+    GMR_CUDA(ctx, gmr::launch_face_attrs(rgb, opacity, faces, F, V, cfg.color_mode, w.face_col, s, &ctx->launches));
+    GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, w.views, C, cfg.tile, cfg.cov_mode, w, s, &ctx->launches));
+  }
+  // S5a: records in ascending depth key (stable: view, face order kept)
+  cudaError_t e = cudaSuccess;
+  int rb;
+  {
+    StageTimer t(ctx, GMR_STAGE_SORT_RECORDS, s, cfg);
+    rb = gmr::radix_sort_pairs(w.rec_key, w.rec_id, nullptr, n_rec, 32, w.radix_counts, w.scan_tmp, s,
+                               &ctx->launches, &e);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "record sort");
+  // S3: pair offsets in sorted record order, total to the counters
+  {
+    StageTimer t(ctx, GMR_STAGE_SCAN, s, cfg);
+    GMR_CUDA(ctx, gmr::scan_exclusive(w.rec_ntiles, w.rec_id[rb], n_rec, w.rec_off, &w.counters->n_pairs,
+                                      w.scan_tmp, s, &ctx->launches));
+  }
+  if ((cfg.flags & GMR_FLAG_SYNC_CHECK) && !capturing) {
+    GMR_CUDA(ctx, cudaMemcpyAsync(&ctx->counters_pinned->n_pairs, &w.counters->n_pairs, sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, s));
+    GMR_CUDA(ctx, cudaStreamSynchronize(s));
+    int64_t P = ctx->counters_pinned->n_pairs;
+    if ((st = ensure_pairs(ctx, P, false)) != GMR_OK) return st;
+  }
+  // S4: emit (global tile, face) pairs
+  {
+    StageTimer t(ctx, GMR_STAGE_EMIT, s, cfg);
+    GMR_CUDA(ctx, cudaMemsetAsync(w.tile_range, 0, sizeof(uint2) * (size_t)n_tiles, s));
+    GMR_CUDA(ctx, gmr::launch_emit_pairs(w, w.rec_id[rb], n_rec, w.views, F, s, &ctx->launches));
+  }
+  // S5b: pairs by tile id (stable)
+  int pb;
+  {
+    StageTimer t(ctx, GMR_STAGE_SORT_PAIRS, s, cfg);
+    pb = gmr::radix_sort_pairs(w.pair_tile, w.pair_face, &w.counters->n_pairs, w.cap_pairs, bits_for(n_tiles),
+                               w.radix_counts, w.scan_tmp, s, &ctx->launches, &e);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pair sort");
+  // S6: tile ranges
+  {
+    StageTimer t(ctx, GMR_STAGE_RANGES, s, cfg);
+    GMR_CUDA(ctx, gmr::launch_tile_ranges(w.pair_tile[pb], w.counters, w.cap_pairs, w.tile_range, s,
+                                          &ctx->launches));
+  }
+  // S7: compositing
+  {
+    StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
+    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.batch, w, w.pair_face[pb], w.views, C, F, n_tiles, cfg.bg,
+                                         images, t_final, s, &ctx->launches));
+  }
+
+  ctx->fwd_valid = true;
+  ctx->verts = verts; ctx->faces = faces; ctx->rgb = rgb; ctx->opacity = opacity;
+  ctx->V = V; ctx->F = F; ctx->C = C;
+  ctx->n_tiles = n_tiles; ctx->n_pixels = n_pixels;
+  ctx->pair_buf = pb; ctx->rec_buf = rb;
+  ctx->fwd_cfg = cfg;
+  return GMR_OK;
+}
+
+gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dverts, float* dL_drgb,
+                          float* dL_dopacity, int32_t accumulate, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (!ctx->fwd_valid) return fail(ctx, GMR_ERR_STATE, "gmr_render_bwd without a preceding gmr_render_fwd");
+  if (!dL_dimages) return fail(ctx, GMR_ERR_INVALID_ARG, "null dL_dimages");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = ctx->ws;
+  const gmr_config& cfg = ctx->fwd_cfg;
+  const int32_t F = ctx->F, C = ctx->C, V = ctx->V;
+  const int64_t n_rec = (int64_t)F * C;
+  if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_grad, 0, sizeof(float4) * 2 * (size_t)n_rec, s));
+  if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
+  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, sizeof(unsigned long long), s));
+  if (!accumulate) {
+    if (dL_dverts && V > 0) GMR_CUDA(ctx, cudaMemsetAsync(dL_dverts, 0, sizeof(float) * 3 * (size_t)V, s));
+    if (dL_drgb && cfg.color_mode == GMR_COLOR_PER_VERTEX && V > 0)
+      GMR_CUDA(ctx, cudaMemsetAsync(dL_drgb, 0, sizeof(float) * 3 * (size_t)V, s));
+  }
+  // S8: compositing backward
+  {
+    StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
+    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.batch, w, w.pair_face[ctx->pair_buf], w.views, C, F,
+                                         ctx->n_tiles, cfg.bg, dL_dimages, s, &ctx->launches));
+  }
+  // S9: projection + conversion backward, vertex scatter
+  {
+    StageTimer t(ctx, GMR_STAGE_PROJECT_BWD, s, cfg);
+    GMR_CUDA(ctx, gmr::launch_project_bwd(ctx->verts, V, ctx->faces, F, w.views, C, cfg.cov_mode, cfg.color_mode,
+                                          ctx->opacity, w, dL_dverts, dL_drgb, dL_dopacity, accumulate, s,
+                                          &ctx->launches));
+  }
+  return GMR_OK;
+}
+
+gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int64_t n, float* dL_dimg,
+                       double* loss, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!img || !target || !dL_dimg)) || !loss)
+    return fail(ctx, GMR_ERR_INVALID_ARG, "bad loss arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+  gmr_status st = grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, std::max<int64_t>(1, gmr::l2_loss_partials_needed(n)),
+                               cap_status != cudaStreamCaptureStatusNone, "loss_part");
+  if (st != GMR_OK) return st;
+  StageTimer t(ctx, GMR_STAGE_LOSS, s, ctx->cfg);
+  GMR_CUDA(ctx, gmr::launch_l2_loss(img, target, n, dL_dimg, loss, ctx->ws.loss_part, ctx->ws.cap_loss, s,
+                                    &ctx->launches));
+  return GMR_OK;
+}
+
+gmr_status gmr_get_device_status(gmr_ctx* ctx, gmr_stream stream, uint32_t* status) {
+  if (!ctx || !status) return GMR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  GMR_CUDA(ctx, cudaMemcpyAsync(&ctx->counters_pinned->status, &ctx->ws.counters->status, sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, s));
+  GMR_CUDA(ctx, cudaMemsetAsync(&ctx->ws.counters->status, 0, sizeof(uint32_t), s));
+  GMR_CUDA(ctx, cudaStreamSynchronize(s));
+  *status = ctx->counters_pinned->status;
+  return GMR_OK;
+}
+
+gmr_status gmr_get_stats(gmr_ctx* ctx, gmr_stream stream, gmr_stats* out) {
+  if (!ctx || !out) return GMR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  GMR_CUDA(ctx, cudaMemcpyAsync(ctx->counters_pinned, ctx->ws.counters, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  GMR_CUDA(ctx, cudaStreamSynchronize(s));
+  out->n_records = (int64_t)ctx->F * ctx->C;
+  out->n_pairs = ctx->counters_pinned->n_pairs;
+  out->n_tiles = ctx->n_tiles;
+  out->n_pixels = ctx->n_pixels;
+  out->evals_fwd = (int64_t)ctx->counters_pinned->evals_fwd;
+  out->evals_bwd = (int64_t)ctx->counters_pinned->evals_bwd;
+  out->contribs = (int64_t)ctx->counters_pinned->contribs;
+  out->launches = ctx->launches;
+  out->pair_capacity = ctx->ws.cap_pairs;
+  return GMR_OK;
+}
+
+gmr_status gmr_get_stage_times(gmr_ctx* ctx, gmr_stream stream, float* ms) {
+  if (!ctx || !ms) return GMR_ERR_INVALID_ARG;
+  GMR_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  for (int k = 0; k < GMR_NUM_STAGES; ++k) {
+    ms[k] = -1.0f;
+    if (!(ctx->stage_mask & (1u << k))) continue;
+    float t = -1.0f;
+    if (cudaEventElapsedTime(&t, ctx->stage_ev[2 * k], ctx->stage_ev[2 * k + 1]) == cudaSuccess) ms[k] = t;
+    else cudaGetLastError();
+  }
+  return GMR_OK;
+}
+
+gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* rects, uint32_t* tile_ids,
+                                   uint32_t* face_ids, int64_t cap, uint32_t* ranges, float* rec_u, float* rec_conic,
+                                   uint32_t* n_last, int64_t* n_pairs, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (!ctx->fwd_valid) return fail(ctx, GMR_ERR_STATE, "no forward state");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = ctx->ws;
+  const int64_t n_rec = (int64_t)ctx->F * ctx->C;
+  GMR_CUDA(ctx, cudaMemcpyAsync(&ctx->counters_pinned->n_pairs, &w.counters->n_pairs, sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, s));
+  GMR_CUDA(ctx, cudaStreamSynchronize(s));
+  int64_t P = ctx->counters_pinned->n_pairs;
+  if (n_pairs) *n_pairs = P;
+  if (n_rec > 0 && (depth_bits || rects || rec_conic)) {
+    GMR_CUDA(ctx, gmr::launch_debug_records(w, w.rec_key[ctx->rec_buf], w.rec_id[ctx->rec_buf], n_rec, depth_bits,
+                                            rects, rec_conic, s, &ctx->launches));
+  }
+  if (rec_u && n_rec > 0)
+    GMR_CUDA(ctx, cudaMemcpyAsync(rec_u, w.rec_u, sizeof(float4) * (size_t)n_rec, cudaMemcpyDeviceToDevice, s));
+  if ((tile_ids || face_ids) && P > cap) return fail(ctx, GMR_ERR_CAPACITY, "cap smaller than the pair count");
+  if (P > w.cap_pairs) return fail(ctx, GMR_ERR_CAPACITY, "pair buffer overflowed in the forward");
+  if (tile_ids && P > 0)
+    GMR_CUDA(ctx, cudaMemcpyAsync(tile_ids, w.pair_tile[ctx->pair_buf], sizeof(uint32_t) * (size_t)P,
+                                  cudaMemcpyDeviceToDevice, s));
+  if (face_ids && P > 0)
+    GMR_CUDA(ctx, cudaMemcpyAsync(face_ids, w.pair_face[ctx->pair_buf], sizeof(uint32_t) * (size_t)P,
+                                  cudaMemcpyDeviceToDevice, s));
+  if (ranges)
+    GMR_CUDA(ctx, cudaMemcpyAsync(ranges, w.tile_range, sizeof(uint2) * (size_t)ctx->n_tiles,
+                                  cudaMemcpyDeviceToDevice, s));
+  if (n_last && ctx->n_pixels > 0)
+    GMR_CUDA(ctx, cudaMemcpyAsync(n_last, w.pix_last, sizeof(uint32_t) * (size_t)ctx->n_pixels,
+                                  cudaMemcpyDeviceToDevice, s));
+  return GMR_OK;
+}
+
+}  // extern "C"

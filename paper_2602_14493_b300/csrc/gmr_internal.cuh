@@ -1,0 +1,249 @@
+// Internal declarations of the Gaussian Mesh Renderer CUDA library.
+// Device helpers shared by the kernels, the per-view table, the workspace
+// and the launchers' prototypes. Not part of the public ABI (include/gmr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gmr.h"
+
+namespace gmr {
+
+// ---------------------------------------------------------------- constants
+// 3DGS compositing constants (Sec. 2.1 renders with the standard 3DGS
+// rasterizer; the values are that rasterizer's).
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;
+// Eq. 12: epsilon clamp of lambda1 lambda2, and s_z.
+constexpr float kEps = 1e-14f;
+constexpr float kSz = 1e-6f;
+constexpr float kPi = 3.14159265358979f;
+// kappa = 6 sqrt(3) / pi when lambda1 lambda2 = |A|^2/108 >= eps.
+constexpr float kKappa = 3.30797337f;
+// Binning spec constants, FP32: 2 ln 255 and kappa / 18.
+constexpr float kTwoLn255 = 11.0825271606445312f;
+constexpr float kKappaOver18 = 0.18377630412578583f;
+// -log2(e)/2, -log2(e), ln 2: the conic is stored pre-scaled so that
+// o * 2^(a2 dx^2 + b2 dx dy + c2 dy^2) = o * exp(-1/2 d^T Q d).
+constexpr float kNegHalfLog2e = -0.72134752044448170f;
+constexpr float kNegLog2e = -1.44269504088896340f;
+constexpr float kLn2 = 0.69314718055994531f;
+
+constexpr int kMaxViews = 65535;
+
+// ---------------------------------------------------------------- view table
+struct ViewInfo {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy, znear;
+  int32_t W, H, tiles_x, tiles_y;
+  int32_t tile_base;  // first global tile id of this view
+  int64_t pix_base;   // first packed pixel of this view
+};
+
+// Device status bits (mirrors GMR_DEV_*).
+constexpr uint32_t kDevBadFace = GMR_DEV_BAD_FACE_INDEX;
+constexpr uint32_t kDevOverflow = GMR_DEV_PAIR_OVERFLOW;
+
+// Device counters block.
+struct Counters {
+  uint32_t n_pairs;      // total pairs of the current forward (scan total)
+  uint32_t status;       // GMR_DEV_* bits
+  unsigned long long evals_fwd;
+  unsigned long long evals_bwd;
+  unsigned long long contribs;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float3 ld_vert(const float* v, int i) {
+  return make_float3(__ldg(v + 3 * i), __ldg(v + 3 * i + 1), __ldg(v + 3 * i + 2));
+}
+
+// FP32 binning specification. Every operation is a separately rounded
+// IEEE-754 single operation in a fixed order (the _rn intrinsics are never
+// contracted), so the depth key and the tile rectangle are reproducible bit
+// for bit by any IEEE implementation of the same sequence. The rectangle is
+// conservative: it holds every pixel centre where o * G can reach 1/255 for
+// o <= 1 (radius sqrt(2 ln 255 lambda_max(Sigma')) + 0.25 px, with the area
+// scale kappa = 6 sqrt(3)/pi, the largest it takes), so the image does not
+// depend on it.
+struct BinResult {
+  bool visible;
+  float depth;
+  int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ float dot3_rn(const float* r, float x, float y, float z) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)), __fmul_rn(r[2], z));
+}
+
+__device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, const ViewInfo& v, int tile,
+                                              float inv_tile) {
+  BinResult r;
+  float mx = __fdiv_rn(__fadd_rn(__fadd_rn(a.x, b.x), c.x), 3.0f);
+  float my = __fdiv_rn(__fadd_rn(__fadd_rn(a.y, b.y), c.y), 3.0f);
+  float mz = __fdiv_rn(__fadd_rn(__fadd_rn(a.z, b.z), c.z), 3.0f);
+  float tx = __fadd_rn(dot3_rn(v.R + 0, mx, my, mz), v.t[0]);
+  float ty = __fadd_rn(dot3_rn(v.R + 3, mx, my, mz), v.t[1]);
+  float tz = __fadd_rn(dot3_rn(v.R + 6, mx, my, mz), v.t[2]);
+  r.depth = tz;
+  float fxx = __fmul_rn(v.fx, tx);
+  float fyy = __fmul_rn(v.fy, ty);
+  float ux = __fadd_rn(__fdiv_rn(fxx, tz), v.cx);
+  float uy = __fadd_rn(__fdiv_rn(fyy, tz), v.cy);
+  float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
+  float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
+  float q1x = dot3_rn(v.R + 0, e1x, e1y, e1z), q1y = dot3_rn(v.R + 3, e1x, e1y, e1z),
+        q1z = dot3_rn(v.R + 6, e1x, e1y, e1z);
+  float q2x = dot3_rn(v.R + 0, e2x, e2y, e2z), q2y = dot3_rn(v.R + 3, e2x, e2y, e2z),
+        q2z = dot3_rn(v.R + 6, e2x, e2y, e2z);
+  float zz = __fmul_rn(tz, tz);
+  float j00 = __fdiv_rn(v.fx, tz);
+  float j11 = __fdiv_rn(v.fy, tz);
+  float j02 = -__fdiv_rn(fxx, zz);
+  float j12 = -__fdiv_rn(fyy, zz);
+  float p1x = __fadd_rn(__fmul_rn(j00, q1x), __fmul_rn(j02, q1z));
+  float p1y = __fadd_rn(__fmul_rn(j11, q1y), __fmul_rn(j12, q1z));
+  float p2x = __fadd_rn(__fmul_rn(j00, q2x), __fmul_rn(j02, q2z));
+  float p2y = __fadd_rn(__fmul_rn(j11, q2y), __fmul_rn(j12, q2z));
+  float kxx = __fmul_rn(kKappaOver18, __fsub_rn(__fadd_rn(__fmul_rn(p1x, p1x), __fmul_rn(p2x, p2x)), __fmul_rn(p1x, p2x)));
+  float kyy = __fmul_rn(kKappaOver18, __fsub_rn(__fadd_rn(__fmul_rn(p1y, p1y), __fmul_rn(p2y, p2y)), __fmul_rn(p1y, p2y)));
+  float hs = __fmul_rn(0.5f, __fadd_rn(__fmul_rn(p1x, p2y), __fmul_rn(p2x, p1y)));
+  float kxy = __fmul_rn(kKappaOver18, __fsub_rn(__fadd_rn(__fmul_rn(p1x, p1y), __fmul_rn(p2x, p2y)), hs));
+  float mid = __fadd_rn(__fmul_rn(0.5f, __fadd_rn(kxx, kyy)), 0.3f);
+  float hd = __fmul_rn(0.5f, __fsub_rn(kxx, kyy));
+  float disc = __fsqrt_rn(__fadd_rn(__fmul_rn(hd, hd), __fmul_rn(kxy, kxy)));
+  float lam = __fadd_rn(mid, disc);
+  float rr = __fadd_rn(__fsqrt_rn(__fmul_rn(kTwoLn255, lam)), 0.25f);
+  r.visible = (tz > v.znear) && isfinite(ux) && isfinite(uy) && isfinite(rr);
+  r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
+  if (!r.visible) return r;
+  float bx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(ux, rr), 0.5f), inv_tile));
+  float bx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(ux, rr), 0.5f), inv_tile));
+  float by0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(uy, rr), 0.5f), inv_tile));
+  float by1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(uy, rr), 0.5f), inv_tile));
+  bx0 = fmaxf(bx0, 0.0f);
+  by0 = fmaxf(by0, 0.0f);
+  bx1 = fminf(bx1, (float)(v.tiles_x - 1));
+  by1 = fminf(by1, (float)(v.tiles_y - 1));
+  if (bx0 > bx1 || by0 > by1) return r;
+  r.x0 = (int)bx0; r.x1 = (int)bx1; r.y0 = (int)by0; r.y1 = (int)by1;
+  return r;
+}
+
+// Compositing weight of one staged Gaussian at one pixel. g = (ux, uy, a2,
+// b2) with (ux, uy) the mean relative to the 32-pixel-aligned anchor of the
+// pixel's block, h = (c2, o, ...), (pcx, pcy) the pixel centre relative to
+// the same anchor. Forward and backward call this same sequence of explicit
+// single-precision operations, so both take identical skip decisions.
+__device__ __forceinline__ float gauss_alpha(float4 g, float c2, float o, float pcx, float pcy, float& dx,
+                                             float& dy, float& graw) {
+  dx = __fsub_rn(g.x, pcx);
+  dy = __fsub_rn(g.y, pcy);
+  float t = __fmaf_rn(g.z, dx, __fmul_rn(g.w, dy));
+  float p2 = __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(c2, dy), dy));
+  float G = ex2_approx(p2);
+  graw = __fmul_rn(o, G);
+  return fminf(graw, kAlphaMax);
+}
+
+// ---------------------------------------------------------------- workspace
+struct Workspace {
+  // records: one per (view, face)
+  int64_t cap_records = 0;
+  float4* rec_u = nullptr;       // (ux_hi, uy_hi, ux_lo, uy_lo)
+  float4* rec_q = nullptr;       // (a2, b2, c2, 0) pre-scaled conic
+  uint2* rec_rect = nullptr;     // packed (x0 | x1 << 16, y0 | y1 << 16)
+  uint32_t* rec_ntiles = nullptr;
+  uint32_t* rec_key[2] = {nullptr, nullptr};  // depth bits, ping-pong
+  uint32_t* rec_id[2] = {nullptr, nullptr};   // record ids, ping-pong
+  uint32_t* rec_off = nullptr;   // pair offsets in sorted record order
+  float4* rec_grad = nullptr;    // 2 float4 per record: (R0..R3), (R4, 0, 0, 0)
+  // faces
+  int64_t cap_faces = 0;
+  float4* face_col = nullptr;    // (r, g, b, o)
+  float4* face_grad = nullptr;   // (dr, dg, db, sum dq)
+  // pixels
+  int64_t cap_pixels = 0;
+  float* pix_T = nullptr;
+  uint32_t* pix_last = nullptr;
+  // tiles
+  int64_t cap_tiles = 0;
+  uint2* tile_range = nullptr;
+  // pairs
+  int64_t cap_pairs = 0;
+  uint32_t* pair_tile[2] = {nullptr, nullptr};
+  uint32_t* pair_face[2] = {nullptr, nullptr};
+  // scratch for scans and radix histograms
+  int64_t cap_scan = 0;
+  uint32_t* scan_tmp = nullptr;     // block sums
+  int64_t cap_counts = 0;
+  uint32_t* radix_counts = nullptr;
+  // loss partial sums
+  int64_t cap_loss = 0;
+  double* loss_part = nullptr;
+  // views
+  int32_t cap_views = 0;
+  ViewInfo* views = nullptr;
+  Counters* counters = nullptr;
+};
+
+// ---------------------------------------------------------------- launchers
+// Every launcher returns cudaGetLastError() after enqueueing on stream s and
+// increments *launches by the number of kernels it launched.
+
+// scan.cu / sort.cu
+cudaError_t scan_exclusive(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* out, uint32_t* total,
+                           uint32_t* block_sums, cudaStream_t s, int64_t* launches);
+int64_t scan_block_sums_needed(int64_t n);
+// Stable LSD radix sort of (key, value) u32 pairs on the low `bits` key bits.
+// n is read from *n_dev when n_dev is not null (then n <= n_cap is required
+// by the caller's capacity check; excess items are ignored), else n_cap.
+// Returns the index (0 or 1) of the buffers holding the result.
+int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], const uint32_t* n_dev, int64_t n_cap, int bits,
+                     uint32_t* counts, uint32_t* scan_tmp, cudaStream_t s, int64_t* launches, cudaError_t* err);
+int64_t radix_counts_needed(int64_t n_cap);
+
+// project.cu
+cudaError_t launch_face_attrs(const float* rgb, const float* opacity, const int32_t* faces, int32_t F, int32_t V,
+                              int color_mode, float4* face_col, cudaStream_t s, int64_t* launches);
+cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const ViewInfo* views,
+                           int32_t C, int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);
+cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                               const ViewInfo* views, int32_t C, int cov_mode, int color_mode, const float* opacity,
+                               const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
+                               cudaStream_t s, int64_t* launches);
+cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
+                           const float* opacity, int cov_mode, int color_mode, float* means, float* cov,
+                           float* face_rgb, float* face_o, Counters* counters, cudaStream_t s, int64_t* launches);
+
+// raster.cu
+cudaError_t launch_emit_pairs(const Workspace& ws, const uint32_t* sorted_rid, int64_t n_rec, const ViewInfo* views,
+                              int32_t F, cudaStream_t s, int64_t* launches);
+cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, int64_t cap_pairs, uint2* ranges,
+                               cudaStream_t s, int64_t* launches);
+// Debug copies of the forward's per-record data: depth key bits and tile
+// rectangle per record id, and the unscaled conic.
+cudaError_t launch_debug_records(const Workspace& ws, const uint32_t* sorted_keys, const uint32_t* sorted_ids,
+                                 int64_t n_rec, uint32_t* depth_bits, int32_t* rects, float* conic, cudaStream_t s,
+                                 int64_t* launches);
+cudaError_t launch_raster_fwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
+                              float* images, float* t_final_out, cudaStream_t s, int64_t* launches);
+cudaError_t launch_raster_bwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
+                              const float* dL_dimages, cudaStream_t s, int64_t* launches);
+cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
+                           double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
+int64_t l2_loss_partials_needed(int64_t n);
+
+}  // namespace gmr

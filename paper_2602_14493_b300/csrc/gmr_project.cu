@@ -1,0 +1,465 @@
+// Mesh-to-Gaussian conversion (Sec. 2.2) fused with EWA projection
+// (Sec. 2.1), its backward, and the standalone conversion.
+//
+// Closed form used on the device. For a facet with vertices v_a (a = 0, 1,
+// 2), centroid mu and d_a = v_a - mu, the uniform density of Eq. 6-8 has
+// second moment Sigma_raw = (1/12) sum_a d_a d_a^T, which equals
+// R_f blkdiag(Sigma2D, 0) R_f^T of Eq. 15 (the moments of Eq. 9 written
+// without the facet frame). Its in-plane eigenvalues satisfy
+// lambda1 lambda2 = det Sigma2D = |A|^2 / 108, so the area-matching factor
+// of Eq. 12 is the constant kappa = 6 sqrt(3) / pi unless |A|^2 / 108 falls
+// below eps = 1e-14, and Eq. 13 (via Eq. 14) becomes
+//   Sigma_f = kappa Sigma_raw + s_z^2 n n^T.
+// Projected through M = J R (J the EWA Jacobian at the camera-space mean):
+//   Sigma' = (kappa/12) sum_a e_a e_a^T + s_z^2 m m^T + 0.3 I,
+//   e_a = M d_a, m = M n,
+// whose determinant is formed from squared 2D cross products (Cauchy-Binet),
+// a sum of non-negative terms, so edge-on facets lose no precision.
+// The image-plane mean is evaluated in FP64 and stored as a float pair so
+// that pixel offsets keep ~1e-6 px accuracy at any image size.
+
+#include "gmr_internal.cuh"
+
+namespace gmr {
+
+namespace {
+
+struct FaceGeom {
+  float3 v0, v1, v2;
+  float3 e1, e2;      // v1 - v0, v2 - v0
+  float3 d[3];        // v_a - centroid
+  float3 n;           // unit normal (0 for a degenerate facet)
+  float cn;           // |e1 x e2| = 2 |A|
+  float w;            // kappa / 12
+  float sz2;          // s_z^2
+  bool clamped;       // Eq. 12 epsilon clamp active
+  double mx, my, mz;  // centroid in FP64
+};
+
+__device__ __forceinline__ float3 f3sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 f3add(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 f3scale(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float f3dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 f3cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ FaceGeom face_geom(float3 a, float3 b, float3 c, int cov_mode) {
+  FaceGeom g;
+  g.v0 = a; g.v1 = b; g.v2 = c;
+  g.e1 = f3sub(b, a);
+  g.e2 = f3sub(c, a);
+  g.d[0] = f3scale(-1.0f / 3.0f, f3add(g.e1, g.e2));
+  g.d[1] = f3add(g.d[0], g.e1);
+  g.d[2] = f3add(g.d[0], g.e2);
+  float3 cr = f3cross(g.e1, g.e2);
+  g.cn = sqrtf(f3dot(cr, cr));
+  g.n = g.cn > 0.0f ? f3scale(1.0f / g.cn, cr) : make_float3(0.f, 0.f, 0.f);
+  // The FP32 cross product of nearly parallel edges is cancellation noise,
+  // and near the Eq. 12 clamp kappa is proportional to |A|: there, redo it in
+  // FP64 from the exact vertex differences (rare, so FP64 costs nothing).
+  float scale = sqrtf(f3dot(g.e1, g.e1) * f3dot(g.e2, g.e2));
+  if (g.cn < 1e-3f * scale || g.cn < 8e-6f) {
+    double ax = a.x, ay = a.y, az = a.z;
+    double p1 = (double)b.x - ax, p2 = (double)b.y - ay, p3 = (double)b.z - az;
+    double q1 = (double)c.x - ax, q2 = (double)c.y - ay, q3 = (double)c.z - az;
+    double r1 = p2 * q3 - p3 * q2, r2 = p3 * q1 - p1 * q3, r3 = p1 * q2 - p2 * q1;
+    double rn = sqrt(r1 * r1 + r2 * r2 + r3 * r3);
+    g.cn = (float)rn;
+    g.n = rn > 0.0 ? make_float3((float)(r1 / rn), (float)(r2 / rn), (float)(r3 / rn)) : make_float3(0.f, 0.f, 0.f);
+  }
+  if (cov_mode == GMR_COV_AREA) {
+    float area = 0.5f * g.cn;
+    // Eq. 12 with lambda1 lambda2 = |A|^2 / 108
+    g.clamped = (area * area) < 108.0f * kEps;
+    float kappa = g.clamped ? area / (kPi * 1e-7f) : kKappa;
+    g.w = kappa * (1.0f / 12.0f);
+    g.sz2 = kSz * kSz;
+  } else {
+    g.clamped = false;
+    g.w = 1.0f / 12.0f;
+    g.sz2 = 0.0f;
+  }
+  g.mx = ((double)a.x + (double)b.x + (double)c.x) * (1.0 / 3.0);
+  g.my = ((double)a.y + (double)b.y + (double)c.y) * (1.0 / 3.0);
+  g.mz = ((double)a.z + (double)b.z + (double)c.z) * (1.0 / 3.0);
+  return g;
+}
+
+struct ProjRec {
+  double tx, ty, tz;      // camera-space mean
+  double ux, uy;          // image-plane mean
+  float J00, J02, J11, J12;
+  float M[6];             // J R, row-major 2x3
+  float2 e[3];            // M d_a
+  float2 m;               // M n
+  float kxx, kxy, kyy;    // Sigma' - 0.3 I
+  float qa, qb, qc;       // conic
+};
+
+__device__ __forceinline__ ProjRec project_rec(const FaceGeom& g, const ViewInfo& v) {
+  ProjRec p;
+  const float* R = v.R;
+  p.tx = (double)R[0] * g.mx + (double)R[1] * g.my + (double)R[2] * g.mz + (double)v.t[0];
+  p.ty = (double)R[3] * g.mx + (double)R[4] * g.my + (double)R[5] * g.mz + (double)v.t[1];
+  p.tz = (double)R[6] * g.mx + (double)R[7] * g.my + (double)R[8] * g.mz + (double)v.t[2];
+  double iz = 1.0 / p.tz;
+  double xz = p.tx * iz, yz = p.ty * iz;
+  p.ux = (double)v.fx * xz + (double)v.cx;
+  p.uy = (double)v.fy * yz + (double)v.cy;
+  p.J00 = (float)((double)v.fx * iz);
+  p.J11 = (float)((double)v.fy * iz);
+  p.J02 = (float)(-(double)v.fx * xz * iz);
+  p.J12 = (float)(-(double)v.fy * yz * iz);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    p.M[q] = p.J00 * R[q] + p.J02 * R[6 + q];
+    p.M[3 + q] = p.J11 * R[3 + q] + p.J12 * R[6 + q];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    p.e[a].x = p.M[0] * g.d[a].x + p.M[1] * g.d[a].y + p.M[2] * g.d[a].z;
+    p.e[a].y = p.M[3] * g.d[a].x + p.M[4] * g.d[a].y + p.M[5] * g.d[a].z;
+  }
+  p.m.x = p.M[0] * g.n.x + p.M[1] * g.n.y + p.M[2] * g.n.z;
+  p.m.y = p.M[3] * g.n.x + p.M[4] * g.n.y + p.M[5] * g.n.z;
+  float sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    sxx += p.e[a].x * p.e[a].x;
+    sxy += p.e[a].x * p.e[a].y;
+    syy += p.e[a].y * p.e[a].y;
+  }
+  p.kxx = g.w * sxx + g.sz2 * p.m.x * p.m.x;
+  p.kxy = g.w * sxy + g.sz2 * p.m.x * p.m.y;
+  p.kyy = g.w * syy + g.sz2 * p.m.y * p.m.y;
+  // det(K) by Cauchy-Binet over the four rank-one terms
+  float c01 = p.e[0].x * p.e[1].y - p.e[0].y * p.e[1].x;
+  float c02 = p.e[0].x * p.e[2].y - p.e[0].y * p.e[2].x;
+  float c12 = p.e[1].x * p.e[2].y - p.e[1].y * p.e[2].x;
+  float cm = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float t = p.e[a].x * p.m.y - p.e[a].y * p.m.x;
+    cm += t * t;
+  }
+  float detK = g.w * g.w * (c01 * c01 + c02 * c02 + c12 * c12) + g.w * g.sz2 * cm;
+  float det = detK + kDilation * (p.kxx + p.kyy) + kDilation * kDilation;
+  float inv = 1.0f / det;
+  p.qa = (p.kyy + kDilation) * inv;
+  p.qb = -p.kxy * inv;
+  p.qc = (p.kxx + kDilation) * inv;
+  return p;
+}
+
+__device__ __forceinline__ bool load_face(const int32_t* faces, int f, int V, int& i0, int& i1, int& i2) {
+  i0 = __ldg(faces + 3 * f);
+  i1 = __ldg(faces + 3 * f + 1);
+  i2 = __ldg(faces + 3 * f + 2);
+  return (unsigned)i0 < (unsigned)V && (unsigned)i1 < (unsigned)V && (unsigned)i2 < (unsigned)V;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Per-face colour (Eq. 16 in per-vertex mode) and clamped opacity.
+__global__ void k_face_attrs(const float* __restrict__ rgb, const float* __restrict__ opacity,
+                             const int32_t* __restrict__ faces, int32_t F, int32_t V, int color_mode,
+                             float4* __restrict__ face_col) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  float r, g, b;
+  if (color_mode == GMR_COLOR_PER_FACE) {
+    r = __ldg(rgb + 3 * f); g = __ldg(rgb + 3 * f + 1); b = __ldg(rgb + 3 * f + 2);
+  } else {
+    int i0, i1, i2;
+    if (!load_face(faces, f, V, i0, i1, i2)) { face_col[f] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+    r = (__ldg(rgb + 3 * i0) + __ldg(rgb + 3 * i1) + __ldg(rgb + 3 * i2)) * (1.0f / 3.0f);
+    g = (__ldg(rgb + 3 * i0 + 1) + __ldg(rgb + 3 * i1 + 1) + __ldg(rgb + 3 * i2 + 1)) * (1.0f / 3.0f);
+    b = (__ldg(rgb + 3 * i0 + 2) + __ldg(rgb + 3 * i1 + 2) + __ldg(rgb + 3 * i2 + 2)) * (1.0f / 3.0f);
+  }
+  float o = opacity ? __ldg(opacity + f) : 1.0f;
+  o = fminf(fmaxf(o, 0.0f), 1.0f);
+  face_col[f] = make_float4(r, g, b, o);
+}
+
+constexpr int kProjThreads = 128;
+
+// One thread per (face, view): binning spec, depth key, tile count, and the
+// precise record (image mean as a float pair, pre-scaled conic).
+__global__ void __launch_bounds__(kProjThreads) k_project(
+    const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
+    const ViewInfo* __restrict__ views, int tile, float inv_tile, int cov_mode, float4* __restrict__ rec_u,
+    float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
+    uint32_t* __restrict__ rec_key, uint32_t* __restrict__ rec_id, Counters* __restrict__ counters) {
+  __shared__ ViewInfo sv;
+  int c = blockIdx.y;
+  if (threadIdx.x == 0) sv = views[c];
+  __syncthreads();
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  uint32_t rid = (uint32_t)c * (uint32_t)F + (uint32_t)f;
+  rec_id[rid] = rid;
+  int i0, i1, i2;
+  if (!load_face(faces, f, V, i0, i1, i2)) {
+    if (c == 0) atomicOr(&counters->status, kDevBadFace);
+    rec_key[rid] = 0xffffffffu;
+    rec_ntiles[rid] = 0;
+    rec_rect[rid] = make_uint2(1u, 1u);
+    return;
+  }
+  float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
+  BinResult br = bin_spec(a, b, cc, sv, tile, inv_tile);
+  uint32_t nt = 0;
+  uint2 rect = make_uint2(1u, 1u);  // x0 = 1 > x1 = 0: empty
+  if (br.visible && br.x0 <= br.x1) {
+    nt = (uint32_t)(br.x1 - br.x0 + 1) * (uint32_t)(br.y1 - br.y0 + 1);
+    rect = make_uint2((uint32_t)br.x0 | ((uint32_t)br.x1 << 16), (uint32_t)br.y0 | ((uint32_t)br.y1 << 16));
+  }
+  rec_key[rid] = br.visible ? __float_as_uint(br.depth) : 0xffffffffu;
+  rec_ntiles[rid] = nt;
+  rec_rect[rid] = rect;
+  if (nt == 0) return;
+  FaceGeom g = face_geom(a, b, cc, cov_mode);
+  ProjRec p = project_rec(g, sv);
+  float uxh = __double2float_rn(p.ux), uyh = __double2float_rn(p.uy);
+  float uxl = __double2float_rn(p.ux - (double)uxh), uyl = __double2float_rn(p.uy - (double)uyh);
+  rec_u[rid] = make_float4(uxh, uyh, uxl, uyl);
+  rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, 0.0f);
+}
+
+// Backward of conversion + projection. One thread per face, looping over the
+// views; the per-(view, face) gradient sums R0..R4 from the compositing
+// backward are chained through the conic inverse, Sigma' = M Sigma M^T +
+// 0.3 I, M = J R, J(t) and u(t), to dL/dmu, dL/dd_a and dL/dn, then to the
+// three vertices (d_a = v_a - mu, n = e1 x e2 / |e1 x e2|).
+__global__ void __launch_bounds__(128) k_project_bwd(
+    const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
+    const ViewInfo* __restrict__ views, int32_t C, int cov_mode, int color_mode, const float* __restrict__ opacity,
+    const float4* __restrict__ rec_grad, const float4* __restrict__ face_grad, float* __restrict__ dverts,
+    float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  int i0, i1, i2;
+  if (!load_face(faces, f, V, i0, i1, i2)) return;
+  float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
+  FaceGeom g = face_geom(a, b, cc, cov_mode);
+  float3 dmu = make_float3(0.f, 0.f, 0.f);
+  float3 dd[3] = {dmu, dmu, dmu};
+  float3 dn = dmu;
+  float dw = 0.f;  // dL/d(kappa/12)
+  for (int c = 0; c < C; ++c) {
+    size_t rid = (size_t)c * F + f;
+    float4 r0 = rec_grad[2 * rid];
+    float r4 = rec_grad[2 * rid + 1].x;
+    if (r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f) continue;
+    const ViewInfo& v = views[c];
+    ProjRec p = project_rec(g, v);
+    float dux = kLn2 * r0.x, duy = kLn2 * r0.y;
+    float dqa = -0.5f * r0.z, dqb = -r0.w, dqc = -0.5f * r4;
+    // dL/dSigma' = -Q G_Q Q with G_Q = [[dqa, dqb/2], [dqb/2, dqc]]
+    float g00 = dqa, g01 = 0.5f * dqb, g11 = dqc;
+    float t00 = p.qa * g00 + p.qb * g01, t01 = p.qa * g01 + p.qb * g11;
+    float t10 = p.qb * g00 + p.qc * g01, t11 = p.qb * g01 + p.qc * g11;
+    float s00 = -(t00 * p.qa + t01 * p.qb);
+    float s01 = -(t00 * p.qb + t01 * p.qc);
+    float s11 = -(t10 * p.qb + t11 * p.qc);
+    // Sigma' = w sum e e^T + sz2 m m^T + 0.3 I
+    float2 de[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      de[k].x = 2.f * g.w * (s00 * p.e[k].x + s01 * p.e[k].y);
+      de[k].y = 2.f * g.w * (s01 * p.e[k].x + s11 * p.e[k].y);
+      dw += s00 * p.e[k].x * p.e[k].x + 2.f * s01 * p.e[k].x * p.e[k].y + s11 * p.e[k].y * p.e[k].y;
+    }
+    float2 dm;
+    dm.x = 2.f * g.sz2 * (s00 * p.m.x + s01 * p.m.y);
+    dm.y = 2.f * g.sz2 * (s01 * p.m.x + s11 * p.m.y);
+    // e_a = M d_a, m = M n
+    float dM[6];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float dq0 = dm.x * (&g.n.x)[q], dq1 = dm.y * (&g.n.x)[q];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        dq0 += de[k].x * (&g.d[k].x)[q];
+        dq1 += de[k].y * (&g.d[k].x)[q];
+      }
+      dM[q] = dq0;
+      dM[3 + q] = dq1;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dd[k].x += p.M[0] * de[k].x + p.M[3] * de[k].y;
+      dd[k].y += p.M[1] * de[k].x + p.M[4] * de[k].y;
+      dd[k].z += p.M[2] * de[k].x + p.M[5] * de[k].y;
+    }
+    dn.x += p.M[0] * dm.x + p.M[3] * dm.y;
+    dn.y += p.M[1] * dm.x + p.M[4] * dm.y;
+    dn.z += p.M[2] * dm.x + p.M[5] * dm.y;
+    // M = J R: dJ = dM R^T (only the non-zero entries of J)
+    const float* R = v.R;
+    float dJ00 = dM[0] * R[0] + dM[1] * R[1] + dM[2] * R[2];
+    float dJ02 = dM[0] * R[6] + dM[1] * R[7] + dM[2] * R[8];
+    float dJ11 = dM[3] * R[3] + dM[4] * R[4] + dM[5] * R[5];
+    float dJ12 = dM[3] * R[6] + dM[4] * R[7] + dM[5] * R[8];
+    // J(t), u(t) -> dL/dt
+    float iz = (float)(1.0 / p.tz);
+    float x = (float)p.tx, y = (float)p.ty;
+    float fxz2 = v.fx * iz * iz, fyz2 = v.fy * iz * iz;
+    float dtx = dJ02 * (-fxz2) + dux * v.fx * iz;
+    float dty = dJ12 * (-fyz2) + duy * v.fy * iz;
+    float dtz = dJ00 * (-fxz2) + dJ02 * (2.f * v.fx * x * iz * iz * iz) + dJ11 * (-fyz2) +
+                dJ12 * (2.f * v.fy * y * iz * iz * iz) - dux * v.fx * x * iz * iz - duy * v.fy * y * iz * iz;
+    // t = R mu + t_cam
+    dmu.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
+    dmu.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
+    dmu.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
+  }
+  // to vertices: d_a = v_a - mu (mu = mean of v), n from e1 x e2
+  float3 sdd = f3add(f3add(dd[0], dd[1]), dd[2]);
+  float3 dv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dv[k] = f3add(f3scale(1.0f / 3.0f, f3sub(dmu, sdd)), dd[k]);
+  if (g.cn > 0.f) {
+    float3 dcr = f3scale(1.0f / g.cn, f3sub(dn, f3scale(f3dot(g.n, dn), g.n)));
+    if (g.clamped) {
+      // kappa = |A| / (pi 1e-7), |A| = cn / 2, w = kappa / 12
+      float dcn = dw * (1.0f / 12.0f) * (0.5f / (kPi * 1e-7f));
+      dcr = f3add(dcr, f3scale(dcn, g.n));
+    }
+    float3 de1 = f3cross(g.e2, dcr);
+    float3 de2 = f3cross(dcr, g.e1);
+    dv[0] = f3sub(dv[0], f3add(de1, de2));
+    dv[1] = f3add(dv[1], de1);
+    dv[2] = f3add(dv[2], de2);
+  }
+  if (dverts) {
+    int idx[3] = {i0, i1, i2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(dverts + 3 * idx[k], dv[k].x);
+      atomicAdd(dverts + 3 * idx[k] + 1, dv[k].y);
+      atomicAdd(dverts + 3 * idx[k] + 2, dv[k].z);
+    }
+  }
+  float4 fg = face_grad[f];
+  if (drgb) {
+    if (color_mode == GMR_COLOR_PER_FACE) {
+      if (accumulate) {
+        drgb[3 * f] += fg.x; drgb[3 * f + 1] += fg.y; drgb[3 * f + 2] += fg.z;
+      } else {
+        drgb[3 * f] = fg.x; drgb[3 * f + 1] = fg.y; drgb[3 * f + 2] = fg.z;
+      }
+    } else {
+      int idx[3] = {i0, i1, i2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        atomicAdd(drgb + 3 * idx[k], fg.x * (1.0f / 3.0f));
+        atomicAdd(drgb + 3 * idx[k] + 1, fg.y * (1.0f / 3.0f));
+        atomicAdd(drgb + 3 * idx[k] + 2, fg.z * (1.0f / 3.0f));
+      }
+    }
+  }
+  if (dop && opacity) {
+    float o = opacity[f];
+    // alpha = o G: dL/do = sum dalpha G = (sum dalpha alpha) / o; clamp to [0, 1]
+    float go = (o > 0.f && o <= 1.f) ? fg.w / o : 0.f;
+    if (accumulate) dop[f] += go; else dop[f] = go;
+  }
+}
+
+// Standalone conversion: means, 6 covariance entries, colour, opacity.
+__global__ void k_convert(const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
+                          const float* __restrict__ rgb, const float* __restrict__ opacity, int cov_mode,
+                          int color_mode, float* __restrict__ means, float* __restrict__ cov,
+                          float* __restrict__ face_rgb, float* __restrict__ face_o, Counters* counters) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  int i0, i1, i2;
+  if (!load_face(faces, f, V, i0, i1, i2)) {
+    atomicOr(&counters->status, kDevBadFace);
+    for (int k = 0; k < 3; ++k) {
+      if (means) means[3 * f + k] = 0.f;
+      if (face_rgb) face_rgb[3 * f + k] = 0.f;
+    }
+    if (cov) for (int k = 0; k < 6; ++k) cov[6 * f + k] = 0.f;
+    if (face_o) face_o[f] = 0.f;
+    return;
+  }
+  float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), c = ld_vert(verts, i2);
+  FaceGeom g = face_geom(a, b, c, cov_mode);
+  if (means) {
+    means[3 * f] = (float)g.mx; means[3 * f + 1] = (float)g.my; means[3 * f + 2] = (float)g.mz;
+  }
+  if (cov) {
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // degenerate facets (|A| = 0) get zero covariance (kappa = 0)
+    float w = (g.cn > 0.f) ? g.w : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float3 d = g.d[k];
+      s[0] += d.x * d.x; s[1] += d.x * d.y; s[2] += d.x * d.z;
+      s[3] += d.y * d.y; s[4] += d.y * d.z; s[5] += d.z * d.z;
+    }
+    float3 n = g.n;
+    cov[6 * f + 0] = w * s[0] + g.sz2 * n.x * n.x;
+    cov[6 * f + 1] = w * s[1] + g.sz2 * n.x * n.y;
+    cov[6 * f + 2] = w * s[2] + g.sz2 * n.x * n.z;
+    cov[6 * f + 3] = w * s[3] + g.sz2 * n.y * n.y;
+    cov[6 * f + 4] = w * s[4] + g.sz2 * n.y * n.z;
+    cov[6 * f + 5] = w * s[5] + g.sz2 * n.z * n.z;
+  }
+  if (face_rgb) {
+    for (int k = 0; k < 3; ++k) {
+      float v = (color_mode == GMR_COLOR_PER_FACE)
+                    ? rgb[3 * f + k]
+                    : (rgb[3 * i0 + k] + rgb[3 * i1 + k] + rgb[3 * i2 + k]) * (1.0f / 3.0f);
+      face_rgb[3 * f + k] = v;
+    }
+  }
+  if (face_o) face_o[f] = fminf(fmaxf(opacity ? opacity[f] : 1.0f, 0.0f), 1.0f);
+}
+
+}  // namespace
+
+cudaError_t launch_face_attrs(const float* rgb, const float* opacity, const int32_t* faces, int32_t F, int32_t V,
+                              int color_mode, float4* face_col, cudaStream_t s, int64_t* launches) {
+  if (F <= 0) return cudaSuccess;
+  k_face_attrs<<<(F + 255) / 256, 256, 0, s>>>(rgb, opacity, faces, F, V, color_mode, face_col);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const ViewInfo* views,
+                           int32_t C, int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
+  if (F <= 0 || C <= 0) return cudaSuccess;
+  dim3 grid((F + kProjThreads - 1) / kProjThreads, C);
+  k_project<<<grid, kProjThreads, 0, s>>>(verts, V, faces, F, views, tile, 1.0f / (float)tile, cov_mode, ws.rec_u,
+                                          ws.rec_q, ws.rec_rect, ws.rec_ntiles, ws.rec_key[0], ws.rec_id[0],
+                                          ws.counters);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                               const ViewInfo* views, int32_t C, int cov_mode, int color_mode, const float* opacity,
+                               const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
+                               cudaStream_t s, int64_t* launches) {
+  if (F <= 0) return cudaSuccess;
+  k_project_bwd<<<(F + 127) / 128, 128, 0, s>>>(verts, V, faces, F, views, C, cov_mode, color_mode, opacity,
+                                                ws.rec_grad, ws.face_grad, dverts, drgb, dop, accumulate);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
+                           const float* opacity, int cov_mode, int color_mode, float* means, float* cov,
+                           float* face_rgb, float* face_o, Counters* counters, cudaStream_t s, int64_t* launches) {
+  if (F <= 0) return cudaSuccess;
+  k_convert<<<(F + 255) / 256, 256, 0, s>>>(verts, V, faces, F, rgb, opacity, cov_mode, color_mode, means, cov,
+                                            face_rgb, face_o, counters);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace gmr

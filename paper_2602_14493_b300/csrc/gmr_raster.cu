@@ -1,0 +1,549 @@
+// Tile binning and front-to-back alpha compositing (Sec. 2.1, standard 3DGS
+// rasterization), forward and backward.
+//
+// Forward, per pixel, over the Gaussians listed for its tile in (depth, face)
+// order: alpha = min(0.99, o * G) with G = exp(-1/2 d^T Q d); Gaussians with
+// alpha < 1/255 are skipped; the pixel stops before the Gaussian that would
+// take its transmittance T below 1e-4; otherwise C += c alpha T and
+// T *= 1 - alpha. I = C + T bg. The final T and the list position of the last
+// contributor are kept per pixel.
+//
+// Backward, per pixel, walks the same list from the last contributor to the
+// front, recovering T_i = T_(i+1) / (1 - alpha_i) from the stored final T
+// (no per-pixel lists are stored), with S the colour composited behind
+// Gaussian i (plus T_final bg):
+//   dL/dc_i     = alpha_i T_i g
+//   dL/dalpha_i = T_i (c_i . g) - (S . g) / (1 - alpha_i)
+// and alpha = o 2^(a2 dx^2 + b2 dx dy + c2 dy^2) gives the mean, conic and
+// opacity terms. A warp reduces its 32 pixels' contributions to one Gaussian
+// with a transposed butterfly (9 values in 14 shuffles) and eight lanes then
+// issue one atomic add each.
+//
+// Layout: one CTA of 256 threads per screen tile of one view (all views of a
+// batched call in one launch; the tile id selects the view). A warp covers an
+// 8x4 pixel block; with 32x32 tiles each thread owns four pixels, one per
+// 16x16 quadrant. Each batch of listed Gaussians is staged in shared memory
+// (float4 loads of the records and face colours), with the image mean made
+// relative to the pixel block's 32-aligned anchor in float-pair arithmetic.
+
+#include "gmr_internal.cuh"
+
+namespace gmr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Binary search of the view owning global tile g.
+__device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (views[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int TS>
+struct PixMap {
+  static constexpr int PPT = TS * TS / kThreads;  // pixels per thread: 1 or 4
+  __device__ __forceinline__ static void local(int k, int& lx, int& ly) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int wx = (warp & 1) * 8, wy = (warp >> 1) * 4;
+    int qx = (k & 1) * 16, qy = (k >> 1) * 16;
+    lx = qx + wx + (lane & 7);
+    ly = qy + wy + (lane >> 3);
+  }
+};
+
+// ---------------------------------------------------------------- emit
+// One thread per record in sorted (depth) order: writes (global tile, face)
+// for every tile of its rectangle at its scanned offset.
+__global__ void k_emit_pairs(const uint32_t* __restrict__ sorted_rid, const uint32_t* __restrict__ rec_ntiles,
+                             const uint2* __restrict__ rec_rect, const uint32_t* __restrict__ rec_off,
+                             const ViewInfo* __restrict__ views, int64_t n_rec, int32_t F, int64_t cap,
+                             uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_face,
+                             Counters* __restrict__ counters) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_rec) return;
+  uint32_t total = counters->n_pairs;
+  if ((int64_t)total > cap) {
+    if (k == 0) atomicOr(&counters->status, kDevOverflow);
+    return;
+  }
+  uint32_t rid = sorted_rid[k];
+  uint32_t nt = rec_ntiles[rid];
+  if (nt == 0) return;
+  uint32_t off = rec_off[k];
+  int c = (int)(rid / (uint32_t)F);
+  uint32_t f = rid - (uint32_t)c * (uint32_t)F;
+  uint2 r = rec_rect[rid];
+  int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+  int tx = views[c].tiles_x;
+  uint32_t base = (uint32_t)views[c].tile_base;
+  for (int y = y0; y <= y1; ++y)
+    for (int x = x0; x <= x1; ++x) {
+      pair_tile[off] = base + (uint32_t)(y * tx + x);
+      pair_face[off] = f;
+      ++off;
+    }
+}
+
+// [start, end) of each tile's run in the sorted pair list.
+__global__ void k_tile_ranges(const uint32_t* __restrict__ tiles, const Counters* __restrict__ counters, int64_t cap,
+                              uint2* __restrict__ ranges) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = counters->n_pairs;
+  if (n > cap) return;
+  if (i >= n) return;
+  uint32_t t = tiles[i];
+  if (i == 0 || tiles[i - 1] != t) ranges[t].x = (uint32_t)i;
+  if (i == n - 1 || tiles[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+// ---------------------------------------------------------------- staging
+template <int BATCH>
+struct Stage {
+  float4 g[BATCH];  // (ux, uy, a2, b2), mean relative to the anchor
+  float4 h[BATCH];  // (c2, o, r, g)
+  float b[BATCH];   // blue
+  uint32_t rid[BATCH];
+  uint32_t face[BATCH];
+};
+
+template <int BATCH>
+__device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
+                                            int count, uint32_t rec_base, const float4* __restrict__ rec_u,
+                                            const float4* __restrict__ rec_q, const float4* __restrict__ face_col,
+                                            float ax, float ay, bool want_ids) {
+  for (int i = threadIdx.x; i < count; i += kThreads) {
+    uint32_t f = __ldg(pair_face + lo + i);
+    uint32_t rid = rec_base + f;
+    float4 u = __ldg(rec_u + rid);
+    float4 q = __ldg(rec_q + rid);
+    float4 col = __ldg(face_col + f);
+    float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
+    float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
+    st.g[i] = make_float4(ux, uy, q.x, q.y);
+    st.h[i] = make_float4(q.z, col.w, col.x, col.y);
+    st.b[i] = col.z;
+    if (want_ids) {
+      st.rid[i] = rid;
+      st.face[i] = f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- forward
+template <int TS, int BATCH>
+__global__ void __launch_bounds__(kThreads) k_raster_fwd(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
+    const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
+    int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
+    uint32_t* __restrict__ pix_last, float* __restrict__ t_out, Counters* __restrict__ counters) {
+  constexpr int PPT = PixMap<TS>::PPT;
+  __shared__ Stage<BATCH> st;
+  __shared__ int s_view;
+  const int g = blockIdx.x;
+  if (threadIdx.x == 0) s_view = find_view(views, C, g);
+  __syncthreads();
+  const int c = s_view;
+  const ViewInfo& v = views[c];
+  const int lt = g - v.tile_base;
+  const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
+  const int ox = txi * TS, oy = tyi * TS;
+  const int axi = ox & ~31, ayi = oy & ~31;
+  const float ax = (float)axi, ay = (float)ayi;
+
+  float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+  uint32_t last[PPT], term[PPT], ncontrib[PPT];
+  bool done[PPT], inside[PPT];
+  int px[PPT], py[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    int lx, ly;
+    PixMap<TS>::local(k, lx, ly);
+    px[k] = ox + lx;
+    py[k] = oy + ly;
+    pcx[k] = (float)(px[k] - axi) + 0.5f;
+    pcy[k] = (float)(py[k] - ayi) + 0.5f;
+    inside[k] = px[k] < v.W && py[k] < v.H;
+    done[k] = !inside[k];
+    T[k] = 1.0f;
+    Cr[k] = Cg[k] = Cb[k] = 0.0f;
+    last[k] = 0;
+    term[k] = 0;
+    ncontrib[k] = 0;
+  }
+  const uint2 range = ranges[g];
+  const int n = (int)(range.y - range.x);
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
+
+  for (int base = 0; base < n; base += BATCH) {
+    bool tdone = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) tdone &= done[k];
+    if (__syncthreads_and(tdone)) break;
+    int cnt = min(BATCH, n - base);
+    stage_batch<BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, false);
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      bool wd = true;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) wd &= done[k];
+      if (__all_sync(kFull, wd)) break;
+      const float4 gg = st.g[j];
+      const float4 hh = st.h[j];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (done[k]) continue;
+        float dx, dy, graw;
+        float alpha = gauss_alpha(gg, hh.x, hh.y, pcx[k], pcy[k], dx, dy, graw);
+        if (alpha < kAlphaMin) continue;
+        float test = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+        if (test < kTMin) {
+          done[k] = true;
+          term[k] = (uint32_t)(base + j + 1);
+          continue;
+        }
+        float w = __fmul_rn(alpha, T[k]);
+        Cr[k] = __fmaf_rn(hh.z, w, Cr[k]);
+        Cg[k] = __fmaf_rn(hh.w, w, Cg[k]);
+        Cb[k] = __fmaf_rn(st.b[j], w, Cb[k]);
+        T[k] = test;
+        last[k] = (uint32_t)(base + j + 1);
+        ++ncontrib[k];
+      }
+    }
+  }
+  unsigned long long evals = 0, ncon = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (!inside[k]) continue;
+    ncon += ncontrib[k];
+    int64_t pid = v.pix_base + (int64_t)py[k] * v.W + px[k];
+    images[3 * pid] = Cr[k] + T[k] * bg0;
+    images[3 * pid + 1] = Cg[k] + T[k] * bg1;
+    images[3 * pid + 2] = Cb[k] + T[k] * bg2;
+    pix_T[pid] = T[k];
+    pix_last[pid] = last[k];
+    if (t_out) t_out[pid] = T[k];
+    evals += term[k] ? term[k] : (uint32_t)n;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(kFull, evals, o);
+    ncon += __shfl_xor_sync(kFull, ncon, o);
+  }
+  if ((threadIdx.x & 31) == 0 && evals) atomicAdd(&counters->evals_fwd, evals);
+  if ((threadIdx.x & 31) == 0 && ncon) atomicAdd(&counters->contribs, ncon);
+}
+
+// ---------------------------------------------------------------- backward
+// Sum of v[0..7] over the warp, transposed: on return lane L (L % 4 == 0)
+// holds the total of value index ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 +
+// ((L >> 2) & 1).
+__device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float k0 = (b4 ? v[4] : v[0]) + __shfl_xor_sync(kFull, b4 ? v[0] : v[4], 16);
+  float k1 = (b4 ? v[5] : v[1]) + __shfl_xor_sync(kFull, b4 ? v[1] : v[5], 16);
+  float k2 = (b4 ? v[6] : v[2]) + __shfl_xor_sync(kFull, b4 ? v[2] : v[6], 16);
+  float k3 = (b4 ? v[7] : v[3]) + __shfl_xor_sync(kFull, b4 ? v[3] : v[7], 16);
+  float m0 = (b3 ? k2 : k0) + __shfl_xor_sync(kFull, b3 ? k0 : k2, 8);
+  float m1 = (b3 ? k3 : k1) + __shfl_xor_sync(kFull, b3 ? k1 : k3, 8);
+  float s = (b2 ? m1 : m0) + __shfl_xor_sync(kFull, b2 ? m0 : m1, 4);
+  s += __shfl_xor_sync(kFull, s, 2);
+  s += __shfl_xor_sync(kFull, s, 1);
+  return s;
+}
+
+template <int TS, int BATCH>
+__global__ void __launch_bounds__(kThreads) k_raster_bwd(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
+    const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
+    int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
+    const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
+    float4* __restrict__ face_grad, Counters* __restrict__ counters) {
+  constexpr int PPT = PixMap<TS>::PPT;
+  __shared__ Stage<BATCH> st;
+  __shared__ int s_view;
+  __shared__ uint32_t s_maxlast;
+  const int g = blockIdx.x;
+  if (threadIdx.x == 0) {
+    s_view = find_view(views, C, g);
+    s_maxlast = 0;
+  }
+  __syncthreads();
+  const int c = s_view;
+  const ViewInfo& v = views[c];
+  const int lt = g - v.tile_base;
+  const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
+  const int ox = txi * TS, oy = tyi * TS;
+  const int axi = ox & ~31, ayi = oy & ~31;
+  const float ax = (float)axi, ay = (float)ayi;
+  const int lane = threadIdx.x & 31;
+
+  float pcx[PPT], pcy[PPT], T[PPT], S0[PPT], S1[PPT], S2[PPT], G0[PPT], G1[PPT], G2[PPT];
+  uint32_t last[PPT];
+  uint32_t tmax = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    int lx, ly;
+    PixMap<TS>::local(k, lx, ly);
+    int px = ox + lx, py = oy + ly;
+    pcx[k] = (float)(px - axi) + 0.5f;
+    pcy[k] = (float)(py - ayi) + 0.5f;
+    bool inside = px < v.W && py < v.H;
+    if (inside) {
+      int64_t pid = v.pix_base + (int64_t)py * v.W + px;
+      T[k] = pix_T[pid];
+      last[k] = pix_last[pid];
+      G0[k] = dL_dimg[3 * pid];
+      G1[k] = dL_dimg[3 * pid + 1];
+      G2[k] = dL_dimg[3 * pid + 2];
+    } else {
+      T[k] = 1.0f;
+      last[k] = 0;
+      G0[k] = G1[k] = G2[k] = 0.0f;
+    }
+    S0[k] = T[k] * bg0;
+    S1[k] = T[k] * bg1;
+    S2[k] = T[k] * bg2;
+    tmax = max(tmax, last[k]);
+  }
+  uint32_t wmax = tmax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
+  if (lane == 0) atomicMax(&s_maxlast, wmax);
+  __syncthreads();
+  const int end_all = (int)s_maxlast;
+  const uint2 range = ranges[g];
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
+  unsigned long long evals = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) evals += last[k];
+
+  for (int end = end_all; end > 0; end -= BATCH) {
+    const int start = max(0, end - BATCH);
+    __syncthreads();
+    stage_batch<BATCH>(st, pair_face, range.x + start, end - start, rec_base, rec_u, rec_q, face_col, ax, ay, true);
+    __syncthreads();
+    for (int j = end - 1 - start; j >= 0; --j) {
+      const int pos = start + j;
+      if ((uint32_t)pos >= wmax) continue;  // warp-uniform: no pixel of this warp reaches pos
+      const float4 gg = st.g[j];
+      const float4 hh = st.h[j];
+      const float cb = st.b[j];
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if ((uint32_t)pos >= last[k]) continue;
+        float dx, dy, graw;
+        float alpha = gauss_alpha(gg, hh.x, hh.y, pcx[k], pcy[k], dx, dy, graw);
+        if (alpha < kAlphaMin) continue;
+        any = true;
+        float om = __fsub_rn(1.0f, alpha);
+        float inv = __fdividef(1.0f, om);
+        float Tb = T[k] * inv;
+        float w = alpha * Tb;
+        float cg = hh.z * G0[k] + hh.w * G1[k] + cb * G2[k];
+        float sg = S0[k] * G0[k] + S1[k] * G1[k] + S2[k] * G2[k];
+        float dalpha = Tb * cg - sg * inv;
+        S0[k] += hh.z * w;
+        S1[k] += hh.w * w;
+        S2[k] += cb * w;
+        T[k] = Tb;
+        float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
+        float qx = dq * dx, qy = dq * dy;
+        acc[0] += 2.0f * gg.z * qx + gg.w * qy;
+        acc[1] += gg.w * qx + 2.0f * hh.x * qy;
+        acc[2] += qx * dx;
+        acc[3] += qx * dy;
+        acc[4] += qy * dy;
+        acc[5] += dq;
+        acc[6] += w * G0[k];
+        acc[7] += w * G1[k];
+        acc[8] += w * G2[k];
+      }
+      if (!__any_sync(kFull, any)) continue;
+      float s8 = acc[8];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(kFull, s8, o);
+      float s = warp_reduce8_transposed(acc, lane);
+      if ((lane & 3) == 0) {
+        int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        float* dst;
+        if (vi < 5) dst = reinterpret_cast<float*>(rec_grad + 2 * (size_t)st.rid[j]) + vi;
+        else if (vi == 5) dst = reinterpret_cast<float*>(face_grad + st.face[j]) + 3;
+        else dst = reinterpret_cast<float*>(face_grad + st.face[j]) + (vi - 6);
+        atomicAdd(dst, s);
+      }
+      if (lane == 0) atomicAdd(reinterpret_cast<float*>(face_grad + st.face[j]) + 2, s8);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(kFull, evals, o);
+  if (lane == 0 && evals) atomicAdd(&counters->evals_bwd, evals);
+}
+
+// ---------------------------------------------------------------- loss
+constexpr int kLossThreads = 256;
+constexpr int kLossItems = 16;
+
+__global__ void __launch_bounds__(kLossThreads) k_l2_partial(const float* __restrict__ img,
+                                                              const float* __restrict__ tgt, int64_t n,
+                                                              float* __restrict__ grad, double* __restrict__ part) {
+  __shared__ double sw[kLossThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < kLossItems; ++k) {
+    int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
+    if (i < n) {
+      float d = img[i] - tgt[i];
+      grad[i] = 2.0f * d;
+      acc += (double)d * (double)d;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kLossThreads / 32; ++w) s += sw[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_l2_final(const double* __restrict__ part, int64_t nb, double* __restrict__ loss) {
+  __shared__ double sw[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sw[w];
+    *loss = s;
+  }
+}
+
+__global__ void k_debug_records(const uint32_t* __restrict__ sorted_keys, const uint32_t* __restrict__ sorted_ids,
+                                const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_q, int64_t n_rec,
+                                uint32_t* __restrict__ depth_bits, int32_t* __restrict__ rects,
+                                float* __restrict__ conic) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_rec) return;
+  if (depth_bits) depth_bits[sorted_ids[k]] = sorted_keys[k];
+  if (rects) {
+    uint2 r = rec_rect[k];
+    rects[4 * k] = (int32_t)(r.x & 0xffff);
+    rects[4 * k + 1] = (int32_t)(r.x >> 16);
+    rects[4 * k + 2] = (int32_t)(r.y & 0xffff);
+    rects[4 * k + 3] = (int32_t)(r.y >> 16);
+  }
+  if (conic) {
+    float4 q = rec_q[k];
+    conic[4 * k] = q.x / kNegHalfLog2e;
+    conic[4 * k + 1] = q.y / kNegLog2e;
+    conic[4 * k + 2] = q.z / kNegHalfLog2e;
+    conic[4 * k + 3] = 0.0f;
+  }
+}
+
+template <int TS, int BATCH>
+void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
+                int32_t F, const float* bg, float* images, float* t_out, cudaStream_t s) {
+  k_raster_fwd<TS, BATCH><<<(unsigned)n_tiles, kThreads, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
+                                                                 ws.face_col, views, C, F, bg[0], bg[1], bg[2],
+                                                                 images, ws.pix_T, ws.pix_last, t_out, ws.counters);
+}
+
+template <int TS, int BATCH>
+void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
+                int32_t F, const float* bg, const float* dL, cudaStream_t s) {
+  k_raster_bwd<TS, BATCH><<<(unsigned)n_tiles, kThreads, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
+                                                                 ws.face_col, views, C, F, bg[0], bg[1], bg[2], dL,
+                                                                 ws.pix_T, ws.pix_last, ws.rec_grad, ws.face_grad,
+                                                                 ws.counters);
+}
+
+}  // namespace
+
+cudaError_t launch_emit_pairs(const Workspace& ws, const uint32_t* sorted_rid, int64_t n_rec, const ViewInfo* views,
+                              int32_t F, cudaStream_t s, int64_t* launches) {
+  if (n_rec <= 0) return cudaSuccess;
+  k_emit_pairs<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(sorted_rid, ws.rec_ntiles, ws.rec_rect, ws.rec_off,
+                                                               views, n_rec, F, ws.cap_pairs, ws.pair_tile[0],
+                                                               ws.pair_face[0], ws.counters);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, int64_t cap_pairs, uint2* ranges,
+                               cudaStream_t s, int64_t* launches) {
+  if (cap_pairs <= 0) return cudaSuccess;
+  k_tile_ranges<<<(unsigned)((cap_pairs + 255) / 256), 256, 0, s>>>(tiles, counters, cap_pairs, ranges);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
+                              float* images, float* t_final_out, cudaStream_t s, int64_t* launches) {
+  if (n_tiles <= 0) return cudaSuccess;
+#define GMR_FWD(TS_, B_) \
+  if (tile == TS_ && batch == B_) fwd_launch<TS_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, s)
+  GMR_FWD(16, 64); else GMR_FWD(16, 128); else GMR_FWD(16, 256);
+  else GMR_FWD(32, 64); else GMR_FWD(32, 128); else GMR_FWD(32, 256);
+  else return cudaErrorInvalidValue;
+#undef GMR_FWD
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
+                              const float* dL_dimages, cudaStream_t s, int64_t* launches) {
+  if (n_tiles <= 0) return cudaSuccess;
+#define GMR_BWD(TS_, B_) \
+  if (tile == TS_ && batch == B_) bwd_launch<TS_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, s)
+  GMR_BWD(16, 64); else GMR_BWD(16, 128); else GMR_BWD(16, 256);
+  else GMR_BWD(32, 64); else GMR_BWD(32, 128); else GMR_BWD(32, 256);
+  else return cudaErrorInvalidValue;
+#undef GMR_BWD
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_records(const Workspace& ws, const uint32_t* sorted_keys, const uint32_t* sorted_ids,
+                                 int64_t n_rec, uint32_t* depth_bits, int32_t* rects, float* conic, cudaStream_t s,
+                                 int64_t* launches) {
+  if (n_rec <= 0) return cudaSuccess;
+  k_debug_records<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(sorted_keys, sorted_ids, ws.rec_rect, ws.rec_q,
+                                                                  n_rec, depth_bits, rects, conic);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+int64_t l2_loss_partials_needed(int64_t n) { return (n + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems); }
+
+cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
+                           double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches) {
+  int64_t nb = l2_loss_partials_needed(n);
+  if (nb > n_partials) return cudaErrorInvalidValue;
+  if (nb > 0) {
+    k_l2_partial<<<(unsigned)nb, kLossThreads, 0, s>>>(img, target, n, grad, partials);
+    *launches += 1;
+  }
+  k_l2_final<<<1, 1024, 0, s>>>(partials, nb, loss);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace gmr

@@ -1,0 +1,263 @@
+"""Python front end of the Gaussian Mesh Renderer CUDA library.
+
+``Renderer`` owns one library context (workspace + forward state) and marshals
+torch CUDA tensors into the C ABI of include/gmr.h; ``GMRRender`` is the
+``torch.autograd.Function`` whose forward and backward are the library's
+``gmr_render_fwd`` / ``gmr_render_bwd``. PyTorch only provides device memory
+and streams here.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_COV = {"area": _lib.GMR_COV_AREA, "embed_raw": _lib.GMR_COV_EMBED_RAW}
+_COLOR = {"face": _lib.GMR_COLOR_PER_FACE, "vertex": _lib.GMR_COLOR_PER_VERTEX}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_dev(t: torch.Tensor, name: str, dtype):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def camera_array(cams) -> ctypes.Array:
+    """CAMERA_DTYPE numpy array -> ctypes array of gmr_camera (same bytes)."""
+    a = np.ascontiguousarray(cams)
+    if a.dtype.itemsize != ctypes.sizeof(_lib.GmrCamera):
+        raise ValueError("camera records must be 76 bytes (gmr_inputs.CAMERA_DTYPE)")
+    arr = (_lib.GmrCamera * len(a))()
+    ctypes.memmove(arr, a.ctypes.data, a.nbytes)
+    return arr
+
+
+def pixel_offsets(cams) -> np.ndarray:
+    off = [0]
+    for c in cams:
+        off.append(off[-1] + int(c["width"]) * int(c["height"]))
+    return np.array(off, dtype=np.int64)
+
+
+class Renderer:
+    """One library context on the current CUDA device.
+
+    tile: 16 or 32; batch: Gaussians per shared-memory batch (64/128/256);
+    cov_mode: "area" (Eq. 13) or "embed_raw" (Eq. 15 literally);
+    color_mode: "face" (F x 3 colours) or "vertex" (V x 3, Eq. 16);
+    sync_check: read the pair count back once per forward and grow buffers
+    (False: never synchronise; pre-size with ``reserve`` for graph capture).
+    """
+
+    def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
+                 sync_check=True, profile=False):
+        if not torch.cuda.is_available():
+            raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
+        torch.cuda.init()
+        self._L = _lib.load()
+        self.cfg = _lib.GmrConfig()
+        self._L.gmr_config_default(ctypes.byref(self.cfg))
+        self.cfg.tile = tile
+        self.cfg.batch = batch
+        self.cfg.cov_mode = _COV[cov_mode]
+        self.cfg.color_mode = _COLOR[color_mode]
+        self.cfg.bg[:] = [float(x) for x in bg]
+        self.cfg.flags = (_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
+        self.color_mode = color_mode
+        self._ctx = ctypes.c_void_p()
+        self._check(self._L.gmr_create(ctypes.byref(self.cfg), ctypes.byref(self._ctx)), "gmr_create")
+        self.fwd_token = 0
+        self._saved = None
+
+    # -- plumbing
+    def _check(self, status, what):
+        if status != _lib.GMR_OK:
+            msg = self._L.gmr_last_error(self._ctx).decode() if self._ctx else ""
+            raise _lib.GmrError(f"{what} failed: {_lib.STATUS_NAMES.get(status, status)} {msg}")
+
+    def close(self):
+        if self._ctx:
+            torch.cuda.synchronize()
+            self._L.gmr_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._ctx:
+                self._L.gmr_destroy(self._ctx)
+        except Exception:
+            pass
+
+    def set_config(self, **kw):
+        for k, v in kw.items():
+            if k == "cov_mode":
+                v = _COV[v]
+            if k == "color_mode":
+                self.color_mode = v
+                v = _COLOR[v]
+            if k == "bg":
+                self.cfg.bg[:] = [float(x) for x in v]
+                continue
+            if k == "sync_check":
+                self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_SYNC_CHECK) | (_lib.GMR_FLAG_SYNC_CHECK if v else 0)
+                continue
+            if k == "profile":
+                self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_PROFILE) | (_lib.GMR_FLAG_PROFILE if v else 0)
+                continue
+            setattr(self.cfg, k, v)
+        self._check(self._L.gmr_set_config(self._ctx, ctypes.byref(self.cfg)), "gmr_set_config")
+
+    def reserve(self, max_faces, max_views, max_pixels, max_pairs):
+        self._check(self._L.gmr_reserve(self._ctx, int(max_faces), int(max_views), int(max_pixels), int(max_pairs)),
+                    "gmr_reserve")
+
+    # -- entry points
+    def convert(self, verts, faces, rgb=None, opacity=None, stream=None):
+        _check_dev(verts, "verts", torch.float32)
+        _check_dev(faces, "faces", torch.int32)
+        F = faces.shape[0]
+        dev = verts.device
+        means = torch.empty((F, 3), device=dev, dtype=torch.float32)
+        cov = torch.empty((F, 6), device=dev, dtype=torch.float32)
+        face_rgb = torch.empty((F, 3), device=dev, dtype=torch.float32) if rgb is not None else None
+        face_o = torch.empty((F,), device=dev, dtype=torch.float32)
+        self._check(self._L.gmr_convert(self._ctx, _ptr(verts), verts.shape[0], _ptr(faces), F, _ptr(rgb),
+                                        _ptr(opacity), _ptr(means), _ptr(cov), _ptr(face_rgb), _ptr(face_o),
+                                        _stream(stream)), "gmr_convert")
+        return {"means": means, "cov": cov, "rgb": face_rgb, "opacity": face_o}
+
+    def forward(self, verts, faces, rgb, opacity, cams, images=None, t_final=None, stream=None, want_t=True):
+        """Render all views; returns (images [Npix, 3], t_final [Npix] or None)."""
+        _check_dev(verts, "verts", torch.float32)
+        _check_dev(faces, "faces", torch.int32)
+        _check_dev(rgb, "rgb", torch.float32)
+        if opacity is not None:
+            _check_dev(opacity, "opacity", torch.float32)
+        cam_arr = cams if isinstance(cams, ctypes.Array) else camera_array(cams)
+        npix = sum(int(c.width) * int(c.height) for c in cam_arr)
+        dev = verts.device
+        if images is None:
+            images = torch.empty((npix, 3), device=dev, dtype=torch.float32)
+        if t_final is None and want_t:
+            t_final = torch.empty((npix,), device=dev, dtype=torch.float32)
+        self._check(self._L.gmr_render_fwd(self._ctx, _ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
+                                           _ptr(rgb), _ptr(opacity), cam_arr, len(cam_arr), _ptr(images),
+                                           _ptr(t_final), _stream(stream)), "gmr_render_fwd")
+        self.fwd_token += 1
+        self._saved = (verts, faces, rgb, opacity)
+        return images, t_final
+
+    def backward(self, dL_dimages, dverts=None, drgb=None, dopacity=None, accumulate=False, stream=None):
+        _check_dev(dL_dimages, "dL_dimages", torch.float32)
+        verts, faces, rgb, opacity = self._saved
+        dev = verts.device
+        if dverts is None:
+            dverts = torch.empty_like(verts)
+        if drgb is None:
+            drgb = torch.empty_like(rgb)
+        if dopacity is None and opacity is not None:
+            dopacity = torch.empty_like(opacity)
+        self._check(self._L.gmr_render_bwd(self._ctx, _ptr(dL_dimages), _ptr(dverts), _ptr(drgb), _ptr(dopacity),
+                                           1 if accumulate else 0, _stream(stream)), "gmr_render_bwd")
+        return dverts, drgb, dopacity
+
+    def l2_loss(self, img, target, grad=None, loss=None, stream=None):
+        _check_dev(img, "img", torch.float32)
+        _check_dev(target, "target", torch.float32)
+        if grad is None:
+            grad = torch.empty_like(img)
+        if loss is None:
+            loss = torch.empty((), device=img.device, dtype=torch.float64)
+        self._check(self._L.gmr_l2_loss(self._ctx, _ptr(img), _ptr(target), img.numel(), _ptr(grad), _ptr(loss),
+                                        _stream(stream)), "gmr_l2_loss")
+        return loss, grad
+
+    def device_status(self, stream=None) -> int:
+        st = ctypes.c_uint32()
+        self._check(self._L.gmr_get_device_status(self._ctx, _stream(stream), ctypes.byref(st)),
+                    "gmr_get_device_status")
+        return int(st.value)
+
+    def stats(self, stream=None) -> dict:
+        s = _lib.GmrStats()
+        self._check(self._L.gmr_get_stats(self._ctx, _stream(stream), ctypes.byref(s)), "gmr_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in _lib.GmrStats._fields_}
+
+    def stage_times(self, stream=None) -> dict:
+        """Milliseconds of each stage's last profiled run (None if not run)."""
+        ms = (ctypes.c_float * len(_lib.STAGES))()
+        self._check(self._L.gmr_get_stage_times(self._ctx, _stream(stream), ms), "gmr_get_stage_times")
+        return {k: (float(ms[i]) if ms[i] >= 0 else None) for i, k in enumerate(_lib.STAGES)}
+
+    def debug_state(self, n_views, n_faces, n_tiles, n_pixels, stream=None):
+        """Copies of the last forward's binning data (for tests)."""
+        dev = torch.device("cuda")
+        R = n_views * n_faces
+        depth = torch.empty(R, dtype=torch.int32, device=dev)
+        rects = torch.empty((R, 4), dtype=torch.int32, device=dev)
+        rec_u = torch.empty((R, 4), dtype=torch.float32, device=dev)
+        conic = torch.empty((R, 4), dtype=torch.float32, device=dev)
+        ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device=dev)
+        n_last = torch.empty(n_pixels, dtype=torch.int32, device=dev)
+        npairs = ctypes.c_int64()
+        self._check(self._L.gmr_debug_forward_state(self._ctx, _ptr(depth), _ptr(rects), None, None, 0, _ptr(ranges),
+                                                    _ptr(rec_u), _ptr(conic), _ptr(n_last), ctypes.byref(npairs),
+                                                    _stream(stream)), "gmr_debug_forward_state")
+        P = int(npairs.value)
+        tiles = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
+        fids = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
+        self._check(self._L.gmr_debug_forward_state(self._ctx, None, None, _ptr(tiles), _ptr(fids), max(P, 1), None,
+                                                    None, None, None, ctypes.byref(npairs), _stream(stream)),
+                    "gmr_debug_forward_state")
+        torch.cuda.synchronize()
+        u32 = lambda t: t.cpu().numpy().view(np.uint32)
+        return {"depth_bits": u32(depth), "rects": rects.cpu().numpy(), "rec_u": rec_u.cpu().numpy(),
+                "conic": conic.cpu().numpy()[:, :3], "ranges": u32(ranges), "n_last": u32(n_last),
+                "tile_ids": u32(tiles)[:P], "face_ids": u32(fids)[:P], "n_pairs": P}
+
+
+class GMRRender(torch.autograd.Function):
+    """images = GMRRender.apply(verts, rgb, opacity, faces, cams, renderer)
+
+    Differentiable w.r.t. verts (V x 3), rgb and opacity (per face). The
+    backward runs gmr_render_bwd on the renderer's stored forward state, so a
+    renderer serves one outstanding forward at a time.
+    """
+
+    @staticmethod
+    def forward(ctx, verts, rgb, opacity, faces, cams, renderer: Renderer):
+        images, _ = renderer.forward(verts, faces, rgb, opacity, cams, want_t=False)
+        ctx.renderer = renderer
+        ctx.token = renderer.fwd_token
+        ctx.has_opacity = opacity is not None
+        return images
+
+    @staticmethod
+    def backward(ctx, dimg):
+        r: Renderer = ctx.renderer
+        if r.fwd_token != ctx.token:
+            raise _lib.GmrError("the renderer ran another forward before this backward")
+        dverts, drgb, dop = r.backward(dimg.contiguous())
+        return dverts, drgb, (dop if ctx.has_opacity else None), None, None, None
+
+
+def render(verts, faces, rgb, opacity, cams, renderer: Renderer):
+    """Differentiable batched render of all views (packed [Npix, 3])."""
+    return GMRRender.apply(verts, rgb, opacity, faces, cams, renderer)

@@ -1,0 +1,208 @@
+"""GPU behaviour beyond parity: invariances (tile size, batch size, batched
+vs per-view), CUDA-graph capture, edge cases and error reporting (host-side
+errors and device status words; nothing here faults or hangs a GPU)."""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import gmr_inputs as gi
+import oracle
+from gpu_util import DEV, GRAD_TOL, IMG_TOL, rel_l2, render_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _renderer(**kw):
+    from paper_2602_14493_b300 import Renderer
+
+    return Renderer(**kw)
+
+
+def _uneven():
+    v, f = gi.icosphere(4)
+    rng = np.random.default_rng(5)
+    cams = gi.fibonacci_cameras(6, 3.0, [(256, 256), (384, 384), (100, 37), (512, 512), (33, 65), (128, 128)])
+    return gi.Scene("uneven4", v.astype(np.float32), f, rng.random((len(f), 3)).astype(np.float32),
+                    np.full(len(f), 0.9, np.float32), cams)
+
+
+def test_image_invariant_to_tile_and_batch_size():
+    s = _uneven()
+    ref = None
+    for tile in (16, 32):
+        for batch in (64, 128, 256):
+            r = _renderer(tile=tile, batch=batch)
+            _, img, T = render_gpu(r, s)
+            a = img.cpu().numpy()
+            if ref is None:
+                ref = a
+            else:
+                np.testing.assert_array_equal(a, ref)
+            r.close()
+
+
+def test_batched_equals_per_view():
+    s = _uneven()
+    r = _renderer()
+    (v, f, c, o), img, T = render_gpu(r, s)
+    g = torch.randn_like(img)
+    dv, dc, do = r.backward(g)
+    dv, dc, do = dv.clone(), dc.clone(), do.clone()
+    off = oracle.pixel_offsets(s.cams)
+    dv2 = torch.zeros_like(dv)
+    dc2 = torch.zeros_like(dc)
+    do2 = torch.zeros_like(do)
+    for k in range(len(s.cams)):
+        im1, _ = r.forward(v, f, c, o, s.cams[k:k + 1])
+        np.testing.assert_array_equal(im1.cpu().numpy(), img[off[k]:off[k + 1]].cpu().numpy())
+        r.backward(g[off[k]:off[k + 1]].contiguous(), dv2, dc2, do2, accumulate=True)
+    torch.cuda.synchronize()
+    assert rel_l2(dv2.cpu().numpy(), dv.cpu().numpy()) < 1e-5
+    assert rel_l2(dc2.cpu().numpy(), dc.cpu().numpy()) < 1e-5
+    assert rel_l2(do2.cpu().numpy(), do.cpu().numpy()) < 1e-5
+    r.close()
+
+
+def test_cuda_graph_capture_replays_fwd_loss_bwd():
+    s = gi.scene_ring(level=4, n_views=4, res=256)
+    r = _renderer(sync_check=True)
+    v, f, c, o = to_dev(s)
+    target = torch.rand((s.n_pixels, 3), device=DEV)
+    img0, _ = r.forward(v, f, c, o, s.cams)
+    P = r.stats()["n_pairs"]
+    r.set_config(sync_check=False)
+    r.reserve(len(s.faces), len(s.cams), s.n_pixels, int(P * 1.5) + 1024)
+    cams = __import__("paper_2602_14493_b300").camera_array(s.cams)
+    img = torch.empty((s.n_pixels, 3), device=DEV)
+    dv = torch.empty_like(v)
+    dc = torch.empty_like(c)
+    do = torch.empty_like(o)
+    grad = torch.empty_like(img)
+    loss = torch.empty((), dtype=torch.float64, device=DEV)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        # eager warm-up on the capture stream (uploads the camera table)
+        r.forward(v, f, c, o, cams, images=img, want_t=False, stream=stream)
+        r.l2_loss(img, target, grad, loss, stream=stream)
+        r.backward(grad, dv, dc, do, stream=stream)
+    stream.synchronize()
+    eager = (img.clone(), dv.clone(), dc.clone(), do.clone(), loss.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        r.forward(v, f, c, o, cams, images=img, want_t=False, stream=stream)
+        r.l2_loss(img, target, grad, loss, stream=stream)
+        r.backward(grad, dv, dc, do, stream=stream)
+    for _ in range(3):
+        img.zero_(); dv.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    assert r.device_status() == 0
+    np.testing.assert_array_equal(img.cpu().numpy(), eager[0].cpu().numpy())
+    np.testing.assert_array_equal(img.cpu().numpy(), img0.cpu().numpy())
+    assert rel_l2(dv.cpu().numpy(), eager[1].cpu().numpy()) < 1e-5
+    assert abs(float(loss) - float(eager[4])) <= 1e-9 * abs(float(eager[4]))
+    r.close()
+
+
+def test_empty_mesh_and_offscreen_views_render_background():
+    r = _renderer(bg=(0.25, 0.5, 0.75))
+    s = gi.scene_single_view(level=1, width=40, height=24)
+    v, f, c, o = to_dev(s)
+    img, T = r.forward(v, f[:0].contiguous(), c[:0].contiguous(), o[:0].contiguous(), s.cams)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(img.cpu().numpy(), np.tile([0.25, 0.5, 0.75], (40 * 24, 1)), atol=0)
+    assert np.all(T.cpu().numpy() == 1.0)
+    dv, dc, do = r.backward(torch.ones_like(img))
+    # camera looking away from the mesh
+    cam = gi.look_at((0.0, 0.0, 3.0), 31, 17, target=(0.0, 0.0, 10.0))
+    cams = np.array([cam], dtype=gi.CAMERA_DTYPE)
+    img, T = r.forward(v, f, c, o, cams)
+    torch.cuda.synchronize()
+    assert np.all(T.cpu().numpy() == 1.0)
+    dv, dc, do = r.backward(torch.ones_like(img))
+    torch.cuda.synchronize()
+    assert float(dv.abs().max()) == 0.0
+    assert r.device_status() == 0
+    r.close()
+
+
+def test_tiny_and_degenerate_inputs_match_oracle():
+    r = _renderer()
+    # one facet; a collinear (zero-area) facet; a facet behind the camera
+    cams = gi.ring_cameras(2, 10.0, 2.5, 9, 13)
+    v = np.array([[0, 0, 0], [0.3, 0, 0.1], [0, 0.25, 0.2],
+                  [0.1, 0.1, 0.1], [0.2, 0.2, 0.2], [0.3, 0.3, 0.3],
+                  [0, 0, 9], [0.1, 0, 9], [0, 0.1, 9]], dtype=np.float32)
+    faces = np.arange(9, dtype=np.int32).reshape(3, 3)
+    s = gi.Scene("tiny", v, faces, np.random.default_rng(0).random((3, 3)).astype(np.float32),
+                 np.array([0.8, 0.9, 1.0], np.float32), cams)
+    _, img, T = render_gpu(r, s)
+    ref = oracle.render(s)
+    ok = ref["flags"] == 0
+    assert np.abs(img.cpu().numpy() - ref["rgb"]).max(1)[ok].max() <= IMG_TOL
+    g = np.random.default_rng(1).normal(size=ref["rgb"].shape).astype(np.float32)
+    g[~ok] = 0
+    dv, dc, do = r.backward(torch.from_numpy(g).to(DEV))
+    ob = oracle.backward(s, g.astype(np.float64))
+    assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    r.close()
+
+
+def test_host_side_argument_errors():
+    from paper_2602_14493_b300 import GmrError, _lib
+
+    r = _renderer()
+    s = gi.scene_single_view(level=1, width=16, height=16)
+    v, f, c, o = to_dev(s)
+    # backward before any forward
+    st = r._L.gmr_render_bwd(r._ctx, ctypes.c_void_p(torch.zeros(3, device=DEV).data_ptr()), None, None, None, 0, None)
+    assert st == 6  # GMR_ERR_STATE
+    with pytest.raises(GmrError):
+        r.set_config(tile=8)
+    with pytest.raises(GmrError):
+        r.set_config(batch=100)
+    bad = s.cams.copy()
+    bad[0]["width"] = 0
+    with pytest.raises(GmrError):
+        r.forward(v, f, c, o, bad)
+    L = r._L
+    assert L.gmr_render_fwd(r._ctx, None, 5, None, 3, None, None, None, 1, None, None, None) == 1
+    r.close()
+
+
+def test_device_status_bad_face_and_pair_overflow():
+    r = _renderer()
+    s = gi.scene_single_view(level=4, width=256, height=256)
+    v, f, c, o = to_dev(s)
+    fb = f.clone()
+    fb[3, 1] = 10 ** 6
+    img, T = r.forward(v, fb, c, o, s.cams)
+    torch.cuda.synchronize()
+    assert r.device_status() & 1
+    assert r.device_status() == 0  # cleared by the read
+    # no-sync mode with a pair buffer that is too small: reported, no fault
+    r2 = _renderer(sync_check=False)
+    r2.reserve(len(s.faces), 1, 256 * 256, 16)
+    img, T = r2.forward(v, f, c, o, s.cams)
+    torch.cuda.synchronize()
+    assert r2.device_status() & 2
+    r2.close()
+    r.close()
+
+
+def test_stats_and_launch_count():
+    r = _renderer()
+    s = gi.scene_single_view()
+    (v, f, c, o), img, T = render_gpu(r, s)
+    st0 = r.stats()
+    r.backward(torch.ones_like(img))
+    st = r.stats()
+    assert st["n_pairs"] == len(oracle.sorted_pairs(s.verts, s.faces, s.cams, 16)[0])
+    assert st["n_pixels"] == 128 * 128 and st["n_tiles"] == 64
+    assert st["evals_fwd"] > 0 and st["evals_bwd"] > 0
+    assert st["launches"] > st0["launches"] >= 10
+    r.close()

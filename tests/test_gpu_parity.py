@@ -1,0 +1,213 @@
+"""GPU parity of the CUDA path (called through the C ABI) against the FP64
+oracle: conversion, binning (bit-exact), projected records, images, and
+gradients."""
+
+import numpy as np
+import pytest
+import torch
+
+import gmr_inputs as gi
+import oracle
+from gpu_util import DEV, GRAD_TOL, IMG_TOL, rel_l2, render_gpu, sample_pixels, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    from paper_2602_14493_b300 import Renderer
+
+    r = Renderer()
+    yield r
+    r.close()
+
+
+def _uneven_scene():
+    v, f = gi.icosphere(3)
+    rng = np.random.default_rng(31)
+    cams = gi.fibonacci_cameras(5, 3.0, [(256, 256), (100, 37), (64, 200), (17, 5), (384, 384)])
+    return gi.Scene("uneven", v.astype(np.float32), f, rng.random((len(f), 3)).astype(np.float32),
+                    rng.uniform(0.3, 1.0, len(f)).astype(np.float32), cams)
+
+
+def _scenes():
+    return {
+        "icosphere3_1x128": gi.scene_single_view(),
+        "soup": gi.random_triangle_soup(7, 150, n_views=3, res=(100, 37)),
+        "uneven": _uneven_scene(),
+    }
+
+
+# ------------------------------------------------------------------ conversion
+@pytest.mark.parametrize("cov_mode", ["area", "embed_raw"])
+@pytest.mark.parametrize("color_mode", ["face", "vertex"])
+def test_convert_matches_oracle(cov_mode, color_mode):
+    from paper_2602_14493_b300 import Renderer
+
+    r = Renderer(cov_mode=cov_mode, color_mode=color_mode)
+    for s in (gi.scene_ring(), gi.random_triangle_soup(3, 1000)):
+        rgb = s.rgb if color_mode == "face" else np.random.default_rng(1).random((len(s.verts), 3)).astype(np.float32)
+        v, f, c, o = to_dev(s, rgb)
+        o_in = o.clone()
+        o_in[::7] = 1.7
+        o_in[1::11] = -0.2
+        out = r.convert(v, f, c, o_in)
+        torch.cuda.synchronize()
+        ref = oracle.convert(s.verts.astype(np.float64), s.faces, cov_mode=0 if cov_mode == "area" else 1)
+        means = out["means"].cpu().numpy()
+        np.testing.assert_allclose(means, ref["means"], atol=3e-7 * np.abs(ref["means"]).max())
+        cov = out["cov"].cpu().numpy()
+        full = ref["cov"]
+        six = np.stack([full[:, 0, 0], full[:, 0, 1], full[:, 0, 2], full[:, 1, 1], full[:, 1, 2], full[:, 2, 2]], 1)
+        scale = np.abs(six).max(1, keepdims=True)
+        assert np.all(np.abs(cov - six) <= 1e-5 * scale + 1e-13)
+        fc = rgb if color_mode == "face" else rgb.astype(np.float64)[s.faces].mean(1)
+        np.testing.assert_allclose(out["rgb"].cpu().numpy(), fc, atol=1e-7)
+        np.testing.assert_array_equal(out["opacity"].cpu().numpy(), np.clip(o_in.cpu().numpy(), 0, 1))
+    assert r.device_status() == 0
+    r.close()
+
+
+# ------------------------------------------------------------------ binning
+@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven"])
+def test_binning_bit_exact(renderer, tile, name):
+    s = _scenes()[name]
+    renderer.set_config(tile=tile)
+    render_gpu(renderer, s)
+    tx, ty = oracle.tile_counts(s.cams, tile)
+    n_tiles = int(sum(a * b for a, b in zip(tx, ty)))
+    st = renderer.debug_state(len(s.cams), len(s.faces), n_tiles, s.n_pixels)
+    ob = oracle.bins(s.verts, s.faces, s.cams, tile)
+    vis = ob["visible"]
+    gvis = st["depth_bits"] != 0xFFFFFFFF
+    np.testing.assert_array_equal(gvis, vis)
+    np.testing.assert_array_equal(st["depth_bits"][vis], ob["depth_bits"][vis])
+    # rectangles: identical where non-empty; empty on both sides otherwise
+    orect, grect = ob["rect"], st["rects"]
+    oe = (orect[:, 0] > orect[:, 1]) | (orect[:, 2] > orect[:, 3]) | ~vis
+    ge = (grect[:, 0] > grect[:, 1]) | (grect[:, 2] > grect[:, 3])
+    np.testing.assert_array_equal(ge, oe)
+    np.testing.assert_array_equal(grect[~oe], orect[~oe])
+    tiles, fids, ranges = oracle.sorted_pairs(s.verts, s.faces, s.cams, tile)
+    assert st["n_pairs"] == len(tiles)
+    np.testing.assert_array_equal(st["tile_ids"], tiles)
+    np.testing.assert_array_equal(st["face_ids"], fids)
+    np.testing.assert_array_equal(st["ranges"], ranges)
+    renderer.set_config(tile=16)
+
+
+def test_records_match_oracle_projection(renderer):
+    s = _scenes()["uneven"]
+    render_gpu(renderer, s)
+    tx, ty = oracle.tile_counts(s.cams, 16)
+    st = renderer.debug_state(len(s.cams), len(s.faces), int(sum(a * b for a, b in zip(tx, ty))), s.n_pixels)
+    conv = oracle.convert(s.verts.astype(np.float64), s.faces)
+    pr = oracle.project(conv["means"], conv["cov"], s.cams)
+    rect = st["rects"]
+    live = rect[:, 0] <= rect[:, 1]
+    u = st["rec_u"][:, :2].astype(np.float64) + st["rec_u"][:, 2:].astype(np.float64)
+    assert np.abs(u[live] - pr["u"][live]).max() < 1e-5
+    q = st["conic"][live].astype(np.float64)
+    qo = pr["conic"][live]
+    scale = np.abs(qo).max(1, keepdims=True)
+    assert np.all(np.abs(q - qo) <= 2e-5 * scale)
+
+
+# ------------------------------------------------------------------ images
+@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven"])
+@pytest.mark.parametrize("tile", [16, 32])
+def test_image_matches_oracle(renderer, name, tile):
+    s = _scenes()[name]
+    renderer.set_config(tile=tile, bg=(0.1, 0.2, 0.3))
+    _, img, T = render_gpu(renderer, s)
+    ref = oracle.render(s, bg=(0.1, 0.2, 0.3))
+    amb = (ref["flags"] & (oracle.FLAG_ALPHA_SKIP | oracle.FLAG_TERMINATE)) != 0
+    err = np.abs(img.cpu().numpy() - ref["rgb"]).max(1)
+    terr = np.abs(T.cpu().numpy() - ref["T"])
+    assert amb.mean() < 1e-3
+    assert err[~amb].max() <= IMG_TOL, (err[~amb].max(), np.argmax(np.where(amb, 0, err)))
+    assert terr[~amb].max() <= IMG_TOL
+    assert renderer.device_status() == 0
+    renderer.set_config(tile=16, bg=(0.0, 0.0, 0.0))
+
+
+def test_image_full_size_ring_sampled(renderer):
+    """The 8 x 512^2 ring workload at full size, in the benchmark's launch
+    configuration (batched, tile 16, batch 256), on sampled pixels."""
+    s = gi.scene_ring()
+    _, img, T = render_gpu(renderer, s)
+    pix, lin = sample_pixels(s.cams, 2400, 5)
+    ref = oracle.render(s, pixels=pix)
+    amb = (ref["flags"] & (oracle.FLAG_ALPHA_SKIP | oracle.FLAG_TERMINATE)) != 0
+    g = img.cpu().numpy()[lin]
+    err = np.abs(g - ref["rgb"]).max(1)
+    assert err[~amb].max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy()[lin] - ref["T"])[~amb].max() <= IMG_TOL
+    # whole-image invariants
+    a = img.cpu().numpy()
+    t = T.cpu().numpy()
+    assert np.all(a >= 0) and np.all(a <= 1.0 + 1e-6) and np.all(t >= 1e-4 - 1e-9) and np.all(t <= 1.0)
+
+
+# ------------------------------------------------------------------ gradients
+@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven"])
+@pytest.mark.parametrize("cov_mode", ["area", "embed_raw"])
+def test_gradients_match_oracle(name, cov_mode):
+    from paper_2602_14493_b300 import Renderer
+
+    r = Renderer(cov_mode=cov_mode, bg=(0.2, 0.1, 0.4))
+    s = _scenes()[name]
+    cm = 0 if cov_mode == "area" else 1
+    ref = oracle.render(s, cov_mode=cm, bg=(0.2, 0.1, 0.4))
+    rng = np.random.default_rng(11)
+    g = rng.normal(size=ref["rgb"].shape).astype(np.float32)
+    g[ref["flags"] != 0] = 0.0
+    (v, f, c, o), img, T = render_gpu(r, s)
+    dv, dc, do = r.backward(torch.from_numpy(g).to(DEV))
+    torch.cuda.synchronize()
+    ob = oracle.backward(s, g.astype(np.float64), cov_mode=cm, bg=(0.2, 0.1, 0.4))
+    assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    assert rel_l2(do.cpu().numpy(), ob["dopacity"]) <= GRAD_TOL
+    r.close()
+
+
+def test_gradients_full_size_ring_sparse(renderer):
+    """Full-size ring workload; dL/dI non-zero on sampled pixels only, so the
+    oracle's backward over those pixels is the exact reference."""
+    s = gi.scene_ring()
+    (v, f, c, o), img, T = render_gpu(renderer, s)
+    pix, lin = sample_pixels(s.cams, 2400, 6)
+    ref = oracle.render(s, pixels=pix)
+    rng = np.random.default_rng(12)
+    gs = rng.normal(size=(len(pix), 3))
+    gs[ref["flags"] != 0] = 0.0
+    g = np.zeros((s.n_pixels, 3), dtype=np.float32)
+    g[lin] = gs
+    dv, dc, do = renderer.backward(torch.from_numpy(g).to(DEV))
+    torch.cuda.synchronize()
+    ob = oracle.backward(s, gs.astype(np.float32).astype(np.float64), pixels=pix)
+    assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    assert rel_l2(do.cpu().numpy(), ob["dopacity"]) <= GRAD_TOL
+
+
+def test_per_vertex_colour_gradients():
+    from paper_2602_14493_b300 import Renderer
+
+    r = Renderer(color_mode="vertex")
+    s0 = gi.scene_single_view()
+    vcol = np.random.default_rng(3).random((len(s0.verts), 3)).astype(np.float32)
+    s = gi.Scene("v", s0.verts, s0.faces, vcol, s0.opacity, s0.cams)
+    ref = oracle.render(s, color_mode=1)
+    g = np.random.default_rng(4).normal(size=ref["rgb"].shape).astype(np.float32)
+    g[ref["flags"] != 0] = 0
+    _, img, _ = render_gpu(r, s)
+    amb = ref["flags"] != 0
+    assert np.abs(img.cpu().numpy() - ref["rgb"]).max(1)[~amb].max() <= IMG_TOL
+    dv, dc, _ = r.backward(torch.from_numpy(g).to(DEV))
+    ob = oracle.backward(s, g.astype(np.float64), color_mode=1)
+    assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    r.close()
