@@ -72,75 +72,68 @@ def measured_peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """Samples SM clock, power and clock-event reasons through NVML."""
+    """Samples SM clock, power and clock-event reasons with nvidia-smi while
+    the benchmark runs (read-only queries)."""
 
-    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
-               0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, device_index, period=0.1):
+    def __init__(self, local_rank, period_ms=100):
         self.samples = []
-        self.period = period
-        self.ok = False
-        self._stop = threading.Event()
-        try:
-            import pynvml
+        self.proc = None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.cmd = ["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                    f"-lms", str(period_ms)]
 
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = None
+    def _reader(self):
+        for line in self.proc.stdout:
+            t = time.perf_counter()
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 7:
+                continue
             try:
-                import torch
-
-                uuid = str(torch.cuda.get_device_properties(device_index).uuid)
-                self.h = pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid) if not uuid.startswith("GPU") else uuid)
-            except Exception:
-                self.h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            self.ok = True
-        except Exception as e:  # no NVML: report no clocks
-            log(f"clock sampling unavailable: {e}")
-
-    def _run(self):
-        nv = self.nv
-        while not self._stop.is_set():
-            try:
-                t = time.perf_counter()
-                mhz = nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
-                try:
-                    rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                except Exception:
-                    rs = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
-                pw = nv.nvmlDeviceGetPowerUsage(self.h) / 1000.0
-                self.samples.append((t, mhz, rs, pw))
-            except Exception:
-                pass
-            self._stop.wait(self.period)
+                mhz, mx, pw = float(parts[0]), float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            active = [n for n, v in zip(self.NAMES, parts[3:]) if v.lower() == "active"]
+            self.samples.append((t, mhz, mx, pw, active))
 
     def start(self):
-        if self.ok:
-            self.th = threading.Thread(target=self._run, daemon=True)
-            self.th.start()
+        import subprocess
+
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError as e:
+            log(f"clock sampling unavailable: {e}")
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._reader, daemon=True)
+        self.th.start()
 
     def stop(self):
-        if self.ok:
-            self._stop.set()
-            self.th.join()
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.th.join(timeout=5)
 
     def summary(self, t0, t1):
-        if not self.ok or not self.samples:
+        if not self.samples:
             return None
-        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        inside = [s for s in self.samples if t0 <= s[0] <= t1 + 0.15]
         window = "timed"
         if len(inside) < 3:
             inside = self.samples
             window = "warmup+timed"
-        reasons = set()
-        for s in inside:
-            for bit, name in self.REASONS.items():
-                if s[2] & bit and name != "gpu_idle":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+        reasons = sorted({n for s in inside for n in s[4]})
+        return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": max(s[2] for s in inside),
+                "reasons": reasons, "samples": len(inside), "window": window,
                 "power_w_max": max(s[3] for s in inside)}
 
 
@@ -191,9 +184,11 @@ def oracle_sample_time(scene, n_pix, seed=0):
 
 def cpu_baseline(scene, target_seconds):
     oracle_sample_time(scene, 4)  # build + warm
-    t_small = oracle_sample_time(scene, 32)
-    per_px = max(t_small / 32, 1e-6)
-    n = int(max(64, min(200000, target_seconds / per_px)))
+    t_a = oracle_sample_time(scene, 32)
+    t_b = oracle_sample_time(scene, 288)
+    per_px = max((t_b - t_a) / 256, 1e-7)
+    fixed = max(t_a - 32 * per_px, 0.0)
+    n = int(max(64, min(400000, (target_seconds - fixed) / per_px)))
     t = oracle_sample_time(scene, n, seed=1)
     return {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
@@ -232,6 +227,8 @@ def run_gmr(args, ws, rank, local):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sampler = ClockSampler(local, period_ms=50)
+    sampler.start()
     scene = WORKLOADS[args.workload]()
     C, F = len(scene.cams), len(scene.faces)
     n_pix = scene.n_pixels
@@ -242,11 +239,19 @@ def run_gmr(args, ws, rank, local):
     o = torch.from_numpy(scene.opacity).to(dev)
     cams = camera_array(scene.cams)
 
-    r = Renderer(tile=args.tile, batch=args.batch, profile=True)
+    r = Renderer(profile=True)
     # target: render of the jittered mesh
     vt = torch.from_numpy(scene.extra["target_verts"]).to(dev)
     target, _ = r.forward(vt, f, c, o, cams, want_t=False)
     target = target.clone()
+    if args.tile == "auto":
+        from paper_2602_14493_b300.autotune import tune
+
+        (tile, threads, batch), tuned = tune(r, v, f, c, o, cams, target, use_cache=False)
+        log("autotune:", {f"{k[0]}x{k[1]}x{k[2]}": round(t, 4) for k, t in tuned.items()})
+    else:
+        tile, threads, batch = int(args.tile), args.threads, args.batch
+        r.set_config(tile=tile, threads=threads, batch=batch)
     img, _ = r.forward(v, f, c, o, cams, want_t=False)
     torch.cuda.synchronize()
     P = r.stats()["n_pairs"]
@@ -273,8 +278,6 @@ def run_gmr(args, ws, rank, local):
     launches_per_step = r.stats()["launches"] - l0
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    sampler = ClockSampler(local)
-    sampler.start()
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
@@ -398,8 +401,9 @@ def run_gmr(args, ws, rank, local):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "fp32", "data": "synthetic",
         "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
-                   "form": "batched, one call for all views, CUDA graph", "tile": args.tile,
-                   "batch": args.batch, "l2": "flushed between timed steps (512 MB write)",
+                   "form": "batched, one call for all views, CUDA graph", "tile": tile, "threads": threads,
+                   "batch": batch, "shape_choice": "autotuned" if args.tile == "auto" else "fixed",
+                   "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "per_view": {"value": n_pix / (pv_ms / 1e3) / 1e6, "ms_per_step": pv_ms, "form": "one call per view, eager"},
         "batched_eager": {"value": n_pix / (be_ms / 1e3) / 1e6, "ms_per_step": be_ms},
@@ -448,7 +452,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gmr", choices=["gmr", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", default="auto", help="16, 32 or auto (autotuner)")
+    ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

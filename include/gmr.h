@@ -88,6 +88,8 @@ typedef struct {
  * low-pass term is added to every projected covariance. */
 typedef struct {
   int32_t tile;       /* tile edge in pixels: 16 or 32 */
+  int32_t threads;    /* threads per tile: 64, 128 or 256 (16x16 tiles), 256 (32x32);
+                         each thread composites tile^2 / threads pixels */
   int32_t batch;      /* Gaussians staged per shared-memory batch: 64, 128 or 256 */
   int32_t cov_mode;   /* gmr_cov_mode */
   int32_t color_mode; /* gmr_color_mode */
@@ -136,7 +138,7 @@ typedef struct {
   int64_t pair_capacity; /* current pair buffer capacity */
 } gmr_stats;
 
-/* Fills *cfg with the defaults: tile 16, batch 256, GMR_COV_AREA,
+/* Fills *cfg with the defaults: tile 16, 256 threads, batch 256, GMR_COV_AREA,
  * GMR_COLOR_PER_FACE, black background, GMR_FLAG_SYNC_CHECK. */
 GMR_API gmr_status gmr_config_default(gmr_config* cfg);
 

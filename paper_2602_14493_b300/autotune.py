@@ -1,0 +1,96 @@
+"""Autotuner for the rasterizer's launch shape: tile size, threads per tile
+and Gaussians per shared-memory batch.
+
+Every candidate renders the same forward + L2 loss + backward step; the
+fastest (median of CUDA-event timings after warm-up) wins. Images do not
+depend on the choice (the compositing order and arithmetic are the same for
+all shapes), so tuning never changes results. Choices are cached in a JSON
+file keyed by the workload signature (faces, views, resolution multiset).
+"""
+
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import statistics
+
+import torch
+
+CANDIDATES = [
+    (16, 256, 256), (16, 256, 128), (16, 256, 64),
+    (16, 128, 256), (16, 128, 128), (16, 128, 64),
+    (16, 64, 256), (16, 64, 128), (16, 64, 64),
+    (32, 256, 256), (32, 256, 128),
+]
+
+
+def cache_path() -> str:
+    return os.environ.get("GMR_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "gmr_b300_autotune.json"))
+
+
+def signature(n_faces, cams) -> str:
+    res = sorted((int(c["width"]) if not hasattr(c, "width") else int(c.width),
+                  int(c["height"]) if not hasattr(c, "height") else int(c.height)) for c in cams)
+    dev = torch.cuda.get_device_name()
+    key = json.dumps([n_faces, len(res), res, dev])
+    return hashlib.sha1(key.encode()).hexdigest()[:16]
+
+
+def _load():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d):
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        with open(p + ".tmp", "w") as f:
+            json.dump(d, f, indent=1)
+        os.replace(p + ".tmp", p)
+    except OSError:
+        pass
+
+
+def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=CANDIDATES, use_cache=True):
+    """Times each candidate shape on this workload and configures
+    ``renderer`` with the fastest. Returns (best (tile, threads, batch),
+    {shape: median ms})."""
+    sig = signature(faces.shape[0], cams)
+    cache = _load() if use_cache else {}
+    if use_cache and sig in cache:
+        best = tuple(cache[sig]["best"])
+        renderer.set_config(tile=best[0], threads=best[1], batch=best[2])
+        return best, {}
+    stream = torch.cuda.current_stream()
+    img = torch.empty((target.shape[0], 3), device=verts.device)
+    grad = torch.empty_like(img)
+    loss = torch.empty((), dtype=torch.float64, device=verts.device)
+    dv, dc = torch.empty_like(verts), torch.empty_like(rgb)
+    do = torch.empty_like(opacity) if opacity is not None else None
+    results = {}
+    for tile, threads, batch in candidates:
+        renderer.set_config(tile=tile, threads=threads, batch=batch)
+        ts = []
+        for rep in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            renderer.forward(verts, faces, rgb, opacity, cams, images=img, want_t=False)
+            renderer.l2_loss(img, target, grad, loss)
+            renderer.backward(grad, dv, dc, do)
+            b.record(stream)
+            b.synchronize()
+            if rep >= 2:
+                ts.append(a.elapsed_time(b))
+        results[(tile, threads, batch)] = statistics.median(ts)
+    best = min(results, key=results.get)
+    renderer.set_config(tile=best[0], threads=best[1], batch=best[2])
+    if use_cache:
+        cache[sig] = {"best": list(best), "ms": {f"{k[0]}x{k[1]}x{k[2]}": v for k, v in results.items()}}
+        _store(cache)
+    return best, results

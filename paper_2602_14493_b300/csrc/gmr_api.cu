@@ -60,6 +60,11 @@ gmr_status cuda_fail(gmr_ctx* ctx, cudaError_t e, const char* where) {
 
 bool valid_config(const gmr_config* c, std::string* why) {
   if (c->tile != 16 && c->tile != 32) { *why = "tile must be 16 or 32"; return false; }
+  if (c->tile == 16 && c->threads != 64 && c->threads != 128 && c->threads != 256) {
+    *why = "threads must be 64, 128 or 256 with 16x16 tiles";
+    return false;
+  }
+  if (c->tile == 32 && c->threads != 256) { *why = "threads must be 256 with 32x32 tiles"; return false; }
   if (c->batch != 64 && c->batch != 128 && c->batch != 256) { *why = "batch must be 64, 128 or 256"; return false; }
   if (c->cov_mode != GMR_COV_AREA && c->cov_mode != GMR_COV_EMBED_RAW) { *why = "bad cov_mode"; return false; }
   if (c->color_mode != GMR_COLOR_PER_FACE && c->color_mode != GMR_COLOR_PER_VERTEX) {
@@ -267,6 +272,7 @@ gmr_status gmr_config_default(gmr_config* cfg) {
   if (!cfg) return GMR_ERR_INVALID_ARG;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->tile = 16;
+  cfg->threads = 256;
   cfg->batch = 256;
   cfg->cov_mode = GMR_COV_AREA;
   cfg->color_mode = GMR_COLOR_PER_FACE;
@@ -477,7 +483,7 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   // S7: compositing
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.batch, w, w.pair_face[pb], w.views, C, F, n_tiles, cfg.bg,
+    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face[pb], w.views, C, F, n_tiles, cfg.bg,
                                          images, t_final, s, &ctx->launches));
   }
 
@@ -511,7 +517,7 @@ gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dvert
   // S8: compositing backward
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.batch, w, w.pair_face[ctx->pair_buf], w.views, C, F,
+    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face[ctx->pair_buf], w.views, C, F,
                                          ctx->n_tiles, cfg.bg, dL_dimages, s, &ctx->launches));
   }
   // S9: projection + conversion backward, vertex scatter

@@ -236,10 +236,10 @@ cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, 
 cudaError_t launch_debug_records(const Workspace& ws, const uint32_t* sorted_keys, const uint32_t* sorted_ids,
                                  int64_t n_rec, uint32_t* depth_bits, int32_t* rects, float* conic, cudaStream_t s,
                                  int64_t* launches);
-cudaError_t launch_raster_fwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               float* images, float* t_final_out, cudaStream_t s, int64_t* launches);
-cudaError_t launch_raster_bwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               const float* dL_dimages, cudaStream_t s, int64_t* launches);
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,

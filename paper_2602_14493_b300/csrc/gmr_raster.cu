@@ -19,10 +19,10 @@
 // with a transposed butterfly (9 values in 14 shuffles) and eight lanes then
 // issue one atomic add each.
 //
-// Layout: one CTA of 256 threads per screen tile of one view (all views of a
-// batched call in one launch; the tile id selects the view). A warp covers an
-// 8x4 pixel block; with 32x32 tiles each thread owns four pixels, one per
-// 16x16 quadrant. Each batch of listed Gaussians is staged in shared memory
+// Layout: one CTA per screen tile of one view (all views of a batched call in
+// one launch; the tile id selects the view). The tile is cut into 8x4 pixel
+// blocks; each warp owns one or more consecutive blocks (one pixel per lane
+// in each), so a thread composites 1, 2 or 4 pixels. Each batch of listed Gaussians is staged in shared memory
 // (float4 loads of the records and face colours), with the image mean made
 // relative to the pixel block's 32-aligned anchor in float-pair arithmetic.
 
@@ -32,7 +32,6 @@ namespace gmr {
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Binary search of the view owning global tile g.
@@ -45,15 +44,19 @@ __device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
   return lo;
 }
 
-template <int TS>
+// Pixel layout of a tile of TS x TS pixels served by NT threads: the tile is
+// cut into 8x4-pixel blocks (row-major, TS/8 per row); warp w owns the PPT
+// consecutive blocks w*PPT ... w*PPT + PPT - 1 and lane l the pixel
+// (l % 8, l / 8) of each of them.
+template <int TS, int NT>
 struct PixMap {
-  static constexpr int PPT = TS * TS / kThreads;  // pixels per thread: 1 or 4
+  static constexpr int PPT = TS * TS / NT;  // pixels per thread
+  static_assert(PPT >= 1 && PPT * NT == TS * TS, "bad tile / thread split");
+  __device__ __forceinline__ static int block(int k) { return (threadIdx.x >> 5) * PPT + k; }
   __device__ __forceinline__ static void local(int k, int& lx, int& ly) {
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int wx = (warp & 1) * 8, wy = (warp >> 1) * 4;
-    int qx = (k & 1) * 16, qy = (k >> 1) * 16;
-    lx = qx + wx + (lane & 7);
-    ly = qy + wy + (lane >> 3);
+    int lane = threadIdx.x & 31, b = block(k);
+    lx = (b % (TS / 8)) * 8 + (lane & 7);
+    ly = (b / (TS / 8)) * 4 + (lane >> 3);
   }
 };
 
@@ -110,14 +113,49 @@ struct Stage {
   float b[BATCH];   // blue
   uint32_t rid[BATCH];
   uint32_t face[BATCH];
+  uint32_t mask[BATCH];  // 8x4 pixel blocks of the tile the Gaussian can reach
 };
 
-template <int BATCH>
+// Bit mask of the tile's 8x4-pixel warp blocks that the Gaussian's region
+// alpha >= 1/255 can reach. In log2 units that region is
+// A dx^2 + B dx dy + C dy^2 <= log2(255 o) with (A, B, C) = -(a2, b2, c2);
+// its bounding box has half-widths sqrt(k C / (AC - B^2/4)) and
+// sqrt(k A / (AC - B^2/4)). The box is widened (k by 1e-4 relative, 1e-3 px)
+// so that every skipped Gaussian has alpha below 1/255 by a margin (at least
+// 1e-4 in log2 units) far above
+// the rounding of the alpha evaluation: culling never changes a result.
+template <int TS>
+__device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, float b2, float c2, float o, float tox,
+                                               float toy) {
+  constexpr int NC = TS / 8, NR = TS / 4;
+  const float A = -a2, B = -b2, Cq = -c2;
+  const float det = A * Cq - 0.25f * B * B;
+  if (!(o > kAlphaMin) || !(det > 0.0f)) return 0u;
+  const float k2 = 7.99435344f + log2f(o);  // log2(255 o)
+  if (!(k2 > 0.0f)) return 0u;
+  const float kk = (k2 * 1.0001f + 1e-4f) / det;
+  const float hx = sqrtf(kk * Cq) + 1e-3f, hy = sqrtf(kk * A) + 1e-3f;
+  uint32_t cols = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    float lo = tox + (float)(8 * c) + 0.5f;
+    if (gx + hx >= lo && gx - hx <= lo + 7.0f) cols |= 1u << c;
+  }
+  uint32_t m = 0;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    float lo = toy + (float)(4 * r) + 0.5f;
+    if (gy + hy >= lo && gy - hy <= lo + 3.0f) m |= cols << (r * NC);
+  }
+  return m;
+}
+
+template <int TS, int NT, int BATCH>
 __device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
                                             int count, uint32_t rec_base, const float4* __restrict__ rec_u,
                                             const float4* __restrict__ rec_q, const float4* __restrict__ face_col,
-                                            float ax, float ay, bool want_ids) {
-  for (int i = threadIdx.x; i < count; i += kThreads) {
+                                            float ax, float ay, float tox, float toy, bool want_ids) {
+  for (int i = threadIdx.x; i < count; i += NT) {
     uint32_t f = __ldg(pair_face + lo + i);
     uint32_t rid = rec_base + f;
     float4 u = __ldg(rec_u + rid);
@@ -128,6 +166,7 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __
     st.g[i] = make_float4(ux, uy, q.x, q.y);
     st.h[i] = make_float4(q.z, col.w, col.x, col.y);
     st.b[i] = col.z;
+    st.mask[i] = block_mask<TS>(ux, uy, q.x, q.y, q.z, col.w, tox, toy);
     if (want_ids) {
       st.rid[i] = rid;
       st.face[i] = f;
@@ -136,13 +175,13 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __
 }
 
 // ---------------------------------------------------------------- forward
-template <int TS, int BATCH>
-__global__ void __launch_bounds__(kThreads) k_raster_fwd(
+template <int TS, int NT, int BATCH>
+__global__ void __launch_bounds__(NT) k_raster_fwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
     uint32_t* __restrict__ pix_last, float* __restrict__ t_out, Counters* __restrict__ counters) {
-  constexpr int PPT = PixMap<TS>::PPT;
+  constexpr int PPT = PixMap<TS, NT>::PPT;
   __shared__ Stage<BATCH> st;
   __shared__ int s_view;
   const int g = blockIdx.x;
@@ -155,15 +194,17 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(
   const int ox = txi * TS, oy = tyi * TS;
   const int axi = ox & ~31, ayi = oy & ~31;
   const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
 
   float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
   uint32_t last[PPT], term[PPT], ncontrib[PPT];
+  int blk[PPT];
   bool done[PPT], inside[PPT];
   int px[PPT], py[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     int lx, ly;
-    PixMap<TS>::local(k, lx, ly);
+    PixMap<TS, NT>::local(k, lx, ly);
     px[k] = ox + lx;
     py[k] = oy + ly;
     pcx[k] = (float)(px[k] - axi) + 0.5f;
@@ -175,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(
     last[k] = 0;
     term[k] = 0;
     ncontrib[k] = 0;
+    blk[k] = PixMap<TS, NT>::block(k);
   }
   const uint2 range = ranges[g];
   const int n = (int)(range.y - range.x);
@@ -186,18 +228,24 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(
     for (int k = 0; k < PPT; ++k) tdone &= done[k];
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
-    stage_batch<BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, false);
+    stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
+                           false);
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
       bool wd = true;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) wd &= done[k];
       if (__all_sync(kFull, wd)) break;
+      const uint32_t m = st.mask[j];
+      bool hit = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) hit |= (m >> blk[k]) & 1u;
+      if (!hit) continue;  // warp-uniform: no pixel of this thread's blocks is reached
       const float4 gg = st.g[j];
       const float4 hh = st.h[j];
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        if (done[k]) continue;
+        if (done[k] || !((m >> blk[k]) & 1u)) continue;
         float dx, dy, graw;
         float alpha = gauss_alpha(gg, hh.x, hh.y, pcx[k], pcy[k], dx, dy, graw);
         if (alpha < kAlphaMin) continue;
@@ -258,14 +306,14 @@ __device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int l
   return s;
 }
 
-template <int TS, int BATCH>
-__global__ void __launch_bounds__(kThreads) k_raster_bwd(
+template <int TS, int NT, int BATCH>
+__global__ void __launch_bounds__(NT) k_raster_bwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
     const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
     float4* __restrict__ face_grad, Counters* __restrict__ counters) {
-  constexpr int PPT = PixMap<TS>::PPT;
+  constexpr int PPT = PixMap<TS, NT>::PPT;
   __shared__ Stage<BATCH> st;
   __shared__ int s_view;
   __shared__ uint32_t s_maxlast;
@@ -282,15 +330,17 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(
   const int ox = txi * TS, oy = tyi * TS;
   const int axi = ox & ~31, ayi = oy & ~31;
   const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
   const int lane = threadIdx.x & 31;
 
   float pcx[PPT], pcy[PPT], T[PPT], S0[PPT], S1[PPT], S2[PPT], G0[PPT], G1[PPT], G2[PPT];
   uint32_t last[PPT];
+  int blk[PPT];
   uint32_t tmax = 0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     int lx, ly;
-    PixMap<TS>::local(k, lx, ly);
+    PixMap<TS, NT>::local(k, lx, ly);
     int px = ox + lx, py = oy + ly;
     pcx[k] = (float)(px - axi) + 0.5f;
     pcy[k] = (float)(py - ayi) + 0.5f;
@@ -311,6 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(
     S1[k] = T[k] * bg1;
     S2[k] = T[k] * bg2;
     tmax = max(tmax, last[k]);
+    blk[k] = PixMap<TS, NT>::block(k);
   }
   uint32_t wmax = tmax;
 #pragma unroll
@@ -327,11 +378,17 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(
   for (int end = end_all; end > 0; end -= BATCH) {
     const int start = max(0, end - BATCH);
     __syncthreads();
-    stage_batch<BATCH>(st, pair_face, range.x + start, end - start, rec_base, rec_u, rec_q, face_col, ax, ay, true);
+    stage_batch<TS, NT, BATCH>(st, pair_face, range.x + start, end - start, rec_base, rec_u, rec_q, face_col, ax, ay,
+                           tox, toy, true);
     __syncthreads();
     for (int j = end - 1 - start; j >= 0; --j) {
       const int pos = start + j;
       if ((uint32_t)pos >= wmax) continue;  // warp-uniform: no pixel of this warp reaches pos
+      const uint32_t m = st.mask[j];
+      bool hit = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) hit |= (m >> blk[k]) & 1u;
+      if (!hit) continue;  // warp-uniform
       const float4 gg = st.g[j];
       const float4 hh = st.h[j];
       const float cb = st.b[j];
@@ -339,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        if ((uint32_t)pos >= last[k]) continue;
+        if ((uint32_t)pos >= last[k] || !((m >> blk[k]) & 1u)) continue;
         float dx, dy, graw;
         float alpha = gauss_alpha(gg, hh.x, hh.y, pcx[k], pcy[k], dx, dy, graw);
         if (alpha < kAlphaMin) continue;
@@ -456,18 +513,18 @@ __global__ void k_debug_records(const uint32_t* __restrict__ sorted_keys, const 
   }
 }
 
-template <int TS, int BATCH>
+template <int TS, int NT, int BATCH>
 void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
                 int32_t F, const float* bg, float* images, float* t_out, cudaStream_t s) {
-  k_raster_fwd<TS, BATCH><<<(unsigned)n_tiles, kThreads, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
+  k_raster_fwd<TS, NT, BATCH><<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
                                                                  images, ws.pix_T, ws.pix_last, t_out, ws.counters);
 }
 
-template <int TS, int BATCH>
+template <int TS, int NT, int BATCH>
 void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
                 int32_t F, const float* bg, const float* dL, cudaStream_t s) {
-  k_raster_bwd<TS, BATCH><<<(unsigned)n_tiles, kThreads, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
+  k_raster_bwd<TS, NT, BATCH><<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2], dL,
                                                                  ws.pix_T, ws.pix_last, ws.rec_grad, ws.face_grad,
                                                                  ws.counters);
@@ -493,28 +550,34 @@ cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_fwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               float* images, float* t_final_out, cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
-#define GMR_FWD(TS_, B_) \
-  if (tile == TS_ && batch == B_) fwd_launch<TS_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, s)
-  GMR_FWD(16, 64); else GMR_FWD(16, 128); else GMR_FWD(16, 256);
-  else GMR_FWD(32, 64); else GMR_FWD(32, 128); else GMR_FWD(32, 256);
+#define GMR_FWD(TS_, NT_, B_)                                                                               \
+  if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
+  fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, s)
+  GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
+  else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
+  else GMR_FWD(16, 64, 64); else GMR_FWD(16, 64, 128); else GMR_FWD(16, 64, 256);
+  else GMR_FWD(32, 256, 64); else GMR_FWD(32, 256, 128); else GMR_FWD(32, 256, 256);
   else return cudaErrorInvalidValue;
 #undef GMR_FWD
   *launches += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_bwd(int tile, int batch, const Workspace& ws, const uint32_t* pair_face,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               const float* dL_dimages, cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
-#define GMR_BWD(TS_, B_) \
-  if (tile == TS_ && batch == B_) bwd_launch<TS_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, s)
-  GMR_BWD(16, 64); else GMR_BWD(16, 128); else GMR_BWD(16, 256);
-  else GMR_BWD(32, 64); else GMR_BWD(32, 128); else GMR_BWD(32, 256);
+#define GMR_BWD(TS_, NT_, B_)                                                                               \
+  if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
+  bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, s)
+  GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
+  else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
+  else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
+  else GMR_BWD(32, 256, 64); else GMR_BWD(32, 256, 128); else GMR_BWD(32, 256, 256);
   else return cudaErrorInvalidValue;
 #undef GMR_BWD
   *launches += 1;

@@ -59,7 +59,8 @@ def pixel_offsets(cams) -> np.ndarray:
 class Renderer:
     """One library context on the current CUDA device.
 
-    tile: 16 or 32; batch: Gaussians per shared-memory batch (64/128/256);
+    tile: 16 or 32; threads: threads per tile (64/128/256 for 16x16 tiles,
+    256 for 32x32); batch: Gaussians per shared-memory batch (64/128/256);
     cov_mode: "area" (Eq. 13) or "embed_raw" (Eq. 15 literally);
     color_mode: "face" (F x 3 colours) or "vertex" (V x 3, Eq. 16);
     sync_check: read the pair count back once per forward and grow buffers
@@ -67,7 +68,7 @@ class Renderer:
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
-                 sync_check=True, profile=False):
+                 sync_check=True, profile=False, threads=256):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -75,6 +76,7 @@ class Renderer:
         self.cfg = _lib.GmrConfig()
         self._L.gmr_config_default(ctypes.byref(self.cfg))
         self.cfg.tile = tile
+        self.cfg.threads = threads
         self.cfg.batch = batch
         self.cfg.cov_mode = _COV[cov_mode]
         self.cfg.color_mode = _COLOR[color_mode]

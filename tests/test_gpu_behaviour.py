@@ -32,9 +32,9 @@ def _uneven():
 def test_image_invariant_to_tile_and_batch_size():
     s = _uneven()
     ref = None
-    for tile in (16, 32):
+    for tile, threads in ((16, 256), (16, 128), (16, 64), (32, 256)):
         for batch in (64, 128, 256):
-            r = _renderer(tile=tile, batch=batch)
+            r = _renderer(tile=tile, batch=batch, threads=threads)
             _, img, T = render_gpu(r, s)
             a = img.cpu().numpy()
             if ref is None:
