@@ -136,7 +136,7 @@ def bins(verts, faces, cams, tile=16):
     vis = np.zeros(C * F, dtype=np.uint8)
     db = np.zeros(C * F, dtype=np.uint32)
     rect = np.zeros((C * F, 4), dtype=np.int32)
-    uxyr = np.zeros((C * F, 3), dtype=np.float32)
+    uxyr = np.zeros((C * F, 4), dtype=np.float32)
     rc = lib().gmr_oracle_bins(len(v), _p(v), F, _p(f), C, _p(cf), _p(ci), tile, _p(vis), _p(db), _p(rect),
                                _p(uxyr))
     if rc != 0:

@@ -312,14 +312,15 @@ Proj<T> project(const FaceGauss<T>& g, const Cam& cam) {
 // rectangle of tiles they are listed in) are integer results of FP32
 // arithmetic, so both sides take them with the same IEEE-754 single
 // operations in the same order (round to nearest, no contraction). The
-// rectangle is conservative: it holds every pixel centre at which
-// o * exp(power) could reach 1/255 for any o <= 1, with a 0.25 px margin, so
-// the composited image does not depend on it.
+// rectangle is conservative: it is the bounding box, widened by 0.25 px, of
+// the ellipse of pixel centres at which o * exp(power) could reach 1/255 for
+// any o <= 1 (with the area scale kappa = 6 sqrt(3)/pi, the largest it
+// takes), so the composited image does not depend on it.
 struct Bin {
   bool visible;
   float depth;
   uint32_t depth_bits;
-  float ux, uy, radius;
+  float ux, uy, rx, ry;
   int x0, x1, y0, y1;  // inclusive tile rectangle; empty when x0 > x1
 };
 
@@ -366,28 +367,24 @@ Bin bin_spec(const float* a, const float* b, const float* c, const Cam& cam, int
   { float u = j11 * q1[1], v = j12 * q1[2]; p1y = u + v; }
   { float u = j00 * q2[0], v = j02 * q2[2]; p2x = u + v; }
   { float u = j11 * q2[1], v = j12 * q2[2]; p2y = u + v; }
-  float kxx, kyy, kxy;
+  float kxx, kyy;
   { float u = p1x * p1x, v = p2x * p2x, w = p1x * p2x; s = u + v; s = s - w; kxx = kKappaOver18F * s; }
   { float u = p1y * p1y, v = p2y * p2y, w = p1y * p2y; s = u + v; s = s - w; kyy = kKappaOver18F * s; }
-  {
-    float u = p1x * p1y, v = p2x * p2y, w1 = p1x * p2y, w2 = p2x * p1y;
-    float hs = w1 + w2; hs = 0.5f * hs;
-    s = u + v; s = s - hs; kxy = kKappaOver18F * s;
-  }
-  float mid = kxx + kyy; mid = 0.5f * mid; mid = mid + 0.3f;
-  float hd = kxx - kyy; hd = 0.5f * hd;
-  float d2 = hd * hd, o2 = kxy * kxy; float disc = d2 + o2; disc = std::sqrt(disc);
-  float lam = mid + disc;
-  float rr = kTwoLn255F * lam; rr = std::sqrt(rr); rr = rr + 0.25f;
-  r.radius = rr;
-  r.visible = (r.depth > cam.znear) && std::isfinite(r.ux) && std::isfinite(r.uy) && std::isfinite(rr);
+  // half-widths of the bounding box of {d : d^T Sigma'^-1 d <= 2 ln 255}:
+  // sqrt(2 ln 255 Sigma'_xx), sqrt(2 ln 255 Sigma'_yy), plus 0.25 px
+  float sxx = kxx + 0.3f, syy = kyy + 0.3f;
+  float rx = kTwoLn255F * sxx; rx = std::sqrt(rx); rx = rx + 0.25f;
+  float ry = kTwoLn255F * syy; ry = std::sqrt(ry); ry = ry + 0.25f;
+  r.rx = rx; r.ry = ry;
+  r.visible = (r.depth > cam.znear) && std::isfinite(r.ux) && std::isfinite(r.uy) && std::isfinite(rx) &&
+              std::isfinite(ry);
   r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
   if (!r.visible) return r;
   float inv = 1.0f / (float)tile;  // exact: tile is a power of two
-  float bx0 = r.ux - rr; bx0 = bx0 - 0.5f; bx0 = bx0 * inv; bx0 = std::floor(bx0);
-  float bx1 = r.ux + rr; bx1 = bx1 - 0.5f; bx1 = bx1 * inv; bx1 = std::floor(bx1);
-  float by0 = r.uy - rr; by0 = by0 - 0.5f; by0 = by0 * inv; by0 = std::floor(by0);
-  float by1 = r.uy + rr; by1 = by1 - 0.5f; by1 = by1 * inv; by1 = std::floor(by1);
+  float bx0 = r.ux - rx; bx0 = bx0 - 0.5f; bx0 = bx0 * inv; bx0 = std::floor(bx0);
+  float bx1 = r.ux + rx; bx1 = bx1 - 0.5f; bx1 = bx1 * inv; bx1 = std::floor(bx1);
+  float by0 = r.uy - ry; by0 = by0 - 0.5f; by0 = by0 * inv; by0 = std::floor(by0);
+  float by1 = r.uy + ry; by1 = by1 - 0.5f; by1 = by1 * inv; by1 = std::floor(by1);
   int tx = (cam.W + tile - 1) / tile, ty = (cam.H + tile - 1) / tile;
   bx0 = std::max(bx0, 0.0f); by0 = std::max(by0, 0.0f);
   bx1 = std::min(bx1, (float)(tx - 1)); by1 = std::min(by1, (float)(ty - 1));
@@ -828,7 +825,7 @@ int gmr_oracle_project(int F, const double* means, const double* cov, int C, con
 
 // FP32 binning specification per (view, face), view-major: visible flag,
 // depth key bits, tile rectangle (x0, x1, y0, y1 inclusive; x0 > x1 when
-// empty), and the FP32 screen mean and radius it was derived from.
+// empty), and the FP32 screen mean and box half-widths it was derived from.
 int gmr_oracle_bins(int V, const float* verts, int F, const int* faces, int C, const float* cam_f, const int* cam_i,
                     int tile, uint8_t* visible, uint32_t* depth_bits, int32_t* rect, float* uxyr) {
   if (tile <= 0 || (tile & (tile - 1))) return -2;
@@ -844,7 +841,7 @@ int gmr_oracle_bins(int V, const float* verts, int F, const int* faces, int C, c
       if (visible) visible[r] = b.visible ? 1 : 0;
       if (depth_bits) depth_bits[r] = b.depth_bits;
       if (rect) { rect[4 * r] = b.x0; rect[4 * r + 1] = b.x1; rect[4 * r + 2] = b.y0; rect[4 * r + 3] = b.y1; }
-      if (uxyr) { uxyr[3 * r] = b.ux; uxyr[3 * r + 1] = b.uy; uxyr[3 * r + 2] = b.radius; }
+      if (uxyr) { uxyr[4 * r] = b.ux; uxyr[4 * r + 1] = b.uy; uxyr[4 * r + 2] = b.rx; uxyr[4 * r + 3] = b.ry; }
     }
   return 0;
 }

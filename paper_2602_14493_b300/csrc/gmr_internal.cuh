@@ -72,9 +72,10 @@ __device__ __forceinline__ float3 ld_vert(const float* v, int i) {
 // IEEE-754 single operation in a fixed order (the _rn intrinsics are never
 // contracted), so the depth key and the tile rectangle are reproducible bit
 // for bit by any IEEE implementation of the same sequence. The rectangle is
-// conservative: it holds every pixel centre where o * G can reach 1/255 for
-// o <= 1 (radius sqrt(2 ln 255 lambda_max(Sigma')) + 0.25 px, with the area
-// scale kappa = 6 sqrt(3)/pi, the largest it takes), so the image does not
+// conservative: it covers the bounding box (half-widths
+// sqrt(2 ln 255 Sigma'_xx) + 0.25 px and sqrt(2 ln 255 Sigma'_yy) + 0.25 px,
+// with the area scale kappa = 6 sqrt(3)/pi, the largest it takes) of the
+// pixel centres where o * G can reach 1/255 for o <= 1, so the image does not
 // depend on it.
 struct BinResult {
   bool visible;
@@ -117,20 +118,15 @@ __device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, cons
   float p2y = __fadd_rn(__fmul_rn(j11, q2y), __fmul_rn(j12, q2z));
   float kxx = __fmul_rn(kKappaOver18, __fsub_rn(__fadd_rn(__fmul_rn(p1x, p1x), __fmul_rn(p2x, p2x)), __fmul_rn(p1x, p2x)));
   float kyy = __fmul_rn(kKappaOver18, __fsub_rn(__fadd_rn(__fmul_rn(p1y, p1y), __fmul_rn(p2y, p2y)), __fmul_rn(p1y, p2y)));
-  float hs = __fmul_rn(0.5f, __fadd_rn(__fmul_rn(p1x, p2y), __fmul_rn(p2x, p1y)));
-  float kxy = __fmul_rn(kKappaOver18, __fsub_rn(__fadd_rn(__fmul_rn(p1x, p1y), __fmul_rn(p2x, p2y)), hs));
-  float mid = __fadd_rn(__fmul_rn(0.5f, __fadd_rn(kxx, kyy)), 0.3f);
-  float hd = __fmul_rn(0.5f, __fsub_rn(kxx, kyy));
-  float disc = __fsqrt_rn(__fadd_rn(__fmul_rn(hd, hd), __fmul_rn(kxy, kxy)));
-  float lam = __fadd_rn(mid, disc);
-  float rr = __fadd_rn(__fsqrt_rn(__fmul_rn(kTwoLn255, lam)), 0.25f);
-  r.visible = (tz > v.znear) && isfinite(ux) && isfinite(uy) && isfinite(rr);
+  float rx = __fadd_rn(__fsqrt_rn(__fmul_rn(kTwoLn255, __fadd_rn(kxx, 0.3f))), 0.25f);
+  float ry = __fadd_rn(__fsqrt_rn(__fmul_rn(kTwoLn255, __fadd_rn(kyy, 0.3f))), 0.25f);
+  r.visible = (tz > v.znear) && isfinite(ux) && isfinite(uy) && isfinite(rx) && isfinite(ry);
   r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
   if (!r.visible) return r;
-  float bx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(ux, rr), 0.5f), inv_tile));
-  float bx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(ux, rr), 0.5f), inv_tile));
-  float by0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(uy, rr), 0.5f), inv_tile));
-  float by1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(uy, rr), 0.5f), inv_tile));
+  float bx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(ux, rx), 0.5f), inv_tile));
+  float bx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(ux, rx), 0.5f), inv_tile));
+  float by0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(uy, ry), 0.5f), inv_tile));
+  float by1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(uy, ry), 0.5f), inv_tile));
   bx0 = fmaxf(bx0, 0.0f);
   by0 = fmaxf(by0, 0.0f);
   bx1 = fminf(bx1, (float)(v.tiles_x - 1));
@@ -140,21 +136,28 @@ __device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, cons
   return r;
 }
 
-// Compositing weight of one staged Gaussian at one pixel. g = (ux, uy, a2,
-// b2) with (ux, uy) the mean relative to the 32-pixel-aligned anchor of the
-// pixel's block, h = (c2, o, ...), (pcx, pcy) the pixel centre relative to
-// the same anchor. Forward and backward call this same sequence of explicit
-// single-precision operations, so both take identical skip decisions.
-__device__ __forceinline__ float gauss_alpha(float4 g, float c2, float o, float pcx, float pcy, float& dx,
-                                             float& dy, float& graw) {
+// Exponent of one staged Gaussian at one pixel, in log2 units:
+// p2 = a2 dx^2 + b2 dx dy + c2 dy^2 = -1/2 d^T Q d / ln 2, so that
+// G = 2^p2. g = (ux, uy, a2, b2) with (ux, uy) the mean relative to the
+// 32-pixel-aligned anchor of the pixel's block, (pcx, pcy) the pixel centre
+// relative to the same anchor. A Gaussian is skipped at the pixel when
+// p2 < t2 = log2(1 / (255 o)), i.e. when o G < 1/255; otherwise its weight is
+// alpha = min(0.99, o 2^p2). Forward and backward use this same sequence of
+// explicit single-precision operations, so they take identical decisions.
+__device__ __forceinline__ float gauss_p2(float4 g, float c2, float pcx, float pcy, float& dx, float& dy) {
   dx = __fsub_rn(g.x, pcx);
   dy = __fsub_rn(g.y, pcy);
   float t = __fmaf_rn(g.z, dx, __fmul_rn(g.w, dy));
-  float p2 = __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(c2, dy), dy));
-  float G = ex2_approx(p2);
-  graw = __fmul_rn(o, G);
+  return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(c2, dy), dy));
+}
+
+__device__ __forceinline__ float gauss_alpha(float p2, float o, float& graw) {
+  graw = __fmul_rn(o, ex2_approx(p2));
   return fminf(graw, kAlphaMax);
 }
+
+// log2(255)
+constexpr float kLog2_255 = 7.99435343685886f;
 
 // ---------------------------------------------------------------- workspace
 struct Workspace {

@@ -108,12 +108,11 @@ __global__ void k_tile_ranges(const uint32_t* __restrict__ tiles, const Counters
 // ---------------------------------------------------------------- staging
 template <int BATCH>
 struct Stage {
-  float4 g[BATCH];  // (ux, uy, a2, b2), mean relative to the anchor
-  float4 h[BATCH];  // (c2, o, r, g)
-  float b[BATCH];   // blue
+  float4 g[BATCH];    // (ux, uy, a2, b2), mean relative to the anchor
+  float4 h[BATCH];    // (c2, t2 = log2(1/(255 o)), o, block mask bits)
+  float4 col[BATCH];  // (r, g, b, 0)
   uint32_t rid[BATCH];
   uint32_t face[BATCH];
-  uint32_t mask[BATCH];  // 8x4 pixel blocks of the tile the Gaussian can reach
 };
 
 // Bit mask of the tile's 8x4-pixel warp blocks that the Gaussian's region
@@ -125,14 +124,12 @@ struct Stage {
 // 1e-4 in log2 units) far above
 // the rounding of the alpha evaluation: culling never changes a result.
 template <int TS>
-__device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, float b2, float c2, float o, float tox,
+__device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, float b2, float c2, float k2, float tox,
                                                float toy) {
   constexpr int NC = TS / 8, NR = TS / 4;
   const float A = -a2, B = -b2, Cq = -c2;
   const float det = A * Cq - 0.25f * B * B;
-  if (!(o > kAlphaMin) || !(det > 0.0f)) return 0u;
-  const float k2 = 7.99435344f + log2f(o);  // log2(255 o)
-  if (!(k2 > 0.0f)) return 0u;
+  if (!(k2 > 0.0f) || !(det > 0.0f)) return 0u;  // k2 = log2(255 o)
   const float kk = (k2 * 1.0001f + 1e-4f) / det;
   const float hx = sqrtf(kk * Cq) + 1e-3f, hy = sqrtf(kk * A) + 1e-3f;
   uint32_t cols = 0;
@@ -163,10 +160,11 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __
     float4 col = __ldg(face_col + f);
     float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
+    const float k2 = kLog2_255 + log2f(col.w);  // -inf for o = 0
+    const uint32_t m = block_mask<TS>(ux, uy, q.x, q.y, q.z, k2, tox, toy);
     st.g[i] = make_float4(ux, uy, q.x, q.y);
-    st.h[i] = make_float4(q.z, col.w, col.x, col.y);
-    st.b[i] = col.z;
-    st.mask[i] = block_mask<TS>(ux, uy, q.x, q.y, q.z, col.w, tox, toy);
+    st.h[i] = make_float4(q.z, -k2, col.w, __uint_as_float(m));
+    st.col[i] = make_float4(col.x, col.y, col.z, 0.0f);
     if (want_ids) {
       st.rid[i] = rid;
       st.face[i] = f;
@@ -236,19 +234,30 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(
 #pragma unroll
       for (int k = 0; k < PPT; ++k) wd &= done[k];
       if (__all_sync(kFull, wd)) break;
-      const uint32_t m = st.mask[j];
+      const float4 hh = st.h[j];
+      const uint32_t m = __float_as_uint(hh.w);
       bool hit = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) hit |= (m >> blk[k]) & 1u;
-      if (!hit) continue;  // warp-uniform: no pixel of this thread's blocks is reached
+      if (!hit) continue;  // warp-uniform: the Gaussian reaches none of this thread's blocks
       const float4 gg = st.g[j];
-      const float4 hh = st.h[j];
+      float p2[PPT];
+      bool con[PPT];
+      bool anyc = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        if (done[k] || !((m >> blk[k]) & 1u)) continue;
-        float dx, dy, graw;
-        float alpha = gauss_alpha(gg, hh.x, hh.y, pcx[k], pcy[k], dx, dy, graw);
-        if (alpha < kAlphaMin) continue;
+        float dx, dy;
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dx, dy);
+        con[k] = !done[k] && ((m >> blk[k]) & 1u) && !(p2[k] < hh.y);
+        anyc |= con[k];
+      }
+      if (!anyc) continue;
+      const float4 col = st.col[j];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (!con[k]) continue;
+        float graw;
+        float alpha = gauss_alpha(p2[k], hh.z, graw);
         float test = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
         if (test < kTMin) {
           done[k] = true;
@@ -256,9 +265,9 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(
           continue;
         }
         float w = __fmul_rn(alpha, T[k]);
-        Cr[k] = __fmaf_rn(hh.z, w, Cr[k]);
-        Cg[k] = __fmaf_rn(hh.w, w, Cg[k]);
-        Cb[k] = __fmaf_rn(st.b[j], w, Cb[k]);
+        Cr[k] = __fmaf_rn(col.x, w, Cr[k]);
+        Cg[k] = __fmaf_rn(col.y, w, Cg[k]);
+        Cb[k] = __fmaf_rn(col.z, w, Cb[k]);
         T[k] = test;
         last[k] = (uint32_t)(base + j + 1);
         ++ncontrib[k];
@@ -384,45 +393,54 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     for (int j = end - 1 - start; j >= 0; --j) {
       const int pos = start + j;
       if ((uint32_t)pos >= wmax) continue;  // warp-uniform: no pixel of this warp reaches pos
-      const uint32_t m = st.mask[j];
+      const float4 hh = st.h[j];
+      const uint32_t m = __float_as_uint(hh.w);
       bool hit = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) hit |= (m >> blk[k]) & 1u;
       if (!hit) continue;  // warp-uniform
       const float4 gg = st.g[j];
-      const float4 hh = st.h[j];
-      const float cb = st.b[j];
-      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float p2[PPT], dxs[PPT], dys[PPT];
+      bool con[PPT];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        if ((uint32_t)pos >= last[k] || !((m >> blk[k]) & 1u)) continue;
-        float dx, dy, graw;
-        float alpha = gauss_alpha(gg, hh.x, hh.y, pcx[k], pcy[k], dx, dy, graw);
-        if (alpha < kAlphaMin) continue;
-        any = true;
-        float om = __fsub_rn(1.0f, alpha);
-        float inv = __fdividef(1.0f, om);
-        float Tb = T[k] * inv;
-        float w = alpha * Tb;
-        float cg = hh.z * G0[k] + hh.w * G1[k] + cb * G2[k];
-        float sg = S0[k] * G0[k] + S1[k] * G1[k] + S2[k] * G2[k];
-        float dalpha = Tb * cg - sg * inv;
-        S0[k] += hh.z * w;
-        S1[k] += hh.w * w;
-        S2[k] += cb * w;
-        T[k] = Tb;
-        float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
-        float qx = dq * dx, qy = dq * dy;
-        acc[0] += 2.0f * gg.z * qx + gg.w * qy;
-        acc[1] += gg.w * qx + 2.0f * hh.x * qy;
-        acc[2] += qx * dx;
-        acc[3] += qx * dy;
-        acc[4] += qy * dy;
-        acc[5] += dq;
-        acc[6] += w * G0[k];
-        acc[7] += w * G1[k];
-        acc[8] += w * G2[k];
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
+        con[k] = ((uint32_t)pos < last[k]) && ((m >> blk[k]) & 1u) && !(p2[k] < hh.y);
+        any |= con[k];
+      }
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (any) {
+        const float4 col = st.col[j];
+        const float a2x2 = 2.0f * gg.z, c2x2 = 2.0f * hh.x;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (!con[k]) continue;
+          float graw;
+          float alpha = gauss_alpha(p2[k], hh.z, graw);
+          float om = __fsub_rn(1.0f, alpha);
+          float inv = __fdividef(1.0f, om);
+          float Tb = T[k] * inv;
+          float w = alpha * Tb;
+          float cg = col.x * G0[k] + col.y * G1[k] + col.z * G2[k];
+          float sg = S0[k] * G0[k] + S1[k] * G1[k] + S2[k] * G2[k];
+          float dalpha = Tb * cg - sg * inv;
+          S0[k] += col.x * w;
+          S1[k] += col.y * w;
+          S2[k] += col.z * w;
+          T[k] = Tb;
+          float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
+          float qx = dq * dxs[k], qy = dq * dys[k];
+          acc[0] += a2x2 * qx + gg.w * qy;
+          acc[1] += gg.w * qx + c2x2 * qy;
+          acc[2] += qx * dxs[k];
+          acc[3] += qx * dys[k];
+          acc[4] += qy * dys[k];
+          acc[5] += dq;
+          acc[6] += w * G0[k];
+          acc[7] += w * G1[k];
+          acc[8] += w * G2[k];
+        }
       }
       if (!__any_sync(kFull, any)) continue;
       float s8 = acc[8];
@@ -454,16 +472,19 @@ __global__ void __launch_bounds__(kLossThreads) k_l2_partial(const float* __rest
                                                               float* __restrict__ grad, double* __restrict__ part) {
   __shared__ double sw[kLossThreads / 32];
   int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
-  double acc = 0.0;
+  // FP32 within a thread (16 terms), FP64 across threads: FP64 arithmetic is
+  // a slow pipe on this GPU, so it is kept off the per-element path.
+  float accf = 0.0f;
 #pragma unroll 4
   for (int k = 0; k < kLossItems; ++k) {
     int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
     if (i < n) {
       float d = img[i] - tgt[i];
       grad[i] = 2.0f * d;
-      acc += (double)d * (double)d;
+      accf = fmaf(d, d, accf);
     }
   }
+  double acc = (double)accf;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
   if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;

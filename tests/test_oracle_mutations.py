@@ -29,7 +29,7 @@ MUTATIONS = {
     "eigen_swap": ("T sx2 = kappa * lam1, sy2 = kappa * lam2", "T sx2 = kappa * lam2, sy2 = kappa * lam1"),
     "centroid_component": ("V3<T> m = vi + mux * xa + muy * ya;", "V3<T> m = vi + mux * xa + mux * ya;"),
     "normal_cross_order": ("dya = dya + cross(dnv, g.xa);", "dya = dya + cross(g.xa, dnv);"),
-    "rect_too_small": ("rr = rr + 0.25f;", "rr = rr - 1.5f;"),
+    "rect_too_small": ("rx = rx + 0.25f;", "rx = rx - 1.5f;"),
     "depth_order": ("return bins[(size_t)view * F + i].depth_bits < bins[(size_t)view * F + j].depth_bits;",
                     "return bins[(size_t)view * F + i].depth_bits > bins[(size_t)view * F + j].depth_bits;"),
 }
