@@ -106,14 +106,36 @@ __global__ void k_tile_ranges(const uint32_t* __restrict__ tiles, const Counters
 }
 
 // ---------------------------------------------------------------- staging
-template <int BATCH>
+template <int BATCH, int NW>
 struct Stage {
   float4 g[BATCH];    // (ux, uy, a2, b2), mean relative to the anchor
-  float4 h[BATCH];    // (c2, t2 = log2(1/(255 o)), o, block mask bits)
+  float4 h[BATCH];    // (c2, t2 = log2(1/(255 o)), o, 0)
   float4 col[BATCH];  // (r, g, b, 0)
+  uint32_t mask[BATCH];  // 8x4 pixel blocks of the tile the Gaussian can reach
   uint32_t rid[BATCH];
   uint32_t face[BATCH];
+  uint8_t list[NW][BATCH];  // per warp: batch indices that reach its blocks, in order
 };
+
+// Each warp compacts, in order, the batch entries whose mask reaches one of
+// its PPT blocks (bits warp*PPT ... warp*PPT + PPT - 1) and whose list
+// position is below `limit`. Returns the count (warp-uniform).
+template <int BATCH, int NW, int PPT>
+__device__ __forceinline__ int warp_list(Stage<BATCH, NW>& st, int count, int first_pos, int limit) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t bits = ((1u << PPT) - 1u) << (warp * PPT);
+  const uint32_t lt = (1u << lane) - 1u;
+  int n = 0;
+  for (int c = 0; c < count; c += 32) {
+    int i = c + lane;
+    bool rel = i < count && (st.mask[i] & bits) && (first_pos + i) < limit;
+    uint32_t bal = __ballot_sync(0xffffffffu, rel);
+    if (rel) st.list[warp][n + __popc(bal & lt)] = (uint8_t)i;
+    n += __popc(bal);
+  }
+  __syncwarp();
+  return n;
+}
 
 // Bit mask of the tile's 8x4-pixel warp blocks that the Gaussian's region
 // alpha >= 1/255 can reach. In log2 units that region is
@@ -148,7 +170,7 @@ __device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, flo
 }
 
 template <int TS, int NT, int BATCH>
-__device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
+__device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
                                             int count, uint32_t rec_base, const float4* __restrict__ rec_u,
                                             const float4* __restrict__ rec_q, const float4* __restrict__ face_col,
                                             float ax, float ay, float tox, float toy, bool want_ids) {
@@ -163,7 +185,8 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __
     const float k2 = kLog2_255 + log2f(col.w);  // -inf for o = 0
     const uint32_t m = block_mask<TS>(ux, uy, q.x, q.y, q.z, k2, tox, toy);
     st.g[i] = make_float4(ux, uy, q.x, q.y);
-    st.h[i] = make_float4(q.z, -k2, col.w, __uint_as_float(m));
+    st.h[i] = make_float4(q.z, -k2, col.w, 0.0f);
+    st.mask[i] = m;
     st.col[i] = make_float4(col.x, col.y, col.z, 0.0f);
     if (want_ids) {
       st.rid[i] = rid;
@@ -173,14 +196,23 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH>& st, const uint32_t* __
 }
 
 // ---------------------------------------------------------------- forward
+// Resident warps per SM the compiler must allow (register cap); 0 = none.
+#ifndef GMR_FWD_MIN_WARPS
+#define GMR_FWD_MIN_WARPS 0
+#endif
+#ifndef GMR_BWD_MIN_WARPS
+#define GMR_BWD_MIN_WARPS 0
+#endif
+
 template <int TS, int NT, int BATCH>
-__global__ void __launch_bounds__(NT) k_raster_fwd(
+__global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_raster_fwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
     uint32_t* __restrict__ pix_last, float* __restrict__ t_out, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
-  __shared__ Stage<BATCH> st;
+  constexpr int NW = NT / 32;
+  __shared__ Stage<BATCH, NW> st;
   __shared__ int s_view;
   const int g = blockIdx.x;
   if (threadIdx.x == 0) s_view = find_view(views, C, g);
@@ -229,18 +261,17 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
                            false);
     __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
+    const int nl = warp_list<BATCH, NW, PPT>(st, cnt, 0, cnt);
+    const int warp = threadIdx.x >> 5;
+    for (int jj = 0; jj < nl; ++jj) {
       bool wd = true;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) wd &= done[k];
       if (__all_sync(kFull, wd)) break;
+      const int j = st.list[warp][jj];
       const float4 hh = st.h[j];
-      const uint32_t m = __float_as_uint(hh.w);
-      bool hit = false;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) hit |= (m >> blk[k]) & 1u;
-      if (!hit) continue;  // warp-uniform: the Gaussian reaches none of this thread's blocks
       const float4 gg = st.g[j];
+      const uint32_t m = st.mask[j];
       float p2[PPT];
       bool con[PPT];
       bool anyc = false;
@@ -248,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(
       for (int k = 0; k < PPT; ++k) {
         float dx, dy;
         p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dx, dy);
-        con[k] = !done[k] && ((m >> blk[k]) & 1u) && !(p2[k] < hh.y);
+        con[k] = !done[k] && (PPT == 1 || ((m >> blk[k]) & 1u)) && !(p2[k] < hh.y);
         anyc |= con[k];
       }
       if (!anyc) continue;
@@ -316,14 +347,15 @@ __device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int l
 }
 
 template <int TS, int NT, int BATCH>
-__global__ void __launch_bounds__(NT) k_raster_bwd(
+__global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_raster_bwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
     const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
     float4* __restrict__ face_grad, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
-  __shared__ Stage<BATCH> st;
+  constexpr int NW = NT / 32;
+  __shared__ Stage<BATCH, NW> st;
   __shared__ int s_view;
   __shared__ uint32_t s_maxlast;
   const int g = blockIdx.x;
@@ -390,23 +422,21 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + start, end - start, rec_base, rec_u, rec_q, face_col, ax, ay,
                            tox, toy, true);
     __syncthreads();
-    for (int j = end - 1 - start; j >= 0; --j) {
+    const int nl = warp_list<BATCH, NW, PPT>(st, end - start, start, (int)wmax);
+    const int warp = threadIdx.x >> 5;
+    for (int jj = nl - 1; jj >= 0; --jj) {
+      const int j = st.list[warp][jj];
       const int pos = start + j;
-      if ((uint32_t)pos >= wmax) continue;  // warp-uniform: no pixel of this warp reaches pos
       const float4 hh = st.h[j];
-      const uint32_t m = __float_as_uint(hh.w);
-      bool hit = false;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) hit |= (m >> blk[k]) & 1u;
-      if (!hit) continue;  // warp-uniform
       const float4 gg = st.g[j];
+      const uint32_t m = st.mask[j];
       float p2[PPT], dxs[PPT], dys[PPT];
       bool con[PPT];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
-        con[k] = ((uint32_t)pos < last[k]) && ((m >> blk[k]) & 1u) && !(p2[k] < hh.y);
+        con[k] = ((uint32_t)pos < last[k]) && (PPT == 1 || ((m >> blk[k]) & 1u)) && !(p2[k] < hh.y);
         any |= con[k];
       }
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
