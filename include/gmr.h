@@ -55,6 +55,7 @@ typedef enum {
 /* Device status bits reported by gmr_get_device_status. */
 #define GMR_DEV_BAD_FACE_INDEX 1u /* a face referenced a vertex outside [0, V) */
 #define GMR_DEV_PAIR_OVERFLOW 2u  /* more (tile, Gaussian) pairs than capacity */
+#define GMR_DEV_SORT_TIMEOUT 4u   /* a bounded wait in the radix sort expired */
 
 /* Sec. 2.2: which 3D covariance a facet becomes. */
 typedef enum {

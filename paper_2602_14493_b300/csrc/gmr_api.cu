@@ -96,31 +96,38 @@ gmr_status grow(gmr_ctx* ctx, T** ptr, int64_t* cap, int64_t need, bool capturin
   return GMR_OK;
 }
 
-// Capacity groups: records (2 ping-pong arrays share one capacity).
+// (Re)allocates *ptr to exactly `count` elements (contents not kept).
+template <class T>
+gmr_status realloc_exact(gmr_ctx* ctx, T** ptr, int64_t count, const char* what) {
+  T* p = nullptr;
+  cudaError_t e = cudaMalloc((void**)&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, GMR_ERR_OOM, std::string("cudaMalloc of workspace '") + what + "' failed");
+  }
+  if (*ptr) cudaFree(*ptr);
+  *ptr = p;
+  return GMR_OK;
+}
+
+// All per-record buffers are sized from one capacity (cap_records records).
 gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
   Workspace& w = ctx->ws;
   if (n <= w.cap_records) return GMR_OK;
   if (capturing) return fail(ctx, GMR_ERR_STATE, "record workspace must grow during stream capture; call gmr_reserve");
-  int64_t c0 = w.cap_records;
-  int64_t cap;
+  const int64_t cap = n + n / 4 + 1024;
   gmr_status s;
-#define G(field, T)                                              \
-  cap = c0;                                                      \
-  s = grow<T>(ctx, &w.field, &cap, n, false, #field);            \
-  if (s != GMR_OK) return s;
-  G(rec_u, float4);
-  G(rec_q, float4);
-  G(rec_rect, uint2);
-  G(rec_ntiles, uint32_t);
-  G(rec_key[0], uint32_t);
-  G(rec_key[1], uint32_t);
-  G(rec_id[0], uint32_t);
-  G(rec_id[1], uint32_t);
-  G(rec_off, uint32_t);
-#undef G
-  int64_t gcap = 2 * c0;
-  s = grow<float4>(ctx, &w.rec_grad, &gcap, 2 * n, false, "rec_grad");
-  if (s != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_u, cap, "rec_u")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_q, cap, "rec_q")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_rect, cap, "rec_rect")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_ntiles, cap, "rec_ntiles")) != GMR_OK) return s;
+  for (int b = 0; b < 2; ++b) {
+    if ((s = realloc_exact(ctx, &w.rec_key[b], cap, "rec_key")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.rec_id[b], cap, "rec_id")) != GMR_OK) return s;
+  }
+  if ((s = realloc_exact(ctx, &w.rec_off, cap, "rec_off")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_grad, 2 * cap, "rec_grad")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_contrib, 4 * cap, "rec_contrib")) != GMR_OK) return s;
   w.cap_records = cap;
   return GMR_OK;
 }
@@ -137,15 +144,13 @@ gmr_status ensure_scratch(gmr_ctx* ctx, int64_t n_items, bool capturing) {
 gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
   Workspace& w = ctx->ws;
   if (n <= w.cap_pairs) return GMR_OK;
-  if (n >= (int64_t)0x7fffffff) return fail(ctx, GMR_ERR_CAPACITY, "more than 2^31 - 1 (tile, Gaussian) pairs");
+  if (n >= (int64_t)(1 << 30) - 4096) return fail(ctx, GMR_ERR_CAPACITY, "more than 2^30 (tile, Gaussian) pairs");
   if (capturing) return fail(ctx, GMR_ERR_STATE, "pair workspace must grow during stream capture; call gmr_reserve");
-  int64_t c0 = w.cap_pairs, cap;
+  const int64_t cap = std::min<int64_t>(n + n / 4 + 4096, (int64_t)(1 << 30) - 4096);
   gmr_status s;
   for (int b = 0; b < 2; ++b) {
-    cap = c0;
-    if ((s = grow<uint32_t>(ctx, &w.pair_tile[b], &cap, n, false, "pair_tile")) != GMR_OK) return s;
-    cap = c0;
-    if ((s = grow<uint32_t>(ctx, &w.pair_face[b], &cap, n, false, "pair_face")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.pair_tile[b], cap, "pair_tile")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.pair_face[b], cap, "pair_face")) != GMR_OK) return s;
   }
   w.cap_pairs = cap;
   return ensure_scratch(ctx, std::max(cap, w.cap_records), false);
@@ -155,13 +160,24 @@ gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
 gmr_status ensure_faces(gmr_ctx* ctx, int64_t n, bool capturing) {
   Workspace& w = ctx->ws;
   if (n <= w.cap_faces) return GMR_OK;
-  int64_t c0 = w.cap_faces, cap = c0;
-  gmr_status s = grow<float4>(ctx, &w.face_col, &cap, n, capturing, "face_col");
-  if (s != GMR_OK) return s;
-  int64_t cap2 = c0;
-  s = grow<float4>(ctx, &w.face_grad, &cap2, n, capturing, "face_grad");
-  if (s != GMR_OK) return s;
-  w.cap_faces = std::min(cap, cap2);
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "face workspace must grow during stream capture; call gmr_reserve");
+  const int64_t cap = n + n / 4 + 1024;
+  gmr_status s;
+  if ((s = realloc_exact(ctx, &w.face_col, cap, "face_col")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.face_grad, cap, "face_grad")) != GMR_OK) return s;
+  w.cap_faces = cap;
+  return GMR_OK;
+}
+
+gmr_status ensure_pixels(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_pixels) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "pixel workspace must grow during stream capture; call gmr_reserve");
+  const int64_t cap = n + n / 4 + 1024;
+  gmr_status s;
+  if ((s = realloc_exact(ctx, &w.pix_T, cap, "pix_T")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.pix_last, cap, "pix_last")) != GMR_OK) return s;
+  w.cap_pixels = cap;
   return GMR_OK;
 }
 
@@ -308,7 +324,7 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   Workspace& w = ctx->ws;
   void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key[0], w.rec_key[1], w.rec_id[0],
-                  w.rec_id[1], w.rec_off, w.rec_grad, w.face_col, w.face_grad, w.pix_T, w.pix_last,
+                  w.rec_id[1], w.rec_off, w.rec_grad, w.rec_contrib, w.face_col, w.face_grad, w.pix_T, w.pix_last,
                   w.tile_range, w.pair_tile[0], w.pair_tile[1], w.pair_face[0], w.pair_face[1], w.scan_tmp,
                   w.radix_counts, w.loss_part, w.views, w.counters};
   for (void* p : bufs)
@@ -351,10 +367,7 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   gmr_status s;
   if ((s = ensure_records(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK) return s;
   if ((s = ensure_faces(ctx, max_faces, false)) != GMR_OK) return s;
-  int64_t pc = ctx->ws.cap_pixels, pc2 = ctx->ws.cap_pixels;
-  if ((s = grow<float>(ctx, &ctx->ws.pix_T, &pc, max_pixels, false, "pix_T")) != GMR_OK) return s;
-  if ((s = grow<uint32_t>(ctx, &ctx->ws.pix_last, &pc2, max_pixels, false, "pix_last")) != GMR_OK) return s;
-  ctx->ws.cap_pixels = std::min(pc, pc2);
+  if ((s = ensure_pixels(ctx, max_pixels, false)) != GMR_OK) return s;
   // tiles: at most one per 16x16 block plus one ragged tile per row/column and view
   int64_t mt = max_pixels / 256 + 2 * (int64_t)max_views * 1024 + 16;
   if ((s = grow<uint2>(ctx, &ctx->ws.tile_range, &ctx->ws.cap_tiles, mt, false, "tile_range")) != GMR_OK) return s;
@@ -410,12 +423,7 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   if ((st = ensure_views(ctx, C, capturing)) != GMR_OK) return st;
   if ((st = ensure_records(ctx, n_rec, capturing)) != GMR_OK) return st;
   if ((st = ensure_faces(ctx, F, capturing)) != GMR_OK) return st;
-  {
-    int64_t pc = w.cap_pixels, pc2 = w.cap_pixels;
-    if ((st = grow<float>(ctx, &w.pix_T, &pc, n_pixels, capturing, "pix_T")) != GMR_OK) return st;
-    if ((st = grow<uint32_t>(ctx, &w.pix_last, &pc2, n_pixels, capturing, "pix_last")) != GMR_OK) return st;
-    w.cap_pixels = std::min(pc, pc2);
-  }
+  if ((st = ensure_pixels(ctx, n_pixels, capturing)) != GMR_OK) return st;
   if ((st = grow<uint2>(ctx, &w.tile_range, &w.cap_tiles, n_tiles, capturing, "tile_range")) != GMR_OK) return st;
   if ((st = ensure_scratch(ctx, std::max(n_rec, w.cap_pairs), capturing)) != GMR_OK) return st;
 
@@ -443,7 +451,7 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   int rb;
   {
     StageTimer t(ctx, GMR_STAGE_SORT_RECORDS, s, cfg);
-    rb = gmr::radix_sort_pairs(w.rec_key, w.rec_id, nullptr, n_rec, 32, w.radix_counts, w.scan_tmp, s,
+    rb = gmr::radix_sort_pairs(w.rec_key, w.rec_id, nullptr, n_rec, 32, w.radix_counts, &w.counters->status, s,
                                &ctx->launches, &e);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "record sort");
@@ -471,7 +479,7 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   {
     StageTimer t(ctx, GMR_STAGE_SORT_PAIRS, s, cfg);
     pb = gmr::radix_sort_pairs(w.pair_tile, w.pair_face, &w.counters->n_pairs, w.cap_pairs, bits_for(n_tiles),
-                               w.radix_counts, w.scan_tmp, s, &ctx->launches, &e);
+                               w.radix_counts, &w.counters->status, s, &ctx->launches, &e);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pair sort");
   // S6: tile ranges

@@ -171,6 +171,7 @@ struct Workspace {
   uint32_t* rec_id[2] = {nullptr, nullptr};   // record ids, ping-pong
   uint32_t* rec_off = nullptr;   // pair offsets in sorted record order
   float4* rec_grad = nullptr;    // 2 float4 per record: (R0..R3), (R4, 0, 0, 0)
+  float4* rec_contrib = nullptr; // 4 float4 per record: backward contributions per view
   // faces
   int64_t cap_faces = 0;
   float4* face_col = nullptr;    // (r, g, b, o)
@@ -208,12 +209,12 @@ struct Workspace {
 cudaError_t scan_exclusive(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* out, uint32_t* total,
                            uint32_t* block_sums, cudaStream_t s, int64_t* launches);
 int64_t scan_block_sums_needed(int64_t n);
-// Stable LSD radix sort of (key, value) u32 pairs on the low `bits` key bits.
-// n is read from *n_dev when n_dev is not null (then n <= n_cap is required
-// by the caller's capacity check; excess items are ignored), else n_cap.
-// Returns the index (0 or 1) of the buffers holding the result.
+// Stable LSD radix sort of (key, value) u32 pairs on the low `bits` key bits
+// (at most 32), 8 bits per pass. n is read from *n_dev when n_dev is not null
+// (clamped to n_cap), else n_cap. scratch holds radix_counts_needed(n_cap)
+// u32. Returns the index (0 or 1) of the buffers holding the result.
 int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], const uint32_t* n_dev, int64_t n_cap, int bits,
-                     uint32_t* counts, uint32_t* scan_tmp, cudaStream_t s, int64_t* launches, cudaError_t* err);
+                     uint32_t* scratch, uint32_t* dev_status, cudaStream_t s, int64_t* launches, cudaError_t* err);
 int64_t radix_counts_needed(int64_t n_cap);
 
 // project.cu

@@ -15,8 +15,9 @@
 //   e_a = M d_a, m = M n,
 // whose determinant is formed from squared 2D cross products (Cauchy-Binet),
 // a sum of non-negative terms, so edge-on facets lose no precision.
-// The image-plane mean is evaluated in FP64 and stored as a float pair so
-// that pixel offsets keep ~1e-6 px accuracy at any image size.
+// The image-plane mean is evaluated in double-float arithmetic (pairs of
+// floats, error-free transformations) and stored as a float pair so that pixel
+// offsets keep ~1e-6 px accuracy at any image size; FP64 is not used.
 
 #include "gmr_internal.cuh"
 
@@ -33,7 +34,7 @@ struct FaceGeom {
   float w;            // kappa / 12
   float sz2;          // s_z^2
   bool clamped;       // Eq. 12 epsilon clamp active
-  double mx, my, mz;  // centroid in FP64
+  float mx, my, mz;   // centroid (rounded)
 };
 
 __device__ __forceinline__ float3 f3sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -42,6 +43,52 @@ __device__ __forceinline__ float3 f3scale(float s, float3 a) { return make_float
 __device__ __forceinline__ float f3dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 f3cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// ---- double-float arithmetic (an unevaluated sum hi + lo of two floats) with
+// the error-free transformations TwoSum (Knuth) and TwoProduct (by FMA); every
+// operation is an explicit rounded intrinsic so that none is contracted or
+// reassociated. Used for the image-plane mean, which must stay accurate to
+// ~1e-6 px at any image size while FP64 is a slow pipe on this GPU.
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df qb = df_mul_f(b, q1);
+  df r = df_add(a, df{-qb.hi, -qb.lo});
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return fast_two_sum(q1, q2);
+}
+// (a + b + c) / 3 of three floats as a double-float.
+__device__ __forceinline__ df df_mean3(float a, float b, float c) {
+  df s1 = two_sum(a, b);
+  df s = df_add(df{s1.hi, s1.lo}, df{c, 0.0f});
+  float q = __fdiv_rn(s.hi, 3.0f);
+  float r = __fmaf_rn(-3.0f, q, s.hi);  // exact remainder
+  return fast_two_sum(q, __fdiv_rn(__fadd_rn(r, s.lo), 3.0f));
 }
 
 __device__ __forceinline__ FaceGeom face_geom(float3 a, float3 b, float3 c, int cov_mode) {
@@ -80,15 +127,14 @@ __device__ __forceinline__ FaceGeom face_geom(float3 a, float3 b, float3 c, int 
     g.w = 1.0f / 12.0f;
     g.sz2 = 0.0f;
   }
-  g.mx = ((double)a.x + (double)b.x + (double)c.x) * (1.0 / 3.0);
-  g.my = ((double)a.y + (double)b.y + (double)c.y) * (1.0 / 3.0);
-  g.mz = ((double)a.z + (double)b.z + (double)c.z) * (1.0 / 3.0);
+  g.mx = (a.x + b.x + c.x) * (1.0f / 3.0f);
+  g.my = (a.y + b.y + c.y) * (1.0f / 3.0f);
+  g.mz = (a.z + b.z + c.z) * (1.0f / 3.0f);
   return g;
 }
 
 struct ProjRec {
-  double tx, ty, tz;      // camera-space mean
-  double ux, uy;          // image-plane mean
+  float tx, ty, tz;       // camera-space mean
   float J00, J02, J11, J12;
   float M[6];             // J R, row-major 2x3
   float2 e[3];            // M d_a
@@ -97,20 +143,35 @@ struct ProjRec {
   float qa, qb, qc;       // conic
 };
 
+// Image-plane mean u = (fx x/z + cx, fy y/z + cy) of the centroid in
+// double-float arithmetic from the FP32 vertices.
+__device__ __forceinline__ void image_mean(float3 a, float3 b, float3 c, const ViewInfo& v, df& ux, df& uy) {
+  df m[3] = {df_mean3(a.x, b.x, c.x), df_mean3(a.y, b.y, c.y), df_mean3(a.z, b.z, c.z)};
+  df t[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    df acc = {v.t[r], 0.0f};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc = df_add(acc, df_mul_f(m[q], v.R[3 * r + q]));
+    t[r] = acc;
+  }
+  df xz = df_div(t[0], t[2]), yz = df_div(t[1], t[2]);
+  ux = df_add(df_mul_f(xz, v.fx), df{v.cx, 0.0f});
+  uy = df_add(df_mul_f(yz, v.fy), df{v.cy, 0.0f});
+}
+
 __device__ __forceinline__ ProjRec project_rec(const FaceGeom& g, const ViewInfo& v) {
   ProjRec p;
   const float* R = v.R;
-  p.tx = (double)R[0] * g.mx + (double)R[1] * g.my + (double)R[2] * g.mz + (double)v.t[0];
-  p.ty = (double)R[3] * g.mx + (double)R[4] * g.my + (double)R[5] * g.mz + (double)v.t[1];
-  p.tz = (double)R[6] * g.mx + (double)R[7] * g.my + (double)R[8] * g.mz + (double)v.t[2];
-  double iz = 1.0 / p.tz;
-  double xz = p.tx * iz, yz = p.ty * iz;
-  p.ux = (double)v.fx * xz + (double)v.cx;
-  p.uy = (double)v.fy * yz + (double)v.cy;
-  p.J00 = (float)((double)v.fx * iz);
-  p.J11 = (float)((double)v.fy * iz);
-  p.J02 = (float)(-(double)v.fx * xz * iz);
-  p.J12 = (float)(-(double)v.fy * yz * iz);
+  p.tx = R[0] * g.mx + R[1] * g.my + R[2] * g.mz + v.t[0];
+  p.ty = R[3] * g.mx + R[4] * g.my + R[5] * g.mz + v.t[1];
+  p.tz = R[6] * g.mx + R[7] * g.my + R[8] * g.mz + v.t[2];
+  const float iz = 1.0f / p.tz;
+  const float xz = p.tx * iz, yz = p.ty * iz;
+  p.J00 = v.fx * iz;
+  p.J11 = v.fy * iz;
+  p.J02 = -v.fx * xz * iz;
+  p.J12 = -v.fy * yz * iz;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     p.M[q] = p.J00 * R[q] + p.J02 * R[6 + q];
@@ -221,102 +282,141 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   if (nt == 0) return;
   FaceGeom g = face_geom(a, b, cc, cov_mode);
   ProjRec p = project_rec(g, sv);
-  float uxh = __double2float_rn(p.ux), uyh = __double2float_rn(p.uy);
-  float uxl = __double2float_rn(p.ux - (double)uxh), uyl = __double2float_rn(p.uy - (double)uyh);
-  rec_u[rid] = make_float4(uxh, uyh, uxl, uyl);
+  df ux, uy;
+  image_mean(a, b, cc, sv, ux, uy);
+  rec_u[rid] = make_float4(ux.hi, uy.hi, ux.lo, uy.lo);
   rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, 0.0f);
 }
 
-// Backward of conversion + projection. One thread per face, looping over the
-// views; the per-(view, face) gradient sums R0..R4 from the compositing
-// backward are chained through the conic inverse, Sigma' = M Sigma M^T +
-// 0.3 I, M = J R, J(t) and u(t), to dL/dmu, dL/dd_a and dL/dn, then to the
-// three vertices (d_a = v_a - mu, n = e1 x e2 / |e1 x e2|).
-__global__ void __launch_bounds__(128) k_project_bwd(
+// Backward of conversion + projection, part 1: one thread per (view, face)
+// record. The record's gradient sums R0..R4 from the compositing backward are
+// chained through the conic inverse, Sigma' = M Sigma M^T + 0.3 I, M = J R,
+// J(t) and u(t), to this view's share of dL/dmu, dL/dd_a (d_a = v_a - mu),
+// dL/dn and dL/d(kappa/12), written as 4 float4:
+// (dmu, dw), (dd_0, dn.x), (dd_1, dn.y), (dd_2, dn.z).
+__global__ void __launch_bounds__(128) k_record_bwd(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
-    const ViewInfo* __restrict__ views, int32_t C, int cov_mode, int color_mode, const float* __restrict__ opacity,
-    const float4* __restrict__ rec_grad, const float4* __restrict__ face_grad, float* __restrict__ dverts,
-    float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const ViewInfo* __restrict__ views, int cov_mode, const float4* __restrict__ rec_grad,
+    float4* __restrict__ rec_contrib) {
+  __shared__ ViewInfo sv;
+  const int c = blockIdx.y;
+  if (threadIdx.x == 0) sv = views[c];
+  __syncthreads();
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const size_t rid = (size_t)c * F + f;
+  float4* out = rec_contrib + 4 * rid;
+  const float4 r0 = rec_grad[2 * rid];
+  const float r4 = rec_grad[2 * rid + 1].x;
+  int i0, i1, i2;
+  if ((r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f) || !load_face(faces, f, V, i0, i1, i2)) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    out[0] = z; out[1] = z; out[2] = z; out[3] = z;
+    return;
+  }
+  const float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
+  const FaceGeom g = face_geom(a, b, cc, cov_mode);
+  const ViewInfo& v = sv;
+  const ProjRec p = project_rec(g, v);
+  const float dux = kLn2 * r0.x, duy = kLn2 * r0.y;
+  const float dqa = -0.5f * r0.z, dqb = -r0.w, dqc = -0.5f * r4;
+  // dL/dSigma' = -Q G_Q Q with G_Q = [[dqa, dqb/2], [dqb/2, dqc]]
+  const float g00 = dqa, g01 = 0.5f * dqb, g11 = dqc;
+  const float t00 = p.qa * g00 + p.qb * g01, t01 = p.qa * g01 + p.qb * g11;
+  const float t10 = p.qb * g00 + p.qc * g01, t11 = p.qb * g01 + p.qc * g11;
+  const float s00 = -(t00 * p.qa + t01 * p.qb);
+  const float s01 = -(t00 * p.qb + t01 * p.qc);
+  const float s11 = -(t10 * p.qb + t11 * p.qc);
+  // Sigma' = w sum e e^T + sz2 m m^T + 0.3 I
+  float2 de[3];
+  float dw = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    de[k].x = 2.f * g.w * (s00 * p.e[k].x + s01 * p.e[k].y);
+    de[k].y = 2.f * g.w * (s01 * p.e[k].x + s11 * p.e[k].y);
+    dw += s00 * p.e[k].x * p.e[k].x + 2.f * s01 * p.e[k].x * p.e[k].y + s11 * p.e[k].y * p.e[k].y;
+  }
+  float2 dm;
+  dm.x = 2.f * g.sz2 * (s00 * p.m.x + s01 * p.m.y);
+  dm.y = 2.f * g.sz2 * (s01 * p.m.x + s11 * p.m.y);
+  // e_a = M d_a, m = M n
+  float dM[6];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float dq0 = dm.x * (&g.n.x)[q], dq1 = dm.y * (&g.n.x)[q];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dq0 += de[k].x * (&g.d[k].x)[q];
+      dq1 += de[k].y * (&g.d[k].x)[q];
+    }
+    dM[q] = dq0;
+    dM[3 + q] = dq1;
+  }
+  float3 dd[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dd[k].x = p.M[0] * de[k].x + p.M[3] * de[k].y;
+    dd[k].y = p.M[1] * de[k].x + p.M[4] * de[k].y;
+    dd[k].z = p.M[2] * de[k].x + p.M[5] * de[k].y;
+  }
+  float3 dn;
+  dn.x = p.M[0] * dm.x + p.M[3] * dm.y;
+  dn.y = p.M[1] * dm.x + p.M[4] * dm.y;
+  dn.z = p.M[2] * dm.x + p.M[5] * dm.y;
+  // M = J R: dJ = dM R^T (only the non-zero entries of J)
+  const float* R = v.R;
+  const float dJ00 = dM[0] * R[0] + dM[1] * R[1] + dM[2] * R[2];
+  const float dJ02 = dM[0] * R[6] + dM[1] * R[7] + dM[2] * R[8];
+  const float dJ11 = dM[3] * R[3] + dM[4] * R[4] + dM[5] * R[5];
+  const float dJ12 = dM[3] * R[6] + dM[4] * R[7] + dM[5] * R[8];
+  // J(t), u(t) -> dL/dt
+  const float iz = 1.0f / p.tz;
+  const float x = p.tx, y = p.ty;
+  const float fxz2 = v.fx * iz * iz, fyz2 = v.fy * iz * iz;
+  const float dtx = dJ02 * (-fxz2) + dux * v.fx * iz;
+  const float dty = dJ12 * (-fyz2) + duy * v.fy * iz;
+  const float dtz = dJ00 * (-fxz2) + dJ02 * (2.f * v.fx * x * iz * iz * iz) + dJ11 * (-fyz2) +
+                    dJ12 * (2.f * v.fy * y * iz * iz * iz) - dux * v.fx * x * iz * iz - duy * v.fy * y * iz * iz;
+  // t = R mu + t_cam
+  float3 dmu;
+  dmu.x = R[0] * dtx + R[3] * dty + R[6] * dtz;
+  dmu.y = R[1] * dtx + R[4] * dty + R[7] * dtz;
+  dmu.z = R[2] * dtx + R[5] * dty + R[8] * dtz;
+  out[0] = make_float4(dmu.x, dmu.y, dmu.z, dw);
+  out[1] = make_float4(dd[0].x, dd[0].y, dd[0].z, dn.x);
+  out[2] = make_float4(dd[1].x, dd[1].y, dd[1].z, dn.y);
+  out[3] = make_float4(dd[2].x, dd[2].y, dd[2].z, dn.z);
+}
+
+// Part 2: one thread per face sums the views' contributions in view order
+// (deterministic), maps them to the three vertices (d_a = v_a - mu with mu
+// the vertex mean, n = e1 x e2 / |e1 x e2|, kappa = |A| / (pi 1e-7) when
+// clamped) and scatters them; colour and opacity gradients are per face.
+__global__ void __launch_bounds__(256) k_face_bwd(
+    const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
+    int cov_mode, int color_mode, const float* __restrict__ opacity, const float4* __restrict__ rec_contrib,
+    const float4* __restrict__ face_grad, float* __restrict__ dverts, float* __restrict__ drgb,
+    float* __restrict__ dop, int accumulate) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   int i0, i1, i2;
   if (!load_face(faces, f, V, i0, i1, i2)) return;
-  float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
-  FaceGeom g = face_geom(a, b, cc, cov_mode);
   float3 dmu = make_float3(0.f, 0.f, 0.f);
   float3 dd[3] = {dmu, dmu, dmu};
   float3 dn = dmu;
-  float dw = 0.f;  // dL/d(kappa/12)
+  float dw = 0.f;
   for (int c = 0; c < C; ++c) {
-    size_t rid = (size_t)c * F + f;
-    float4 r0 = rec_grad[2 * rid];
-    float r4 = rec_grad[2 * rid + 1].x;
-    if (r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f) continue;
-    const ViewInfo& v = views[c];
-    ProjRec p = project_rec(g, v);
-    float dux = kLn2 * r0.x, duy = kLn2 * r0.y;
-    float dqa = -0.5f * r0.z, dqb = -r0.w, dqc = -0.5f * r4;
-    // dL/dSigma' = -Q G_Q Q with G_Q = [[dqa, dqb/2], [dqb/2, dqc]]
-    float g00 = dqa, g01 = 0.5f * dqb, g11 = dqc;
-    float t00 = p.qa * g00 + p.qb * g01, t01 = p.qa * g01 + p.qb * g11;
-    float t10 = p.qb * g00 + p.qc * g01, t11 = p.qb * g01 + p.qc * g11;
-    float s00 = -(t00 * p.qa + t01 * p.qb);
-    float s01 = -(t00 * p.qb + t01 * p.qc);
-    float s11 = -(t10 * p.qb + t11 * p.qc);
-    // Sigma' = w sum e e^T + sz2 m m^T + 0.3 I
-    float2 de[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      de[k].x = 2.f * g.w * (s00 * p.e[k].x + s01 * p.e[k].y);
-      de[k].y = 2.f * g.w * (s01 * p.e[k].x + s11 * p.e[k].y);
-      dw += s00 * p.e[k].x * p.e[k].x + 2.f * s01 * p.e[k].x * p.e[k].y + s11 * p.e[k].y * p.e[k].y;
-    }
-    float2 dm;
-    dm.x = 2.f * g.sz2 * (s00 * p.m.x + s01 * p.m.y);
-    dm.y = 2.f * g.sz2 * (s01 * p.m.x + s11 * p.m.y);
-    // e_a = M d_a, m = M n
-    float dM[6];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      float dq0 = dm.x * (&g.n.x)[q], dq1 = dm.y * (&g.n.x)[q];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        dq0 += de[k].x * (&g.d[k].x)[q];
-        dq1 += de[k].y * (&g.d[k].x)[q];
-      }
-      dM[q] = dq0;
-      dM[3 + q] = dq1;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      dd[k].x += p.M[0] * de[k].x + p.M[3] * de[k].y;
-      dd[k].y += p.M[1] * de[k].x + p.M[4] * de[k].y;
-      dd[k].z += p.M[2] * de[k].x + p.M[5] * de[k].y;
-    }
-    dn.x += p.M[0] * dm.x + p.M[3] * dm.y;
-    dn.y += p.M[1] * dm.x + p.M[4] * dm.y;
-    dn.z += p.M[2] * dm.x + p.M[5] * dm.y;
-    // M = J R: dJ = dM R^T (only the non-zero entries of J)
-    const float* R = v.R;
-    float dJ00 = dM[0] * R[0] + dM[1] * R[1] + dM[2] * R[2];
-    float dJ02 = dM[0] * R[6] + dM[1] * R[7] + dM[2] * R[8];
-    float dJ11 = dM[3] * R[3] + dM[4] * R[4] + dM[5] * R[5];
-    float dJ12 = dM[3] * R[6] + dM[4] * R[7] + dM[5] * R[8];
-    // J(t), u(t) -> dL/dt
-    float iz = (float)(1.0 / p.tz);
-    float x = (float)p.tx, y = (float)p.ty;
-    float fxz2 = v.fx * iz * iz, fyz2 = v.fy * iz * iz;
-    float dtx = dJ02 * (-fxz2) + dux * v.fx * iz;
-    float dty = dJ12 * (-fyz2) + duy * v.fy * iz;
-    float dtz = dJ00 * (-fxz2) + dJ02 * (2.f * v.fx * x * iz * iz * iz) + dJ11 * (-fyz2) +
-                dJ12 * (2.f * v.fy * y * iz * iz * iz) - dux * v.fx * x * iz * iz - duy * v.fy * y * iz * iz;
-    // t = R mu + t_cam
-    dmu.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
-    dmu.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
-    dmu.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
+    const float4* in = rec_contrib + 4 * ((size_t)c * F + f);
+    const float4 q0 = in[0], q1 = in[1], q2 = in[2], q3 = in[3];
+    dmu.x += q0.x; dmu.y += q0.y; dmu.z += q0.z; dw += q0.w;
+    dd[0].x += q1.x; dd[0].y += q1.y; dd[0].z += q1.z; dn.x += q1.w;
+    dd[1].x += q2.x; dd[1].y += q2.y; dd[1].z += q2.z; dn.y += q2.w;
+    dd[2].x += q3.x; dd[2].y += q3.y; dd[2].z += q3.z; dn.z += q3.w;
   }
+  const float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
+  const FaceGeom g = face_geom(a, b, cc, cov_mode);
   // to vertices: d_a = v_a - mu (mu = mean of v), n from e1 x e2
-  float3 sdd = f3add(f3add(dd[0], dd[1]), dd[2]);
+  const float3 sdd = f3add(f3add(dd[0], dd[1]), dd[2]);
   float3 dv[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) dv[k] = f3add(f3scale(1.0f / 3.0f, f3sub(dmu, sdd)), dd[k]);
@@ -324,17 +424,17 @@ __global__ void __launch_bounds__(128) k_project_bwd(
     float3 dcr = f3scale(1.0f / g.cn, f3sub(dn, f3scale(f3dot(g.n, dn), g.n)));
     if (g.clamped) {
       // kappa = |A| / (pi 1e-7), |A| = cn / 2, w = kappa / 12
-      float dcn = dw * (1.0f / 12.0f) * (0.5f / (kPi * 1e-7f));
+      const float dcn = dw * (1.0f / 12.0f) * (0.5f / (kPi * 1e-7f));
       dcr = f3add(dcr, f3scale(dcn, g.n));
     }
-    float3 de1 = f3cross(g.e2, dcr);
-    float3 de2 = f3cross(dcr, g.e1);
+    const float3 de1 = f3cross(g.e2, dcr);
+    const float3 de2 = f3cross(dcr, g.e1);
     dv[0] = f3sub(dv[0], f3add(de1, de2));
     dv[1] = f3add(dv[1], de1);
     dv[2] = f3add(dv[2], de2);
   }
+  const int idx[3] = {i0, i1, i2};
   if (dverts) {
-    int idx[3] = {i0, i1, i2};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       atomicAdd(dverts + 3 * idx[k], dv[k].x);
@@ -342,7 +442,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(
       atomicAdd(dverts + 3 * idx[k] + 2, dv[k].z);
     }
   }
-  float4 fg = face_grad[f];
+  const float4 fg = face_grad[f];
   if (drgb) {
     if (color_mode == GMR_COLOR_PER_FACE) {
       if (accumulate) {
@@ -351,7 +451,6 @@ __global__ void __launch_bounds__(128) k_project_bwd(
         drgb[3 * f] = fg.x; drgb[3 * f + 1] = fg.y; drgb[3 * f + 2] = fg.z;
       }
     } else {
-      int idx[3] = {i0, i1, i2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         atomicAdd(drgb + 3 * idx[k], fg.x * (1.0f / 3.0f));
@@ -361,9 +460,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(
     }
   }
   if (dop && opacity) {
-    float o = opacity[f];
+    const float o = opacity[f];
     // alpha = o G: dL/do = sum dalpha G = (sum dalpha alpha) / o; clamp to [0, 1]
-    float go = (o > 0.f && o <= 1.f) ? fg.w / o : 0.f;
+    const float go = (o > 0.f && o <= 1.f) ? fg.w / o : 0.f;
     if (accumulate) dop[f] += go; else dop[f] = go;
   }
 }
@@ -389,7 +488,9 @@ __global__ void k_convert(const float* __restrict__ verts, int32_t V, const int3
   float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), c = ld_vert(verts, i2);
   FaceGeom g = face_geom(a, b, c, cov_mode);
   if (means) {
-    means[3 * f] = (float)g.mx; means[3 * f + 1] = (float)g.my; means[3 * f + 2] = (float)g.mz;
+    // correctly rounded (to ~1e-14) centroid from its double-float value
+    df mx = df_mean3(a.x, b.x, c.x), my = df_mean3(a.y, b.y, c.y), mz = df_mean3(a.z, b.z, c.z);
+    means[3 * f] = mx.hi + mx.lo; means[3 * f + 1] = my.hi + my.lo; means[3 * f + 2] = mz.hi + mz.lo;
   }
   if (cov) {
     float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -446,9 +547,11 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
                                const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
                                cudaStream_t s, int64_t* launches) {
   if (F <= 0) return cudaSuccess;
-  k_project_bwd<<<(F + 127) / 128, 128, 0, s>>>(verts, V, faces, F, views, C, cov_mode, color_mode, opacity,
-                                                ws.rec_grad, ws.face_grad, dverts, drgb, dop, accumulate);
-  *launches += 1;
+  dim3 grid((F + 127) / 128, C);
+  k_record_bwd<<<grid, 128, 0, s>>>(verts, V, faces, F, views, cov_mode, ws.rec_grad, ws.rec_contrib);
+  k_face_bwd<<<(F + 255) / 256, 256, 0, s>>>(verts, V, faces, F, C, cov_mode, color_mode, opacity, ws.rec_contrib,
+                                             ws.face_grad, dverts, drgb, dop, accumulate);
+  *launches += 2;
   return cudaGetLastError();
 }
 
