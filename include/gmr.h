@@ -109,6 +109,12 @@ typedef struct {
  * gmr_get_stage_times returns their durations. */
 #define GMR_FLAG_PROFILE 2
 
+/* With this flag the forward also records, per pixel, how many Gaussians
+ * contributed and an order-sensitive hash of their face ids (returned by
+ * gmr_debug_forward_state); for tests that need to know whether a
+ * perturbation changed any discrete decision or the compositing order. */
+#define GMR_FLAG_DEBUG_COUNTS 4
+
 /* Stages timed under GMR_FLAG_PROFILE (paper step in brackets). */
 typedef enum {
   GMR_STAGE_PROJECT = 0,      /* face colours + conversion fused with EWA projection (Sec. 2.2, 2.1) */
@@ -240,10 +246,13 @@ GMR_API gmr_status gmr_get_stage_times(gmr_ctx* ctx, gmr_stream stream, float* m
  *                    being x_hi + x_lo (float pair)
  *  rec_conic   C*F*4 (a, b, c, 0) of the conic Sigma'^-1 = [[a, b], [b, c]]
  *  n_last      n_pixels  list position + 1 of the last contributor
+ *  n_contrib   2*n_pixels  contributors per pixel, then a hash of the ordered
+ *                          contributor face ids (needs GMR_FLAG_DEBUG_COUNTS)
  * Any pointer may be NULL. n_pairs (host) receives the pair count. */
 GMR_API gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* rects, uint32_t* tile_ids,
                                    uint32_t* face_ids, int64_t cap, uint32_t* ranges, float* rec_u,
-                                   float* rec_conic, uint32_t* n_last, int64_t* n_pairs, gmr_stream stream);
+                                   float* rec_conic, uint32_t* n_last, uint32_t* n_contrib, int64_t* n_pairs,
+                                   gmr_stream stream);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,7 @@ GMR_COV_AREA, GMR_COV_EMBED_RAW = 0, 1
 GMR_COLOR_PER_FACE, GMR_COLOR_PER_VERTEX = 0, 1
 GMR_FLAG_SYNC_CHECK = 1
 GMR_FLAG_PROFILE = 2
+GMR_FLAG_DEBUG_COUNTS = 4
 STAGES = ["project", "sort_records", "scan", "emit", "sort_pairs", "ranges", "raster_fwd", "loss", "raster_bwd",
           "project_bwd"]
 
@@ -85,7 +86,7 @@ def load(path: str = LIB_PATH):
         "gmr_get_device_status": (st, [P, P, ctypes.POINTER(ctypes.c_uint32)]),
         "gmr_get_stats": (st, [P, P, ctypes.POINTER(GmrStats)]),
         "gmr_get_stage_times": (st, [P, P, ctypes.POINTER(ctypes.c_float)]),
-        "gmr_debug_forward_state": (st, [P, P, P, P, P, i64, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]),
+        "gmr_debug_forward_state": (st, [P, P, P, P, P, i64, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -177,6 +177,7 @@ gmr_status ensure_pixels(gmr_ctx* ctx, int64_t n, bool capturing) {
   gmr_status s;
   if ((s = realloc_exact(ctx, &w.pix_T, cap, "pix_T")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.pix_last, cap, "pix_last")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.pix_ncontrib, 2 * cap, "pix_ncontrib")) != GMR_OK) return s;
   w.cap_pixels = cap;
   return GMR_OK;
 }
@@ -324,7 +325,7 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   Workspace& w = ctx->ws;
   void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key[0], w.rec_key[1], w.rec_id[0],
-                  w.rec_id[1], w.rec_off, w.rec_grad, w.rec_contrib, w.face_col, w.face_grad, w.pix_T, w.pix_last,
+                  w.rec_id[1], w.rec_off, w.rec_grad, w.rec_contrib, w.face_col, w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib,
                   w.tile_range, w.pair_tile[0], w.pair_tile[1], w.pair_face[0], w.pair_face[1], w.scan_tmp,
                   w.radix_counts, w.loss_part, w.views, w.counters};
   for (void* p : bufs)
@@ -491,8 +492,9 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   // S7: compositing
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face[pb], w.views, C, F, n_tiles, cfg.bg,
-                                         images, t_final, s, &ctx->launches));
+    uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
+    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face[pb], w.views, C, F, n_tiles,
+                                         cfg.bg, images, t_final, nc, s, &ctx->launches));
   }
 
   ctx->fwd_valid = true;
@@ -598,7 +600,7 @@ gmr_status gmr_get_stage_times(gmr_ctx* ctx, gmr_stream stream, float* ms) {
 
 gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* rects, uint32_t* tile_ids,
                                    uint32_t* face_ids, int64_t cap, uint32_t* ranges, float* rec_u, float* rec_conic,
-                                   uint32_t* n_last, int64_t* n_pairs, gmr_stream stream) {
+                                   uint32_t* n_last, uint32_t* n_contrib, int64_t* n_pairs, gmr_stream stream) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   if (!ctx->fwd_valid) return fail(ctx, GMR_ERR_STATE, "no forward state");
   cudaStream_t s = (cudaStream_t)stream;
@@ -629,6 +631,14 @@ gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* 
   if (n_last && ctx->n_pixels > 0)
     GMR_CUDA(ctx, cudaMemcpyAsync(n_last, w.pix_last, sizeof(uint32_t) * (size_t)ctx->n_pixels,
                                   cudaMemcpyDeviceToDevice, s));
+  if (n_contrib && ctx->n_pixels > 0) {
+    if (!(ctx->fwd_cfg.flags & GMR_FLAG_DEBUG_COUNTS))
+      return fail(ctx, GMR_ERR_STATE, "contributor counts need GMR_FLAG_DEBUG_COUNTS in the forward");
+    GMR_CUDA(ctx, cudaMemcpyAsync(n_contrib, w.pix_ncontrib, sizeof(uint32_t) * (size_t)ctx->n_pixels,
+                                  cudaMemcpyDeviceToDevice, s));
+    GMR_CUDA(ctx, cudaMemcpyAsync(n_contrib + ctx->n_pixels, w.pix_ncontrib + w.cap_pixels,
+                                  sizeof(uint32_t) * (size_t)ctx->n_pixels, cudaMemcpyDeviceToDevice, s));
+  }
   return GMR_OK;
 }
 

@@ -180,6 +180,7 @@ struct Workspace {
   int64_t cap_pixels = 0;
   float* pix_T = nullptr;
   uint32_t* pix_last = nullptr;
+  uint32_t* pix_ncontrib = nullptr;  // 2 x cap_pixels: counts, then order hashes (GMR_FLAG_DEBUG_COUNTS)
   // tiles
   int64_t cap_tiles = 0;
   uint2* tile_range = nullptr;
@@ -242,7 +243,8 @@ cudaError_t launch_debug_records(const Workspace& ws, const uint32_t* sorted_key
                                  int64_t* launches);
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              float* images, float* t_final_out, cudaStream_t s, int64_t* launches);
+                              float* images, float* t_final_out, uint32_t* ncontrib_out, cudaStream_t s,
+                              int64_t* launches);
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               const float* dL_dimages, cudaStream_t s, int64_t* launches);

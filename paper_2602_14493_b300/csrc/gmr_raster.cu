@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
-    uint32_t* __restrict__ pix_last, float* __restrict__ t_out, Counters* __restrict__ counters) {
+    uint32_t* __restrict__ pix_last, float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
+    int64_t n_pix_total, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
   const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
 
   float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
-  uint32_t last[PPT], term[PPT], ncontrib[PPT];
+  uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
   int blk[PPT];
   bool done[PPT], inside[PPT];
   int px[PPT], py[PPT];
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     last[k] = 0;
     term[k] = 0;
     ncontrib[k] = 0;
+    chash[k] = 0;
     blk[k] = PixMap<TS, NT>::block(k);
   }
   const uint2 range = ranges[g];
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
-                           false);
+                           nc_out != nullptr);
     __syncthreads();
     const int nl = warp_list<BATCH, NW, PPT>(st, cnt, 0, cnt);
     const int warp = threadIdx.x >> 5;
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
         T[k] = test;
         last[k] = (uint32_t)(base + j + 1);
         ++ncontrib[k];
+        if (nc_out) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
       }
     }
   }
@@ -317,6 +320,10 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     pix_T[pid] = T[k];
     pix_last[pid] = last[k];
     if (t_out) t_out[pid] = T[k];
+    if (nc_out) {
+      nc_out[pid] = ncontrib[k];
+      nc_out[n_pix_total + pid] = chash[k];
+    }
     evals += term[k] ? term[k] : (uint32_t)n;
   }
 #pragma unroll
@@ -566,10 +573,11 @@ __global__ void k_debug_records(const uint32_t* __restrict__ sorted_keys, const 
 
 template <int TS, int NT, int BATCH>
 void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, float* images, float* t_out, cudaStream_t s) {
+                int32_t F, const float* bg, float* images, float* t_out, uint32_t* nc_out, cudaStream_t s) {
   k_raster_fwd<TS, NT, BATCH><<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
-                                                                 images, ws.pix_T, ws.pix_last, t_out, ws.counters);
+                                                                 images, ws.pix_T, ws.pix_last, t_out, nc_out,
+                                                                 ws.cap_pixels, ws.counters);
 }
 
 template <int TS, int NT, int BATCH>
@@ -603,11 +611,12 @@ cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, 
 
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              float* images, float* t_final_out, cudaStream_t s, int64_t* launches) {
+                              float* images, float* t_final_out, uint32_t* ncontrib_out, cudaStream_t s,
+                              int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
 #define GMR_FWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, s)
+  fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, ncontrib_out, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
   else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
   else GMR_FWD(16, 64, 64); else GMR_FWD(16, 64, 128); else GMR_FWD(16, 64, 256);

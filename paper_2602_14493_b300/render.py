@@ -68,7 +68,7 @@ class Renderer:
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
-                 sync_check=True, profile=False, threads=256):
+                 sync_check=True, profile=False, threads=256, debug_counts=False):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -81,7 +81,8 @@ class Renderer:
         self.cfg.cov_mode = _COV[cov_mode]
         self.cfg.color_mode = _COLOR[color_mode]
         self.cfg.bg[:] = [float(x) for x in bg]
-        self.cfg.flags = (_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
+        self.cfg.flags = ((_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
+                          | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0))
         self.color_mode = color_mode
         self._ctx = ctypes.c_void_p()
         self._check(self._L.gmr_create(ctypes.byref(self.cfg), ctypes.byref(self._ctx)), "gmr_create")
@@ -220,19 +221,30 @@ class Renderer:
         n_last = torch.empty(n_pixels, dtype=torch.int32, device=dev)
         npairs = ctypes.c_int64()
         self._check(self._L.gmr_debug_forward_state(self._ctx, _ptr(depth), _ptr(rects), None, None, 0, _ptr(ranges),
-                                                    _ptr(rec_u), _ptr(conic), _ptr(n_last), ctypes.byref(npairs),
-                                                    _stream(stream)), "gmr_debug_forward_state")
+                                                    _ptr(rec_u), _ptr(conic), _ptr(n_last), None,
+                                                    ctypes.byref(npairs), _stream(stream)), "gmr_debug_forward_state")
         P = int(npairs.value)
         tiles = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
         fids = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
         self._check(self._L.gmr_debug_forward_state(self._ctx, None, None, _ptr(tiles), _ptr(fids), max(P, 1), None,
-                                                    None, None, None, ctypes.byref(npairs), _stream(stream)),
+                                                    None, None, None, None, ctypes.byref(npairs), _stream(stream)),
                     "gmr_debug_forward_state")
         torch.cuda.synchronize()
         u32 = lambda t: t.cpu().numpy().view(np.uint32)
         return {"depth_bits": u32(depth), "rects": rects.cpu().numpy(), "rec_u": rec_u.cpu().numpy(),
                 "conic": conic.cpu().numpy()[:, :3], "ranges": u32(ranges), "n_last": u32(n_last),
                 "tile_ids": u32(tiles)[:P], "face_ids": u32(fids)[:P], "n_pairs": P}
+
+
+    def contributor_counts(self, n_pixels, stream=None) -> torch.Tensor:
+        """Per-pixel contributor counts of the last forward, then per-pixel
+        hashes of the ordered contributor lists (debug_counts)."""
+        out = torch.empty(2 * n_pixels, dtype=torch.int32, device="cuda")
+        npairs = ctypes.c_int64()
+        self._check(self._L.gmr_debug_forward_state(self._ctx, None, None, None, None, 0, None, None, None, None,
+                                                    _ptr(out), ctypes.byref(npairs), _stream(stream)),
+                    "gmr_debug_forward_state")
+        return out
 
 
 class GMRRender(torch.autograd.Function):
