@@ -53,7 +53,7 @@ FLOPS_BWD_CONTRIB = 59
 # DRAM bytes per launch measured by ncu for the dominant kernel on the
 # default workload (profiles/raster_bwd_icosphere5_sin_8x512.md); None when
 # the kernel has changed since the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("raster_bwd", "icosphere5_sin_8x512"): 56187136}
 
 L2_FLUSH_BYTES = 512 << 20
 
