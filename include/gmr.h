@@ -222,6 +222,24 @@ GMR_API gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* 
 GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int64_t n, float* dL_dimg,
                        double* loss, gmr_stream stream);
 
+/* gmr_l2_loss without a context and without allocating anything: the same
+ * loss sum((img - target)^2) (device double, overwritten) and gradient
+ * 2 (img - target) (dL_dimg, n floats), for callers that must not call
+ * cudaMalloc where they compute the loss (latency-critical loops, where an
+ * allocation may synchronise the device; processes whose device memory is
+ * owned by their own pool or by a framework's caching allocator). The
+ * paper has no counterpart; this is an interface convenience. The reduction's
+ * partial sums live in a fixed 128 KB array inside the library on each GPU,
+ * which limits n to GMR_L2_NOALLOC_MAX_ELEMS (larger n returns
+ * GMR_ERR_CAPACITY before anything is enqueued). The array's address is
+ * looked up on the first call on each device: make that call before any
+ * stream capture. Calls on one GPU share the array, so calls that can run
+ * concurrently on the same GPU race; order them. Bad pointers or n < 0 return
+ * GMR_ERR_INVALID_ARG; a failing CUDA call returns GMR_ERR_CUDA. */
+#define GMR_L2_NOALLOC_MAX_ELEMS 67108864
+GMR_API gmr_status gmr_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* dL_dimg,
+                                       double* loss, gmr_stream stream);
+
 /* Synchronises the stream, returns and clears the device status bits
  * (GMR_DEV_*) accumulated since the last call. */
 GMR_API gmr_status gmr_get_device_status(gmr_ctx* ctx, gmr_stream stream, uint32_t* status);

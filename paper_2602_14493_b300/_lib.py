@@ -23,6 +23,7 @@ GMR_COLOR_PER_FACE, GMR_COLOR_PER_VERTEX = 0, 1
 GMR_FLAG_SYNC_CHECK = 1
 GMR_FLAG_PROFILE = 2
 GMR_FLAG_DEBUG_COUNTS = 4
+GMR_L2_NOALLOC_MAX_ELEMS = 67108864
 STAGES = ["project", "sort_records", "scan", "emit", "sort_pairs", "ranges", "raster_fwd", "loss", "raster_bwd",
           "project_bwd"]
 
@@ -31,6 +32,7 @@ EXPORTS = [
     "gmr_config_default", "gmr_create", "gmr_destroy", "gmr_set_config", "gmr_last_error", "gmr_status_string",
     "gmr_image_offsets", "gmr_reserve", "gmr_convert", "gmr_render_fwd", "gmr_render_bwd", "gmr_l2_loss",
     "gmr_get_device_status", "gmr_get_stats", "gmr_get_stage_times", "gmr_debug_forward_state",
+    "gmr_l2_loss_noalloc",
 ]
 
 
@@ -83,6 +85,7 @@ def load(path: str = LIB_PATH):
         "gmr_render_fwd": (st, [P, P, i32, P, i32, P, P, P, i32, P, P, P]),
         "gmr_render_bwd": (st, [P, P, P, P, P, i32, P]),
         "gmr_l2_loss": (st, [P, P, P, i64, P, P, P]),
+        "gmr_l2_loss_noalloc": (st, [P, P, i64, P, P, P]),
         "gmr_get_device_status": (st, [P, P, ctypes.POINTER(ctypes.c_uint32)]),
         "gmr_get_stats": (st, [P, P, ctypes.POINTER(GmrStats)]),
         "gmr_get_stage_times": (st, [P, P, ctypes.POINTER(ctypes.c_float)]),
