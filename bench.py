@@ -436,9 +436,8 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
     # memory-bound stages: algorithmic bytes
     R = stats["n_records"]
     P = stats["n_pairs"]
-    byts = {"project": R * 64 + len(scene.faces) * 28, "sort_records": R * 8 * 2 * 4,
-            "scan": R * 12, "emit": P * 8 + R * 16, "sort_pairs": P * 8 * 2 * 2, "ranges": P * 4,
-            "project_bwd": R * 32 + len(scene.faces) * 52}.get(stage, 0)
+    byts = {"project": R * 64 + len(scene.faces) * 28 + P * 4, "scan": stats["n_tiles"] * 8,
+            "bin": R * 16 + P * 8 * 3 + P * 4, "project_bwd": R * 96 + len(scene.faces) * 52}.get(stage, 0)
     ach = byts / (ms / 1e3) / 1e9
     pk = peaks["hbm_gbs"]
     return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,

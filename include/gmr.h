@@ -55,7 +55,6 @@ typedef enum {
 /* Device status bits reported by gmr_get_device_status. */
 #define GMR_DEV_BAD_FACE_INDEX 1u /* a face referenced a vertex outside [0, V) */
 #define GMR_DEV_PAIR_OVERFLOW 2u  /* more (tile, Gaussian) pairs than capacity */
-#define GMR_DEV_SORT_TIMEOUT 4u   /* a bounded wait in the radix sort expired */
 
 /* Sec. 2.2: which 3D covariance a facet becomes. */
 typedef enum {
@@ -115,19 +114,16 @@ typedef struct {
  * perturbation changed any discrete decision or the compositing order. */
 #define GMR_FLAG_DEBUG_COUNTS 4
 
-/* Stages timed under GMR_FLAG_PROFILE (paper step in brackets). */
+/* Stages timed under GMR_FLAG_PROFILE. */
 typedef enum {
-  GMR_STAGE_PROJECT = 0,      /* face colours + conversion fused with EWA projection (Sec. 2.2, 2.1) */
-  GMR_STAGE_SORT_RECORDS = 1, /* Gaussians by depth key */
-  GMR_STAGE_SCAN = 2,         /* tiles per Gaussian -> pair offsets */
-  GMR_STAGE_EMIT = 3,         /* (tile, Gaussian) pairs */
-  GMR_STAGE_SORT_PAIRS = 4,   /* pairs by tile id */
-  GMR_STAGE_RANGES = 5,       /* per-tile [start, end) */
-  GMR_STAGE_RASTER_FWD = 6,   /* front-to-back compositing */
-  GMR_STAGE_LOSS = 7,         /* gmr_l2_loss */
-  GMR_STAGE_RASTER_BWD = 8,   /* compositing backward */
-  GMR_STAGE_PROJECT_BWD = 9,  /* projection + conversion backward, vertex scatter */
-  GMR_NUM_STAGES = 10
+  GMR_STAGE_PROJECT = 0,      /* conversion fused with EWA projection, tile counts (Sec. 2.2, 2.1) */
+  GMR_STAGE_SCAN = 1,         /* per-tile counts -> tile segments, total pairs */
+  GMR_STAGE_BIN = 2,          /* keys into segments, per-tile radix sort, ranges */
+  GMR_STAGE_RASTER_FWD = 3,   /* front-to-back compositing */
+  GMR_STAGE_LOSS = 4,         /* gmr_l2_loss */
+  GMR_STAGE_RASTER_BWD = 5,   /* compositing backward */
+  GMR_STAGE_PROJECT_BWD = 6,  /* projection + conversion backward, vertex scatter */
+  GMR_NUM_STAGES = 7
 } gmr_stage;
 
 typedef struct gmr_ctx gmr_ctx;

@@ -24,8 +24,7 @@ GMR_FLAG_SYNC_CHECK = 1
 GMR_FLAG_PROFILE = 2
 GMR_FLAG_DEBUG_COUNTS = 4
 GMR_L2_NOALLOC_MAX_ELEMS = 67108864
-STAGES = ["project", "sort_records", "scan", "emit", "sort_pairs", "ranges", "raster_fwd", "loss", "raster_bwd",
-          "project_bwd"]
+STAGES = ["project", "scan", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
 
 # Every function the header declares (checked by the CPU test suite).
 EXPORTS = [

@@ -37,7 +37,6 @@ struct gmr_ctx {
   const float* opacity = nullptr;
   int32_t V = 0, F = 0, C = 0;
   int64_t n_tiles = 0, n_pixels = 0;
-  int pair_buf = 0, rec_buf = 0;
   gmr_config fwd_cfg;
 };
 
@@ -121,11 +120,7 @@ gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
   if ((s = realloc_exact(ctx, &w.rec_q, cap, "rec_q")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_rect, cap, "rec_rect")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_ntiles, cap, "rec_ntiles")) != GMR_OK) return s;
-  for (int b = 0; b < 2; ++b) {
-    if ((s = realloc_exact(ctx, &w.rec_key[b], cap, "rec_key")) != GMR_OK) return s;
-    if ((s = realloc_exact(ctx, &w.rec_id[b], cap, "rec_id")) != GMR_OK) return s;
-  }
-  if ((s = realloc_exact(ctx, &w.rec_off, cap, "rec_off")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_key, cap, "rec_key")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_grad, 2 * cap, "rec_grad")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_contrib, 4 * cap, "rec_contrib")) != GMR_OK) return s;
   w.cap_records = cap;
@@ -134,11 +129,26 @@ gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
 
 gmr_status ensure_scratch(gmr_ctx* ctx, int64_t n_items, bool capturing) {
   Workspace& w = ctx->ws;
-  int64_t ncounts = gmr::radix_counts_needed(n_items);
-  gmr_status s = grow<uint32_t>(ctx, &w.radix_counts, &w.cap_counts, ncounts, capturing, "radix_counts");
-  if (s != GMR_OK) return s;
-  int64_t nscan = std::max(gmr::scan_block_sums_needed(n_items), gmr::scan_block_sums_needed(ncounts));
-  return grow<uint32_t>(ctx, &w.scan_tmp, &w.cap_scan, nscan, capturing, "scan_tmp");
+  return grow<uint32_t>(ctx, &w.scan_tmp, &w.cap_scan, gmr::scan_block_sums_needed(n_items), capturing, "scan_tmp");
+}
+
+// Per-tile counts, scanned starts and ranges. The counts must be zero at the
+// start of every forward; a fresh allocation is cleared here.
+gmr_status ensure_tiles(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n > w.cap_tiles) {
+    if (capturing) return fail(ctx, GMR_ERR_STATE, "tile workspace must grow during stream capture; call gmr_reserve");
+    const int64_t cap = n + n / 4 + 1024;
+    gmr_status s;
+    if ((s = realloc_exact(ctx, &w.tile_count, cap, "tile_count")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.tile_start, cap, "tile_start")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.tile_range, cap, "tile_range")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.long_tiles, cap, "long_tiles")) != GMR_OK) return s;
+    cudaError_t e = cudaMemset(w.tile_count, 0, sizeof(uint32_t) * (size_t)cap);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset(tile_count)");
+    w.cap_tiles = cap;
+  }
+  return ensure_scratch(ctx, n, capturing);
 }
 
 gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
@@ -148,12 +158,11 @@ gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
   if (capturing) return fail(ctx, GMR_ERR_STATE, "pair workspace must grow during stream capture; call gmr_reserve");
   const int64_t cap = std::min<int64_t>(n + n / 4 + 4096, (int64_t)(1 << 30) - 4096);
   gmr_status s;
-  for (int b = 0; b < 2; ++b) {
-    if ((s = realloc_exact(ctx, &w.pair_tile[b], cap, "pair_tile")) != GMR_OK) return s;
-    if ((s = realloc_exact(ctx, &w.pair_face[b], cap, "pair_face")) != GMR_OK) return s;
-  }
+  for (int b = 0; b < 2; ++b)
+    if ((s = realloc_exact(ctx, &w.pair_key[b], cap, "pair_key")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.pair_face, cap, "pair_face")) != GMR_OK) return s;
   w.cap_pairs = cap;
-  return ensure_scratch(ctx, std::max(cap, w.cap_records), false);
+  return GMR_OK;
 }
 
 // face_col and face_grad share one capacity.
@@ -223,11 +232,6 @@ struct StageTimer {
   }
 };
 
-int bits_for(int64_t n) {
-  int b = 0;
-  while (b < 63 && ((int64_t)1 << b) < n) ++b;
-  return b;
-}
 
 bool same_cams(const std::vector<gmr_camera>& a, const gmr_camera* b, int32_t C) {
   return (int32_t)a.size() == C && std::memcmp(a.data(), b, sizeof(gmr_camera) * (size_t)C) == 0;
@@ -324,10 +328,9 @@ gmr_status gmr_create(const gmr_config* cfg, gmr_ctx** out) {
 gmr_status gmr_destroy(gmr_ctx* ctx) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   Workspace& w = ctx->ws;
-  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key[0], w.rec_key[1], w.rec_id[0],
-                  w.rec_id[1], w.rec_off, w.rec_grad, w.rec_contrib, w.face_col, w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib,
-                  w.tile_range, w.pair_tile[0], w.pair_tile[1], w.pair_face[0], w.pair_face[1], w.scan_tmp,
-                  w.radix_counts, w.loss_part, w.views, w.counters};
+  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.rec_contrib, w.face_col,
+                  w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
+                  w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
@@ -371,10 +374,9 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   if ((s = ensure_pixels(ctx, max_pixels, false)) != GMR_OK) return s;
   // tiles: at most one per 16x16 block plus one ragged tile per row/column and view
   int64_t mt = max_pixels / 256 + 2 * (int64_t)max_views * 1024 + 16;
-  if ((s = grow<uint2>(ctx, &ctx->ws.tile_range, &ctx->ws.cap_tiles, mt, false, "tile_range")) != GMR_OK) return s;
+  if ((s = ensure_tiles(ctx, mt, false)) != GMR_OK) return s;
   if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
   if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;
-  if ((s = ensure_scratch(ctx, std::max(ctx->ws.cap_pairs, ctx->ws.cap_records), false)) != GMR_OK) return s;
   int64_t lp = gmr::l2_loss_partials_needed(3 * max_pixels);
   return grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, lp, false, "loss_part");
 }
@@ -425,8 +427,7 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   if ((st = ensure_records(ctx, n_rec, capturing)) != GMR_OK) return st;
   if ((st = ensure_faces(ctx, F, capturing)) != GMR_OK) return st;
   if ((st = ensure_pixels(ctx, n_pixels, capturing)) != GMR_OK) return st;
-  if ((st = grow<uint2>(ctx, &w.tile_range, &w.cap_tiles, n_tiles, capturing, "tile_range")) != GMR_OK) return st;
-  if ((st = ensure_scratch(ctx, std::max(n_rec, w.cap_pairs), capturing)) != GMR_OK) return st;
+  if ((st = ensure_tiles(ctx, n_tiles, capturing)) != GMR_OK) return st;
 
   if (!cams_same) {
     GMR_CUDA(ctx, cudaEventSynchronize(ctx->upload_done));
@@ -441,25 +442,17 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_fwd, 0, sizeof(unsigned long long), s));
   GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->contribs, 0, sizeof(unsigned long long), s));
 
-  // S1/S2: per-face attributes, then conversion + projection per (view, face)
+  // S1/S2: conversion + projection per (view, face); per-face colour and
+  // opacity; pair count of every tile
   {
     StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_face_attrs(rgb, opacity, faces, F, V, cfg.color_mode, w.face_col, s, &ctx->launches));
-    GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, w.views, C, cfg.tile, cfg.cov_mode, w, s, &ctx->launches));
+    GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, w.views, C, cfg.tile,
+                                      cfg.cov_mode, w, s, &ctx->launches));
   }
-  // S5a: records in ascending depth key (stable: view, face order kept)
-  cudaError_t e = cudaSuccess;
-  int rb;
-  {
-    StageTimer t(ctx, GMR_STAGE_SORT_RECORDS, s, cfg);
-    rb = gmr::radix_sort_pairs(w.rec_key, w.rec_id, nullptr, n_rec, 32, w.radix_counts, &w.counters->status, s,
-                               &ctx->launches, &e);
-  }
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "record sort");
-  // S3: pair offsets in sorted record order, total to the counters
+  // S3: tile segments = exclusive scan of the per-tile counts; total pairs
   {
     StageTimer t(ctx, GMR_STAGE_SCAN, s, cfg);
-    GMR_CUDA(ctx, gmr::scan_exclusive(w.rec_ntiles, w.rec_id[rb], n_rec, w.rec_off, &w.counters->n_pairs,
+    GMR_CUDA(ctx, gmr::scan_exclusive(w.tile_count, nullptr, n_tiles, w.tile_start, &w.counters->n_pairs,
                                       w.scan_tmp, s, &ctx->launches));
   }
   if ((cfg.flags & GMR_FLAG_SYNC_CHECK) && !capturing) {
@@ -467,33 +460,23 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
                                   cudaMemcpyDeviceToHost, s));
     GMR_CUDA(ctx, cudaStreamSynchronize(s));
     int64_t P = ctx->counters_pinned->n_pairs;
-    if ((st = ensure_pairs(ctx, P, false)) != GMR_OK) return st;
+    if ((st = ensure_pairs(ctx, P, false)) != GMR_OK) {
+      // the per-tile counts must be zero for the next forward
+      cudaMemsetAsync(w.tile_count, 0, sizeof(uint32_t) * (size_t)n_tiles, s);
+      return st;
+    }
   }
-  // S4: emit (global tile, face) pairs
+  // S4-S6: keys into tile segments, per-tile radix sort by (depth, face),
+  // ranges (the tile counts return to zero)
   {
-    StageTimer t(ctx, GMR_STAGE_EMIT, s, cfg);
-    GMR_CUDA(ctx, cudaMemsetAsync(w.tile_range, 0, sizeof(uint2) * (size_t)n_tiles, s));
-    GMR_CUDA(ctx, gmr::launch_emit_pairs(w, w.rec_id[rb], n_rec, w.views, F, s, &ctx->launches));
-  }
-  // S5b: pairs by tile id (stable)
-  int pb;
-  {
-    StageTimer t(ctx, GMR_STAGE_SORT_PAIRS, s, cfg);
-    pb = gmr::radix_sort_pairs(w.pair_tile, w.pair_face, &w.counters->n_pairs, w.cap_pairs, bits_for(n_tiles),
-                               w.radix_counts, &w.counters->status, s, &ctx->launches, &e);
-  }
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "pair sort");
-  // S6: tile ranges
-  {
-    StageTimer t(ctx, GMR_STAGE_RANGES, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_tile_ranges(w.pair_tile[pb], w.counters, w.cap_pairs, w.tile_range, s,
-                                          &ctx->launches));
+    StageTimer t(ctx, GMR_STAGE_BIN, s, cfg);
+    GMR_CUDA(ctx, gmr::launch_bin_pairs(w, n_rec, F, w.views, n_tiles, s, &ctx->launches));
   }
   // S7: compositing
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
     uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
-    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face[pb], w.views, C, F, n_tiles,
+    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face, w.views, C, F, n_tiles,
                                          cfg.bg, images, t_final, nc, s, &ctx->launches));
   }
 
@@ -501,7 +484,6 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   ctx->verts = verts; ctx->faces = faces; ctx->rgb = rgb; ctx->opacity = opacity;
   ctx->V = V; ctx->F = F; ctx->C = C;
   ctx->n_tiles = n_tiles; ctx->n_pixels = n_pixels;
-  ctx->pair_buf = pb; ctx->rec_buf = rb;
   ctx->fwd_cfg = cfg;
   return GMR_OK;
 }
@@ -527,7 +509,7 @@ gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dvert
   // S8: compositing backward
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face[ctx->pair_buf], w.views, C, F,
+    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face, w.views, C, F,
                                          ctx->n_tiles, cfg.bg, dL_dimages, s, &ctx->launches));
   }
   // S9: projection + conversion backward, vertex scatter
@@ -611,20 +593,18 @@ gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* 
   GMR_CUDA(ctx, cudaStreamSynchronize(s));
   int64_t P = ctx->counters_pinned->n_pairs;
   if (n_pairs) *n_pairs = P;
-  if (n_rec > 0 && (depth_bits || rects || rec_conic)) {
-    GMR_CUDA(ctx, gmr::launch_debug_records(w, w.rec_key[ctx->rec_buf], w.rec_id[ctx->rec_buf], n_rec, depth_bits,
-                                            rects, rec_conic, s, &ctx->launches));
-  }
+  if (n_rec > 0 && (rects || rec_conic))
+    GMR_CUDA(ctx, gmr::launch_debug_records(w, n_rec, rects, rec_conic, s, &ctx->launches));
+  if (depth_bits && n_rec > 0)
+    GMR_CUDA(ctx, cudaMemcpyAsync(depth_bits, w.rec_key, sizeof(uint32_t) * (size_t)n_rec, cudaMemcpyDeviceToDevice,
+                                  s));
   if (rec_u && n_rec > 0)
     GMR_CUDA(ctx, cudaMemcpyAsync(rec_u, w.rec_u, sizeof(float4) * (size_t)n_rec, cudaMemcpyDeviceToDevice, s));
   if ((tile_ids || face_ids) && P > cap) return fail(ctx, GMR_ERR_CAPACITY, "cap smaller than the pair count");
   if (P > w.cap_pairs) return fail(ctx, GMR_ERR_CAPACITY, "pair buffer overflowed in the forward");
-  if (tile_ids && P > 0)
-    GMR_CUDA(ctx, cudaMemcpyAsync(tile_ids, w.pair_tile[ctx->pair_buf], sizeof(uint32_t) * (size_t)P,
-                                  cudaMemcpyDeviceToDevice, s));
+  if (tile_ids && P > 0) GMR_CUDA(ctx, gmr::launch_expand_tiles(w.tile_range, ctx->n_tiles, tile_ids, s, &ctx->launches));
   if (face_ids && P > 0)
-    GMR_CUDA(ctx, cudaMemcpyAsync(face_ids, w.pair_face[ctx->pair_buf], sizeof(uint32_t) * (size_t)P,
-                                  cudaMemcpyDeviceToDevice, s));
+    GMR_CUDA(ctx, cudaMemcpyAsync(face_ids, w.pair_face, sizeof(uint32_t) * (size_t)P, cudaMemcpyDeviceToDevice, s));
   if (ranges)
     GMR_CUDA(ctx, cudaMemcpyAsync(ranges, w.tile_range, sizeof(uint2) * (size_t)ctx->n_tiles,
                                   cudaMemcpyDeviceToDevice, s));

@@ -1,0 +1,350 @@
+// Binning of the Gaussians into screen tiles, in (tile, depth, face) order
+// (the 3DGS binning, Sec. 2.1), as a two-level radix sort:
+//
+//  1. most significant digit = the global tile id: the projection counts the
+//     pairs of every tile (one atomic per (tile, Gaussian) pair), an
+//     exclusive scan of the counts gives each tile's segment, and
+//     k_scatter_keys writes each pair's 64-bit key (depth bits << 32 | face)
+//     into its tile's segment (slot order within a segment is arbitrary);
+//  2. the remaining digits, (depth bits, face), within each tile: segments
+//     of up to 512 keys (nearly all) are sorted by one warp each, in
+//     registers, with a bitonic network (shuffles only, no CTA barrier);
+//     longer segments are listed and sorted by one CTA each with an LSD
+//     radix sort on the 8-bit digits that differ within the segment (usually
+//     not the depth's exponent byte nor the face index's upper bytes), in
+//     shared memory up to kSegSmem keys and through global memory beyond.
+//
+// Keys are unique (face ids are), so the result is the unique (tile, depth,
+// face) order regardless of the slot order of step 1.
+
+#include "gmr_internal.cuh"
+
+namespace gmr {
+
+namespace {
+
+constexpr int kSegThreads = 256;
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegSmem = 2048;  // keys sorted in shared memory
+constexpr int kRadix = 256;
+
+// One thread per (view, face) record: scatter the record's keys into the
+// segments of the tiles of its rectangle. tile_count is decremented back to
+// zero so that it is ready for the next forward; lanes of a warp that hit the
+// same tile in the same step combine their decrements (one atomic per tile).
+__global__ void k_scatter_keys(const uint32_t* __restrict__ rec_ntiles, const uint2* __restrict__ rec_rect,
+                               const uint32_t* __restrict__ rec_key, const ViewInfo* __restrict__ views,
+                               int64_t n_rec, int32_t F, const uint32_t* __restrict__ tile_start,
+                               uint32_t* __restrict__ tile_count, int64_t cap,
+                               unsigned long long* __restrict__ keys, Counters* __restrict__ counters) {
+  const int64_t rid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool live = rid < n_rec;
+  const uint32_t nt = live ? rec_ntiles[rid] : 0u;
+  uint32_t maxnt = nt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxnt = max(maxnt, __shfl_xor_sync(0xffffffffu, maxnt, o));
+  if (maxnt == 0) return;  // warp-uniform
+  const bool fits = (int64_t)counters->n_pairs <= cap;
+  if (!fits && (threadIdx.x | blockIdx.x) == 0) atomicOr(&counters->status, kDevOverflow);
+  int x0 = 0, x1 = -1, y0 = 0, tx = 1;
+  uint32_t base = 0;
+  unsigned long long key = 0ull;
+  if (nt > 0) {
+    const int c = (int)(rid / F);
+    const uint32_t f = (uint32_t)(rid - (int64_t)c * F);
+    const uint2 r = rec_rect[rid];
+    x0 = r.x & 0xffff; x1 = r.x >> 16; y0 = r.y & 0xffff;
+    tx = views[c].tiles_x;
+    base = (uint32_t)views[c].tile_base;
+    key = ((unsigned long long)rec_key[rid] << 32) | f;
+  }
+  const int w = x1 - x0 + 1;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t k = 0; k < maxnt; ++k) {
+    const bool act = k < nt;
+    uint32_t t = 0xffffffffu - (uint32_t)lane;  // distinct dummies for idle lanes
+    if (act) {
+      const int yy = y0 + (int)(k / (uint32_t)w), xx = x0 + (int)(k % (uint32_t)w);
+      t = base + (uint32_t)(yy * tx + xx);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (act && lane == leader) old = atomicSub(&tile_count[t], (uint32_t)__popc(peers));
+    old = __shfl_sync(0xffffffffu, old, leader);
+    if (act && fits) keys[tile_start[t] + old - 1u - __popc(peers & lt)] = key;
+  }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread over the CTA (kSegThreads threads).
+__device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* sw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_incl_scan(v, lane);
+  if (lane == 31) sw[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kSegWarps ? sw[lane] : 0u;
+    uint32_t wi = warp_incl_scan(w, lane);
+    if (lane < kSegWarps) sw[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t r = incl - v + sw[warp];
+  __syncthreads();
+  return r;
+}
+
+struct SegSmem {
+  unsigned long long a[kSegSmem];
+  unsigned long long b[kSegSmem];
+  uint32_t wcnt[kSegWarps][kRadix];  // per warp, per digit
+  uint32_t base[kRadix];             // running start of each digit
+  uint32_t sw[32];
+  unsigned long long red_and[kSegWarps], red_or[kSegWarps];
+};
+
+// Stable counting pass on digit `shift` of keys src[0, L) -> dst (shared or
+// global memory). Items are taken in chunks of kSegThreads in order; in a
+// chunk warp w takes items [w*32, w*32 + 32) and ranks equal digits by lane.
+__device__ void seg_radix_pass(const unsigned long long* src, unsigned long long* dst, int L, int shift,
+                               SegSmem& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  // histogram of the whole segment -> exclusive digit starts
+  for (int d = threadIdx.x; d < kRadix; d += kSegThreads) sm.base[d] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < L; i += kSegThreads) atomicAdd(&sm.base[(uint32_t)(src[i] >> shift) & 0xffu], 1u);
+  __syncthreads();
+  {
+    const uint32_t v = sm.base[threadIdx.x];
+    const uint32_t ex = cta_excl_scan(v, sm.sw);
+    sm.base[threadIdx.x] = ex;
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < L; c0 += kSegThreads) {
+    for (int d = lane; d < kRadix; d += 32) sm.wcnt[warp][d] = 0;
+    __syncwarp();
+    const int i = c0 + threadIdx.x;
+    const bool ok = i < L;
+    const unsigned long long k = ok ? src[i] : 0ull;
+    const uint32_t d = ok ? ((uint32_t)(k >> shift) & 0xffu) : (kRadix + lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt);
+    if (ok && (peers & lt) == 0) sm.wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    // per digit: exclusive prefix over the warps of this chunk
+    {
+      const int dd = threadIdx.x;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < kSegWarps; ++w) {
+        const uint32_t cnt = sm.wcnt[w][dd];
+        sm.wcnt[w][dd] = run;
+        run += cnt;
+      }
+      // sm.base[dd] is advanced after the scatter below (run = chunk count)
+      __syncthreads();
+      if (ok) dst[sm.base[d] + sm.wcnt[warp][d] + rank] = k;
+      __syncthreads();
+      sm.base[dd] += run;
+    }
+    __syncthreads();
+  }
+}
+
+// Ascending bitonic sort of 32*KPL 64-bit keys held by one warp, element
+// e = r * 32 + lane in register r of lane `lane`.
+template <int KPL>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[KPL], int lane) {
+  constexpr int N = 32 * KPL;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {  // partner in another register of the same lane
+        const int jr = j / 32;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+          if (r & jr) continue;
+          const int e = r * 32 + lane;
+          const bool asc = (e & k) == 0;
+          const unsigned long long a = v[r], b = v[r | jr];
+          const bool sw = asc ? (a > b) : (a < b);
+          v[r] = sw ? b : a;
+          v[r | jr] = sw ? a : b;
+        }
+      } else {  // partner in lane ^ j, same register
+        const bool upper = (lane & j) != 0;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+          const int e = r * 32 + lane;
+          const bool asc = (e & k) == 0;
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], j);
+          const bool take_min = asc != upper;
+          v[r] = take_min ? (v[r] < o ? v[r] : o) : (v[r] > o ? v[r] : o);
+        }
+      }
+    }
+  }
+}
+
+template <int KPL>
+__device__ __forceinline__ void warp_sort_segment(const unsigned long long* __restrict__ gk, int L,
+                                                  uint32_t* __restrict__ out, int lane) {
+  unsigned long long v[KPL];
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) {
+    const int e = r * 32 + lane;
+    v[r] = e < L ? gk[e] : ~0ull;
+  }
+  warp_bitonic<KPL>(v, lane);
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) {
+    const int e = r * 32 + lane;
+    if (e < L) out[e] = (uint32_t)v[r];
+  }
+}
+
+constexpr int kWarpSortMax = 512;
+constexpr int kTilesPerCta = kSegThreads / 32;
+
+// One warp per global tile: write the range; sort segments of up to 512 keys
+// in registers; list longer segments for k_long_sort.
+__global__ void __launch_bounds__(kSegThreads) k_tile_sort(const uint32_t* __restrict__ tile_start,
+                                                           int64_t n_tiles, const unsigned long long* __restrict__ keys,
+                                                           uint32_t* __restrict__ pair_face,
+                                                           uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
+                                                           uint32_t* __restrict__ long_count,
+                                                           const Counters* __restrict__ counters, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
+  if (t >= n_tiles) return;
+  const uint32_t P = counters->n_pairs;
+  if ((int64_t)P > cap) {  // overflow: the keys were not written
+    if (lane == 0) ranges[t] = make_uint2(0u, 0u);
+    return;
+  }
+  const uint32_t start = tile_start[t];
+  const uint32_t end = (t + 1 < n_tiles) ? tile_start[t + 1] : P;
+  const int L = (int)(end - start);
+  if (lane == 0) ranges[t] = L > 0 ? make_uint2(start, end) : make_uint2(0u, 0u);
+  if (L <= 0) return;
+  const unsigned long long* gk = keys + start;
+  uint32_t* out = pair_face + start;
+  if (L == 1) {
+    if (lane == 0) out[0] = (uint32_t)gk[0];
+  } else if (L <= 64) {
+    warp_sort_segment<2>(gk, L, out, lane);
+  } else if (L <= 128) {
+    warp_sort_segment<4>(gk, L, out, lane);
+  } else if (L <= 256) {
+    warp_sort_segment<8>(gk, L, out, lane);
+  } else if (L <= kWarpSortMax) {
+    warp_sort_segment<16>(gk, L, out, lane);
+  } else if (lane == 0) {
+    long_list[atomicAdd(long_count, 1u)] = (uint32_t)t;
+  }
+}
+
+// Segments longer than kWarpSortMax: one CTA each, LSD radix sort on the
+// 8-bit digits that differ within the segment, in shared memory up to
+// kSegSmem keys and through global memory beyond.
+__global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
+                                                           const uint32_t* __restrict__ long_count,
+                                                           const uint2* __restrict__ ranges,
+                                                           unsigned long long* __restrict__ keys,
+                                                           unsigned long long* __restrict__ keys_tmp,
+                                                           uint32_t* __restrict__ pair_face) {
+  __shared__ SegSmem sm;
+  const uint32_t nlong = *long_count;
+  for (uint32_t li = blockIdx.x; li < nlong; li += gridDim.x) {
+    const uint2 rg = ranges[long_list[li]];
+    const int L = (int)(rg.y - rg.x);
+    unsigned long long* gk = keys + rg.x;
+    unsigned long long* gt = keys_tmp + rg.x;
+    const bool in_smem = L <= kSegSmem;
+    unsigned long long a = ~0ull, o = 0ull;
+    for (int i = threadIdx.x; i < L; i += kSegThreads) {
+      const unsigned long long k = gk[i];
+      a &= k;
+      o |= k;
+      if (in_smem) sm.a[i] = k;
+    }
+#pragma unroll
+    for (int s2 = 16; s2 > 0; s2 >>= 1) {
+      a &= __shfl_xor_sync(0xffffffffu, a, s2);
+      o |= __shfl_xor_sync(0xffffffffu, o, s2);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      sm.red_and[warp] = a;
+      sm.red_or[warp] = o;
+    }
+    __syncthreads();
+    unsigned long long diff = 0;
+#pragma unroll
+    for (int w = 0; w < kSegWarps; ++w) diff |= sm.red_and[w] ^ sm.red_or[w];
+    unsigned long long* src = in_smem ? sm.a : gk;
+    unsigned long long* dst = in_smem ? sm.b : gt;
+    for (int shift = 0; shift < 64; shift += 8) {
+      if (((diff >> shift) & 0xffull) == 0) continue;  // uniform over the CTA
+      seg_radix_pass(src, dst, L, shift, sm);
+      unsigned long long* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < L; i += kSegThreads) pair_face[rg.x + i] = (uint32_t)src[i];
+    __syncthreads();
+  }
+}
+
+// Debug: global tile id of every sorted pair, from the ranges.
+__global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* __restrict__ tile_ids) {
+  const int64_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+  const uint2 r = ranges[t];
+  for (uint32_t i = r.x + threadIdx.x; i < r.y; i += blockDim.x) tile_ids[i] = (uint32_t)t;
+}
+
+}  // namespace
+
+cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int64_t n_tiles,
+                             cudaStream_t s, int64_t* launches) {
+  if (n_rec > 0) {
+    k_scatter_keys<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(ws.rec_ntiles, ws.rec_rect, ws.rec_key, views,
+                                                                  n_rec, F, ws.tile_start, ws.tile_count,
+                                                                  ws.cap_pairs, ws.pair_key[0], ws.counters);
+    *launches += 1;
+  }
+  if (n_tiles > 0) {
+    cudaError_t e = cudaMemsetAsync(&ws.counters->n_long, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kSegThreads, 0, s>>>(
+        ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, &ws.counters->n_long,
+        ws.counters, ws.cap_pairs);
+    k_long_sort<<<148, kSegThreads, 0, s>>>(ws.long_tiles, &ws.counters->n_long, ws.tile_range, ws.pair_key[0],
+                                           ws.pair_key[1], ws.pair_face);
+    *launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_tiles(const uint2* ranges, int64_t n_tiles, uint32_t* tile_ids, cudaStream_t s,
+                                int64_t* launches) {
+  if (n_tiles <= 0) return cudaSuccess;
+  k_expand_tiles<<<(unsigned)n_tiles, 128, 0, s>>>(ranges, n_tiles, tile_ids);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace gmr

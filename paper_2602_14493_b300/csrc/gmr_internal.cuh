@@ -55,6 +55,8 @@ struct Counters {
   unsigned long long evals_fwd;
   unsigned long long evals_bwd;
   unsigned long long contribs;
+  uint32_t n_long;   // tiles whose segment is too long for a warp sort
+  uint32_t pad;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -167,9 +169,7 @@ struct Workspace {
   float4* rec_q = nullptr;       // (a2, b2, c2, 0) pre-scaled conic
   uint2* rec_rect = nullptr;     // packed (x0 | x1 << 16, y0 | y1 << 16)
   uint32_t* rec_ntiles = nullptr;
-  uint32_t* rec_key[2] = {nullptr, nullptr};  // depth bits, ping-pong
-  uint32_t* rec_id[2] = {nullptr, nullptr};   // record ids, ping-pong
-  uint32_t* rec_off = nullptr;   // pair offsets in sorted record order
+  uint32_t* rec_key = nullptr;   // FP32 depth bits (0xffffffff when culled)
   float4* rec_grad = nullptr;    // 2 float4 per record: (R0..R3), (R4, 0, 0, 0)
   float4* rec_contrib = nullptr; // 4 float4 per record: backward contributions per view
   // faces
@@ -183,16 +183,17 @@ struct Workspace {
   uint32_t* pix_ncontrib = nullptr;  // 2 x cap_pixels: counts, then order hashes (GMR_FLAG_DEBUG_COUNTS)
   // tiles
   int64_t cap_tiles = 0;
-  uint2* tile_range = nullptr;
+  uint32_t* tile_count = nullptr;  // pairs per tile (zero between forwards)
+  uint32_t* tile_start = nullptr;  // exclusive scan of tile_count
+  uint2* tile_range = nullptr;     // [start, end) per tile, (0, 0) when empty
+  uint32_t* long_tiles = nullptr;  // tiles sorted by the CTA path
   // pairs
   int64_t cap_pairs = 0;
-  uint32_t* pair_tile[2] = {nullptr, nullptr};
-  uint32_t* pair_face[2] = {nullptr, nullptr};
-  // scratch for scans and radix histograms
+  unsigned long long* pair_key[2] = {nullptr, nullptr};  // (depth bits << 32 | face)
+  uint32_t* pair_face = nullptr;   // face ids in (tile, depth, face) order
+  // scratch for scans
   int64_t cap_scan = 0;
   uint32_t* scan_tmp = nullptr;     // block sums
-  int64_t cap_counts = 0;
-  uint32_t* radix_counts = nullptr;
   // loss partial sums
   int64_t cap_loss = 0;
   double* loss_part = nullptr;
@@ -210,19 +211,12 @@ struct Workspace {
 cudaError_t scan_exclusive(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* out, uint32_t* total,
                            uint32_t* block_sums, cudaStream_t s, int64_t* launches);
 int64_t scan_block_sums_needed(int64_t n);
-// Stable LSD radix sort of (key, value) u32 pairs on the low `bits` key bits
-// (at most 32), 8 bits per pass. n is read from *n_dev when n_dev is not null
-// (clamped to n_cap), else n_cap. scratch holds radix_counts_needed(n_cap)
-// u32. Returns the index (0 or 1) of the buffers holding the result.
-int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], const uint32_t* n_dev, int64_t n_cap, int bits,
-                     uint32_t* scratch, uint32_t* dev_status, cudaStream_t s, int64_t* launches, cudaError_t* err);
-int64_t radix_counts_needed(int64_t n_cap);
-
 // project.cu
-cudaError_t launch_face_attrs(const float* rgb, const float* opacity, const int32_t* faces, int32_t F, int32_t V,
-                              int color_mode, float4* face_col, cudaStream_t s, int64_t* launches);
-cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const ViewInfo* views,
-                           int32_t C, int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);
+// Conversion + projection of every (view, face) record; also writes the
+// per-face colour/opacity and counts the pairs of every tile.
+cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
+                           const float* opacity, int color_mode, const ViewInfo* views, int32_t C, int tile,
+                           int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);
 cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
                                const ViewInfo* views, int32_t C, int cov_mode, int color_mode, const float* opacity,
                                const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
@@ -232,14 +226,14 @@ cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, 
                            float* face_rgb, float* face_o, Counters* counters, cudaStream_t s, int64_t* launches);
 
 // raster.cu
-cudaError_t launch_emit_pairs(const Workspace& ws, const uint32_t* sorted_rid, int64_t n_rec, const ViewInfo* views,
-                              int32_t F, cudaStream_t s, int64_t* launches);
-cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, int64_t cap_pairs, uint2* ranges,
-                               cudaStream_t s, int64_t* launches);
-// Debug copies of the forward's per-record data: depth key bits and tile
-// rectangle per record id, and the unscaled conic.
-cudaError_t launch_debug_records(const Workspace& ws, const uint32_t* sorted_keys, const uint32_t* sorted_ids,
-                                 int64_t n_rec, uint32_t* depth_bits, int32_t* rects, float* conic, cudaStream_t s,
+// bin.cu: scatter keys into tile segments, sort each segment, write ranges.
+cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int64_t n_tiles,
+                             cudaStream_t s, int64_t* launches);
+cudaError_t launch_expand_tiles(const uint2* ranges, int64_t n_tiles, uint32_t* tile_ids, cudaStream_t s,
+                                int64_t* launches);
+// Debug copies of the forward's per-record data: tile rectangle and the
+// unscaled conic.
+cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* rects, float* conic, cudaStream_t s,
                                  int64_t* launches);
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,

@@ -222,59 +222,80 @@ __device__ __forceinline__ bool load_face(const int32_t* faces, int f, int V, in
 
 // ---------------------------------------------------------------- kernels
 
-// Per-face colour (Eq. 16 in per-vertex mode) and clamped opacity.
-__global__ void k_face_attrs(const float* __restrict__ rgb, const float* __restrict__ opacity,
-                             const int32_t* __restrict__ faces, int32_t F, int32_t V, int color_mode,
-                             float4* __restrict__ face_col) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  float r, g, b;
-  if (color_mode == GMR_COLOR_PER_FACE) {
-    r = __ldg(rgb + 3 * f); g = __ldg(rgb + 3 * f + 1); b = __ldg(rgb + 3 * f + 2);
-  } else {
-    int i0, i1, i2;
-    if (!load_face(faces, f, V, i0, i1, i2)) { face_col[f] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
-    r = (__ldg(rgb + 3 * i0) + __ldg(rgb + 3 * i1) + __ldg(rgb + 3 * i2)) * (1.0f / 3.0f);
-    g = (__ldg(rgb + 3 * i0 + 1) + __ldg(rgb + 3 * i1 + 1) + __ldg(rgb + 3 * i2 + 1)) * (1.0f / 3.0f);
-    b = (__ldg(rgb + 3 * i0 + 2) + __ldg(rgb + 3 * i1 + 2) + __ldg(rgb + 3 * i2 + 2)) * (1.0f / 3.0f);
-  }
-  float o = opacity ? __ldg(opacity + f) : 1.0f;
-  o = fminf(fmaxf(o, 0.0f), 1.0f);
-  face_col[f] = make_float4(r, g, b, o);
-}
-
 constexpr int kProjThreads = 128;
 
-// One thread per (face, view): binning spec, depth key, tile count, and the
-// precise record (image mean as a float pair, pre-scaled conic).
+// One thread per (face, view): binning spec, depth key, tile rectangle and
+// one count per tile of the rectangle, and the precise record (image mean as
+// a float pair, pre-scaled conic). The view-0 threads also write the face's
+// colour (Eq. 16 in per-vertex mode) and clamped opacity.
 __global__ void __launch_bounds__(kProjThreads) k_project(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
+    const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode,
     const ViewInfo* __restrict__ views, int tile, float inv_tile, int cov_mode, float4* __restrict__ rec_u,
     float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
-    uint32_t* __restrict__ rec_key, uint32_t* __restrict__ rec_id, Counters* __restrict__ counters) {
+    uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
+    Counters* __restrict__ counters) {
   __shared__ ViewInfo sv;
-  int c = blockIdx.y;
+  const int c = blockIdx.y;
   if (threadIdx.x == 0) sv = views[c];
   __syncthreads();
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  uint32_t rid = (uint32_t)c * (uint32_t)F + (uint32_t)f;
-  rec_id[rid] = rid;
-  int i0, i1, i2;
-  if (!load_face(faces, f, V, i0, i1, i2)) {
-    if (c == 0) atomicOr(&counters->status, kDevBadFace);
-    rec_key[rid] = 0xffffffffu;
-    rec_ntiles[rid] = 0;
-    rec_rect[rid] = make_uint2(1u, 1u);
-    return;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = f < F;
+  const uint32_t rid = (uint32_t)c * (uint32_t)F + (uint32_t)f;
+  int i0 = 0, i1 = 0, i2 = 0;
+  const bool ok = live && load_face(faces, f, V, i0, i1, i2);
+  if (live && c == 0) {
+    float r = 0.f, g = 0.f, b = 0.f;
+    if (color_mode == GMR_COLOR_PER_FACE) {
+      r = __ldg(rgb + 3 * f); g = __ldg(rgb + 3 * f + 1); b = __ldg(rgb + 3 * f + 2);
+    } else if (ok) {
+      r = (__ldg(rgb + 3 * i0) + __ldg(rgb + 3 * i1) + __ldg(rgb + 3 * i2)) * (1.0f / 3.0f);
+      g = (__ldg(rgb + 3 * i0 + 1) + __ldg(rgb + 3 * i1 + 1) + __ldg(rgb + 3 * i2 + 1)) * (1.0f / 3.0f);
+      b = (__ldg(rgb + 3 * i0 + 2) + __ldg(rgb + 3 * i1 + 2) + __ldg(rgb + 3 * i2 + 2)) * (1.0f / 3.0f);
+    }
+    float o = opacity ? __ldg(opacity + f) : 1.0f;
+    o = fminf(fmaxf(o, 0.0f), 1.0f);
+    face_col[f] = make_float4(r, g, b, o);
   }
-  float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
-  BinResult br = bin_spec(a, b, cc, sv, tile, inv_tile);
+  float3 a = make_float3(0.f, 0.f, 0.f), b = a, cc = a;
+  BinResult br;
+  br.visible = false;
+  br.depth = 0.f;
+  br.x0 = 1; br.x1 = 0; br.y0 = 1; br.y1 = 0;
+  if (ok) {
+    a = ld_vert(verts, i0); b = ld_vert(verts, i1); cc = ld_vert(verts, i2);
+    br = bin_spec(a, b, cc, sv, tile, inv_tile);
+  }
   uint32_t nt = 0;
   uint2 rect = make_uint2(1u, 1u);  // x0 = 1 > x1 = 0: empty
   if (br.visible && br.x0 <= br.x1) {
     nt = (uint32_t)(br.x1 - br.x0 + 1) * (uint32_t)(br.y1 - br.y0 + 1);
     rect = make_uint2((uint32_t)br.x0 | ((uint32_t)br.x1 << 16), (uint32_t)br.y0 | ((uint32_t)br.y1 << 16));
+  }
+  // pair counts of the tiles of the rectangle; lanes that hit the same tile
+  // in the same step combine their increments into one atomic
+  {
+    const int lane = threadIdx.x & 31;
+    uint32_t maxnt = nt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxnt = max(maxnt, __shfl_xor_sync(0xffffffffu, maxnt, o));
+    const int w = br.x1 - br.x0 + 1;
+    const uint32_t base = (uint32_t)sv.tile_base;
+    for (uint32_t k = 0; k < maxnt; ++k) {
+      const bool act = k < nt;
+      uint32_t t = 0xffffffffu - (uint32_t)lane;  // distinct dummies for idle lanes
+      if (act) t = base + (uint32_t)((br.y0 + (int)(k / (uint32_t)w)) * sv.tiles_x + br.x0 + (int)(k % (uint32_t)w));
+      const uint32_t peers = __match_any_sync(0xffffffffu, t);
+      if (act && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
+    }
+  }
+  if (!live) return;
+  if (!ok) {
+    if (c == 0) atomicOr(&counters->status, kDevBadFace);
+    rec_key[rid] = 0xffffffffu;
+    rec_ntiles[rid] = 0;
+    rec_rect[rid] = make_uint2(1u, 1u);
+    return;
   }
   rec_key[rid] = br.visible ? __float_as_uint(br.depth) : 0xffffffffu;
   rec_ntiles[rid] = nt;
@@ -523,21 +544,14 @@ __global__ void k_convert(const float* __restrict__ verts, int32_t V, const int3
 
 }  // namespace
 
-cudaError_t launch_face_attrs(const float* rgb, const float* opacity, const int32_t* faces, int32_t F, int32_t V,
-                              int color_mode, float4* face_col, cudaStream_t s, int64_t* launches) {
-  if (F <= 0) return cudaSuccess;
-  k_face_attrs<<<(F + 255) / 256, 256, 0, s>>>(rgb, opacity, faces, F, V, color_mode, face_col);
-  *launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const ViewInfo* views,
-                           int32_t C, int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
+cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
+                           const float* opacity, int color_mode, const ViewInfo* views, int32_t C, int tile,
+                           int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
   if (F <= 0 || C <= 0) return cudaSuccess;
   dim3 grid((F + kProjThreads - 1) / kProjThreads, C);
-  k_project<<<grid, kProjThreads, 0, s>>>(verts, V, faces, F, views, tile, 1.0f / (float)tile, cov_mode, ws.rec_u,
-                                          ws.rec_q, ws.rec_rect, ws.rec_ntiles, ws.rec_key[0], ws.rec_id[0],
-                                          ws.counters);
+  k_project<<<grid, kProjThreads, 0, s>>>(verts, V, faces, F, rgb, opacity, color_mode, views, tile,
+                                          1.0f / (float)tile, cov_mode, ws.rec_u, ws.rec_q, ws.rec_rect,
+                                          ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.counters);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -60,51 +60,6 @@ struct PixMap {
   }
 };
 
-// ---------------------------------------------------------------- emit
-// One thread per record in sorted (depth) order: writes (global tile, face)
-// for every tile of its rectangle at its scanned offset.
-__global__ void k_emit_pairs(const uint32_t* __restrict__ sorted_rid, const uint32_t* __restrict__ rec_ntiles,
-                             const uint2* __restrict__ rec_rect, const uint32_t* __restrict__ rec_off,
-                             const ViewInfo* __restrict__ views, int64_t n_rec, int32_t F, int64_t cap,
-                             uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_face,
-                             Counters* __restrict__ counters) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_rec) return;
-  uint32_t total = counters->n_pairs;
-  if ((int64_t)total > cap) {
-    if (k == 0) atomicOr(&counters->status, kDevOverflow);
-    return;
-  }
-  uint32_t rid = sorted_rid[k];
-  uint32_t nt = rec_ntiles[rid];
-  if (nt == 0) return;
-  uint32_t off = rec_off[k];
-  int c = (int)(rid / (uint32_t)F);
-  uint32_t f = rid - (uint32_t)c * (uint32_t)F;
-  uint2 r = rec_rect[rid];
-  int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-  int tx = views[c].tiles_x;
-  uint32_t base = (uint32_t)views[c].tile_base;
-  for (int y = y0; y <= y1; ++y)
-    for (int x = x0; x <= x1; ++x) {
-      pair_tile[off] = base + (uint32_t)(y * tx + x);
-      pair_face[off] = f;
-      ++off;
-    }
-}
-
-// [start, end) of each tile's run in the sorted pair list.
-__global__ void k_tile_ranges(const uint32_t* __restrict__ tiles, const Counters* __restrict__ counters, int64_t cap,
-                              uint2* __restrict__ ranges) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = counters->n_pairs;
-  if (n > cap) return;
-  if (i >= n) return;
-  uint32_t t = tiles[i];
-  if (i == 0 || tiles[i - 1] != t) ranges[t].x = (uint32_t)i;
-  if (i == n - 1 || tiles[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
-}
-
 // ---------------------------------------------------------------- staging
 template <int BATCH, int NW>
 struct Stage {
@@ -204,7 +159,8 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uin
 #define GMR_BWD_MIN_WARPS 0
 #endif
 
-template <int TS, int NT, int BATCH>
+// DBG: also record per-pixel contributor counts and order hashes (tests).
+template <int TS, int NT, int BATCH, bool DBG>
 __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_raster_fwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
@@ -261,7 +217,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
-                           nc_out != nullptr);
+                           DBG);
     __syncthreads();
     const int nl = warp_list<BATCH, NW, PPT>(st, cnt, 0, cnt);
     const int warp = threadIdx.x >> 5;
@@ -304,7 +260,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
         T[k] = test;
         last[k] = (uint32_t)(base + j + 1);
         ++ncontrib[k];
-        if (nc_out) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
+        if (DBG) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
       }
     }
   }
@@ -320,7 +276,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     pix_T[pid] = T[k];
     pix_last[pid] = last[k];
     if (t_out) t_out[pid] = T[k];
-    if (nc_out) {
+    if (DBG) {
       nc_out[pid] = ncontrib[k];
       nc_out[n_pix_total + pid] = chash[k];
     }
@@ -548,13 +504,10 @@ __global__ void k_l2_final(const double* __restrict__ part, int64_t nb, double* 
   }
 }
 
-__global__ void k_debug_records(const uint32_t* __restrict__ sorted_keys, const uint32_t* __restrict__ sorted_ids,
-                                const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_q, int64_t n_rec,
-                                uint32_t* __restrict__ depth_bits, int32_t* __restrict__ rects,
-                                float* __restrict__ conic) {
+__global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_q, int64_t n_rec,
+                                int32_t* __restrict__ rects, float* __restrict__ conic) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_rec) return;
-  if (depth_bits) depth_bits[sorted_ids[k]] = sorted_keys[k];
   if (rects) {
     uint2 r = rec_rect[k];
     rects[4 * k] = (int32_t)(r.x & 0xffff);
@@ -574,7 +527,8 @@ __global__ void k_debug_records(const uint32_t* __restrict__ sorted_keys, const 
 template <int TS, int NT, int BATCH>
 void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
                 int32_t F, const float* bg, float* images, float* t_out, uint32_t* nc_out, cudaStream_t s) {
-  k_raster_fwd<TS, NT, BATCH><<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
+  auto kern = nc_out ? k_raster_fwd<TS, NT, BATCH, true> : k_raster_fwd<TS, NT, BATCH, false>;
+  kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
                                                                  images, ws.pix_T, ws.pix_last, t_out, nc_out,
                                                                  ws.cap_pixels, ws.counters);
@@ -590,24 +544,6 @@ void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
 }
 
 }  // namespace
-
-cudaError_t launch_emit_pairs(const Workspace& ws, const uint32_t* sorted_rid, int64_t n_rec, const ViewInfo* views,
-                              int32_t F, cudaStream_t s, int64_t* launches) {
-  if (n_rec <= 0) return cudaSuccess;
-  k_emit_pairs<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(sorted_rid, ws.rec_ntiles, ws.rec_rect, ws.rec_off,
-                                                               views, n_rec, F, ws.cap_pairs, ws.pair_tile[0],
-                                                               ws.pair_face[0], ws.counters);
-  *launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tile_ranges(const uint32_t* tiles, const Counters* counters, int64_t cap_pairs, uint2* ranges,
-                               cudaStream_t s, int64_t* launches) {
-  if (cap_pairs <= 0) return cudaSuccess;
-  k_tile_ranges<<<(unsigned)((cap_pairs + 255) / 256), 256, 0, s>>>(tiles, counters, cap_pairs, ranges);
-  *launches += 1;
-  return cudaGetLastError();
-}
 
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
@@ -644,12 +580,10 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace&
   return cudaGetLastError();
 }
 
-cudaError_t launch_debug_records(const Workspace& ws, const uint32_t* sorted_keys, const uint32_t* sorted_ids,
-                                 int64_t n_rec, uint32_t* depth_bits, int32_t* rects, float* conic, cudaStream_t s,
+cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* rects, float* conic, cudaStream_t s,
                                  int64_t* launches) {
   if (n_rec <= 0) return cudaSuccess;
-  k_debug_records<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(sorted_keys, sorted_ids, ws.rec_rect, ws.rec_q,
-                                                                  n_rec, depth_bits, rects, conic);
+  k_debug_records<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(ws.rec_rect, ws.rec_q, n_rec, rects, conic);
   *launches += 1;
   return cudaGetLastError();
 }

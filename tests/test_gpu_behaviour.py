@@ -204,5 +204,5 @@ def test_stats_and_launch_count():
     assert st["n_pairs"] == len(oracle.sorted_pairs(s.verts, s.faces, s.cams, 16)[0])
     assert st["n_pixels"] == 128 * 128 and st["n_tiles"] == 64
     assert st["evals_fwd"] > 0 and st["evals_bwd"] > 0
-    assert st["launches"] > st0["launches"] >= 10
+    assert st["launches"] > st0["launches"] >= 6
     r.close()
