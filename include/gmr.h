@@ -88,13 +88,16 @@ typedef struct {
  * low-pass term is added to every projected covariance. */
 typedef struct {
   int32_t tile;       /* tile edge in pixels: 16 or 32 */
-  int32_t threads;    /* threads per tile: 64, 128 or 256 (16x16 tiles), 256 (32x32);
-                         each thread composites tile^2 / threads pixels */
+  int32_t threads;    /* forward threads per tile: 64, 128 or 256 (16x16 tiles), 256
+                         (32x32); each thread composites tile^2 / threads pixels */
+  int32_t threads_bwd; /* backward threads per tile, same choices */
   int32_t batch;      /* Gaussians staged per shared-memory batch: 64, 128 or 256 */
   int32_t cov_mode;   /* gmr_cov_mode */
   int32_t color_mode; /* gmr_color_mode */
   float bg[3];        /* background colour added as T_final * bg */
   int32_t flags;      /* GMR_FLAG_* */
+  uint32_t profile_stages; /* under GMR_FLAG_PROFILE: bit s set = time gmr_stage s;
+                              0 = time every stage */
 } gmr_config;
 
 /* With this flag the forward reads the pair count back to the host once
@@ -103,9 +106,10 @@ typedef struct {
  * graph) and an undersized buffer sets GMR_DEV_PAIR_OVERFLOW instead. */
 #define GMR_FLAG_SYNC_CHECK 1
 
-/* With this flag every stage of the forward and backward is bracketed by
- * CUDA events on the call's stream (also inside a captured graph), and
- * gmr_get_stage_times returns their durations. */
+/* With this flag every stage of the forward and backward (or those selected
+ * by profile_stages) is bracketed by CUDA events on the call's stream (also
+ * inside a captured graph), and gmr_get_stage_times returns their
+ * durations. */
 #define GMR_FLAG_PROFILE 2
 
 /* With this flag the forward also records, per pixel, how many Gaussians
@@ -141,7 +145,8 @@ typedef struct {
   int64_t pair_capacity; /* current pair buffer capacity */
 } gmr_stats;
 
-/* Fills *cfg with the defaults: tile 16, 256 threads, batch 256, GMR_COV_AREA,
+/* Fills *cfg with the defaults: tile 16, 128 threads (forward and backward),
+ * batch 256, GMR_COV_AREA,
  * GMR_COLOR_PER_FACE, black background, GMR_FLAG_SYNC_CHECK. */
 GMR_API gmr_status gmr_config_default(gmr_config* cfg);
 

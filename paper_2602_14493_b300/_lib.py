@@ -36,9 +36,11 @@ EXPORTS = [
 
 
 class GmrConfig(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int32), ("threads", ctypes.c_int32), ("batch", ctypes.c_int32),
+    _fields_ = [("tile", ctypes.c_int32), ("threads", ctypes.c_int32), ("threads_bwd", ctypes.c_int32),
+                ("batch", ctypes.c_int32),
                 ("cov_mode", ctypes.c_int32),
-                ("color_mode", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32)]
+                ("color_mode", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32),
+                ("profile_stages", ctypes.c_uint32)]
 
 
 class GmrCamera(ctypes.Structure):

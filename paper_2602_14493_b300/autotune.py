@@ -1,5 +1,5 @@
 """Autotuner for the rasterizer's launch shape: tile size, threads per tile
-and Gaussians per shared-memory batch.
+(forward and backward separately) and Gaussians per shared-memory batch.
 
 Every candidate renders the same forward + L2 loss + backward step; the
 fastest (median of CUDA-event timings after warm-up) wins. Images do not
@@ -17,12 +17,19 @@ import statistics
 
 import torch
 
-CANDIDATES = [
-    (16, 256, 256), (16, 256, 128), (16, 256, 64),
-    (16, 128, 256), (16, 128, 128), (16, 128, 64),
-    (16, 64, 256), (16, 64, 128), (16, 64, 64),
-    (32, 256, 256), (32, 256, 128),
+# (tile, forward threads per tile, backward threads per tile, batch)
+CANDIDATES = [(16, tf, tb, b) for tf in (256, 128, 64) for tb in (256, 128, 64) for b in (256, 128, 64)] + [
+    (32, 256, 256, 256), (32, 256, 256, 128),
 ]
+
+
+def _apply(renderer, shape):
+    tile, threads, threads_bwd, batch = shape
+    renderer.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch)
+
+
+def shape_name(shape) -> str:
+    return "x".join(str(x) for x in shape)
 
 
 def cache_path() -> str:
@@ -59,13 +66,13 @@ def _store(d):
 
 def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=CANDIDATES, use_cache=True):
     """Times each candidate shape on this workload and configures
-    ``renderer`` with the fastest. Returns (best (tile, threads, batch),
-    {shape: median ms})."""
+    ``renderer`` with the fastest. Returns (best (tile, threads,
+    threads_bwd, batch), {shape: median ms})."""
     sig = signature(faces.shape[0], cams)
     cache = _load() if use_cache else {}
-    if use_cache and sig in cache:
+    if use_cache and sig in cache and len(cache[sig]["best"]) == 4:
         best = tuple(cache[sig]["best"])
-        renderer.set_config(tile=best[0], threads=best[1], batch=best[2])
+        _apply(renderer, best)
         return best, {}
     stream = torch.cuda.current_stream()
     img = torch.empty((target.shape[0], 3), device=verts.device)
@@ -74,8 +81,8 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=
     dv, dc = torch.empty_like(verts), torch.empty_like(rgb)
     do = torch.empty_like(opacity) if opacity is not None else None
     results = {}
-    for tile, threads, batch in candidates:
-        renderer.set_config(tile=tile, threads=threads, batch=batch)
+    for shape in candidates:
+        _apply(renderer, shape)
         ts = []
         for rep in range(reps + 2):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -87,10 +94,10 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=
             b.synchronize()
             if rep >= 2:
                 ts.append(a.elapsed_time(b))
-        results[(tile, threads, batch)] = statistics.median(ts)
+        results[shape] = statistics.median(ts)
     best = min(results, key=results.get)
-    renderer.set_config(tile=best[0], threads=best[1], batch=best[2])
+    _apply(renderer, best)
     if use_cache:
-        cache[sig] = {"best": list(best), "ms": {f"{k[0]}x{k[1]}x{k[2]}": v for k, v in results.items()}}
+        cache[sig] = {"best": list(best), "ms": {shape_name(k): v for k, v in results.items()}}
         _store(cache)
     return best, results

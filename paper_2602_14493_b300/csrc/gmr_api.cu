@@ -59,11 +59,17 @@ gmr_status cuda_fail(gmr_ctx* ctx, cudaError_t e, const char* where) {
 
 bool valid_config(const gmr_config* c, std::string* why) {
   if (c->tile != 16 && c->tile != 32) { *why = "tile must be 16 or 32"; return false; }
-  if (c->tile == 16 && c->threads != 64 && c->threads != 128 && c->threads != 256) {
-    *why = "threads must be 64, 128 or 256 with 16x16 tiles";
+  if (c->profile_stages >> GMR_NUM_STAGES) {
+    *why = "profile_stages has bits beyond the last stage";
     return false;
   }
-  if (c->tile == 32 && c->threads != 256) { *why = "threads must be 256 with 32x32 tiles"; return false; }
+  for (int32_t th : {c->threads, c->threads_bwd}) {
+    if (c->tile == 16 && th != 64 && th != 128 && th != 256) {
+      *why = "threads must be 64, 128 or 256 with 16x16 tiles";
+      return false;
+    }
+    if (c->tile == 32 && th != 256) { *why = "threads must be 256 with 32x32 tiles"; return false; }
+  }
   if (c->batch != 64 && c->batch != 128 && c->batch != 256) { *why = "batch must be 64, 128 or 256"; return false; }
   if (c->cov_mode != GMR_COV_AREA && c->cov_mode != GMR_COV_EMBED_RAW) { *why = "bad cov_mode"; return false; }
   if (c->color_mode != GMR_COLOR_PER_FACE && c->color_mode != GMR_COLOR_PER_VERTEX) {
@@ -134,6 +140,25 @@ gmr_status ensure_scratch(gmr_ctx* ctx, int64_t n_items, bool capturing) {
 
 // Per-tile counts, scanned starts and ranges. The counts must be zero at the
 // start of every forward; a fresh allocation is cleared here.
+// Zero-fills a freshly allocated buffer and waits for it, so that work on any
+// stream (blocking or not) sees the zeros.
+gmr_status zero_new(gmr_ctx* ctx, void* p, size_t bytes, const char* what) {
+  cudaError_t e = cudaMemset(p, 0, bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return GMR_OK;
+}
+
+// The loss partials: partials[0] is the loss kernel's ticket counter, zero
+// between calls.
+gmr_status ensure_loss(gmr_ctx* ctx, int64_t n_elems, bool capturing) {
+  double* before = ctx->ws.loss_part;
+  gmr_status st = grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, gmr::l2_loss_partials_needed(n_elems),
+                               capturing, "loss_part");
+  if (st != GMR_OK || ctx->ws.loss_part == before) return st;
+  return zero_new(ctx, ctx->ws.loss_part, sizeof(double), "loss_part");
+}
+
 gmr_status ensure_tiles(gmr_ctx* ctx, int64_t n, bool capturing) {
   Workspace& w = ctx->ws;
   if (n > w.cap_tiles) {
@@ -144,8 +169,7 @@ gmr_status ensure_tiles(gmr_ctx* ctx, int64_t n, bool capturing) {
     if ((s = realloc_exact(ctx, &w.tile_start, cap, "tile_start")) != GMR_OK) return s;
     if ((s = realloc_exact(ctx, &w.tile_range, cap, "tile_range")) != GMR_OK) return s;
     if ((s = realloc_exact(ctx, &w.long_tiles, cap, "long_tiles")) != GMR_OK) return s;
-    cudaError_t e = cudaMemset(w.tile_count, 0, sizeof(uint32_t) * (size_t)cap);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset(tile_count)");
+    if ((s = zero_new(ctx, w.tile_count, sizeof(uint32_t) * (size_t)cap, "tile_count")) != GMR_OK) return s;
     w.cap_tiles = cap;
   }
   return ensure_scratch(ctx, n, capturing);
@@ -215,7 +239,10 @@ struct StageTimer {
   bool on;
   unsigned flags;
   StageTimer(gmr_ctx* c, int st, cudaStream_t strm, const gmr_config& cfg)
-      : ctx(c), stage(st), s(strm), on((cfg.flags & GMR_FLAG_PROFILE) && c->stage_ev[0] != nullptr), flags(0) {
+      : ctx(c), stage(st), s(strm),
+        on((cfg.flags & GMR_FLAG_PROFILE) && c->stage_ev[0] != nullptr &&
+           (cfg.profile_stages == 0u || ((cfg.profile_stages >> st) & 1u))),
+        flags(0) {
     if (!on) return;
     // under stream capture the records must become event-record nodes of the
     // graph (external events), not capture-internal dependencies
@@ -293,7 +320,8 @@ gmr_status gmr_config_default(gmr_config* cfg) {
   if (!cfg) return GMR_ERR_INVALID_ARG;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->tile = 16;
-  cfg->threads = 256;
+  cfg->threads = 128;
+  cfg->threads_bwd = 128;
   cfg->batch = 256;
   cfg->cov_mode = GMR_COV_AREA;
   cfg->color_mode = GMR_COLOR_PER_FACE;
@@ -377,8 +405,7 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   if ((s = ensure_tiles(ctx, mt, false)) != GMR_OK) return s;
   if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
   if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;
-  int64_t lp = gmr::l2_loss_partials_needed(3 * max_pixels);
-  return grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, lp, false, "loss_part");
+  return ensure_loss(ctx, 3 * max_pixels, false);
 }
 
 gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
@@ -437,37 +464,35 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
     ctx->cams.assign(cams, cams + C);
   }
 
-  // counters: pair total and forward evaluation counts
-  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->n_pairs, 0, sizeof(uint32_t), s));
-  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_fwd, 0, sizeof(unsigned long long), s));
-  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->contribs, 0, sizeof(unsigned long long), s));
-
-  // S1/S2: conversion + projection per (view, face); per-face colour and
-  // opacity; pair count of every tile
-  {
-    StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, w.views, C, cfg.tile,
-                                      cfg.cov_mode, w, s, &ctx->launches));
-  }
-  // S3: tile segments = exclusive scan of the per-tile counts; total pairs
-  {
-    StageTimer t(ctx, GMR_STAGE_SCAN, s, cfg);
-    GMR_CUDA(ctx, gmr::scan_exclusive(w.tile_count, nullptr, n_tiles, w.tile_start, &w.counters->n_pairs,
-                                      w.scan_tmp, s, &ctx->launches));
-  }
-  if ((cfg.flags & GMR_FLAG_SYNC_CHECK) && !capturing) {
+  // S1-S3: conversion + projection per (view, face), per-face colour and
+  // opacity, pair counts and in-tile ranks; tile segments = exclusive scan of
+  // the per-tile counts (which it returns to zero), total pairs. With
+  // SYNC_CHECK, a pair total beyond the pair buffers grows them and runs the
+  // two stages again (the first run's pair scratch was incomplete).
+  for (int attempt = 0;; ++attempt) {
+    // counters: pair total and slots, forward evaluation counts
+    GMR_CUDA(ctx, cudaMemsetAsync(w.counters, 0, gmr::kFwdCountersBytes, s));
+    {
+      StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
+      GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, w.views, C, cfg.tile,
+                                        cfg.cov_mode, w, s, &ctx->launches));
+    }
+    {
+      StageTimer t(ctx, GMR_STAGE_SCAN, s, cfg);
+      GMR_CUDA(ctx, gmr::scan_exclusive(w.tile_count, n_tiles, w.tile_start, &w.counters->n_pairs,
+                                        w.scan_tmp, s, &ctx->launches));
+    }
+    if (!(cfg.flags & GMR_FLAG_SYNC_CHECK) || capturing) break;
     GMR_CUDA(ctx, cudaMemcpyAsync(&ctx->counters_pinned->n_pairs, &w.counters->n_pairs, sizeof(uint32_t),
                                   cudaMemcpyDeviceToHost, s));
     GMR_CUDA(ctx, cudaStreamSynchronize(s));
-    int64_t P = ctx->counters_pinned->n_pairs;
-    if ((st = ensure_pairs(ctx, P, false)) != GMR_OK) {
-      // the per-tile counts must be zero for the next forward
-      cudaMemsetAsync(w.tile_count, 0, sizeof(uint32_t) * (size_t)n_tiles, s);
-      return st;
-    }
+    const int64_t P = ctx->counters_pinned->n_pairs;
+    if (P <= w.cap_pairs) break;
+    if (attempt > 0) return fail(ctx, GMR_ERR_STATE, "pair total changed between two identical projections");
+    if ((st = ensure_pairs(ctx, P, false)) != GMR_OK) return st;
   }
-  // S4-S6: keys into tile segments, per-tile radix sort by (depth, face),
-  // ranges (the tile counts return to zero)
+  // S4-S6: keys to segment start + rank, per-tile sort by (depth, face),
+  // ranges
   {
     StageTimer t(ctx, GMR_STAGE_BIN, s, cfg);
     GMR_CUDA(ctx, gmr::launch_bin_pairs(w, n_rec, F, w.views, n_tiles, s, &ctx->launches));
@@ -509,7 +534,7 @@ gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dvert
   // S8: compositing backward
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face, w.views, C, F,
+    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, w, w.pair_face, w.views, C, F,
                                          ctx->n_tiles, cfg.bg, dL_dimages, s, &ctx->launches));
   }
   // S9: projection + conversion backward, vertex scatter
@@ -530,8 +555,7 @@ gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int6
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
   GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
-  gmr_status st = grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, std::max<int64_t>(1, gmr::l2_loss_partials_needed(n)),
-                               cap_status != cudaStreamCaptureStatusNone, "loss_part");
+  gmr_status st = ensure_loss(ctx, n, cap_status != cudaStreamCaptureStatusNone);
   if (st != GMR_OK) return st;
   StageTimer t(ctx, GMR_STAGE_LOSS, s, ctx->cfg);
   GMR_CUDA(ctx, gmr::launch_l2_loss(img, target, n, dL_dimg, loss, ctx->ws.loss_part, ctx->ws.cap_loss, s,

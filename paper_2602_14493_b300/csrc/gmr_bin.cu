@@ -2,10 +2,11 @@
 // (the 3DGS binning, Sec. 2.1), as a two-level radix sort:
 //
 //  1. most significant digit = the global tile id: the projection counts the
-//     pairs of every tile (one atomic per (tile, Gaussian) pair), an
-//     exclusive scan of the counts gives each tile's segment, and
-//     k_scatter_keys writes each pair's 64-bit key (depth bits << 32 | face)
-//     into its tile's segment (slot order within a segment is arbitrary);
+//     pairs of every tile and gives each pair its rank among the tile's
+//     pairs (atomics on the tile counters, in whatever order the pairs
+//     arrive); an exclusive scan of the counts gives each tile's segment,
+//     and k_place_keys writes each pair's 64-bit key (depth bits << 32 |
+//     face) to segment start + rank, with no atomics;
 //  2. the remaining digits, (depth bits, face), within each tile: segments
 //     of up to 512 keys (nearly all) are sorted by one warp each, in
 //     registers, with a bitonic network (shuffles only, no CTA barrier);
@@ -15,7 +16,9 @@
 //     shared memory up to kSegSmem keys and through global memory beyond.
 //
 // Keys are unique (face ids are), so the result is the unique (tile, depth,
-// face) order regardless of the slot order of step 1.
+// face) order whatever order step 1 put the keys of a segment in.
+
+#include <algorithm>
 
 #include "gmr_internal.cuh"
 
@@ -28,55 +31,6 @@ constexpr int kSegWarps = kSegThreads / 32;
 constexpr int kSegSmem = 2048;  // keys sorted in shared memory
 constexpr int kRadix = 256;
 
-// One thread per (view, face) record: scatter the record's keys into the
-// segments of the tiles of its rectangle. tile_count is decremented back to
-// zero so that it is ready for the next forward; lanes of a warp that hit the
-// same tile in the same step combine their decrements (one atomic per tile).
-__global__ void k_scatter_keys(const uint32_t* __restrict__ rec_ntiles, const uint2* __restrict__ rec_rect,
-                               const uint32_t* __restrict__ rec_key, const ViewInfo* __restrict__ views,
-                               int64_t n_rec, int32_t F, const uint32_t* __restrict__ tile_start,
-                               uint32_t* __restrict__ tile_count, int64_t cap,
-                               unsigned long long* __restrict__ keys, Counters* __restrict__ counters) {
-  const int64_t rid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const bool live = rid < n_rec;
-  const uint32_t nt = live ? rec_ntiles[rid] : 0u;
-  uint32_t maxnt = nt;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) maxnt = max(maxnt, __shfl_xor_sync(0xffffffffu, maxnt, o));
-  if (maxnt == 0) return;  // warp-uniform
-  const bool fits = (int64_t)counters->n_pairs <= cap;
-  if (!fits && (threadIdx.x | blockIdx.x) == 0) atomicOr(&counters->status, kDevOverflow);
-  int x0 = 0, x1 = -1, y0 = 0, tx = 1;
-  uint32_t base = 0;
-  unsigned long long key = 0ull;
-  if (nt > 0) {
-    const int c = (int)(rid / F);
-    const uint32_t f = (uint32_t)(rid - (int64_t)c * F);
-    const uint2 r = rec_rect[rid];
-    x0 = r.x & 0xffff; x1 = r.x >> 16; y0 = r.y & 0xffff;
-    tx = views[c].tiles_x;
-    base = (uint32_t)views[c].tile_base;
-    key = ((unsigned long long)rec_key[rid] << 32) | f;
-  }
-  const int w = x1 - x0 + 1;
-  const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t k = 0; k < maxnt; ++k) {
-    const bool act = k < nt;
-    uint32_t t = 0xffffffffu - (uint32_t)lane;  // distinct dummies for idle lanes
-    if (act) {
-      const int yy = y0 + (int)(k / (uint32_t)w), xx = x0 + (int)(k % (uint32_t)w);
-      t = base + (uint32_t)(yy * tx + xx);
-    }
-    const uint32_t peers = __match_any_sync(0xffffffffu, t);
-    const int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (act && lane == leader) old = atomicSub(&tile_count[t], (uint32_t)__popc(peers));
-    old = __shfl_sync(0xffffffffu, old, leader);
-    if (act && fits) keys[tile_start[t] + old - 1u - __popc(peers & lt)] = key;
-  }
-}
-
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -84,6 +38,25 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
     if (lane >= o) v += u;
   }
   return v;
+}
+
+constexpr int kPlaceThreads = 256;
+
+// One thread per pair slot of the projection: key to segment start + rank.
+__global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
+    const unsigned long long* __restrict__ pair_tr, const uint32_t* __restrict__ pair_rec,
+    const uint32_t* __restrict__ rec_key, int32_t F, const uint32_t* __restrict__ tile_start, int64_t cap,
+    unsigned long long* __restrict__ keys, const Counters* __restrict__ counters) {
+  const int64_t n = counters->n_pairs;
+  if (n > cap) return;  // overflow: the pair scratch is incomplete
+  for (int64_t i = (int64_t)blockIdx.x * kPlaceThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kPlaceThreads) {
+    const unsigned long long tr = pair_tr[i];
+    const uint32_t rid = pair_rec[i];
+    const uint32_t c = rid / (uint32_t)F;
+    const uint32_t f = rid - c * (uint32_t)F;
+    keys[tile_start[(uint32_t)(tr >> 32)] + (uint32_t)tr] = ((unsigned long long)rec_key[rid] << 32) | f;
+  }
 }
 
 // Exclusive scan of one value per thread over the CTA (kSegThreads threads).
@@ -162,36 +135,52 @@ __device__ void seg_radix_pass(const unsigned long long* src, unsigned long long
 }
 
 // Ascending bitonic sort of 32*KPL 64-bit keys held by one warp, element
-// e = r * 32 + lane in register r of lane `lane`.
+// e = r * 32 + lane in register r of lane `lane`. The stage loops are not
+// unrolled (one body per exchange distance class keeps the code small enough
+// for the instruction cache); the register loops are, so `v` stays in
+// registers.
+template <int KPL>
+__device__ __forceinline__ void cmp_lanes(unsigned long long (&v)[KPL], int k, int j, int lane) {
+  const bool upper = (lane & j) != 0;
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) {
+    const bool asc = (((r << 5) | lane) & k) == 0;
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], j);
+    const bool take_min = asc != upper;
+    const bool lt = v[r] < o;
+    v[r] = (take_min == lt) ? v[r] : o;
+  }
+}
+
+// partner in register r ^ JR of the same lane (j = 32 JR, k >= 64)
+template <int KPL, int JR>
+__device__ __forceinline__ void cmp_regs(unsigned long long (&v)[KPL], int k) {
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) {
+    if (r & JR) continue;
+    const bool asc = ((r << 5) & k) == 0;
+    const unsigned long long a = v[r], b = v[r | JR];
+    const bool sw = asc ? (a > b) : (a < b);
+    v[r] = sw ? b : a;
+    v[r | JR] = sw ? a : b;
+  }
+}
+
 template <int KPL>
 __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[KPL], int lane) {
   constexpr int N = 32 * KPL;
-#pragma unroll
+#pragma unroll 1
   for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {  // partner in another register of the same lane
-        const int jr = j / 32;
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-          if (r & jr) continue;
-          const int e = r * 32 + lane;
-          const bool asc = (e & k) == 0;
-          const unsigned long long a = v[r], b = v[r | jr];
-          const bool sw = asc ? (a > b) : (a < b);
-          v[r] = sw ? b : a;
-          v[r | jr] = sw ? a : b;
-        }
-      } else {  // partner in lane ^ j, same register
-        const bool upper = (lane & j) != 0;
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-          const int e = r * 32 + lane;
-          const bool asc = (e & k) == 0;
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], j);
-          const bool take_min = asc != upper;
-          v[r] = take_min ? (v[r] < o ? v[r] : o) : (v[r] > o ? v[r] : o);
-        }
+      if (j < 32) {
+        cmp_lanes<KPL>(v, k, j, lane);
+      } else {
+        const int jr = j >> 5;
+        if (KPL > 1 && jr == 1) cmp_regs<KPL, 1>(v, k);
+        if (KPL > 2 && jr == 2) cmp_regs<KPL, 2>(v, k);
+        if (KPL > 4 && jr == 4) cmp_regs<KPL, 4>(v, k);
+        if (KPL > 8 && jr == 8) cmp_regs<KPL, 8>(v, k);
       }
     }
   }
@@ -219,18 +208,19 @@ constexpr int kTilesPerCta = kSegThreads / 32;
 
 // One warp per global tile: write the range; sort segments of up to 512 keys
 // in registers; list longer segments for k_long_sort.
-__global__ void __launch_bounds__(kSegThreads) k_tile_sort(const uint32_t* __restrict__ tile_start,
+__global__ void __launch_bounds__(kSegThreads, 2) k_tile_sort(const uint32_t* __restrict__ tile_start,
                                                            int64_t n_tiles, const unsigned long long* __restrict__ keys,
                                                            uint32_t* __restrict__ pair_face,
                                                            uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
                                                            uint32_t* __restrict__ long_count,
-                                                           const Counters* __restrict__ counters, int64_t cap) {
+                                                           Counters* __restrict__ counters, int64_t cap) {
   const int lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
   if (t >= n_tiles) return;
   const uint32_t P = counters->n_pairs;
   if ((int64_t)P > cap) {  // overflow: the keys were not written
     if (lane == 0) ranges[t] = make_uint2(0u, 0u);
+    if (t == 0 && lane == 0) atomicOr(&counters->status, kDevOverflow);
     return;
   }
   const uint32_t start = tile_start[t];
@@ -242,6 +232,8 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(const uint32_t* __res
   uint32_t* out = pair_face + start;
   if (L == 1) {
     if (lane == 0) out[0] = (uint32_t)gk[0];
+  } else if (L <= 32) {
+    warp_sort_segment<1>(gk, L, out, lane);
   } else if (L <= 64) {
     warp_sort_segment<2>(gk, L, out, lane);
   } else if (L <= 128) {
@@ -320,15 +312,14 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int64_t n_tiles,
                              cudaStream_t s, int64_t* launches) {
-  if (n_rec > 0) {
-    k_scatter_keys<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(ws.rec_ntiles, ws.rec_rect, ws.rec_key, views,
-                                                                  n_rec, F, ws.tile_start, ws.tile_count,
-                                                                  ws.cap_pairs, ws.pair_key[0], ws.counters);
+  (void)views;
+  if (n_rec > 0 && ws.cap_pairs > 0) {
+    const int64_t blocks = std::min<int64_t>((ws.cap_pairs + kPlaceThreads - 1) / kPlaceThreads, 148 * 8);
+    k_place_keys<<<(unsigned)blocks, kPlaceThreads, 0, s>>>(ws.pair_key[1], ws.pair_face, ws.rec_key, F,
+                                                          ws.tile_start, ws.cap_pairs, ws.pair_key[0], ws.counters);
     *launches += 1;
   }
   if (n_tiles > 0) {
-    cudaError_t e = cudaMemsetAsync(&ws.counters->n_long, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
     k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kSegThreads, 0, s>>>(
         ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, &ws.counters->n_long,
         ws.counters, ws.cap_pairs);

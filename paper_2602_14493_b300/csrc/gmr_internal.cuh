@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/gmr.h"
+#include "gmr.h"
 
 namespace gmr {
 
@@ -50,14 +50,20 @@ constexpr uint32_t kDevOverflow = GMR_DEV_PAIR_OVERFLOW;
 
 // Device counters block.
 struct Counters {
-  uint32_t n_pairs;      // total pairs of the current forward (scan total)
-  uint32_t status;       // GMR_DEV_* bits
+  // cleared together at the start of every forward (kFwdCountersBytes)
+  uint32_t n_pairs;     // total pairs of the current forward (scan total)
+  uint32_t pair_alloc;  // pair slots handed out by the projection
+  uint32_t n_long;      // tiles whose segment is too long for a warp sort
+  uint32_t pad0;
   unsigned long long evals_fwd;
-  unsigned long long evals_bwd;
   unsigned long long contribs;
-  uint32_t n_long;   // tiles whose segment is too long for a warp sort
-  uint32_t pad;
+  // cleared at the start of every backward
+  unsigned long long evals_bwd;
+  // GMR_DEV_* bits, sticky until gmr_get_device_status reads them
+  uint32_t status;
+  uint32_t pad1;
 };
+constexpr size_t kFwdCountersBytes = offsetof(Counters, evals_bwd);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -170,7 +176,9 @@ struct Workspace {
   uint2* rec_rect = nullptr;     // packed (x0 | x1 << 16, y0 | y1 << 16)
   uint32_t* rec_ntiles = nullptr;
   uint32_t* rec_key = nullptr;   // FP32 depth bits (0xffffffff when culled)
-  float4* rec_grad = nullptr;    // 2 float4 per record: (R0..R3), (R4, 0, 0, 0)
+  // 2 float4 per record: (sum q dx, sum q dy, sum q dx^2, sum q dx dy),
+  // (sum q dy^2, 0, 0, 0) with q = alpha dL/dalpha over the record's pixels
+  float4* rec_grad = nullptr;
   float4* rec_contrib = nullptr; // 4 float4 per record: backward contributions per view
   // faces
   int64_t cap_faces = 0;
@@ -189,8 +197,13 @@ struct Workspace {
   uint32_t* long_tiles = nullptr;  // tiles sorted by the CTA path
   // pairs
   int64_t cap_pairs = 0;
-  unsigned long long* pair_key[2] = {nullptr, nullptr};  // (depth bits << 32 | face)
-  uint32_t* pair_face = nullptr;   // face ids in (tile, depth, face) order
+  // pair_key[0]: (depth bits << 32 | face) per pair in tile segments;
+  // pair_key[1]: scratch of the long-segment sort, and before that, per pair
+  // slot of the projection, (tile << 32 | rank of the pair in its tile)
+  unsigned long long* pair_key[2] = {nullptr, nullptr};
+  // face ids in (tile, depth, face) order; before the sort, per pair slot of
+  // the projection, the pair's record id
+  uint32_t* pair_face = nullptr;
   // scratch for scans
   int64_t cap_scan = 0;
   uint32_t* scan_tmp = nullptr;     // block sums
@@ -207,9 +220,10 @@ struct Workspace {
 // Every launcher returns cudaGetLastError() after enqueueing on stream s and
 // increments *launches by the number of kernels it launched.
 
-// scan.cu / sort.cu
-cudaError_t scan_exclusive(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* out, uint32_t* total,
-                           uint32_t* block_sums, cudaStream_t s, int64_t* launches);
+// gmr_sort.cu: exclusive scan of n u32 values into out, their sum into
+// *total; src is set to zero
+cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* total, uint32_t* block_sums,
+                           cudaStream_t s, int64_t* launches);
 int64_t scan_block_sums_needed(int64_t n);
 // project.cu
 // Conversion + projection of every (view, face) record; also writes the
@@ -242,6 +256,8 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               const float* dL_dimages, cudaStream_t s, int64_t* launches);
+// partials: l2_loss_partials_needed(n) doubles; partials[0] holds a ticket
+// counter that must be zero before the first call (every call leaves it zero)
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
 int64_t l2_loss_partials_needed(int64_t n);

@@ -19,9 +19,10 @@
 // capture that includes this entry point. Each GPU has its own copy, and all
 // calls on one GPU share it: two calls whose work can overlap on the same GPU
 // (for example on two streams without an ordering between them) race on it,
-// so the caller must order them. Every call writes all the partial sums it
-// later reads, so nothing needs clearing between calls and the previous
-// call's leftovers are never used.
+// so the caller must order them. The array's first slot is the loss
+// kernel's completion counter: it starts at zero (static storage) and every
+// call leaves it at zero; every call writes all the partial sums it later
+// reads, so the previous call's leftovers are never used.
 
 #include <mutex>
 
@@ -29,8 +30,9 @@
 
 namespace {
 
-// Partial sums of one call: one double per block of 4096 floats.
-constexpr int64_t kNoAllocPartials = 16384;
+// Completion counter + partial sums of one call (one double per block of
+// 4096 floats).
+constexpr int64_t kNoAllocPartials = 16384 + 1;
 static __device__ __align__(256) double g_l2_partials[kNoAllocPartials];
 
 constexpr int kMaxDevices = 64;

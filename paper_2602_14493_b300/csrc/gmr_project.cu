@@ -223,19 +223,32 @@ __device__ __forceinline__ bool load_face(const int32_t* faces, int f, int V, in
 // ---------------------------------------------------------------- kernels
 
 constexpr int kProjThreads = 128;
+constexpr int kPairUnroll = 4;
 
 // One thread per (face, view): binning spec, depth key, tile rectangle and
 // one count per tile of the rectangle, and the precise record (image mean as
 // a float pair, pre-scaled conic). The view-0 threads also write the face's
 // colour (Eq. 16 in per-vertex mode) and clamped opacity.
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(kProjThreads) k_project(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
     const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode,
     const ViewInfo* __restrict__ views, int tile, float inv_tile, int cov_mode, float4* __restrict__ rec_u,
     float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
+    int64_t cap_pairs, unsigned long long* __restrict__ pair_tr, uint32_t* __restrict__ pair_rec,
     Counters* __restrict__ counters) {
   __shared__ ViewInfo sv;
+  __shared__ uint32_t s_off[kProjThreads / 32][32];
+  __shared__ uint2 s_first[kProjThreads / 32][32];  // (first tile, rectangle width)
   const int c = blockIdx.y;
   if (threadIdx.x == 0) sv = views[c];
   __syncthreads();
@@ -272,21 +285,67 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     nt = (uint32_t)(br.x1 - br.x0 + 1) * (uint32_t)(br.y1 - br.y0 + 1);
     rect = make_uint2((uint32_t)br.x0 | ((uint32_t)br.x1 << 16), (uint32_t)br.y0 | ((uint32_t)br.y1 << 16));
   }
-  // pair counts of the tiles of the rectangle; lanes that hit the same tile
-  // in the same step combine their increments into one atomic
+  // (record, tile) pairs: the warp takes a run of pair slots from a global
+  // counter and deals its records' pairs out evenly over its lanes (pair p to
+  // lane p % 32, its record found by binary search over the exclusive pair
+  // offsets). Each pair's rank within its tile comes from the tile's counter
+  // (lanes that hit the same tile in the same step combine into one atomic;
+  // kPairUnroll steps are issued before their results are used, so that the
+  // round trips overlap); slot, tile, rank and record go to the pair scratch
+  // (slots beyond its capacity are dropped; the binning reports that).
   {
-    const int lane = threadIdx.x & 31;
-    uint32_t maxnt = nt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t incl = warp_incl_scan_u32(nt, lane);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total > 0) {
+      s_off[warp][lane] = incl - nt;
+      s_first[warp][lane] = make_uint2((uint32_t)sv.tile_base + (uint32_t)br.y0 * (uint32_t)sv.tiles_x +
+                                           (uint32_t)br.x0,
+                                       (uint32_t)(br.x1 - br.x0 + 1));
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&counters->pair_alloc, total);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      __syncwarp();
+      const uint32_t tx = (uint32_t)sv.tiles_x;
+      const uint32_t rid0 = rid - (uint32_t)lane;
+      for (uint32_t p0 = 0; p0 < total; p0 += 32 * kPairUnroll) {
+        uint32_t t[kPairUnroll], peers[kPairUnroll], old[kPairUnroll], own[kPairUnroll];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxnt = max(maxnt, __shfl_xor_sync(0xffffffffu, maxnt, o));
-    const int w = br.x1 - br.x0 + 1;
-    const uint32_t base = (uint32_t)sv.tile_base;
-    for (uint32_t k = 0; k < maxnt; ++k) {
-      const bool act = k < nt;
-      uint32_t t = 0xffffffffu - (uint32_t)lane;  // distinct dummies for idle lanes
-      if (act) t = base + (uint32_t)((br.y0 + (int)(k / (uint32_t)w)) * sv.tiles_x + br.x0 + (int)(k % (uint32_t)w));
-      const uint32_t peers = __match_any_sync(0xffffffffu, t);
-      if (act && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
+        for (int u = 0; u < kPairUnroll; ++u) {
+          const uint32_t p = p0 + 32u * u + lane;
+          t[u] = 0xffffffffu - (uint32_t)lane;  // distinct dummies for idle lanes
+          own[u] = 0;
+          if (p < total) {
+            int o = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+              if (s_off[warp][o + st] <= p) o += st;
+            const uint2 fr = s_first[warp][o];
+            const uint32_t k = p - s_off[warp][o];
+            const uint32_t row = k / fr.y;
+            t[u] = fr.x + row * tx + (k - row * fr.y);
+            own[u] = (uint32_t)o;
+          }
+          peers[u] = __match_any_sync(0xffffffffu, t[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kPairUnroll; ++u) {
+          old[u] = 0;
+          if (p0 + 32u * u + lane < total && (peers[u] & lt) == 0)
+            old[u] = atomicAdd(&tile_count[t[u]], (uint32_t)__popc(peers[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < kPairUnroll; ++u) {
+          const uint32_t p = p0 + 32u * u + lane;
+          const uint32_t rank = __shfl_sync(0xffffffffu, old[u], __ffs(peers[u]) - 1) + __popc(peers[u] & lt);
+          const int64_t slot = (int64_t)base + p;
+          if (p < total && slot < cap_pairs) {
+            pair_tr[slot] = ((unsigned long long)t[u] << 32) | rank;
+            pair_rec[slot] = rid0 + own[u];
+          }
+        }
+      }
     }
   }
   if (!live) return;
@@ -318,7 +377,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
 __global__ void __launch_bounds__(128) k_record_bwd(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
     const ViewInfo* __restrict__ views, int cov_mode, const float4* __restrict__ rec_grad,
-    float4* __restrict__ rec_contrib) {
+    const float4* __restrict__ rec_q, float4* __restrict__ rec_contrib) {
   __shared__ ViewInfo sv;
   const int c = blockIdx.y;
   if (threadIdx.x == 0) sv = views[c];
@@ -339,7 +398,12 @@ __global__ void __launch_bounds__(128) k_record_bwd(
   const FaceGeom g = face_geom(a, b, cc, cov_mode);
   const ViewInfo& v = sv;
   const ProjRec p = project_rec(g, v);
-  const float dux = kLn2 * r0.x, duy = kLn2 * r0.y;
+  // p2 = a2 dx^2 + b2 dx dy + c2 dy^2 with dx = pixel - u: the mean gradient
+  // is ln2 (2 a2 sum q dx + b2 sum q dy, b2 sum q dx + 2 c2 sum q dy), taken
+  // with the conic the forward used
+  const float4 cq = rec_q[rid];
+  const float dux = kLn2 * (2.0f * cq.x * r0.x + cq.y * r0.y);
+  const float duy = kLn2 * (cq.y * r0.x + 2.0f * cq.z * r0.y);
   const float dqa = -0.5f * r0.z, dqb = -r0.w, dqc = -0.5f * r4;
   // dL/dSigma' = -Q G_Q Q with G_Q = [[dqa, dqb/2], [dqb/2, dqc]]
   const float g00 = dqa, g01 = 0.5f * dqb, g11 = dqc;
@@ -551,7 +615,8 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
   dim3 grid((F + kProjThreads - 1) / kProjThreads, C);
   k_project<<<grid, kProjThreads, 0, s>>>(verts, V, faces, F, rgb, opacity, color_mode, views, tile,
                                           1.0f / (float)tile, cov_mode, ws.rec_u, ws.rec_q, ws.rec_rect,
-                                          ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.counters);
+                                          ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
+                                          ws.pair_key[1], ws.pair_face, ws.counters);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -562,7 +627,7 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
                                cudaStream_t s, int64_t* launches) {
   if (F <= 0) return cudaSuccess;
   dim3 grid((F + 127) / 128, C);
-  k_record_bwd<<<grid, 128, 0, s>>>(verts, V, faces, F, views, cov_mode, ws.rec_grad, ws.rec_contrib);
+  k_record_bwd<<<grid, 128, 0, s>>>(verts, V, faces, F, views, cov_mode, ws.rec_grad, ws.rec_q, ws.rec_contrib);
   k_face_bwd<<<(F + 255) / 256, 256, 0, s>>>(verts, V, faces, F, C, cov_mode, color_mode, opacity, ws.rec_contrib,
                                              ws.face_grad, dverts, drgb, dop, accumulate);
   *launches += 2;

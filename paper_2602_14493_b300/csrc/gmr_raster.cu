@@ -15,14 +15,18 @@
 //   dL/dc_i     = alpha_i T_i g
 //   dL/dalpha_i = T_i (c_i . g) - (S . g) / (1 - alpha_i)
 // and alpha = o 2^(a2 dx^2 + b2 dx dy + c2 dy^2) gives the mean, conic and
-// opacity terms. A warp reduces its 32 pixels' contributions to one Gaussian
+// opacity terms. With q = alpha dL/dalpha, each record collects the moments
+// (sum q dx, sum q dy, sum q dx^2, sum q dx dy, sum q dy^2) and the face
+// sum q and sum alpha T g; the record backward turns the first two into the
+// mean gradient with the conic. A warp reduces its 32 pixels' contributions to one Gaussian
 // with a transposed butterfly (9 values in 14 shuffles) and eight lanes then
 // issue one atomic add each.
 //
 // Layout: one CTA per screen tile of one view (all views of a batched call in
 // one launch; the tile id selects the view). The tile is cut into 8x4 pixel
-// blocks; each warp owns one or more consecutive blocks (one pixel per lane
-// in each), so a thread composites 1, 2 or 4 pixels. Each batch of listed Gaussians is staged in shared memory
+// blocks; each warp owns a rectangle of 1, 2 or 4 blocks (8x4, 8x8 or 16x8
+// pixels, one pixel per lane in each block), so a thread composites 1, 2 or
+// 4 pixels. Each batch of listed Gaussians is staged in shared memory
 // (float4 loads of the records and face colours), with the image mean made
 // relative to the pixel block's 32-aligned anchor in float-pair arithmetic.
 
@@ -45,18 +49,34 @@ __device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
 }
 
 // Pixel layout of a tile of TS x TS pixels served by NT threads: the tile is
-// cut into 8x4-pixel blocks (row-major, TS/8 per row); warp w owns the PPT
-// consecutive blocks w*PPT ... w*PPT + PPT - 1 and lane l the pixel
-// (l % 8, l / 8) of each of them.
+// cut into 8x4-pixel blocks (row-major, TS/8 per row). Each warp owns a
+// rectangle of PPT blocks, RW blocks wide and PPT/RW high (1 block, 8x8 or
+// 16x8 pixels: the squarest region, so that a Gaussian's footprint meets as
+// few warps as possible), and lane l the pixel (l % 8, l / 8) of each block.
 template <int TS, int NT>
 struct PixMap {
   static constexpr int PPT = TS * TS / NT;  // pixels per thread
   static_assert(PPT >= 1 && PPT * NT == TS * TS, "bad tile / thread split");
-  __device__ __forceinline__ static int block(int k) { return (threadIdx.x >> 5) * PPT + k; }
+  static constexpr int NC = TS / 8;          // blocks per tile row
+  static constexpr int RW = PPT >= 4 ? 2 : 1;  // region width in blocks
+  static constexpr int RH = PPT / RW;          // region height in blocks
+  static_assert(NC % RW == 0 && (TS / 4) % RH == 0, "bad warp region");
+  static constexpr int RX = NC / RW;           // regions per tile row
+  __device__ __forceinline__ static int block_of(int warp, int k) {
+    const int rx = warp % RX, ry = warp / RX;
+    return (ry * RH + k / RW) * NC + rx * RW + k % RW;
+  }
+  __device__ __forceinline__ static int block(int k) { return block_of(threadIdx.x >> 5, k); }
+  __device__ __forceinline__ static uint32_t warp_bits() {
+    uint32_t b = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) b |= 1u << block(k);
+    return b;
+  }
   __device__ __forceinline__ static void local(int k, int& lx, int& ly) {
     int lane = threadIdx.x & 31, b = block(k);
-    lx = (b % (TS / 8)) * 8 + (lane & 7);
-    ly = (b / (TS / 8)) * 4 + (lane >> 3);
+    lx = (b % NC) * 8 + (lane & 7);
+    ly = (b / NC) * 4 + (lane >> 3);
   }
 };
 
@@ -73,12 +93,11 @@ struct Stage {
 };
 
 // Each warp compacts, in order, the batch entries whose mask reaches one of
-// its PPT blocks (bits warp*PPT ... warp*PPT + PPT - 1) and whose list
-// position is below `limit`. Returns the count (warp-uniform).
-template <int BATCH, int NW, int PPT>
-__device__ __forceinline__ int warp_list(Stage<BATCH, NW>& st, int count, int first_pos, int limit) {
+// its blocks (`bits`) and whose list position is below `limit`. Returns the
+// count (warp-uniform).
+template <int BATCH, int NW>
+__device__ __forceinline__ int warp_list(Stage<BATCH, NW>& st, int count, int first_pos, int limit, uint32_t bits) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t bits = ((1u << PPT) - 1u) << (warp * PPT);
   const uint32_t lt = (1u << lane) - 1u;
   int n = 0;
   for (int c = 0; c < count; c += 32) {
@@ -151,17 +170,18 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uin
 }
 
 // ---------------------------------------------------------------- forward
-// Resident warps per SM the compiler must allow (register cap); 0 = none.
-#ifndef GMR_FWD_MIN_WARPS
-#define GMR_FWD_MIN_WARPS 0
-#endif
-#ifndef GMR_BWD_MIN_WARPS
-#define GMR_BWD_MIN_WARPS 0
-#endif
+// Resident CTAs per SM that the register allocation must allow, per launch
+// shape (0: the compiler's choice). Measured on the 8 x 512^2 ring workload:
+// one pixel per thread runs best at 40 resident warps (<= 51 registers);
+// the other shapes and the backward run best uncapped.
+template <int TS, int NT>
+struct FwdMinBlocks {
+  static constexpr int value = (TS == 16 && NT == 256) ? 5 : 0;
+};
 
 // DBG: also record per-pixel contributor counts and order hashes (tests).
 template <int TS, int NT, int BATCH, bool DBG>
-__global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_raster_fwd(
+__global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(NT, (GMR_FWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
                            DBG);
     __syncthreads();
-    const int nl = warp_list<BATCH, NW, PPT>(st, cnt, 0, cnt);
+    const int nl = warp_list<BATCH, NW>(st, cnt, 0, cnt, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
     for (int jj = 0; jj < nl; ++jj) {
       bool wd = true;
@@ -310,7 +330,7 @@ __device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int l
 }
 
 template <int TS, int NT, int BATCH>
-__global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_raster_bwd(
+__global__ void __launch_bounds__(NT) k_raster_bwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
@@ -337,7 +357,8 @@ __global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_
   const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
   const int lane = threadIdx.x & 31;
 
-  float pcx[PPT], pcy[PPT], T[PPT], S0[PPT], S1[PPT], S2[PPT], G0[PPT], G1[PPT], G2[PPT];
+  // SG = (colour composited behind the current Gaussian, plus T_final bg) . g
+  float pcx[PPT], pcy[PPT], T[PPT], SG[PPT], G0[PPT], G1[PPT], G2[PPT];
   uint32_t last[PPT];
   int blk[PPT];
   uint32_t tmax = 0;
@@ -361,9 +382,7 @@ __global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_
       last[k] = 0;
       G0[k] = G1[k] = G2[k] = 0.0f;
     }
-    S0[k] = T[k] * bg0;
-    S1[k] = T[k] * bg1;
-    S2[k] = T[k] * bg2;
+    SG[k] = T[k] * (bg0 * G0[k] + bg1 * G1[k] + bg2 * G2[k]);
     tmax = max(tmax, last[k]);
     blk[k] = PixMap<TS, NT>::block(k);
   }
@@ -385,7 +404,7 @@ __global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + start, end - start, rec_base, rec_u, rec_q, face_col, ax, ay,
                            tox, toy, true);
     __syncthreads();
-    const int nl = warp_list<BATCH, NW, PPT>(st, end - start, start, (int)wmax);
+    const int nl = warp_list<BATCH, NW>(st, end - start, start, (int)wmax, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
     for (int jj = nl - 1; jj >= 0; --jj) {
       const int j = st.list[warp][jj];
@@ -405,7 +424,6 @@ __global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (any) {
         const float4 col = st.col[j];
-        const float a2x2 = 2.0f * gg.z, c2x2 = 2.0f * hh.x;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (!con[k]) continue;
@@ -416,16 +434,13 @@ __global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_
           float Tb = T[k] * inv;
           float w = alpha * Tb;
           float cg = col.x * G0[k] + col.y * G1[k] + col.z * G2[k];
-          float sg = S0[k] * G0[k] + S1[k] * G1[k] + S2[k] * G2[k];
-          float dalpha = Tb * cg - sg * inv;
-          S0[k] += col.x * w;
-          S1[k] += col.y * w;
-          S2[k] += col.z * w;
+          float dalpha = Tb * cg - SG[k] * inv;
+          SG[k] += w * cg;
           T[k] = Tb;
           float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
           float qx = dq * dxs[k], qy = dq * dys[k];
-          acc[0] += a2x2 * qx + gg.w * qy;
-          acc[1] += gg.w * qx + c2x2 * qy;
+          acc[0] += qx;
+          acc[1] += qy;
           acc[2] += qx * dxs[k];
           acc[3] += qx * dys[k];
           acc[4] += qy * dys[k];
@@ -457,50 +472,83 @@ __global__ void __launch_bounds__(NT, (GMR_BWD_MIN_WARPS * 32 + NT - 1) / NT) k_
 }
 
 // ---------------------------------------------------------------- loss
+// L = sum (img - target)^2 and dL/dimg = 2 (img - target) in one launch: each
+// block writes the FP64 sum of its 4096 elements to partials[1 + block], and
+// the block that finishes last (a ticket counter in partials[0]) adds the
+// partials in index order, so the result does not depend on which block
+// that is, then returns the counter to zero for the next call.
 constexpr int kLossThreads = 256;
-constexpr int kLossItems = 16;
+constexpr int kLossItems = 16;  // floats per thread
+constexpr int kLossBlockElems = kLossThreads * kLossItems;
 
-__global__ void __launch_bounds__(kLossThreads) k_l2_partial(const float* __restrict__ img,
-                                                              const float* __restrict__ tgt, int64_t n,
-                                                              float* __restrict__ grad, double* __restrict__ part) {
+__device__ __forceinline__ double block_sum_f64(double v, double* sw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kLossThreads / 32; ++w) s += sw[w];
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restrict__ img,
+                                                           const float* __restrict__ tgt, int64_t n,
+                                                           float* __restrict__ grad, double* __restrict__ part,
+                                                           double* __restrict__ loss, bool vec4) {
   __shared__ double sw[kLossThreads / 32];
-  int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
+  __shared__ bool s_last;
+  const int64_t base = (int64_t)blockIdx.x * kLossBlockElems;
   // FP32 within a thread (16 terms), FP64 across threads: FP64 arithmetic is
   // a slow pipe on this GPU, so it is kept off the per-element path.
   float accf = 0.0f;
+  if (vec4 && base + kLossBlockElems <= n) {
+    const float4* i4 = reinterpret_cast<const float4*>(img + base);
+    const float4* t4 = reinterpret_cast<const float4*>(tgt + base);
+    float4* g4 = reinterpret_cast<float4*>(grad + base);
+    float4 x[kLossItems / 4], y[kLossItems / 4];
+#pragma unroll
+    for (int k = 0; k < kLossItems / 4; ++k) {
+      x[k] = __ldcs(i4 + k * kLossThreads + threadIdx.x);
+      y[k] = __ldcs(t4 + k * kLossThreads + threadIdx.x);
+    }
+#pragma unroll
+    for (int k = 0; k < kLossItems / 4; ++k) {
+      const float4 d = make_float4(x[k].x - y[k].x, x[k].y - y[k].y, x[k].z - y[k].z, x[k].w - y[k].w);
+      g4[k * kLossThreads + threadIdx.x] = make_float4(2.0f * d.x, 2.0f * d.y, 2.0f * d.z, 2.0f * d.w);
+      accf = fmaf(d.x, d.x, accf);
+      accf = fmaf(d.y, d.y, accf);
+      accf = fmaf(d.z, d.z, accf);
+      accf = fmaf(d.w, d.w, accf);
+    }
+  } else {
 #pragma unroll 4
-  for (int k = 0; k < kLossItems; ++k) {
-    int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
-    if (i < n) {
-      float d = img[i] - tgt[i];
-      grad[i] = 2.0f * d;
-      accf = fmaf(d, d, accf);
+    for (int k = 0; k < kLossItems; ++k) {
+      const int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
+      if (i < n) {
+        const float d = img[i] - tgt[i];
+        grad[i] = 2.0f * d;
+        accf = fmaf(d, d, accf);
+      }
     }
   }
-  double acc = (double)accf;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
-  __syncthreads();
+  const double bs = block_sum_f64((double)accf, sw);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kLossThreads / 32; ++w) s += sw[w];
-    part[blockIdx.x] = s;
+    part[1 + blockIdx.x] = bs;
+    __threadfence();
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(part);
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
-}
-
-__global__ void k_l2_final(const double* __restrict__ part, int64_t nb, double* __restrict__ loss) {
-  __shared__ double sw[32];
-  double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
   __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += kLossThreads) acc += __ldcg(part + 1 + i);
+  __syncthreads();
+  const double tot = block_sum_f64(acc, sw);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sw[w];
-    *loss = s;
+    *loss = tot;
+    *reinterpret_cast<unsigned int*>(part) = 0u;
   }
 }
 
@@ -588,17 +636,16 @@ cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* re
   return cudaGetLastError();
 }
 
-int64_t l2_loss_partials_needed(int64_t n) { return (n + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems); }
+int64_t l2_loss_partials_needed(int64_t n) { return 1 + (n + kLossBlockElems - 1) / kLossBlockElems; }
 
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches) {
-  int64_t nb = l2_loss_partials_needed(n);
-  if (nb > n_partials) return cudaErrorInvalidValue;
-  if (nb > 0) {
-    k_l2_partial<<<(unsigned)nb, kLossThreads, 0, s>>>(img, target, n, grad, partials);
-    *launches += 1;
-  }
-  k_l2_final<<<1, 1024, 0, s>>>(partials, nb, loss);
+  const int64_t nb = l2_loss_partials_needed(n) - 1;
+  if (nb + 1 > n_partials) return cudaErrorInvalidValue;
+  if (nb == 0) return cudaMemsetAsync(loss, 0, sizeof(double), s);
+  const bool vec4 = ((reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(target) |
+                      reinterpret_cast<uintptr_t>(grad)) & 15u) == 0;
+  k_l2_loss<<<(unsigned)nb, kLossThreads, 0, s>>>(img, target, n, grad, partials, loss, vec4);
   *launches += 1;
   return cudaGetLastError();
 }

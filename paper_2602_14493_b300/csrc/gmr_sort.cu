@@ -1,6 +1,9 @@
-// Device-wide exclusive scan of u32 values (reduce-then-scan: no block waits
-// on another). Turns the per-tile pair counts into the tile segments of the
-// binning and gives the total pair count.
+// Device-wide exclusive scan of u32 values. Turns the per-tile pair counts
+// into the tile segments of the binning and gives the total pair count; the
+// counts are consumed (set back to zero, ready for the next forward).
+// Up to kSingleMax values: one CTA walks the array in chunks of 8192 with a
+// running carry (one launch); beyond, reduce-then-scan over many CTAs (three
+// launches, no block waits on another).
 
 #include "gmr_internal.cuh"
 
@@ -43,12 +46,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem_w
   return r;
 }
 
-__device__ __forceinline__ uint32_t load_item(const uint32_t* src, const uint32_t* idx, int64_t i) {
-  return idx ? src[idx[i]] : src[i];
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ src,
-                                                              const uint32_t* __restrict__ idx, int64_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ src, int64_t n,
                                                               uint32_t* __restrict__ block_sums) {
   __shared__ uint32_t sw[33];
   int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -56,7 +54,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-    if (i < n) acc += load_item(src, idx, i);
+    if (i < n) acc += src[i];
   }
   uint32_t tot;
   block_excl_scan(acc, sw, &tot);
@@ -79,8 +77,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ sums, 
   if (threadIdx.x == 0 && total) *total = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ src,
-                                                            const uint32_t* __restrict__ idx, int64_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ src, int64_t n,
                                                             const uint32_t* __restrict__ block_sums,
                                                             uint32_t* __restrict__ out) {
   __shared__ uint32_t sw[33];
@@ -91,7 +88,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
   for (int k = 0; k < kScanItems; ++k) {
     int j = k * kScanThreads + threadIdx.x;
     int64_t i = base + j;
-    tile[j] = i < n ? load_item(src, idx, i) : 0u;
+    tile[j] = i < n ? src[i] : 0u;
+    if (i < n) src[i] = 0u;
   }
   __syncthreads();
   uint32_t v[kScanItems];
@@ -117,20 +115,73 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
   }
 }
 
+constexpr int kSingleThreads = 1024;
+constexpr int kSingleChunk = kSingleThreads * kScanItems;  // 8192
+constexpr int64_t kSingleMax = 4 * kSingleChunk;
+
+__global__ void __launch_bounds__(kSingleThreads) k_scan_single(uint32_t* __restrict__ src, int64_t n,
+                                                                uint32_t* __restrict__ out,
+                                                                uint32_t* __restrict__ total) {
+  __shared__ uint32_t sw[33];
+  __shared__ uint32_t tile[kSingleChunk];
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n; base += kSingleChunk) {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int j = k * kSingleThreads + threadIdx.x;
+      if (base + j < n) {
+        tile[j] = src[base + j];
+        src[base + j] = 0u;
+      } else {
+        tile[j] = 0u;
+      }
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = tile[threadIdx.x * kScanItems + k];
+      acc += v[k];
+    }
+    uint32_t tot;
+    uint32_t pre = block_excl_scan(acc, sw, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      tile[threadIdx.x * kScanItems + k] = pre;
+      pre += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int j = k * kSingleThreads + threadIdx.x;
+      if (base + j < n) out[base + j] = tile[j];
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
 }  // namespace
 
 int64_t scan_block_sums_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-cudaError_t scan_exclusive(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* out, uint32_t* total,
-                           uint32_t* block_sums, cudaStream_t s, int64_t* launches) {
+cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* total, uint32_t* block_sums,
+                           cudaStream_t s, int64_t* launches) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
     return cudaGetLastError();
   }
+  if (n <= kSingleMax) {
+    k_scan_single<<<1, kSingleThreads, 0, s>>>(src, n, out, total);
+    *launches += 1;
+    return cudaGetLastError();
+  }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(src, idx, n, block_sums);
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums);
   k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, total);
-  k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(src, idx, n, block_sums, out);
+  k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums, out);
   *launches += 3;
   return cudaGetLastError();
 }

@@ -56,19 +56,33 @@ def pixel_offsets(cams) -> np.ndarray:
     return np.array(off, dtype=np.int64)
 
 
+def _stage_mask(profile):
+    """profile: False / True (every stage) / stage names to time."""
+    if isinstance(profile, (bool, int)) or profile is None:
+        return 0
+    return sum(1 << _lib.STAGES.index(name) for name in profile)
+
+
+def _default_threads(tile):
+    return 256 if tile == 32 else 128
+
+
 class Renderer:
     """One library context on the current CUDA device.
 
-    tile: 16 or 32; threads: threads per tile (64/128/256 for 16x16 tiles,
-    256 for 32x32); batch: Gaussians per shared-memory batch (64/128/256);
+    tile: 16 or 32; threads / threads_bwd: threads per tile in the forward /
+    backward (64/128/256 for 16x16 tiles, 256 for 32x32; None: 128 for 16x16
+    tiles, 256 for 32x32); batch: Gaussians per shared-memory batch (64/128/256);
     cov_mode: "area" (Eq. 13) or "embed_raw" (Eq. 15 literally);
     color_mode: "face" (F x 3 colours) or "vertex" (V x 3, Eq. 16);
     sync_check: read the pair count back once per forward and grow buffers
     (False: never synchronise; pre-size with ``reserve`` for graph capture).
+    profile: time the stages with CUDA events (True: all of them; or a list
+    of stage names from ``STAGES``).
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
-                 sync_check=True, profile=False, threads=256, debug_counts=False):
+                 sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -76,13 +90,15 @@ class Renderer:
         self.cfg = _lib.GmrConfig()
         self._L.gmr_config_default(ctypes.byref(self.cfg))
         self.cfg.tile = tile
-        self.cfg.threads = threads
+        self.cfg.threads = threads or _default_threads(tile)
+        self.cfg.threads_bwd = threads_bwd or _default_threads(tile)
         self.cfg.batch = batch
         self.cfg.cov_mode = _COV[cov_mode]
         self.cfg.color_mode = _COLOR[color_mode]
         self.cfg.bg[:] = [float(x) for x in bg]
         self.cfg.flags = ((_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
                           | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0))
+        self.cfg.profile_stages = _stage_mask(profile)
         self.color_mode = color_mode
         self._ctx = ctypes.c_void_p()
         self._check(self._L.gmr_create(ctypes.byref(self.cfg), ctypes.byref(self._ctx)), "gmr_create")
@@ -109,6 +125,11 @@ class Renderer:
             pass
 
     def set_config(self, **kw):
+        """Changes configuration fields; a new tile size without thread
+        counts takes that size's default thread counts."""
+        if "tile" in kw:
+            kw.setdefault("threads", _default_threads(kw["tile"]))
+            kw.setdefault("threads_bwd", _default_threads(kw["tile"]))
         for k, v in kw.items():
             if k == "cov_mode":
                 v = _COV[v]
@@ -123,6 +144,7 @@ class Renderer:
                 continue
             if k == "profile":
                 self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_PROFILE) | (_lib.GMR_FLAG_PROFILE if v else 0)
+                self.cfg.profile_stages = _stage_mask(v)
                 continue
             setattr(self.cfg, k, v)
         self._check(self._L.gmr_set_config(self._ctx, ctypes.byref(self.cfg)), "gmr_set_config")

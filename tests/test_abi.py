@@ -35,7 +35,7 @@ def test_struct_layouts_match_header():
     from paper_2602_14493_b300 import _lib
 
     assert ctypes.sizeof(_lib.GmrCamera) == 76 == gi.CAMERA_DTYPE.itemsize
-    assert ctypes.sizeof(_lib.GmrConfig) == 36
+    assert ctypes.sizeof(_lib.GmrConfig) == 44
     assert ctypes.sizeof(_lib.GmrStats) == 72
     cam = gi.look_at((0.0, -3.0, 1.0), 32, 16)
     arr = np.array([cam], dtype=gi.CAMERA_DTYPE)
@@ -54,7 +54,8 @@ def test_host_only_entry_points_without_gpu():
     L = _lib.load()
     cfg = _lib.GmrConfig()
     assert L.gmr_config_default(ctypes.byref(cfg)) == 0
-    assert (cfg.tile, cfg.threads, cfg.batch, cfg.cov_mode, cfg.color_mode, cfg.flags) == (16, 256, 256, 0, 0, 1)
+    assert (cfg.tile, cfg.threads, cfg.threads_bwd, cfg.batch, cfg.cov_mode, cfg.color_mode, cfg.flags) == (
+        16, 128, 128, 256, 0, 0, 1)
     assert L.gmr_status_string(4) == b"GMR_ERR_CAPACITY"
     cams = (_lib.GmrCamera * 3)()
     for i, (w, h) in enumerate([(10, 7), (3, 3), (256, 1)]):

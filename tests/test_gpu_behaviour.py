@@ -44,6 +44,25 @@ def test_image_invariant_to_tile_and_batch_size():
             r.close()
 
 
+def test_gradients_invariant_to_backward_shape():
+    """The backward's launch shape changes only the order of the float
+    atomics, so gradients agree to rounding across all shapes."""
+    s = _uneven()
+    ref = None
+    for tile, threads_bwd in ((16, 256), (16, 128), (16, 64), (32, 256)):
+        for batch in (64, 256):
+            r = _renderer(tile=tile, batch=batch, threads=256, threads_bwd=threads_bwd)
+            _, img, T = render_gpu(r, s)
+            g = torch.sin(torch.arange(img.numel(), device=DEV, dtype=torch.float32)).reshape(img.shape)
+            got = [x.cpu().numpy().copy() for x in r.backward(g.contiguous())]
+            if ref is None:
+                ref = got
+            else:
+                for a, b in zip(got, ref):
+                    assert rel_l2(a, b) < 1e-5
+            r.close()
+
+
 def test_batched_equals_per_view():
     s = _uneven()
     r = _renderer()
