@@ -267,6 +267,8 @@ def run_gmr(args, ws, rank, local):
     dv, dc, do = torch.empty_like(v), torch.empty_like(c), torch.empty_like(o)
 
     def step(s):
+        # forward, squared-error loss, backward (the loss fused into the
+        # forward's epilogue, gmr_render_fwd_l2, measured slower here)
         r.forward(v, f, c, o, cams, images=img, want_t=False, stream=s)
         r.l2_loss(img, target, grad, loss, stream=s)
         r.backward(grad, dv, dc, do, stream=s)

@@ -29,7 +29,8 @@ STAGES = ["project", "scan", "bin", "raster_fwd", "loss", "raster_bwd", "project
 # Every function the header declares (checked by the CPU test suite).
 EXPORTS = [
     "gmr_config_default", "gmr_create", "gmr_destroy", "gmr_set_config", "gmr_last_error", "gmr_status_string",
-    "gmr_image_offsets", "gmr_reserve", "gmr_convert", "gmr_render_fwd", "gmr_render_bwd", "gmr_l2_loss",
+    "gmr_image_offsets", "gmr_reserve", "gmr_convert", "gmr_render_fwd", "gmr_render_fwd_l2", "gmr_render_bwd",
+    "gmr_l2_loss",
     "gmr_get_device_status", "gmr_get_stats", "gmr_get_stage_times", "gmr_debug_forward_state",
     "gmr_l2_loss_noalloc",
 ]
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
         "gmr_reserve": (st, [P, i64, i32, i64, i64]),
         "gmr_convert": (st, [P, P, i32, P, i32, P, P, P, P, P, P, P]),
         "gmr_render_fwd": (st, [P, P, i32, P, i32, P, P, P, i32, P, P, P]),
+        "gmr_render_fwd_l2": (st, [P, P, i32, P, i32, P, P, P, i32, P, P, P, P, P, P]),
         "gmr_render_bwd": (st, [P, P, P, P, P, i32, P]),
         "gmr_l2_loss": (st, [P, P, P, i64, P, P, P]),
         "gmr_l2_loss_noalloc": (st, [P, P, i64, P, P, P]),

@@ -149,12 +149,11 @@ gmr_status zero_new(gmr_ctx* ctx, void* p, size_t bytes, const char* what) {
   return GMR_OK;
 }
 
-// The loss partials: partials[0] is the loss kernel's ticket counter, zero
-// between calls.
-gmr_status ensure_loss(gmr_ctx* ctx, int64_t n_elems, bool capturing) {
+// The loss partials (`slots` doubles): slot 0 is the loss kernels' ticket
+// counter, zero between calls.
+gmr_status ensure_loss(gmr_ctx* ctx, int64_t slots, bool capturing) {
   double* before = ctx->ws.loss_part;
-  gmr_status st = grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, gmr::l2_loss_partials_needed(n_elems),
-                               capturing, "loss_part");
+  gmr_status st = grow<double>(ctx, &ctx->ws.loss_part, &ctx->ws.cap_loss, slots, capturing, "loss_part");
   if (st != GMR_OK || ctx->ws.loss_part == before) return st;
   return zero_new(ctx, ctx->ws.loss_part, sizeof(double), "loss_part");
 }
@@ -405,7 +404,7 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   if ((s = ensure_tiles(ctx, mt, false)) != GMR_OK) return s;
   if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
   if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;
-  return ensure_loss(ctx, 3 * max_pixels, false);
+  return ensure_loss(ctx, std::max<int64_t>(gmr::l2_loss_partials_needed(3 * max_pixels), 1 + mt * 4), false);
 }
 
 gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
@@ -421,9 +420,11 @@ gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_
   return GMR_OK;
 }
 
-gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
-                          const float* rgb, const float* opacity, const gmr_camera* cams, int32_t C, float* images,
-                          float* t_final, gmr_stream stream) {
+namespace {
+
+gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
+                      const float* opacity, const gmr_camera* cams, int32_t C, float* images, float* t_final,
+                      gmr::FwdLoss fl, gmr_stream stream) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   ctx->fwd_valid = false;
   if (V < 0 || F < 0) return fail(ctx, GMR_ERR_INVALID_ARG, "negative size");
@@ -455,6 +456,12 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   if ((st = ensure_faces(ctx, F, capturing)) != GMR_OK) return st;
   if ((st = ensure_pixels(ctx, n_pixels, capturing)) != GMR_OK) return st;
   if ((st = ensure_tiles(ctx, n_tiles, capturing)) != GMR_OK) return st;
+  if (fl.target) {
+    // one float per forward warp after slot 0 (gmr_l2_loss's ticket counter)
+    const int64_t n_warp_sums = n_tiles * (ctx->cfg.threads / 32);
+    if ((st = ensure_loss(ctx, 1 + (n_warp_sums + 1) / 2, capturing)) != GMR_OK) return st;
+    fl.part = reinterpret_cast<float*>(w.loss_part + 1);
+  }
 
   if (!cams_same) {
     GMR_CUDA(ctx, cudaEventSynchronize(ctx->upload_done));
@@ -502,7 +509,7 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
     uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
     GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face, w.views, C, F, n_tiles,
-                                         cfg.bg, images, t_final, nc, s, &ctx->launches));
+                                         cfg.bg, images, t_final, nc, fl, s, &ctx->launches));
   }
 
   ctx->fwd_valid = true;
@@ -511,6 +518,27 @@ gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int
   ctx->n_tiles = n_tiles; ctx->n_pixels = n_pixels;
   ctx->fwd_cfg = cfg;
   return GMR_OK;
+}
+
+}  // namespace
+
+gmr_status gmr_render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                          const float* rgb, const float* opacity, const gmr_camera* cams, int32_t C, float* images,
+                          float* t_final, gmr_stream stream) {
+  return render_fwd(ctx, verts, V, faces, F, rgb, opacity, cams, C, images, t_final, gmr::FwdLoss{}, stream);
+}
+
+gmr_status gmr_render_fwd_l2(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                             const float* rgb, const float* opacity, const gmr_camera* cams, int32_t C,
+                             float* images, float* t_final, const float* target, float* dL_dimg, double* loss,
+                             gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (!target || !dL_dimg || !loss) return fail(ctx, GMR_ERR_INVALID_ARG, "null target, dL_dimg or loss");
+  gmr::FwdLoss fl;
+  fl.target = target;
+  fl.grad = dL_dimg;
+  fl.loss = loss;
+  return render_fwd(ctx, verts, V, faces, F, rgb, opacity, cams, C, images, t_final, fl, stream);
 }
 
 gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dverts, float* dL_drgb,
@@ -555,7 +583,7 @@ gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int6
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
   GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
-  gmr_status st = ensure_loss(ctx, n, cap_status != cudaStreamCaptureStatusNone);
+  gmr_status st = ensure_loss(ctx, gmr::l2_loss_partials_needed(n), cap_status != cudaStreamCaptureStatusNone);
   if (st != GMR_OK) return st;
   StageTimer t(ctx, GMR_STAGE_LOSS, s, ctx->cfg);
   GMR_CUDA(ctx, gmr::launch_l2_loss(img, target, n, dL_dimg, loss, ctx->ws.loss_part, ctx->ws.cap_loss, s,

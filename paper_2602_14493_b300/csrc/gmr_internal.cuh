@@ -66,6 +66,44 @@ struct Counters {
 constexpr size_t kFwdCountersBytes = offsetof(Counters, evals_bwd);
 
 // ---------------------------------------------------------------- helpers
+// ---- double-float arithmetic (an unevaluated sum hi + lo of two floats) with
+// the error-free transformations TwoSum (Knuth) and TwoProduct (by FMA); every
+// operation is an explicit rounded intrinsic so that none is contracted or
+// reassociated. Used for the image-plane mean, which must stay accurate to
+// ~1e-6 px at any image size, and for the loss sums, while FP64 is a slow
+// pipe on this GPU.
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df qb = df_mul_f(b, q1);
+  df r = df_add(a, df{-qb.hi, -qb.lo});
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return fast_two_sum(q1, q2);
+}
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -249,10 +287,20 @@ cudaError_t launch_expand_tiles(const uint2* ranges, int64_t n_tiles, uint32_t* 
 // unscaled conic.
 cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* rects, float* conic, cudaStream_t s,
                                  int64_t* launches);
+// Optional squared-error loss fused into the forward's epilogue (target ==
+// nullptr: none): grad = 2 (image - target), *loss = sum (image - target)^2;
+// part holds one FP32 partial sum per warp (n_tiles * threads / 32 floats),
+// added up by a one-block kernel after the compositing.
+struct FwdLoss {
+  const float* target = nullptr;
+  float* grad = nullptr;
+  float* part = nullptr;
+  double* loss = nullptr;
+};
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              float* images, float* t_final_out, uint32_t* ncontrib_out, cudaStream_t s,
-                              int64_t* launches);
+                              float* images, float* t_final_out, uint32_t* ncontrib_out, const FwdLoss& fl,
+                              cudaStream_t s, int64_t* launches);
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               const float* dL_dimages, cudaStream_t s, int64_t* launches);

@@ -45,43 +45,6 @@ __device__ __forceinline__ float3 f3cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-// ---- double-float arithmetic (an unevaluated sum hi + lo of two floats) with
-// the error-free transformations TwoSum (Knuth) and TwoProduct (by FMA); every
-// operation is an explicit rounded intrinsic so that none is contracted or
-// reassociated. Used for the image-plane mean, which must stay accurate to
-// ~1e-6 px at any image size while FP64 is a slow pipe on this GPU.
-struct df {
-  float hi, lo;
-};
-__device__ __forceinline__ df two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
-  float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df two_prod(float a, float b) {
-  float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-  df s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-  df p = two_prod(a.hi, b);
-  return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
-}
-__device__ __forceinline__ df df_div(df a, df b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
-  df qb = df_mul_f(b, q1);
-  df r = df_add(a, df{-qb.hi, -qb.lo});
-  float q2 = __fdiv_rn(r.hi, b.hi);
-  return fast_two_sum(q1, q2);
-}
 // (a + b + c) / 3 of three floats as a double-float.
 __device__ __forceinline__ df df_mean3(float a, float b, float c) {
   df s1 = two_sum(a, b);

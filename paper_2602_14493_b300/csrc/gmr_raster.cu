@@ -179,14 +179,76 @@ struct FwdMinBlocks {
   static constexpr int value = (TS == 16 && NT == 256) ? 5 : 0;
 };
 
-// DBG: also record per-pixel contributor counts and order hashes (tests).
-template <int TS, int NT, int BATCH, bool DBG>
+// Block sum of one FP32 value per thread: a warp tree in FP32, then the
+// warps' sums added in FP64 by thread 0 (FP64 is a slow pipe on this GPU:
+// a full-warp FP64 tree per block costs more than the rest of a loss pass).
+// Relative error at most (5 + depth of the per-thread sums) u, u = 2^-24.
+template <int NT>
+__device__ __forceinline__ double block_sum_f32(float v, float* sw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += (double)sw[w];
+  return s;  // valid in thread 0
+}
+
+// Block sum of one FP64 value per thread (FP64 warp tree).
+template <int NT>
+__device__ __forceinline__ double block_sum_f64(double v, double* sw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += sw[w];
+  return s;  // valid in thread 0
+}
+
+// Block sum of v written to part[1 + blockIdx.x]; the block that finishes
+// last (ticket counter in part[0]) adds the partials in index order into
+// *loss and returns the counter to zero. Called by every thread of every
+// block of the grid.
+template <int NT>
+__device__ __forceinline__ void loss_partial_and_finish(float v, double* __restrict__ part,
+                                                        double* __restrict__ loss) {
+  __shared__ double sw[NT / 32];
+  __shared__ float swf[NT / 32];
+  __shared__ bool s_last;
+  const double bs = block_sum_f32<NT>(v, swf);
+  if (threadIdx.x == 0) {
+    part[1 + blockIdx.x] = bs;
+    __threadfence();
+    s_last = atomicAdd(reinterpret_cast<unsigned int*>(part), 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += NT) acc += __ldcg(part + 1 + i);
+  __syncthreads();
+  const double tot = block_sum_f64<NT>(acc, sw);
+  if (threadIdx.x == 0) {
+    *loss = tot;
+    *reinterpret_cast<unsigned int*>(part) = 0u;
+  }
+}
+
+// MODE: kFwdPlain; kFwdDebug also records per-pixel contributor counts and
+// order hashes (tests); kFwdLoss also computes the squared-error loss
+// against fl.target in the epilogue.
+constexpr int kFwdPlain = 0, kFwdDebug = 1, kFwdLoss = 2;
+
+template <int TS, int NT, int BATCH, int MODE>
 __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
     uint32_t* __restrict__ pix_last, float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
-    int64_t n_pix_total, Counters* __restrict__ counters) {
+    int64_t n_pix_total, FwdLoss fl, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
@@ -204,6 +266,9 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
 
   float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+  // fused loss: each thread's target pixels, copied to shared memory
+  // asynchronously at the start and read in the epilogue
+  __shared__ float s_tgt[MODE == kFwdLoss ? 3 * PPT * NT : 1];
   uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
   int blk[PPT];
   bool done[PPT], inside[PPT];
@@ -225,7 +290,15 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     ncontrib[k] = 0;
     chash[k] = 0;
     blk[k] = PixMap<TS, NT>::block(k);
+    if (MODE == kFwdLoss && inside[k]) {
+      const float* tp = fl.target + 3 * (v.pix_base + (int64_t)py[k] * v.W + px[k]);
+      const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&s_tgt[3 * (k * NT + threadIdx.x)]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + 4u * q), "l"(tp + q) : "memory");
+    }
   }
+  if (MODE == kFwdLoss) asm volatile("cp.async.commit_group;" ::: "memory");
   const uint2 range = ranges[g];
   const int n = (int)(range.y - range.x);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
@@ -237,7 +310,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
     stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
-                           DBG);
+                           MODE == kFwdDebug);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, cnt, 0, cnt, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
@@ -280,23 +353,36 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
         T[k] = test;
         last[k] = (uint32_t)(base + j + 1);
         ++ncontrib[k];
-        if (DBG) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
+        if (MODE == kFwdDebug) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
       }
     }
   }
   unsigned long long evals = 0, ncon = 0;
+  float lsum = 0.0f;  // fused loss: FP32 over this thread's pixels
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     if (!inside[k]) continue;
     ncon += ncontrib[k];
     int64_t pid = v.pix_base + (int64_t)py[k] * v.W + px[k];
-    images[3 * pid] = Cr[k] + T[k] * bg0;
-    images[3 * pid + 1] = Cg[k] + T[k] * bg1;
-    images[3 * pid + 2] = Cb[k] + T[k] * bg2;
+    const float i0 = Cr[k] + T[k] * bg0, i1 = Cg[k] + T[k] * bg1, i2 = Cb[k] + T[k] * bg2;
+    images[3 * pid] = i0;
+    images[3 * pid + 1] = i1;
+    images[3 * pid + 2] = i2;
+    if (MODE == kFwdLoss) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      const float* tg = &s_tgt[3 * (k * NT + threadIdx.x)];
+      const float d0 = i0 - tg[0], d1 = i1 - tg[1], d2 = i2 - tg[2];
+      fl.grad[3 * pid] = 2.0f * d0;
+      fl.grad[3 * pid + 1] = 2.0f * d1;
+      fl.grad[3 * pid + 2] = 2.0f * d2;
+      lsum = fmaf(d0, d0, lsum);
+      lsum = fmaf(d1, d1, lsum);
+      lsum = fmaf(d2, d2, lsum);
+    }
     pix_T[pid] = T[k];
     pix_last[pid] = last[k];
     if (t_out) t_out[pid] = T[k];
-    if (DBG) {
+    if (MODE == kFwdDebug) {
       nc_out[pid] = ncontrib[k];
       nc_out[n_pix_total + pid] = chash[k];
     }
@@ -309,6 +395,43 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   }
   if ((threadIdx.x & 31) == 0 && evals) atomicAdd(&counters->evals_fwd, evals);
   if ((threadIdx.x & 31) == 0 && ncon) atomicAdd(&counters->contribs, ncon);
+  if (MODE == kFwdLoss) {  // one FP32 partial per warp, no block barrier
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
+    if ((threadIdx.x & 31) == 0) fl.part[(int64_t)blockIdx.x * NW + (threadIdx.x >> 5)] = lsum;
+  }
+}
+
+// Sum of n floats into *out, one block, in a fixed order, with double-float
+// accumulation in FP32 arithmetic (error ~n 2^-44 relative, no FP64 pipe).
+__global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__ part, int64_t n,
+                                                       double* __restrict__ out) {
+  __shared__ df sw[32];
+  // rounds of 16 independent loads per thread, then their (fixed-order) sum
+  constexpr int R = 16;
+  df acc{0.0f, 0.0f};
+  for (int64_t i0 = 0; i0 < n; i0 += 1024 * R) {
+    float x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = i0 + (int64_t)r * 1024 + threadIdx.x;
+      x[r] = i < n ? part[i] : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc = df_add(acc, df{x[r], 0.0f});
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    acc = df_add(acc, df{__shfl_xor_sync(kFull, acc.hi, o), __shfl_xor_sync(kFull, acc.lo, o)});
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = sw[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      acc = df_add(acc, df{__shfl_xor_sync(kFull, acc.hi, o), __shfl_xor_sync(kFull, acc.lo, o)});
+    if (threadIdx.x == 0) *out = (double)acc.hi + (double)acc.lo;
+  }
 }
 
 // ---------------------------------------------------------------- backward
@@ -481,26 +604,13 @@ constexpr int kLossThreads = 256;
 constexpr int kLossItems = 16;  // floats per thread
 constexpr int kLossBlockElems = kLossThreads * kLossItems;
 
-__device__ __forceinline__ double block_sum_f64(double v, double* sw) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < kLossThreads / 32; ++w) s += sw[w];
-  return s;  // valid in thread 0
-}
-
 __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restrict__ img,
                                                            const float* __restrict__ tgt, int64_t n,
                                                            float* __restrict__ grad, double* __restrict__ part,
                                                            double* __restrict__ loss, bool vec4) {
-  __shared__ double sw[kLossThreads / 32];
-  __shared__ bool s_last;
   const int64_t base = (int64_t)blockIdx.x * kLossBlockElems;
-  // FP32 within a thread (16 terms), FP64 across threads: FP64 arithmetic is
-  // a slow pipe on this GPU, so it is kept off the per-element path.
+  // FP32 within a thread (16 terms) and a warp, FP64 across warps and
+  // blocks: FP64 arithmetic is a slow pipe on this GPU.
   float accf = 0.0f;
   if (vec4 && base + kLossBlockElems <= n) {
     const float4* i4 = reinterpret_cast<const float4*>(img + base);
@@ -532,24 +642,7 @@ __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restric
       }
     }
   }
-  const double bs = block_sum_f64((double)accf, sw);
-  if (threadIdx.x == 0) {
-    part[1 + blockIdx.x] = bs;
-    __threadfence();
-    unsigned int* ticket = reinterpret_cast<unsigned int*>(part);
-    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double acc = 0.0;
-  for (unsigned i = threadIdx.x; i < gridDim.x; i += kLossThreads) acc += __ldcg(part + 1 + i);
-  __syncthreads();
-  const double tot = block_sum_f64(acc, sw);
-  if (threadIdx.x == 0) {
-    *loss = tot;
-    *reinterpret_cast<unsigned int*>(part) = 0u;
-  }
+  loss_partial_and_finish<kLossThreads>(accf, part, loss);
 }
 
 __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_q, int64_t n_rec,
@@ -574,12 +667,16 @@ __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4
 
 template <int TS, int NT, int BATCH>
 void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, float* images, float* t_out, uint32_t* nc_out, cudaStream_t s) {
-  auto kern = nc_out ? k_raster_fwd<TS, NT, BATCH, true> : k_raster_fwd<TS, NT, BATCH, false>;
+                int32_t F, const float* bg, float* images, float* t_out, uint32_t* nc_out, const FwdLoss& fl,
+                cudaStream_t s) {
+  auto kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss>
+              : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug>
+                        : k_raster_fwd<TS, NT, BATCH, kFwdPlain>;
   kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
                                                                  images, ws.pix_T, ws.pix_last, t_out, nc_out,
-                                                                 ws.cap_pixels, ws.counters);
+                                                                 ws.cap_pixels, fl, ws.counters);
+  if (fl.target) k_sum_partials<<<1, 1024, 0, s>>>(fl.part, n_tiles * (NT / 32), fl.loss);
 }
 
 template <int TS, int NT, int BATCH>
@@ -595,12 +692,13 @@ void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
 
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              float* images, float* t_final_out, uint32_t* ncontrib_out, cudaStream_t s,
-                              int64_t* launches) {
-  if (n_tiles <= 0) return cudaSuccess;
+                              float* images, float* t_final_out, uint32_t* ncontrib_out, const FwdLoss& fl,
+                              cudaStream_t s, int64_t* launches) {
+  if (n_tiles <= 0) return fl.target ? cudaMemsetAsync(fl.loss, 0, sizeof(double), s) : cudaSuccess;
+  if (fl.target) *launches += 1;  // k_sum_partials
 #define GMR_FWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, ncontrib_out, s)
+  fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
   else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
   else GMR_FWD(16, 64, 64); else GMR_FWD(16, 64, 128); else GMR_FWD(16, 64, 256);

@@ -189,6 +189,33 @@ class Renderer:
         self._saved = (verts, faces, rgb, opacity)
         return images, t_final
 
+    def forward_l2(self, verts, faces, rgb, opacity, cams, target, images=None, grad=None, loss=None, stream=None):
+        """Render all views and the squared-error loss against ``target`` in
+        one pass (gmr_render_fwd_l2); returns (images, dL/dimages, loss)."""
+        for t, name in ((verts, "verts"), (rgb, "rgb"), (target, "target")):
+            _check_dev(t, name, torch.float32)
+        _check_dev(faces, "faces", torch.int32)
+        if opacity is not None:
+            _check_dev(opacity, "opacity", torch.float32)
+        cam_arr = cams if isinstance(cams, ctypes.Array) else camera_array(cams)
+        npix = sum(int(c.width) * int(c.height) for c in cam_arr)
+        if tuple(target.shape) != (npix, 3):
+            raise _lib.GmrError(f"target must be [{npix}, 3]")
+        dev = verts.device
+        if images is None:
+            images = torch.empty((npix, 3), device=dev, dtype=torch.float32)
+        if grad is None:
+            grad = torch.empty((npix, 3), device=dev, dtype=torch.float32)
+        if loss is None:
+            loss = torch.empty((), device=dev, dtype=torch.float64)
+        self._check(self._L.gmr_render_fwd_l2(self._ctx, _ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
+                                              _ptr(rgb), _ptr(opacity), cam_arr, len(cam_arr), _ptr(images), None,
+                                              _ptr(target), _ptr(grad), _ptr(loss), _stream(stream)),
+                    "gmr_render_fwd_l2")
+        self.fwd_token += 1
+        self._saved = (verts, faces, rgb, opacity)
+        return images, grad, loss
+
     def backward(self, dL_dimages, dverts=None, drgb=None, dopacity=None, accumulate=False, stream=None):
         _check_dev(dL_dimages, "dL_dimages", torch.float32)
         verts, faces, rgb, opacity = self._saved

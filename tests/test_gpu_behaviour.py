@@ -63,6 +63,54 @@ def test_gradients_invariant_to_backward_shape():
             r.close()
 
 
+@pytest.mark.parametrize("n", [1, 4095, 4096, 3 * 100003, 1 << 22])
+def test_l2_loss_against_fp64(n):
+    """gmr_l2_loss on ragged sizes (partial blocks, unaligned tails): the
+    gradient 2 (img - target) bit for bit (the same two FP32 roundings as
+    NumPy), the loss within its stated 1.3e-6 relative of the FP64 sum."""
+    from paper_2602_14493_b300 import Renderer
+
+    rng = np.random.default_rng(n)
+    a = rng.random(n, dtype=np.float32)
+    b = rng.random(n, dtype=np.float32)
+    r = Renderer()
+    loss, grad = r.l2_loss(torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV))
+    d = a - b
+    np.testing.assert_array_equal(grad.cpu().numpy(), np.float32(2.0) * d)
+    ref = float(np.sum(d.astype(np.float64) ** 2))
+    assert abs(float(loss) - ref) <= 1.3e-6 * ref
+    r.close()
+
+
+def test_fused_forward_loss_matches_separate():
+    """gmr_render_fwd_l2: same image, the same dL/dI bit for bit, and the
+    same loss up to the FP32 rounding of the per-thread partial sums as
+    gmr_render_fwd + gmr_l2_loss; twice in a row, on views of uneven
+    sizes."""
+    s = _uneven()
+    for tile, threads in ((16, 256), (16, 128), (32, 256)):
+        r = _renderer(tile=tile, threads=threads)
+        (v, f, c, o), img, T = render_gpu(r, s)
+        img = img.clone()
+        target = torch.rand_like(img)
+        loss, grad = r.l2_loss(img, target)
+        grad, loss = grad.clone(), float(loss)
+        for _ in range(2):
+            img2, grad2, loss2 = r.forward_l2(v, f, c, o, s.cams, target)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(img2.cpu().numpy(), img.cpu().numpy())
+            np.testing.assert_array_equal(grad2.cpu().numpy(), grad.cpu().numpy())
+            # FP32 sums of <= 16 squares per thread and a 5-level FP32 warp
+            # tree on both sides: each within 21 u = 1.3e-6 relative
+            assert abs(float(loss2) - loss) <= 2.6e-6 * abs(loss)
+        # the backward after the fused forward matches the one after the plain forward
+        dv2 = r.backward(grad2)[0].clone()
+        r.forward(v, f, c, o, s.cams)
+        dv1 = r.backward(grad)[0].clone()
+        assert rel_l2(dv2.cpu().numpy(), dv1.cpu().numpy()) < 1e-5
+        r.close()
+
+
 def test_batched_equals_per_view():
     s = _uneven()
     r = _renderer()
