@@ -37,8 +37,9 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def sample_pixels(cams, n, seed):
-    """n random pixels over all views plus one full 16x16 window per view."""
+def sample_pixels(cams, n, seed, window=16):
+    """n random pixels over all views plus one full window x window block at
+    the centre of each view."""
     rng = np.random.default_rng(seed)
     off = oracle.pixel_offsets(cams)
     out = []
@@ -48,9 +49,9 @@ def sample_pixels(cams, n, seed):
         xs = rng.integers(0, W, k)
         ys = rng.integers(0, H, k)
         out.append(np.stack([np.full(k, c), xs, ys], 1))
-        x0, y0 = W // 2 - 8, H // 2 - 8
-        yy, xx = np.meshgrid(np.arange(y0, y0 + 16), np.arange(x0, x0 + 16), indexing="ij")
-        out.append(np.stack([np.full(256, c), xx.ravel(), yy.ravel()], 1))
+        x0, y0 = W // 2 - window // 2, H // 2 - window // 2
+        yy, xx = np.meshgrid(np.arange(y0, y0 + window), np.arange(x0, x0 + window), indexing="ij")
+        out.append(np.stack([np.full(window * window, c), xx.ravel(), yy.ravel()], 1))
     pix = np.concatenate(out, 0).astype(np.int32)
     pix = np.unique(pix, axis=0)
     lin = off[pix[:, 0]] + pix[:, 2] * np.array([int(cams[c]["width"]) for c in pix[:, 0]]) + pix[:, 1]
