@@ -236,7 +236,7 @@ GMR_API gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* 
 /* Squared-error loss sum((img - target)^2) over n floats and its gradient
  * 2 (img - target). loss is a device double (overwritten); dL_dimg may
  * alias neither input. Deterministic (fixed reduction order); FP32 sums of
- * 16 squares per thread and 32 threads per warp, FP64 above that (relative
+ * 16 squares (two per thread) and 32 threads per warp, FP64 above that (relative
  * error below 1.3e-6). */
 GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int64_t n, float* dL_dimg,
                        double* loss, gmr_stream stream);
@@ -258,6 +258,26 @@ GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* targ
 #define GMR_L2_NOALLOC_MAX_ELEMS 67108864
 GMR_API gmr_status gmr_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* dL_dimg,
                                        double* loss, gmr_stream stream);
+
+/* One optimiser step of the fitting loop around the renderer (Sec. 3.1) on
+ * n device floats, in place: params -= lr m_hat / (sqrt(v_hat) + eps) with
+ * m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2, m_hat =
+ * m / (1 - beta1^step), v_hat = v / (1 - beta2^step) (Adam, Kingma and Ba
+ * 2015). group = 3 is VectorAdam, the optimiser the paper uses: params are
+ * 3-vectors (n a multiple of 3) and v holds one entry per 3-vector, updated
+ * with the squared norm |g|^2. m (n floats) and v (n / group floats) are
+ * caller-owned and zero before step 1; step counts from 1. */
+GMR_API gmr_status gmr_adam_step(gmr_ctx* ctx, float* params, const float* grads, float* m, float* v, int64_t n,
+                                 int32_t group, float lr, float beta1, float beta2, float eps, int32_t step,
+                                 gmr_stream stream);
+
+/* Chamfer distance (the paper's CD, Sec. 3.1) between two device point sets
+ * a (na x 3) and b (nb x 3), by brute force over all pairs:
+ * out[0] = mean over a of min over b |a - b|^2, out[1] = the same from b to
+ * a (device doubles; CD = out[0] + out[1]). Distances in FP32, means summed
+ * in double-float arithmetic. */
+GMR_API gmr_status gmr_chamfer(gmr_ctx* ctx, const float* a, int64_t na, const float* b, int64_t nb, double* out,
+                               gmr_stream stream);
 
 /* Synchronises the stream, returns and clears the device status bits
  * (GMR_DEV_*) accumulated since the last call. */

@@ -591,6 +591,35 @@ gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int6
   return GMR_OK;
 }
 
+gmr_status gmr_adam_step(gmr_ctx* ctx, float* params, const float* grads, float* m, float* v, int64_t n,
+                         int32_t group, float lr, float beta1, float beta2, float eps, int32_t step,
+                         gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (n < 0 || (group != 1 && group != 3) || n % group != 0 || step < 1 ||
+      (n > 0 && (!params || !grads || !m || !v)))
+    return fail(ctx, GMR_ERR_INVALID_ARG, "bad Adam arguments");
+  if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return fail(ctx, GMR_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  GMR_CUDA(ctx, gmr::launch_adam(params, grads, m, v, n, group, lr, beta1, beta2, eps, step, (cudaStream_t)stream,
+                                 &ctx->launches));
+  return GMR_OK;
+}
+
+gmr_status gmr_chamfer(gmr_ctx* ctx, const float* a, int64_t na, const float* b, int64_t nb, double* out,
+                       gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (na < 1 || nb < 1 || !a || !b || !out) return fail(ctx, GMR_ERR_INVALID_ARG, "bad chamfer arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+  // per-point minima as floats after slot 0 (gmr_l2_loss's ticket counter)
+  gmr_status st = ensure_loss(ctx, 1 + (na + nb + 1) / 2, cap_status != cudaStreamCaptureStatusNone);
+  if (st != GMR_OK) return st;
+  GMR_CUDA(ctx, gmr::launch_chamfer(a, na, b, nb, reinterpret_cast<float*>(ctx->ws.loss_part + 1), out, s,
+                                    &ctx->launches));
+  return GMR_OK;
+}
+
 gmr_status gmr_get_device_status(gmr_ctx* ctx, gmr_stream stream, uint32_t* status) {
   if (!ctx || !status) return GMR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;

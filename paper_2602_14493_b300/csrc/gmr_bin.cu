@@ -8,12 +8,13 @@
 //     and k_place_keys writes each pair's 64-bit key (depth bits << 32 |
 //     face) to segment start + rank, with no atomics;
 //  2. the remaining digits, (depth bits, face), within each tile: segments
-//     of up to 512 keys (nearly all) are sorted by one warp each, in
-//     registers, with a bitonic network (shuffles only, no CTA barrier);
-//     longer segments are listed and sorted by one CTA each with an LSD
-//     radix sort on the 8-bit digits that differ within the segment (usually
-//     not the depth's exponent byte nor the face index's upper bytes), in
-//     shared memory up to kSegSmem keys and through global memory beyond.
+//     of up to 512 keys (nearly all) are sorted by one warp each with a
+//     bitonic network, up to 256 keys in registers (shuffles only) and 257 to
+//     512 in shared memory; longer segments are listed and sorted by one CTA
+//     each with an LSD radix sort on the 8-bit digits that differ within the
+//     segment (usually not the depth's exponent byte nor the face index's
+//     upper bytes), in shared memory up to kSegSmem keys and through global
+//     memory beyond.
 //
 // Keys are unique (face ids are), so the result is the unique (tile, depth,
 // face) order whatever order step 1 put the keys of a segment in.
@@ -135,52 +136,56 @@ __device__ void seg_radix_pass(const unsigned long long* src, unsigned long long
 }
 
 // Ascending bitonic sort of 32*KPL 64-bit keys held by one warp, element
-// e = r * 32 + lane in register r of lane `lane`. The stage loops are not
-// unrolled (one body per exchange distance class keeps the code small enough
-// for the instruction cache); the register loops are, so `v` stays in
-// registers.
+// e = lane * KPL + r in register r of lane `lane`: the stages that compare
+// elements less than KPL apart stay inside a thread (two selects, no
+// shuffle), the others exchange whole registers between lanes. The stage
+// loops are not unrolled (one body per exchange distance class keeps the
+// code small enough for the instruction cache); the register loops are, so
+// `v` stays in registers.
 template <int KPL>
-__device__ __forceinline__ void cmp_lanes(unsigned long long (&v)[KPL], int k, int j, int lane) {
-  const bool upper = (lane & j) != 0;
+__device__ __forceinline__ void cmp_lanes(unsigned long long (&v)[KPL], int k, int jl, int lane) {
+  // partner lane ^ jl (distance j = jl * KPL >= KPL, so k > KPL: the
+  // direction depends on the lane only)
+  const bool upper = (lane & jl) != 0;
+  const bool asc = ((lane * KPL) & k) == 0;
+  const bool take_min = asc != upper;
 #pragma unroll
   for (int r = 0; r < KPL; ++r) {
-    const bool asc = (((r << 5) | lane) & k) == 0;
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], j);
-    const bool take_min = asc != upper;
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], jl);
     const bool lt = v[r] < o;
     v[r] = (take_min == lt) ? v[r] : o;
   }
 }
 
-// partner in register r ^ JR of the same lane (j = 32 JR, k >= 64)
-template <int KPL, int JR>
-__device__ __forceinline__ void cmp_regs(unsigned long long (&v)[KPL], int k) {
+// partner in register r ^ J of the same lane (distance J < KPL)
+template <int KPL, int J>
+__device__ __forceinline__ void cmp_regs(unsigned long long (&v)[KPL], int k, int lane) {
 #pragma unroll
   for (int r = 0; r < KPL; ++r) {
-    if (r & JR) continue;
-    const bool asc = ((r << 5) & k) == 0;
-    const unsigned long long a = v[r], b = v[r | JR];
+    if (r & J) continue;
+    const bool asc = ((lane * KPL + r) & k) == 0;
+    const unsigned long long a = v[r], b = v[r | J];
     const bool sw = asc ? (a > b) : (a < b);
     v[r] = sw ? b : a;
-    v[r | JR] = sw ? a : b;
+    v[r | J] = sw ? a : b;
   }
 }
 
 template <int KPL>
 __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[KPL], int lane) {
   constexpr int N = 32 * KPL;
+  constexpr int LOG = KPL == 1 ? 0 : KPL == 2 ? 1 : KPL == 4 ? 2 : 3;
+  static_assert(KPL == 1 || KPL == 2 || KPL == 4 || KPL == 8, "KPL");
 #pragma unroll 1
   for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll 1
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < 32) {
-        cmp_lanes<KPL>(v, k, j, lane);
+      if (j >= KPL) {
+        cmp_lanes<KPL>(v, k, j >> LOG, lane);
       } else {
-        const int jr = j >> 5;
-        if (KPL > 1 && jr == 1) cmp_regs<KPL, 1>(v, k);
-        if (KPL > 2 && jr == 2) cmp_regs<KPL, 2>(v, k);
-        if (KPL > 4 && jr == 4) cmp_regs<KPL, 4>(v, k);
-        if (KPL > 8 && jr == 8) cmp_regs<KPL, 8>(v, k);
+        if (KPL > 1 && j == 1) cmp_regs<KPL, 1>(v, k, lane);
+        if (KPL > 2 && j == 2) cmp_regs<KPL, 2>(v, k, lane);
+        if (KPL > 4 && j == 4) cmp_regs<KPL, 4>(v, k, lane);
       }
     }
   }
@@ -192,28 +197,58 @@ __device__ __forceinline__ void warp_sort_segment(const unsigned long long* __re
   unsigned long long v[KPL];
 #pragma unroll
   for (int r = 0; r < KPL; ++r) {
-    const int e = r * 32 + lane;
+    const int e = lane * KPL + r;
     v[r] = e < L ? gk[e] : ~0ull;
   }
   warp_bitonic<KPL>(v, lane);
 #pragma unroll
   for (int r = 0; r < KPL; ++r) {
-    const int e = r * 32 + lane;
+    const int e = lane * KPL + r;
     if (e < L) out[e] = (uint32_t)v[r];
   }
 }
 
-constexpr int kWarpSortMax = 512;
-constexpr int kTilesPerCta = kSegThreads / 32;
+// Ascending bitonic sort of up to 512 64-bit keys by one warp in shared
+// memory (s holds 512 keys): each lane takes 8 of the 256 compare-exchange
+// pairs of every stage.
+__device__ __forceinline__ void warp_sort_smem512(const unsigned long long* __restrict__ gk, int L,
+                                                  uint32_t* __restrict__ out, unsigned long long* s, int lane) {
+  for (int i = lane; i < 512; i += 32) s[i] = i < L ? gk[i] : ~0ull;
+  __syncwarp();
+#pragma unroll 1
+  for (int k = 2; k <= 512; k <<= 1) {
+#pragma unroll 1
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int p = q * 32 + lane;                  // pair index 0..255
+        const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));  // lower element of the pair
+        const unsigned long long a = s[i], b = s[i + j];
+        const bool asc = (i & k) == 0;
+        if ((a > b) == asc) {
+          s[i] = b;
+          s[i + j] = a;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < L; i += 32) out[i] = (uint32_t)s[i];
+}
 
-// One warp per global tile: write the range; sort segments of up to 512 keys
-// in registers; list longer segments for k_long_sort.
-__global__ void __launch_bounds__(kSegThreads, 2) k_tile_sort(const uint32_t* __restrict__ tile_start,
-                                                           int64_t n_tiles, const unsigned long long* __restrict__ keys,
-                                                           uint32_t* __restrict__ pair_face,
-                                                           uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
-                                                           uint32_t* __restrict__ long_count,
-                                                           Counters* __restrict__ counters, int64_t cap) {
+constexpr int kWarpSortMax = 512;   // keys sorted by one warp
+constexpr int kTileSortThreads = 64;  // small CTAs: tiles of uneven length retire independently
+constexpr int kTilesPerCta = kTileSortThreads / 32;
+
+// One warp per global tile: write the range; sort segments of up to 256 keys
+// in registers (8 per lane at most, which keeps the register count and so
+// the occupancy at that of the common case) and of 257 to 512 keys in
+// shared memory; list longer segments for k_long_sort.
+__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
+    const uint32_t* __restrict__ tile_start, int64_t n_tiles, const unsigned long long* __restrict__ keys,
+    uint32_t* __restrict__ pair_face, uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
+    Counters* __restrict__ counters, int64_t cap) {
+  __shared__ unsigned long long s_keys[kTilesPerCta][kWarpSortMax];
   const int lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
   if (t >= n_tiles) return;
@@ -241,9 +276,9 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_tile_sort(const uint32_t* __
   } else if (L <= 256) {
     warp_sort_segment<8>(gk, L, out, lane);
   } else if (L <= kWarpSortMax) {
-    warp_sort_segment<16>(gk, L, out, lane);
+    warp_sort_smem512(gk, L, out, s_keys[threadIdx.x >> 5], lane);
   } else if (lane == 0) {
-    long_list[atomicAdd(long_count, 1u)] = (uint32_t)t;
+    long_list[atomicAdd(&counters->n_long, 1u)] = (uint32_t)t;
   }
 }
 
@@ -251,13 +286,13 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_tile_sort(const uint32_t* __
 // 8-bit digits that differ within the segment, in shared memory up to
 // kSegSmem keys and through global memory beyond.
 __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
-                                                           const uint32_t* __restrict__ long_count,
+                                                           const Counters* __restrict__ counters,
                                                            const uint2* __restrict__ ranges,
                                                            unsigned long long* __restrict__ keys,
                                                            unsigned long long* __restrict__ keys_tmp,
                                                            uint32_t* __restrict__ pair_face) {
   __shared__ SegSmem sm;
-  const uint32_t nlong = *long_count;
+  const uint32_t nlong = counters->n_long;
   for (uint32_t li = blockIdx.x; li < nlong; li += gridDim.x) {
     const uint2 rg = ranges[long_list[li]];
     const int L = (int)(rg.y - rg.x);
@@ -320,10 +355,10 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
     *launches += 1;
   }
   if (n_tiles > 0) {
-    k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kSegThreads, 0, s>>>(
-        ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, &ws.counters->n_long,
-        ws.counters, ws.cap_pairs);
-    k_long_sort<<<148, kSegThreads, 0, s>>>(ws.long_tiles, &ws.counters->n_long, ws.tile_range, ws.pair_key[0],
+    k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kTileSortThreads, 0, s>>>(
+        ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.counters,
+        ws.cap_pairs);
+    k_long_sort<<<148, kSegThreads, 0, s>>>(ws.long_tiles, ws.counters, ws.tile_range, ws.pair_key[0],
                                            ws.pair_key[1], ws.pair_face);
     *launches += 2;
   }

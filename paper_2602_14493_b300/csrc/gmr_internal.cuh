@@ -110,6 +110,18 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// 1 / a for a in [0.01, 1] (the 1 - alpha of compositing): the hardware
+// approximation refined by one Newton-Raphson step for f(x) = 1/x - a,
+// x1 = x0 + x0 (1 - a x0), which squares the relative error of x0 (to well
+// under one ulp of FP32). The backward reconstructs the transmittance of
+// every layer by repeated division, so the error per step compounds.
+__device__ __forceinline__ float rcp_refined(float a) {
+  float x0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x0) : "f"(a));
+  const float e = __fmaf_rn(-a, x0, 1.0f);
+  return __fmaf_rn(x0, e, x0);
+}
+
 __device__ __forceinline__ float3 ld_vert(const float* v, int i) {
   return make_float3(__ldg(v + 3 * i), __ldg(v + 3 * i + 1), __ldg(v + 3 * i + 2));
 }
@@ -232,7 +244,7 @@ struct Workspace {
   uint32_t* tile_count = nullptr;  // pairs per tile (zero between forwards)
   uint32_t* tile_start = nullptr;  // exclusive scan of tile_count
   uint2* tile_range = nullptr;     // [start, end) per tile, (0, 0) when empty
-  uint32_t* long_tiles = nullptr;  // tiles sorted by the CTA path
+  uint32_t* long_tiles = nullptr;  // tiles of more than 512 pairs (sorted by one CTA each)
   // pairs
   int64_t cap_pairs = 0;
   // pair_key[0]: (depth bits << 32 | face) per pair in tile segments;
@@ -309,5 +321,14 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace&
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
 int64_t l2_loss_partials_needed(int64_t n);
+// *out = scale * sum of n floats (one CTA, fixed order, double-float sums)
+cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* out, cudaStream_t s,
+                              int64_t* launches);
+// gmr_optim.cu
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int group, float lr, float b1,
+                        float b2, float eps, int step, cudaStream_t s, int64_t* launches);
+// out[0] = mean_a min_b |a - b|^2, out[1] = mean_b min_a |b - a|^2; scratch: na + nb floats
+cudaError_t launch_chamfer(const float* a, int64_t na, const float* b, int64_t nb, float* scratch, double* out,
+                           cudaStream_t s, int64_t* launches);
 
 }  // namespace gmr

@@ -440,7 +440,11 @@ __global__ void __launch_bounds__(128) k_record_bwd(
 // (deterministic), maps them to the three vertices (d_a = v_a - mu with mu
 // the vertex mean, n = e1 x e2 / |e1 x e2|, kappa = |A| / (pi 1e-7) when
 // clamped) and scatters them; colour and opacity gradients are per face.
-__global__ void __launch_bounds__(256) k_face_bwd(
+// Small CTAs: there is one thread per face, and at 256 threads a mesh of
+// 20K faces would occupy only 80 SMs.
+constexpr int kFaceBwdThreads = 64;
+
+__global__ void __launch_bounds__(kFaceBwdThreads) k_face_bwd(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
     int cov_mode, int color_mode, const float* __restrict__ opacity, const float4* __restrict__ rec_contrib,
     const float4* __restrict__ face_grad, float* __restrict__ dverts, float* __restrict__ drgb,
@@ -453,6 +457,7 @@ __global__ void __launch_bounds__(256) k_face_bwd(
   float3 dd[3] = {dmu, dmu, dmu};
   float3 dn = dmu;
   float dw = 0.f;
+#pragma unroll 4
   for (int c = 0; c < C; ++c) {
     const float4* in = rec_contrib + 4 * ((size_t)c * F + f);
     const float4 q0 = in[0], q1 = in[1], q2 = in[2], q3 = in[3];
@@ -591,7 +596,8 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
   if (F <= 0) return cudaSuccess;
   dim3 grid((F + 127) / 128, C);
   k_record_bwd<<<grid, 128, 0, s>>>(verts, V, faces, F, views, cov_mode, ws.rec_grad, ws.rec_q, ws.rec_contrib);
-  k_face_bwd<<<(F + 255) / 256, 256, 0, s>>>(verts, V, faces, F, C, cov_mode, color_mode, opacity, ws.rec_contrib,
+  k_face_bwd<<<(F + kFaceBwdThreads - 1) / kFaceBwdThreads, kFaceBwdThreads, 0, s>>>(
+      verts, V, faces, F, C, cov_mode, color_mode, opacity, ws.rec_contrib,
                                              ws.face_grad, dverts, drgb, dop, accumulate);
   *launches += 2;
   return cudaGetLastError();

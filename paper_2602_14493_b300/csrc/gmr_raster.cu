@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
 
 // Sum of n floats into *out, one block, in a fixed order, with double-float
 // accumulation in FP32 arithmetic (error ~n 2^-44 relative, no FP64 pipe).
-__global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__ part, int64_t n,
+__global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__ part, int64_t n, double scale,
                                                        double* __restrict__ out) {
   __shared__ df sw[32];
   // rounds of 16 independent loads per thread, then their (fixed-order) sum
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
       acc = df_add(acc, df{__shfl_xor_sync(kFull, acc.hi, o), __shfl_xor_sync(kFull, acc.lo, o)});
-    if (threadIdx.x == 0) *out = (double)acc.hi + (double)acc.lo;
+    if (threadIdx.x == 0) *out = ((double)acc.hi + (double)acc.lo) * scale;
   }
 }
 
@@ -553,11 +553,13 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
           float graw;
           float alpha = gauss_alpha(p2[k], hh.z, graw);
           float om = __fsub_rn(1.0f, alpha);
-          float inv = __fdividef(1.0f, om);
+          float inv = rcp_refined(om);
           float Tb = T[k] * inv;
           float w = alpha * Tb;
           float cg = col.x * G0[k] + col.y * G1[k] + col.z * G2[k];
-          float dalpha = Tb * cg - SG[k] * inv;
+          // T_i (c.g) - S.g / (1 - alpha) = (T_(i+1) (c.g) - S.g) / (1 - alpha):
+          // the difference of the two (often nearly equal) terms in one FMA
+          float dalpha = inv * __fmaf_rn(T[k], cg, -SG[k]);
           SG[k] += w * cg;
           T[k] = Tb;
           float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
 // partials in index order, so the result does not depend on which block
 // that is, then returns the counter to zero for the next call.
 constexpr int kLossThreads = 256;
-constexpr int kLossItems = 16;  // floats per thread
+constexpr int kLossItems = 32;  // floats per thread: 16 float4 loads in flight
 constexpr int kLossBlockElems = kLossThreads * kLossItems;
 
 __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restrict__ img,
@@ -609,9 +611,9 @@ __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restric
                                                            float* __restrict__ grad, double* __restrict__ part,
                                                            double* __restrict__ loss, bool vec4) {
   const int64_t base = (int64_t)blockIdx.x * kLossBlockElems;
-  // FP32 within a thread (16 terms) and a warp, FP64 across warps and
-  // blocks: FP64 arithmetic is a slow pipe on this GPU.
-  float accf = 0.0f;
+  // FP32 within a thread (two running sums of 16 squares each) and a warp,
+  // FP64 across warps and blocks: FP64 arithmetic is a slow pipe on this GPU.
+  float acc0 = 0.0f, acc1 = 0.0f;
   if (vec4 && base + kLossBlockElems <= n) {
     const float4* i4 = reinterpret_cast<const float4*>(img + base);
     const float4* t4 = reinterpret_cast<const float4*>(tgt + base);
@@ -626,10 +628,11 @@ __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restric
     for (int k = 0; k < kLossItems / 4; ++k) {
       const float4 d = make_float4(x[k].x - y[k].x, x[k].y - y[k].y, x[k].z - y[k].z, x[k].w - y[k].w);
       g4[k * kLossThreads + threadIdx.x] = make_float4(2.0f * d.x, 2.0f * d.y, 2.0f * d.z, 2.0f * d.w);
-      accf = fmaf(d.x, d.x, accf);
-      accf = fmaf(d.y, d.y, accf);
-      accf = fmaf(d.z, d.z, accf);
-      accf = fmaf(d.w, d.w, accf);
+      float& acc = (k & 1) ? acc1 : acc0;
+      acc = fmaf(d.x, d.x, acc);
+      acc = fmaf(d.y, d.y, acc);
+      acc = fmaf(d.z, d.z, acc);
+      acc = fmaf(d.w, d.w, acc);
     }
   } else {
 #pragma unroll 4
@@ -638,10 +641,12 @@ __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restric
       if (i < n) {
         const float d = img[i] - tgt[i];
         grad[i] = 2.0f * d;
-        accf = fmaf(d, d, accf);
+        if (k < kLossItems / 2) acc0 = fmaf(d, d, acc0);
+        else acc1 = fmaf(d, d, acc1);
       }
     }
   }
+  const float accf = acc0 + acc1;
   loss_partial_and_finish<kLossThreads>(accf, part, loss);
 }
 
@@ -676,7 +681,7 @@ void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
                                                                  images, ws.pix_T, ws.pix_last, t_out, nc_out,
                                                                  ws.cap_pixels, fl, ws.counters);
-  if (fl.target) k_sum_partials<<<1, 1024, 0, s>>>(fl.part, n_tiles * (NT / 32), fl.loss);
+  if (fl.target) k_sum_partials<<<1, 1024, 0, s>>>(fl.part, n_tiles * (NT / 32), 1.0, fl.loss);
 }
 
 template <int TS, int NT, int BATCH>
@@ -730,6 +735,13 @@ cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* re
                                  int64_t* launches) {
   if (n_rec <= 0) return cudaSuccess;
   k_debug_records<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(ws.rec_rect, ws.rec_q, n_rec, rects, conic);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* out, cudaStream_t s,
+                              int64_t* launches) {
+  k_sum_partials<<<1, 1024, 0, s>>>(x, n, scale, out);
   *launches += 1;
   return cudaGetLastError();
 }

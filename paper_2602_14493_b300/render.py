@@ -241,6 +241,30 @@ class Renderer:
                                         _stream(stream)), "gmr_l2_loss")
         return loss, grad
 
+    def adam_step(self, params, grads, m, v, lr, step, group=1, betas=(0.9, 0.999), eps=1e-8, stream=None):
+        """In-place Adam (group=1) or VectorAdam (group=3, per 3-vector
+        second moment; v has params.numel() / 3 entries) step; step >= 1."""
+        for t, name in ((params, "params"), (grads, "grads"), (m, "m"), (v, "v")):
+            _check_dev(t, name, torch.float32)
+        n = params.numel()
+        if grads.numel() != n or m.numel() != n or v.numel() * group != n:
+            raise ValueError("adam_step: params, grads, m and v sizes do not match")
+        self._check(self._L.gmr_adam_step(self._ctx, _ptr(params), _ptr(grads), _ptr(m), _ptr(v), n, group,
+                                          float(lr), float(betas[0]), float(betas[1]), float(eps), int(step),
+                                          _stream(stream)), "gmr_adam_step")
+
+    def chamfer(self, a, b, out=None, stream=None):
+        """Chamfer distance between point sets a [na, 3] and b [nb, 3]:
+        a device tensor of 2 doubles (mean a->b and b->a squared nearest
+        distances; CD = their sum)."""
+        _check_dev(a, "a", torch.float32)
+        _check_dev(b, "b", torch.float32)
+        if out is None:
+            out = torch.empty(2, device=a.device, dtype=torch.float64)
+        self._check(self._L.gmr_chamfer(self._ctx, _ptr(a), a.shape[0], _ptr(b), b.shape[0], _ptr(out),
+                                        _stream(stream)), "gmr_chamfer")
+        return out
+
     def device_status(self, stream=None) -> int:
         st = ctypes.c_uint32()
         self._check(self._L.gmr_get_device_status(self._ctx, _stream(stream), ctypes.byref(st)),
