@@ -41,7 +41,11 @@ WORKLOADS = {
     "icosphere3_1x128": gi.scene_single_view,
     "icosphere6_noise_64xuneven": gi.scene_fibonacci_uneven,
     "icosphere8_perlin_16x1024": gi.scene_large,
+    "icosphere7_fit_4x512": gi.scene_fit,
 }
+# the optimisation-loop workload: a step is one Adam step of the fit (render
+# 4 views of 512^2, loss, backward, parameter update)
+FIT_WORKLOAD = "icosphere7_fit_4x512"
 
 # FP32 peak of the CUDA cores: 148 SMs x 128 lanes x 2 (FMA) x 2.032 GHz.
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -52,9 +56,9 @@ FLOPS_FWD_CONTRIB = 10
 FLOPS_BWD_CONTRIB = 59
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that
 # ncu measured for the dominant kernel on the default workload
-# (profiles/raster_icosphere5_sin_8x512.md); to be removed when the kernel
-# changes after the capture.
-NCU_TRAFFIC = {}
+# (profiles/raster_bwd_traffic_icosphere5_sin_8x512.md); to be removed when
+# the kernel changes after the capture.
+NCU_TRAFFIC = {("raster_bwd", "icosphere5_sin_8x512"): 55733504}
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -217,6 +221,68 @@ def run_reference(args, ws, rank):
 
 
 # ---------------------------------------------------------------- GPU arm
+def run_fit(args, ws, rank, local):
+    """The fitting loop (level-7 icosphere to a deformed shape, 4 random
+    views of 512^2 per step, Adam lr 1e-3): per-step time of the batched and
+    the per-view form, loss and chamfer distance before and after."""
+    import torch
+
+    from paper_2602_14493_b300 import Renderer
+    from paper_2602_14493_b300.fit import fit, render_targets
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sampler = ClockSampler(local, period_ms=50)
+    sampler.start()
+    K, W = args.steps, args.warmup
+    scene = gi.scene_fit(steps=K)
+    r = Renderer()
+    faces = torch.from_numpy(scene.faces).to(dev)
+    op = torch.from_numpy(scene.opacity).to(dev)
+    targets = render_targets(r, torch.from_numpy(scene.extra["target_verts"]).to(dev), faces,
+                             torch.from_numpy(scene.extra["target_rgb"]).to(dev), op, scene.extra["view_sets"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    fit(scene, steps=W, renderer=r, targets=targets[:W])  # warm-up of both forms
+    fit(scene, steps=W, form="per_view", renderer=r, targets=targets[:W])
+    torch.cuda.synchronize()
+    barrier(ws)
+    t_wall0 = time.perf_counter()
+    out_b = fit(scene, steps=K, form="batched", renderer=r, targets=targets, between_steps=flush.zero_)
+    out_p = fit(scene, steps=K, form="per_view", renderer=r, targets=targets, between_steps=flush.zero_)
+    t_wall1 = time.perf_counter()
+    sampler.stop()
+    n_pix = out_b["pixels_per_step"]
+    tb = max_over_ranks(float(out_b["ms"].sum()) / 1e3, ws)
+    tp = max_over_ranks(float(out_p["ms"].sum()) / 1e3, ws)
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(scene, args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": ws * n_pix * K / tb / 1e6, "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": W, "ms_per_step": 1e3 * tb / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": FIT_WORKLOAD, "faces": len(scene.faces), "views_per_step": len(scene.cams),
+                   "pixels_per_step": n_pix, "optimizer": "adam", "lr": 1e-3,
+                   "step": "render 4 views + L2 loss + backward + Adam on vertices and face colours",
+                   "form": "batched, one call for all views of a step, eager",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "per_view": {"value": ws * n_pix * K / tp / 1e6, "ms_per_step": 1e3 * tp / K,
+                     "form": "one call per view, eager"},
+        "fit": {"loss_first": float(out_b["loss"][0]), "loss_last": float(out_b["loss"][-1]),
+                "chamfer_initial": out_b["chamfer_initial"], "chamfer_final": out_b["chamfer_final"],
+                "chamfer_final_per_view": out_p["chamfer_final"]},
+        "roofline": None, "cpu_baseline": cpu, "e2e": None,
+        "clocks": sampler.summary(t_wall0, t_wall1),
+        "device_status": out_b["status"] | out_p["status"],
+    }
+    print(json.dumps(out), flush=True)
+
+
 def run_gmr(args, ws, rank, local):
     import torch
 
@@ -501,6 +567,9 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == FIT_WORKLOAD:
+        run_fit(args, ws, rank, local)
         return
     run_gmr(args, ws, rank, local)
 

@@ -30,7 +30,7 @@ def render_targets(renderer: Renderer, target_verts, faces, target_rgb, opacity,
 
 
 def fit(scene, steps=None, lr=1e-3, form="batched", optimizer="adam", renderer=None, targets=None,
-        betas=(0.9, 0.999), eps=1e-8):
+        betas=(0.9, 0.999), eps=1e-8, between_steps=None):
     """Optimise scene.verts and scene.rgb against renders of
     scene.extra["target_verts"] / ["target_rgb"] from scene.extra["view_sets"].
 
@@ -38,7 +38,9 @@ def fit(scene, steps=None, lr=1e-3, form="batched", optimizer="adam", renderer=N
     optimizer: "adam" (per element) or "vectoradam" (vertex second moments
     per 3-vector). Returns a dict with the per-step losses and times (ms,
     CUDA events around each whole step), the fitted vertices and colours,
-    and the chamfer distances to the target vertices before and after."""
+    and the chamfer distances to the target vertices before and after.
+    between_steps, if given, is called after each step's closing event (so
+    outside the timed region), e.g. to flush the L2 cache."""
     if form not in ("batched", "per_view"):
         raise ValueError("form must be 'batched' or 'per_view'")
     if optimizer not in ("adam", "vectoradam"):
@@ -90,6 +92,8 @@ def fit(scene, steps=None, lr=1e-3, form="batched", optimizer="adam", renderer=N
         r.adam_step(verts, dv, m_v, v_v, lr, t + 1, group=gv, betas=betas, eps=eps)
         r.adam_step(rgb, dc, m_c, v_c, lr, t + 1, group=1, betas=betas, eps=eps)
         events[t][1].record()
+        if between_steps is not None:
+            between_steps()
     cd1 = r.chamfer(verts, tverts).sum()
     torch.cuda.synchronize()
     return {
