@@ -11,10 +11,10 @@
 //     of up to 512 keys (nearly all) are sorted by one warp each with a
 //     bitonic network, up to 256 keys in registers (shuffles only) and 257 to
 //     512 in shared memory; longer segments are listed and sorted by one CTA
-//     each with an LSD radix sort on the 8-bit digits that differ within the
+//     each, up to 4096 keys with a bitonic network in shared memory, beyond
+//     with an LSD radix sort on the 8-bit digits that differ within the
 //     segment (usually not the depth's exponent byte nor the face index's
-//     upper bytes), in shared memory up to kSegSmem keys and through global
-//     memory beyond.
+//     upper bytes) through global memory.
 //
 // Keys are unique (face ids are), so the result is the unique (tile, depth,
 // face) order whatever order step 1 put the keys of a segment in.
@@ -78,8 +78,13 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* sw) {
 }
 
 struct SegSmem {
-  unsigned long long a[kSegSmem];
-  unsigned long long b[kSegSmem];
+  union {
+    struct {
+      unsigned long long a[kSegSmem];
+      unsigned long long b[kSegSmem];
+    };
+    unsigned long long all[2 * kSegSmem];  // the CTA bitonic sort's buffer
+  };
   uint32_t wcnt[kSegWarps][kRadix];  // per warp, per digit
   uint32_t base[kRadix];             // running start of each digit
   uint32_t sw[32];
@@ -282,9 +287,36 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
   }
 }
 
-// Segments longer than kWarpSortMax: one CTA each, LSD radix sort on the
-// 8-bit digits that differ within the segment, in shared memory up to
-// kSegSmem keys and through global memory beyond.
+// Ascending bitonic sort of L <= 2 kSegSmem 64-bit keys by the whole CTA in
+// shared memory (padded to the next power of two with the largest key):
+// every stage's compare-exchange pairs are spread over the threads, one
+// barrier per stage.
+__device__ void cta_sort_smem(const unsigned long long* __restrict__ gk, int L, uint32_t* __restrict__ out,
+                              unsigned long long* s) {
+  int N = 2;
+  while (N < L) N <<= 1;
+  for (int i = threadIdx.x; i < N; i += kSegThreads) s[i] = i < L ? gk[i] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int p = threadIdx.x; p < (N >> 1); p += kSegThreads) {
+        const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+        const unsigned long long a = s[i], b = s[i + j];
+        if ((a > b) == ((i & k) == 0)) {
+          s[i] = b;
+          s[i + j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < L; i += kSegThreads) out[i] = (uint32_t)s[i];
+  __syncthreads();
+}
+
+// Segments longer than kWarpSortMax: one CTA each; up to 2 kSegSmem keys a
+// bitonic sort in shared memory, beyond an LSD radix sort on the 8-bit
+// digits that differ within the segment, through global memory.
 __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
                                                            const Counters* __restrict__ counters,
                                                            const uint2* __restrict__ ranges,
@@ -298,13 +330,15 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
     const int L = (int)(rg.y - rg.x);
     unsigned long long* gk = keys + rg.x;
     unsigned long long* gt = keys_tmp + rg.x;
-    const bool in_smem = L <= kSegSmem;
+    if (L <= 2 * kSegSmem) {
+      cta_sort_smem(gk, L, pair_face + rg.x, sm.all);
+      continue;
+    }
     unsigned long long a = ~0ull, o = 0ull;
     for (int i = threadIdx.x; i < L; i += kSegThreads) {
       const unsigned long long k = gk[i];
       a &= k;
       o |= k;
-      if (in_smem) sm.a[i] = k;
     }
 #pragma unroll
     for (int s2 = 16; s2 > 0; s2 >>= 1) {
@@ -320,8 +354,8 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
     unsigned long long diff = 0;
 #pragma unroll
     for (int w = 0; w < kSegWarps; ++w) diff |= sm.red_and[w] ^ sm.red_or[w];
-    unsigned long long* src = in_smem ? sm.a : gk;
-    unsigned long long* dst = in_smem ? sm.b : gt;
+    unsigned long long* src = gk;
+    unsigned long long* dst = gt;
     for (int shift = 0; shift < 64; shift += 8) {
       if (((diff >> shift) & 0xffull) == 0) continue;  // uniform over the CTA
       seg_radix_pass(src, dst, L, shift, sm);
@@ -358,8 +392,8 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
     k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kTileSortThreads, 0, s>>>(
         ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.counters,
         ws.cap_pairs);
-    k_long_sort<<<148, kSegThreads, 0, s>>>(ws.long_tiles, ws.counters, ws.tile_range, ws.pair_key[0],
-                                           ws.pair_key[1], ws.pair_face);
+    k_long_sort<<<148 * 3, kSegThreads, 0, s>>>(ws.long_tiles, ws.counters, ws.tile_range, ws.pair_key[0],
+                                               ws.pair_key[1], ws.pair_face);
     *launches += 2;
   }
   return cudaGetLastError();

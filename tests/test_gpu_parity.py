@@ -69,10 +69,21 @@ def test_convert_matches_oracle(cov_mode, color_mode):
 
 
 # ------------------------------------------------------------------ binning
+def _dense_scene():
+    """A level-6 icosphere (81,920 faces) in one 128^2 view: tile segments
+    of every length class (up to 256 keys, 257-512, 513-4096 and beyond:
+    the longest holds 4,920 keys with 16x16 tiles)."""
+    v, f = gi.icosphere(6)
+    rng = np.random.default_rng(61)
+    cams = gi.ring_cameras(1, 20.0, 3.0, 128, 128)
+    return gi.Scene("dense6_1x128", v.astype(np.float32), f, rng.random((len(f), 3)).astype(np.float32),
+                    np.full(len(f), 0.9, np.float32), cams)
+
+
 @pytest.mark.parametrize("tile", [16, 32])
-@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven"])
+@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven", "dense6_1x128"])
 def test_binning_bit_exact(renderer, tile, name):
-    s = _scenes()[name]
+    s = _dense_scene() if name == "dense6_1x128" else _scenes()[name]
     renderer.set_config(tile=tile)
     render_gpu(renderer, s)
     tx, ty = oracle.tile_counts(s.cams, tile)
