@@ -11,15 +11,16 @@
 //     of up to 512 keys (nearly all) are sorted by one warp each with a
 //     bitonic network, up to 256 keys in registers (shuffles only) and 257 to
 //     512 in shared memory; longer segments are listed and sorted by one CTA
-//     each, up to 4096 keys with a bitonic network in shared memory, beyond
-//     with an LSD radix sort on the 8-bit digits that differ within the
+//     each with LSD radix passes on the 8-bit digits that differ within the
 //     segment (usually not the depth's exponent byte nor the face index's
-//     upper bytes) through global memory.
+//     upper bytes), in shared memory up to 4096 keys and through global
+//     memory beyond.
 //
 // Keys are unique (face ids are), so the result is the unique (tile, depth,
 // face) order whatever order step 1 put the keys of a segment in.
 
 #include <algorithm>
+#include <atomic>
 
 #include "gmr_internal.cuh"
 
@@ -29,7 +30,7 @@ namespace {
 
 constexpr int kSegThreads = 256;
 constexpr int kSegWarps = kSegThreads / 32;
-constexpr int kSegSmem = 2048;  // keys sorted in shared memory
+constexpr int kSegSmem = 4096;  // keys of a long segment sorted in shared memory
 constexpr int kRadix = 256;
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
@@ -77,67 +78,59 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* sw) {
   return r;
 }
 
-struct SegSmem {
-  union {
-    struct {
-      unsigned long long a[kSegSmem];
-      unsigned long long b[kSegSmem];
-    };
-    unsigned long long all[2 * kSegSmem];  // the CTA bitonic sort's buffer
-  };
-  uint32_t wcnt[kSegWarps][kRadix];  // per warp, per digit
-  uint32_t base[kRadix];             // running start of each digit
-  uint32_t sw[32];
-  unsigned long long red_and[kSegWarps], red_or[kSegWarps];
-};
-
-// Stable counting pass on digit `shift` of keys src[0, L) -> dst (shared or
-// global memory). Items are taken in chunks of kSegThreads in order; in a
-// chunk warp w takes items [w*32, w*32 + 32) and ranks equal digits by lane.
-__device__ void seg_radix_pass(const unsigned long long* src, unsigned long long* dst, int L, int shift,
-                               SegSmem& sm) {
+// Stable LSD counting pass on the 8-bit digit at `shift` of keys src[0, n)
+// -> dst (shared or global memory), by the whole CTA with 3 barriers: warp w
+// owns the consecutive chunk [w C, (w + 1) C) of the keys (C a multiple of
+// 32), so the order of equal digits is chunk order, then round order within
+// a chunk, then lane order (`__match_any_sync` ranks equal digits among the
+// lanes of a round). hist holds kSegWarps x kRadix counters.
+__device__ void cta_radix_pass(const unsigned long long* src, unsigned long long* dst, int n, int shift,
+                               uint32_t* hist, uint32_t* sw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  // histogram of the whole segment -> exclusive digit starts
-  for (int d = threadIdx.x; d < kRadix; d += kSegThreads) sm.base[d] = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < L; i += kSegThreads) atomicAdd(&sm.base[(uint32_t)(src[i] >> shift) & 0xffu], 1u);
-  __syncthreads();
-  {
-    const uint32_t v = sm.base[threadIdx.x];
-    const uint32_t ex = cta_excl_scan(v, sm.sw);
-    sm.base[threadIdx.x] = ex;
-  }
-  __syncthreads();
-  for (int c0 = 0; c0 < L; c0 += kSegThreads) {
-    for (int d = lane; d < kRadix; d += 32) sm.wcnt[warp][d] = 0;
-    __syncwarp();
-    const int i = c0 + threadIdx.x;
-    const bool ok = i < L;
-    const unsigned long long k = ok ? src[i] : 0ull;
-    const uint32_t d = ok ? ((uint32_t)(k >> shift) & 0xffu) : (kRadix + lane);
+  const int C = ((n + kSegWarps * 32 - 1) / (kSegWarps * 32)) * 32;
+  const int c0 = min(n, warp * C), c1 = min(n, c0 + C);
+  uint32_t* h = hist + warp * kRadix;
+  for (int d = lane; d < kRadix; d += 32) h[d] = 0u;
+  __syncwarp();
+  // A: digit counts of this warp's chunk
+  for (int base = c0; base < c1; base += 32) {
+    const int i = base + lane;
+    const bool ok = i < c1;
+    const uint32_t d = ok ? (uint32_t)(src[i] >> shift) & 0xffu : (uint32_t)(kRadix + lane);
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lt);
-    if (ok && (peers & lt) == 0) sm.wcnt[warp][d] = __popc(peers);
-    __syncthreads();
-    // per digit: exclusive prefix over the warps of this chunk
-    {
-      const int dd = threadIdx.x;
-      uint32_t run = 0;
-#pragma unroll
-      for (int w = 0; w < kSegWarps; ++w) {
-        const uint32_t cnt = sm.wcnt[w][dd];
-        sm.wcnt[w][dd] = run;
-        run += cnt;
-      }
-      // sm.base[dd] is advanced after the scatter below (run = chunk count)
-      __syncthreads();
-      if (ok) dst[sm.base[d] + sm.wcnt[warp][d] + rank] = k;
-      __syncthreads();
-      sm.base[dd] += run;
-    }
-    __syncthreads();
+    if (ok && (peers & lt) == 0) h[d] += (uint32_t)__popc(peers);
+    __syncwarp();
   }
+  __syncthreads();
+  // B: start of every (digit, warp) run: digits in order, warps in order
+  {
+    const int d = threadIdx.x;  // kSegThreads == kRadix
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kSegWarps; ++w) {
+      const uint32_t c = hist[w * kRadix + d];
+      hist[w * kRadix + d] = run;
+      run += c;
+    }
+    const uint32_t start = cta_excl_scan(run, sw);  // barriers inside
+#pragma unroll
+    for (int w = 0; w < kSegWarps; ++w) hist[w * kRadix + d] += start;
+  }
+  __syncthreads();
+  // C: scatter, in the same order as A
+  for (int base = c0; base < c1; base += 32) {
+    const int i = base + lane;
+    const bool ok = i < c1;
+    const unsigned long long k = ok ? src[i] : 0ull;
+    const uint32_t d = ok ? (uint32_t)(k >> shift) & 0xffu : (uint32_t)(kRadix + lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (ok) dst[h[d] + __popc(peers & lt)] = k;
+    __syncwarp();
+    if (ok && (peers & lt) == 0) h[d] += (uint32_t)__popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
 }
 
 // Ascending bitonic sort of 32*KPL 64-bit keys held by one warp, element
@@ -287,87 +280,64 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
   }
 }
 
-// Ascending bitonic sort of L <= 2 kSegSmem 64-bit keys by the whole CTA in
-// shared memory (padded to the next power of two with the largest key):
-// every stage's compare-exchange pairs are spread over the threads, one
-// barrier per stage.
-__device__ void cta_sort_smem(const unsigned long long* __restrict__ gk, int L, uint32_t* __restrict__ out,
-                              unsigned long long* s) {
-  int N = 2;
-  while (N < L) N <<= 1;
-  for (int i = threadIdx.x; i < N; i += kSegThreads) s[i] = i < L ? gk[i] : ~0ull;
-  __syncthreads();
-  for (int k = 2; k <= N; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int p = threadIdx.x; p < (N >> 1); p += kSegThreads) {
-        const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-        const unsigned long long a = s[i], b = s[i + j];
-        if ((a > b) == ((i & k) == 0)) {
-          s[i] = b;
-          s[i + j] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < L; i += kSegThreads) out[i] = (uint32_t)s[i];
-  __syncthreads();
-}
-
-// Segments longer than kWarpSortMax: one CTA each; up to 2 kSegSmem keys a
-// bitonic sort in shared memory, beyond an LSD radix sort on the 8-bit
-// digits that differ within the segment, through global memory.
+// Segments longer than kWarpSortMax: one CTA each (a persistent grid over
+// the long list), LSD radix passes on the 8-bit digits that differ within the
+// segment, in dynamic shared memory up to kSegSmem keys and through global
+// memory beyond.
 __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
                                                            const Counters* __restrict__ counters,
                                                            const uint2* __restrict__ ranges,
                                                            unsigned long long* __restrict__ keys,
                                                            unsigned long long* __restrict__ keys_tmp,
                                                            uint32_t* __restrict__ pair_face) {
-  __shared__ SegSmem sm;
+  extern __shared__ __align__(16) unsigned long long s_dyn[];
+  unsigned long long* sa = s_dyn;                 // kSegSmem keys
+  unsigned long long* sb = s_dyn + kSegSmem;      // kSegSmem keys
+  uint32_t* hist = reinterpret_cast<uint32_t*>(s_dyn + 2 * kSegSmem);  // kSegWarps x kRadix
+  __shared__ uint32_t sw[32];
+  __shared__ unsigned long long red_and[kSegWarps], red_or[kSegWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nlong = counters->n_long;
   for (uint32_t li = blockIdx.x; li < nlong; li += gridDim.x) {
     const uint2 rg = ranges[long_list[li]];
     const int L = (int)(rg.y - rg.x);
     unsigned long long* gk = keys + rg.x;
-    unsigned long long* gt = keys_tmp + rg.x;
-    if (L <= 2 * kSegSmem) {
-      cta_sort_smem(gk, L, pair_face + rg.x, sm.all);
-      continue;
-    }
+    const bool in_smem = L <= kSegSmem;
     unsigned long long a = ~0ull, o = 0ull;
     for (int i = threadIdx.x; i < L; i += kSegThreads) {
       const unsigned long long k = gk[i];
       a &= k;
       o |= k;
+      if (in_smem) sa[i] = k;
     }
 #pragma unroll
     for (int s2 = 16; s2 > 0; s2 >>= 1) {
       a &= __shfl_xor_sync(0xffffffffu, a, s2);
       o |= __shfl_xor_sync(0xffffffffu, o, s2);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-      sm.red_and[warp] = a;
-      sm.red_or[warp] = o;
+      red_and[warp] = a;
+      red_or[warp] = o;
     }
     __syncthreads();
     unsigned long long diff = 0;
 #pragma unroll
-    for (int w = 0; w < kSegWarps; ++w) diff |= sm.red_and[w] ^ sm.red_or[w];
-    unsigned long long* src = gk;
-    unsigned long long* dst = gt;
+    for (int w = 0; w < kSegWarps; ++w) diff |= red_and[w] ^ red_or[w];
+    unsigned long long* src = in_smem ? sa : gk;
+    unsigned long long* dst = in_smem ? sb : keys_tmp + rg.x;
     for (int shift = 0; shift < 64; shift += 8) {
       if (((diff >> shift) & 0xffull) == 0) continue;  // uniform over the CTA
-      seg_radix_pass(src, dst, L, shift, sm);
+      cta_radix_pass(src, dst, L, shift, hist, sw);
       unsigned long long* tmp = src;
       src = dst;
       dst = tmp;
     }
-    __syncthreads();
     for (int i = threadIdx.x; i < L; i += kSegThreads) pair_face[rg.x + i] = (uint32_t)src[i];
     __syncthreads();
   }
 }
+
+constexpr size_t kLongSortSmem = (2 * kSegSmem) * sizeof(unsigned long long) + kSegWarps * kRadix * sizeof(uint32_t);
 
 // Debug: global tile id of every sorted pair, from the ranges.
 __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* __restrict__ tile_ids) {
@@ -392,8 +362,18 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
     k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kTileSortThreads, 0, s>>>(
         ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.counters,
         ws.cap_pairs);
-    k_long_sort<<<148 * 3, kSegThreads, 0, s>>>(ws.long_tiles, ws.counters, ws.tile_range, ws.pair_key[0],
-                                               ws.pair_key[1], ws.pair_face);
+    // the dynamic shared memory limit is a per-device attribute of the kernel
+    static std::atomic<bool> smem_set[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !smem_set[dev].load()) {
+      e = cudaFuncSetAttribute(k_long_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSortSmem);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) smem_set[dev].store(true);
+    }
+    k_long_sort<<<148 * 3, kSegThreads, kLongSortSmem, s>>>(ws.long_tiles, ws.counters, ws.tile_range,
+                                                             ws.pair_key[0], ws.pair_key[1], ws.pair_face);
     *launches += 2;
   }
   return cudaGetLastError();
