@@ -119,46 +119,53 @@ constexpr int kSingleThreads = 1024;
 constexpr int kSingleChunk = kSingleThreads * kScanItems;  // 8192
 constexpr int64_t kSingleMax = 4 * kSingleChunk;
 
+// One CTA; each thread owns 8 consecutive values of a chunk, loaded and
+// stored as two 16-byte vectors (no shared-memory transpose), with a scalar
+// path for the ragged last chunk.
 __global__ void __launch_bounds__(kSingleThreads) k_scan_single(uint32_t* __restrict__ src, int64_t n,
                                                                 uint32_t* __restrict__ out,
                                                                 uint32_t* __restrict__ total) {
   __shared__ uint32_t sw[33];
-  __shared__ uint32_t tile[kSingleChunk];
   uint32_t carry = 0;
   for (int64_t base = 0; base < n; base += kSingleChunk) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    const bool full = i0 + kScanItems <= n;
+    if (full) {
+      const uint4 a = *reinterpret_cast<const uint4*>(src + i0);
+      const uint4 b = *reinterpret_cast<const uint4*>(src + i0 + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(src + i0) = z;
+      *reinterpret_cast<uint4*>(src + i0 + 4) = z;
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      const int j = k * kSingleThreads + threadIdx.x;
-      if (base + j < n) {
-        tile[j] = src[base + j];
-        src[base + j] = 0u;
-      } else {
-        tile[j] = 0u;
+      for (int k = 0; k < kScanItems; ++k) {
+        v[k] = i0 + k < n ? src[i0 + k] : 0u;
+        if (i0 + k < n) src[i0 + k] = 0u;
       }
     }
-    __syncthreads();
-    uint32_t v[kScanItems];
     uint32_t acc = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      v[k] = tile[threadIdx.x * kScanItems + k];
-      acc += v[k];
-    }
+    for (int k = 0; k < kScanItems; ++k) acc += v[k];
     uint32_t tot;
     uint32_t pre = block_excl_scan(acc, sw, &tot) + carry;
+    uint32_t o[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      tile[threadIdx.x * kScanItems + k] = pre;
+      o[k] = pre;
       pre += v[k];
     }
-    __syncthreads();
+    if (full) {
+      *reinterpret_cast<uint4*>(out + i0) = make_uint4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<uint4*>(out + i0 + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      const int j = k * kSingleThreads + threadIdx.x;
-      if (base + j < n) out[base + j] = tile[j];
+      for (int k = 0; k < kScanItems; ++k)
+        if (i0 + k < n) out[i0 + k] = o[k];
     }
     carry += tot;
-    __syncthreads();
   }
   if (threadIdx.x == 0 && total) *total = carry;
 }
@@ -173,7 +180,9 @@ cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* to
     if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
     return cudaGetLastError();
   }
-  if (n <= kSingleMax) {
+  // the vector path needs 16-byte aligned arrays (workspace allocations are)
+  const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+  if (n <= kSingleMax && aligned) {
     k_scan_single<<<1, kSingleThreads, 0, s>>>(src, n, out, total);
     *launches += 1;
     return cudaGetLastError();
