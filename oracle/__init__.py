@@ -47,9 +47,9 @@ def lib():
         L.gmr_oracle_render.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P,
                                         P, P, P, P, P, P]
         L.gmr_oracle_backward.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P,
-                                          P, P, P, P, P]
+                                          P, P, P, P, P, P]
         L.gmr_oracle_jvp.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P, P,
-                                     P, P, P, P]
+                                     P, P, P, P, P]
         _LIB = L
     return _LIB
 
@@ -202,8 +202,9 @@ def render(scene, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, bands
     return {"rgb": out, "T": T, "last_face": last, "n_contrib": nc, "flags": fl}
 
 
-def backward(scene, dLdI, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, opacity_scalar=1.0):
-    """Reverse-mode FP64 gradients for dL/dI given at ``pixels``."""
+def backward(scene, dLdI, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, opacity_scalar=1.0, dLdT=None):
+    """Reverse-mode FP64 gradients for dL/dI (and optionally dL/dT_final)
+    given at ``pixels``."""
     if pixels is None:
         pixels = all_pixels(scene.cams)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
@@ -215,17 +216,20 @@ def backward(scene, dLdI, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=1
     drgb = np.zeros(c.shape)
     dop = np.zeros(F)
     rec = np.zeros((C * F, 9))
+    gT = None if dLdT is None else np.ascontiguousarray(np.asarray(dLdT, dtype=np.float64).reshape(-1))
+    assert gT is None or len(gT) == len(pix)
     rc = lib().gmr_oracle_backward(V, _p(v), F, _p(f), _p(c), color_mode, _p(o), opacity_scalar, cov_mode, C,
                                    _p(cf), _p(ci), _p(b), tile, len(pix), _p(pix), _p(g), _p(dV), _p(drgb),
-                                   _p(dop), _p(rec))
+                                   _p(dop), _p(rec), _p(gT))
     if rc != 0:
         raise ValueError(f"oracle backward failed ({rc})")
     return {"dverts": dV, "drgb": drgb, "dopacity": dop, "rec": rec}
 
 
 def jvp(scene, w, dverts=None, drgb=None, dop=None, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16,
-        opacity_scalar=1.0):
-    """Forward-mode d/de sum <w, I(x + e dir)> with dual numbers."""
+        opacity_scalar=1.0, wT=None):
+    """Forward-mode d/de (sum <w, I(x + e dir)> + sum wT T_final) with dual
+    numbers."""
     if pixels is None:
         pixels = all_pixels(scene.cams)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
@@ -239,7 +243,8 @@ def jvp(scene, w, dverts=None, drgb=None, dop=None, pixels=None, cov_mode=0, col
     out = np.zeros(1)
     rc = lib().gmr_oracle_jvp(len(v), _p(v), len(f), _p(f), _p(c), color_mode, _p(o), opacity_scalar, cov_mode,
                               len(scene.cams), _p(cf), _p(ci), _p(b), tile, len(pix), _p(pix), _p(ww), _p(dv),
-                              _p(dc), _p(do), _p(out))
+                              _p(dc), _p(do), _p(out),
+                              _p(None if wT is None else np.ascontiguousarray(np.asarray(wT, dtype=np.float64))))
     if rc != 0:
         raise ValueError(f"oracle jvp failed ({rc})")
     return float(out[0])

@@ -943,13 +943,15 @@ int gmr_oracle_render(int V, const float* verts, int F, const int* faces, const 
 }
 
 // Reverse pass: given dL/dI at the listed pixels (npix x 3; all other pixels
-// contribute nothing), writes dL/dverts (V x 3), dL/drgb (shape of rgb) and
+// contribute nothing) and optionally dL/dT_final there (npix; NULL: zero),
+// writes dL/dverts (V x 3), dL/drgb (shape of rgb) and
 // dL/dopacity (F, when opacity is per face). rec_grads, if not null, receives
 // per (view, face) the 9 values (du_x, du_y, dQ_a, dQ_b, dQ_c, do, dr, dg, db).
 int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, const float* rgb, int color_mode,
                         const float* opacity, float opacity_scalar, int cov_mode, int C, const float* cam_f,
                         const int* cam_i, const double* bg, int tile, long long npix, const int* pix,
-                        const double* dLdI, double* dverts, double* drgb, double* dopac, double* rec_grads) {
+                        const double* dLdI, double* dverts, double* drgb, double* dopac, double* rec_grads,
+                        const double* dLdT) {
   Scene s;
   build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile);
   if (!check_scene(s)) return -1;
@@ -962,7 +964,8 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
     int view = pix[3 * i], x = pix[3 * i + 1], y = pix[3 * i + 2];
     if (view < 0 || view >= C) return -3;
     const double* g = dLdI + 3 * i;
-    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+    const double gT = dLdT ? dLdT[i] : 0.0;
+    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 && gT == 0.0) continue;
     rec.clear();
     double o[3], Tf;
     composite_pixel<double>(s, P, view, x, y, o, &Tf, nullptr, nullptr, nullptr, nullptr, &rec);
@@ -978,6 +981,8 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
         dcol[3 * (size_t)f + ch] += cb.alpha * cb.Tb * g[ch];
         dalpha += g[ch] * (col[ch] * cb.Tb - S[ch] / (1.0 - cb.alpha));
       }
+      // final transmittance T_N = prod_j (1 - alpha_j): dT_N/dalpha_i = -T_N / (1 - alpha_i)
+      dalpha += gT * (-Tf / (1.0 - cb.alpha));
       for (int ch = 0; ch < 3; ++ch) S[ch] += col[ch] * cb.alpha * cb.Tb;
       if (cb.clamped) continue;  // alpha = 0.99 does not depend on o or the geometry
       // alpha = o exp(power)
@@ -1052,13 +1057,14 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
   return 0;
 }
 
-// Forward-mode directional derivative d/de sum_pixels <w, I(x + e dir)> at
-// e = 0, evaluated with dual numbers through the same forward code (eigen
-// route of Eq. 10-13 included). Returns it in *out.
+// Forward-mode directional derivative d/de sum_pixels (<w, I(x + e dir)> +
+// wT T_final(x + e dir)) at e = 0 (wT may be NULL), evaluated with dual
+// numbers through the same forward code (eigen route of Eq. 10-13 included).
+// Returns it in *out.
 int gmr_oracle_jvp(int V, const float* verts, int F, const int* faces, const float* rgb, int color_mode,
                    const float* opacity, float opacity_scalar, int cov_mode, int C, const float* cam_f,
                    const int* cam_i, const double* bg, int tile, long long npix, const int* pix, const double* w,
-                   const double* dverts, const double* drgb, const double* dop, double* out) {
+                   const double* dverts, const double* drgb, const double* dop, double* out, const double* wT) {
   Scene s;
   build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile);
   if (!check_scene(s)) return -1;
@@ -1069,9 +1075,10 @@ int gmr_oracle_jvp(int V, const float* verts, int F, const int* faces, const flo
   for (long long i = 0; i < npix; ++i) {
     int view = pix[3 * i], x = pix[3 * i + 1], y = pix[3 * i + 2];
     if (view < 0 || view >= C) return -3;
-    Dual o[3];
-    composite_pixel<Dual>(s, P, view, x, y, o, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    Dual o[3], Tf;
+    composite_pixel<Dual>(s, P, view, x, y, o, &Tf, nullptr, nullptr, nullptr, nullptr, nullptr);
     for (int k = 0; k < 3; ++k) acc += w[3 * i + k] * o[k].d;
+    if (wT) acc += wT[i] * Tf.d;
   }
   *out = acc;
   return 0;
