@@ -233,6 +233,28 @@ GMR_API gmr_status gmr_render_fwd_l2(gmr_ctx* ctx, const float* verts, int32_t V
 GMR_API gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dverts, float* dL_drgb,
                           float* dL_dopacity, int32_t accumulate, gmr_stream stream);
 
+/* gmr_render_bwd with, in addition, the gradient of the loss with respect
+ * to the final transmittance of every pixel (the silhouette loss of Sec. 3.1
+ * compares the rendered mask 1 - T_final with the target silhouette):
+ *  dL_dimages   as in gmr_render_bwd, or NULL for zero,
+ *  dL_dtfinal   packed, offsets[C] floats (same layout as t_final), or NULL
+ *               for zero; not both NULL.
+ * Since T_final = prod_j (1 - alpha_j), dL/dalpha_i gains
+ * -dL/dT_final T_final / (1 - alpha_i); colours are unaffected. */
+GMR_API gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtfinal,
+                                     float* dL_dverts, float* dL_drgb, float* dL_dopacity, int32_t accumulate,
+                                     gmr_stream stream);
+
+/* Silhouette loss (Sec. 3.1: binary cross-entropy between the rendered mask
+ * and the target silhouette) over n pixels, the rendered mask being
+ * M = 1 - T_final clamped to [1e-6, 1 - 1e-6]:
+ * loss = -(1/n) sum (m log M + (1 - m) log(1 - M)) (device double, FP32
+ * terms and partial sums, FP64 above the warp), and dL_dtfinal =
+ * (1/n) (m / M - (1 - m) / (1 - M)) where M is not clamped, 0 where it is.
+ * t_final, mask and dL_dtfinal are n device floats (mask in [0, 1]). */
+GMR_API gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* mask, int64_t n,
+                                      float* dL_dtfinal, double* loss, gmr_stream stream);
+
 /* Squared-error loss sum((img - target)^2) over n floats and its gradient
  * 2 (img - target). loss is a device double (overwritten); dL_dimg may
  * alias neither input. Deterministic (fixed reduction order); FP32 sums of

@@ -544,8 +544,30 @@ gmr_status gmr_render_fwd_l2(gmr_ctx* ctx, const float* verts, int32_t V, const 
 gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dverts, float* dL_drgb,
                           float* dL_dopacity, int32_t accumulate, gmr_stream stream) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
-  if (!ctx->fwd_valid) return fail(ctx, GMR_ERR_STATE, "gmr_render_bwd without a preceding gmr_render_fwd");
   if (!dL_dimages) return fail(ctx, GMR_ERR_INVALID_ARG, "null dL_dimages");
+  return gmr_render_bwd_ex(ctx, dL_dimages, nullptr, dL_dverts, dL_drgb, dL_dopacity, accumulate, stream);
+}
+
+gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* mask, int64_t n, float* dL_dtfinal,
+                              double* loss, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!t_final || !mask || !dL_dtfinal)) || !loss)
+    return fail(ctx, GMR_ERR_INVALID_ARG, "bad silhouette loss arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+  gmr_status st = ensure_loss(ctx, gmr::bce_partials_needed(n), cap_status != cudaStreamCaptureStatusNone);
+  if (st != GMR_OK) return st;
+  GMR_CUDA(ctx, gmr::launch_silhouette_bce(t_final, mask, n, dL_dtfinal, loss, ctx->ws.loss_part, ctx->ws.cap_loss,
+                                           s, &ctx->launches));
+  return GMR_OK;
+}
+
+gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtfinal, float* dL_dverts,
+                             float* dL_drgb, float* dL_dopacity, int32_t accumulate, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (!ctx->fwd_valid) return fail(ctx, GMR_ERR_STATE, "gmr_render_bwd without a preceding gmr_render_fwd");
+  if (!dL_dimages && !dL_dtfinal) return fail(ctx, GMR_ERR_INVALID_ARG, "null dL_dimages and dL_dtfinal");
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& w = ctx->ws;
   const gmr_config& cfg = ctx->fwd_cfg;
@@ -563,7 +585,7 @@ gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dvert
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, w, w.pair_face, w.views, C, F,
-                                         ctx->n_tiles, cfg.bg, dL_dimages, s, &ctx->launches));
+                                         ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal, s, &ctx->launches));
   }
   // S9: projection + conversion backward, vertex scatter
   {

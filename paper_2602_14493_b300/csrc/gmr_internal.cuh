@@ -315,12 +315,17 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
                               cudaStream_t s, int64_t* launches);
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, cudaStream_t s, int64_t* launches);
+                              const float* dL_dimages, const float* dL_dT, cudaStream_t s, int64_t* launches);
 // partials: l2_loss_partials_needed(n) doubles; partials[0] holds a ticket
 // counter that must be zero before the first call (every call leaves it zero)
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
 int64_t l2_loss_partials_needed(int64_t n);
+// silhouette binary cross-entropy of the mask 1 - T_final against a target
+// mask (mean over n pixels), with dL/dT_final; partials as for the L2 loss
+cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64_t n, float* dL_dT, double* loss,
+                                  double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
+int64_t bce_partials_needed(int64_t n);
 // *out = scale * sum of n floats (one CTA, fixed order, double-float sums)
 cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* out, cudaStream_t s,
                               int64_t* launches);

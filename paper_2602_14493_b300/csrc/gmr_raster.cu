@@ -457,8 +457,8 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
-    const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
-    float4* __restrict__ face_grad, Counters* __restrict__ counters) {
+    const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
+    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
@@ -493,19 +493,29 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     pcx[k] = (float)(px - axi) + 0.5f;
     pcy[k] = (float)(py - ayi) + 0.5f;
     bool inside = px < v.W && py < v.H;
+    float gT;
     if (inside) {
       int64_t pid = v.pix_base + (int64_t)py * v.W + px;
       T[k] = pix_T[pid];
       last[k] = pix_last[pid];
-      G0[k] = dL_dimg[3 * pid];
-      G1[k] = dL_dimg[3 * pid + 1];
-      G2[k] = dL_dimg[3 * pid + 2];
+      if (dL_dimg) {
+        G0[k] = dL_dimg[3 * pid];
+        G1[k] = dL_dimg[3 * pid + 1];
+        G2[k] = dL_dimg[3 * pid + 2];
+      } else {
+        G0[k] = G1[k] = G2[k] = 0.0f;
+      }
+      gT = dL_dT ? dL_dT[pid] : 0.0f;
     } else {
       T[k] = 1.0f;
       last[k] = 0;
       G0[k] = G1[k] = G2[k] = 0.0f;
+      gT = 0.0f;
     }
-    SG[k] = T[k] * (bg0 * G0[k] + bg1 * G1[k] + bg2 * G2[k]);
+    // the background term T_final bg and the final transmittance itself
+    // (dL/dT_final, a silhouette loss) both enter as "colour behind every
+    // Gaussian": a fourth channel with Gaussian colour 0 and background 1
+    SG[k] = T[k] * (bg0 * G0[k] + bg1 * G1[k] + bg2 * G2[k] + gT);
     tmax = max(tmax, last[k]);
     blk[k] = PixMap<TS, NT>::block(k);
   }
@@ -686,9 +696,9 @@ void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
 
 template <int TS, int NT, int BATCH>
 void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, const float* dL, cudaStream_t s) {
+                int32_t F, const float* bg, const float* dL, const float* dLdT, cudaStream_t s) {
   k_raster_bwd<TS, NT, BATCH><<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
-                                                                 ws.face_col, views, C, F, bg[0], bg[1], bg[2], dL,
+                                                                 ws.face_col, views, C, F, bg[0], bg[1], bg[2], dL, dLdT,
                                                                  ws.pix_T, ws.pix_last, ws.rec_grad, ws.face_grad,
                                                                  ws.counters);
 }
@@ -716,11 +726,11 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
 
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, cudaStream_t s, int64_t* launches) {
+                              const float* dL_dimages, const float* dL_dT, cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, s)
+  bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
@@ -742,6 +752,50 @@ cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* re
 cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* out, cudaStream_t s,
                               int64_t* launches) {
   k_sum_partials<<<1, 1024, 0, s>>>(x, n, scale, out);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+// Silhouette loss (Sec. 3.1: binary cross-entropy between the rendered mask
+// and the target silhouette), mask M = 1 - T_final clamped to
+// [kBceEps, 1 - kBceEps]: L = -(1/n) sum (m log M + (1 - m) log(1 - M)),
+// dL/dT_final = (1/n) (m / M - (1 - m) / (1 - M)) where M is not clamped, 0
+// where it is. 1 - M is taken as T itself (no cancellation).
+constexpr float kBceEps = 1e-6f;
+constexpr int kBceItems = 16;
+
+__global__ void __launch_bounds__(kLossThreads) k_silhouette_bce(const float* __restrict__ t_final,
+                                                                  const float* __restrict__ mask, int64_t n,
+                                                                  float inv_n, float* __restrict__ dL_dT,
+                                                                  double* __restrict__ part, double* __restrict__ loss) {
+  const int64_t base = (int64_t)blockIdx.x * kLossThreads * kBceItems;
+  float acc = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < kBceItems; ++k) {
+    const int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
+    if (i < n) {
+      const float T = t_final[i], m = mask[i];
+      const float Mraw = 1.0f - T;
+      const float M = fminf(fmaxf(Mraw, kBceEps), 1.0f - kBceEps);
+      const float Tc = fminf(fmaxf(T, kBceEps), 1.0f - kBceEps);  // 1 - M
+      acc -= m * logf(M) + (1.0f - m) * logf(Tc);
+      const bool inside = Mraw > kBceEps && Mraw < 1.0f - kBceEps;
+      dL_dT[i] = inside ? inv_n * (m / M - (1.0f - m) / Tc) : 0.0f;
+    }
+  }
+  // the loss is the mean: scale the FP32 partial here (exact power-of-two
+  // scalings aside, one rounding per thread)
+  loss_partial_and_finish<kLossThreads>(acc * inv_n, part, loss);
+}
+
+int64_t bce_partials_needed(int64_t n) { return 1 + (n + kLossThreads * kBceItems - 1) / (kLossThreads * kBceItems); }
+
+cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64_t n, float* dL_dT, double* loss,
+                                  double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches) {
+  const int64_t nb = bce_partials_needed(n) - 1;
+  if (nb + 1 > n_partials) return cudaErrorInvalidValue;
+  if (nb == 0) return cudaMemsetAsync(loss, 0, sizeof(double), s);
+  k_silhouette_bce<<<(unsigned)nb, kLossThreads, 0, s>>>(t_final, mask, n, 1.0f / (float)n, dL_dT, partials, loss);
   *launches += 1;
   return cudaGetLastError();
 }

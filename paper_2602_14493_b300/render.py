@@ -216,8 +216,14 @@ class Renderer:
         self._saved = (verts, faces, rgb, opacity)
         return images, grad, loss
 
-    def backward(self, dL_dimages, dverts=None, drgb=None, dopacity=None, accumulate=False, stream=None):
-        _check_dev(dL_dimages, "dL_dimages", torch.float32)
+    def backward(self, dL_dimages, dverts=None, drgb=None, dopacity=None, accumulate=False, stream=None,
+                 dL_dtfinal=None):
+        """Gradients of the last forward from dL/dimages and/or dL/dT_final
+        (either may be None, not both)."""
+        if dL_dimages is not None:
+            _check_dev(dL_dimages, "dL_dimages", torch.float32)
+        if dL_dtfinal is not None:
+            _check_dev(dL_dtfinal, "dL_dtfinal", torch.float32)
         verts, faces, rgb, opacity = self._saved
         dev = verts.device
         if dverts is None:
@@ -226,9 +232,23 @@ class Renderer:
             drgb = torch.empty_like(rgb)
         if dopacity is None and opacity is not None:
             dopacity = torch.empty_like(opacity)
-        self._check(self._L.gmr_render_bwd(self._ctx, _ptr(dL_dimages), _ptr(dverts), _ptr(drgb), _ptr(dopacity),
-                                           1 if accumulate else 0, _stream(stream)), "gmr_render_bwd")
+        self._check(self._L.gmr_render_bwd_ex(self._ctx, _ptr(dL_dimages), _ptr(dL_dtfinal), _ptr(dverts),
+                                              _ptr(drgb), _ptr(dopacity), 1 if accumulate else 0, _stream(stream)),
+                    "gmr_render_bwd_ex")
         return dverts, drgb, dopacity
+
+    def silhouette_bce(self, t_final, mask, grad=None, loss=None, stream=None):
+        """Binary cross-entropy of the rendered mask 1 - t_final against
+        mask (mean over pixels); returns (loss, dL/dt_final)."""
+        _check_dev(t_final, "t_final", torch.float32)
+        _check_dev(mask, "mask", torch.float32)
+        if grad is None:
+            grad = torch.empty_like(t_final)
+        if loss is None:
+            loss = torch.empty((), device=t_final.device, dtype=torch.float64)
+        self._check(self._L.gmr_silhouette_bce(self._ctx, _ptr(t_final), _ptr(mask), t_final.numel(), _ptr(grad),
+                                               _ptr(loss), _stream(stream)), "gmr_silhouette_bce")
+        return loss, grad
 
     def l2_loss(self, img, target, grad=None, loss=None, stream=None):
         _check_dev(img, "img", torch.float32)
@@ -342,6 +362,31 @@ class GMRRender(torch.autograd.Function):
         if r.fwd_token != ctx.token:
             raise _lib.GmrError("the renderer ran another forward before this backward")
         dverts, drgb, dop = r.backward(dimg.contiguous())
+        return dverts, drgb, (dop if ctx.has_opacity else None), None, None, None
+
+
+class GMRRenderWithT(torch.autograd.Function):
+    """images, t_final = GMRRenderWithT.apply(verts, rgb, opacity, faces,
+    cams, renderer): as GMRRender, with the final transmittance (1 - the
+    rendered silhouette) as a second differentiable output."""
+
+    @staticmethod
+    def forward(ctx, verts, rgb, opacity, faces, cams, renderer: Renderer):
+        images, t_final = renderer.forward(verts, faces, rgb, opacity, cams, want_t=True)
+        ctx.renderer = renderer
+        ctx.token = renderer.fwd_token
+        ctx.has_opacity = opacity is not None
+        return images, t_final
+
+    @staticmethod
+    def backward(ctx, dimg, dt):
+        r: Renderer = ctx.renderer
+        if r.fwd_token != ctx.token:
+            raise _lib.GmrError("the renderer ran another forward before this backward")
+        if dimg is None and dt is None:
+            return None, None, None, None, None, None
+        dverts, drgb, dop = r.backward(None if dimg is None else dimg.contiguous(),
+                                       dL_dtfinal=None if dt is None else dt.contiguous())
         return dverts, drgb, (dop if ctx.has_opacity else None), None, None, None
 
 

@@ -91,3 +91,32 @@ def test_autograd_matches_central_differences():
     assert cos > 0.999
     assert err < 2e-2
     r.close()
+
+
+def test_autograd_with_final_transmittance():
+    """GMRRenderWithT: a loss on the images and the silhouette 1 - T_final
+    gives the same gradients as gmr_render_bwd_ex called directly (up to the
+    order of the float atomics)."""
+    from paper_2602_14493_b300 import GMRRenderWithT, Renderer, camera_array
+
+    s = gi.scene_single_view()
+    r = Renderer()
+    v, f, c, o = to_dev(s)
+    cams = camera_array(s.cams)
+    vr, cr, orr = v.clone().requires_grad_(True), c.clone().requires_grad_(True), o.clone().requires_grad_(True)
+    img, T = GMRRenderWithT.apply(vr, cr, orr, f, cams, r)
+    wi = torch.sin(torch.arange(img.numel(), device=DEV, dtype=torch.float32)).reshape(img.shape)
+    wt = torch.cos(torch.arange(T.numel(), device=DEV, dtype=torch.float32))
+    ((img * wi).sum() + (T * wt).sum()).backward()
+    r.forward(v, f, c, o, cams)
+    dv, dc, do = r.backward(wi, dL_dtfinal=wt)
+    torch.cuda.synchronize()
+    # equal up to the order of the float atomics of the two runs
+    for a, b in ((vr.grad, dv), (cr.grad, dc), (orr.grad, do)):
+        assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+    # silhouette only
+    vr.grad = None
+    img, T = GMRRenderWithT.apply(vr, cr, orr, f, cams, r)
+    (1.0 - T).sum().backward()
+    assert vr.grad is not None and float(vr.grad.abs().max()) > 0
+    r.close()

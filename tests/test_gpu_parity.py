@@ -222,3 +222,62 @@ def test_per_vertex_colour_gradients():
     assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
     assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
     r.close()
+
+
+# ------------------------------------------------------------------ silhouette
+@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven"])
+@pytest.mark.parametrize("with_image", [False, True])
+def test_final_transmittance_gradients_match_oracle(name, with_image):
+    """dL/dT_final (the silhouette loss's gradient) through gmr_render_bwd_ex,
+    alone and with dL/dI, against the oracle's reverse pass."""
+    from paper_2602_14493_b300 import Renderer
+
+    r = Renderer(bg=(0.2, 0.1, 0.4))
+    s = _scenes()[name]
+    ref = oracle.render(s, bg=(0.2, 0.1, 0.4))
+    rng = np.random.default_rng(21)
+    gT = rng.normal(size=ref["T"].shape).astype(np.float32)
+    gT[ref["flags"] != 0] = 0.0
+    g = rng.normal(size=ref["rgb"].shape).astype(np.float32)
+    g[ref["flags"] != 0] = 0.0
+    if not with_image:
+        g[:] = 0.0
+    (v, f, c, o), img, T = render_gpu(r, s)
+    dv, dc, do = r.backward(torch.from_numpy(g).to(DEV) if with_image else None,
+                            dL_dtfinal=torch.from_numpy(gT).to(DEV))
+    torch.cuda.synchronize()
+    ob = oracle.backward(s, g.astype(np.float64), bg=(0.2, 0.1, 0.4), dLdT=gT.astype(np.float64))
+    assert np.abs(ob["dverts"]).max() > 0
+    assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(do.cpu().numpy(), ob["dopacity"]) <= GRAD_TOL
+    if with_image:
+        assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    else:
+        assert np.all(dc.cpu().numpy() == 0.0)
+    r.close()
+
+
+def test_silhouette_bce_against_fp64():
+    """The loss and dL/dT_final of gmr_silhouette_bce against the same
+    formula in FP64 on random transmittances (including clamped ends) and
+    binary and fractional masks."""
+    from paper_2602_14493_b300 import Renderer
+
+    rng = np.random.default_rng(5)
+    n = 100003
+    T = rng.uniform(1e-4, 1.0, n).astype(np.float32)
+    T[:50] = 1.0  # empty pixels: mask 0 exactly, clamped
+    m = (rng.random(n) < 0.5).astype(np.float32)
+    m[::7] = rng.random(len(m[::7])).astype(np.float32)
+    r = Renderer()
+    loss, grad = r.silhouette_bce(torch.from_numpy(T).to(DEV), torch.from_numpy(m).to(DEV))
+    eps = 1e-6
+    Td = T.astype(np.float64)
+    M = np.clip(1.0 - Td, eps, 1.0 - eps)
+    Tc = np.clip(Td, eps, 1.0 - eps)
+    ref = -np.mean(m * np.log(M) + (1.0 - m) * np.log(Tc))
+    inside = ((1.0 - Td) > eps) & ((1.0 - Td) < 1.0 - eps)
+    gref = np.where(inside, (m / M - (1.0 - m) / Tc) / n, 0.0)
+    assert abs(float(loss) - ref) <= 1e-5 * abs(ref)
+    np.testing.assert_allclose(grad.cpu().numpy(), gref, rtol=1e-5, atol=1e-12)
+    r.close()
