@@ -248,12 +248,12 @@ GMR_API gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, cons
 /* Silhouette loss (Sec. 3.1: binary cross-entropy between the rendered mask
  * and the target silhouette) over n pixels, the rendered mask being
  * M = 1 - T_final clamped to [1e-6, 1 - 1e-6]:
- * loss = -(1/n) sum (m log M + (1 - m) log(1 - M)) (device double, FP32
- * terms and partial sums, FP64 above the warp), and dL_dtfinal =
- * (1/n) (m / M - (1 - m) / (1 - M)) where M is not clamped, 0 where it is.
- * t_final, mask and dL_dtfinal are n device floats (mask in [0, 1]). */
+ * loss = -(weight/n) sum (m log M + (1 - m) log(1 - M)) (device double,
+ * FP32 terms and partial sums, FP64 above the warp), and dL_dtfinal =
+ * (weight/n) (m / M - (1 - m) / (1 - M)) where M is not clamped, 0 where it
+ * is. t_final, mask and dL_dtfinal are n device floats (mask in [0, 1]). */
 GMR_API gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* mask, int64_t n,
-                                      float* dL_dtfinal, double* loss, gmr_stream stream);
+                                      float weight, float* dL_dtfinal, double* loss, gmr_stream stream);
 
 /* Squared-error loss sum((img - target)^2) over n floats and its gradient
  * 2 (img - target). loss is a device double (overwritten); dL_dimg may
@@ -292,6 +292,19 @@ GMR_API gmr_status gmr_l2_loss_noalloc(const float* img, const float* target, in
 GMR_API gmr_status gmr_adam_step(gmr_ctx* ctx, float* params, const float* grads, float* m, float* v, int64_t n,
                                  int32_t group, float lr, float beta1, float beta2, float eps, int32_t step,
                                  gmr_stream stream);
+
+/* The two mesh regularisers of the fitting loop (Sec. 3.1: edge length and
+ * Laplacian smoothing), with these readings:
+ *  losses[0] = (1/3F) sum over the 3F face edges of (l - mean l)^2 (the
+ *              variance of the edge lengths: uniform edges),
+ *  losses[1] = (1/V) sum_v |v - n_v|^2, n_v the mean of the two other
+ *              vertices of every face at v (uniform weights),
+ * both unweighted, as device doubles; w_edge * dlosses[0]/dverts +
+ * w_lap * dlosses[1]/dverts is ADDED to dL_dverts (V x 3, may be NULL:
+ * losses only). Faces with an index outside [0, V) are skipped. */
+GMR_API gmr_status gmr_mesh_regularizers(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces,
+                                         int32_t F, float w_edge, float w_lap, float* dL_dverts, double* losses,
+                                         gmr_stream stream);
 
 /* Chamfer distance (the paper's CD, Sec. 3.1) between two device point sets
  * a (na x 3) and b (nb x 3), by brute force over all pairs:

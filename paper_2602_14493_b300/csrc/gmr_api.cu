@@ -357,7 +357,7 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
   Workspace& w = ctx->ws;
   void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.rec_contrib, w.face_col,
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
-                  w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters};
+                  w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
@@ -548,8 +548,8 @@ gmr_status gmr_render_bwd(gmr_ctx* ctx, const float* dL_dimages, float* dL_dvert
   return gmr_render_bwd_ex(ctx, dL_dimages, nullptr, dL_dverts, dL_drgb, dL_dopacity, accumulate, stream);
 }
 
-gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* mask, int64_t n, float* dL_dtfinal,
-                              double* loss, gmr_stream stream) {
+gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* mask, int64_t n, float weight,
+                              float* dL_dtfinal, double* loss, gmr_stream stream) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   if (n < 0 || (n > 0 && (!t_final || !mask || !dL_dtfinal)) || !loss)
     return fail(ctx, GMR_ERR_INVALID_ARG, "bad silhouette loss arguments");
@@ -558,8 +558,8 @@ gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* m
   GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
   gmr_status st = ensure_loss(ctx, gmr::bce_partials_needed(n), cap_status != cudaStreamCaptureStatusNone);
   if (st != GMR_OK) return st;
-  GMR_CUDA(ctx, gmr::launch_silhouette_bce(t_final, mask, n, dL_dtfinal, loss, ctx->ws.loss_part, ctx->ws.cap_loss,
-                                           s, &ctx->launches));
+  GMR_CUDA(ctx, gmr::launch_silhouette_bce(t_final, mask, n, weight, dL_dtfinal, loss, ctx->ws.loss_part,
+                                           ctx->ws.cap_loss, s, &ctx->launches));
   return GMR_OK;
 }
 
@@ -624,6 +624,23 @@ gmr_status gmr_adam_step(gmr_ctx* ctx, float* params, const float* grads, float*
     return fail(ctx, GMR_ERR_INVALID_ARG, "bad Adam hyper-parameters");
   GMR_CUDA(ctx, gmr::launch_adam(params, grads, m, v, n, group, lr, beta1, beta2, eps, step, (cudaStream_t)stream,
                                  &ctx->launches));
+  return GMR_OK;
+}
+
+gmr_status gmr_mesh_regularizers(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
+                                 float w_edge, float w_lap, float* dL_dverts, double* losses, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (V < 1 || F < 1 || !verts || !faces || !losses) return fail(ctx, GMR_ERR_INVALID_ARG, "bad regulariser arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+  // 2 leading floats hold the mean edge length (a double)
+  gmr_status st = grow<float>(ctx, &ctx->ws.reg_scratch, &ctx->ws.cap_reg, 2 + gmr::regularizer_scratch_floats(V, F),
+                              cap_status != cudaStreamCaptureStatusNone, "reg_scratch");
+  if (st != GMR_OK) return st;
+  GMR_CUDA(ctx, gmr::launch_regularizers(verts, V, faces, F, w_edge, w_lap, dL_dverts, losses,
+                                         ctx->ws.reg_scratch + 2, reinterpret_cast<double*>(ctx->ws.reg_scratch), s,
+                                         &ctx->launches));
   return GMR_OK;
 }
 

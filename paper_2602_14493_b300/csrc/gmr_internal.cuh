@@ -260,6 +260,8 @@ struct Workspace {
   // loss partial sums
   int64_t cap_loss = 0;
   double* loss_part = nullptr;
+  float* reg_scratch = nullptr;  // mesh regularisers (edge lengths, neighbour sums), 1 double of mean first
+  int64_t cap_reg = 0;
   // views
   int32_t cap_views = 0;
   ViewInfo* views = nullptr;
@@ -321,10 +323,12 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace&
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
 int64_t l2_loss_partials_needed(int64_t n);
-// silhouette binary cross-entropy of the mask 1 - T_final against a target
-// mask (mean over n pixels), with dL/dT_final; partials as for the L2 loss
-cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64_t n, float* dL_dT, double* loss,
-                                  double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
+// weight x the silhouette binary cross-entropy of the mask 1 - T_final
+// against a target mask (mean over n pixels), with dL/dT_final; partials as
+// for the L2 loss
+cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64_t n, float weight, float* dL_dT,
+                                  double* loss, double* partials, int64_t n_partials, cudaStream_t s,
+                                  int64_t* launches);
 int64_t bce_partials_needed(int64_t n);
 // *out = scale * sum of n floats (one CTA, fixed order, double-float sums)
 cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* out, cudaStream_t s,
@@ -332,6 +336,13 @@ cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* o
 // gmr_optim.cu
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int group, float lr, float b1,
                         float b2, float eps, int step, cudaStream_t s, int64_t* launches);
+// edge-length and Laplacian regularisers: losses[0..1] (unweighted), vertex
+// gradients (weighted) added to dverts (may be null); scratch holds
+// regularizer_scratch_floats(V, F) floats, mean_slot one double
+int64_t regularizer_scratch_floats(int32_t V, int32_t F);
+cudaError_t launch_regularizers(const float* verts, int32_t V, const int32_t* faces, int32_t F, float w_edge,
+                                float w_lap, float* dverts, double* losses, float* scratch, double* mean_slot,
+                                cudaStream_t s, int64_t* launches);
 // out[0] = mean_a min_b |a - b|^2, out[1] = mean_b min_a |b - a|^2; scratch: na + nb floats
 cudaError_t launch_chamfer(const float* a, int64_t na, const float* b, int64_t nb, float* scratch, double* out,
                            cudaStream_t s, int64_t* launches);

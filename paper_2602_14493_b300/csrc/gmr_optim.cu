@@ -107,4 +107,157 @@ cudaError_t launch_chamfer(const float* a, int64_t na, const float* b, int64_t n
   return launch_sum_floats(scratch + na, nb, 1.0 / (double)nb, out + 1, s, launches);
 }
 
+
+// ---------------------------------------------------------------- mesh regularisers
+// The two mesh regularisers of the fitting loop (Sec. 3.1; the paper names
+// them, this file takes the readings below), with their vertex gradients:
+//  * edge length: the variance of the lengths of the 3F face edges (interior
+//    edges counted once per face), L_edge = (1/3F) sum_i (l_i - mean l)^2,
+//    dL/dv = (2/3F) sum_{i at v} (l_i - mean l) (v - other end) / l_i (the
+//    mean's own derivative drops out, its deviations summing to zero);
+//  * Laplacian smoothing, uniform weights over the face neighbourhood:
+//    delta_v = v - (sum over faces at v of their two other vertices) /
+//    (2 |faces at v|), L_lap = (1/V) sum_v |delta_v|^2, dL/dv = (2/V)
+//    (delta_v - sum_w delta_w c_wv) with c_wv = (faces holding w and v) /
+//    (2 |faces at w|).
+// Gradients are added to dL/dverts with float atomics (weighted by w_edge,
+// w_lap); the losses (unweighted) are summed in a fixed order.
+
+namespace {
+
+constexpr int kRegThreads = 256;
+
+__device__ __forceinline__ bool reg_face(const int32_t* faces, int f, int32_t V, int& a, int& b, int& c) {
+  a = faces[3 * f]; b = faces[3 * f + 1]; c = faces[3 * f + 2];
+  return a >= 0 && a < V && b >= 0 && b < V && c >= 0 && c < V;
+}
+
+__device__ __forceinline__ float3 reg_v(const float* v, int i) { return make_float3(v[3 * i], v[3 * i + 1], v[3 * i + 2]); }
+
+// per face: the three edge lengths; neighbour sums and counts of its corners
+__global__ void __launch_bounds__(kRegThreads) k_reg_faces(const float* __restrict__ verts, int32_t V,
+                                                          const int32_t* __restrict__ faces, int32_t F,
+                                                          float* __restrict__ len, float* __restrict__ nsum,
+                                                          float* __restrict__ ncnt) {
+  const int f = blockIdx.x * kRegThreads + threadIdx.x;
+  if (f >= F) return;
+  int id[3];
+  if (!reg_face(faces, f, V, id[0], id[1], id[2])) {
+    len[3 * f] = len[3 * f + 1] = len[3 * f + 2] = 0.0f;
+    return;
+  }
+  float3 p[3] = {reg_v(verts, id[0]), reg_v(verts, id[1]), reg_v(verts, id[2])};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float3 a = p[k], b = p[(k + 1) % 3];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    len[3 * f + k] = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float3 u = p[(k + 1) % 3], w = p[(k + 2) % 3];
+    atomicAdd(nsum + 3 * id[k], u.x + w.x);
+    atomicAdd(nsum + 3 * id[k] + 1, u.y + w.y);
+    atomicAdd(nsum + 3 * id[k] + 2, u.z + w.z);
+    atomicAdd(ncnt + id[k], 2.0f);
+  }
+}
+
+// per face: edge-length gradient; len[] becomes (l - mean l)^2 for the loss sum
+__global__ void __launch_bounds__(kRegThreads) k_reg_edge_grad(const float* __restrict__ verts, int32_t V,
+                                                              const int32_t* __restrict__ faces, int32_t F,
+                                                              float* __restrict__ len, const double* __restrict__ len_mean,
+                                                              float w_edge, float* __restrict__ dverts) {
+  const int f = blockIdx.x * kRegThreads + threadIdx.x;
+  if (f >= F) return;
+  int id[3];
+  if (!reg_face(faces, f, V, id[0], id[1], id[2])) return;
+  const float lm = (float)*len_mean;
+  const float scale = w_edge * 2.0f / (3.0f * (float)F);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float l = len[3 * f + k];
+    const float dl = l - lm;
+    len[3 * f + k] = dl * dl;
+    if (!dverts || !(l > 0.0f)) continue;
+    const int ia = id[k], ib = id[(k + 1) % 3];
+    const float3 a = reg_v(verts, ia), b = reg_v(verts, ib);
+    const float s = scale * dl / l;
+    const float gx = s * (a.x - b.x), gy = s * (a.y - b.y), gz = s * (a.z - b.z);
+    atomicAdd(dverts + 3 * ia, gx); atomicAdd(dverts + 3 * ia + 1, gy); atomicAdd(dverts + 3 * ia + 2, gz);
+    atomicAdd(dverts + 3 * ib, -gx); atomicAdd(dverts + 3 * ib + 1, -gy); atomicAdd(dverts + 3 * ib + 2, -gz);
+  }
+}
+
+// per vertex: delta_v, |delta_v|^2, the direct gradient term; keeps
+// delta_v / (2 |faces at v|) in nsum for the scatter of the neighbour terms
+__global__ void __launch_bounds__(kRegThreads) k_reg_lap_vert(const float* __restrict__ verts, int32_t V,
+                                                             float* __restrict__ nsum, const float* __restrict__ ncnt,
+                                                             float* __restrict__ sq, float w_lap,
+                                                             float* __restrict__ dverts) {
+  const int v = blockIdx.x * kRegThreads + threadIdx.x;
+  if (v >= V) return;
+  const float n = ncnt[v];
+  float3 d = make_float3(0.f, 0.f, 0.f);
+  if (n > 0.0f) {
+    const float3 p = reg_v(verts, v);
+    d = make_float3(p.x - nsum[3 * v] / n, p.y - nsum[3 * v + 1] / n, p.z - nsum[3 * v + 2] / n);
+  }
+  sq[v] = d.x * d.x + d.y * d.y + d.z * d.z;
+  const float scale = w_lap * 2.0f / (float)V;
+  if (dverts) {
+    atomicAdd(dverts + 3 * v, scale * d.x);
+    atomicAdd(dverts + 3 * v + 1, scale * d.y);
+    atomicAdd(dverts + 3 * v + 2, scale * d.z);
+  }
+  const float inv = n > 0.0f ? 1.0f / n : 0.0f;
+  nsum[3 * v] = d.x * inv; nsum[3 * v + 1] = d.y * inv; nsum[3 * v + 2] = d.z * inv;
+}
+
+// per face: -(2/V) delta_w / (2 |faces at w|) to each of the two other corners of w
+__global__ void __launch_bounds__(kRegThreads) k_reg_lap_scatter(const int32_t* __restrict__ faces, int32_t F,
+                                                                int32_t V, const float* __restrict__ dn,
+                                                                float w_lap, float* __restrict__ dverts) {
+  const int f = blockIdx.x * kRegThreads + threadIdx.x;
+  if (f >= F) return;
+  int id[3];
+  if (!reg_face(faces, f, V, id[0], id[1], id[2])) return;
+  const float scale = -w_lap * 2.0f / (float)V;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int w = id[k];
+    const float gx = scale * dn[3 * w], gy = scale * dn[3 * w + 1], gz = scale * dn[3 * w + 2];
+#pragma unroll
+    for (int j = 1; j < 3; ++j) {
+      const int u = id[(k + j) % 3];
+      atomicAdd(dverts + 3 * u, gx); atomicAdd(dverts + 3 * u + 1, gy); atomicAdd(dverts + 3 * u + 2, gz);
+    }
+  }
+}
+
+}  // namespace
+
+int64_t regularizer_scratch_floats(int32_t V, int32_t F) { return 3 * (int64_t)F + 3 * (int64_t)V + 2 * (int64_t)V; }
+
+cudaError_t launch_regularizers(const float* verts, int32_t V, const int32_t* faces, int32_t F, float w_edge,
+                                float w_lap, float* dverts, double* losses, float* scratch, double* mean_slot,
+                                cudaStream_t s, int64_t* launches) {
+  float* len = scratch;                 // 3F
+  float* nsum = len + 3 * (int64_t)F;   // 3V
+  float* ncnt = nsum + 3 * (int64_t)V;  // V
+  float* sq = ncnt + V;                 // V
+  cudaError_t e = cudaMemsetAsync(nsum, 0, sizeof(float) * 4 * (size_t)V, s);  // nsum and ncnt
+  if (e != cudaSuccess) return e;
+  const unsigned gf = (unsigned)((F + kRegThreads - 1) / kRegThreads), gv = (unsigned)((V + kRegThreads - 1) / kRegThreads);
+  k_reg_faces<<<gf, kRegThreads, 0, s>>>(verts, V, faces, F, len, nsum, ncnt);
+  *launches += 1;
+  if ((e = launch_sum_floats(len, 3 * (int64_t)F, 1.0 / (3.0 * F), mean_slot, s, launches)) != cudaSuccess) return e;
+  k_reg_edge_grad<<<gf, kRegThreads, 0, s>>>(verts, V, faces, F, len, mean_slot, w_edge, dverts);
+  k_reg_lap_vert<<<gv, kRegThreads, 0, s>>>(verts, V, nsum, ncnt, sq, w_lap, dverts);
+  *launches += 2;
+  if (dverts) {
+    k_reg_lap_scatter<<<gf, kRegThreads, 0, s>>>(faces, F, V, nsum, w_lap, dverts);
+    *launches += 1;
+  }
+  if ((e = launch_sum_floats(len, 3 * (int64_t)F, 1.0 / (3.0 * F), losses, s, launches)) != cudaSuccess) return e;
+  return launch_sum_floats(sq, V, 1.0 / (double)V, losses + 1, s, launches);
+}
+
 }  // namespace gmr

@@ -760,13 +760,14 @@ cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* o
 // and the target silhouette), mask M = 1 - T_final clamped to
 // [kBceEps, 1 - kBceEps]: L = -(1/n) sum (m log M + (1 - m) log(1 - M)),
 // dL/dT_final = (1/n) (m / M - (1 - m) / (1 - M)) where M is not clamped, 0
-// where it is. 1 - M is taken as T itself (no cancellation).
+// where it is, both times a weight. 1 - M is taken as T itself (no
+// cancellation).
 constexpr float kBceEps = 1e-6f;
 constexpr int kBceItems = 16;
 
 __global__ void __launch_bounds__(kLossThreads) k_silhouette_bce(const float* __restrict__ t_final,
                                                                   const float* __restrict__ mask, int64_t n,
-                                                                  float inv_n, float* __restrict__ dL_dT,
+                                                                  float inv_n, float weight, float* __restrict__ dL_dT,
                                                                   double* __restrict__ part, double* __restrict__ loss) {
   const int64_t base = (int64_t)blockIdx.x * kLossThreads * kBceItems;
   float acc = 0.0f;
@@ -780,22 +781,24 @@ __global__ void __launch_bounds__(kLossThreads) k_silhouette_bce(const float* __
       const float Tc = fminf(fmaxf(T, kBceEps), 1.0f - kBceEps);  // 1 - M
       acc -= m * logf(M) + (1.0f - m) * logf(Tc);
       const bool inside = Mraw > kBceEps && Mraw < 1.0f - kBceEps;
-      dL_dT[i] = inside ? inv_n * (m / M - (1.0f - m) / Tc) : 0.0f;
+      dL_dT[i] = inside ? weight * inv_n * (m / M - (1.0f - m) / Tc) : 0.0f;
     }
   }
   // the loss is the mean: scale the FP32 partial here (exact power-of-two
   // scalings aside, one rounding per thread)
-  loss_partial_and_finish<kLossThreads>(acc * inv_n, part, loss);
+  loss_partial_and_finish<kLossThreads>(acc * (weight * inv_n), part, loss);
 }
 
 int64_t bce_partials_needed(int64_t n) { return 1 + (n + kLossThreads * kBceItems - 1) / (kLossThreads * kBceItems); }
 
-cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64_t n, float* dL_dT, double* loss,
-                                  double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches) {
+cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64_t n, float weight, float* dL_dT,
+                                  double* loss, double* partials, int64_t n_partials, cudaStream_t s,
+                                  int64_t* launches) {
   const int64_t nb = bce_partials_needed(n) - 1;
   if (nb + 1 > n_partials) return cudaErrorInvalidValue;
   if (nb == 0) return cudaMemsetAsync(loss, 0, sizeof(double), s);
-  k_silhouette_bce<<<(unsigned)nb, kLossThreads, 0, s>>>(t_final, mask, n, 1.0f / (float)n, dL_dT, partials, loss);
+  k_silhouette_bce<<<(unsigned)nb, kLossThreads, 0, s>>>(t_final, mask, n, 1.0f / (float)n, weight, dL_dT, partials,
+                                                          loss);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -237,17 +237,18 @@ class Renderer:
                     "gmr_render_bwd_ex")
         return dverts, drgb, dopacity
 
-    def silhouette_bce(self, t_final, mask, grad=None, loss=None, stream=None):
-        """Binary cross-entropy of the rendered mask 1 - t_final against
-        mask (mean over pixels); returns (loss, dL/dt_final)."""
+    def silhouette_bce(self, t_final, mask, grad=None, loss=None, weight=1.0, stream=None):
+        """weight x the binary cross-entropy of the rendered mask 1 - t_final
+        against mask (mean over pixels); returns (loss, dL/dt_final)."""
         _check_dev(t_final, "t_final", torch.float32)
         _check_dev(mask, "mask", torch.float32)
         if grad is None:
             grad = torch.empty_like(t_final)
         if loss is None:
             loss = torch.empty((), device=t_final.device, dtype=torch.float64)
-        self._check(self._L.gmr_silhouette_bce(self._ctx, _ptr(t_final), _ptr(mask), t_final.numel(), _ptr(grad),
-                                               _ptr(loss), _stream(stream)), "gmr_silhouette_bce")
+        self._check(self._L.gmr_silhouette_bce(self._ctx, _ptr(t_final), _ptr(mask), t_final.numel(),
+                                               float(weight), _ptr(grad), _ptr(loss), _stream(stream)),
+                    "gmr_silhouette_bce")
         return loss, grad
 
     def l2_loss(self, img, target, grad=None, loss=None, stream=None):
@@ -272,6 +273,21 @@ class Renderer:
         self._check(self._L.gmr_adam_step(self._ctx, _ptr(params), _ptr(grads), _ptr(m), _ptr(v), n, group,
                                           float(lr), float(betas[0]), float(betas[1]), float(eps), int(step),
                                           _stream(stream)), "gmr_adam_step")
+
+    def mesh_regularizers(self, verts, faces, w_edge=1.0, w_lap=1.0, dverts=None, losses=None, stream=None):
+        """Edge-length and Laplacian regularisers: returns a device tensor of
+        the two (unweighted) losses; adds w_edge and w_lap times their vertex
+        gradients to dverts when it is given."""
+        _check_dev(verts, "verts", torch.float32)
+        _check_dev(faces, "faces", torch.int32)
+        if dverts is not None:
+            _check_dev(dverts, "dverts", torch.float32)
+        if losses is None:
+            losses = torch.empty(2, device=verts.device, dtype=torch.float64)
+        self._check(self._L.gmr_mesh_regularizers(self._ctx, _ptr(verts), verts.shape[0], _ptr(faces),
+                                                  faces.shape[0], float(w_edge), float(w_lap), _ptr(dverts),
+                                                  _ptr(losses), _stream(stream)), "gmr_mesh_regularizers")
+        return losses
 
     def chamfer(self, a, b, out=None, stream=None):
         """Chamfer distance between point sets a [na, 3] and b [nb, 3]:

@@ -1,5 +1,6 @@
-"""The fitting loop around the renderer: the Adam / VectorAdam step and the
-chamfer distance against plain FP64 restatements of their definitions, a
+"""The fitting loop around the renderer: the Adam / VectorAdam step, the
+chamfer distance and the mesh regularisers against the FP64 oracle of
+these terms, a
 short fit that lowers the image loss and the chamfer distance in both the
 batched and the per-view form, and the first step's gradients on the
 level-7 fitting problem (4 views of 512^2) against the FP64 oracle."""
@@ -10,26 +11,10 @@ import torch
 
 import gmr_inputs as gi
 import oracle
+from oracle import fit_terms
 from gpu_util import DEV, GRAD_TOL, rel_l2, sample_pixels, to_dev
 
 pytestmark = pytest.mark.gpu
-
-
-def _adam_ref(p, g_steps, lr, b1, b2, eps, group):
-    """FP64 Adam (group 1) / VectorAdam (group 3), written from the update
-    rule: m and v are exponential averages of g and g^2 (|g|^2 per 3-vector),
-    bias-corrected by 1 - b^t."""
-    p = p.astype(np.float64).copy()
-    m = np.zeros_like(p)
-    v = np.zeros(p.size // group)
-    for t, g in enumerate(g_steps, start=1):
-        g = g.astype(np.float64)
-        m = b1 * m + (1 - b1) * g
-        v = b2 * v + (1 - b2) * (g.reshape(-1, group) ** 2).sum(1)
-        mh = m / (1 - b1 ** t)
-        vh = v / (1 - b2 ** t)
-        p = p - lr * mh / (np.repeat(np.sqrt(vh), group) + eps)
-    return p
 
 
 @pytest.mark.parametrize("group", [1, 3])
@@ -46,7 +31,7 @@ def test_adam_step_against_fp64(group):
     v = torch.zeros(n // group, device=DEV)
     for t, g in enumerate(gs, start=1):
         r.adam_step(p, torch.from_numpy(g).to(DEV), m, v, 1e-3, t, group=group)
-    ref = _adam_ref(p0, gs, 1e-3, 0.9, 0.999, 1e-8, group)
+    ref = fit_terms.adam(p0, gs, 1e-3, group=group)
     step = ref - p0
     assert np.abs(p.cpu().numpy().astype(np.float64) - ref).max() <= 1e-6 + 1e-5 * np.abs(step).max()
     r.close()
@@ -60,9 +45,7 @@ def test_chamfer_against_brute_force():
     b = (rng.normal(size=(1777, 3)) * 0.7 + 0.1).astype(np.float32)
     r = Renderer()
     out = r.chamfer(torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)).cpu().numpy()
-    d = ((a[:, None, :].astype(np.float64) - b[None, :, :]) ** 2).sum(2)
-    ref = np.array([d.min(1).mean(), d.min(0).mean()])
-    np.testing.assert_allclose(out, ref, rtol=2e-6)
+    np.testing.assert_allclose(out, np.array(fit_terms.chamfer(a, b)), rtol=2e-6)
     # identical sets: zero
     z = r.chamfer(torch.from_numpy(a).to(DEV), torch.from_numpy(a).to(DEV)).cpu().numpy()
     assert np.all(z == 0.0)
@@ -84,6 +67,28 @@ def test_short_fit_lowers_loss_and_chamfer(optimizer):
     # the two forms compute the same step (up to the order of float atomics)
     np.testing.assert_allclose(out_b["loss"][:3], out_p["loss"][:3], rtol=1e-5)
     assert abs(out_b["chamfer_final"] - out_p["chamfer_final"]) <= 0.05 * out_b["chamfer_final"]
+
+
+def test_short_fit_with_silhouette_and_regularizers():
+    """All four losses of the paper's fitting loop (image, silhouette,
+    edge length, Laplacian) with VectorAdam: every loss term is finite, the
+    image and silhouette losses fall, and the batched and per-view forms take
+    the same first steps."""
+    from paper_2602_14493_b300.fit import fit
+
+    s = gi.scene_fit(level=4, res=128, views_per_step=4, steps=30)
+    kw = dict(lr=2e-3, optimizer="vectoradam", w_silhouette=2e3, w_edge=1e2, w_laplacian=1e2)
+    out_b = fit(s, form="batched", **kw)
+    out_p = fit(s, form="per_view", **kw)
+    for out in (out_b, out_p):
+        assert out["status"] == 0
+        for key in ("loss", "silhouette_loss", "regularizer_losses"):
+            assert np.all(np.isfinite(out[key]))
+        assert out["loss"][-5:].mean() < 0.9 * out["loss"][:5].mean()
+        assert out["silhouette_loss"][-5:].mean() < out["silhouette_loss"][:5].mean()
+        assert np.all(out["regularizer_losses"] > 0)
+    np.testing.assert_allclose(out_b["loss"][:3], out_p["loss"][:3], rtol=1e-5)
+    np.testing.assert_allclose(out_b["silhouette_loss"][:3], out_p["silhouette_loss"][:3], rtol=1e-5)
 
 
 def test_fit_first_step_gradients_match_oracle():
@@ -113,4 +118,33 @@ def test_fit_first_step_gradients_match_oracle():
     assert np.abs(ob["dverts"]).max() > 0
     assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
     assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    r.close()
+
+
+@pytest.mark.parametrize("level", [2, 4])
+def test_mesh_regularizers_match_oracle(level):
+    """Edge-length and Laplacian losses and their weighted vertex gradients
+    (added to a non-zero dL/dverts) against the FP64 oracle, on a randomly
+    bumped icosphere."""
+    from paper_2602_14493_b300 import Renderer
+
+    v, f = gi.icosphere(level)
+    rng = np.random.default_rng(level)
+    v = (v * (1.0 + 0.1 * rng.normal(size=(len(v), 1)))).astype(np.float32)
+    r = Renderer()
+    vd = torch.from_numpy(v).to(DEV)
+    fd = torch.from_numpy(f).to(DEV)
+    base = (1e-6 * rng.normal(size=v.shape)).astype(np.float32)  # small: recovering g = dv - base stays exact-ish
+    dv = torch.from_numpy(base).to(DEV)
+    losses = r.mesh_regularizers(vd, fd, w_edge=0.7, w_lap=1.3, dverts=dv).cpu().numpy()
+    le, ge = fit_terms.edge_length_loss(v, f)
+    ll, gl = fit_terms.laplacian_loss(v, f)
+    # FP32: the edge variance cancels (l - mean l) to ~10% of l
+    assert abs(losses[0] - le) <= 1e-4 * le
+    assert abs(losses[1] - ll) <= 1e-5 * ll
+    g = dv.cpu().numpy().astype(np.float64) - base
+    assert rel_l2(g, 0.7 * ge + 1.3 * gl) <= 1e-5
+    # losses only (the neighbour sums are float atomics: equal up to their order)
+    l2 = r.mesh_regularizers(vd, fd).cpu().numpy()
+    np.testing.assert_allclose(l2, losses, rtol=1e-6)
     r.close()
