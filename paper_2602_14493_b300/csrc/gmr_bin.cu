@@ -11,10 +11,11 @@
 //     of up to 512 keys (nearly all) are sorted by one warp each with a
 //     bitonic network, up to 256 keys in registers (shuffles only) and 257 to
 //     512 in shared memory; longer segments are listed and sorted by one CTA
-//     each with LSD radix passes on the 8-bit digits that differ within the
-//     segment (usually not the depth's exponent byte nor the face index's
-//     upper bytes), in shared memory up to 4096 keys and through global
-//     memory beyond.
+//     each: up to 4096 keys by a merge sort in shared memory (register
+//     bitonic chunks, then merge-path rounds), beyond that by LSD radix
+//     passes through global memory on the 8-bit digits that differ within
+//     the segment (usually not the depth's exponent byte nor the face
+//     index's upper bytes).
 //
 // Keys are unique (face ids are), so the result is the unique (tile, depth,
 // face) order whatever order step 1 put the keys of a segment in.
@@ -280,10 +281,62 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
   }
 }
 
+// One merge round of a CTA-wide merge sort: the sorted runs of length R in
+// src[0, P) are merged pairwise into dst (P and R powers of two, P / R >= 2).
+// Thread t writes the P / kSegThreads outputs from t P / kSegThreads on: it
+// finds where that output diagonal crosses the merge path of its two runs by
+// binary search (taking from the first run on ties), then merges its outputs
+// sequentially.
+__device__ __forceinline__ void cta_merge_round(const unsigned long long* __restrict__ src,
+                                                unsigned long long* __restrict__ dst, int P, int R) {
+  const int ipt = P / kSegThreads;
+  const int out0 = threadIdx.x * ipt;
+  const int pair0 = out0 & ~(2 * R - 1);
+  const unsigned long long* A = src + pair0;
+  const unsigned long long* B = A + R;
+  const int diag = out0 - pair0;
+  int lo = max(0, diag - R), hi = min(diag, R);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  int i = lo, j = diag - lo;
+  unsigned long long a = i < R ? A[i] : ~0ull, b = j < R ? B[j] : ~0ull;
+  for (int n = 0; n < ipt; ++n) {
+    const bool take_a = j >= R || (i < R && a <= b);
+    dst[out0 + n] = take_a ? a : b;
+    if (take_a) {
+      ++i;
+      a = i < R ? A[i] : ~0ull;
+    } else {
+      ++j;
+      b = j < R ? B[j] : ~0ull;
+    }
+  }
+}
+
+// Each warp sorts the 32 KPL-key chunks warp, warp + kSegWarps, ... of s in
+// registers.
+template <int KPL>
+__device__ __forceinline__ void cta_sort_chunks(unsigned long long* s, int nchunks, int warp, int lane) {
+  for (int c = warp; c < nchunks; c += kSegWarps) {
+    unsigned long long* p = s + c * (32 * KPL) + lane * KPL;
+    unsigned long long v[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) v[r] = p[r];
+    warp_bitonic<KPL>(v, lane);
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) p[r] = v[r];
+  }
+}
+
 // Segments longer than kWarpSortMax: one CTA each (a persistent grid over
-// the long list), LSD radix passes on the 8-bit digits that differ within the
-// segment, in dynamic shared memory up to kSegSmem keys and through global
-// memory beyond.
+// the long list). Up to kSegSmem keys: a merge sort in dynamic shared memory
+// (the segment padded with all-ones keys to P = 2^k >= 1024, eight register
+// sorted chunks of P / 8 keys or 256-key chunks, then log2 of their number
+// merge rounds). Longer: LSD radix passes on the 8-bit digits that differ
+// within the segment, through global memory.
 __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
                                                            const Counters* __restrict__ counters,
                                                            const uint2* __restrict__ ranges,
@@ -302,13 +355,33 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
     const uint2 rg = ranges[long_list[li]];
     const int L = (int)(rg.y - rg.x);
     unsigned long long* gk = keys + rg.x;
-    const bool in_smem = L <= kSegSmem;
+    if (L <= kSegSmem) {
+      int P = 1024;
+      while (P < L) P <<= 1;
+      for (int i = threadIdx.x; i < P; i += kSegThreads) sa[i] = i < L ? gk[i] : ~0ull;
+      __syncthreads();
+      const int cs = min(256, P / kSegWarps);
+      if (cs == 256) cta_sort_chunks<8>(sa, P / 256, warp, lane);
+      else cta_sort_chunks<4>(sa, P / 128, warp, lane);
+      __syncthreads();
+      unsigned long long* src = sa;
+      unsigned long long* dst = sb;
+      for (int R = cs; R < P; R <<= 1) {
+        cta_merge_round(src, dst, P, R);
+        __syncthreads();
+        unsigned long long* tmp = src;
+        src = dst;
+        dst = tmp;
+      }
+      for (int i = threadIdx.x; i < L; i += kSegThreads) pair_face[rg.x + i] = (uint32_t)src[i];
+      __syncthreads();
+      continue;
+    }
     unsigned long long a = ~0ull, o = 0ull;
     for (int i = threadIdx.x; i < L; i += kSegThreads) {
       const unsigned long long k = gk[i];
       a &= k;
       o |= k;
-      if (in_smem) sa[i] = k;
     }
 #pragma unroll
     for (int s2 = 16; s2 > 0; s2 >>= 1) {
@@ -323,8 +396,8 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
     unsigned long long diff = 0;
 #pragma unroll
     for (int w = 0; w < kSegWarps; ++w) diff |= red_and[w] ^ red_or[w];
-    unsigned long long* src = in_smem ? sa : gk;
-    unsigned long long* dst = in_smem ? sb : keys_tmp + rg.x;
+    unsigned long long* src = gk;
+    unsigned long long* dst = keys_tmp + rg.x;
     for (int shift = 0; shift < 64; shift += 8) {
       if (((diff >> shift) & 0xffull) == 0) continue;  // uniform over the CTA
       cta_radix_pass(src, dst, L, shift, hist, sw);
