@@ -128,7 +128,6 @@ gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
   if ((s = realloc_exact(ctx, &w.rec_ntiles, cap, "rec_ntiles")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_key, cap, "rec_key")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_grad, 2 * cap, "rec_grad")) != GMR_OK) return s;
-  if ((s = realloc_exact(ctx, &w.rec_contrib, 4 * cap, "rec_contrib")) != GMR_OK) return s;
   w.cap_records = cap;
   return GMR_OK;
 }
@@ -355,7 +354,7 @@ gmr_status gmr_create(const gmr_config* cfg, gmr_ctx** out) {
 gmr_status gmr_destroy(gmr_ctx* ctx) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   Workspace& w = ctx->ws;
-  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.rec_contrib, w.face_col,
+  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.face_col,
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
                   w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch};
   for (void* p : bufs)

@@ -282,61 +282,71 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
 }
 
 // One merge round of a CTA-wide merge sort: the sorted runs of length R in
-// src[0, P) are merged pairwise into dst (P and R powers of two, P / R >= 2).
-// Thread t writes the P / kSegThreads outputs from t P / kSegThreads on: it
-// finds where that output diagonal crosses the merge path of its two runs by
-// binary search (taking from the first run on ties), then merges its outputs
-// sequentially.
+// src[0, n) (the last one possibly shorter) are merged pairwise into dst
+// (R a power of two, n a multiple of 128). Thread t writes the ipt outputs
+// from t ipt on (ipt the power of two >= n / kSegThreads, which divides 2R,
+// so no thread's outputs cross a pair of runs): it finds where that output
+// diagonal crosses the merge path of its two runs by binary search (taking
+// from the first run on ties), then merges its outputs sequentially.
 __device__ __forceinline__ void cta_merge_round(const unsigned long long* __restrict__ src,
-                                                unsigned long long* __restrict__ dst, int P, int R) {
-  const int ipt = P / kSegThreads;
+                                                unsigned long long* __restrict__ dst, int n, int R) {
+  int ipt = 1;
+  while (ipt * kSegThreads < n) ipt <<= 1;
   const int out0 = threadIdx.x * ipt;
+  if (out0 >= n) return;
   const int pair0 = out0 & ~(2 * R - 1);
+  const int la = min(R, n - pair0), lb = max(0, min(R, n - pair0 - R));
   const unsigned long long* A = src + pair0;
   const unsigned long long* B = A + R;
   const int diag = out0 - pair0;
-  int lo = max(0, diag - R), hi = min(diag, R);
+  int lo = max(0, diag - lb), hi = min(diag, la);
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
     else hi = mid;
   }
   int i = lo, j = diag - lo;
-  unsigned long long a = i < R ? A[i] : ~0ull, b = j < R ? B[j] : ~0ull;
-  for (int n = 0; n < ipt; ++n) {
-    const bool take_a = j >= R || (i < R && a <= b);
-    dst[out0 + n] = take_a ? a : b;
+  unsigned long long a = i < la ? A[i] : ~0ull, b = j < lb ? B[j] : ~0ull;
+  for (int k = 0; k < ipt; ++k) {
+    const bool take_a = j >= lb || (i < la && a <= b);
+    dst[out0 + k] = take_a ? a : b;
     if (take_a) {
       ++i;
-      a = i < R ? A[i] : ~0ull;
+      a = i < la ? A[i] : ~0ull;
     } else {
       ++j;
-      b = j < R ? B[j] : ~0ull;
+      b = j < lb ? B[j] : ~0ull;
     }
   }
 }
 
-// Each warp sorts the 32 KPL-key chunks warp, warp + kSegWarps, ... of s in
-// registers.
+// Each warp sorts the 32 KPL-key chunks warp, warp + kSegWarps, ... of the
+// segment gk[0, L) (padded with all-ones keys) in registers and stores them,
+// sorted, to s. Any input order suits a sort: the loads take the coalesced
+// (and bank-conflict-free) one.
 template <int KPL>
-__device__ __forceinline__ void cta_sort_chunks(unsigned long long* s, int nchunks, int warp, int lane) {
+__device__ __forceinline__ void cta_sort_chunks(const unsigned long long* __restrict__ gk, int L,
+                                                unsigned long long* s, int nchunks, int warp, int lane) {
   for (int c = warp; c < nchunks; c += kSegWarps) {
-    unsigned long long* p = s + c * (32 * KPL) + lane * KPL;
     unsigned long long v[KPL];
 #pragma unroll
-    for (int r = 0; r < KPL; ++r) v[r] = p[r];
+    for (int r = 0; r < KPL; ++r) {
+      const int e = c * (32 * KPL) + r * 32 + lane;
+      v[r] = e < L ? gk[e] : ~0ull;
+    }
     warp_bitonic<KPL>(v, lane);
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(s + c * (32 * KPL) + lane * KPL);
 #pragma unroll
-    for (int r = 0; r < KPL; ++r) p[r] = v[r];
+    for (int r = 0; r < KPL / 2; ++r) p[r] = make_ulonglong2(v[2 * r], v[2 * r + 1]);
   }
 }
 
 // Segments longer than kWarpSortMax: one CTA each (a persistent grid over
 // the long list). Up to kSegSmem keys: a merge sort in dynamic shared memory
-// (the segment padded with all-ones keys to P = 2^k >= 1024, eight register
-// sorted chunks of P / 8 keys or 256-key chunks, then log2 of their number
-// merge rounds). Longer: LSD radix passes on the 8-bit digits that differ
-// within the segment, through global memory.
+// (register-sorted chunks of 128 keys, or 256 above 1024 keys, the last one
+// padded with all-ones keys, then ceil(log2(chunks)) merge rounds). Longer:
+// LSD radix passes on the 8-bit digits that differ within the segment,
+// through global memory.
 __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
                                                            const Counters* __restrict__ counters,
                                                            const uint2* __restrict__ ranges,
@@ -356,18 +366,17 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
     const int L = (int)(rg.y - rg.x);
     unsigned long long* gk = keys + rg.x;
     if (L <= kSegSmem) {
-      int P = 1024;
-      while (P < L) P <<= 1;
-      for (int i = threadIdx.x; i < P; i += kSegThreads) sa[i] = i < L ? gk[i] : ~0ull;
-      __syncthreads();
-      const int cs = min(256, P / kSegWarps);
-      if (cs == 256) cta_sort_chunks<8>(sa, P / 256, warp, lane);
-      else cta_sort_chunks<4>(sa, P / 128, warp, lane);
+      // chunks of 128 keys (one per warp) up to 1024 keys, of 256 beyond
+      const int cs = L <= 1024 ? 128 : 256;
+      const int nch = (L + cs - 1) / cs;
+      const int n = nch * cs;
+      if (cs == 128) cta_sort_chunks<4>(gk, L, sa, nch, warp, lane);
+      else cta_sort_chunks<8>(gk, L, sa, nch, warp, lane);
       __syncthreads();
       unsigned long long* src = sa;
       unsigned long long* dst = sb;
-      for (int R = cs; R < P; R <<= 1) {
-        cta_merge_round(src, dst, P, R);
+      for (int R = cs; R < n; R <<= 1) {
+        cta_merge_round(src, dst, n, R);
         __syncthreads();
         unsigned long long* tmp = src;
         src = dst;

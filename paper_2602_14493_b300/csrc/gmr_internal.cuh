@@ -229,7 +229,6 @@ struct Workspace {
   // 2 float4 per record: (sum q dx, sum q dy, sum q dx^2, sum q dx dy),
   // (sum q dy^2, 0, 0, 0) with q = alpha dL/dalpha over the record's pixels
   float4* rec_grad = nullptr;
-  float4* rec_contrib = nullptr; // 4 float4 per record: backward contributions per view
   // faces
   int64_t cap_faces = 0;
   float4* face_col = nullptr;    // (r, g, b, o)

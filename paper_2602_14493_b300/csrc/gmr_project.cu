@@ -331,40 +331,24 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, 0.0f);
 }
 
-// Backward of conversion + projection, part 1: one thread per (view, face)
-// record. The record's gradient sums R0..R4 from the compositing backward are
+// Backward of conversion + projection. A face's gradient sums over its
+// views, per view: the record's sums R0..R4 from the compositing backward
 // chained through the conic inverse, Sigma' = M Sigma M^T + 0.3 I, M = J R,
-// J(t) and u(t), to this view's share of dL/dmu, dL/dd_a (d_a = v_a - mu),
-// dL/dn and dL/d(kappa/12), written as 4 float4:
-// (dmu, dw), (dd_0, dn.x), (dd_1, dn.y), (dd_2, dn.z).
-__global__ void __launch_bounds__(128) k_record_bwd(
-    const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
-    const ViewInfo* __restrict__ views, int cov_mode, const float4* __restrict__ rec_grad,
-    const float4* __restrict__ rec_q, float4* __restrict__ rec_contrib) {
-  __shared__ ViewInfo sv;
-  const int c = blockIdx.y;
-  if (threadIdx.x == 0) sv = views[c];
-  __syncthreads();
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  const size_t rid = (size_t)c * F + f;
-  float4* out = rec_contrib + 4 * rid;
-  const float4 r0 = rec_grad[2 * rid];
-  const float r4 = rec_grad[2 * rid + 1].x;
-  int i0, i1, i2;
-  if ((r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f) || !load_face(faces, f, V, i0, i1, i2)) {
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    out[0] = z; out[1] = z; out[2] = z; out[3] = z;
-    return;
-  }
-  const float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
-  const FaceGeom g = face_geom(a, b, cc, cov_mode);
-  const ViewInfo& v = sv;
+// J(t) and u(t), to dL/dmu, dL/dd_a (d_a = v_a - mu), dL/dn and
+// dL/d(kappa/12).
+struct FaceAcc {
+  float3 dmu;
+  float3 dd[3];
+  float3 dn;
+  float dw;
+};
+
+__device__ __forceinline__ void record_bwd(const FaceGeom& g, const ViewInfo& v, float4 r0, float r4, float4 cq,
+                                           FaceAcc& acc) {
   const ProjRec p = project_rec(g, v);
   // p2 = a2 dx^2 + b2 dx dy + c2 dy^2 with dx = pixel - u: the mean gradient
   // is ln2 (2 a2 sum q dx + b2 sum q dy, b2 sum q dx + 2 c2 sum q dy), taken
   // with the conic the forward used
-  const float4 cq = rec_q[rid];
   const float dux = kLn2 * (2.0f * cq.x * r0.x + cq.y * r0.y);
   const float duy = kLn2 * (cq.y * r0.x + 2.0f * cq.z * r0.y);
   const float dqa = -0.5f * r0.z, dqb = -r0.w, dqc = -0.5f * r4;
@@ -377,12 +361,11 @@ __global__ void __launch_bounds__(128) k_record_bwd(
   const float s11 = -(t10 * p.qb + t11 * p.qc);
   // Sigma' = w sum e e^T + sz2 m m^T + 0.3 I
   float2 de[3];
-  float dw = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     de[k].x = 2.f * g.w * (s00 * p.e[k].x + s01 * p.e[k].y);
     de[k].y = 2.f * g.w * (s01 * p.e[k].x + s11 * p.e[k].y);
-    dw += s00 * p.e[k].x * p.e[k].x + 2.f * s01 * p.e[k].x * p.e[k].y + s11 * p.e[k].y * p.e[k].y;
+    acc.dw += s00 * p.e[k].x * p.e[k].x + 2.f * s01 * p.e[k].x * p.e[k].y + s11 * p.e[k].y * p.e[k].y;
   }
   float2 dm;
   dm.x = 2.f * g.sz2 * (s00 * p.m.x + s01 * p.m.y);
@@ -400,17 +383,15 @@ __global__ void __launch_bounds__(128) k_record_bwd(
     dM[q] = dq0;
     dM[3 + q] = dq1;
   }
-  float3 dd[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    dd[k].x = p.M[0] * de[k].x + p.M[3] * de[k].y;
-    dd[k].y = p.M[1] * de[k].x + p.M[4] * de[k].y;
-    dd[k].z = p.M[2] * de[k].x + p.M[5] * de[k].y;
+    acc.dd[k].x += p.M[0] * de[k].x + p.M[3] * de[k].y;
+    acc.dd[k].y += p.M[1] * de[k].x + p.M[4] * de[k].y;
+    acc.dd[k].z += p.M[2] * de[k].x + p.M[5] * de[k].y;
   }
-  float3 dn;
-  dn.x = p.M[0] * dm.x + p.M[3] * dm.y;
-  dn.y = p.M[1] * dm.x + p.M[4] * dm.y;
-  dn.z = p.M[2] * dm.x + p.M[5] * dm.y;
+  acc.dn.x += p.M[0] * dm.x + p.M[3] * dm.y;
+  acc.dn.y += p.M[1] * dm.x + p.M[4] * dm.y;
+  acc.dn.z += p.M[2] * dm.x + p.M[5] * dm.y;
   // M = J R: dJ = dM R^T (only the non-zero entries of J)
   const float* R = v.R;
   const float dJ00 = dM[0] * R[0] + dM[1] * R[1] + dM[2] * R[2];
@@ -426,58 +407,89 @@ __global__ void __launch_bounds__(128) k_record_bwd(
   const float dtz = dJ00 * (-fxz2) + dJ02 * (2.f * v.fx * x * iz * iz * iz) + dJ11 * (-fyz2) +
                     dJ12 * (2.f * v.fy * y * iz * iz * iz) - dux * v.fx * x * iz * iz - duy * v.fy * y * iz * iz;
   // t = R mu + t_cam
-  float3 dmu;
-  dmu.x = R[0] * dtx + R[3] * dty + R[6] * dtz;
-  dmu.y = R[1] * dtx + R[4] * dty + R[7] * dtz;
-  dmu.z = R[2] * dtx + R[5] * dty + R[8] * dtz;
-  out[0] = make_float4(dmu.x, dmu.y, dmu.z, dw);
-  out[1] = make_float4(dd[0].x, dd[0].y, dd[0].z, dn.x);
-  out[2] = make_float4(dd[1].x, dd[1].y, dd[1].z, dn.y);
-  out[3] = make_float4(dd[2].x, dd[2].y, dd[2].z, dn.z);
+  acc.dmu.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
+  acc.dmu.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
+  acc.dmu.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
 }
 
-// Part 2: one thread per face sums the views' contributions in view order
-// (deterministic), maps them to the three vertices (d_a = v_a - mu with mu
-// the vertex mean, n = e1 x e2 / |e1 x e2|, kappa = |A| / (pi 1e-7) when
-// clamped) and scatters them; colour and opacity gradients are per face.
-// Small CTAs: there is one thread per face, and at 256 threads a mesh of
-// 20K faces would occupy only 80 SMs.
-constexpr int kFaceBwdThreads = 64;
+// Sum over the G lanes of a group (butterfly: every lane ends with the same,
+// order-independent total, so the result is deterministic).
+template <int G>
+__device__ __forceinline__ float group_sum(float x) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
 
-__global__ void __launch_bounds__(kFaceBwdThreads) k_face_bwd(
+// One group of G lanes per face (G a power of two <= 8): lane k of the group
+// takes views k, k + G, ... (records with no gradient are skipped), the
+// group sums its lanes, and its first lane maps the sums to the three
+// vertices (d_a = v_a - mu with mu the vertex mean, n = e1 x e2 / |e1 x e2|,
+// kappa = |A| / (pi 1e-7) when clamped) and scatters them; colour and
+// opacity gradients are per face. No per-record intermediate goes through
+// memory.
+constexpr int kProjBwdThreads = 128;
+
+template <int G>
+__global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
-    int cov_mode, int color_mode, const float* __restrict__ opacity, const float4* __restrict__ rec_contrib,
-    const float4* __restrict__ face_grad, float* __restrict__ dverts, float* __restrict__ drgb,
-    float* __restrict__ dop, int accumulate) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  int i0, i1, i2;
-  if (!load_face(faces, f, V, i0, i1, i2)) return;
-  float3 dmu = make_float3(0.f, 0.f, 0.f);
-  float3 dd[3] = {dmu, dmu, dmu};
-  float3 dn = dmu;
-  float dw = 0.f;
-#pragma unroll 4
-  for (int c = 0; c < C; ++c) {
-    const float4* in = rec_contrib + 4 * ((size_t)c * F + f);
-    const float4 q0 = in[0], q1 = in[1], q2 = in[2], q3 = in[3];
-    dmu.x += q0.x; dmu.y += q0.y; dmu.z += q0.z; dw += q0.w;
-    dd[0].x += q1.x; dd[0].y += q1.y; dd[0].z += q1.z; dn.x += q1.w;
-    dd[1].x += q2.x; dd[1].y += q2.y; dd[1].z += q2.z; dn.y += q2.w;
-    dd[2].x += q3.x; dd[2].y += q3.y; dd[2].z += q3.z; dn.z += q3.w;
+    const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ opacity,
+    const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q, const float4* __restrict__ face_grad,
+    float* __restrict__ dverts, float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
+  const int64_t gid = (int64_t)blockIdx.x * kProjBwdThreads + threadIdx.x;
+  const int f = (int)(gid / G);
+  const int sub = (int)(gid % G);
+  int i0 = 0, i1 = 0, i2 = 0;
+  const bool ok = f < F && load_face(faces, f, V, i0, i1, i2);
+  FaceAcc acc;
+  acc.dmu = make_float3(0.f, 0.f, 0.f);
+  acc.dd[0] = acc.dd[1] = acc.dd[2] = acc.dn = acc.dmu;
+  acc.dw = 0.f;
+  float3 a = acc.dmu, b = acc.dmu, cc = acc.dmu;
+  FaceGeom g;
+  if (ok) {
+    a = ld_vert(verts, i0);
+    b = ld_vert(verts, i1);
+    cc = ld_vert(verts, i2);
+    g = face_geom(a, b, cc, cov_mode);
+    // the next view's sums are loaded before this view's arithmetic
+    float4 r0n = make_float4(0.f, 0.f, 0.f, 0.f);
+    float r4n = 0.f;
+    if (sub < C) {
+      r0n = rec_grad[2 * ((size_t)sub * F + f)];
+      r4n = rec_grad[2 * ((size_t)sub * F + f) + 1].x;
+    }
+    for (int c = sub; c < C; c += G) {
+      const size_t rid = (size_t)c * F + f;
+      const float4 r0 = r0n;
+      const float r4 = r4n;
+      if (c + G < C) {
+        r0n = rec_grad[2 * (rid + (size_t)G * F)];
+        r4n = rec_grad[2 * (rid + (size_t)G * F) + 1].x;
+      }
+      if (r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f) continue;
+      record_bwd(g, views[c], r0, r4, rec_q[rid], acc);
+    }
   }
-  const float3 a = ld_vert(verts, i0), b = ld_vert(verts, i1), cc = ld_vert(verts, i2);
-  const FaceGeom g = face_geom(a, b, cc, cov_mode);
+  if (G > 1) {  // every lane of the warp takes part in the shuffles
+    acc.dmu = make_float3(group_sum<G>(acc.dmu.x), group_sum<G>(acc.dmu.y), group_sum<G>(acc.dmu.z));
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      acc.dd[k] = make_float3(group_sum<G>(acc.dd[k].x), group_sum<G>(acc.dd[k].y), group_sum<G>(acc.dd[k].z));
+    acc.dn = make_float3(group_sum<G>(acc.dn.x), group_sum<G>(acc.dn.y), group_sum<G>(acc.dn.z));
+    acc.dw = group_sum<G>(acc.dw);
+  }
+  if (!ok || sub != 0) return;
   // to vertices: d_a = v_a - mu (mu = mean of v), n from e1 x e2
-  const float3 sdd = f3add(f3add(dd[0], dd[1]), dd[2]);
+  const float3 sdd = f3add(f3add(acc.dd[0], acc.dd[1]), acc.dd[2]);
   float3 dv[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) dv[k] = f3add(f3scale(1.0f / 3.0f, f3sub(dmu, sdd)), dd[k]);
+  for (int k = 0; k < 3; ++k) dv[k] = f3add(f3scale(1.0f / 3.0f, f3sub(acc.dmu, sdd)), acc.dd[k]);
   if (g.cn > 0.f) {
-    float3 dcr = f3scale(1.0f / g.cn, f3sub(dn, f3scale(f3dot(g.n, dn), g.n)));
+    float3 dcr = f3scale(1.0f / g.cn, f3sub(acc.dn, f3scale(f3dot(g.n, acc.dn), g.n)));
     if (g.clamped) {
       // kappa = |A| / (pi 1e-7), |A| = cn / 2, w = kappa / 12
-      const float dcn = dw * (1.0f / 12.0f) * (0.5f / (kPi * 1e-7f));
+      const float dcn = acc.dw * (1.0f / 12.0f) * (0.5f / (kPi * 1e-7f));
       dcr = f3add(dcr, f3scale(dcn, g.n));
     }
     const float3 de1 = f3cross(g.e2, dcr);
@@ -594,12 +606,16 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
                                const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
                                cudaStream_t s, int64_t* launches) {
   if (F <= 0) return cudaSuccess;
-  dim3 grid((F + 127) / 128, C);
-  k_record_bwd<<<grid, 128, 0, s>>>(verts, V, faces, F, views, cov_mode, ws.rec_grad, ws.rec_q, ws.rec_contrib);
-  k_face_bwd<<<(F + kFaceBwdThreads - 1) / kFaceBwdThreads, kFaceBwdThreads, 0, s>>>(
-      verts, V, faces, F, C, cov_mode, color_mode, opacity, ws.rec_contrib,
-                                             ws.face_grad, dverts, drgb, dop, accumulate);
-  *launches += 2;
+  // lanes per face: enough threads to fill the GPU when faces are few, no
+  // more lanes than views
+  int G = 1;
+  while (G < 8 && G < C && (int64_t)F * G < 148 * 2048) G <<= 1;
+  const int64_t threads = (int64_t)F * G;
+  const unsigned blocks = (unsigned)((threads + kProjBwdThreads - 1) / kProjBwdThreads);
+  auto kern = G == 1 ? k_proj_bwd<1> : G == 2 ? k_proj_bwd<2> : G == 4 ? k_proj_bwd<4> : k_proj_bwd<8>;
+  kern<<<blocks, kProjBwdThreads, 0, s>>>(verts, V, faces, F, C, views, cov_mode, color_mode, opacity, ws.rec_grad,
+                                          ws.rec_q, ws.face_grad, dverts, drgb, dop, accumulate);
+  *launches += 1;
   return cudaGetLastError();
 }
 

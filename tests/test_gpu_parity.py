@@ -70,20 +70,26 @@ def test_convert_matches_oracle(cov_mode, color_mode):
 
 # ------------------------------------------------------------------ binning
 def _dense_scene():
-    """A level-6 icosphere (81,920 faces) in one 128^2 view: tile segments
-    of every length class (up to 256 keys, 257-512, 513-4096 and beyond:
-    the longest holds 4,920 keys with 16x16 tiles)."""
+    """A level-6 icosphere (81,920 faces) in a 128^2 and a 256^2 view: with
+    16x16 tiles, segments of every length class of the per-tile sort (up to
+    256 keys in registers, 257-512 in shared memory, 513-1024 and 1025-4096
+    by the CTA merge sort, longer by radix passes: the longest holds 4,920
+    keys)."""
     v, f = gi.icosphere(6)
     rng = np.random.default_rng(61)
-    cams = gi.ring_cameras(1, 20.0, 3.0, 128, 128)
-    return gi.Scene("dense6_1x128", v.astype(np.float32), f, rng.random((len(f), 3)).astype(np.float32),
+    cams = np.concatenate([gi.ring_cameras(1, 20.0, 3.0, 128, 128),
+                           gi.ring_cameras(1, 35.0, 3.0, 256, 256, azimuth0_deg=40.0)])
+    return gi.Scene("dense6_128_256", v.astype(np.float32), f, rng.random((len(f), 3)).astype(np.float32),
                     np.full(len(f), 0.9, np.float32), cams)
 
 
+SORT_CLASSES = [(0, 256), (256, 512), (512, 1024), (1024, 4096), (4096, 1 << 30)]
+
+
 @pytest.mark.parametrize("tile", [16, 32])
-@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven", "dense6_1x128"])
+@pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven", "dense6_128_256"])
 def test_binning_bit_exact(renderer, tile, name):
-    s = _dense_scene() if name == "dense6_1x128" else _scenes()[name]
+    s = _dense_scene() if name == "dense6_128_256" else _scenes()[name]
     renderer.set_config(tile=tile)
     render_gpu(renderer, s)
     tx, ty = oracle.tile_counts(s.cams, tile)
@@ -101,6 +107,9 @@ def test_binning_bit_exact(renderer, tile, name):
     np.testing.assert_array_equal(ge, oe)
     np.testing.assert_array_equal(grect[~oe], orect[~oe])
     tiles, fids, ranges = oracle.sorted_pairs(s.verts, s.faces, s.cams, tile)
+    if name == "dense6_128_256" and tile == 16:
+        seg = (ranges[:, 1] - ranges[:, 0]).astype(np.int64)
+        assert all(((seg > a) & (seg <= b)).sum() >= 5 for a, b in SORT_CLASSES)
     assert st["n_pairs"] == len(tiles)
     np.testing.assert_array_equal(st["tile_ids"], tiles)
     np.testing.assert_array_equal(st["face_ids"], fids)
