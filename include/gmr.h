@@ -245,6 +245,23 @@ GMR_API gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, cons
                                      float* dL_dverts, float* dL_drgb, float* dL_dopacity, int32_t accumulate,
                                      gmr_stream stream);
 
+/* Backward of the squared-error image loss of the last forward, with the
+ * loss formed inside the compositing backward (one pass over the images
+ * fewer than gmr_l2_loss + gmr_render_bwd):
+ *  images       the images the last forward wrote (packed, device),
+ *  target       the target images (same layout, device),
+ *  loss         output, one device double: sum of (images - target)^2
+ *               (each square in FP32, summed in FP32 per thread and warp and
+ *               in double-float above: relative error below 1.3e-6),
+ *  dL_dtfinal   as in gmr_render_bwd_ex, or NULL,
+ *  the rest     as in gmr_render_bwd.
+ * The gradients equal those of gmr_render_bwd_ex with dL_dimages =
+ * 2 (images - target) (bit for bit up to the order of the float atomics);
+ * no dL/dimages buffer is written. */
+GMR_API gmr_status gmr_render_bwd_l2(gmr_ctx* ctx, const float* images, const float* target, double* loss,
+                                     const float* dL_dtfinal, float* dL_dverts, float* dL_drgb,
+                                     float* dL_dopacity, int32_t accumulate, gmr_stream stream);
+
 /* Silhouette loss (Sec. 3.1: binary cross-entropy between the rendered mask
  * and the target silhouette) over n pixels, the rendered mask being
  * M = 1 - T_final clamped to [1e-6, 1 - 1e-6]:
@@ -257,9 +274,9 @@ GMR_API gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const 
 
 /* Squared-error loss sum((img - target)^2) over n floats and its gradient
  * 2 (img - target). loss is a device double (overwritten); dL_dimg may
- * alias neither input. Deterministic (fixed reduction order); FP32 sums of
- * 16 squares (two per thread) and 32 threads per warp, FP64 above that (relative
- * error below 1.3e-6). */
+ * alias neither input. Deterministic (fixed reduction order for a given n);
+ * FP32 sums of 8 squares, double-float across a thread's chunks of 16 and
+ * the warp, FP64 above that (relative error below 1.3e-6). */
 GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int64_t n, float* dL_dimg,
                        double* loss, gmr_stream stream);
 

@@ -76,7 +76,6 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=
         return best, {}
     stream = torch.cuda.current_stream()
     img = torch.empty((target.shape[0], 3), device=verts.device)
-    grad = torch.empty_like(img)
     loss = torch.empty((), dtype=torch.float64, device=verts.device)
     dv, dc = torch.empty_like(verts), torch.empty_like(rgb)
     do = torch.empty_like(opacity) if opacity is not None else None
@@ -88,8 +87,7 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             renderer.forward(verts, faces, rgb, opacity, cams, images=img, want_t=False)
-            renderer.l2_loss(img, target, grad, loss)
-            renderer.backward(grad, dv, dc, do)
+            renderer.backward_l2(img, target, loss, dv, dc, do)
             b.record(stream)
             b.synchronize()
             if rep >= 2:

@@ -562,15 +562,30 @@ gmr_status gmr_silhouette_bce(gmr_ctx* ctx, const float* t_final, const float* m
   return GMR_OK;
 }
 
-gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtfinal, float* dL_dverts,
-                             float* dL_drgb, float* dL_dopacity, int32_t accumulate, gmr_stream stream) {
-  if (!ctx) return GMR_ERR_INVALID_ARG;
+namespace {
+
+// The backward of the last forward from dL/dimages (or, with images and
+// target, from the squared-error loss formed inside the compositing
+// backward, whose sum goes to *loss) and dL/dT_final.
+gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtfinal, const float* images,
+                      const float* target, double* loss, float* dL_dverts, float* dL_drgb, float* dL_dopacity,
+                      int32_t accumulate, gmr_stream stream) {
   if (!ctx->fwd_valid) return fail(ctx, GMR_ERR_STATE, "gmr_render_bwd without a preceding gmr_render_fwd");
-  if (!dL_dimages && !dL_dtfinal) return fail(ctx, GMR_ERR_INVALID_ARG, "null dL_dimages and dL_dtfinal");
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& w = ctx->ws;
   const gmr_config& cfg = ctx->fwd_cfg;
   const int32_t F = ctx->F, C = ctx->C, V = ctx->V;
+  gmr::BwdLoss bl;
+  const int64_t n_warp_sums = ctx->n_tiles * (cfg.threads_bwd / 32);
+  if (images) {
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+    gmr_status st = ensure_loss(ctx, 1 + (n_warp_sums + 1) / 2, cap_status != cudaStreamCaptureStatusNone);
+    if (st != GMR_OK) return st;
+    bl.img = images;
+    bl.target = target;
+    bl.part = reinterpret_cast<float*>(w.loss_part + 1);
+  }
   const int64_t n_rec = (int64_t)F * C;
   if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_grad, 0, sizeof(float4) * 2 * (size_t)n_rec, s));
   if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
@@ -584,7 +599,15 @@ gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, const float*
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, w, w.pair_face, w.views, C, F,
-                                         ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal, s, &ctx->launches));
+                                         ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal, bl, s, &ctx->launches));
+  }
+  if (images) {  // the loss: sum of the warps' partial sums
+    StageTimer t(ctx, GMR_STAGE_LOSS, s, cfg);
+    if (n_warp_sums > 0) {
+      GMR_CUDA(ctx, gmr::launch_sum_floats(bl.part, n_warp_sums, 1.0, loss, s, &ctx->launches));
+    } else {
+      GMR_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(double), s));
+    }
   }
   // S9: projection + conversion backward, vertex scatter
   {
@@ -594,6 +617,25 @@ gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, const float*
                                           &ctx->launches));
   }
   return GMR_OK;
+}
+
+}  // namespace
+
+gmr_status gmr_render_bwd_ex(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtfinal, float* dL_dverts,
+                             float* dL_drgb, float* dL_dopacity, int32_t accumulate, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (!dL_dimages && !dL_dtfinal) return fail(ctx, GMR_ERR_INVALID_ARG, "null dL_dimages and dL_dtfinal");
+  return render_bwd(ctx, dL_dimages, dL_dtfinal, nullptr, nullptr, nullptr, dL_dverts, dL_drgb, dL_dopacity,
+                    accumulate, stream);
+}
+
+gmr_status gmr_render_bwd_l2(gmr_ctx* ctx, const float* images, const float* target, double* loss,
+                             const float* dL_dtfinal, float* dL_dverts, float* dL_drgb, float* dL_dopacity,
+                             int32_t accumulate, gmr_stream stream) {
+  if (!ctx) return GMR_ERR_INVALID_ARG;
+  if (!images || !target || !loss) return fail(ctx, GMR_ERR_INVALID_ARG, "null images, target or loss");
+  return render_bwd(ctx, nullptr, dL_dtfinal, images, target, loss, dL_dverts, dL_drgb, dL_dopacity, accumulate,
+                    stream);
 }
 
 gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* target, int64_t n, float* dL_dimg,

@@ -314,9 +314,20 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
                               float* images, float* t_final_out, uint32_t* ncontrib_out, const FwdLoss& fl,
                               cudaStream_t s, int64_t* launches);
+// Optional squared-error loss fused into the backward's prologue (img ==
+// nullptr: none): dL/dimg = 2 (img - target) is formed per pixel instead of
+// being read, and the loss sum goes to one FP32 partial per warp (part,
+// n_tiles * threads / 32 floats), added up by a one-block kernel
+// (launch_sum_floats) after the compositing backward.
+struct BwdLoss {
+  const float* img = nullptr;
+  const float* target = nullptr;
+  float* part = nullptr;
+};
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, const float* dL_dT, cudaStream_t s, int64_t* launches);
+                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, cudaStream_t s,
+                              int64_t* launches);
 // partials: l2_loss_partials_needed(n) doubles; partials[0] holds a ticket
 // counter that must be zero before the first call (every call leaves it zero)
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,

@@ -33,6 +33,8 @@
 // (float4 loads of the records and face colours), with the image mean made
 // relative to the pixel block's 32-aligned anchor in float-pair arithmetic.
 
+#include <algorithm>
+
 #include "gmr_internal.cuh"
 
 namespace gmr {
@@ -211,17 +213,15 @@ __device__ __forceinline__ double block_sum_f64(double v, double* sw) {
   return s;  // valid in thread 0
 }
 
-// Block sum of v written to part[1 + blockIdx.x]; the block that finishes
-// last (ticket counter in part[0]) adds the partials in index order into
-// *loss and returns the counter to zero. Called by every thread of every
-// block of the grid.
+// The block's sum bs (valid in thread 0) written to part[1 + blockIdx.x];
+// the block that finishes last (ticket counter in part[0]) adds the partials
+// in index order into *loss and returns the counter to zero. Called by every
+// thread of every block of the grid.
 template <int NT>
-__device__ __forceinline__ void loss_partial_and_finish(float v, double* __restrict__ part,
-                                                        double* __restrict__ loss) {
+__device__ __forceinline__ void finish_loss_partial(double bs, double* __restrict__ part,
+                                                    double* __restrict__ loss) {
   __shared__ double sw[NT / 32];
-  __shared__ float swf[NT / 32];
   __shared__ bool s_last;
-  const double bs = block_sum_f32<NT>(v, swf);
   if (threadIdx.x == 0) {
     part[1 + blockIdx.x] = bs;
     __threadfence();
@@ -238,6 +238,13 @@ __device__ __forceinline__ void loss_partial_and_finish(float v, double* __restr
     *loss = tot;
     *reinterpret_cast<unsigned int*>(part) = 0u;
   }
+}
+
+template <int NT>
+__device__ __forceinline__ void loss_partial_and_finish(float v, double* __restrict__ part,
+                                                        double* __restrict__ loss) {
+  __shared__ float swf[NT / 32];
+  finish_loss_partial<NT>(block_sum_f32<NT>(v, swf), part, loss);
 }
 
 // MODE: kFwdPlain; kFwdDebug also records per-pixel contributor counts and
@@ -464,13 +471,16 @@ __device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int l
 #endif
 constexpr int kBwdDirectLanes = GMR_BWD_DIRECT_LANES;
 
-template <int TS, int NT, int BATCH>
+// LOSS: dL/dimg = 2 (img - target) is formed from bl.img and bl.target (the
+// squared-error loss), and each warp writes its pixels' sum of squared
+// errors to bl.part; otherwise dL/dimg is read from dL_dimg (or is zero).
+template <int TS, int NT, int BATCH, bool LOSS>
 __global__ void __launch_bounds__(NT) k_raster_bwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
     const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
-    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, Counters* __restrict__ counters) {
+    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
@@ -497,6 +507,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
   uint32_t last[PPT];
   int blk[PPT];
   uint32_t tmax = 0;
+  float lsum = 0.0f;  // LOSS: FP32 sum of this thread's squared errors
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     int lx, ly;
@@ -510,7 +521,17 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
       int64_t pid = v.pix_base + (int64_t)py * v.W + px;
       T[k] = pix_T[pid];
       last[k] = pix_last[pid];
-      if (dL_dimg) {
+      if (LOSS) {
+        const float d0 = bl.img[3 * pid] - bl.target[3 * pid];
+        const float d1 = bl.img[3 * pid + 1] - bl.target[3 * pid + 1];
+        const float d2 = bl.img[3 * pid + 2] - bl.target[3 * pid + 2];
+        G0[k] = 2.0f * d0;
+        G1[k] = 2.0f * d1;
+        G2[k] = 2.0f * d2;
+        lsum = fmaf(d0, d0, lsum);
+        lsum = fmaf(d1, d1, lsum);
+        lsum = fmaf(d2, d2, lsum);
+      } else if (dL_dimg) {
         G0[k] = dL_dimg[3 * pid];
         G1[k] = dL_dimg[3 * pid + 1];
         G2[k] = dL_dimg[3 * pid + 2];
@@ -535,6 +556,11 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
   if (lane == 0) atomicMax(&s_maxlast, wmax);
+  if (LOSS) {  // one partial per warp, written before the main loop
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
+    if (lane == 0) bl.part[(int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5)] = lsum;
+  }
   __syncthreads();
   const int end_all = (int)s_maxlast;
   const uint2 range = ranges[g];
@@ -635,57 +661,83 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
 }
 
 // ---------------------------------------------------------------- loss
-// L = sum (img - target)^2 and dL/dimg = 2 (img - target) in one launch: each
-// block writes the FP64 sum of its 4096 elements to partials[1 + block], and
+// L = sum (img - target)^2 and dL/dimg = 2 (img - target) in one launch: a
+// persistent grid of at most kLossMaxBlocks blocks (one wave on 148 SMs)
+// walks the 4096-element chunks (block b takes chunks b, b + grid, ...);
+// each block writes the FP64 sum of its chunks to partials[1 + block], and
 // the block that finishes last (a ticket counter in partials[0]) adds the
 // partials in index order, so the result does not depend on which block
-// that is, then returns the counter to zero for the next call.
+// that is, then returns the counter to zero for the next call. The chunk
+// assignment depends only on n, so the sum is deterministic.
 constexpr int kLossThreads = 256;
-constexpr int kLossItems = 32;  // floats per thread: 16 float4 loads in flight
+constexpr int kLossItems = 16;  // floats per thread and chunk: 4 float4 of each operand
 constexpr int kLossBlockElems = kLossThreads * kLossItems;
+constexpr int kLossMaxBlocks = 148 * 4;
+
+// Block sum of one double-float per thread (warp tree in double-float,
+// FP64 across the warps); valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum_df(df v, df* sw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, df{__shfl_xor_sync(kFull, v.hi, o), __shfl_xor_sync(kFull, v.lo, o)});
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += (double)sw[w].hi + (double)sw[w].lo;
+  return s;
+}
 
 __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restrict__ img,
                                                            const float* __restrict__ tgt, int64_t n,
                                                            float* __restrict__ grad, double* __restrict__ part,
                                                            double* __restrict__ loss, bool vec4) {
-  const int64_t base = (int64_t)blockIdx.x * kLossBlockElems;
-  // FP32 within a thread (two running sums of 16 squares each) and a warp,
-  // FP64 across warps and blocks: FP64 arithmetic is a slow pipe on this GPU.
-  float acc0 = 0.0f, acc1 = 0.0f;
-  if (vec4 && base + kLossBlockElems <= n) {
-    const float4* i4 = reinterpret_cast<const float4*>(img + base);
-    const float4* t4 = reinterpret_cast<const float4*>(tgt + base);
-    float4* g4 = reinterpret_cast<float4*>(grad + base);
-    float4 x[kLossItems / 4], y[kLossItems / 4];
+  // FP32 within a chunk (two running sums of 8 squares each), double-float
+  // across a thread's chunks and the warp, FP64 across warps and blocks: FP64
+  // arithmetic is a slow pipe on this GPU.
+  const int64_t nchunks = (n + kLossBlockElems - 1) / kLossBlockElems;
+  df acc{0.0f, 0.0f};
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t base = c * kLossBlockElems;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    if (vec4 && base + kLossBlockElems <= n) {
+      const float4* i4 = reinterpret_cast<const float4*>(img + base);
+      const float4* t4 = reinterpret_cast<const float4*>(tgt + base);
+      float4* g4 = reinterpret_cast<float4*>(grad + base);
+      float4 x[kLossItems / 4], y[kLossItems / 4];
 #pragma unroll
-    for (int k = 0; k < kLossItems / 4; ++k) {
-      x[k] = __ldcs(i4 + k * kLossThreads + threadIdx.x);
-      y[k] = __ldcs(t4 + k * kLossThreads + threadIdx.x);
-    }
+      for (int k = 0; k < kLossItems / 4; ++k) {
+        x[k] = __ldcs(i4 + k * kLossThreads + threadIdx.x);
+        y[k] = __ldcs(t4 + k * kLossThreads + threadIdx.x);
+      }
 #pragma unroll
-    for (int k = 0; k < kLossItems / 4; ++k) {
-      const float4 d = make_float4(x[k].x - y[k].x, x[k].y - y[k].y, x[k].z - y[k].z, x[k].w - y[k].w);
-      g4[k * kLossThreads + threadIdx.x] = make_float4(2.0f * d.x, 2.0f * d.y, 2.0f * d.z, 2.0f * d.w);
-      float& acc = (k & 1) ? acc1 : acc0;
-      acc = fmaf(d.x, d.x, acc);
-      acc = fmaf(d.y, d.y, acc);
-      acc = fmaf(d.z, d.z, acc);
-      acc = fmaf(d.w, d.w, acc);
-    }
-  } else {
+      for (int k = 0; k < kLossItems / 4; ++k) {
+        const float4 d = make_float4(x[k].x - y[k].x, x[k].y - y[k].y, x[k].z - y[k].z, x[k].w - y[k].w);
+        g4[k * kLossThreads + threadIdx.x] = make_float4(2.0f * d.x, 2.0f * d.y, 2.0f * d.z, 2.0f * d.w);
+        float& a = (k & 1) ? acc1 : acc0;
+        a = fmaf(d.x, d.x, a);
+        a = fmaf(d.y, d.y, a);
+        a = fmaf(d.z, d.z, a);
+        a = fmaf(d.w, d.w, a);
+      }
+    } else {
 #pragma unroll 4
-    for (int k = 0; k < kLossItems; ++k) {
-      const int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
-      if (i < n) {
-        const float d = img[i] - tgt[i];
-        grad[i] = 2.0f * d;
-        if (k < kLossItems / 2) acc0 = fmaf(d, d, acc0);
-        else acc1 = fmaf(d, d, acc1);
+      for (int k = 0; k < kLossItems; ++k) {
+        const int64_t i = base + (int64_t)k * kLossThreads + threadIdx.x;
+        if (i < n) {
+          const float d = img[i] - tgt[i];
+          grad[i] = 2.0f * d;
+          if (k < kLossItems / 2) acc0 = fmaf(d, d, acc0);
+          else acc1 = fmaf(d, d, acc1);
+        }
       }
     }
+    acc = df_add(acc, df{acc0 + acc1, 0.0f});
   }
-  const float accf = acc0 + acc1;
-  loss_partial_and_finish<kLossThreads>(accf, part, loss);
+  __shared__ df sw[kLossThreads / 32];
+  const double bs = block_sum_df<kLossThreads>(acc, sw);
+  finish_loss_partial<kLossThreads>(bs, part, loss);
 }
 
 __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_q, int64_t n_rec,
@@ -724,11 +776,11 @@ void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
 
 template <int TS, int NT, int BATCH>
 void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, const float* dL, const float* dLdT, cudaStream_t s) {
-  k_raster_bwd<TS, NT, BATCH><<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
-                                                                 ws.face_col, views, C, F, bg[0], bg[1], bg[2], dL, dLdT,
-                                                                 ws.pix_T, ws.pix_last, ws.rec_grad, ws.face_grad,
-                                                                 ws.counters);
+                int32_t F, const float* bg, const float* dL, const float* dLdT, const BwdLoss& bl, cudaStream_t s) {
+  auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
+  kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q, ws.face_col, views, C, F,
+                                        bg[0], bg[1], bg[2], dL, dLdT, ws.pix_T, ws.pix_last, ws.rec_grad,
+                                        ws.face_grad, bl, ws.counters);
 }
 
 }  // namespace
@@ -754,11 +806,12 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
 
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, const float* dL_dT, cudaStream_t s, int64_t* launches) {
+                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, cudaStream_t s,
+                              int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, s)
+  bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
@@ -831,7 +884,9 @@ cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64
   return cudaGetLastError();
 }
 
-int64_t l2_loss_partials_needed(int64_t n) { return 1 + (n + kLossBlockElems - 1) / kLossBlockElems; }
+int64_t l2_loss_partials_needed(int64_t n) {
+  return 1 + std::min<int64_t>((n + kLossBlockElems - 1) / kLossBlockElems, kLossMaxBlocks);
+}
 
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches) {

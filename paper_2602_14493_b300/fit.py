@@ -80,7 +80,6 @@ def fit(scene, steps=None, lr=1e-3, form="batched", optimizer="adam", renderer=N
     per_view_cams = [[camera_array(cams[k:k + 1]) for k in range(len(cams))] for cams in view_sets]
     npix = targets[0].shape[0]
     img = torch.empty((npix, 3), device=dev)
-    grad = torch.empty_like(img)
     tfin = torch.empty(npix, device=dev) if use_sil else None
     gradT = torch.empty_like(tfin) if use_sil else None
     losses = torch.zeros(steps, n_views if form == "per_view" else 1, dtype=torch.float64, device=dev)
@@ -92,10 +91,9 @@ def fit(scene, steps=None, lr=1e-3, form="batched", optimizer="adam", renderer=N
         events[t][0].record()
         if form == "batched":
             r.forward(verts, faces, rgb, opacity, cam_arrays[t], images=img, t_final=tfin, want_t=use_sil)
-            r.l2_loss(img, targets[t], grad, losses[t, 0])
             if use_sil:
                 r.silhouette_bce(tfin, masks[t], gradT, sil_losses[t, 0], weight=w_silhouette)
-            r.backward(grad, dv, dc, dop, dL_dtfinal=gradT)
+            r.backward_l2(img, targets[t], losses[t, 0], dv, dc, dop, dL_dtfinal=gradT)
         else:
             off = 0
             for k, cam in enumerate(per_view_cams[t]):
@@ -103,12 +101,12 @@ def fit(scene, steps=None, lr=1e-3, form="batched", optimizer="adam", renderer=N
                 sl = slice(off, off + n)
                 r.forward(verts, faces, rgb, opacity, cam, images=img[sl], t_final=tfin[sl] if use_sil else None,
                           want_t=use_sil)
-                r.l2_loss(img[sl], targets[t][sl], grad[sl], losses[t, k])
                 if use_sil:
                     # the batched form's mean over all views' pixels: weight n / npix per view
                     r.silhouette_bce(tfin[sl], masks[t][sl], gradT[sl], sil_losses[t, k],
                                      weight=w_silhouette * n / npix)
-                r.backward(grad[sl], dv, dc, dop, accumulate=k > 0, dL_dtfinal=gradT[sl] if use_sil else None)
+                r.backward_l2(img[sl], targets[t][sl], losses[t, k], dv, dc, dop, accumulate=k > 0,
+                              dL_dtfinal=gradT[sl] if use_sil else None)
                 off += n
         if use_reg:
             r.mesh_regularizers(verts, faces, w_edge, w_laplacian, dverts=dv, losses=reg_losses[t])

@@ -237,6 +237,31 @@ class Renderer:
                     "gmr_render_bwd_ex")
         return dverts, drgb, dopacity
 
+    def backward_l2(self, images, target, loss=None, dverts=None, drgb=None, dopacity=None, accumulate=False,
+                    stream=None, dL_dtfinal=None):
+        """Backward of the squared-error loss sum((images - target)^2) of the
+        last forward, the loss formed inside the compositing backward
+        (gmr_render_bwd_l2): returns (loss, dverts, drgb, dopacity)."""
+        _check_dev(images, "images", torch.float32)
+        _check_dev(target, "target", torch.float32)
+        if tuple(target.shape) != tuple(images.shape):
+            raise _lib.GmrError("target must have the shape of images")
+        if dL_dtfinal is not None:
+            _check_dev(dL_dtfinal, "dL_dtfinal", torch.float32)
+        verts, faces, rgb, opacity = self._saved
+        if loss is None:
+            loss = torch.empty((), device=verts.device, dtype=torch.float64)
+        if dverts is None:
+            dverts = torch.empty_like(verts)
+        if drgb is None:
+            drgb = torch.empty_like(rgb)
+        if dopacity is None and opacity is not None:
+            dopacity = torch.empty_like(opacity)
+        self._check(self._L.gmr_render_bwd_l2(self._ctx, _ptr(images), _ptr(target), _ptr(loss), _ptr(dL_dtfinal),
+                                              _ptr(dverts), _ptr(drgb), _ptr(dopacity), 1 if accumulate else 0,
+                                              _stream(stream)), "gmr_render_bwd_l2")
+        return loss, dverts, drgb, dopacity
+
     def silhouette_bce(self, t_final, mask, grad=None, loss=None, weight=1.0, stream=None):
         """weight x the binary cross-entropy of the rendered mask 1 - t_final
         against mask (mean over pixels); returns (loss, dL/dt_final)."""

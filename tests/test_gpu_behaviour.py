@@ -111,6 +111,37 @@ def test_fused_forward_loss_matches_separate():
         r.close()
 
 
+def test_backward_with_fused_loss_matches_separate():
+    """gmr_render_bwd_l2 (the loss formed in the compositing backward): the
+    same gradients as gmr_l2_loss + gmr_render_bwd up to the order of the
+    float atomics, the same loss up to the FP32 partial sums, on views of
+    uneven sizes, for every backward shape, also with dL/dT_final."""
+    s = _uneven()
+    for tile, threads in ((16, 128), (16, 256), (16, 64), (32, 256)):
+        r = _renderer(tile=tile, threads=threads)
+        (v, f, c, o), img, T = render_gpu(r, s)
+        img, T = img.clone(), T.clone()
+        target = torch.rand_like(img)
+        loss, grad = r.l2_loss(img, target)
+        loss = float(loss)
+        ref = [t.clone() for t in r.backward(grad)]
+        gT = torch.randn_like(T) * 1e-3
+        ref_t = [t.clone() for t in r.backward(grad, dL_dtfinal=gT)]
+        for _ in range(2):
+            loss2, dv, dc, do = r.backward_l2(img, target)
+            torch.cuda.synchronize()
+            assert abs(float(loss2) - loss) <= 2.6e-6 * abs(loss)
+            for a, b in zip((dv, dc, do), ref):
+                assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+        _, dv, dc, do = r.backward_l2(img, target, dL_dtfinal=gT)
+        for a, b in zip((dv, dc, do), ref_t):
+            assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+        # accumulate adds to the given gradients
+        _, dv2, _, _ = r.backward_l2(img, target, dverts=dv.clone(), accumulate=True)
+        assert rel_l2(dv2.cpu().numpy(), dv.cpu().numpy() + ref[0].cpu().numpy()) < 1e-6
+        r.close()
+
+
 def test_batched_equals_per_view():
     s = _uneven()
     r = _renderer()
