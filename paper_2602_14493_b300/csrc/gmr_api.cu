@@ -576,11 +576,11 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   const gmr_config& cfg = ctx->fwd_cfg;
   const int32_t F = ctx->F, C = ctx->C, V = ctx->V;
   gmr::BwdLoss bl;
-  const int64_t n_warp_sums = ctx->n_tiles * (cfg.threads_bwd / 32);
+  const int64_t n_cta_sums = ctx->n_tiles;
   if (images) {
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
     GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
-    gmr_status st = ensure_loss(ctx, 1 + (n_warp_sums + 1) / 2, cap_status != cudaStreamCaptureStatusNone);
+    gmr_status st = ensure_loss(ctx, 1 + (n_cta_sums + 1) / 2, cap_status != cudaStreamCaptureStatusNone);
     if (st != GMR_OK) return st;
     bl.img = images;
     bl.target = target;
@@ -603,8 +603,8 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   }
   if (images) {  // the loss: sum of the warps' partial sums
     StageTimer t(ctx, GMR_STAGE_LOSS, s, cfg);
-    if (n_warp_sums > 0) {
-      GMR_CUDA(ctx, gmr::launch_sum_floats(bl.part, n_warp_sums, 1.0, loss, s, &ctx->launches));
+    if (n_cta_sums > 0) {
+      GMR_CUDA(ctx, gmr::launch_sum_floats(bl.part, n_cta_sums, 1.0, loss, s, &ctx->launches));
     } else {
       GMR_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(double), s));
     }

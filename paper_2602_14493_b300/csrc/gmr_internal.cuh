@@ -316,9 +316,9 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
                               cudaStream_t s, int64_t* launches);
 // Optional squared-error loss fused into the backward's prologue (img ==
 // nullptr: none): dL/dimg = 2 (img - target) is formed per pixel instead of
-// being read, and the loss sum goes to one FP32 partial per warp (part,
-// n_tiles * threads / 32 floats), added up by a one-block kernel
-// (launch_sum_floats) after the compositing backward.
+// being read, and the loss sum goes to one FP32 partial per CTA (part,
+// n_tiles floats), added up by a one-block kernel (launch_sum_floats) after
+// the compositing backward.
 struct BwdLoss {
   const float* img = nullptr;
   const float* target = nullptr;

@@ -280,7 +280,6 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   // asynchronously at the start and read in the epilogue
   __shared__ float s_tgt[MODE == kFwdLoss ? 3 * PPT * NT : 1];
   uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
-  int blk[PPT];
   bool done[PPT], inside[PPT];
   int px[PPT], py[PPT];
 #pragma unroll
@@ -299,7 +298,6 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     term[k] = 0;
     ncontrib[k] = 0;
     chash[k] = 0;
-    blk[k] = PixMap<TS, NT>::block(k);
     if (MODE == kFwdLoss && inside[k]) {
       const float* tp = fl.target + 3 * (v.pix_base + (int64_t)py[k] * v.W + px[k]);
       const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&s_tgt[3 * (k * NT + threadIdx.x)]);
@@ -325,14 +323,15 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     const int nl = warp_list<BATCH, NW>(st, cnt, 0, cnt, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
     for (int jj = 0; jj < nl; ++jj) {
-      bool wd = true;
+      if ((jj & 3) == 0) {  // the warp's early exit, checked every 4 entries
+        bool wd = true;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) wd &= done[k];
-      if (__all_sync(kFull, wd)) break;
+        for (int k = 0; k < PPT; ++k) wd &= done[k];
+        if (__all_sync(kFull, wd)) break;
+      }
       const int j = st.list[warp][jj];
       const float4 hh = st.h[j];
       const float4 gg = st.g[j];
-      const uint32_t m = st.mask[j];
       float p2[PPT];
       bool con[PPT];
       bool anyc = false;
@@ -340,7 +339,9 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
       for (int k = 0; k < PPT; ++k) {
         float dx, dy;
         p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dx, dy);
-        con[k] = !done[k] && (PPT == 1 || ((m >> blk[k]) & 1u)) && !(p2[k] < hh.y);
+        // (a pixel of a block outside the Gaussian's block mask fails the
+        // alpha test by construction of the mask: no block test here)
+        con[k] = !done[k] && !(p2[k] < hh.y);
         anyc |= con[k];
       }
       if (!anyc) continue;
@@ -505,7 +506,6 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
   // SG = (colour composited behind the current Gaussian, plus T_final bg) . g
   float pcx[PPT], pcy[PPT], T[PPT], SG[PPT], G0[PPT], G1[PPT], G2[PPT];
   uint32_t last[PPT];
-  int blk[PPT];
   uint32_t tmax = 0;
   float lsum = 0.0f;  // LOSS: FP32 sum of this thread's squared errors
 #pragma unroll
@@ -550,18 +550,28 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     // Gaussian": a fourth channel with Gaussian colour 0 and background 1
     SG[k] = T[k] * (bg0 * G0[k] + bg1 * G1[k] + bg2 * G2[k] + gT);
     tmax = max(tmax, last[k]);
-    blk[k] = PixMap<TS, NT>::block(k);
   }
   uint32_t wmax = tmax;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
   if (lane == 0) atomicMax(&s_maxlast, wmax);
-  if (LOSS) {  // one partial per warp, written before the main loop
+  __shared__ float s_lsum[LOSS ? NT / 32 : 1];
+  if (LOSS) {  // warp sums now, the CTA's partial after the barrier
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
-    if (lane == 0) bl.part[(int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5)] = lsum;
+    if (lane == 0) s_lsum[threadIdx.x >> 5] = lsum;
   }
   __syncthreads();
+  if (LOSS && threadIdx.x == 0) {  // pairwise over the warps (<= 3 levels)
+    float b[NT / 32];
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) b[w] = s_lsum[w];
+#pragma unroll
+    for (int h = 1; h < NT / 32; h <<= 1)
+#pragma unroll
+      for (int w = 0; w + h < NT / 32; w += 2 * h) b[w] += b[w + h];
+    bl.part[blockIdx.x] = b[0];
+  }
   const int end_all = (int)s_maxlast;
   const uint2 range = ranges[g];
   const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
@@ -582,14 +592,13 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
       const int pos = start + j;
       const float4 hh = st.h[j];
       const float4 gg = st.g[j];
-      const uint32_t m = st.mask[j];
       float p2[PPT], dxs[PPT], dys[PPT];
       bool con[PPT];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
-        con[k] = ((uint32_t)pos < last[k]) && (PPT == 1 || ((m >> blk[k]) & 1u)) && !(p2[k] < hh.y);
+        con[k] = ((uint32_t)pos < last[k]) && !(p2[k] < hh.y);
         any |= con[k];
       }
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
