@@ -526,6 +526,16 @@ def run_gmr(args, ws, rank, local):
     else:
         roof = None
         log("no stage times were recorded")
+    # memory-type stages: algorithmic bytes over their live stage times
+    stage_gbs = {}
+    for name in ("project", "scan", "bin", "project_bwd"):
+        if stage_ms.get(name):
+            rf = roofline_for(name, stage_ms[name], stats, scene, peaks, peak_kind, args)
+            stage_gbs[name] = {"achieved_gbs": round(rf["achieved"], 1), "frac": round(rf["frac"], 4)}
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    memory = {"workspace_gb": stats["workspace_bytes"] / 1e9,
+              "torch_peak_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
+              "device_used_gb": (total_b - free_b) / 1e9}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, args.cpu_seconds)
@@ -544,6 +554,8 @@ def run_gmr(args, ws, rank, local):
         "stages_source": "separate replays of the step captured with events around every stage "
                          f"({statistics.mean(prof_ms):.4f} ms per profiled step)",
         "roofline": roof,
+        "stage_hbm": stage_gbs,
+        "memory": memory,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * n_pix / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s,
@@ -576,7 +588,7 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
     R = stats["n_records"]
     P = stats["n_pairs"]
     byts = {"project": R * 64 + len(scene.faces) * 28 + P * 4, "scan": stats["n_tiles"] * 8,
-            "bin": R * 16 + P * 8 * 3 + P * 4, "project_bwd": R * 96 + len(scene.faces) * 52}.get(stage, 0)
+            "bin": R * 16 + P * 8 * 3 + P * 4, "project_bwd": R * 48 + len(scene.faces) * 116}.get(stage, 0)
     ach = byts / (ms / 1e3) / 1e9
     pk = peaks["hbm_gbs"]
     return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,

@@ -143,6 +143,7 @@ typedef struct {
   int64_t contribs;      /* (pixel, Gaussian) pairs that contributed, last forward */
   int64_t launches;      /* kernels launched by this context since creation */
   int64_t pair_capacity; /* current pair buffer capacity */
+  int64_t workspace_bytes; /* device memory the context's workspace holds */
 } gmr_stats;
 
 /* Fills *cfg with the defaults: tile 16, 128 threads (forward and backward),

@@ -54,7 +54,7 @@ class GmrCamera(ctypes.Structure):
 class GmrStats(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_pairs", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
                 ("n_pixels", ctypes.c_int64), ("evals_fwd", ctypes.c_int64), ("evals_bwd", ctypes.c_int64), ("contribs", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("pair_capacity", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("pair_capacity", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
 
 
 class GmrError(RuntimeError):

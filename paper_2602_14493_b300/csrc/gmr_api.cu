@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "gmr_internal.cuh"
@@ -38,9 +39,24 @@ struct gmr_ctx {
   int32_t V = 0, F = 0, C = 0;
   int64_t n_tiles = 0, n_pixels = 0;
   gmr_config fwd_cfg;
+  // device bytes held by the workspace (per allocation, and the total)
+  std::unordered_map<void*, size_t> dev_sizes;
+  int64_t dev_bytes = 0;
 };
 
 namespace {
+
+// Workspace allocation bookkeeping (for gmr_stats.workspace_bytes).
+void track_alloc(gmr_ctx* ctx, void* p, size_t bytes) {
+  ctx->dev_sizes[p] = bytes;
+  ctx->dev_bytes += (int64_t)bytes;
+}
+void track_free(gmr_ctx* ctx, void* p) {
+  auto it = ctx->dev_sizes.find(p);
+  if (it == ctx->dev_sizes.end()) return;
+  ctx->dev_bytes -= (int64_t)it->second;
+  ctx->dev_sizes.erase(it);
+}
 
 gmr_status fail(gmr_ctx* ctx, gmr_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -95,7 +111,11 @@ gmr_status grow(gmr_ctx* ctx, T** ptr, int64_t* cap, int64_t need, bool capturin
     cudaGetLastError();
     return fail(ctx, GMR_ERR_OOM, std::string("cudaMalloc of workspace '") + what + "' failed");
   }
-  if (*ptr) cudaFree(*ptr);
+  track_alloc(ctx, p, (size_t)ncap * sizeof(T));
+  if (*ptr) {
+    track_free(ctx, *ptr);
+    cudaFree(*ptr);
+  }
   *ptr = p;
   *cap = ncap;
   return GMR_OK;
@@ -105,12 +125,17 @@ gmr_status grow(gmr_ctx* ctx, T** ptr, int64_t* cap, int64_t need, bool capturin
 template <class T>
 gmr_status realloc_exact(gmr_ctx* ctx, T** ptr, int64_t count, const char* what) {
   T* p = nullptr;
-  cudaError_t e = cudaMalloc((void**)&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+  const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, GMR_ERR_OOM, std::string("cudaMalloc of workspace '") + what + "' failed");
   }
-  if (*ptr) cudaFree(*ptr);
+  track_alloc(ctx, p, bytes);
+  if (*ptr) {
+    track_free(ctx, *ptr);
+    cudaFree(*ptr);
+  }
   *ptr = p;
   return GMR_OK;
 }
@@ -725,6 +750,7 @@ gmr_status gmr_get_stats(gmr_ctx* ctx, gmr_stream stream, gmr_stats* out) {
   out->contribs = (int64_t)ctx->counters_pinned->contribs;
   out->launches = ctx->launches;
   out->pair_capacity = ctx->ws.cap_pairs;
+  out->workspace_bytes = ctx->dev_bytes;
   return GMR_OK;
 }
 

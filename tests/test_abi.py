@@ -36,7 +36,7 @@ def test_struct_layouts_match_header():
 
     assert ctypes.sizeof(_lib.GmrCamera) == 76 == gi.CAMERA_DTYPE.itemsize
     assert ctypes.sizeof(_lib.GmrConfig) == 44
-    assert ctypes.sizeof(_lib.GmrStats) == 72
+    assert ctypes.sizeof(_lib.GmrStats) == 80
     cam = gi.look_at((0.0, -3.0, 1.0), 32, 16)
     arr = np.array([cam], dtype=gi.CAMERA_DTYPE)
     from paper_2602_14493_b300.render import camera_array

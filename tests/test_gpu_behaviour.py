@@ -303,4 +303,6 @@ def test_stats_and_launch_count():
     assert st["n_pixels"] == 128 * 128 and st["n_tiles"] == 64
     assert st["evals_fwd"] > 0 and st["evals_bwd"] > 0
     assert st["launches"] > st0["launches"] >= 6
+    # the workspace holds at least the per-record buffers (80 B per record)
+    assert st["workspace_bytes"] >= 80 * st["n_records"]
     r.close()
