@@ -169,35 +169,75 @@ def barrier(ws):
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_sample_time(scene, n_pix, seed=0):
-    """Oracle fwd + bwd on n_pix random pixels of the workload; seconds."""
+def oracle_sample_time(scene, n_pix, seed=0, keep=False):
+    """Oracle fwd + bwd on n_pix random (distinct) pixels of the workload:
+    seconds and the number of pixels; with keep=True also the pixels, the
+    oracle's render and backward and the upstream gradient it used."""
     import oracle
 
     rng = np.random.default_rng(seed)
-    off = oracle.pixel_offsets(scene.cams)
     pix = []
     for _ in range(n_pix):
         c = int(rng.integers(len(scene.cams)))
         pix.append((c, int(rng.integers(int(scene.cams[c]["width"]))), int(rng.integers(int(scene.cams[c]["height"])))))
-    pix = np.array(pix, dtype=np.int32)
+    pix = np.unique(np.array(pix, dtype=np.int32), axis=0)
     t0 = time.perf_counter()
     r = oracle.render(scene, pixels=pix, bands=None)
     g = 2.0 * (r["rgb"] - 0.5)
-    oracle.backward(scene, g, pixels=pix)
-    return time.perf_counter() - t0
+    g[r["flags"] != 0] = 0.0  # no gradient through pixels near a decision threshold
+    b = oracle.backward(scene, g, pixels=pix)
+    t = time.perf_counter() - t0
+    if keep:
+        return t, len(pix), (pix, r, g, b)
+    return t, len(pix)
 
 
-def cpu_baseline(scene, target_seconds):
+def cpu_baseline(scene, target_seconds, gpu_check=None):
+    """The oracle timed on a bounded sample of the workload's pixels. With
+    gpu_check, the GPU's image at the sampled pixels and its gradients for
+    the same upstream gradient are compared with the oracle's."""
     oracle_sample_time(scene, 4)  # build + warm
-    t_a = oracle_sample_time(scene, 32)
-    t_b = oracle_sample_time(scene, 288)
-    per_px = max((t_b - t_a) / 256, 1e-7)
-    fixed = max(t_a - 32 * per_px, 0.0)
+    t_a, n_a = oracle_sample_time(scene, 32)
+    t_b, n_b = oracle_sample_time(scene, 288)
+    per_px = max((t_b - t_a) / max(n_b - n_a, 1), 1e-7)
+    fixed = max(t_a - n_a * per_px, 0.0)
     n = int(max(64, min(400000, (target_seconds - fixed) / per_px)))
-    t = oracle_sample_time(scene, n, seed=1)
-    return {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
-                      f"(single thread), {t:.1f} s"}
+    t, n, kept = oracle_sample_time(scene, n, seed=1, keep=True)
+    out = {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
+                     f"(single thread), {t:.1f} s"}
+    if gpu_check is not None:
+        out["parity"] = gpu_check(*kept)
+    return out
+
+
+def parity_with_oracle(r, v, f, c, o, cams, scene, pix, ref, g, bref):
+    """GPU image at the oracle's pixels (max abs error over the pixels no
+    decision threshold is near, as the tests count it) and GPU gradients for
+    the oracle's upstream gradient at those pixels (relative L2)."""
+    import torch
+
+    img, _ = r.forward(v, f, c, o, cams, want_t=False)
+    widths = np.array([int(cm["width"]) for cm in scene.cams])
+    heights = np.array([int(cm["height"]) for cm in scene.cams])
+    off = np.concatenate([[0], np.cumsum(widths * heights)])
+    lin = off[pix[:, 0]] + pix[:, 2] * widths[pix[:, 0]] + pix[:, 1]
+    gimg = img[torch.from_numpy(lin).to(img.device)].double().cpu().numpy()
+    amb = (ref["flags"] & 3) != 0  # alpha-skip or termination decision near its threshold
+    err = np.abs(gimg - ref["rgb"]).max(1)
+    gfull = torch.zeros_like(img)
+    gfull[torch.from_numpy(lin).to(img.device)] = torch.from_numpy(g.astype(np.float32)).to(img.device)
+    dv, dc, _ = r.backward(gfull)
+    dv, dc = dv.double().cpu().numpy(), dc.double().cpu().numpy()
+
+    def rel(a, b):
+        nb = np.linalg.norm(b)
+        return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+    e_img = float(err[~amb].max()) if (~amb).any() else 0.0
+    e_v, e_c = rel(dv, bref["dverts"]), rel(dc, bref["drgb"])
+    return {"pixels": int(len(pix)), "ambiguous_pixels": int(amb.sum()), "img_max_abs_err": e_img,
+            "dverts_rel_l2": e_v, "drgb_rel_l2": e_c, "ok": bool(e_img <= 1e-5 and e_v <= 1e-4 and e_c <= 1e-4)}
 
 
 def run_reference(args, ws, rank):
@@ -207,9 +247,10 @@ def run_reference(args, ws, rank):
     n_pix = args.ref_pixels
     for _ in range(args.warmup):
         oracle_sample_time(scene, max(8, n_pix // 8))
-    ts = [oracle_sample_time(scene, n_pix, seed=k + 1) for k in range(args.steps)]
-    total = sum(ts)
-    value = n_pix * args.steps / total / 1e6
+    runs = [oracle_sample_time(scene, n_pix, seed=k + 1) for k in range(args.steps)]
+    total = sum(t for t, _ in runs)
+    n_done = sum(n for _, n in runs)
+    value = n_done / total / 1e6
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -538,7 +579,8 @@ def run_gmr(args, ws, rank, local):
               "device_used_gb": (total_b - free_b) / 1e9}
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(scene, args.cpu_seconds)
+        cpu = cpu_baseline(scene, args.cpu_seconds,
+                           lambda *kept: parity_with_oracle(r, v, f, c, o, cams, scene, *kept))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
