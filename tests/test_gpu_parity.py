@@ -152,10 +152,13 @@ def test_image_matches_oracle(renderer, name, tile):
     renderer.set_config(tile=16, bg=(0.0, 0.0, 0.0))
 
 
-def test_image_full_size_ring_sampled(renderer):
-    """The 8 x 512^2 ring workload at full size, in the benchmark's launch
-    configuration (batched, tile 16, batch 256), on sampled pixels."""
+@pytest.mark.parametrize("threads", [(128, 128), (256, 128)])
+def test_image_full_size_ring_sampled(renderer, threads):
+    """The 8 x 512^2 ring workload at full size, batched, tile 16, batch 256,
+    in the default launch shape and the one the benchmark times (256
+    forward threads per tile), on sampled pixels."""
     s = gi.scene_ring()
+    renderer.set_config(threads=threads[0], threads_bwd=threads[1])
     _, img, T = render_gpu(renderer, s)
     pix, lin = sample_pixels(s.cams, 2400, 5)
     ref = oracle.render(s, pixels=pix)
@@ -168,6 +171,7 @@ def test_image_full_size_ring_sampled(renderer):
     a = img.cpu().numpy()
     t = T.cpu().numpy()
     assert np.all(a >= 0) and np.all(a <= 1.0 + 1e-6) and np.all(t >= 1e-4 - 1e-9) and np.all(t <= 1.0)
+    renderer.set_config(threads=128, threads_bwd=128)
 
 
 # ------------------------------------------------------------------ gradients
@@ -193,10 +197,13 @@ def test_gradients_match_oracle(name, cov_mode):
     r.close()
 
 
-def test_gradients_full_size_ring_sparse(renderer):
-    """Full-size ring workload; dL/dI non-zero on sampled pixels only, so the
-    oracle's backward over those pixels is the exact reference."""
+@pytest.mark.parametrize("threads", [(128, 128), (256, 128)])
+def test_gradients_full_size_ring_sparse(renderer, threads):
+    """Full-size ring workload (default and benchmark launch shapes); dL/dI
+    non-zero on sampled pixels only, so the oracle's backward over those
+    pixels is the exact reference."""
     s = gi.scene_ring()
+    renderer.set_config(threads=threads[0], threads_bwd=threads[1])
     (v, f, c, o), img, T = render_gpu(renderer, s)
     pix, lin = sample_pixels(s.cams, 2400, 6)
     ref = oracle.render(s, pixels=pix)
@@ -211,6 +218,7 @@ def test_gradients_full_size_ring_sparse(renderer):
     assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
     assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
     assert rel_l2(do.cpu().numpy(), ob["dopacity"]) <= GRAD_TOL
+    renderer.set_config(threads=128, threads_bwd=128)
 
 
 def test_per_vertex_colour_gradients():
