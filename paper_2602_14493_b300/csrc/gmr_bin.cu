@@ -435,7 +435,9 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
                              cudaStream_t s, int64_t* launches) {
   (void)views;
   if (n_rec > 0 && ws.cap_pairs > 0) {
-    const int64_t blocks = std::min<int64_t>((ws.cap_pairs + kPlaceThreads - 1) / kPlaceThreads, 148 * 8);
+    // one thread per pair slot (a grid-stride loop over 148 x 8 blocks left
+    // each thread's dependent gathers in series: 13% slower on 38M pairs)
+    const int64_t blocks = (ws.cap_pairs + kPlaceThreads - 1) / kPlaceThreads;
     k_place_keys<<<(unsigned)blocks, kPlaceThreads, 0, s>>>(ws.pair_key[1], ws.pair_face, ws.rec_key, F,
                                                           ws.tile_start, ws.cap_pairs, ws.pair_key[0], ws.counters);
     *launches += 1;
