@@ -268,7 +268,7 @@ def run_fit(args, ws, rank, local):
     the per-view form, loss and chamfer distance before and after."""
     import torch
 
-    from paper_2602_14493_b300 import Renderer
+    from paper_2602_14493_b300 import Renderer, camera_array
     from paper_2602_14493_b300.fit import fit, render_targets
 
     if ws > 1:
@@ -284,19 +284,25 @@ def run_fit(args, ws, rank, local):
     r = Renderer()
     faces = torch.from_numpy(scene.faces).to(dev)
     op = torch.from_numpy(scene.opacity).to(dev)
+    v0 = torch.from_numpy(scene.verts).to(dev)
+    c0 = torch.from_numpy(scene.rgb).to(dev)
+    cams0 = camera_array(scene.extra["view_sets"][0])
     targets = render_targets(r, torch.from_numpy(scene.extra["target_verts"]).to(dev), faces,
                              torch.from_numpy(scene.extra["target_rgb"]).to(dev), op, scene.extra["view_sets"])
     shape_choice = "default"
     if args.tile == "auto":  # launch shape tuned on the first step's views
-        from paper_2602_14493_b300 import camera_array
         from paper_2602_14493_b300.autotune import shape_name, tune
 
-        v0 = torch.from_numpy(scene.verts).to(dev)
-        c0 = torch.from_numpy(scene.rgb).to(dev)
-        best, tuned = tune(r, v0, faces, c0, op, camera_array(scene.extra["view_sets"][0]), targets[0],
-                           use_cache=False)
+        best, tuned = tune(r, v0, faces, c0, op, cams0, targets[0], use_cache=False)
         log("autotune:", {shape_name(k): round(t, 4) for k, t in sorted(tuned.items(), key=lambda kv: kv[1])[:8]})
         shape_choice = "autotuned " + shape_name(best)
+    # no host synchronisation inside a step: workspace reserved with room for
+    # twice the first views' pairs (an overflow would set the device status
+    # reported below)
+    r.forward(v0, faces, c0, op, cams0, want_t=False)
+    n_pix0 = sum(int(cm.width) * int(cm.height) for cm in cams0)
+    r.reserve(len(scene.faces), len(cams0), n_pix0, 2 * r.stats()["n_pairs"] + 4096)
+    r.set_config(sync_check=False)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     fit(scene, steps=W, renderer=r, targets=targets[:W])  # warm-up of both forms
     fit(scene, steps=W, form="per_view", renderer=r, targets=targets[:W])
@@ -321,7 +327,7 @@ def run_fit(args, ws, rank, local):
                    "pixels_per_step": n_pix, "optimizer": "adam", "lr": 1e-3,
                    "step": "render 4 views + L2 loss + backward + Adam on vertices and face colours",
                    "form": "batched, one call for all views of a step, eager",
-                   "shape_choice": shape_choice,
+                   "shape_choice": shape_choice, "host_sync": "none inside a step (workspace reserved)",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "per_view": {"value": ws * n_pix * K / tp / 1e6, "ms_per_step": 1e3 * tp / K,
