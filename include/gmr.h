@@ -299,6 +299,17 @@ GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* targ
 GMR_API gmr_status gmr_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* dL_dimg,
                                        double* loss, gmr_stream stream);
 
+/* Host-to-device copy of `bytes` bytes from page-locked host memory `src`
+ * (allocated with cudaHostAlloc / cudaMallocHost, or registered) to device
+ * memory `dst`, done by a kernel that reads the host buffer directly over the
+ * bus (no copy engine), asynchronously on `stream`. No context: any device.
+ * Returns GMR_ERR_INVALID_ARG when src is not page-locked memory mapped into
+ * the device's address space (nothing is launched then), GMR_ERR_CUDA when
+ * the launch fails. 16-byte aligned buffers take the vector path; the rest
+ * is copied byte by byte. src must stay valid and unmodified until the copy
+ * has run. */
+GMR_API gmr_status gmr_copy_h2d(void* dst, const void* src, int64_t bytes, gmr_stream stream);
+
 /* One optimiser step of the fitting loop around the renderer (Sec. 3.1) on
  * n device floats, in place: params -= lr m_hat / (sqrt(v_hat) + eps) with
  * m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2, m_hat =

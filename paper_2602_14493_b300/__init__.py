@@ -8,6 +8,7 @@ streams only.
 """
 
 from ._lib import GmrError, load as load_library
-from .render import GMRRender, GMRRenderWithT, Renderer, camera_array, pixel_offsets, render
+from .render import GMRRender, GMRRenderWithT, Renderer, camera_array, copy_h2d, pixel_offsets, render
 
-__all__ = ["GMRRender", "GMRRenderWithT", "Renderer", "GmrError", "camera_array", "load_library", "pixel_offsets", "render"]
+__all__ = ["GMRRender", "GMRRenderWithT", "Renderer", "GmrError", "camera_array", "copy_h2d", "load_library",
+           "pixel_offsets", "render"]

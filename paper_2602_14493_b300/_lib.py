@@ -33,7 +33,7 @@ EXPORTS = [
     "gmr_l2_loss",
     "gmr_get_device_status", "gmr_get_stats", "gmr_get_stage_times", "gmr_debug_forward_state",
     "gmr_l2_loss_noalloc", "gmr_adam_step", "gmr_chamfer", "gmr_render_bwd_ex", "gmr_silhouette_bce",
-    "gmr_mesh_regularizers", "gmr_render_bwd_l2",
+    "gmr_mesh_regularizers", "gmr_render_bwd_l2", "gmr_copy_h2d",
 ]
 
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "gmr_chamfer": (st, [P, P, i64, P, i64, P, P]),
         "gmr_render_bwd_ex": (st, [P, P, P, P, P, P, i32, P]),
         "gmr_render_bwd_l2": (st, [P, P, P, P, P, P, P, P, i32, P]),
+        "gmr_copy_h2d": (st, [P, P, i64, P]),
         "gmr_silhouette_bce": (st, [P, P, P, i64, ctypes.c_float, P, P, P]),
         "gmr_mesh_regularizers": (st, [P, P, i32, P, i32, ctypes.c_float, ctypes.c_float, P, P, P]),
         "gmr_get_device_status": (st, [P, P, ctypes.POINTER(ctypes.c_uint32)]),

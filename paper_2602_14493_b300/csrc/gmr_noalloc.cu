@@ -31,7 +31,7 @@
 namespace {
 
 // Completion counter + partial sums of one call (one double per block of
-// 8192 floats).
+// the loss kernel's grid, at most a few hundred).
 constexpr int64_t kNoAllocPartials = 16384 + 1;
 static __device__ __align__(256) double g_l2_partials[kNoAllocPartials];
 

@@ -431,6 +431,24 @@ class GMRRenderWithT(torch.autograd.Function):
         return dverts, drgb, (dop if ctx.has_opacity else None), None, None, None
 
 
+def copy_h2d(dst: torch.Tensor, src: torch.Tensor, stream=None) -> torch.Tensor:
+    """dst (device) <- src (page-locked host tensor, e.g. from pin_memory()),
+    copied by a kernel that reads the host buffer over the bus
+    (gmr_copy_h2d); asynchronous on the stream. Returns dst."""
+    if not dst.is_cuda or src.is_cuda or not src.is_pinned():
+        raise _lib.GmrError("copy_h2d: dst must be a CUDA tensor and src a pinned host tensor")
+    if not dst.is_contiguous() or not src.is_contiguous():
+        raise _lib.GmrError("copy_h2d: tensors must be contiguous")
+    n = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != n:
+        raise _lib.GmrError("copy_h2d: sizes differ")
+    L = _lib.load()
+    st = L.gmr_copy_h2d(ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(src.data_ptr()), n, _stream(stream))
+    if st != 0:
+        raise _lib.GmrError(f"gmr_copy_h2d failed ({st})")
+    return dst
+
+
 def render(verts, faces, rgb, opacity, cams, renderer: Renderer):
     """Differentiable batched render of all views (packed [Npix, 3])."""
     return GMRRender.apply(verts, rgb, opacity, faces, cams, renderer)

@@ -306,3 +306,35 @@ def test_stats_and_launch_count():
     # the workspace holds at least the per-record buffers (80 B per record)
     assert st["workspace_bytes"] >= 80 * st["n_records"]
     r.close()
+
+
+def test_copy_h2d_kernel_copy():
+    """gmr_copy_h2d: bytes equal after the copy for sizes with and without a
+    16-byte tail and for offset (unaligned) views; a pageable source is
+    refused before anything is launched."""
+    from paper_2602_14493_b300 import GmrError, copy_h2d
+
+    rng = np.random.default_rng(5)
+    for nbytes in (1, 15, 16, 17, 4096, 1 << 20, (25 << 20) + 12):
+        src = torch.from_numpy(rng.integers(0, 256, nbytes, dtype=np.uint8)).pin_memory()
+        dst = torch.zeros(nbytes, dtype=torch.uint8, device=DEV)
+        copy_h2d(dst, src)
+        torch.cuda.synchronize()
+        assert torch.equal(dst.cpu(), src)
+    big = torch.from_numpy(rng.integers(0, 256, 1 << 16, dtype=np.uint8)).pin_memory()
+    dst = torch.zeros(1 << 16, dtype=torch.uint8, device=DEV)
+    copy_h2d(dst[3:1003], big[7:1007])  # both views unaligned: the byte path
+    torch.cuda.synchronize()
+    assert torch.equal(dst[3:1003].cpu(), big[7:1007]) and int(dst[:3].sum()) == 0
+    with pytest.raises(GmrError):
+        copy_h2d(torch.zeros(64, dtype=torch.uint8, device=DEV), torch.zeros(64, dtype=torch.uint8))
+    # the library itself refuses pageable memory (no launch)
+    import ctypes
+
+    from paper_2602_14493_b300 import _lib
+
+    pageable = torch.zeros(64, dtype=torch.uint8)
+    d64 = torch.zeros(64, dtype=torch.uint8, device=DEV)
+    st = _lib.load().gmr_copy_h2d(ctypes.c_void_p(d64.data_ptr()), ctypes.c_void_p(pageable.data_ptr()), 64,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 1  # GMR_ERR_INVALID_ARG
