@@ -635,7 +635,7 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((stage, args.workload)),
                 "peak_source": "FP32 CUDA-core peak from unit counts and max clock (148 SM x 128 x 2 x 2.032 GHz)",
                 "ms": ms}
-    # memory-bound stages: algorithmic bytes
+    # memory-type stages: algorithmic bytes per record, pair, tile and face
     R = stats["n_records"]
     P = stats["n_pairs"]
     byts = {"project": R * 64 + len(scene.faces) * 28 + P * 4, "scan": stats["n_tiles"] * 8,
