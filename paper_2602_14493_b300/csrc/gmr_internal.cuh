@@ -57,6 +57,7 @@ struct Counters {
   uint32_t pad0;
   unsigned long long evals_fwd;
   unsigned long long contribs;
+  uint32_t n_class[16];  // tiles per work class (see tile_of_block)
   // cleared at the start of every backward
   unsigned long long evals_bwd;
   // GMR_DEV_* bits, sticky until gmr_get_device_status reads them
@@ -64,6 +65,30 @@ struct Counters {
   uint32_t pad1;
 };
 constexpr size_t kFwdCountersBytes = offsetof(Counters, evals_bwd);
+
+// Compositing order of the tiles, heaviest first (a longest-job-first
+// schedule: a heavy tile started late is what leaves SMs idle at the end of
+// a compositing launch). The binning puts every tile in the work class of
+// its pair count L, class 15 - bit_length(L) clamped to [0, 15] (so one
+// class per power of two, empty tiles last), at an atomically taken
+// position of that class's region of tile_order (regions of n_tiles
+// entries; filed by the scan of the tile counts); the compositing CTA b
+// takes the b-th tile in class order.
+constexpr int kTileClasses = 16;
+__device__ __forceinline__ int tile_class(uint32_t L) {
+  const int bits = 32 - __clz((int)L);
+  return kTileClasses - 1 - min(bits, kTileClasses - 1);
+}
+__device__ __forceinline__ int tile_of_block(const uint32_t* __restrict__ tile_order,
+                                             const uint32_t* __restrict__ n_class, int64_t n_tiles, int64_t b) {
+#pragma unroll 1
+  for (int c = 0; c < kTileClasses; ++c) {
+    const int64_t n = n_class[c];
+    if (b < n) return (int)tile_order[c * n_tiles + b];
+    b -= n;
+  }
+  return 0;  // not reached: the classes hold every tile
+}
 
 // ---------------------------------------------------------------- helpers
 // ---- double-float arithmetic (an unevaluated sum hi + lo of two floats) with
@@ -244,6 +269,7 @@ struct Workspace {
   uint32_t* tile_start = nullptr;  // exclusive scan of tile_count
   uint2* tile_range = nullptr;     // [start, end) per tile, (0, 0) when empty
   uint32_t* long_tiles = nullptr;  // tiles of more than 512 pairs (sorted by one CTA each)
+  uint32_t* tile_order = nullptr;  // kTileClasses regions of cap_tiles: compositing order
   // pairs
   int64_t cap_pairs = 0;
   // pair_key[0]: (depth bits << 32 | face) per pair in tile segments;
@@ -274,7 +300,7 @@ struct Workspace {
 // gmr_sort.cu: exclusive scan of n u32 values into out, their sum into
 // *total; src is set to zero
 cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* total, uint32_t* block_sums,
-                           cudaStream_t s, int64_t* launches);
+                           uint32_t* tile_order, uint32_t* n_class, cudaStream_t s, int64_t* launches);
 int64_t scan_block_sums_needed(int64_t n);
 // project.cu
 // Conversion + projection of every (view, face) record; also writes the

@@ -26,7 +26,9 @@
 // Gaussians cover a pixel or two).
 //
 // Layout: one CTA per screen tile of one view (all views of a batched call in
-// one launch; the tile id selects the view). The tile is cut into 8x4 pixel
+// one launch; the tile id selects the view), CTAs taking the tiles heaviest
+// first (pair-count classes set by the binning: fewer SMs idle at the end of
+// the launch). The tile is cut into 8x4 pixel
 // blocks; each warp owns a rectangle of 1, 2 or 4 blocks (8x4, 8x8 or 16x8
 // pixels, one pixel per lane in each block), so a thread composites 1, 2 or
 // 4 pixels. Each batch of listed Gaussians is staged in shared memory
@@ -258,14 +260,17 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
     uint32_t* __restrict__ pix_last, float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
-    int64_t n_pix_total, FwdLoss fl, Counters* __restrict__ counters) {
+    int64_t n_pix_total, FwdLoss fl, const uint32_t* __restrict__ tile_order, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
-  __shared__ int s_view;
-  const int g = blockIdx.x;
-  if (threadIdx.x == 0) s_view = find_view(views, C, g);
+  __shared__ int s_view, s_tile;
+  if (threadIdx.x == 0) {
+    s_tile = tile_of_block(tile_order, counters->n_class, gridDim.x, blockIdx.x);
+    s_view = find_view(views, C, s_tile);
+  }
   __syncthreads();
+  const int g = s_tile;
   const int c = s_view;
   const ViewInfo& v = views[c];
   const int lt = g - v.tile_base;
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   if (MODE == kFwdLoss) {  // one FP32 partial per warp, no block barrier
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
-    if ((threadIdx.x & 31) == 0) fl.part[(int64_t)blockIdx.x * NW + (threadIdx.x >> 5)] = lsum;
+    if ((threadIdx.x & 31) == 0) fl.part[(int64_t)g * NW + (threadIdx.x >> 5)] = lsum;
   }
 }
 
@@ -481,18 +486,20 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
     const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
-    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, Counters* __restrict__ counters) {
+    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, const uint32_t* __restrict__ tile_order,
+    Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
-  __shared__ int s_view;
+  __shared__ int s_view, s_tile;
   __shared__ uint32_t s_maxlast;
-  const int g = blockIdx.x;
   if (threadIdx.x == 0) {
-    s_view = find_view(views, C, g);
+    s_tile = tile_of_block(tile_order, counters->n_class, gridDim.x, blockIdx.x);
+    s_view = find_view(views, C, s_tile);
     s_maxlast = 0;
   }
   __syncthreads();
+  const int g = s_tile;
   const int c = s_view;
   const ViewInfo& v = views[c];
   const int lt = g - v.tile_base;
@@ -570,7 +577,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     for (int h = 1; h < NT / 32; h <<= 1)
 #pragma unroll
       for (int w = 0; w + h < NT / 32; w += 2 * h) b[w] += b[w + h];
-    bl.part[blockIdx.x] = b[0];
+    bl.part[g] = b[0];
   }
   const int end_all = (int)s_maxlast;
   const uint2 range = ranges[g];
@@ -779,7 +786,7 @@ void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
   kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
                                                                  images, ws.pix_T, ws.pix_last, t_out, nc_out,
-                                                                 ws.cap_pixels, fl, ws.counters);
+                                                                 ws.cap_pixels, fl, ws.tile_order, ws.counters);
   if (fl.target) k_sum_partials<<<1, 1024, 0, s>>>(fl.part, n_tiles * (NT / 32), 1.0, fl.loss);
 }
 
@@ -789,7 +796,7 @@ void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
   auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
   kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q, ws.face_col, views, C, F,
                                         bg[0], bg[1], bg[2], dL, dLdT, ws.pix_T, ws.pix_last, ws.rec_grad,
-                                        ws.face_grad, bl, ws.counters);
+                                        ws.face_grad, bl, ws.tile_order, ws.counters);
 }
 
 }  // namespace

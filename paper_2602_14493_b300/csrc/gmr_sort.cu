@@ -4,6 +4,14 @@
 // Up to kSingleMax values: one CTA walks the array in chunks of 8192 with a
 // running carry (one launch); beyond, reduce-then-scan over many CTAs (three
 // launches, no block waits on another).
+//
+// The same pass files every tile under its work class (tile_class of its
+// pair count) in the compositing order (tile_of_block): each CTA counts its
+// chunk's tiles per class in shared memory (warp-aggregated) and writes them
+// into its run of each class's region, the runs in chunk order (so tiles of
+// one view stay together within a class): the single CTA takes its runs
+// chunk by chunk, the multi-CTA scan from per-block class counts scanned in
+// block order.
 
 #include "gmr_internal.cuh"
 
@@ -46,25 +54,100 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem_w
   return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ src, int64_t n,
-                                                              uint32_t* __restrict__ block_sums) {
-  __shared__ uint32_t sw[33];
-  int64_t base = (int64_t)blockIdx.x * kScanTile;
-  uint32_t acc = 0;
+// Counts the tiles i0 + k (k < NI, i0 + k < n) of the calling thread, with
+// pair counts v[k], in the CTA's per-class counters s_hist (warp-aggregated
+// shared-memory atomics) and returns each tile's class and rank within the
+// CTA's tiles of that class.
+template <int NI>
+__device__ __forceinline__ void count_classes(const uint32_t (&v)[NI], int64_t i0, int64_t n, uint32_t (&rank)[NI],
+                                              int (&cls)[NI], uint32_t* s_hist) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-    if (i < n) acc += src[i];
+  for (int k = 0; k < NI; ++k) {
+    const bool ok = i0 + k < n;
+    cls[k] = tile_class(v[k]);
+    const uint32_t key = ok ? (uint32_t)cls[k] : 0xffffffffu;  // idle lanes in a group of their own
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (ok && lane == leader) base = atomicAdd(&s_hist[cls[k]], (uint32_t)__popc(peers));
+    rank[k] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & lt);
   }
-  uint32_t tot;
-  block_excl_scan(acc, sw, &tot);
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-// Single block: exclusive scan of the block sums in place, total to *total.
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ sums, int64_t nb,
-                                                   uint32_t* __restrict__ total) {
+// Files the tiles i0 + k (k < NI, i0 + k < n) of every thread of the CTA
+// under their classes: tile_order[c * n + slot], slot = the CTA's run of
+// class c + the tile's rank. The runs come from block_base (kTileClasses
+// offsets, when given) or are reserved from n_class by one global atomic per
+// class. Every thread of the CTA calls it (it holds barriers); s_hist and
+// s_base are kTileClasses words of shared memory each.
+template <int NI>
+__device__ __forceinline__ void file_tiles(const uint32_t (&v)[NI], int64_t i0, int64_t n,
+                                           uint32_t* __restrict__ tile_order, uint32_t* __restrict__ n_class,
+                                           const uint32_t* __restrict__ block_base, uint32_t* s_hist,
+                                           uint32_t* s_base) {
+  if (threadIdx.x < kTileClasses) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
+  uint32_t rank[NI];
+  int cls[NI];
+  count_classes<NI>(v, i0, n, rank, cls, s_hist);
+  __syncthreads();
+  if (threadIdx.x < kTileClasses) {
+    const uint32_t cnt = s_hist[threadIdx.x];
+    s_base[threadIdx.x] = block_base ? block_base[threadIdx.x] : (cnt ? atomicAdd(&n_class[threadIdx.x], cnt) : 0u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NI; ++k)
+    if (i0 + k < n) tile_order[cls[k] * n + s_base[cls[k]] + rank[k]] = (uint32_t)(i0 + k);
+  __syncthreads();
+}
+
+// Per block of kScanTile values: their sum, and (block_hist, kTileClasses
+// words per block) how many of them fall in each work class.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ src, int64_t n,
+                                                              uint32_t* __restrict__ block_sums,
+                                                              uint32_t* __restrict__ block_hist) {
   __shared__ uint32_t sw[33];
+  __shared__ uint32_t s_hist[kTileClasses];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (threadIdx.x < kTileClasses) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
+  uint32_t acc = 0;
+  uint32_t v[kScanItems];
+  const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = i0 + k < n ? src[i0 + k] : 0u;
+    acc += v[k];
+  }
+  uint32_t rank[kScanItems];
+  int cls[kScanItems];
+  count_classes<kScanItems>(v, i0, n, rank, cls, s_hist);
+  uint32_t tot;
+  block_excl_scan(acc, sw, &tot);  // (barriers inside)
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+  if (threadIdx.x < kTileClasses) block_hist[(int64_t)blockIdx.x * kTileClasses + threadIdx.x] = s_hist[threadIdx.x];
+}
+
+// Single block: exclusive scan of the block sums in place, total to *total;
+// per class, the blocks' counts turned into their offsets in block order
+// (so each class keeps the tiles' order across blocks) and the class
+// totals written to n_class.
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ sums, int64_t nb,
+                                                   uint32_t* __restrict__ total, uint32_t* __restrict__ block_hist,
+                                                   uint32_t* __restrict__ n_class) {
+  __shared__ uint32_t sw[33];
+  if (threadIdx.x < kTileClasses) {
+    uint32_t run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+      const uint32_t c = block_hist[b * kTileClasses + threadIdx.x];
+      block_hist[b * kTileClasses + threadIdx.x] = run;
+      run += c;
+    }
+    n_class[threadIdx.x] = run;
+  }
   uint32_t carry = 0;
   for (int64_t base = 0; base < nb; base += blockDim.x) {
     int64_t i = base + threadIdx.x;
@@ -79,9 +162,11 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ sums, 
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ src, int64_t n,
                                                             const uint32_t* __restrict__ block_sums,
-                                                            uint32_t* __restrict__ out) {
+                                                            uint32_t* __restrict__ out, uint32_t* __restrict__ tile_order,
+                                                            const uint32_t* __restrict__ block_hist) {
   __shared__ uint32_t sw[33];
   __shared__ uint32_t tile[kScanTile];
+  __shared__ uint32_t s_hist[kTileClasses], s_base[kTileClasses];
   int64_t base = (int64_t)blockIdx.x * kScanTile;
   // coalesced load into shared memory, then each thread scans 8 consecutive
 #pragma unroll
@@ -99,6 +184,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
     v[k] = tile[threadIdx.x * kScanItems + k];
     acc += v[k];
   }
+  file_tiles<kScanItems>(v, base + (int64_t)threadIdx.x * kScanItems, n, tile_order, nullptr,
+                         block_hist + (int64_t)blockIdx.x * kTileClasses, s_hist, s_base);
   uint32_t tot;
   uint32_t pre = block_excl_scan(acc, sw, &tot) + block_sums[blockIdx.x];
 #pragma unroll
@@ -124,8 +211,11 @@ constexpr int64_t kSingleMax = 4 * kSingleChunk;
 // path for the ragged last chunk.
 __global__ void __launch_bounds__(kSingleThreads) k_scan_single(uint32_t* __restrict__ src, int64_t n,
                                                                 uint32_t* __restrict__ out,
-                                                                uint32_t* __restrict__ total) {
+                                                                uint32_t* __restrict__ total,
+                                                                uint32_t* __restrict__ tile_order,
+                                                                uint32_t* __restrict__ n_class) {
   __shared__ uint32_t sw[33];
+  __shared__ uint32_t s_hist[kTileClasses], s_base[kTileClasses];
   uint32_t carry = 0;
   for (int64_t base = 0; base < n; base += kSingleChunk) {
     const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
@@ -146,6 +236,7 @@ __global__ void __launch_bounds__(kSingleThreads) k_scan_single(uint32_t* __rest
         if (i0 + k < n) src[i0 + k] = 0u;
       }
     }
+    file_tiles<kScanItems>(v, i0, n, tile_order, n_class, nullptr, s_hist, s_base);
     uint32_t acc = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) acc += v[k];
@@ -172,10 +263,11 @@ __global__ void __launch_bounds__(kSingleThreads) k_scan_single(uint32_t* __rest
 
 }  // namespace
 
-int64_t scan_block_sums_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+// block sums, then kTileClasses class counts per block
+int64_t scan_block_sums_needed(int64_t n) { return ((n + kScanTile - 1) / kScanTile + 1) * (1 + kTileClasses); }
 
 cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* total, uint32_t* block_sums,
-                           cudaStream_t s, int64_t* launches) {
+                           uint32_t* tile_order, uint32_t* n_class, cudaStream_t s, int64_t* launches) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
     return cudaGetLastError();
@@ -183,14 +275,15 @@ cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* to
   // the vector path needs 16-byte aligned arrays (workspace allocations are)
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
   if (n <= kSingleMax && aligned) {
-    k_scan_single<<<1, kSingleThreads, 0, s>>>(src, n, out, total);
+    k_scan_single<<<1, kSingleThreads, 0, s>>>(src, n, out, total, tile_order, n_class);
     *launches += 1;
     return cudaGetLastError();
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums);
-  k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, total);
-  k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums, out);
+  uint32_t* block_hist = block_sums + nb + 1;
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums, block_hist);
+  k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, total, block_hist, n_class);
+  k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums, out, tile_order, block_hist);
   *launches += 3;
   return cudaGetLastError();
 }
