@@ -246,11 +246,15 @@ constexpr int kTilesPerCta = kTileSortThreads / 32;
 __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
     const uint32_t* __restrict__ tile_start, int64_t n_tiles, const unsigned long long* __restrict__ keys,
     uint32_t* __restrict__ pair_face, uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
-    Counters* __restrict__ counters, int64_t cap) {
+    const uint32_t* __restrict__ tile_order, Counters* __restrict__ counters, int64_t cap) {
   __shared__ unsigned long long s_keys[kTilesPerCta][kWarpSortMax];
   const int lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
-  if (t >= n_tiles) return;
+  const int64_t w = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
+  if (w >= n_tiles) return;
+  // warps take the tiles heaviest first, as the compositing does
+  int64_t t = 0;
+  if (lane == 0) t = tile_of_block(tile_order, counters->n_class, n_tiles, w);
+  t = __shfl_sync(0xffffffffu, t, 0);
   const uint32_t P = counters->n_pairs;
   if ((int64_t)P > cap) {  // overflow: the keys were not written
     if (lane == 0) ranges[t] = make_uint2(0u, 0u);
@@ -444,8 +448,8 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
   }
   if (n_tiles > 0) {
     k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kTileSortThreads, 0, s>>>(
-        ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.counters,
-        ws.cap_pairs);
+        ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.tile_order,
+        ws.counters, ws.cap_pairs);
     // the dynamic shared memory limit is a per-device attribute of the kernel
     static std::atomic<bool> smem_set[64];
     int dev = 0;
