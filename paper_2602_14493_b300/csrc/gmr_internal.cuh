@@ -57,7 +57,7 @@ struct Counters {
   uint32_t pad0;
   unsigned long long evals_fwd;
   unsigned long long contribs;
-  uint32_t n_class[16];  // tiles per work class (see tile_of_block)
+  uint32_t n_class[16];  // tiles per work class (see tile_of_block); 16-byte aligned
   // cleared at the start of every backward
   unsigned long long evals_bwd;
   // GMR_DEV_* bits, sticky until gmr_get_device_status reads them
@@ -65,6 +65,7 @@ struct Counters {
   uint32_t pad1;
 };
 constexpr size_t kFwdCountersBytes = offsetof(Counters, evals_bwd);
+static_assert(offsetof(Counters, n_class) % 16 == 0, "n_class is read with 16-byte loads");
 
 // Compositing order of the tiles, heaviest first (a longest-job-first
 // schedule: a heavy tile started late is what leaves SMs idle at the end of
@@ -81,13 +82,22 @@ __device__ __forceinline__ int tile_class(uint32_t L) {
 }
 __device__ __forceinline__ int tile_of_block(const uint32_t* __restrict__ tile_order,
                                              const uint32_t* __restrict__ n_class, int64_t n_tiles, int64_t b) {
-#pragma unroll 1
-  for (int c = 0; c < kTileClasses; ++c) {
-    const int64_t n = n_class[c];
-    if (b < n) return (int)tile_order[c * n_tiles + b];
-    b -= n;
+  // the 16 class counts in four 16-byte loads issued together (n_class is
+  // 16-byte aligned in the counters block)
+  static_assert(kTileClasses == 16, "class counts are read as four uint4");
+  const uint4* q = reinterpret_cast<const uint4*>(n_class);
+  const uint4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+  const uint32_t n[kTileClasses] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                                    q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < kTileClasses - 1; ++k) {
+    if (c == k && b >= (int64_t)n[k]) {
+      b -= n[k];
+      c = k + 1;
+    }
   }
-  return 0;  // not reached: the classes hold every tile
+  return (int)tile_order[c * n_tiles + b];
 }
 
 // ---------------------------------------------------------------- helpers
