@@ -265,9 +265,12 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
   __shared__ int s_view, s_tile;
-  if (threadIdx.x == 0) {
-    s_tile = tile_of_block(tile_order, counters->n_class, gridDim.x, blockIdx.x);
-    s_view = find_view(views, C, s_tile);
+  __shared__ uint2 s_range;
+  if (threadIdx.x == 0) {  // the tile, its view and its pair range before the other threads need them
+    const int gt = tile_of_block(tile_order, counters->n_class, gridDim.x, blockIdx.x);
+    s_tile = gt;
+    s_range = ranges[gt];
+    s_view = find_view(views, C, gt);
   }
   __syncthreads();
   const int g = s_tile;
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     }
   }
   if (MODE == kFwdLoss) asm volatile("cp.async.commit_group;" ::: "memory");
-  const uint2 range = ranges[g];
+  const uint2 range = s_range;
   const int n = (int)(range.y - range.x);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
 
