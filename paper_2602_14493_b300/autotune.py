@@ -64,7 +64,7 @@ def _store(d):
         pass
 
 
-def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=5, candidates=CANDIDATES, use_cache=True):
+def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates=CANDIDATES, use_cache=True):
     """Times each candidate shape on this workload and configures
     ``renderer`` with the fastest. Returns (best (tile, threads,
     threads_bwd, batch), {shape: median ms})."""
