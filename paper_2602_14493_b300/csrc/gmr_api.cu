@@ -193,6 +193,7 @@ gmr_status ensure_tiles(gmr_ctx* ctx, int64_t n, bool capturing) {
     if ((s = realloc_exact(ctx, &w.tile_range, cap, "tile_range")) != GMR_OK) return s;
     if ((s = realloc_exact(ctx, &w.long_tiles, cap, "long_tiles")) != GMR_OK) return s;
     if ((s = realloc_exact(ctx, &w.tile_order, gmr::kTileClasses * cap, "tile_order")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.tile_desc, cap, "tile_desc")) != GMR_OK) return s;
     if ((s = zero_new(ctx, w.tile_count, sizeof(uint32_t) * (size_t)cap, "tile_count")) != GMR_OK) return s;
     w.cap_tiles = cap;
   }
@@ -382,7 +383,7 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
   Workspace& w = ctx->ws;
   void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.face_col,
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
-                  w.tile_order,
+                  w.tile_order, w.tile_desc,
                   w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch};
   for (void* p : bufs)
     if (p) cudaFree(p);
@@ -528,7 +529,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   // ranges
   {
     StageTimer t(ctx, GMR_STAGE_BIN, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_bin_pairs(w, n_rec, F, w.views, n_tiles, s, &ctx->launches));
+    GMR_CUDA(ctx, gmr::launch_bin_pairs(w, n_rec, F, w.views, C, n_tiles, s, &ctx->launches));
   }
   // S7: compositing
   {

@@ -239,14 +239,17 @@ constexpr int kWarpSortMax = 512;   // keys sorted by one warp
 constexpr int kTileSortThreads = 64;  // small CTAs: tiles of uneven length retire independently
 constexpr int kTilesPerCta = kTileSortThreads / 32;
 
-// One warp per global tile: write the range; sort segments of up to 256 keys
+// One warp per global tile, warp w taking the w-th tile of the compositing
+// order: write the range and, at position w, the tile's descriptor (tile,
+// view, range) for the compositing CTA w; sort segments of up to 256 keys
 // in registers (8 per lane at most, which keeps the register count and so
 // the occupancy at that of the common case) and of 257 to 512 keys in
 // shared memory; list longer segments for k_long_sort.
 __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
     const uint32_t* __restrict__ tile_start, int64_t n_tiles, const unsigned long long* __restrict__ keys,
     uint32_t* __restrict__ pair_face, uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
-    const uint32_t* __restrict__ tile_order, Counters* __restrict__ counters, int64_t cap) {
+    const uint32_t* __restrict__ tile_order, const ViewInfo* __restrict__ views, int32_t C,
+    uint4* __restrict__ tile_desc, Counters* __restrict__ counters, int64_t cap) {
   __shared__ unsigned long long s_keys[kTilesPerCta][kWarpSortMax];
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
@@ -257,14 +260,22 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
   t = __shfl_sync(0xffffffffu, t, 0);
   const uint32_t P = counters->n_pairs;
   if ((int64_t)P > cap) {  // overflow: the keys were not written
-    if (lane == 0) ranges[t] = make_uint2(0u, 0u);
+    if (lane == 0) {
+      ranges[t] = make_uint2(0u, 0u);
+      tile_desc[w] = make_uint4((uint32_t)t, (uint32_t)find_view(views, C, (int)t), 0u, 0u);
+    }
     if (t == 0 && lane == 0) atomicOr(&counters->status, kDevOverflow);
     return;
   }
   const uint32_t start = tile_start[t];
   const uint32_t end = (t + 1 < n_tiles) ? tile_start[t + 1] : P;
   const int L = (int)(end - start);
-  if (lane == 0) ranges[t] = L > 0 ? make_uint2(start, end) : make_uint2(0u, 0u);
+  if (lane == 0) {
+    const uint2 rg = L > 0 ? make_uint2(start, end) : make_uint2(0u, 0u);
+    ranges[t] = rg;
+    // what the compositing CTA at this position needs first, in one record
+    tile_desc[w] = make_uint4((uint32_t)t, (uint32_t)find_view(views, C, (int)t), rg.x, rg.y);
+  }
   if (L <= 0) return;
   const unsigned long long* gk = keys + start;
   uint32_t* out = pair_face + start;
@@ -435,9 +446,8 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 
 }  // namespace
 
-cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int64_t n_tiles,
-                             cudaStream_t s, int64_t* launches) {
-  (void)views;
+cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
+                             int64_t n_tiles, cudaStream_t s, int64_t* launches) {
   if (n_rec > 0 && ws.cap_pairs > 0) {
     // one thread per pair slot (a grid-stride loop over 148 x 8 blocks left
     // each thread's dependent gathers in series: 13% slower on 38M pairs)
@@ -449,7 +459,7 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
   if (n_tiles > 0) {
     k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kTileSortThreads, 0, s>>>(
         ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.tile_order,
-        ws.counters, ws.cap_pairs);
+        views, C, ws.tile_desc, ws.counters, ws.cap_pairs);
     // the dynamic shared memory limit is a per-device attribute of the kernel
     static std::atomic<bool> smem_set[64];
     int dev = 0;

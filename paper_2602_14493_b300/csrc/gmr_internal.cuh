@@ -73,13 +73,25 @@ static_assert(offsetof(Counters, n_class) % 16 == 0, "n_class is read with 16-by
 // its pair count L, class 15 - bit_length(L) clamped to [0, 15] (so one
 // class per power of two, empty tiles last), at an atomically taken
 // position of that class's region of tile_order (regions of n_tiles
-// entries; filed by the scan of the tile counts); the compositing CTA b
-// takes the b-th tile in class order.
+// entries; filed by the scan of the tile counts). The per-tile sort's warp
+// w takes the w-th tile in class order and writes, at position w, the
+// descriptor (tile, view, pair range) that compositing CTA w reads as its
+// first load.
 constexpr int kTileClasses = 16;
 __device__ __forceinline__ int tile_class(uint32_t L) {
   const int bits = 32 - __clz((int)L);
   return kTileClasses - 1 - min(bits, kTileClasses - 1);
 }
+// Binary search of the view owning global tile g.
+__device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (views[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int tile_of_block(const uint32_t* __restrict__ tile_order,
                                              const uint32_t* __restrict__ n_class, int64_t n_tiles, int64_t b) {
   // the 16 class counts in four 16-byte loads issued together (n_class is
@@ -280,6 +292,7 @@ struct Workspace {
   uint2* tile_range = nullptr;     // [start, end) per tile, (0, 0) when empty
   uint32_t* long_tiles = nullptr;  // tiles of more than 512 pairs (sorted by one CTA each)
   uint32_t* tile_order = nullptr;  // kTileClasses regions of cap_tiles: compositing order
+  uint4* tile_desc = nullptr;      // per compositing position: (tile, view, range start, range end)
   // pairs
   int64_t cap_pairs = 0;
   // pair_key[0]: (depth bits << 32 | face) per pair in tile segments;
@@ -328,7 +341,8 @@ cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, 
 
 // raster.cu
 // bin.cu: scatter keys into tile segments, sort each segment, write ranges.
-cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int64_t n_tiles,
+cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
+                             int64_t n_tiles,
                              cudaStream_t s, int64_t* launches);
 cudaError_t launch_expand_tiles(const uint2* ranges, int64_t n_tiles, uint32_t* tile_ids, cudaStream_t s,
                                 int64_t* launches);

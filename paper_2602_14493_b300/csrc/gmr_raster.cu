@@ -45,16 +45,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Binary search of the view owning global tile g.
-__device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
-  int lo = 0, hi = C - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (views[mid].tile_base <= g) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Pixel layout of a tile of TS x TS pixels served by NT threads: the tile is
 // cut into 8x4-pixel blocks (row-major, TS/8 per row). Each warp owns a
 // rectangle of PPT blocks, RW blocks wide and PPT/RW high (1 block, 8x8 or
@@ -260,21 +250,14 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
     uint32_t* __restrict__ pix_last, float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
-    int64_t n_pix_total, FwdLoss fl, const uint32_t* __restrict__ tile_order, Counters* __restrict__ counters) {
+    int64_t n_pix_total, FwdLoss fl, const uint4* __restrict__ tile_desc, Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
-  __shared__ int s_view, s_tile;
-  __shared__ uint2 s_range;
-  if (threadIdx.x == 0) {  // the tile, its view and its pair range before the other threads need them
-    const int gt = tile_of_block(tile_order, counters->n_class, gridDim.x, blockIdx.x);
-    s_tile = gt;
-    s_range = ranges[gt];
-    s_view = find_view(views, C, gt);
-  }
-  __syncthreads();
-  const int g = s_tile;
-  const int c = s_view;
+  // the tile at this compositing position, its view and its pair range
+  const uint4 desc = __ldg(tile_desc + blockIdx.x);
+  const int g = (int)desc.x;
+  const int c = (int)desc.y;
   const ViewInfo& v = views[c];
   const int lt = g - v.tile_base;
   const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
@@ -315,7 +298,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     }
   }
   if (MODE == kFwdLoss) asm volatile("cp.async.commit_group;" ::: "memory");
-  const uint2 range = s_range;
+  const uint2 range = make_uint2(desc.z, desc.w);
   const int n = (int)(range.y - range.x);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
 
@@ -489,21 +472,18 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
     const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
-    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, const uint32_t* __restrict__ tile_order,
+    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, const uint4* __restrict__ tile_desc,
     Counters* __restrict__ counters) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
-  __shared__ int s_view, s_tile;
   __shared__ uint32_t s_maxlast;
-  if (threadIdx.x == 0) {
-    s_tile = tile_of_block(tile_order, counters->n_class, gridDim.x, blockIdx.x);
-    s_view = find_view(views, C, s_tile);
-    s_maxlast = 0;
-  }
+  // the tile at this compositing position, its view and its pair range
+  const uint4 desc = __ldg(tile_desc + blockIdx.x);
+  const int g = (int)desc.x;
+  const int c = (int)desc.y;
+  if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
-  const int g = s_tile;
-  const int c = s_view;
   const ViewInfo& v = views[c];
   const int lt = g - v.tile_base;
   const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
@@ -583,7 +563,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
     bl.part[g] = b[0];
   }
   const int end_all = (int)s_maxlast;
-  const uint2 range = ranges[g];
+  const uint2 range = make_uint2(desc.z, desc.w);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
   unsigned long long evals = 0;
 #pragma unroll
@@ -789,7 +769,7 @@ void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
   kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
                                                                  ws.face_col, views, C, F, bg[0], bg[1], bg[2],
                                                                  images, ws.pix_T, ws.pix_last, t_out, nc_out,
-                                                                 ws.cap_pixels, fl, ws.tile_order, ws.counters);
+                                                                 ws.cap_pixels, fl, ws.tile_desc, ws.counters);
   if (fl.target) k_sum_partials<<<1, 1024, 0, s>>>(fl.part, n_tiles * (NT / 32), 1.0, fl.loss);
 }
 
@@ -799,7 +779,7 @@ void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face,
   auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
   kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q, ws.face_col, views, C, F,
                                         bg[0], bg[1], bg[2], dL, dLdT, ws.pix_T, ws.pix_last, ws.rec_grad,
-                                        ws.face_grad, bl, ws.tile_order, ws.counters);
+                                        ws.face_grad, bl, ws.tile_desc, ws.counters);
 }
 
 }  // namespace
