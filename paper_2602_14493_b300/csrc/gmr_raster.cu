@@ -627,15 +627,11 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(
       if (__popc(cm) <= kBwdDirectLanes) {
         // few contributing lanes: their own atomics cost fewer instructions
         // than the warp reduction
-        if (any) {
-          float* rg = reinterpret_cast<float*>(rec_grad + 2 * (size_t)st.rid[j]);
-          float* fg = reinterpret_cast<float*>(face_grad + st.face[j]);
-#pragma unroll
-          for (int q = 0; q < 5; ++q) atomicAdd(rg + q, acc[q]);
-          atomicAdd(fg + 3, acc[5]);
-          atomicAdd(fg + 0, acc[6]);
-          atomicAdd(fg + 1, acc[7]);
-          atomicAdd(fg + 2, acc[8]);
+        if (any) {  // 16-byte vector atomics: 3 instead of 9
+          float4* rg = rec_grad + 2 * (size_t)st.rid[j];
+          atomicAdd(rg, make_float4(acc[0], acc[1], acc[2], acc[3]));
+          atomicAdd(reinterpret_cast<float*>(rg + 1), acc[4]);
+          atomicAdd(face_grad + st.face[j], make_float4(acc[6], acc[7], acc[8], acc[5]));
         }
         continue;
       }
