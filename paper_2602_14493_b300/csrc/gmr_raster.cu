@@ -20,10 +20,11 @@
 // sum q and sum alpha T g; the record backward turns the first two into the
 // mean gradient with the conic. A warp reduces its 32 pixels' contributions
 // to one Gaussian with a transposed butterfly (9 values in 14 shuffles) and
-// eight lanes then issue one atomic add each; when at most 8 lanes
-// contribute, those lanes add their own values instead (measured faster:
-// 6% on a 20K-face mesh in 8 views of 512^2, 14-17% on meshes whose
-// Gaussians cover a pixel or two).
+// eight lanes then issue one atomic add each; when at most 20 lanes
+// contribute, those lanes add their own values instead, with three atomic
+// adds each (two of them 16-byte vectors): together 11-19% faster than
+// always reducing on a 20K-face mesh in 8 views of 512^2, 25-35% on meshes
+// whose Gaussians cover a pixel or two.
 //
 // Layout: one CTA per screen tile of one view (all views of a batched call in
 // one launch; the tile id selects the view), CTAs taking the tiles heaviest
@@ -456,10 +457,10 @@ __device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int l
 
 // A list entry whose contributions come from at most this many lanes of a
 // warp is added by those lanes' own atomics instead of the warp reduction
-// (swept 0-32 on four workloads: 8 is best on all; above it same-address
-// atomics serialise).
+// (swept 0-32 on four workloads: with scalar atomics 8 was best, with the
+// vector atomics 20; above that, same-address atomics serialise).
 #ifndef GMR_BWD_DIRECT_LANES
-#define GMR_BWD_DIRECT_LANES 8
+#define GMR_BWD_DIRECT_LANES 20
 #endif
 constexpr int kBwdDirectLanes = GMR_BWD_DIRECT_LANES;
 
