@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -13,6 +14,16 @@
 using gmr::Counters;
 using gmr::ViewInfo;
 using gmr::Workspace;
+
+namespace gmr {
+bool chained_launch_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("GMR_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+}  // namespace gmr
 
 struct gmr_ctx {
   gmr_config cfg;

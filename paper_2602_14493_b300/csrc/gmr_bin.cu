@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
     const unsigned long long* __restrict__ pair_tr, const uint32_t* __restrict__ pair_rec,
     const uint32_t* __restrict__ rec_key, int32_t F, const uint32_t* __restrict__ tile_start, int64_t cap,
     unsigned long long* __restrict__ keys, const Counters* __restrict__ counters) {
+  pdl_enter();
   const int64_t n = counters->n_pairs;
   if (n > cap) return;  // overflow: the pair scratch is incomplete
   for (int64_t i = (int64_t)blockIdx.x * kPlaceThreads + threadIdx.x; i < n;
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
     uint32_t* __restrict__ pair_face, uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
     const uint32_t* __restrict__ tile_order, const ViewInfo* __restrict__ views, int32_t C,
     uint4* __restrict__ tile_desc, Counters* __restrict__ counters, int64_t cap) {
+  pdl_enter();
   __shared__ unsigned long long s_keys[kTilesPerCta][kWarpSortMax];
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kTilesPerCta + (threadIdx.x >> 5);
@@ -363,11 +365,12 @@ __device__ __forceinline__ void cta_sort_chunks(const unsigned long long* __rest
 // LSD radix passes on the 8-bit digits that differ within the segment,
 // through global memory.
 __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __restrict__ long_list,
-                                                           const Counters* __restrict__ counters,
+                                                           Counters* __restrict__ counters,
                                                            const uint2* __restrict__ ranges,
                                                            unsigned long long* __restrict__ keys,
                                                            unsigned long long* __restrict__ keys_tmp,
                                                            uint32_t* __restrict__ pair_face) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned long long s_dyn[];
   unsigned long long* sa = s_dyn;                 // kSegSmem keys
   unsigned long long* sb = s_dyn + kSegSmem;      // kSegSmem keys
@@ -375,8 +378,16 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
   __shared__ uint32_t sw[32];
   __shared__ unsigned long long red_and[kSegWarps], red_or[kSegWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ uint32_t s_next;
   const uint32_t nlong = counters->n_long;
-  for (uint32_t li = blockIdx.x; li < nlong; li += gridDim.x) {
+  // segments are taken from a shared cursor, not by CTA index: a CTA that
+  // starts late (or shares its SM) takes fewer
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(&counters->long_next, 1u);
+    __syncthreads();
+    const uint32_t li = s_next;
+    __syncthreads();
+    if (li >= nlong) break;
     const uint2 rg = ranges[long_list[li]];
     const int L = (int)(rg.y - rg.x);
     unsigned long long* gk = keys + rg.x;
@@ -452,14 +463,14 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
     // one thread per pair slot (a grid-stride loop over 148 x 8 blocks left
     // each thread's dependent gathers in series: 13% slower on 38M pairs)
     const int64_t blocks = (ws.cap_pairs + kPlaceThreads - 1) / kPlaceThreads;
-    k_place_keys<<<(unsigned)blocks, kPlaceThreads, 0, s>>>(ws.pair_key[1], ws.pair_face, ws.rec_key, F,
-                                                          ws.tile_start, ws.cap_pairs, ws.pair_key[0], ws.counters);
+    cudaError_t e = launch_chained(k_place_keys, true, dim3((unsigned)blocks), dim3(kPlaceThreads), 0, s,
+                                   (const unsigned long long*)ws.pair_key[1], (const uint32_t*)ws.pair_face,
+                                   (const uint32_t*)ws.rec_key, F, (const uint32_t*)ws.tile_start, ws.cap_pairs,
+                                   ws.pair_key[0], (const Counters*)ws.counters);
     *launches += 1;
+    if (e != cudaSuccess) return e;
   }
   if (n_tiles > 0) {
-    k_tile_sort<<<(unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta), kTileSortThreads, 0, s>>>(
-        ws.tile_start, n_tiles, ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles, ws.tile_order,
-        views, C, ws.tile_desc, ws.counters, ws.cap_pairs);
     // the dynamic shared memory limit is a per-device attribute of the kernel
     static std::atomic<bool> smem_set[64];
     int dev = 0;
@@ -470,9 +481,16 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
       if (e != cudaSuccess) return e;
       if (dev >= 0 && dev < 64) smem_set[dev].store(true);
     }
-    k_long_sort<<<148 * 3, kSegThreads, kLongSortSmem, s>>>(ws.long_tiles, ws.counters, ws.tile_range,
-                                                             ws.pair_key[0], ws.pair_key[1], ws.pair_face);
+    e = launch_chained(k_tile_sort, false, dim3((unsigned)((n_tiles + kTilesPerCta - 1) / kTilesPerCta)),
+                       dim3(kTileSortThreads), 0, s, (const uint32_t*)ws.tile_start, n_tiles,
+                       (const unsigned long long*)ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles,
+                       (const uint32_t*)ws.tile_order, views, C, ws.tile_desc, ws.counters, ws.cap_pairs);
+    if (e != cudaSuccess) return e;
+    e = launch_chained(k_long_sort, true, dim3(148 * 3), dim3(kSegThreads), kLongSortSmem, s,
+                       (const uint32_t*)ws.long_tiles, ws.counters, (const uint2*)ws.tile_range,
+                       ws.pair_key[0], ws.pair_key[1], ws.pair_face);
     *launches += 2;
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

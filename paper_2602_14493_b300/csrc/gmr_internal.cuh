@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "gmr.h"
 
 namespace gmr {
@@ -34,6 +36,47 @@ constexpr float kLn2 = 0.69314718055994531f;
 
 constexpr int kMaxViews = 65535;
 
+// ---------------------------------------------------------------- launch chain
+// Programmatic dependent launch. The step's kernels are launched with
+// launch_chained(kern, chained = true, ...): such a kernel may be scheduled
+// while the kernel before it on the stream is still running, and its CTAs
+// then block in pdl_enter() until that kernel has completed and its writes
+// are visible. So pdl_enter() is the first statement of every kernel of the
+// step (before any global access, and before any early return: a kernel's
+// completion then implies that of every kernel before it). The kernel also
+// releases its own dependent at once: the dependent's CTAs take SM slots
+// only as this kernel's CTAs retire (all of them have started by then),
+// which hides the launch latency and the tail between two kernels. Without
+// the launch attribute both instructions do nothing.
+// Kernels whose CTAs take tiles heaviest first (the per-tile sort and the
+// two compositing kernels) are launched with chained = false: an early
+// launch places their first, heaviest CTAs on whichever SMs free up first,
+// several to one SM, and their tail grows (the level-8 mesh step: +10%).
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Whether launch_chained() sets the attribute (GMR_PDL=0 in the environment
+// turns it off; read once).
+bool chained_launch_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kern)(KArgs...), bool chained, dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained && chained_launch_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------- view table
 struct ViewInfo {
   float R[9];
@@ -54,7 +97,7 @@ struct Counters {
   uint32_t n_pairs;     // total pairs of the current forward (scan total)
   uint32_t pair_alloc;  // pair slots handed out by the projection
   uint32_t n_long;      // tiles whose segment is too long for a warp sort
-  uint32_t pad0;
+  uint32_t long_next;   // k_long_sort's work cursor into the long-segment list
   unsigned long long evals_fwd;
   unsigned long long contribs;
   uint32_t n_class[16];  // tiles per work class (see tile_of_block); 16-byte aligned

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
     int64_t cap_pairs, unsigned long long* __restrict__ pair_tr, uint32_t* __restrict__ pair_rec,
     Counters* __restrict__ counters) {
+  pdl_enter();
   __shared__ ViewInfo sv;
   __shared__ uint32_t s_off[kProjThreads / 32][32];
   __shared__ uint2 s_first[kProjThreads / 32][32];  // (first tile, rectangle width)
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ opacity,
     const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q, const float4* __restrict__ face_grad,
     float* __restrict__ dverts, float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
+  pdl_enter();
   const int64_t gid = (int64_t)blockIdx.x * kProjBwdThreads + threadIdx.x;
   const int f = (int)(gid / G);
   const int sub = (int)(gid % G);
@@ -594,12 +596,12 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
                            int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
   if (F <= 0 || C <= 0) return cudaSuccess;
   dim3 grid((F + kProjThreads - 1) / kProjThreads, C);
-  k_project<<<grid, kProjThreads, 0, s>>>(verts, V, faces, F, rgb, opacity, color_mode, views, tile,
-                                          1.0f / (float)tile, cov_mode, ws.rec_u, ws.rec_q, ws.rec_rect,
-                                          ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
-                                          ws.pair_key[1], ws.pair_face, ws.counters);
+  cudaError_t e = launch_chained(k_project, true, grid, dim3(kProjThreads), 0, s, verts, V, faces, F, rgb, opacity,
+                                 color_mode, views, tile, 1.0f / (float)tile, cov_mode, ws.rec_u, ws.rec_q,
+                                 ws.rec_rect, ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
+                                 ws.pair_key[1], ws.pair_face, ws.counters);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
@@ -615,10 +617,11 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
   const int64_t threads = (int64_t)F * G;
   const unsigned blocks = (unsigned)((threads + kProjBwdThreads - 1) / kProjBwdThreads);
   auto kern = G == 1 ? k_proj_bwd<1> : G == 2 ? k_proj_bwd<2> : G == 4 ? k_proj_bwd<4> : k_proj_bwd<8>;
-  kern<<<blocks, kProjBwdThreads, 0, s>>>(verts, V, faces, F, C, views, cov_mode, color_mode, opacity, ws.rec_grad,
-                                          ws.rec_q, ws.face_grad, dverts, drgb, dop, accumulate);
+  cudaError_t e = launch_chained(kern, true, dim3(blocks), dim3(kProjBwdThreads), 0, s, verts, V, faces, F, C, views,
+                                 cov_mode, color_mode, opacity, (const float4*)ws.rec_grad, (const float4*)ws.rec_q,
+                                 (const float4*)ws.face_grad, dverts, drgb, dop, accumulate);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,

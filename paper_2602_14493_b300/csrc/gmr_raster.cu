@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
     uint32_t* __restrict__ pix_last, float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
     int64_t n_pix_total, FwdLoss fl, const uint4* __restrict__ tile_desc, Counters* __restrict__ counters) {
+  pdl_enter();
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
@@ -409,6 +410,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
 // accumulation in FP32 arithmetic (error ~n 2^-44 relative, no FP64 pipe).
 __global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__ part, int64_t n, double scale,
                                                        double* __restrict__ out) {
+  pdl_enter();
   __shared__ df sw[32];
   // rounds of 16 independent loads per thread, then their (fixed-order) sum
   constexpr int R = 16;
@@ -483,6 +485,7 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
     const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
     float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, const uint4* __restrict__ tile_desc,
     Counters* __restrict__ counters) {
+  pdl_enter();
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
@@ -765,26 +768,31 @@ __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4
 }
 
 template <int TS, int NT, int BATCH>
-void fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
+cudaError_t fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
                 int32_t F, const float* bg, float* images, float* t_out, uint32_t* nc_out, const FwdLoss& fl,
                 cudaStream_t s) {
   auto kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss>
               : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug>
                         : k_raster_fwd<TS, NT, BATCH, kFwdPlain>;
-  kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q,
-                                                                 ws.face_col, views, C, F, bg[0], bg[1], bg[2],
-                                                                 images, ws.pix_T, ws.pix_last, t_out, nc_out,
-                                                                 ws.cap_pixels, fl, ws.tile_desc, ws.counters);
-  if (fl.target) k_sum_partials<<<1, 1024, 0, s>>>(fl.part, n_tiles * (NT / 32), 1.0, fl.loss);
+  cudaError_t e = launch_chained(kern, false, dim3((unsigned)n_tiles), dim3(NT), 0, s, (const uint2*)ws.tile_range,
+                                 pair_face, (const float4*)ws.rec_u, (const float4*)ws.rec_q,
+                                 (const float4*)ws.face_col, views, C, F, bg[0], bg[1], bg[2], images, ws.pix_T,
+                                 ws.pix_last, t_out, nc_out, ws.cap_pixels, fl, (const uint4*)ws.tile_desc,
+                                 ws.counters);
+  if (e == cudaSuccess && fl.target)
+    e = launch_chained(k_sum_partials, true, dim3(1), dim3(1024), 0, s, (const float*)fl.part, n_tiles * (NT / 32), 1.0,
+                       fl.loss);
+  return e;
 }
 
 template <int TS, int NT, int BATCH>
-void bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
+cudaError_t bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
                 int32_t F, const float* bg, const float* dL, const float* dLdT, const BwdLoss& bl, cudaStream_t s) {
   auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
-  kern<<<(unsigned)n_tiles, NT, 0, s>>>(ws.tile_range, pair_face, ws.rec_u, ws.rec_q, ws.face_col, views, C, F,
-                                        bg[0], bg[1], bg[2], dL, dLdT, ws.pix_T, ws.pix_last, ws.rec_grad,
-                                        ws.face_grad, bl, ws.tile_desc, ws.counters);
+  return launch_chained(kern, false, dim3((unsigned)n_tiles), dim3(NT), 0, s, (const uint2*)ws.tile_range, pair_face,
+                        (const float4*)ws.rec_u, (const float4*)ws.rec_q, (const float4*)ws.face_col, views, C, F,
+                        bg[0], bg[1], bg[2], dL, dLdT, (const float*)ws.pix_T, (const uint32_t*)ws.pix_last,
+                        ws.rec_grad, ws.face_grad, bl, (const uint4*)ws.tile_desc, ws.counters);
 }
 
 }  // namespace
@@ -795,9 +803,10 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
                               cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return fl.target ? cudaMemsetAsync(fl.loss, 0, sizeof(double), s) : cudaSuccess;
   if (fl.target) *launches += 1;  // k_sum_partials
+  cudaError_t e = cudaSuccess;
 #define GMR_FWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, ncontrib_out, fl, s)
+  e = fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
   else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
   else GMR_FWD(16, 64, 64); else GMR_FWD(16, 64, 128); else GMR_FWD(16, 64, 256);
@@ -805,7 +814,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
   else return cudaErrorInvalidValue;
 #undef GMR_FWD
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
@@ -813,9 +822,10 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace&
                               const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, cudaStream_t s,
                               int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, s)
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
@@ -823,7 +833,7 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace&
   else return cudaErrorInvalidValue;
 #undef GMR_BWD
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* rects, float* conic, cudaStream_t s,
@@ -836,9 +846,9 @@ cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* re
 
 cudaError_t launch_sum_floats(const float* x, int64_t n, double scale, double* out, cudaStream_t s,
                               int64_t* launches) {
-  k_sum_partials<<<1, 1024, 0, s>>>(x, n, scale, out);
+  cudaError_t e = launch_chained(k_sum_partials, true, dim3(1), dim3(1024), 0, s, x, n, scale, out);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 // Silhouette loss (Sec. 3.1: binary cross-entropy between the rendered mask

@@ -109,6 +109,7 @@ __device__ __forceinline__ void file_tiles(const uint32_t (&v)[NI], int64_t i0, 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ src, int64_t n,
                                                               uint32_t* __restrict__ block_sums,
                                                               uint32_t* __restrict__ block_hist) {
+  pdl_enter();
   __shared__ uint32_t sw[33];
   __shared__ uint32_t s_hist[kTileClasses];
   int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ sums, int64_t nb,
                                                    uint32_t* __restrict__ total, uint32_t* __restrict__ block_hist,
                                                    uint32_t* __restrict__ n_class) {
+  pdl_enter();
   __shared__ uint32_t sw[33];
   if (threadIdx.x < kTileClasses) {
     uint32_t run = 0;
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
                                                             const uint32_t* __restrict__ block_sums,
                                                             uint32_t* __restrict__ out, uint32_t* __restrict__ tile_order,
                                                             const uint32_t* __restrict__ block_hist) {
+  pdl_enter();
   __shared__ uint32_t sw[33];
   __shared__ uint32_t tile[kScanTile];
   __shared__ uint32_t s_hist[kTileClasses], s_base[kTileClasses];
@@ -214,6 +217,7 @@ __global__ void __launch_bounds__(kSingleThreads) k_scan_single(uint32_t* __rest
                                                                 uint32_t* __restrict__ total,
                                                                 uint32_t* __restrict__ tile_order,
                                                                 uint32_t* __restrict__ n_class) {
+  pdl_enter();
   __shared__ uint32_t sw[33];
   __shared__ uint32_t s_hist[kTileClasses], s_base[kTileClasses];
   uint32_t carry = 0;
@@ -275,17 +279,22 @@ cudaError_t scan_exclusive(uint32_t* src, int64_t n, uint32_t* out, uint32_t* to
   // the vector path needs 16-byte aligned arrays (workspace allocations are)
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
   if (n <= kSingleMax && aligned) {
-    k_scan_single<<<1, kSingleThreads, 0, s>>>(src, n, out, total, tile_order, n_class);
+    cudaError_t e = launch_chained(k_scan_single, true, dim3(1), dim3(kSingleThreads), 0, s, src, n, out, total,
+                                   tile_order, n_class);
     *launches += 1;
-    return cudaGetLastError();
+    return e;
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   uint32_t* block_hist = block_sums + nb + 1;
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums, block_hist);
-  k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, total, block_hist, n_class);
-  k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(src, n, block_sums, out, tile_order, block_hist);
+  cudaError_t e = launch_chained(k_scan_reduce, true, dim3((unsigned)nb), dim3(kScanThreads), 0, s, (const uint32_t*)src,
+                                 n, block_sums, block_hist);
+  if (e == cudaSuccess)
+    e = launch_chained(k_scan_top, true, dim3(1), dim3(1024), 0, s, block_sums, nb, total, block_hist, n_class);
+  if (e == cudaSuccess)
+    e = launch_chained(k_scan_down, true, dim3((unsigned)nb), dim3(kScanThreads), 0, s, src, n,
+                       (const uint32_t*)block_sums, out, tile_order, (const uint32_t*)block_hist);
   *launches += 3;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace gmr
