@@ -43,6 +43,13 @@ struct gmr_ctx {
   uint32_t stage_mask = 0;
   // forward state consumed by the backward
   bool fwd_valid = false;
+  // The last forward zeroed the record and face gradient sums and the
+  // backward evaluation counter, and no backward has run since; with the
+  // id of the stream capture that forward was enqueued in (0: none). A
+  // backward enqueued in the same capture (or, uncaptured, after an
+  // uncaptured forward) then needs no memsets of its own.
+  bool grads_zero = false;
+  unsigned long long grads_zero_capture = 0;
   const float* verts = nullptr;
   const int32_t* faces = nullptr;
   const float* rgb = nullptr;
@@ -413,6 +420,7 @@ gmr_status gmr_set_config(gmr_ctx* ctx, const gmr_config* cfg) {
   if (!valid_config(cfg, &why)) return fail(ctx, GMR_ERR_INVALID_ARG, why);
   ctx->cfg = *cfg;
   ctx->fwd_valid = false;
+  ctx->grads_zero = false;
   ctx->cams.clear();  // tile bases depend on the tile size
   return GMR_OK;
 }
@@ -465,6 +473,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
                       gmr::FwdLoss fl, gmr_stream stream) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   ctx->fwd_valid = false;
+  ctx->grads_zero = false;
   if (V < 0 || F < 0) return fail(ctx, GMR_ERR_INVALID_ARG, "negative size");
   if (C < 1 || C > gmr::kMaxViews) return fail(ctx, GMR_ERR_INVALID_ARG, "C must be in [1, 65535]");
   if (!cams || !images) return fail(ctx, GMR_ERR_INVALID_ARG, "null cams or images");
@@ -474,7 +483,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   if (st != GMR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
-  GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cap_status));
+  unsigned long long cap_id = 0;
+  GMR_CUDA(ctx, cudaStreamGetCaptureInfo(s, &cap_status, &cap_id));
   const bool capturing = cap_status != cudaStreamCaptureStatusNone;
   const gmr_config& cfg = ctx->cfg;
   Workspace& w = ctx->ws;
@@ -515,8 +525,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   // SYNC_CHECK, a pair total beyond the pair buffers grows them and runs the
   // two stages again (the first run's pair scratch was incomplete).
   for (int attempt = 0;; ++attempt) {
-    // counters: pair total and slots, forward evaluation counts
-    GMR_CUDA(ctx, cudaMemsetAsync(w.counters, 0, gmr::kFwdCountersBytes, s));
+    // counters: pair total and slots, forward and backward evaluation counts
+    GMR_CUDA(ctx, cudaMemsetAsync(w.counters, 0, gmr::kStepCountersBytes, s));
     {
       StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
       GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, w.views, C, cfg.tile,
@@ -551,6 +561,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   }
 
   ctx->fwd_valid = true;
+  ctx->grads_zero = true;  // by the projection kernel
+  ctx->grads_zero_capture = capturing ? cap_id : 0;
   ctx->verts = verts; ctx->faces = faces; ctx->rgb = rgb; ctx->opacity = opacity;
   ctx->V = V; ctx->F = F; ctx->C = C;
   ctx->n_tiles = n_tiles; ctx->n_pixels = n_pixels;
@@ -626,9 +638,20 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
     bl.part = reinterpret_cast<float*>(w.loss_part + 1);
   }
   const int64_t n_rec = (int64_t)F * C;
-  if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_grad, 0, sizeof(float4) * 2 * (size_t)n_rec, s));
-  if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
-  GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, sizeof(unsigned long long), s));
+  // The record and face gradient sums and the evaluation counter start at
+  // zero: the forward's projection zeroed them if this backward follows it
+  // directly (in stream order, or in the same graph capture); else here.
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  unsigned long long cap_id = 0;
+  GMR_CUDA(ctx, cudaStreamGetCaptureInfo(s, &cap_status, &cap_id));
+  const unsigned long long cap_now = cap_status != cudaStreamCaptureStatusNone ? cap_id : 0;
+  const bool zeroed = ctx->grads_zero && ctx->grads_zero_capture == cap_now;
+  ctx->grads_zero = false;
+  if (!zeroed) {
+    if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_grad, 0, sizeof(float4) * 2 * (size_t)n_rec, s));
+    if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
+    GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, sizeof(unsigned long long), s));
+  }
   if (!accumulate) {
     if (dL_dverts && V > 0) GMR_CUDA(ctx, cudaMemsetAsync(dL_dverts, 0, sizeof(float) * 3 * (size_t)V, s));
     if (dL_drgb && cfg.color_mode == GMR_COLOR_PER_VERTEX && V > 0)

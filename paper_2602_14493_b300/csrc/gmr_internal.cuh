@@ -93,7 +93,8 @@ constexpr uint32_t kDevOverflow = GMR_DEV_PAIR_OVERFLOW;
 
 // Device counters block.
 struct Counters {
-  // cleared together at the start of every forward (kFwdCountersBytes)
+  // cleared together at the start of every forward (kFwdCountersBytes;
+  // evals_bwd too, kStepCountersBytes, when the backward follows in order)
   uint32_t n_pairs;     // total pairs of the current forward (scan total)
   uint32_t pair_alloc;  // pair slots handed out by the projection
   uint32_t n_long;      // tiles whose segment is too long for a warp sort
@@ -108,6 +109,7 @@ struct Counters {
   uint32_t pad1;
 };
 constexpr size_t kFwdCountersBytes = offsetof(Counters, evals_bwd);
+constexpr size_t kStepCountersBytes = offsetof(Counters, status);
 static_assert(offsetof(Counters, n_class) % 16 == 0, "n_class is read with 16-byte loads");
 
 // Compositing order of the tiles, heaviest first (a longest-job-first
@@ -371,6 +373,8 @@ int64_t scan_block_sums_needed(int64_t n);
 // project.cu
 // Conversion + projection of every (view, face) record; also writes the
 // per-face colour/opacity and counts the pairs of every tile.
+// Projection (S1-S2); it also zeroes the record and face gradient sums
+// (ws.rec_grad for all C x F records, ws.face_grad for all F faces).
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int color_mode, const ViewInfo* views, int32_t C, int tile,
                            int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);

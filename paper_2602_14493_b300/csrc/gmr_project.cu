@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
     int64_t cap_pairs, unsigned long long* __restrict__ pair_tr, uint32_t* __restrict__ pair_rec,
-    Counters* __restrict__ counters) {
+    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, Counters* __restrict__ counters) {
   pdl_enter();
   __shared__ ViewInfo sv;
   __shared__ uint32_t s_off[kProjThreads / 32][32];
@@ -221,6 +221,12 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   const uint32_t rid = (uint32_t)c * (uint32_t)F + (uint32_t)f;
   int i0 = 0, i1 = 0, i2 = 0;
   const bool ok = live && load_face(faces, f, V, i0, i1, i2);
+  if (live) {  // the backward's gradient sums of every record and face start at zero
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec_grad[2 * (size_t)rid] = z;
+    rec_grad[2 * (size_t)rid + 1] = z;
+    if (c == 0) face_grad[f] = z;
+  }
   if (live && c == 0) {
     float r = 0.f, g = 0.f, b = 0.f;
     if (color_mode == GMR_COLOR_PER_FACE) {
@@ -599,7 +605,7 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
   cudaError_t e = launch_chained(k_project, true, grid, dim3(kProjThreads), 0, s, verts, V, faces, F, rgb, opacity,
                                  color_mode, views, tile, 1.0f / (float)tile, cov_mode, ws.rec_u, ws.rec_q,
                                  ws.rec_rect, ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
-                                 ws.pair_key[1], ws.pair_face, ws.counters);
+                                 ws.pair_key[1], ws.pair_face, ws.rec_grad, ws.face_grad, ws.counters);
   *launches += 1;
   return e;
 }

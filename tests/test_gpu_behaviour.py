@@ -205,6 +205,45 @@ def test_cuda_graph_capture_replays_fwd_loss_bwd():
     r.close()
 
 
+def test_repeated_and_separately_captured_backwards_start_from_zero():
+    """The forward zeroes the backward's gradient sums; a second backward
+    after one forward, and a backward captured alone and replayed, must
+    clear them themselves (same gradients every time)."""
+    s = gi.scene_ring(level=4, n_views=4, res=256)
+    r = _renderer()
+    v, f, c, o = to_dev(s)
+    g = torch.rand((s.n_pixels, 3), device=DEV) - 0.5
+    img, _ = r.forward(v, f, c, o, s.cams)
+    outs = []
+    for _ in range(3):  # three backwards after one forward
+        dv, dc, do = torch.empty_like(v), torch.empty_like(c), torch.empty_like(o)
+        r.backward(g, dv, dc, do)
+        outs.append((dv.cpu().numpy(), dc.cpu().numpy(), do.cpu().numpy()))
+    for k in range(1, 3):
+        for a, b in zip(outs[0], outs[k]):
+            np.testing.assert_array_equal(a, b)
+    # forward eager, backward alone in a graph, replayed several times
+    P = r.stats()["n_pairs"]
+    r.reserve(len(s.faces), len(s.cams), s.n_pixels, int(P * 1.5) + 1024)
+    cams = __import__("paper_2602_14493_b300").camera_array(s.cams)
+    stream = torch.cuda.Stream()
+    img2 = torch.empty_like(img)
+    dv, dc, do = torch.empty_like(v), torch.empty_like(c), torch.empty_like(o)
+    with torch.cuda.stream(stream):
+        r.forward(v, f, c, o, cams, images=img2, want_t=False, stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        r.backward(g, dv, dc, do, stream=stream)
+    for _ in range(3):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert rel_l2(dv.cpu().numpy(), outs[0][0]) < 1e-5
+        assert rel_l2(dc.cpu().numpy(), outs[0][1]) < 1e-5
+    assert r.device_status() == 0
+    r.close()
+
+
 def test_empty_mesh_and_offscreen_views_render_background():
     r = _renderer(bg=(0.25, 0.5, 0.75))
     s = gi.scene_single_view(level=1, width=40, height=24)
