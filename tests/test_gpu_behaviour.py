@@ -219,9 +219,11 @@ def test_repeated_and_separately_captured_backwards_start_from_zero():
         dv, dc, do = torch.empty_like(v), torch.empty_like(c), torch.empty_like(o)
         r.backward(g, dv, dc, do)
         outs.append((dv.cpu().numpy(), dc.cpu().numpy(), do.cpu().numpy()))
+    # equal up to the order of the float atomics (a sum left over from the
+    # previous backward would double them: relative L2 distance ~1)
     for k in range(1, 3):
         for a, b in zip(outs[0], outs[k]):
-            np.testing.assert_array_equal(a, b)
+            assert rel_l2(a, b) < 1e-5
     # forward eager, backward alone in a graph, replayed several times
     P = r.stats()["n_pairs"]
     r.reserve(len(s.faces), len(s.cams), s.n_pixels, int(P * 1.5) + 1024)
