@@ -652,16 +652,23 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
     if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
     GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, sizeof(unsigned long long), s));
   }
+  // outputs the projection backward accumulates into: zeroed by the
+  // compositing backward's CTAs (or here, when it has no tiles)
+  gmr::BwdZero bz;
   if (!accumulate) {
-    if (dL_dverts && V > 0) GMR_CUDA(ctx, cudaMemsetAsync(dL_dverts, 0, sizeof(float) * 3 * (size_t)V, s));
-    if (dL_drgb && cfg.color_mode == GMR_COLOR_PER_VERTEX && V > 0)
-      GMR_CUDA(ctx, cudaMemsetAsync(dL_drgb, 0, sizeof(float) * 3 * (size_t)V, s));
+    int k = 0;
+    if (dL_dverts && V > 0) { bz.p[k] = dL_dverts; bz.n[k++] = 3 * (int64_t)V; }
+    if (dL_drgb && cfg.color_mode == GMR_COLOR_PER_VERTEX && V > 0) { bz.p[k] = dL_drgb; bz.n[k++] = 3 * (int64_t)V; }
+    if (ctx->n_tiles <= 0) {
+      for (int z = 0; z < k; ++z) GMR_CUDA(ctx, cudaMemsetAsync(bz.p[z], 0, sizeof(float) * (size_t)bz.n[z], s));
+      bz = gmr::BwdZero{};
+    }
   }
   // S8: compositing backward
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, w, w.pair_face, w.views, C, F,
-                                         ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal, bl, s, &ctx->launches));
+                                         ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal, bl, bz, s, &ctx->launches));
   }
   if (images) {  // the loss: sum of the warps' partial sums
     StageTimer t(ctx, GMR_STAGE_LOSS, s, cfg);

@@ -421,10 +421,18 @@ struct BwdLoss {
   const float* target = nullptr;
   float* part = nullptr;
 };
+// Up to two caller buffers (n floats each) that the projection backward
+// accumulates into: the compositing backward's CTAs zero them (it runs
+// before that kernel), which saves their memsets between the two
+// compositing kernels.
+struct BwdZero {
+  float* p[2] = {nullptr, nullptr};
+  int64_t n[2] = {0, 0};
+};
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, cudaStream_t s,
-                              int64_t* launches);
+                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, const BwdZero& bz,
+                              cudaStream_t s, int64_t* launches);
 // partials: l2_loss_partials_needed(n) doubles; partials[0] holds a ticket
 // counter that must be zero before the first call (every call leaves it zero)
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,

@@ -483,8 +483,8 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
     const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
     int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
     const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
-    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, const uint4* __restrict__ tile_desc,
-    Counters* __restrict__ counters) {
+    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz,
+    const uint4* __restrict__ tile_desc, Counters* __restrict__ counters) {
   pdl_enter();
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
@@ -665,6 +665,10 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(kFull, evals, o);
   if (lane == 0 && evals) atomicAdd(&counters->evals_bwd, evals);
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < bz.n[z]; i += (int64_t)gridDim.x * NT)
+      bz.p[z][i] = 0.0f;
 }
 
 // ---------------------------------------------------------------- loss
@@ -787,12 +791,13 @@ cudaError_t fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pai
 
 template <int TS, int NT, int BATCH>
 cudaError_t bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, const float* dL, const float* dLdT, const BwdLoss& bl, cudaStream_t s) {
+                int32_t F, const float* bg, const float* dL, const float* dLdT, const BwdLoss& bl, const BwdZero& bz,
+                cudaStream_t s) {
   auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
   return launch_chained(kern, false, dim3((unsigned)n_tiles), dim3(NT), 0, s, (const uint2*)ws.tile_range, pair_face,
                         (const float4*)ws.rec_u, (const float4*)ws.rec_q, (const float4*)ws.face_col, views, C, F,
                         bg[0], bg[1], bg[2], dL, dLdT, (const float*)ws.pix_T, (const uint32_t*)ws.pix_last,
-                        ws.rec_grad, ws.face_grad, bl, (const uint4*)ws.tile_desc, ws.counters);
+                        ws.rec_grad, ws.face_grad, bl, bz, (const uint4*)ws.tile_desc, ws.counters);
 }
 
 }  // namespace
@@ -819,13 +824,13 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
 
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
                               const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, cudaStream_t s,
-                              int64_t* launches) {
+                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, const BwdZero& bz,
+                              cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                               \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, s)
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
