@@ -176,7 +176,9 @@ GMR_API gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t*
 /* Pre-sizes the workspace for up to max_faces faces, max_views views,
  * max_pixels total pixels and max_pairs (tile, Gaussian) pairs, so that
  * later calls within these limits allocate nothing (needed before stream
- * capture). */
+ * capture). If it has to grow the workspace, the last forward's state is
+ * dropped: gmr_render_bwd then returns GMR_ERR_STATE until the next
+ * forward. */
 GMR_API gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels,
                        int64_t max_pairs);
 

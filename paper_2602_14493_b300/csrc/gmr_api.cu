@@ -441,6 +441,17 @@ gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t* offsets
 gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels, int64_t max_pairs) {
   if (!ctx || max_faces < 0 || max_views < 0 || max_pixels < 0 || max_pairs < 0)
     return fail(ctx, GMR_ERR_INVALID_ARG, "bad reserve sizes");
+  // growing the buffers that hold the last forward's state drops that state
+  struct Invalidate {
+    gmr_ctx* c;
+    int64_t before;
+    ~Invalidate() {
+      if (c->dev_bytes != before) {
+        c->fwd_valid = false;
+        c->grads_zero = false;
+      }
+    }
+  } inval{ctx, ctx->dev_bytes};
   gmr_status s;
   if ((s = ensure_records(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK) return s;
   if ((s = ensure_faces(ctx, max_faces, false)) != GMR_OK) return s;
