@@ -638,7 +638,9 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
     # memory-type stages: algorithmic bytes per record, pair, tile and face
     R = stats["n_records"]
     P = stats["n_pairs"]
-    byts = {"project": R * 64 + len(scene.faces) * 28 + P * 4, "scan": stats["n_tiles"] * 8,
+    # (the projection also writes the zeros of the backward's gradient sums:
+    # 32 B per record, 16 B per face)
+    byts = {"project": R * 96 + len(scene.faces) * 44 + P * 4, "scan": stats["n_tiles"] * 8,
             "bin": R * 16 + P * 8 * 3 + P * 4, "project_bwd": R * 48 + len(scene.faces) * 116}.get(stage, 0)
     ach = byts / (ms / 1e3) / 1e9
     pk = peaks["hbm_gbs"]
