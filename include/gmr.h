@@ -23,6 +23,12 @@
  *  - Images are packed view after view; view c occupies pixels
  *    [off[c], off[c+1]) of the packed buffer (see gmr_image_offsets), rows
  *    top to bottom, 3 floats (RGB) per pixel.
+ *  - The kernels of one forward and one backward may be launched with
+ *    programmatic dependent launch (each may start while the one before it
+ *    on the stream finishes, and waits for it on the device before touching
+ *    memory); the ordering the caller sees is plain stream order. Setting
+ *    GMR_PDL=0 in the environment (read once per process) launches them
+ *    without it.
  */
 #ifndef GMR_H_
 #define GMR_H_
