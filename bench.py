@@ -35,7 +35,7 @@ import gmr_inputs as gi  # noqa: E402
 
 METRIC = "fwd+bwd Mpixel-views/s and ms/iter, batched vs per-view, at ≤1e-5 img err"
 UNIT = "Mpixel-views/s"
-DEFAULT_WORKLOAD = "icosphere5_sin_8x512"
+DEFAULT_WORKLOAD = "icosphere6_noise_64xuneven"
 WORKLOADS = {
     "icosphere5_sin_8x512": gi.scene_ring,
     "icosphere3_1x128": gi.scene_single_view,
@@ -55,10 +55,9 @@ FLOPS_EVAL = 13
 FLOPS_FWD_CONTRIB = 10
 FLOPS_BWD_CONTRIB = 59
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that
-# ncu measured for the dominant kernel on the default workload
-# (profiles/raster_bwd_traffic_icosphere5_sin_8x512.md); to be removed when
-# the kernel changes after the capture.
-NCU_TRAFFIC = {("raster_bwd", "icosphere5_sin_8x512"): 81300992}
+# one ncu capture measured for the dominant kernel, per workload; an entry is
+# removed when the kernel changes after its capture.
+NCU_TRAFFIC = {}
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -193,19 +192,31 @@ def oracle_sample_time(scene, n_pix, seed=0, keep=False):
 
 
 def cpu_baseline(scene, target_seconds, gpu_check=None):
-    """The oracle timed on a bounded sample of the workload's pixels. With
-    gpu_check, the GPU's image at the sampled pixels and its gradients for
-    the same upstream gradient are compared with the oracle's."""
-    oracle_sample_time(scene, 4)  # build + warm
-    t_a, n_a = oracle_sample_time(scene, 32)
-    t_b, n_b = oracle_sample_time(scene, 288)
+    """The oracle timed on bounded samples of the workload's pixels, on every
+    host core (OpenMP over pixels, records and faces; the headline value) and
+    on one thread. With gpu_check, the GPU's image at the all-cores sample's
+    pixels and its gradients for the same upstream gradient are compared with
+    the oracle's."""
+    import oracle
+
+    cores = oracle.set_threads(0)
+    # calibration on all cores: one pixel (the per-call conversion,
+    # projection and depth sort of every record dominate) and 16 per core
+    t_a, n_a = oracle_sample_time(scene, 1)
+    t_b, n_b = oracle_sample_time(scene, 16 * cores)
     per_px = max((t_b - t_a) / max(n_b - n_a, 1), 1e-7)
     fixed = max(t_a - n_a * per_px, 0.0)
     n = int(max(64, min(400000, (target_seconds - fixed) / per_px)))
     t, n, kept = oracle_sample_time(scene, n, seed=1, keep=True)
-    out = {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+    # one thread, on 1/cores of that many pixels
+    oracle.set_threads(1)
+    n1_req = max(8, n // cores)
+    t1, n1 = oracle_sample_time(scene, n1_req, seed=2)
+    out = {"value": n / t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
-                     f"(single thread), {t:.1f} s"}
+                     f"on {cores} host threads (os.cpu_count() = {os.cpu_count()}), {t:.1f} s",
+           "single_thread": {"value": n1 / t1 / 1e6, "unit": UNIT, "cores": 1,
+                             "sample": f"{n1} random pixels, one thread, {t1:.1f} s"}}
     if gpu_check is not None:
         out["parity"] = gpu_check(*kept)
     return out
@@ -241,8 +252,13 @@ def parity_with_oracle(r, v, f, c, o, cams, scene, pix, ref, g, bref):
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle (the paper publishes no code), fwd +
+    bwd of a bounded random pixel sample per step, on every host core."""
     if rank != 0:
         return
+    import oracle
+
+    cores = oracle.set_threads(0)
     scene = WORKLOADS[args.workload]()
     n_pix = args.ref_pixels
     for _ in range(args.warmup):
@@ -255,8 +271,8 @@ def run_reference(args, ws, rank):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "step": f"oracle fwd+bwd on {n_pix} random pixels"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{n_pix} random pixels per step, FP64 brute force, single thread"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n_pix} random pixels per step, FP64 brute force, {cores} host threads"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -661,7 +677,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-pixels", type=int, default=256)
+    ap.add_argument("--ref-pixels", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -50,8 +50,16 @@ def lib():
                                           P, P, P, P, P, P]
         L.gmr_oracle_jvp.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P, P,
                                      P, P, P, P, P]
+        L.gmr_oracle_set_threads.argtypes = [i32]
+        L.gmr_oracle_set_threads.restype = i32
         _LIB = L
     return _LIB
+
+
+def set_threads(n):
+    """Host threads of the oracle's parallel loops (n < 1: every core).
+    Returns the count in use. Results are bit-identical for every count."""
+    return int(lib().gmr_oracle_set_threads(int(n)))
 
 
 def _p(a):

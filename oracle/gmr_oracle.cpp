@@ -33,6 +33,8 @@
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (no -ffast-math).
 
+#include <omp.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -40,6 +42,11 @@
 #include <vector>
 
 namespace {
+
+// Host threads the oracle's loops use (OpenMP). Every parallel loop writes
+// disjoint outputs, and every sum over pixels, views or faces is formed in the
+// same fixed order as with one thread, so results do not depend on it.
+int g_threads = 1;
 
 // ---------------------------------------------------------------- constants
 // 3DGS compositing constants (Sec. 2.1 follows the standard 3DGS rasterizer,
@@ -430,12 +437,13 @@ bool check_scene(const Scene& s) {
 
 std::vector<Bin> all_bins(const Scene& s) {
   std::vector<Bin> bins((size_t)s.C * s.F);
-  for (int c = 0; c < s.C; ++c)
-    for (int f = 0; f < s.F; ++f) {
-      const int* fi = s.faces + 3 * f;
-      bins[(size_t)c * s.F + f] =
-          bin_spec(s.verts + 3 * fi[0], s.verts + 3 * fi[1], s.verts + 3 * fi[2], s.cams[c], s.tile);
-    }
+  const long long n = (long long)s.C * s.F;
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+  for (long long r = 0; r < n; ++r) {
+    const int c = (int)(r / s.F), f = (int)(r % s.F);
+    const int* fi = s.faces + 3 * f;
+    bins[(size_t)r] = bin_spec(s.verts + 3 * fi[0], s.verts + 3 * fi[1], s.verts + 3 * fi[2], s.cams[c], s.tile);
+  }
   return bins;
 }
 
@@ -531,6 +539,7 @@ Prepared<T> prepare(const Scene& s, const Direction* dir) {
   P.g.resize(s.F);
   P.col.resize((size_t)s.F * 3);
   P.op.resize(s.F);
+#pragma omp parallel for schedule(static) num_threads(g_threads)
   for (int f = 0; f < s.F; ++f) {
     const int* fi = s.faces + 3 * f;
     V3<T> v[3];
@@ -543,11 +552,14 @@ Prepared<T> prepare(const Scene& s, const Direction* dir) {
   P.bins = all_bins(s);
   P.p.resize((size_t)s.C * s.F);
   P.order.resize(s.C);
-  for (int c = 0; c < s.C; ++c) {
-    for (int f = 0; f < s.F; ++f)
-      if (P.bins[(size_t)c * s.F + f].visible) P.p[(size_t)c * s.F + f] = project<T>(P.g[f], s.cams[c]);
-    P.order[c] = sorted_visible(P.bins, s.F, c);
+  const long long n = (long long)s.C * s.F;
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+  for (long long r = 0; r < n; ++r) {
+    const int c = (int)(r / s.F), f = (int)(r % s.F);
+    if (P.bins[(size_t)r].visible) P.p[(size_t)r] = project<T>(P.g[f], s.cams[c]);
   }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+  for (int c = 0; c < s.C; ++c) P.order[c] = sorted_visible(P.bins, s.F, c);
   return P;
 }
 
@@ -774,6 +786,14 @@ void convert_backward(const FaceGauss<double>& g, V3<double> vi, V3<double> vj, 
 // ============================================================== C interface
 extern "C" {
 
+// Host threads of the oracle's parallel loops (1 by default; n < 1 means all
+// cores OpenMP reports). Results are identical for every thread count.
+// Returns the count now in use.
+int gmr_oracle_set_threads(int n) {
+  g_threads = n >= 1 ? n : omp_get_num_procs();
+  return g_threads;
+}
+
 // Conversion of every facet (Sec. 2.2). means F x 3, cov F x 9 (row-major),
 // aux F x 8 = (sxx, sxy, syy, lam1, lam2, kappa, area, degenerate),
 // frame F x 9 = (xa, ya, n). Any output may be null. Returns 0, or -1 on a
@@ -927,9 +947,11 @@ int gmr_oracle_render(int V, const float* verts, int F, const int* faces, const 
   Prepared<double> P = prepare<double>(s, nullptr);
   Bands b;
   if (bands) { b.alpha_rel = bands[0]; b.t_rel = bands[1]; }
+  for (long long i = 0; i < npix; ++i)
+    if (pix[3 * i] < 0 || pix[3 * i] >= C) return -3;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
   for (long long i = 0; i < npix; ++i) {
     int view = pix[3 * i], x = pix[3 * i + 1], y = pix[3 * i + 2];
-    if (view < 0 || view >= C) return -3;
     double o[3], Tf;
     int lf, nc, fl;
     composite_pixel<double>(s, P, view, x, y, o, &Tf, &lf, &nc, &fl, bands ? &b : nullptr, nullptr);
@@ -959,44 +981,82 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
   std::vector<FaceGrad> fg((size_t)C * F);
   for (auto& x : fg) { x.du[0] = x.du[1] = 0.0; x.dQ[0] = x.dQ[1] = x.dQ[2] = 0.0; }
   std::vector<double> dcol((size_t)F * 3, 0.0), dop(F, 0.0);
-  std::vector<Contrib> rec;
-  for (long long i = 0; i < npix; ++i) {
-    int view = pix[3 * i], x = pix[3 * i + 1], y = pix[3 * i + 2];
-    if (view < 0 || view >= C) return -3;
-    const double* g = dLdI + 3 * i;
-    const double gT = dLdT ? dLdT[i] : 0.0;
-    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 && gT == 0.0) continue;
-    rec.clear();
-    double o[3], Tf;
-    composite_pixel<double>(s, P, view, x, y, o, &Tf, nullptr, nullptr, nullptr, nullptr, &rec);
-    // I = sum_i c_i alpha_i T_i + T_N bg. Walking back, S is the part of I
-    // contributed after Gaussian i: dI/dalpha_i = c_i T_i - S / (1 - alpha_i).
-    double S[3] = {Tf * s.bg[0], Tf * s.bg[1], Tf * s.bg[2]};
-    for (int k = (int)rec.size() - 1; k >= 0; --k) {
-      const Contrib& cb = rec[k];
-      int f = cb.face;
-      const double* col = &P.col[3 * (size_t)f];
-      double dalpha = 0.0;
-      for (int ch = 0; ch < 3; ++ch) {
-        dcol[3 * (size_t)f + ch] += cb.alpha * cb.Tb * g[ch];
-        dalpha += g[ch] * (col[ch] * cb.Tb - S[ch] / (1.0 - cb.alpha));
+  for (long long i = 0; i < npix; ++i)
+    if (pix[3 * i] < 0 || pix[3 * i] >= C) return -3;
+  // One pixel's terms, in the order they are added: the pixels are walked in
+  // parallel over fixed chunks (each chunk lists its terms), and the terms
+  // are then added in pixel order, so every sum has the same order as with
+  // one thread.
+  struct Term {
+    int f, view;
+    bool clamped;
+    double dcol[3], dop, dQ[3], du[2];
+  };
+  const long long kChunk = 32;
+  const long long nchunks = (npix + kChunk - 1) / kChunk;
+  const long long wave = (long long)std::max(g_threads, 1) * 16;
+  std::vector<std::vector<Term>> terms;
+  for (long long w0 = 0; w0 < nchunks; w0 += wave) {
+    const long long w1 = std::min(nchunks, w0 + wave);
+    terms.assign((size_t)(w1 - w0), std::vector<Term>());
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+    for (long long chk = w0; chk < w1; ++chk) {
+      std::vector<Contrib> rec;
+      std::vector<Term>& out = terms[(size_t)(chk - w0)];
+      for (long long i = chk * kChunk; i < std::min(npix, (chk + 1) * kChunk); ++i) {
+        int view = pix[3 * i], x = pix[3 * i + 1], y = pix[3 * i + 2];
+        const double* g = dLdI + 3 * i;
+        const double gT = dLdT ? dLdT[i] : 0.0;
+        if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 && gT == 0.0) continue;
+        rec.clear();
+        double o[3], Tf;
+        composite_pixel<double>(s, P, view, x, y, o, &Tf, nullptr, nullptr, nullptr, nullptr, &rec);
+        // I = sum_i c_i alpha_i T_i + T_N bg. Walking back, S is the part of I
+        // contributed after Gaussian i: dI/dalpha_i = c_i T_i - S / (1 - alpha_i).
+        double S[3] = {Tf * s.bg[0], Tf * s.bg[1], Tf * s.bg[2]};
+        for (int k = (int)rec.size() - 1; k >= 0; --k) {
+          const Contrib& cb = rec[k];
+          int f = cb.face;
+          const double* col = &P.col[3 * (size_t)f];
+          Term t;
+          t.f = f;
+          t.view = view;
+          double dalpha = 0.0;
+          for (int ch = 0; ch < 3; ++ch) {
+            t.dcol[ch] = cb.alpha * cb.Tb * g[ch];
+            dalpha += g[ch] * (col[ch] * cb.Tb - S[ch] / (1.0 - cb.alpha));
+          }
+          // final transmittance T_N = prod_j (1 - alpha_j): dT_N/dalpha_i = -T_N / (1 - alpha_i)
+          dalpha += gT * (-Tf / (1.0 - cb.alpha));
+          for (int ch = 0; ch < 3; ++ch) S[ch] += col[ch] * cb.alpha * cb.Tb;
+          // alpha = 0.99 does not depend on o or the geometry
+          t.clamped = cb.clamped;
+          if (!cb.clamped) {
+            // alpha = o exp(power)
+            t.dop = dalpha * cb.G;
+            double dpower = dalpha * cb.alpha;
+            const Proj<double>& pr = P.p[(size_t)view * F + f];
+            // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - pixel centre
+            t.dQ[0] = dpower * (-0.5 * cb.dx * cb.dx);
+            t.dQ[1] = dpower * (-cb.dx * cb.dy);
+            t.dQ[2] = dpower * (-0.5 * cb.dy * cb.dy);
+            t.du[0] = dpower * (-(pr.Q[0] * cb.dx + pr.Q[1] * cb.dy));
+            t.du[1] = dpower * (-(pr.Q[1] * cb.dx + pr.Q[2] * cb.dy));
+          }
+          out.push_back(t);
+        }
       }
-      // final transmittance T_N = prod_j (1 - alpha_j): dT_N/dalpha_i = -T_N / (1 - alpha_i)
-      dalpha += gT * (-Tf / (1.0 - cb.alpha));
-      for (int ch = 0; ch < 3; ++ch) S[ch] += col[ch] * cb.alpha * cb.Tb;
-      if (cb.clamped) continue;  // alpha = 0.99 does not depend on o or the geometry
-      // alpha = o exp(power)
-      dop[f] += dalpha * cb.G;
-      double dpower = dalpha * cb.alpha;
-      const Proj<double>& pr = P.p[(size_t)view * F + f];
-      FaceGrad& G = fg[(size_t)view * F + f];
-      // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - pixel centre
-      G.dQ[0] += dpower * (-0.5 * cb.dx * cb.dx);
-      G.dQ[1] += dpower * (-cb.dx * cb.dy);
-      G.dQ[2] += dpower * (-0.5 * cb.dy * cb.dy);
-      G.du[0] += dpower * (-(pr.Q[0] * cb.dx + pr.Q[1] * cb.dy));
-      G.du[1] += dpower * (-(pr.Q[1] * cb.dx + pr.Q[2] * cb.dy));
     }
+    for (const std::vector<Term>& tv : terms)
+      for (const Term& t : tv) {
+        for (int ch = 0; ch < 3; ++ch) dcol[3 * (size_t)t.f + ch] += t.dcol[ch];
+        if (t.clamped) continue;
+        dop[t.f] += t.dop;
+        FaceGrad& G = fg[(size_t)t.view * F + t.f];
+        for (int q = 0; q < 3; ++q) G.dQ[q] += t.dQ[q];
+        G.du[0] += t.du[0];
+        G.du[1] += t.du[1];
+      }
   }
   if (rec_grads) {
     for (int c = 0; c < C; ++c)
@@ -1009,9 +1069,11 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
       }
   }
   // Chain through projection (per view) and conversion (per face).
+  // (per face, the views are added in ascending order whatever the threads)
   std::vector<double> dmean((size_t)F * 3, 0.0), dcov((size_t)F * 9, 0.0);
-  for (int c = 0; c < C; ++c)
-    for (int f = 0; f < F; ++f) {
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+  for (int f = 0; f < F; ++f)
+    for (int c = 0; c < C; ++c) {
       size_t r = (size_t)c * F + f;
       const FaceGrad& G = fg[r];
       if (G.du[0] == 0.0 && G.du[1] == 0.0 && G.dQ[0] == 0.0 && G.dQ[1] == 0.0 && G.dQ[2] == 0.0) continue;
@@ -1019,6 +1081,8 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
     }
   if (dverts)
     for (long long k = 0; k < 3LL * V; ++k) dverts[k] = 0.0;
+  std::vector<double> dvf((size_t)F * 9);
+#pragma omp parallel for schedule(static) num_threads(g_threads)
   for (int f = 0; f < F; ++f) {
     const int* fi = faces + 3 * f;
     V3<double> v[3];
@@ -1026,10 +1090,15 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
       v[k] = mk((double)verts[3 * fi[k]], (double)verts[3 * fi[k] + 1], (double)verts[3 * fi[k] + 2]);
     double dv[3][3];
     convert_backward(P.g[f], v[0], v[1], v[2], cov_mode, &dmean[3 * (size_t)f], &dcov[9 * (size_t)f], dv);
-    if (dverts)
-      for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) dverts[3 * (size_t)fi[a] + k] += dv[a][k];
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) dvf[9 * (size_t)f + 3 * a + k] = dv[a][k];
   }
+  if (dverts)  // the vertex sums in face order
+    for (int f = 0; f < F; ++f) {
+      const int* fi = faces + 3 * f;
+      for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) dverts[3 * (size_t)fi[a] + k] += dvf[9 * (size_t)f + 3 * a + k];
+    }
   if (drgb) {
     if (color_mode == 0) {
       for (long long k = 0; k < 3LL * F; ++k) drgb[k] = dcol[k];

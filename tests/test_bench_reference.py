@@ -21,6 +21,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference"
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "icosphere5_sin_8x512"
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert d["config"]["workload"] == bench.DEFAULT_WORKLOAD == "icosphere6_noise_64xuneven"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert 1 <= d["cpu_baseline"]["cores"] <= (os.cpu_count() or 1)
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
