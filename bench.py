@@ -391,12 +391,18 @@ def run_gmr(args, ws, rank, local):
     if args.tile == "auto":
         from paper_2602_14493_b300.autotune import shape_name, tune
 
-        (tile, threads, threads_bwd, batch), tuned = tune(r, v, f, c, o, cams, target, use_cache=False)
+        (tile, threads, threads_bwd, batch, persistent), tuned = tune(r, v, f, c, o, cams, target, use_cache=False)
         log("autotune:", {shape_name(k): round(t, 4) for k, t in sorted(tuned.items(), key=lambda kv: kv[1])[:8]})
+        # the best shape with one CTA per tile and as a persistent grid
+        scheduler = {"per_tile_grid_ms": tuned.get((tile, threads, threads_bwd, batch, 0)),
+                     "persistent_ms": tuned.get((tile, threads, threads_bwd, batch, 1)),
+                     "source": "autotuner, eager fwd + loss + bwd step, median of 15"}
     else:
         tile, threads, batch = int(args.tile), args.threads, args.batch
         threads_bwd = args.threads_bwd or threads
-        r.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch)
+        persistent = int(args.persistent)
+        scheduler = None
+        r.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent))
     img, _ = r.forward(v, f, c, o, cams, want_t=False)
     torch.cuda.synchronize()
     P = r.stats()["n_pairs"]
@@ -611,11 +617,13 @@ def run_gmr(args, ws, rank, local):
         "dtype": "fp32", "data": "synthetic",
         "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
                    "form": "batched, one call for all views, CUDA graph", "tile": tile, "threads": threads, "threads_bwd": threads_bwd,
-                   "batch": batch, "shape_choice": "autotuned" if args.tile == "auto" else "fixed",
+                   "batch": batch, "persistent": bool(persistent),
+                   "shape_choice": "autotuned" if args.tile == "auto" else "fixed",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "per_view": {"value": n_pix / (pv_ms / 1e3) / 1e6, "ms_per_step": pv_ms, "form": "one call per view, eager"},
         "batched_eager": {"value": n_pix / (be_ms / 1e3) / 1e6, "ms_per_step": be_ms},
+        "scheduler": scheduler,
         "stages_ms": {k: round(vv, 5) for k, vv in stage_ms.items()},
         "stages_source": "separate replays of the step captured with events around every stage "
                          f"({statistics.mean(prof_ms):.4f} ms per profiled step)",
@@ -675,6 +683,7 @@ def main():
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--threads-bwd", type=int, default=0, help="backward threads per tile (0: as --threads)")
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--persistent", type=int, default=0, help="with a fixed shape: 1 = persistent compositing grids")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-pixels", type=int, default=128)

@@ -124,6 +124,12 @@ typedef struct {
  * perturbation changed any discrete decision or the compositing order. */
 #define GMR_FLAG_DEBUG_COUNTS 4
 
+/* With this flag the two compositing kernels run as persistent grids: as
+ * many CTAs as fit on the device at once, each taking the next tile (in the
+ * heaviest-first compositing order) from a device counter until none is
+ * left, instead of one CTA per tile. Results are identical either way. */
+#define GMR_FLAG_PERSISTENT 8
+
 /* Stages timed under GMR_FLAG_PROFILE. */
 typedef enum {
   GMR_STAGE_PROJECT = 0,      /* conversion fused with EWA projection, tile counts (Sec. 2.2, 2.1) */
@@ -187,6 +193,13 @@ GMR_API gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t*
  * forward. */
 GMR_API gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels,
                        int64_t max_pairs);
+
+/* Caps the device memory the context's workspace may hold at max_bytes (0:
+ * no cap, the default). A call that would grow the workspace beyond the cap
+ * returns GMR_ERR_OOM, as when cudaMalloc fails, with nothing enqueued and
+ * the context still usable (a larger cap, or smaller inputs, let the next
+ * call proceed). Memory already held is not released by a lower cap. */
+GMR_API gmr_status gmr_set_workspace_limit(gmr_ctx* ctx, int64_t max_bytes);
 
 /* Mesh-to-Gaussian conversion alone (Sec. 2.2, Eq. 3-16).
  *  verts   V x 3, faces F x 3 (int32 vertex indices in [0, V)),
@@ -296,11 +309,16 @@ GMR_API gmr_status gmr_l2_loss(gmr_ctx* ctx, const float* img, const float* targ
  * allocation may synchronise the device; processes whose device memory is
  * owned by their own pool or by a framework's caching allocator). The
  * paper has no counterpart; this is an interface convenience. The reduction's
- * partial sums live in a fixed 128 KB array inside the library on each GPU,
- * which limits n to GMR_L2_NOALLOC_MAX_ELEMS (larger n returns
- * GMR_ERR_CAPACITY before anything is enqueued). The array's address is
- * looked up on the first call on each device: make that call before any
- * stream capture. Calls on one GPU share the array, so calls that can run
+ * partial sums live in a fixed array inside the library on each GPU (593
+ * doubles, 4,744 bytes: one per block of the loss kernel's grid, which has
+ * at most 592 blocks whatever n). n is bounded by GMR_L2_NOALLOC_MAX_ELEMS
+ * (2^26 floats per operand, so one call moves at most ~0.8 GB), a bound of
+ * this entry point rather than of the array: larger n returns
+ * GMR_ERR_CAPACITY before anything is enqueued. The array's address is
+ * looked up on the first call on each device and kept for the life of the
+ * process: make that call before any stream capture, and do not call this
+ * entry point on a device after cudaDeviceReset() of it (the address is then
+ * stale). Calls on one GPU share the array, so calls that can run
  * concurrently on the same GPU race; order them. Bad pointers or n < 0 return
  * GMR_ERR_INVALID_ARG; a failing CUDA call returns GMR_ERR_CUDA. */
 #define GMR_L2_NOALLOC_MAX_ELEMS 67108864

@@ -13,6 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "gmr_oracle.cpp")
 LIB = os.path.join(HERE, "libgmr_oracle.so")
+FLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
 
 
 def build(force: bool = False) -> str:
@@ -21,8 +22,7 @@ def build(force: bool = False) -> str:
         return override
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-fopenmp", "-Wall", "-o", LIB + ".tmp", SRC]
+    cmd = ["g++", *FLAGS, "-Wall", "-o", LIB + ".tmp", SRC]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

@@ -1089,7 +1089,18 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
     for (int k = 0; k < 3; ++k)
       v[k] = mk((double)verts[3 * fi[k]], (double)verts[3 * fi[k] + 1], (double)verts[3 * fi[k] + 2]);
     double dv[3][3];
-    convert_backward(P.g[f], v[0], v[1], v[2], cov_mode, &dmean[3 * (size_t)f], &dcov[9 * (size_t)f], dv);
+    // A face that reached no pixel (culled in every view, e.g. with a
+    // non-finite vertex) has exactly zero gradient; the chain is skipped so
+    // that 0 times its non-finite geometry does not give NaN.
+    bool reached = false;
+    for (int k = 0; k < 3; ++k) reached |= dmean[3 * (size_t)f + k] != 0.0;
+    for (int k = 0; k < 9; ++k) reached |= dcov[9 * (size_t)f + k] != 0.0;
+    if (reached) {
+      convert_backward(P.g[f], v[0], v[1], v[2], cov_mode, &dmean[3 * (size_t)f], &dcov[9 * (size_t)f], dv);
+    } else {
+      for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) dv[a][k] = 0.0;
+    }
     for (int a = 0; a < 3; ++a)
       for (int k = 0; k < 3; ++k) dvf[9 * (size_t)f + 3 * a + k] = dv[a][k];
   }

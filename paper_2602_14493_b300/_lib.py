@@ -23,6 +23,7 @@ GMR_COLOR_PER_FACE, GMR_COLOR_PER_VERTEX = 0, 1
 GMR_FLAG_SYNC_CHECK = 1
 GMR_FLAG_PROFILE = 2
 GMR_FLAG_DEBUG_COUNTS = 4
+GMR_FLAG_PERSISTENT = 8
 GMR_L2_NOALLOC_MAX_ELEMS = 67108864
 STAGES = ["project", "scan", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
 
@@ -33,7 +34,7 @@ EXPORTS = [
     "gmr_l2_loss",
     "gmr_get_device_status", "gmr_get_stats", "gmr_get_stage_times", "gmr_debug_forward_state",
     "gmr_l2_loss_noalloc", "gmr_adam_step", "gmr_chamfer", "gmr_render_bwd_ex", "gmr_silhouette_bce",
-    "gmr_mesh_regularizers", "gmr_render_bwd_l2", "gmr_copy_h2d",
+    "gmr_mesh_regularizers", "gmr_render_bwd_l2", "gmr_copy_h2d", "gmr_set_workspace_limit",
 ]
 
 
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
         "gmr_status_string": (ctypes.c_char_p, [st]),
         "gmr_image_offsets": (st, [P, i32, P]),
         "gmr_reserve": (st, [P, i64, i32, i64, i64]),
+        "gmr_set_workspace_limit": (st, [P, i64]),
         "gmr_convert": (st, [P, P, i32, P, i32, P, P, P, P, P, P, P]),
         "gmr_render_fwd": (st, [P, P, i32, P, i32, P, P, P, i32, P, P, P]),
         "gmr_render_fwd_l2": (st, [P, P, i32, P, i32, P, P, P, i32, P, P, P, P, P, P]),

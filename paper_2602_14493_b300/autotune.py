@@ -1,5 +1,6 @@
 """Autotuner for the rasterizer's launch shape: tile size, threads per tile
-(forward and backward separately) and Gaussians per shared-memory batch.
+(forward and backward separately), Gaussians per shared-memory batch, and
+whether the compositing kernels run as persistent grids.
 
 Every candidate renders the same forward + L2 loss + backward step; the
 fastest (median of CUDA-event timings after warm-up) wins. Images do not
@@ -24,8 +25,9 @@ CANDIDATES = [(16, tf, tb, b) for tf in (256, 128, 64) for tb in (256, 128, 64) 
 
 
 def _apply(renderer, shape):
-    tile, threads, threads_bwd, batch = shape
-    renderer.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch)
+    tile, threads, threads_bwd, batch = shape[:4]
+    persistent = bool(shape[4]) if len(shape) > 4 else False
+    renderer.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=persistent)
 
 
 def shape_name(shape) -> str:
@@ -65,12 +67,13 @@ def _store(d):
 
 
 def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates=CANDIDATES, use_cache=True):
-    """Times each candidate shape on this workload and configures
-    ``renderer`` with the fastest. Returns (best (tile, threads,
-    threads_bwd, batch), {shape: median ms})."""
+    """Times each candidate shape on this workload with one CTA per tile,
+    then the fastest also as a persistent grid, and configures ``renderer``
+    with the fastest of all. Returns (best (tile, threads, threads_bwd,
+    batch, persistent), {shape: median ms})."""
     sig = signature(faces.shape[0], cams)
     cache = _load() if use_cache else {}
-    if use_cache and sig in cache and len(cache[sig]["best"]) == 4:
+    if use_cache and sig in cache and len(cache[sig]["best"]) == 5:
         best = tuple(cache[sig]["best"])
         _apply(renderer, best)
         return best, {}
@@ -80,7 +83,8 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
     dv, dc = torch.empty_like(verts), torch.empty_like(rgb)
     do = torch.empty_like(opacity) if opacity is not None else None
     results = {}
-    for shape in candidates:
+
+    def time_shape(shape):
         _apply(renderer, shape)
         ts = []
         for rep in range(reps + 2):
@@ -93,6 +97,11 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
             if rep >= 2:
                 ts.append(a.elapsed_time(b))
         results[shape] = statistics.median(ts)
+
+    for shape in candidates:
+        time_shape(tuple(shape[:4]) + (0,))
+    best = min(results, key=results.get)
+    time_shape(best[:4] + (1,))
     best = min(results, key=results.get)
     _apply(renderer, best)
     if use_cache:

@@ -57,9 +57,11 @@ struct gmr_ctx {
   int32_t V = 0, F = 0, C = 0;
   int64_t n_tiles = 0, n_pixels = 0;
   gmr_config fwd_cfg;
-  // device bytes held by the workspace (per allocation, and the total)
+  // device bytes held by the workspace (per allocation, and the total), and
+  // the most it may hold (0: no limit; gmr_set_workspace_limit)
   std::unordered_map<void*, size_t> dev_sizes;
   int64_t dev_bytes = 0;
+  int64_t dev_limit = 0;
 };
 
 namespace {
@@ -74,6 +76,16 @@ void track_free(gmr_ctx* ctx, void* p) {
   if (it == ctx->dev_sizes.end()) return;
   ctx->dev_bytes -= (int64_t)it->second;
   ctx->dev_sizes.erase(it);
+}
+
+// Whether replacing the allocation `old` (may be null) by one of `bytes`
+// bytes keeps the workspace within its limit.
+bool within_limit(const gmr_ctx* ctx, const void* old, size_t bytes) {
+  if (ctx->dev_limit <= 0) return true;
+  int64_t held = ctx->dev_bytes;
+  auto it = old ? ctx->dev_sizes.find(const_cast<void*>(old)) : ctx->dev_sizes.end();
+  if (it != ctx->dev_sizes.end()) held -= (int64_t)it->second;
+  return held + (int64_t)bytes <= ctx->dev_limit;
 }
 
 gmr_status fail(gmr_ctx* ctx, gmr_status s, const std::string& msg) {
@@ -123,6 +135,8 @@ gmr_status grow(gmr_ctx* ctx, T** ptr, int64_t* cap, int64_t need, bool capturin
     return fail(ctx, GMR_ERR_STATE,
                 std::string("workspace '") + what + "' must grow during stream capture; call gmr_reserve first");
   int64_t ncap = need + need / 4 + 1024;
+  if (!within_limit(ctx, *ptr, (size_t)ncap * sizeof(T)))
+    return fail(ctx, GMR_ERR_OOM, std::string("workspace '") + what + "' would exceed the workspace limit");
   T* p = nullptr;
   cudaError_t e = cudaMalloc((void**)&p, (size_t)ncap * sizeof(T));
   if (e != cudaSuccess) {
@@ -144,6 +158,8 @@ template <class T>
 gmr_status realloc_exact(gmr_ctx* ctx, T** ptr, int64_t count, const char* what) {
   T* p = nullptr;
   const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+  if (!within_limit(ctx, *ptr, bytes))
+    return fail(ctx, GMR_ERR_OOM, std::string("workspace '") + what + "' would exceed the workspace limit");
   cudaError_t e = cudaMalloc((void**)&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -438,6 +454,12 @@ gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t* offsets
   return GMR_OK;
 }
 
+gmr_status gmr_set_workspace_limit(gmr_ctx* ctx, int64_t max_bytes) {
+  if (!ctx || max_bytes < 0) return fail(ctx, GMR_ERR_INVALID_ARG, "bad workspace limit");
+  ctx->dev_limit = max_bytes;
+  return GMR_OK;
+}
+
 gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels, int64_t max_pairs) {
   if (!ctx || max_faces < 0 || max_views < 0 || max_pixels < 0 || max_pairs < 0)
     return fail(ctx, GMR_ERR_INVALID_ARG, "bad reserve sizes");
@@ -567,8 +589,9 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
     uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
-    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, w, w.pair_face, w.views, C, F, n_tiles,
-                                         cfg.bg, images, t_final, nc, fl, s, &ctx->launches));
+    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0, w,
+                                         w.pair_face, w.views, C, F, n_tiles, cfg.bg, images, t_final, nc, fl, s,
+                                         &ctx->launches));
   }
 
   ctx->fwd_valid = true;
@@ -649,7 +672,8 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
     bl.part = reinterpret_cast<float*>(w.loss_part + 1);
   }
   const int64_t n_rec = (int64_t)F * C;
-  // The record and face gradient sums and the evaluation counter start at
+  // The record and face gradient sums, the evaluation counter and the
+  // persistent grid's cursor start at
   // zero: the forward's projection zeroed them if this backward follows it
   // directly (in stream order, or in the same graph capture); else here.
   cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
@@ -661,7 +685,7 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   if (!zeroed) {
     if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_grad, 0, sizeof(float4) * 2 * (size_t)n_rec, s));
     if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
-    GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, sizeof(unsigned long long), s));
+    GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, gmr::kBwdCountersBytes, s));
   }
   // outputs the projection backward accumulates into: zeroed by the
   // compositing backward's CTAs (or here, when it has no tiles)
@@ -678,8 +702,9 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   // S8: compositing backward
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, w, w.pair_face, w.views, C, F,
-                                         ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal, bl, bz, s, &ctx->launches));
+    GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
+                                         w, w.pair_face, w.views, C, F, ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal,
+                                         bl, bz, s, &ctx->launches));
   }
   if (images) {  // the loss: sum of the warps' partial sums
     StageTimer t(ctx, GMR_STAGE_LOSS, s, cfg);

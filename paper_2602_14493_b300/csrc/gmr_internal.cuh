@@ -102,14 +102,19 @@ struct Counters {
   unsigned long long evals_fwd;
   unsigned long long contribs;
   uint32_t n_class[16];  // tiles per work class (see tile_of_block); 16-byte aligned
-  // cleared at the start of every backward
+  uint32_t raster_next_fwd;  // next compositing position of the persistent forward grid
+  uint32_t pad0;
+  // cleared at the start of every backward (kBwdCountersBytes from here)
   unsigned long long evals_bwd;
+  uint32_t raster_next_bwd;  // next compositing position of the persistent backward grid
+  uint32_t pad2;
   // GMR_DEV_* bits, sticky until gmr_get_device_status reads them
   uint32_t status;
   uint32_t pad1;
 };
 constexpr size_t kFwdCountersBytes = offsetof(Counters, evals_bwd);
 constexpr size_t kStepCountersBytes = offsetof(Counters, status);
+constexpr size_t kBwdCountersBytes = offsetof(Counters, status) - offsetof(Counters, evals_bwd);
 static_assert(offsetof(Counters, n_class) % 16 == 0, "n_class is read with 16-byte loads");
 
 // Compositing order of the tiles, heaviest first (a longest-job-first
@@ -341,12 +346,20 @@ struct Workspace {
   // pairs
   int64_t cap_pairs = 0;
   // pair_key[0]: (depth bits << 32 | face) per pair in tile segments;
-  // pair_key[1]: scratch of the long-segment sort, and before that, per pair
-  // slot of the projection, (tile << 32 | rank of the pair in its tile)
+  // pair_key[1]: per pair slot of the projection, (tile << 32 | rank of the
+  // pair in its tile); then scratch of the long-segment sort; then, from the
+  // forward compositing to the next forward, the contribution masks
+  // (pair_cmask)
   unsigned long long* pair_key[2] = {nullptr, nullptr};
   // face ids in (tile, depth, face) order; before the sort, per pair slot of
   // the projection, the pair's record id
   uint32_t* pair_face = nullptr;
+  // Per sorted pair, the 8x4-pixel blocks of its tile in which at least one
+  // pixel composited the pair's Gaussian (bit b = block b, row-major), written
+  // by the forward compositing and read by the backward: 32 bits per pair in
+  // the memory of pair_key[1], which holds nothing else between the binning
+  // and the next forward.
+  uint32_t* pair_cmask() const { return reinterpret_cast<uint32_t*>(pair_key[1]); }
   // scratch for scans
   int64_t cap_scan = 0;
   uint32_t* scan_tmp = nullptr;     // block sums
@@ -407,10 +420,13 @@ struct FwdLoss {
   float* part = nullptr;
   double* loss = nullptr;
 };
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
-                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              float* images, float* t_final_out, uint32_t* ncontrib_out, const FwdLoss& fl,
-                              cudaStream_t s, int64_t* launches);
+// persistent: a grid of resident CTAs taking compositing positions from a
+// cursor (Counters::raster_next_fwd / _bwd, zero at launch) instead of one
+// CTA per tile.
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+                              const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
+                              int64_t n_tiles, const float* bg, float* images, float* t_final_out,
+                              uint32_t* ncontrib_out, const FwdLoss& fl, cudaStream_t s, int64_t* launches);
 // Optional squared-error loss fused into the backward's prologue (img ==
 // nullptr: none): dL/dimg = 2 (img - target) is formed per pixel instead of
 // being read, and the loss sum goes to one FP32 partial per CTA (part,
@@ -429,15 +445,25 @@ struct BwdZero {
   float* p[2] = {nullptr, nullptr};
   int64_t n[2] = {0, 0};
 };
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
-                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, const BwdZero& bz,
-                              cudaStream_t s, int64_t* launches);
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+                              const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
+                              int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
+                              const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches);
+// The L2 loss kernel: a one-wave grid of at most kL2LossMaxBlocks blocks
+// striding over chunks of kL2LossBlockElems floats.
+constexpr int kL2LossBlockElems = 256 * 16;
+constexpr int kL2LossMaxBlocks = 148 * 4;
+// Doubles of partial-sum scratch launch_l2_loss needs for n floats: the
+// ticket counter plus one per block; never more than 1 + kL2LossMaxBlocks.
+constexpr int64_t l2_loss_partials_needed(int64_t n) {
+  return 1 + ((n + kL2LossBlockElems - 1) / kL2LossBlockElems < kL2LossMaxBlocks
+                  ? (n + kL2LossBlockElems - 1) / kL2LossBlockElems
+                  : kL2LossMaxBlocks);
+}
 // partials: l2_loss_partials_needed(n) doubles; partials[0] holds a ticket
 // counter that must be zero before the first call (every call leaves it zero)
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,
                            double* partials, int64_t n_partials, cudaStream_t s, int64_t* launches);
-int64_t l2_loss_partials_needed(int64_t n);
 // weight x the silhouette binary cross-entropy of the mask 1 - T_final
 // against a target mask (mean over n pixels), with dL/dT_final; partials as
 // for the L2 loss

@@ -13,10 +13,14 @@
 // this library.
 //
 // The scratch array lives in device memory of every GPU that loads the
-// library, from load until process exit (128 KB per GPU). Its device address
-// is looked up once per device with cudaGetSymbolAddress, during the first
-// call made with that device current; make that first call before any stream
-// capture that includes this entry point. Each GPU has its own copy, and all
+// library, from load until process exit (593 doubles, 4,744 bytes per GPU:
+// the loss kernel's grid never has more than 592 blocks, whatever n). Its
+// device address is looked up once per device with cudaGetSymbolAddress,
+// during the first call made with that device current; make that first call
+// before any stream capture that includes this entry point. The address is
+// kept for the life of the process: after cudaDeviceReset() of a device the
+// library's device code is loaded again elsewhere, so this entry point must
+// not be called on that device afterwards. Each GPU has its own copy, and all
 // calls on one GPU share it: two calls whose work can overlap on the same GPU
 // (for example on two streams without an ordering between them) race on it,
 // so the caller must order them. The array's first slot is the loss
@@ -31,8 +35,10 @@
 namespace {
 
 // Completion counter + partial sums of one call (one double per block of
-// the loss kernel's grid, at most a few hundred).
-constexpr int64_t kNoAllocPartials = 16384 + 1;
+// the loss kernel's grid), sized for the largest grid it launches.
+constexpr int64_t kNoAllocPartials = 1 + gmr::kL2LossMaxBlocks;
+static_assert(gmr::l2_loss_partials_needed(INT64_MAX / 2) == kNoAllocPartials,
+              "the scratch array holds the partials of every n");
 static __device__ __align__(256) double g_l2_partials[kNoAllocPartials];
 
 constexpr int kMaxDevices = 64;
@@ -61,7 +67,9 @@ cudaError_t partials_address(double** out) {
 extern "C" gmr_status gmr_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* dL_dimg,
                                           double* loss, gmr_stream stream) {
   if (n < 0 || !loss || (n > 0 && (!img || !target || !dL_dimg))) return GMR_ERR_INVALID_ARG;
-  if (n > GMR_L2_NOALLOC_MAX_ELEMS || gmr::l2_loss_partials_needed(n) > kNoAllocPartials) return GMR_ERR_CAPACITY;
+  // a bound of this entry point (one call's work stays below ~1 GB of
+  // traffic), not of the scratch array, which fits every n
+  if (n > GMR_L2_NOALLOC_MAX_ELEMS) return GMR_ERR_CAPACITY;
   double* partials = nullptr;
   if (partials_address(&partials) != cudaSuccess) {
     cudaGetLastError();

@@ -335,7 +335,10 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   df ux, uy;
   image_mean(a, b, cc, sv, ux, uy);
   rec_u[rid] = make_float4(ux.hi, uy.hi, ux.lo, uy.lo);
-  rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, 0.0f);
+  // w: the compositing's skip threshold t2 = -log2(255 o) (o G < 1/255 iff
+  // log2 G < t2; +inf for o = 0)
+  const float o = fminf(fmaxf(opacity ? __ldg(opacity + f) : 1.0f, 0.0f), 1.0f);
+  rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, -(kLog2_255 + log2f(o)));
 }
 
 // Backward of conversion + projection. A face's gradient sums over its

@@ -37,6 +37,8 @@
 // relative to the pixel block's 32-aligned anchor in float-pair arithmetic.
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "gmr_internal.cuh"
 
@@ -65,6 +67,9 @@ struct PixMap {
     return (ry * RH + k / RW) * NC + rx * RW + k % RW;
   }
   __device__ __forceinline__ static int block(int k) { return block_of(threadIdx.x >> 5, k); }
+  // block(k) - block(0), a compile-time constant: bit block(k) of a block
+  // mask is bit block(0) shifted left by this
+  static constexpr int boff(int k) { return (k / RW) * NC + k % RW; }
   __device__ __forceinline__ static uint32_t warp_bits() {
     uint32_t b = 0;
 #pragma unroll
@@ -141,6 +146,8 @@ __device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, flo
   return m;
 }
 
+// Forward staging: the block mask is the conservative bounding-box test
+// above. The record's w holds the skip threshold t2 = -log2(255 o).
 template <int TS, int NT, int BATCH>
 __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
                                             int count, uint32_t rec_base, const float4* __restrict__ rec_u,
@@ -154,16 +161,41 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uin
     float4 col = __ldg(face_col + f);
     float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
-    const float k2 = kLog2_255 + log2f(col.w);  // -inf for o = 0
-    const uint32_t m = block_mask<TS>(ux, uy, q.x, q.y, q.z, k2, tox, toy);
+    const uint32_t m = block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy);
     st.g[i] = make_float4(ux, uy, q.x, q.y);
-    st.h[i] = make_float4(q.z, -k2, col.w, 0.0f);
+    st.h[i] = make_float4(q.z, q.w, col.w, 0.0f);
     st.mask[i] = m;
     st.col[i] = make_float4(col.x, col.y, col.z, 0.0f);
     if (want_ids) {
       st.rid[i] = rid;
       st.face[i] = f;
     }
+  }
+}
+
+// Backward staging: the block mask is the forward's contribution mask (the
+// blocks in which some pixel composited the Gaussian), so entries that
+// contributed nowhere are neither loaded nor listed.
+template <int NT, int BATCH>
+__device__ __forceinline__ void stage_batch_bwd(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face,
+                                                const uint32_t* __restrict__ cmask, uint32_t lo, int count,
+                                                uint32_t rec_base, const float4* __restrict__ rec_u,
+                                                const float4* __restrict__ rec_q,
+                                                const float4* __restrict__ face_col, float ax, float ay) {
+  for (int i = threadIdx.x; i < count; i += NT) {
+    const uint32_t m = __ldg(cmask + lo + i);
+    st.mask[i] = m;
+    if (m == 0u) continue;
+    const uint32_t f = __ldg(pair_face + lo + i);
+    const uint32_t rid = rec_base + f;
+    const float4 u = __ldg(rec_u + rid);
+    const float4 q = __ldg(rec_q + rid);
+    const float4 col = __ldg(face_col + f);
+    st.g[i] = make_float4(__fadd_rn(__fsub_rn(u.x, ax), u.z), __fadd_rn(__fsub_rn(u.y, ay), u.w), q.x, q.y);
+    st.h[i] = make_float4(q.z, q.w, col.w, 0.0f);
+    st.col[i] = make_float4(col.x, col.y, col.z, 0.0f);
+    st.rid[i] = rid;
+    st.face[i] = f;
   }
 }
 
@@ -245,28 +277,68 @@ __device__ __forceinline__ void loss_partial_and_finish(float v, double* __restr
 // against fl.target in the epilogue.
 constexpr int kFwdPlain = 0, kFwdDebug = 1, kFwdLoss = 2;
 
+// Per-tile arguments of the compositing kernels.
+struct RasterArgs {
+  const uint32_t* pair_face;
+  uint32_t* cmask;  // per sorted pair: contribution mask (forward writes, backward reads)
+  const float4* rec_u;
+  const float4* rec_q;
+  const float4* face_col;
+  const ViewInfo* views;
+  int32_t F;
+  float bg0, bg1, bg2;
+  const uint4* tile_desc;
+  Counters* counters;
+  uint32_t n_pos;   // compositing positions (tiles)
+  int persistent;   // 1: resident CTAs take positions from a cursor
+};
+
+// The compositing position of each pass of a CTA: its block index, or, in a
+// persistent grid, the next position of the cursor (one atomic per tile;
+// the barrier keeps a CTA's threads on one tile). Returns false when no
+// position is left.
+__device__ __forceinline__ bool next_position(bool persistent, uint32_t* cursor, uint32_t n_pos, int pass,
+                                              uint32_t& pos) {
+  if (!persistent) {
+    pos = blockIdx.x;
+    return pass == 0;
+  }
+  __shared__ uint32_t s_pos;
+  __syncthreads();  // every thread is done with the last tile (and with s_pos)
+  if (threadIdx.x == 0) s_pos = atomicAdd(cursor, 1u);
+  __syncthreads();
+  pos = s_pos;
+  return pos < n_pos;
+}
+
+// One tile of the forward at compositing position pos. Besides the image,
+// final T and last contributor of every pixel, it writes the contribution
+// mask of every list entry it reached: bit b set when some pixel of 8x4
+// block b composited the entry (a warp ORs its lanes' blocks with one
+// reduction and adds them to a shared word; the words of a batch are written
+// out once every warp is past that batch). Entries past the tile's stop are
+// never read by the backward, which ends at the last contributor.
 template <int TS, int NT, int BATCH, int MODE>
-__global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
-    const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
-    int32_t C, int32_t F, float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ pix_T,
-    uint32_t* __restrict__ pix_last, float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
-    int64_t n_pix_total, FwdLoss fl, const uint4* __restrict__ tile_desc, Counters* __restrict__ counters) {
-  pdl_enter();
+__device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, float* __restrict__ images,
+                                         float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
+                                         float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
+                                         int64_t n_pix_total, const FwdLoss& fl) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
+  __shared__ uint32_t s_cm[BATCH];
   // the tile at this compositing position, its view and its pair range
-  const uint4 desc = __ldg(tile_desc + blockIdx.x);
+  const uint4 desc = __ldg(a.tile_desc + pos);
   const int g = (int)desc.x;
   const int c = (int)desc.y;
-  const ViewInfo& v = views[c];
+  const ViewInfo& v = a.views[c];
   const int lt = g - v.tile_base;
   const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
   const int ox = txi * TS, oy = tyi * TS;
   const int axi = ox & ~31, ayi = oy & ~31;
   const float ax = (float)axi, ay = (float)ayi;
   const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
+  const int lane = threadIdx.x & 31;
 
   float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
   // fused loss: each thread's target pixels, copied to shared memory
@@ -275,6 +347,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
   bool done[PPT], inside[PPT];
   int px[PPT], py[PPT];
+  const uint32_t bb0 = 1u << PixMap<TS, NT>::block(0);  // block bit of pixel k: bb0 << boff(k)
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     int lx, ly;
@@ -302,16 +375,25 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
   if (MODE == kFwdLoss) asm volatile("cp.async.commit_group;" ::: "memory");
   const uint2 range = make_uint2(desc.z, desc.w);
   const int n = (int)(range.y - range.x);
-  const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
+  for (int i = threadIdx.x; i < BATCH; i += NT) s_cm[i] = 0u;
+  int prev_base = 0, prev_cnt = 0;
 
   for (int base = 0; base < n; base += BATCH) {
     bool tdone = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) tdone &= done[k];
     if (__syncthreads_and(tdone)) break;
+    // every warp is past the last batch: its masks go out, the words are reset
+    for (int i = threadIdx.x; i < prev_cnt; i += NT) {
+      a.cmask[range.x + prev_base + i] = s_cm[i];
+      s_cm[i] = 0u;
+    }
     int cnt = min(BATCH, n - base);
-    stage_batch<TS, NT, BATCH>(st, pair_face, range.x + base, cnt, rec_base, rec_u, rec_q, face_col, ax, ay, tox, toy,
-                           MODE == kFwdDebug);
+    prev_base = base;
+    prev_cnt = cnt;
+    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.face_col, ax, ay,
+                               tox, toy, MODE == kFwdDebug);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, cnt, 0, cnt, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
@@ -337,30 +419,37 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
         con[k] = !done[k] && !(p2[k] < hh.y);
         anyc |= con[k];
       }
-      if (!anyc) continue;
-      const float4 col = st.col[j];
+      uint32_t lb = 0u;  // blocks of this lane's pixels that composite the entry
+      if (anyc) {
+        const float4 col = st.col[j];
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (!con[k]) continue;
-        float graw;
-        float alpha = gauss_alpha(p2[k], hh.z, graw);
-        float test = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
-        if (test < kTMin) {
-          done[k] = true;
-          term[k] = (uint32_t)(base + j + 1);
-          continue;
+        for (int k = 0; k < PPT; ++k) {
+          if (!con[k]) continue;
+          float graw;
+          float alpha = gauss_alpha(p2[k], hh.z, graw);
+          float test = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+          if (test < kTMin) {
+            done[k] = true;
+            term[k] = (uint32_t)(base + j + 1);
+            continue;
+          }
+          float w = __fmul_rn(alpha, T[k]);
+          Cr[k] = __fmaf_rn(col.x, w, Cr[k]);
+          Cg[k] = __fmaf_rn(col.y, w, Cg[k]);
+          Cb[k] = __fmaf_rn(col.z, w, Cb[k]);
+          T[k] = test;
+          last[k] = (uint32_t)(base + j + 1);
+          lb |= bb0 << PixMap<TS, NT>::boff(k);
+          ++ncontrib[k];
+          if (MODE == kFwdDebug) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
         }
-        float w = __fmul_rn(alpha, T[k]);
-        Cr[k] = __fmaf_rn(col.x, w, Cr[k]);
-        Cg[k] = __fmaf_rn(col.y, w, Cg[k]);
-        Cb[k] = __fmaf_rn(col.z, w, Cb[k]);
-        T[k] = test;
-        last[k] = (uint32_t)(base + j + 1);
-        ++ncontrib[k];
-        if (MODE == kFwdDebug) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
       }
+      const uint32_t wb = __reduce_or_sync(kFull, lb);
+      if (wb != 0u && lane == 0) atomicOr(&s_cm[j], wb);
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < prev_cnt; i += NT) a.cmask[range.x + prev_base + i] = s_cm[i];
   unsigned long long evals = 0, ncon = 0;
   float lsum = 0.0f;  // fused loss: FP32 over this thread's pixels
 #pragma unroll
@@ -368,7 +457,7 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     if (!inside[k]) continue;
     ncon += ncontrib[k];
     int64_t pid = v.pix_base + (int64_t)py[k] * v.W + px[k];
-    const float i0 = Cr[k] + T[k] * bg0, i1 = Cg[k] + T[k] * bg1, i2 = Cb[k] + T[k] * bg2;
+    const float i0 = Cr[k] + T[k] * a.bg0, i1 = Cg[k] + T[k] * a.bg1, i2 = Cb[k] + T[k] * a.bg2;
     images[3 * pid] = i0;
     images[3 * pid + 1] = i1;
     images[3 * pid + 2] = i2;
@@ -392,18 +481,29 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value) k_raster_fwd(
     }
     evals += term[k] ? term[k] : (uint32_t)n;
   }
+  if (MODE == kFwdLoss) asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     evals += __shfl_xor_sync(kFull, evals, o);
     ncon += __shfl_xor_sync(kFull, ncon, o);
   }
-  if ((threadIdx.x & 31) == 0 && evals) atomicAdd(&counters->evals_fwd, evals);
-  if ((threadIdx.x & 31) == 0 && ncon) atomicAdd(&counters->contribs, ncon);
+  if (lane == 0 && evals) atomicAdd(&a.counters->evals_fwd, evals);
+  if (lane == 0 && ncon) atomicAdd(&a.counters->contribs, ncon);
   if (MODE == kFwdLoss) {  // one FP32 partial per warp, no block barrier
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
-    if ((threadIdx.x & 31) == 0) fl.part[(int64_t)g * NW + (threadIdx.x >> 5)] = lsum;
+    if (lane == 0) fl.part[(int64_t)g * NW + (threadIdx.x >> 5)] = lsum;
   }
+}
+
+template <int TS, int NT, int BATCH, int MODE>
+__global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value)
+    k_raster_fwd(RasterArgs a, float* __restrict__ images, float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
+                 float* __restrict__ t_out, uint32_t* __restrict__ nc_out, int64_t n_pix_total, FwdLoss fl) {
+  pdl_enter();
+  uint32_t pos;
+  for (int pass = 0; next_position(a.persistent, &a.counters->raster_next_fwd, a.n_pos, pass, pos); ++pass)
+    fwd_tile<TS, NT, BATCH, MODE>(a, pos, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
 }
 
 // Sum of n floats into *out, one block, in a fixed order, with double-float
@@ -478,37 +578,33 @@ struct BwdMinBlocks {
 };
 
 template <int TS, int NT, int BATCH, bool LOSS>
-__global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ pair_face, const float4* __restrict__ rec_u,
-    const float4* __restrict__ rec_q, const float4* __restrict__ face_col, const ViewInfo* __restrict__ views,
-    int32_t C, int32_t F, float bg0, float bg1, float bg2, const float* __restrict__ dL_dimg,
-    const float* __restrict__ dL_dT, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
-    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz,
-    const uint4* __restrict__ tile_desc, Counters* __restrict__ counters) {
-  pdl_enter();
+__device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, const float* __restrict__ dL_dimg,
+                                         const float* __restrict__ dL_dT, const float* __restrict__ pix_T,
+                                         const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
+                                         float4* __restrict__ face_grad, const BwdLoss& bl) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
   __shared__ uint32_t s_maxlast;
   // the tile at this compositing position, its view and its pair range
-  const uint4 desc = __ldg(tile_desc + blockIdx.x);
+  const uint4 desc = __ldg(a.tile_desc + pos);
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
-  const ViewInfo& v = views[c];
+  const ViewInfo& v = a.views[c];
   const int lt = g - v.tile_base;
   const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
   const int ox = txi * TS, oy = tyi * TS;
   const int axi = ox & ~31, ayi = oy & ~31;
   const float ax = (float)axi, ay = (float)ayi;
-  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
   const int lane = threadIdx.x & 31;
 
   // SG = (colour composited behind the current Gaussian, plus T_final bg) . g
   float pcx[PPT], pcy[PPT], T[PPT], SG[PPT], G0[PPT], G1[PPT], G2[PPT];
   uint32_t last[PPT];
   uint32_t tmax = 0;
+  const uint32_t bb0 = 1u << PixMap<TS, NT>::block(0);  // block bit of pixel k: bb0 << boff(k)
   float lsum = 0.0f;  // LOSS: FP32 sum of this thread's squared errors
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
@@ -550,7 +646,7 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
     // the background term T_final bg and the final transmittance itself
     // (dL/dT_final, a silhouette loss) both enter as "colour behind every
     // Gaussian": a fourth channel with Gaussian colour 0 and background 1
-    SG[k] = T[k] * (bg0 * G0[k] + bg1 * G1[k] + bg2 * G2[k] + gT);
+    SG[k] = T[k] * (a.bg0 * G0[k] + a.bg1 * G1[k] + a.bg2 * G2[k] + gT);
     tmax = max(tmax, last[k]);
   }
   uint32_t wmax = tmax;
@@ -576,7 +672,7 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
   }
   const int end_all = (int)s_maxlast;
   const uint2 range = make_uint2(desc.z, desc.w);
-  const uint32_t rec_base = (uint32_t)c * (uint32_t)F;
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
   unsigned long long evals = 0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) evals += last[k];
@@ -584,14 +680,15 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
   for (int end = end_all; end > 0; end -= BATCH) {
     const int start = max(0, end - BATCH);
     __syncthreads();
-    stage_batch<TS, NT, BATCH>(st, pair_face, range.x + start, end - start, rec_base, rec_u, rec_q, face_col, ax, ay,
-                           tox, toy, true);
+    stage_batch_bwd<NT, BATCH>(st, a.pair_face, a.cmask, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
+                               a.face_col, ax, ay);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, end - start, start, (int)wmax, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
     for (int jj = nl - 1; jj >= 0; --jj) {
       const int j = st.list[warp][jj];
-      const int pos = start + j;
+      const int pos_j = start + j;
+      const uint32_t mj = st.mask[j];
       const float4 hh = st.h[j];
       const float4 gg = st.g[j];
       float p2[PPT], dxs[PPT], dys[PPT];
@@ -599,8 +696,14 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
-        con[k] = ((uint32_t)pos < last[k]) && !(p2[k] < hh.y);
+        // a block in which no pixel composited the entry is skipped whole
+        // (the test is uniform over the warp)
+        con[k] = false;
+        p2[k] = dxs[k] = dys[k] = 0.0f;
+        if ((mj >> PixMap<TS, NT>::boff(k)) & bb0) {
+          p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
+          con[k] = ((uint32_t)pos_j < last[k]) && !(p2[k] < hh.y);
+        }
         any |= con[k];
       }
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -664,7 +767,18 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(kFull, evals, o);
-  if (lane == 0 && evals) atomicAdd(&counters->evals_bwd, evals);
+  if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
+}
+
+template <int TS, int NT, int BATCH, bool LOSS>
+__global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
+    k_raster_bwd(RasterArgs a, const float* __restrict__ dL_dimg, const float* __restrict__ dL_dT,
+                 const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
+                 float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz) {
+  pdl_enter();
+  uint32_t pos;
+  for (int pass = 0; next_position(a.persistent, &a.counters->raster_next_bwd, a.n_pos, pass, pos); ++pass)
+    bwd_tile<TS, NT, BATCH, LOSS>(a, pos, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
 #pragma unroll
   for (int z = 0; z < 2; ++z)
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < bz.n[z]; i += (int64_t)gridDim.x * NT)
@@ -673,7 +787,7 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
 
 // ---------------------------------------------------------------- loss
 // L = sum (img - target)^2 and dL/dimg = 2 (img - target) in one launch: a
-// persistent grid of at most kLossMaxBlocks blocks (one wave on 148 SMs)
+// persistent grid of at most kL2LossMaxBlocks blocks (one wave on 148 SMs)
 // walks the 4096-element chunks (block b takes chunks b, b + grid, ...);
 // each block writes the FP64 sum of its chunks to partials[1 + block], and
 // the block that finishes last (a ticket counter in partials[0]) adds the
@@ -683,7 +797,7 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value) k_raster_bwd(
 constexpr int kLossThreads = 256;
 constexpr int kLossItems = 16;  // floats per thread and chunk: 4 float4 of each operand
 constexpr int kLossBlockElems = kLossThreads * kLossItems;
-constexpr int kLossMaxBlocks = 148 * 4;
+static_assert(kLossBlockElems == kL2LossBlockElems, "chunk size of l2_loss_partials_needed");
 
 // Block sum of one double-float per thread (warp tree in double-float,
 // FP64 across the warps); valid in thread 0.
@@ -771,18 +885,64 @@ __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4
   }
 }
 
+// Resident CTAs of a compositing kernel on the current device (a persistent
+// grid's size), looked up once per kernel and device.
+template <typename K>
+int resident_grid(K kern, int threads) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 148;
+  }
+  const int n = std::max(1, per_sm) * std::max(1, sms);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = n;
+  return n;
+}
+
+RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t F,
+                       const float* bg, int64_t n_tiles, bool persistent) {
+  RasterArgs a;
+  a.pair_face = pair_face;
+  a.cmask = ws.pair_cmask();
+  a.rec_u = ws.rec_u;
+  a.rec_q = ws.rec_q;
+  a.face_col = ws.face_col;
+  a.views = views;
+  a.F = F;
+  a.bg0 = bg[0];
+  a.bg1 = bg[1];
+  a.bg2 = bg[2];
+  a.tile_desc = ws.tile_desc;
+  a.counters = ws.counters;
+  a.n_pos = (uint32_t)n_tiles;
+  a.persistent = persistent ? 1 : 0;
+  return a;
+}
+
 template <int TS, int NT, int BATCH>
-cudaError_t fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, float* images, float* t_out, uint32_t* nc_out, const FwdLoss& fl,
-                cudaStream_t s) {
+cudaError_t fwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, const uint32_t* pair_face,
+                       const ViewInfo* views, int32_t C, int32_t F, const float* bg, float* images, float* t_out,
+                       uint32_t* nc_out, const FwdLoss& fl, cudaStream_t s) {
   auto kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss>
               : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug>
                         : k_raster_fwd<TS, NT, BATCH, kFwdPlain>;
-  cudaError_t e = launch_chained(kern, false, dim3((unsigned)n_tiles), dim3(NT), 0, s, (const uint2*)ws.tile_range,
-                                 pair_face, (const float4*)ws.rec_u, (const float4*)ws.rec_q,
-                                 (const float4*)ws.face_col, views, C, F, bg[0], bg[1], bg[2], images, ws.pix_T,
-                                 ws.pix_last, t_out, nc_out, ws.cap_pixels, fl, (const uint4*)ws.tile_desc,
-                                 ws.counters);
+  const unsigned grid =
+      persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
+  cudaError_t e = launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
+                                 raster_args(ws, pair_face, views, F, bg, n_tiles, persistent), images, ws.pix_T,
+                                 ws.pix_last, t_out, nc_out, ws.cap_pixels, fl);
   if (e == cudaSuccess && fl.target)
     e = launch_chained(k_sum_partials, true, dim3(1), dim3(1024), 0, s, (const float*)fl.part, n_tiles * (NT / 32), 1.0,
                        fl.loss);
@@ -790,28 +950,30 @@ cudaError_t fwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pai
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t bwd_launch(int64_t n_tiles, const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t C,
-                int32_t F, const float* bg, const float* dL, const float* dLdT, const BwdLoss& bl, const BwdZero& bz,
-                cudaStream_t s) {
+cudaError_t bwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, const uint32_t* pair_face,
+                       const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
+                       const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
   auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
-  return launch_chained(kern, false, dim3((unsigned)n_tiles), dim3(NT), 0, s, (const uint2*)ws.tile_range, pair_face,
-                        (const float4*)ws.rec_u, (const float4*)ws.rec_q, (const float4*)ws.face_col, views, C, F,
-                        bg[0], bg[1], bg[2], dL, dLdT, (const float*)ws.pix_T, (const uint32_t*)ws.pix_last,
-                        ws.rec_grad, ws.face_grad, bl, bz, (const uint4*)ws.tile_desc, ws.counters);
+  const unsigned grid =
+      persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
+  return launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
+                        raster_args(ws, pair_face, views, F, bg, n_tiles, persistent), dL, dLdT,
+                        (const float*)ws.pix_T, (const uint32_t*)ws.pix_last, ws.rec_grad, ws.face_grad, bl, bz);
 }
 
 }  // namespace
 
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
-                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              float* images, float* t_final_out, uint32_t* ncontrib_out, const FwdLoss& fl,
-                              cudaStream_t s, int64_t* launches) {
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+                              const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
+                              int64_t n_tiles, const float* bg, float* images, float* t_final_out,
+                              uint32_t* ncontrib_out, const FwdLoss& fl, cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return fl.target ? cudaMemsetAsync(fl.loss, 0, sizeof(double), s) : cudaSuccess;
   if (fl.target) *launches += 1;  // k_sum_partials
   cudaError_t e = cudaSuccess;
-#define GMR_FWD(TS_, NT_, B_)                                                                               \
-  if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  e = fwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, images, t_final_out, ncontrib_out, fl, s)
+#define GMR_FWD(TS_, NT_, B_)                                                                                    \
+  if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
+  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, ws, pair_face, views, C, F, bg, images, t_final_out,          \
+                               ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
   else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
   else GMR_FWD(16, 64, 64); else GMR_FWD(16, 64, 128); else GMR_FWD(16, 64, 256);
@@ -822,15 +984,15 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, const Workspace&
   return e;
 }
 
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, const Workspace& ws, const uint32_t* pair_face,
-                              const ViewInfo* views, int32_t C, int32_t F, int64_t n_tiles, const float* bg,
-                              const float* dL_dimages, const float* dL_dT, const BwdLoss& bl, const BwdZero& bz,
-                              cudaStream_t s, int64_t* launches) {
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+                              const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
+                              int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
+                              const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches) {
   if (n_tiles <= 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-#define GMR_BWD(TS_, NT_, B_)                                                                               \
-  if (tile == TS_ && threads == NT_ && batch == B_)                                                         \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, bz, s)
+#define GMR_BWD(TS_, NT_, B_)                                                                                    \
+  if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
@@ -901,10 +1063,6 @@ cudaError_t launch_silhouette_bce(const float* t_final, const float* mask, int64
                                                           loss);
   *launches += 1;
   return cudaGetLastError();
-}
-
-int64_t l2_loss_partials_needed(int64_t n) {
-  return 1 + std::min<int64_t>((n + kLossBlockElems - 1) / kLossBlockElems, kLossMaxBlocks);
 }
 
 cudaError_t launch_l2_loss(const float* img, const float* target, int64_t n, float* grad, double* loss,

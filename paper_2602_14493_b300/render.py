@@ -79,10 +79,13 @@ class Renderer:
     (False: never synchronise; pre-size with ``reserve`` for graph capture).
     profile: time the stages with CUDA events (True: all of them; or a list
     of stage names from ``STAGES``).
+    persistent: run the compositing kernels as persistent grids (resident
+    CTAs taking tiles from a counter) instead of one CTA per tile.
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
-                 sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None):
+                 sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None,
+                 persistent=False):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -97,7 +100,8 @@ class Renderer:
         self.cfg.color_mode = _COLOR[color_mode]
         self.cfg.bg[:] = [float(x) for x in bg]
         self.cfg.flags = ((_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
-                          | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0))
+                          | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0)
+                          | (_lib.GMR_FLAG_PERSISTENT if persistent else 0))
         self.cfg.profile_stages = _stage_mask(profile)
         self.color_mode = color_mode
         self._ctx = ctypes.c_void_p()
@@ -142,6 +146,9 @@ class Renderer:
             if k == "sync_check":
                 self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_SYNC_CHECK) | (_lib.GMR_FLAG_SYNC_CHECK if v else 0)
                 continue
+            if k == "persistent":
+                self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_PERSISTENT) | (_lib.GMR_FLAG_PERSISTENT if v else 0)
+                continue
             if k == "profile":
                 self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_PROFILE) | (_lib.GMR_FLAG_PROFILE if v else 0)
                 self.cfg.profile_stages = _stage_mask(v)
@@ -149,9 +156,33 @@ class Renderer:
             setattr(self.cfg, k, v)
         self._check(self._L.gmr_set_config(self._ctx, ctypes.byref(self.cfg)), "gmr_set_config")
 
+    def set_workspace_limit(self, max_bytes):
+        """Caps the device bytes of the workspace (0: no cap); a call that
+        would grow it beyond the cap raises GmrError (GMR_ERR_OOM)."""
+        self._check(self._L.gmr_set_workspace_limit(self._ctx, int(max_bytes)), "gmr_set_workspace_limit")
+
     def reserve(self, max_faces, max_views, max_pixels, max_pairs):
         self._check(self._L.gmr_reserve(self._ctx, int(max_faces), int(max_views), int(max_pixels), int(max_pairs)),
                     "gmr_reserve")
+
+    def _remember(self, verts, faces, rgb, opacity):
+        """Keeps the forward's inputs (the backward reads them again) with
+        their version counters, which torch bumps on every in-place change."""
+        self.fwd_token += 1
+        inputs = (verts, faces, rgb, opacity)
+        self._saved = inputs
+        self._saved_versions = tuple(None if t is None else t._version for t in inputs)
+
+    def _saved_inputs(self):
+        """The last forward's inputs; raises when one of them was modified in
+        place since (the backward would mix new values with the forward's
+        compositing state)."""
+        if self._saved is None:
+            raise _lib.GmrError("backward without a forward")
+        for t, ver, name in zip(self._saved, self._saved_versions, ("verts", "faces", "rgb", "opacity")):
+            if t is not None and t._version != ver:
+                raise _lib.GmrError(f"{name} was modified in place between the forward and the backward")
+        return self._saved
 
     # -- entry points
     def convert(self, verts, faces, rgb=None, opacity=None, stream=None):
@@ -185,8 +216,7 @@ class Renderer:
         self._check(self._L.gmr_render_fwd(self._ctx, _ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
                                            _ptr(rgb), _ptr(opacity), cam_arr, len(cam_arr), _ptr(images),
                                            _ptr(t_final), _stream(stream)), "gmr_render_fwd")
-        self.fwd_token += 1
-        self._saved = (verts, faces, rgb, opacity)
+        self._remember(verts, faces, rgb, opacity)
         return images, t_final
 
     def forward_l2(self, verts, faces, rgb, opacity, cams, target, images=None, grad=None, loss=None, stream=None):
@@ -212,8 +242,7 @@ class Renderer:
                                               _ptr(rgb), _ptr(opacity), cam_arr, len(cam_arr), _ptr(images), None,
                                               _ptr(target), _ptr(grad), _ptr(loss), _stream(stream)),
                     "gmr_render_fwd_l2")
-        self.fwd_token += 1
-        self._saved = (verts, faces, rgb, opacity)
+        self._remember(verts, faces, rgb, opacity)
         return images, grad, loss
 
     def backward(self, dL_dimages, dverts=None, drgb=None, dopacity=None, accumulate=False, stream=None,
@@ -224,8 +253,7 @@ class Renderer:
             _check_dev(dL_dimages, "dL_dimages", torch.float32)
         if dL_dtfinal is not None:
             _check_dev(dL_dtfinal, "dL_dtfinal", torch.float32)
-        verts, faces, rgb, opacity = self._saved
-        dev = verts.device
+        verts, faces, rgb, opacity = self._saved_inputs()
         if dverts is None:
             dverts = torch.empty_like(verts)
         if drgb is None:
@@ -248,7 +276,7 @@ class Renderer:
             raise _lib.GmrError("target must have the shape of images")
         if dL_dtfinal is not None:
             _check_dev(dL_dtfinal, "dL_dtfinal", torch.float32)
-        verts, faces, rgb, opacity = self._saved
+        verts, faces, rgb, opacity = self._saved_inputs()
         if loss is None:
             loss = torch.empty((), device=verts.device, dtype=torch.float64)
         if dverts is None:

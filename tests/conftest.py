@@ -13,6 +13,16 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: longer CPU test")
 
 
+@pytest.fixture(scope="session", autouse=True)
+def oracle_on_all_cores():
+    """The oracle's loops run on every host core (its results are identical
+    for any thread count; tests/test_oracle_threads.py checks that)."""
+    import oracle
+
+    oracle.set_threads(0)
+    yield
+
+
 @pytest.fixture(scope="session")
 def oracle_mod():
     import oracle

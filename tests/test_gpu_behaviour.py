@@ -379,3 +379,121 @@ def test_copy_h2d_kernel_copy():
     st = _lib.load().gmr_copy_h2d(ctypes.c_void_p(d64.data_ptr()), ctypes.c_void_p(pageable.data_ptr()), 64,
                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 1  # GMR_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", [(16, 128, 128), (16, 256, 128), (16, 64, 256), (32, 256, 256)])
+def test_persistent_grid_matches_per_tile_grid(shape):
+    """The compositing kernels as persistent grids (resident CTAs taking
+    tiles from a counter) give the same images and final T bit for bit and
+    the same gradients up to the order of the float atomics, also for a
+    second forward and a second backward (each must start its counter
+    again)."""
+    tile, threads, threads_bwd = shape
+    s = _uneven()
+    g = torch.sin(torch.arange(s.n_pixels * 3, device=DEV, dtype=torch.float32)).reshape(-1, 3).contiguous()
+    outs = {}
+    for persistent in (False, True):
+        r = _renderer(tile=tile, threads=threads, threads_bwd=threads_bwd, persistent=persistent)
+        v, f, c, o = to_dev(s)
+        res = []
+        for _ in range(2):  # two forwards, each with two backwards
+            img, T = r.forward(v, f, c, o, s.cams)
+            for _ in range(2):
+                dv, dc, do = r.backward(g)
+                res.append((img.cpu().numpy().copy(), T.cpu().numpy().copy(), dv.cpu().numpy().copy(),
+                            dc.cpu().numpy().copy(), do.cpu().numpy().copy()))
+        assert r.device_status() == 0
+        outs[persistent] = res
+        r.close()
+    ref = outs[False][0]
+    for res in (outs[False], outs[True]):
+        for img, T, dv, dc, do in res:
+            np.testing.assert_array_equal(img, ref[0])
+            np.testing.assert_array_equal(T, ref[1])
+            assert rel_l2(dv, ref[2]) < 1e-5
+            assert rel_l2(dc, ref[3]) < 1e-5
+            assert rel_l2(do, ref[4]) < 1e-5
+
+
+def test_inplace_modification_between_forward_and_backward_raises():
+    from paper_2602_14493_b300 import GmrError
+
+    r = _renderer()
+    s = gi.scene_single_view(level=2, width=32, height=32)
+    v, f, c, o = to_dev(s)
+    img, _ = r.forward(v, f, c, o, s.cams)
+    r.backward(torch.ones_like(img))  # unchanged inputs: fine
+    v.add_(0.01)  # e.g. an optimiser step taken before the backward
+    with pytest.raises(GmrError, match="verts"):
+        r.backward(torch.ones_like(img))
+    img, _ = r.forward(v, f, c, o, s.cams)
+    c.mul_(0.5)
+    with pytest.raises(GmrError, match="rgb"):
+        r.backward_l2(img, torch.zeros_like(img))
+    r.close()
+
+
+def test_workspace_limit_returns_oom_and_context_recovers():
+    """GMR_ERR_OOM without exhausting the device: a workspace cap below what
+    the forward needs fails the call before anything is enqueued; with the
+    cap lifted the same context renders the reference image."""
+    from paper_2602_14493_b300 import GmrError
+
+    s = gi.scene_single_view(level=3, width=96, height=64)
+    v, f, c, o = to_dev(s)
+    ref = _renderer()
+    img_ref, _ = ref.forward(v, f, c, o, s.cams)
+    torch.cuda.synchronize()
+    need = ref.stats()["workspace_bytes"]
+    ref.close()
+    r = _renderer()
+    r.set_workspace_limit(need // 4)
+    with pytest.raises(GmrError, match="GMR_ERR_OOM"):
+        r.forward(v, f, c, o, s.cams)
+    with pytest.raises(GmrError, match="GMR_ERR_OOM"):
+        r.reserve(len(s.faces), 1, s.n_pixels, 10 ** 6)
+    assert r.stats()["workspace_bytes"] <= need // 4
+    r.set_workspace_limit(0)
+    img, _ = r.forward(v, f, c, o, s.cams)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(img.cpu().numpy(), img_ref.cpu().numpy())
+    assert r.device_status() == 0
+    r.close()
+
+
+def test_nonfinite_vertices_are_culled_and_match_oracle():
+    """Faces with a NaN or infinite vertex fail the binning's finiteness test
+    (they reach no tile): the rest of the image matches the oracle, the
+    device status stays clear, and every gradient is finite (exactly zero
+    for the non-finite vertices)."""
+    s = gi.scene_single_view(level=3, width=96, height=80)
+    verts = s.verts.copy()
+    bad = [0, 17, 101, 300]
+    verts[bad[0]] = np.nan
+    verts[bad[1], 2] = np.inf
+    verts[bad[2], 0] = -np.inf
+    verts[bad[3], 1] = np.nan
+    s = gi.Scene(s.name, verts, s.faces, s.rgb, s.opacity, s.cams)
+    r = _renderer()
+    (v, f, c, o), img, T = render_gpu(r, s)
+    ref = oracle.render(s)
+    amb = (ref["flags"] & 3) != 0
+    assert np.isfinite(img.cpu().numpy()).all()
+    assert np.abs(img.cpu().numpy() - ref["rgb"])[~amb].max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy() - ref["T"])[~amb].max() <= IMG_TOL
+    nb = r.stats()
+    assert nb["n_pairs"] > 0
+    gs = np.random.default_rng(3).normal(size=(s.n_pixels, 3))
+    gs[ref["flags"] != 0] = 0.0
+    dv, dc, do = r.backward(torch.from_numpy(gs.astype(np.float32)).to(DEV))
+    torch.cuda.synchronize()
+    assert r.device_status() == 0
+    ob = oracle.backward(s, gs.astype(np.float32).astype(np.float64))
+    dvn = dv.cpu().numpy()
+    assert np.isfinite(dvn).all() and np.isfinite(dc.cpu().numpy()).all() and np.isfinite(do.cpu().numpy()).all()
+    assert np.isfinite(ob["dverts"]).all()
+    np.testing.assert_array_equal(dvn[bad], 0.0)
+    np.testing.assert_array_equal(ob["dverts"][bad], 0.0)
+    assert rel_l2(dvn, ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    r.close()

@@ -6,7 +6,9 @@ the FP64 oracle computes one by one:
   16x16 and 32x32 tiles (the autotuner's two tile sizes) and the launch
   shape the benchmark times;
 * 16 views of 1024^2 of a level-8 icosphere (1.31M faces) with Perlin
-  displacement, in one batched call, in the benchmark's launch shape.
+  displacement, in one batched call, in the benchmark's launch shape;
+
+each also with the compositing kernels as persistent grids.
 
 Images: max abs error 1e-5 on pixels whose discrete decisions are not in the
 ambiguity bands. Gradients: dL/dI is non-zero on the sampled pixels only, so
@@ -44,8 +46,10 @@ def _check(scene, shapes, n_random, window, seed):
     g = np.zeros((scene.n_pixels, 3), dtype=np.float32)
     g[lin] = gs
     g = torch.from_numpy(g).to(DEV)
-    for tile, threads, threads_bwd in shapes:
-        r = Renderer(tile=tile, threads=threads, threads_bwd=threads_bwd)
+    for shape in shapes:
+        tile, threads, threads_bwd = shape[:3]
+        persistent = len(shape) > 3 and bool(shape[3])
+        r = Renderer(tile=tile, threads=threads, threads_bwd=threads_bwd, persistent=persistent)
         img, T = r.forward(v, f, c, o, scene.cams)
         dv, dc, do = r.backward(g)
         torch.cuda.synchronize()
@@ -62,10 +66,10 @@ def _check(scene, shapes, n_random, window, seed):
 def test_fibonacci_64_uneven_views_full_size():
     s = gi.scene_fibonacci_uneven()
     assert len(s.cams) == 64 and s.n_pixels > 20_000_000
-    _check(s, ((16, 128, 128), BENCH_SHAPE, (32, 256, 256)), n_random=256, window=4, seed=301)
+    _check(s, ((16, 128, 128), BENCH_SHAPE, (32, 256, 256), BENCH_SHAPE + (1,)), n_random=256, window=4, seed=301)
 
 
 def test_large_mesh_16_views_1024_full_size():
     s = gi.scene_large()
     assert len(s.faces) == 1_310_720 and s.n_pixels == 16 * 1024 * 1024
-    _check(s, (BENCH_SHAPE,), n_random=128, window=4, seed=401)
+    _check(s, (BENCH_SHAPE, BENCH_SHAPE + (1,)), n_random=128, window=4, seed=401)

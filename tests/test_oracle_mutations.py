@@ -20,8 +20,8 @@ MUTATIONS = {
     "kappa_constant": ("T kappa = area / (T(kPi) *", "T kappa = area / (T(3.0) *"),
     "gram_schmidt_sign": ("dxk += -dot(dw, g.xa);", "dxk += dot(dw, g.xa);"),
     "suffix_division": ("- S[ch] / (1.0 - cb.alpha)", "- S[ch]"),
-    "conic_index": ("G.du[0] += dpower * (-(pr.Q[0] * cb.dx + pr.Q[1] * cb.dy));",
-                    "G.du[0] += dpower * (-(pr.Q[0] * cb.dx + pr.Q[2] * cb.dy));"),
+    "conic_index": ("t.du[0] = dpower * (-(pr.Q[0] * cb.dx + pr.Q[1] * cb.dy));",
+                    "t.du[0] = dpower * (-(pr.Q[0] * cb.dx + pr.Q[2] * cb.dy));"),
     "jacobian_operand": ("p.J[2] = -fx * x / (z * z);", "p.J[2] = -fx * y / (z * z);"),
     "add_after_stop": ("if (val(test) < kTMin) break;",
                        "if (val(test) < kTMin) { for (int ch = 0; ch < 3; ++ch) "
@@ -44,9 +44,14 @@ def test_planted_mistake_is_caught(name, tmp_path):
     cpp = tmp_path / "mutant.cpp"
     lib = tmp_path / "libmutant.so"
     cpp.write_text(src.replace(a, b))
-    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(lib), str(cpp)],
-                   check=True)
+    sys.path.insert(0, ROOT)
+    from oracle import build as obuild
+
+    subprocess.run(["g++", *obuild.FLAGS, "-o", str(lib), str(cpp)], check=True)
     env = dict(os.environ, GMR_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + PINS, cwd=ROOT,
                        env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation {name} was not caught:\n{r.stdout[-2000:]}"
+    # caught by a failing pin, not by a mutant that does not load
+    assert "OSError" not in r.stdout and "undefined symbol" not in r.stdout, r.stdout[-2000:]
+    assert " passed" in r.stdout or "1 failed" in r.stdout, r.stdout[-2000:]

@@ -12,7 +12,7 @@ import oracle
 @pytest.fixture
 def restore_threads():
     yield
-    oracle.set_threads(1)
+    oracle.set_threads(0)
 
 
 def _run(scene, threads, color_mode=0, with_T=False):
