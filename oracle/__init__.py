@@ -45,11 +45,12 @@ def lib():
         L.gmr_oracle_sorted_pairs.argtypes = [i32, P, i32, P, i32, P, P, i32, i64, P, P, P]
         L.gmr_oracle_sorted_pairs.restype = i64
         L.gmr_oracle_render.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P,
-                                        P, P, P, P, P, P]
+                                        P, P, P, P, P, P, i32]
         L.gmr_oracle_backward.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P,
-                                          P, P, P, P, P, P]
+                                          P, P, P, P, P, P, i32]
         L.gmr_oracle_jvp.argtypes = [i32, P, i32, P, P, i32, P, f32, i32, i32, P, P, P, i32, i64, P, P,
-                                     P, P, P, P, P]
+                                     P, P, P, P, P, i32]
+        L.gmr_oracle_sh_basis.argtypes = [i32, i64, P, P]
         L.gmr_oracle_set_threads.argtypes = [i32]
         L.gmr_oracle_set_threads.restype = i32
         _LIB = L
@@ -189,8 +190,10 @@ def _scene_args(scene, cov_mode, color_mode, bg, rgb=None):
 
 
 def render(scene, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, bands=DEFAULT_BANDS,
-           opacity_scalar=1.0):
-    """Brute-force FP64 render of the given pixels (default: every pixel)."""
+           opacity_scalar=1.0, sh_degree=0):
+    """Brute-force FP64 render of the given pixels (default: every pixel).
+    color_mode 0: per-face rgb [F,3]; 1: per-vertex rgb [V,3] (Eq. 16);
+    2: spherical-harmonic coefficients [F,(sh_degree+1)^2,3]."""
     if pixels is None:
         pixels = all_pixels(scene.cams)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
@@ -204,13 +207,14 @@ def render(scene, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, bands
     bd = np.ascontiguousarray(np.asarray(bands, dtype=np.float64)) if bands is not None else None
     rc = lib().gmr_oracle_render(len(v), _p(v), len(f), _p(f), _p(c), color_mode, _p(o), opacity_scalar,
                                  cov_mode, len(scene.cams), _p(cf), _p(ci), _p(b), tile, n, _p(pix), _p(out),
-                                 _p(T), _p(last), _p(nc), _p(fl), _p(bd))
+                                 _p(T), _p(last), _p(nc), _p(fl), _p(bd), sh_degree)
     if rc != 0:
         raise ValueError(f"oracle render failed ({rc})")
     return {"rgb": out, "T": T, "last_face": last, "n_contrib": nc, "flags": fl}
 
 
-def backward(scene, dLdI, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, opacity_scalar=1.0, dLdT=None):
+def backward(scene, dLdI, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, opacity_scalar=1.0, dLdT=None,
+             sh_degree=0):
     """Reverse-mode FP64 gradients for dL/dI (and optionally dL/dT_final)
     given at ``pixels``."""
     if pixels is None:
@@ -228,14 +232,24 @@ def backward(scene, dLdI, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=1
     assert gT is None or len(gT) == len(pix)
     rc = lib().gmr_oracle_backward(V, _p(v), F, _p(f), _p(c), color_mode, _p(o), opacity_scalar, cov_mode, C,
                                    _p(cf), _p(ci), _p(b), tile, len(pix), _p(pix), _p(g), _p(dV), _p(drgb),
-                                   _p(dop), _p(rec), _p(gT))
+                                   _p(dop), _p(rec), _p(gT), sh_degree)
     if rc != 0:
         raise ValueError(f"oracle backward failed ({rc})")
     return {"dverts": dV, "drgb": drgb, "dopacity": dop, "rec": rec}
 
 
+def sh_basis(degree, dirs):
+    """Real spherical harmonics of degree <= ``degree`` (colour mode 2) at
+    unit directions dirs [n,3]: [n,(degree+1)^2]."""
+    d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+    out = np.zeros((len(d), (degree + 1) ** 2))
+    if lib().gmr_oracle_sh_basis(int(degree), len(d), _p(d), _p(out)) != 0:
+        raise ValueError("degree must be 0..3")
+    return out
+
+
 def jvp(scene, w, dverts=None, drgb=None, dop=None, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16,
-        opacity_scalar=1.0, wT=None):
+        opacity_scalar=1.0, wT=None, sh_degree=0):
     """Forward-mode d/de (sum <w, I(x + e dir)> + sum wT T_final) with dual
     numbers."""
     if pixels is None:
@@ -252,7 +266,8 @@ def jvp(scene, w, dverts=None, drgb=None, dop=None, pixels=None, cov_mode=0, col
     rc = lib().gmr_oracle_jvp(len(v), _p(v), len(f), _p(f), _p(c), color_mode, _p(o), opacity_scalar, cov_mode,
                               len(scene.cams), _p(cf), _p(ci), _p(b), tile, len(pix), _p(pix), _p(ww), _p(dv),
                               _p(dc), _p(do), _p(out),
-                              _p(None if wT is None else np.ascontiguousarray(np.asarray(wT, dtype=np.float64))))
+                              _p(None if wT is None else np.ascontiguousarray(np.asarray(wT, dtype=np.float64))),
+                              sh_degree)
     if rc != 0:
         raise ValueError(f"oracle jvp failed ({rc})")
     return float(out[0])

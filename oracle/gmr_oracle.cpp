@@ -269,6 +269,83 @@ FaceGauss<T> convert_face(V3<T> vi, V3<T> vj, V3<T> vk, int cov_mode) {
 // given opacity is taken as a probability and clamped to [0, 1].
 template <class T> T clamp01(T o) { return tmin(tmax(o, T(0.0)), T(1.0)); }
 
+// ---------------------------------------------------------------- view-dependent colour
+// Spherical-harmonic colour, the extension of the facet colour that the
+// colour assignment of Sec. 2.2 names: per facet and channel, K = (L + 1)^2
+// coefficients a_k of the real spherical harmonics Y_k of degree <= L
+// (L <= 3), evaluated at the unit direction d from the camera centre to the
+// facet's centroid (Eq. 3-4); colour = max(0, sum_k a_k Y_k(d) + 1/2) (the
+// offset and the clamp at zero are the 3DGS convention; the paper states
+// none). Basis: real spherical harmonics without the Condon-Shortley phase,
+// ordered (l, m) = (0, 0), (1, -1), (1, 0), (1, 1), (2, -2), ..., (3, 3), each
+// a polynomial in the components (x, y, z) of the unit vector d; the
+// normalisations follow from the closed forms below.
+struct ShConst {
+  double c0, c1, c2a, c2b, c2c, c3a, c3b, c3c, c3d, c3e;
+  ShConst() {
+    c0 = 0.5 * std::sqrt(1.0 / kPi);
+    c1 = std::sqrt(3.0 / (4.0 * kPi));
+    c2a = 0.5 * std::sqrt(15.0 / kPi);   // xy, yz, xz
+    c2b = 0.25 * std::sqrt(5.0 / kPi);   // 3 z^2 - 1
+    c2c = 0.25 * std::sqrt(15.0 / kPi);  // x^2 - y^2
+    c3a = 0.25 * std::sqrt(35.0 / (2.0 * kPi));  // y (3 x^2 - y^2), x (x^2 - 3 y^2)
+    c3b = 0.5 * std::sqrt(105.0 / kPi);          // x y z
+    c3c = 0.25 * std::sqrt(21.0 / (2.0 * kPi));  // y (5 z^2 - 1), x (5 z^2 - 1)
+    c3d = 0.25 * std::sqrt(7.0 / kPi);           // z (5 z^2 - 3)
+    c3e = 0.25 * std::sqrt(105.0 / kPi);         // z (x^2 - y^2)
+  }
+};
+const ShConst kSh;
+
+inline int sh_count(int L) { return (L + 1) * (L + 1); }
+
+template <class T>
+void sh_basis(int L, T x, T y, T z, T* Y) {
+  Y[0] = T(kSh.c0);
+  if (L < 1) return;
+  Y[1] = T(kSh.c1) * y;
+  Y[2] = T(kSh.c1) * z;
+  Y[3] = T(kSh.c1) * x;
+  if (L < 2) return;
+  Y[4] = T(kSh.c2a) * x * y;
+  Y[5] = T(kSh.c2a) * y * z;
+  Y[6] = T(kSh.c2b) * (T(3.0) * z * z - T(1.0));
+  Y[7] = T(kSh.c2a) * x * z;
+  Y[8] = T(kSh.c2c) * (x * x - y * y);
+  if (L < 3) return;
+  Y[9] = T(kSh.c3a) * y * (T(3.0) * x * x - y * y);
+  Y[10] = T(kSh.c3b) * x * y * z;
+  Y[11] = T(kSh.c3c) * y * (T(5.0) * z * z - T(1.0));
+  Y[12] = T(kSh.c3d) * z * (T(5.0) * z * z - T(3.0));
+  Y[13] = T(kSh.c3c) * x * (T(5.0) * z * z - T(1.0));
+  Y[14] = T(kSh.c3e) * z * (x * x - y * y);
+  Y[15] = T(kSh.c3a) * x * (x * x - T(3.0) * y * y);
+}
+
+// Gradient of each polynomial above with respect to (x, y, z) (as written,
+// off the sphere too; callers project it onto the sphere's tangent plane).
+void sh_basis_grad(int L, double x, double y, double z, double G[16][3]) {
+  for (int k = 0; k < 16; ++k) G[k][0] = G[k][1] = G[k][2] = 0.0;
+  if (L < 1) return;
+  G[1][1] = kSh.c1;
+  G[2][2] = kSh.c1;
+  G[3][0] = kSh.c1;
+  if (L < 2) return;
+  G[4][0] = kSh.c2a * y; G[4][1] = kSh.c2a * x;
+  G[5][1] = kSh.c2a * z; G[5][2] = kSh.c2a * y;
+  G[6][2] = kSh.c2b * 6.0 * z;
+  G[7][0] = kSh.c2a * z; G[7][2] = kSh.c2a * x;
+  G[8][0] = kSh.c2c * 2.0 * x; G[8][1] = -kSh.c2c * 2.0 * y;
+  if (L < 3) return;
+  G[9][0] = kSh.c3a * 6.0 * x * y; G[9][1] = kSh.c3a * (3.0 * x * x - 3.0 * y * y);
+  G[10][0] = kSh.c3b * y * z; G[10][1] = kSh.c3b * x * z; G[10][2] = kSh.c3b * x * y;
+  G[11][1] = kSh.c3c * (5.0 * z * z - 1.0); G[11][2] = kSh.c3c * 10.0 * y * z;
+  G[12][2] = kSh.c3d * (15.0 * z * z - 3.0);
+  G[13][0] = kSh.c3c * (5.0 * z * z - 1.0); G[13][2] = kSh.c3c * 10.0 * x * z;
+  G[14][0] = kSh.c3e * 2.0 * x * z; G[14][1] = -kSh.c3e * 2.0 * y * z; G[14][2] = kSh.c3e * (x * x - y * y);
+  G[15][0] = kSh.c3a * (3.0 * x * x - 3.0 * y * y); G[15][1] = -kSh.c3a * 6.0 * x * y;
+}
+
 // ---------------------------------------------------------------- projection
 // EWA splatting (Sec. 2.1, Zwicker et al.): the perspective map is replaced
 // by its Jacobian J at the Gaussian's camera-space mean t.
@@ -418,7 +495,8 @@ struct Scene {
   const float* verts;   // V x 3 FP32
   const int* faces;     // F x 3
   const float* rgb;     // F x 3 (per face) or V x 3 (per vertex)
-  int color_mode;       // 0 per-face, 1 per-vertex averaged (Eq. 16)
+  int color_mode;       // 0 per-face, 1 per-vertex averaged (Eq. 16), 2 spherical harmonics
+  int sh_degree;        // colour mode 2: L, rgb is F x (L + 1)^2 x 3
   const float* opacity; // F, or null -> scalar
   float opacity_scalar;
   int cov_mode;
@@ -426,6 +504,10 @@ struct Scene {
   double bg[3];
   int tile;
 };
+
+bool check_sh(const Scene& s) {
+  return s.color_mode != 2 || (s.sh_degree >= 0 && s.sh_degree <= 3);
+}
 
 bool check_scene(const Scene& s) {
   if (s.V < 0 || s.F < 0 || s.C < 0) return false;
@@ -506,6 +588,44 @@ Dual face_opacity<Dual>(const Scene& s, const Direction* dir, int f) {
   return clamp01(Dual(o, d));
 }
 
+// Coefficient k of channel ch of facet f (colour mode 2; rgb is F x K x 3).
+template <class T>
+T sh_coef(const Scene& s, const Direction* dir, int f, int k, int ch) {
+  return T((double)s.rgb[((size_t)f * sh_count(s.sh_degree) + k) * 3 + ch]);
+}
+template <>
+Dual sh_coef<Dual>(const Scene& s, const Direction* dir, int f, int k, int ch) {
+  const size_t i = ((size_t)f * sh_count(s.sh_degree) + k) * 3 + ch;
+  return Dual((double)s.rgb[i], (dir && dir->drgb) ? dir->drgb[i] : 0.0);
+}
+
+// Camera centre in world coordinates: x_cam = R x + t = 0 at x = -R^T t.
+V3<double> cam_centre(const Cam& c) {
+  double o[3];
+  for (int q = 0; q < 3; ++q)
+    o[q] = -((double)c.R[q] * c.t[0] + (double)c.R[3 + q] * c.t[1] + (double)c.R[6 + q] * c.t[2]);
+  return mk(o[0], o[1], o[2]);
+}
+
+// Colour of facet f seen from camera cam (colour mode 2): out = max(0, raw),
+// raw = sum_k a_k Y_k(d) + 1/2, d the unit vector from the camera centre to
+// the facet's centroid g.mean.
+template <class T>
+void sh_colour(const Scene& s, const Direction* dir, const FaceGauss<T>& g, const Cam& cam, int f, T out[3],
+               T raw[3]) {
+  const V3<double> o = cam_centre(cam);
+  const V3<T> w = mk<T>(g.mean[0] - T(o.x), g.mean[1] - T(o.y), g.mean[2] - T(o.z));
+  const T r = norm(w);
+  T Y[16];
+  sh_basis<T>(s.sh_degree, w.x / r, w.y / r, w.z / r, Y);
+  for (int ch = 0; ch < 3; ++ch) {
+    T acc = T(0.5);
+    for (int k = 0; k < sh_count(s.sh_degree); ++k) acc += sh_coef<T>(s, dir, f, k, ch) * Y[k];
+    raw[ch] = acc;
+    out[ch] = tmax(T(0.0), acc);
+  }
+}
+
 // Ambiguity bands: a pixel is flagged when one of its discrete decisions is
 // so close to its threshold that FP32 evaluation may take the other side.
 struct Bands { double alpha_rel, t_rel; };
@@ -527,17 +647,23 @@ template <class T>
 struct Prepared {
   std::vector<FaceGauss<T>> g;   // F
   std::vector<Proj<T>> p;        // C*F
-  std::vector<T> col;            // F*3
+  std::vector<T> col;            // F*3, or C*F*3 with view-dependent colour
   std::vector<T> op;             // F
   std::vector<Bin> bins;         // C*F
   std::vector<std::vector<int>> order;  // per view
+  bool per_view_colour = false;
+  int F = 0;
+  // index of the colour of facet f in view c
+  size_t cidx(int view, int f) const { return per_view_colour ? (size_t)view * F + f : (size_t)f; }
 };
 
 template <class T>
 Prepared<T> prepare(const Scene& s, const Direction* dir) {
   Prepared<T> P;
+  P.per_view_colour = s.color_mode == 2;
+  P.F = s.F;
   P.g.resize(s.F);
-  P.col.resize((size_t)s.F * 3);
+  P.col.resize((P.per_view_colour ? (size_t)s.C : 1) * (size_t)s.F * 3);
   P.op.resize(s.F);
 #pragma omp parallel for schedule(static) num_threads(g_threads)
   for (int f = 0; f < s.F; ++f) {
@@ -546,7 +672,7 @@ Prepared<T> prepare(const Scene& s, const Direction* dir) {
     for (int k = 0; k < 3; ++k)
       v[k] = mk<T>(input_vert<T>(s, dir, fi[k], 0), input_vert<T>(s, dir, fi[k], 1), input_vert<T>(s, dir, fi[k], 2));
     P.g[f] = convert_face<T>(v[0], v[1], v[2], s.cov_mode);
-    face_colour<T>(s, dir, f, &P.col[3 * (size_t)f]);
+    if (!P.per_view_colour) face_colour<T>(s, dir, f, &P.col[3 * (size_t)f]);
     P.op[f] = face_opacity<T>(s, dir, f);
   }
   P.bins = all_bins(s);
@@ -557,6 +683,10 @@ Prepared<T> prepare(const Scene& s, const Direction* dir) {
   for (long long r = 0; r < n; ++r) {
     const int c = (int)(r / s.F), f = (int)(r % s.F);
     if (P.bins[(size_t)r].visible) P.p[(size_t)r] = project<T>(P.g[f], s.cams[c]);
+    if (P.per_view_colour) {
+      T raw[3];
+      sh_colour<T>(s, dir, P.g[f], s.cams[c], f, &P.col[3 * (size_t)r], raw);
+    }
   }
 #pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
   for (int c = 0; c < s.C; ++c) P.order[c] = sorted_visible(P.bins, s.F, c);
@@ -597,7 +727,7 @@ void composite_pixel(const Scene& s, const Prepared<T>& P, int view, int px, int
       cb.dx = val(dx); cb.dy = val(dy); cb.clamped = !(val(graw) < kAlphaMax);
       rec->push_back(cb);
     }
-    for (int ch = 0; ch < 3; ++ch) C[ch] += P.col[3 * (size_t)f + ch] * alpha * Tr;
+    for (int ch = 0; ch < 3; ++ch) C[ch] += P.col[3 * P.cidx(view, f) + ch] * alpha * Tr;
     Tr = test;
     lastf = f;
     ++nc;
@@ -611,8 +741,9 @@ void composite_pixel(const Scene& s, const Prepared<T>& P, int view, int px, int
 
 void build_scene(Scene& s, int V, const float* verts, int F, const int* faces, const float* rgb, int color_mode,
                  const float* opacity, float opacity_scalar, int cov_mode, int C, const float* cam_f,
-                 const int* cam_i, const double* bg, int tile) {
+                 const int* cam_i, const double* bg, int tile, int sh_degree) {
   s.V = V; s.F = F; s.C = C; s.verts = verts; s.faces = faces; s.rgb = rgb; s.color_mode = color_mode;
+  s.sh_degree = sh_degree;
   s.opacity = opacity; s.opacity_scalar = opacity_scalar; s.cov_mode = cov_mode;
   s.cams = read_cams(cam_f, cam_i, C);
   for (int k = 0; k < 3; ++k) s.bg[k] = bg ? bg[k] : 0.0;
@@ -786,6 +917,20 @@ void convert_backward(const FaceGauss<double>& g, V3<double> vi, V3<double> vj, 
 // ============================================================== C interface
 extern "C" {
 
+// The real spherical harmonics of degree <= L (colour mode 2) at n unit
+// directions dirs (n x 3): out is n x (L + 1)^2. Returns -1 for L outside
+// [0, 3].
+int gmr_oracle_sh_basis(int L, long long n, const double* dirs, double* out) {
+  if (L < 0 || L > 3) return -1;
+  const int K = sh_count(L);
+  for (long long i = 0; i < n; ++i) {
+    double Y[16];
+    sh_basis<double>(L, dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], Y);
+    for (int k = 0; k < K; ++k) out[i * K + k] = Y[k];
+  }
+  return 0;
+}
+
 // Host threads of the oracle's parallel loops (1 by default; n < 1 means all
 // cores OpenMP reports). Results are identical for every thread count.
 // Returns the count now in use.
@@ -940,9 +1085,12 @@ long long gmr_oracle_sorted_pairs(int V, const float* verts, int F, const int* f
 int gmr_oracle_render(int V, const float* verts, int F, const int* faces, const float* rgb, int color_mode,
                       const float* opacity, float opacity_scalar, int cov_mode, int C, const float* cam_f,
                       const int* cam_i, const double* bg, int tile, long long npix, const int* pix, double* out_rgb,
-                      double* out_T, int* out_last, int* out_nc, int* out_flags, const double* bands) {
+                      double* out_T, int* out_last, int* out_nc, int* out_flags, const double* bands,
+                      int sh_degree) {
   Scene s;
-  build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile);
+  build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile,
+              sh_degree);
+  if (!check_sh(s)) return -4;
   if (!check_scene(s)) return -1;
   Prepared<double> P = prepare<double>(s, nullptr);
   Bands b;
@@ -973,14 +1121,16 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
                         const float* opacity, float opacity_scalar, int cov_mode, int C, const float* cam_f,
                         const int* cam_i, const double* bg, int tile, long long npix, const int* pix,
                         const double* dLdI, double* dverts, double* drgb, double* dopac, double* rec_grads,
-                        const double* dLdT) {
+                        const double* dLdT, int sh_degree) {
   Scene s;
-  build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile);
+  build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile,
+              sh_degree);
+  if (!check_sh(s)) return -4;
   if (!check_scene(s)) return -1;
   Prepared<double> P = prepare<double>(s, nullptr);
   std::vector<FaceGrad> fg((size_t)C * F);
   for (auto& x : fg) { x.du[0] = x.du[1] = 0.0; x.dQ[0] = x.dQ[1] = x.dQ[2] = 0.0; }
-  std::vector<double> dcol((size_t)F * 3, 0.0), dop(F, 0.0);
+  std::vector<double> dcol(P.col.size(), 0.0), dop(F, 0.0);
   for (long long i = 0; i < npix; ++i)
     if (pix[3 * i] < 0 || pix[3 * i] >= C) return -3;
   // One pixel's terms, in the order they are added: the pixels are walked in
@@ -1017,7 +1167,7 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
         for (int k = (int)rec.size() - 1; k >= 0; --k) {
           const Contrib& cb = rec[k];
           int f = cb.face;
-          const double* col = &P.col[3 * (size_t)f];
+          const double* col = &P.col[3 * P.cidx(view, f)];
           Term t;
           t.f = f;
           t.view = view;
@@ -1049,7 +1199,7 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
     }
     for (const std::vector<Term>& tv : terms)
       for (const Term& t : tv) {
-        for (int ch = 0; ch < 3; ++ch) dcol[3 * (size_t)t.f + ch] += t.dcol[ch];
+        for (int ch = 0; ch < 3; ++ch) dcol[3 * P.cidx(t.view, t.f) + ch] += t.dcol[ch];
         if (t.clamped) continue;
         dop[t.f] += t.dop;
         FaceGrad& G = fg[(size_t)t.view * F + t.f];
@@ -1071,13 +1221,43 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
   // Chain through projection (per view) and conversion (per face).
   // (per face, the views are added in ascending order whatever the threads)
   std::vector<double> dmean((size_t)F * 3, 0.0), dcov((size_t)F * 9, 0.0);
+  // colour mode 2: dL/d(coefficients), per face summed over the views
+  const int K = color_mode == 2 ? sh_count(sh_degree) : 0;
+  std::vector<double> dsh((size_t)F * K * 3, 0.0);
 #pragma omp parallel for schedule(static) num_threads(g_threads)
   for (int f = 0; f < F; ++f)
     for (int c = 0; c < C; ++c) {
       size_t r = (size_t)c * F + f;
       const FaceGrad& G = fg[r];
-      if (G.du[0] == 0.0 && G.du[1] == 0.0 && G.dQ[0] == 0.0 && G.dQ[1] == 0.0 && G.dQ[2] == 0.0) continue;
-      project_backward(P.g[f], P.p[r], s.cams[c], G, &dmean[3 * (size_t)f], &dcov[9 * (size_t)f]);
+      if (!(G.du[0] == 0.0 && G.du[1] == 0.0 && G.dQ[0] == 0.0 && G.dQ[1] == 0.0 && G.dQ[2] == 0.0))
+        project_backward(P.g[f], P.p[r], s.cams[c], G, &dmean[3 * (size_t)f], &dcov[9 * (size_t)f]);
+      if (color_mode != 2) continue;
+      // colour = max(0, sum_k a_k Y_k(d) + 1/2), d = w / |w|, w = mean - o
+      const double* gc = &dcol[3 * r];
+      if (gc[0] == 0.0 && gc[1] == 0.0 && gc[2] == 0.0) continue;
+      double col[3], raw[3];
+      sh_colour<double>(s, nullptr, P.g[f], s.cams[c], f, col, raw);
+      const V3<double> o = cam_centre(s.cams[c]);
+      const V3<double> w = mk(P.g[f].mean[0] - o.x, P.g[f].mean[1] - o.y, P.g[f].mean[2] - o.z);
+      const double rn = norm(w);
+      const V3<double> d = (1.0 / rn) * w;
+      double Y[16], GY[16][3];
+      sh_basis<double>(sh_degree, d.x, d.y, d.z, Y);
+      sh_basis_grad(sh_degree, d.x, d.y, d.z, GY);
+      V3<double> dd = mk(0.0, 0.0, 0.0);
+      for (int ch = 0; ch < 3; ++ch) {
+        if (!(raw[ch] > 0.0)) continue;  // clamped at zero: no gradient
+        for (int k = 0; k < K; ++k) {
+          dsh[((size_t)f * K + k) * 3 + ch] += gc[ch] * Y[k];
+          const double a = (double)rgb[((size_t)f * K + k) * 3 + ch];
+          dd = dd + (gc[ch] * a) * mk(GY[k][0], GY[k][1], GY[k][2]);
+        }
+      }
+      // d = w / |w|: dL/dw = (dL/dd - d (d . dL/dd)) / |w|, and w = mean - o
+      const V3<double> dw = (1.0 / rn) * (dd - dot(d, dd) * d);
+      dmean[3 * (size_t)f] += dw.x;
+      dmean[3 * (size_t)f + 1] += dw.y;
+      dmean[3 * (size_t)f + 2] += dw.z;
     }
   if (dverts)
     for (long long k = 0; k < 3LL * V; ++k) dverts[k] = 0.0;
@@ -1113,6 +1293,8 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
   if (drgb) {
     if (color_mode == 0) {
       for (long long k = 0; k < 3LL * F; ++k) drgb[k] = dcol[k];
+    } else if (color_mode == 2) {
+      for (size_t k = 0; k < dsh.size(); ++k) drgb[k] = dsh[k];
     } else {
       for (long long k = 0; k < 3LL * V; ++k) drgb[k] = 0.0;
       for (int f = 0; f < F; ++f)
@@ -1127,11 +1309,15 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
     }
   }
   if (rec_grads) {
-    // per-face colour/opacity gradients are reported in view 0's slot
+    // per-face opacity gradients (and colour gradients, unless the colour is
+    // view-dependent: then per record) are reported in view 0's slot
     for (int f = 0; f < F && C > 0; ++f) {
       double* o = rec_grads + 9 * (size_t)f;
       o[5] = dop[f];
-      o[6] = dcol[3 * (size_t)f]; o[7] = dcol[3 * (size_t)f + 1]; o[8] = dcol[3 * (size_t)f + 2];
+    }
+    for (size_t i = 0; i < dcol.size() / 3; ++i) {
+      double* o = rec_grads + 9 * i;
+      o[6] = dcol[3 * i]; o[7] = dcol[3 * i + 1]; o[8] = dcol[3 * i + 2];
     }
   }
   return 0;
@@ -1144,9 +1330,12 @@ int gmr_oracle_backward(int V, const float* verts, int F, const int* faces, cons
 int gmr_oracle_jvp(int V, const float* verts, int F, const int* faces, const float* rgb, int color_mode,
                    const float* opacity, float opacity_scalar, int cov_mode, int C, const float* cam_f,
                    const int* cam_i, const double* bg, int tile, long long npix, const int* pix, const double* w,
-                   const double* dverts, const double* drgb, const double* dop, double* out, const double* wT) {
+                   const double* dverts, const double* drgb, const double* dop, double* out, const double* wT,
+                   int sh_degree) {
   Scene s;
-  build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile);
+  build_scene(s, V, verts, F, faces, rgb, color_mode, opacity, opacity_scalar, cov_mode, C, cam_f, cam_i, bg, tile,
+              sh_degree);
+  if (!check_sh(s)) return -4;
   if (!check_scene(s)) return -1;
   Direction dir;
   dir.dverts = dverts; dir.drgb = drgb; dir.dop = dop;

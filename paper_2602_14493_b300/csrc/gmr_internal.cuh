@@ -346,20 +346,12 @@ struct Workspace {
   // pairs
   int64_t cap_pairs = 0;
   // pair_key[0]: (depth bits << 32 | face) per pair in tile segments;
-  // pair_key[1]: per pair slot of the projection, (tile << 32 | rank of the
-  // pair in its tile); then scratch of the long-segment sort; then, from the
-  // forward compositing to the next forward, the contribution masks
-  // (pair_cmask)
+  // pair_key[1]: scratch of the long-segment sort, and before that, per pair
+  // slot of the projection, (tile << 32 | rank of the pair in its tile)
   unsigned long long* pair_key[2] = {nullptr, nullptr};
   // face ids in (tile, depth, face) order; before the sort, per pair slot of
   // the projection, the pair's record id
   uint32_t* pair_face = nullptr;
-  // Per sorted pair, the 8x4-pixel blocks of its tile in which at least one
-  // pixel composited the pair's Gaussian (bit b = block b, row-major), written
-  // by the forward compositing and read by the backward: 32 bits per pair in
-  // the memory of pair_key[1], which holds nothing else between the binning
-  // and the next forward.
-  uint32_t* pair_cmask() const { return reinterpret_cast<uint32_t*>(pair_key[1]); }
   // scratch for scans
   int64_t cap_scan = 0;
   uint32_t* scan_tmp = nullptr;     // block sums

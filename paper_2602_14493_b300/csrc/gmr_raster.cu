@@ -67,9 +67,7 @@ struct PixMap {
     return (ry * RH + k / RW) * NC + rx * RW + k % RW;
   }
   __device__ __forceinline__ static int block(int k) { return block_of(threadIdx.x >> 5, k); }
-  // block(k) - block(0), a compile-time constant: bit block(k) of a block
-  // mask is bit block(0) shifted left by this
-  static constexpr int boff(int k) { return (k / RW) * NC + k % RW; }
+
   __device__ __forceinline__ static uint32_t warp_bits() {
     uint32_t b = 0;
 #pragma unroll
@@ -146,8 +144,10 @@ __device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, flo
   return m;
 }
 
-// Forward staging: the block mask is the conservative bounding-box test
-// above. The record's w holds the skip threshold t2 = -log2(255 o).
+// Staging of one batch: records and colours of the listed Gaussians, the
+// mean relative to the anchor, and the block mask (the conservative
+// bounding-box test above). The record's w holds the skip threshold
+// t2 = -log2(255 o).
 template <int TS, int NT, int BATCH>
 __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
                                             int count, uint32_t rec_base, const float4* __restrict__ rec_u,
@@ -170,32 +170,6 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uin
       st.rid[i] = rid;
       st.face[i] = f;
     }
-  }
-}
-
-// Backward staging: the block mask is the forward's contribution mask (the
-// blocks in which some pixel composited the Gaussian), so entries that
-// contributed nowhere are neither loaded nor listed.
-template <int NT, int BATCH>
-__device__ __forceinline__ void stage_batch_bwd(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face,
-                                                const uint32_t* __restrict__ cmask, uint32_t lo, int count,
-                                                uint32_t rec_base, const float4* __restrict__ rec_u,
-                                                const float4* __restrict__ rec_q,
-                                                const float4* __restrict__ face_col, float ax, float ay) {
-  for (int i = threadIdx.x; i < count; i += NT) {
-    const uint32_t m = __ldg(cmask + lo + i);
-    st.mask[i] = m;
-    if (m == 0u) continue;
-    const uint32_t f = __ldg(pair_face + lo + i);
-    const uint32_t rid = rec_base + f;
-    const float4 u = __ldg(rec_u + rid);
-    const float4 q = __ldg(rec_q + rid);
-    const float4 col = __ldg(face_col + f);
-    st.g[i] = make_float4(__fadd_rn(__fsub_rn(u.x, ax), u.z), __fadd_rn(__fsub_rn(u.y, ay), u.w), q.x, q.y);
-    st.h[i] = make_float4(q.z, q.w, col.w, 0.0f);
-    st.col[i] = make_float4(col.x, col.y, col.z, 0.0f);
-    st.rid[i] = rid;
-    st.face[i] = f;
   }
 }
 
@@ -280,7 +254,6 @@ constexpr int kFwdPlain = 0, kFwdDebug = 1, kFwdLoss = 2;
 // Per-tile arguments of the compositing kernels.
 struct RasterArgs {
   const uint32_t* pair_face;
-  uint32_t* cmask;  // per sorted pair: contribution mask (forward writes, backward reads)
   const float4* rec_u;
   const float4* rec_q;
   const float4* face_col;
@@ -290,34 +263,23 @@ struct RasterArgs {
   const uint4* tile_desc;
   Counters* counters;
   uint32_t n_pos;   // compositing positions (tiles)
-  int persistent;   // 1: resident CTAs take positions from a cursor
 };
 
-// The compositing position of each pass of a CTA: its block index, or, in a
-// persistent grid, the next position of the cursor (one atomic per tile;
-// the barrier keeps a CTA's threads on one tile). Returns false when no
-// position is left.
-__device__ __forceinline__ bool next_position(bool persistent, uint32_t* cursor, uint32_t n_pos, int pass,
-                                              uint32_t& pos) {
-  if (!persistent) {
-    pos = blockIdx.x;
-    return pass == 0;
-  }
+// The next compositing position of a persistent grid's CTA: one atomic on
+// the cursor per tile, broadcast through shared memory (the first barrier
+// waits until every thread is done with the last tile and with s_pos).
+// Returns false when no position is left.
+__device__ __forceinline__ bool next_position(uint32_t* cursor, uint32_t n_pos, uint32_t& pos) {
   __shared__ uint32_t s_pos;
-  __syncthreads();  // every thread is done with the last tile (and with s_pos)
+  __syncthreads();
   if (threadIdx.x == 0) s_pos = atomicAdd(cursor, 1u);
   __syncthreads();
   pos = s_pos;
   return pos < n_pos;
 }
 
-// One tile of the forward at compositing position pos. Besides the image,
-// final T and last contributor of every pixel, it writes the contribution
-// mask of every list entry it reached: bit b set when some pixel of 8x4
-// block b composited the entry (a warp ORs its lanes' blocks with one
-// reduction and adds them to a shared word; the words of a batch are written
-// out once every warp is past that batch). Entries past the tile's stop are
-// never read by the backward, which ends at the last contributor.
+// One tile of the forward at compositing position pos: image, final T and
+// last contributor of every pixel.
 template <int TS, int NT, int BATCH, int MODE>
 __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, float* __restrict__ images,
                                          float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
@@ -326,7 +288,6 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, NW> st;
-  __shared__ uint32_t s_cm[BATCH];
   // the tile at this compositing position, its view and its pair range
   const uint4 desc = __ldg(a.tile_desc + pos);
   const int g = (int)desc.x;
@@ -347,7 +308,6 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
   uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
   bool done[PPT], inside[PPT];
   int px[PPT], py[PPT];
-  const uint32_t bb0 = 1u << PixMap<TS, NT>::block(0);  // block bit of pixel k: bb0 << boff(k)
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     int lx, ly;
@@ -376,22 +336,13 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
   const uint2 range = make_uint2(desc.z, desc.w);
   const int n = (int)(range.y - range.x);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
-  for (int i = threadIdx.x; i < BATCH; i += NT) s_cm[i] = 0u;
-  int prev_base = 0, prev_cnt = 0;
 
   for (int base = 0; base < n; base += BATCH) {
     bool tdone = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) tdone &= done[k];
     if (__syncthreads_and(tdone)) break;
-    // every warp is past the last batch: its masks go out, the words are reset
-    for (int i = threadIdx.x; i < prev_cnt; i += NT) {
-      a.cmask[range.x + prev_base + i] = s_cm[i];
-      s_cm[i] = 0u;
-    }
     int cnt = min(BATCH, n - base);
-    prev_base = base;
-    prev_cnt = cnt;
     stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.face_col, ax, ay,
                                tox, toy, MODE == kFwdDebug);
     __syncthreads();
@@ -419,8 +370,8 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
         con[k] = !done[k] && !(p2[k] < hh.y);
         anyc |= con[k];
       }
-      uint32_t lb = 0u;  // blocks of this lane's pixels that composite the entry
-      if (anyc) {
+      if (!anyc) continue;
+      {
         const float4 col = st.col[j];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -439,17 +390,12 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
           Cb[k] = __fmaf_rn(col.z, w, Cb[k]);
           T[k] = test;
           last[k] = (uint32_t)(base + j + 1);
-          lb |= bb0 << PixMap<TS, NT>::boff(k);
           ++ncontrib[k];
           if (MODE == kFwdDebug) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;  // ordered contributor list
         }
       }
-      const uint32_t wb = __reduce_or_sync(kFull, lb);
-      if (wb != 0u && lane == 0) atomicOr(&s_cm[j], wb);
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < prev_cnt; i += NT) a.cmask[range.x + prev_base + i] = s_cm[i];
   unsigned long long evals = 0, ncon = 0;
   float lsum = 0.0f;  // fused loss: FP32 over this thread's pixels
 #pragma unroll
@@ -496,14 +442,20 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
   }
 }
 
-template <int TS, int NT, int BATCH, int MODE>
+// PERSIST: a persistent grid of resident CTAs taking positions from the
+// cursor; otherwise one CTA per position (the default: measured faster).
+template <int TS, int NT, int BATCH, int MODE, bool PERSIST>
 __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value)
     k_raster_fwd(RasterArgs a, float* __restrict__ images, float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
                  float* __restrict__ t_out, uint32_t* __restrict__ nc_out, int64_t n_pix_total, FwdLoss fl) {
   pdl_enter();
-  uint32_t pos;
-  for (int pass = 0; next_position(a.persistent, &a.counters->raster_next_fwd, a.n_pos, pass, pos); ++pass)
-    fwd_tile<TS, NT, BATCH, MODE>(a, pos, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
+  if (!PERSIST) {
+    fwd_tile<TS, NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
+  } else {
+    uint32_t pos;
+    while (next_position(&a.counters->raster_next_fwd, a.n_pos, pos))
+      fwd_tile<TS, NT, BATCH, MODE>(a, pos, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
+  }
 }
 
 // Sum of n floats into *out, one block, in a fixed order, with double-float
@@ -598,13 +550,13 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
   const int ox = txi * TS, oy = tyi * TS;
   const int axi = ox & ~31, ayi = oy & ~31;
   const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
   const int lane = threadIdx.x & 31;
 
   // SG = (colour composited behind the current Gaussian, plus T_final bg) . g
   float pcx[PPT], pcy[PPT], T[PPT], SG[PPT], G0[PPT], G1[PPT], G2[PPT];
   uint32_t last[PPT];
   uint32_t tmax = 0;
-  const uint32_t bb0 = 1u << PixMap<TS, NT>::block(0);  // block bit of pixel k: bb0 << boff(k)
   float lsum = 0.0f;  // LOSS: FP32 sum of this thread's squared errors
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
@@ -680,15 +632,14 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
   for (int end = end_all; end > 0; end -= BATCH) {
     const int start = max(0, end - BATCH);
     __syncthreads();
-    stage_batch_bwd<NT, BATCH>(st, a.pair_face, a.cmask, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
-                               a.face_col, ax, ay);
+    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
+                               a.face_col, ax, ay, tox, toy, true);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, end - start, start, (int)wmax, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
     for (int jj = nl - 1; jj >= 0; --jj) {
       const int j = st.list[warp][jj];
       const int pos_j = start + j;
-      const uint32_t mj = st.mask[j];
       const float4 hh = st.h[j];
       const float4 gg = st.g[j];
       float p2[PPT], dxs[PPT], dys[PPT];
@@ -696,14 +647,8 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        // a block in which no pixel composited the entry is skipped whole
-        // (the test is uniform over the warp)
-        con[k] = false;
-        p2[k] = dxs[k] = dys[k] = 0.0f;
-        if ((mj >> PixMap<TS, NT>::boff(k)) & bb0) {
-          p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
-          con[k] = ((uint32_t)pos_j < last[k]) && !(p2[k] < hh.y);
-        }
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
+        con[k] = ((uint32_t)pos_j < last[k]) && !(p2[k] < hh.y);
         any |= con[k];
       }
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -770,15 +715,19 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
   if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
 }
 
-template <int TS, int NT, int BATCH, bool LOSS>
+template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST>
 __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
     k_raster_bwd(RasterArgs a, const float* __restrict__ dL_dimg, const float* __restrict__ dL_dT,
                  const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
                  float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz) {
   pdl_enter();
-  uint32_t pos;
-  for (int pass = 0; next_position(a.persistent, &a.counters->raster_next_bwd, a.n_pos, pass, pos); ++pass)
-    bwd_tile<TS, NT, BATCH, LOSS>(a, pos, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+  if (!PERSIST) {
+    bwd_tile<TS, NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+  } else {
+    uint32_t pos;
+    while (next_position(&a.counters->raster_next_bwd, a.n_pos, pos))
+      bwd_tile<TS, NT, BATCH, LOSS>(a, pos, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+  }
 #pragma unroll
   for (int z = 0; z < 2; ++z)
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < bz.n[z]; i += (int64_t)gridDim.x * NT)
@@ -912,10 +861,9 @@ int resident_grid(K kern, int threads) {
 }
 
 RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t F,
-                       const float* bg, int64_t n_tiles, bool persistent) {
+                       const float* bg, int64_t n_tiles) {
   RasterArgs a;
   a.pair_face = pair_face;
-  a.cmask = ws.pair_cmask();
   a.rec_u = ws.rec_u;
   a.rec_q = ws.rec_q;
   a.face_col = ws.face_col;
@@ -927,7 +875,6 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
   a.tile_desc = ws.tile_desc;
   a.counters = ws.counters;
   a.n_pos = (uint32_t)n_tiles;
-  a.persistent = persistent ? 1 : 0;
   return a;
 }
 
@@ -935,13 +882,16 @@ template <int TS, int NT, int BATCH>
 cudaError_t fwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, float* images, float* t_out,
                        uint32_t* nc_out, const FwdLoss& fl, cudaStream_t s) {
-  auto kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss>
-              : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug>
-                        : k_raster_fwd<TS, NT, BATCH, kFwdPlain>;
+  auto kern = persistent ? (fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, true>
+                           : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, true>
+                                     : k_raster_fwd<TS, NT, BATCH, kFwdPlain, true>)
+                        : (fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false>
+                           : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false>
+                                     : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false>);
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
   cudaError_t e = launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
-                                 raster_args(ws, pair_face, views, F, bg, n_tiles, persistent), images, ws.pix_T,
+                                 raster_args(ws, pair_face, views, F, bg, n_tiles), images, ws.pix_T,
                                  ws.pix_last, t_out, nc_out, ws.cap_pixels, fl);
   if (e == cudaSuccess && fl.target)
     e = launch_chained(k_sum_partials, true, dim3(1), dim3(1024), 0, s, (const float*)fl.part, n_tiles * (NT / 32), 1.0,
@@ -953,11 +903,12 @@ template <int TS, int NT, int BATCH>
 cudaError_t bwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
                        const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
-  auto kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true> : k_raster_bwd<TS, NT, BATCH, false>;
+  auto kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true> : k_raster_bwd<TS, NT, BATCH, false, true>)
+                        : (bl.img ? k_raster_bwd<TS, NT, BATCH, true, false> : k_raster_bwd<TS, NT, BATCH, false, false>);
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
   return launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
-                        raster_args(ws, pair_face, views, F, bg, n_tiles, persistent), dL, dLdT,
+                        raster_args(ws, pair_face, views, F, bg, n_tiles), dL, dLdT,
                         (const float*)ws.pix_T, (const uint32_t*)ws.pix_last, ws.rec_grad, ws.face_grad, bl, bz);
 }
 

@@ -10,7 +10,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "gmr_oracle.cpp")
-PINS = ["tests/test_oracle_convert.py", "tests/test_oracle_render.py", "tests/test_oracle_grad.py"]
+PINS = ["tests/test_oracle_convert.py", "tests/test_oracle_render.py", "tests/test_oracle_grad.py",
+        "tests/test_oracle_sh.py"]
 
 MUTATIONS = {
     "jacobian_z_sign": ("dt[2] += dJ[0] * (-fx / (z * z));", "dt[2] += dJ[0] * (fx / (z * z));"),
@@ -30,6 +31,9 @@ MUTATIONS = {
     "centroid_component": ("V3<T> m = vi + mux * xa + muy * ya;", "V3<T> m = vi + mux * xa + mux * ya;"),
     "normal_cross_order": ("dya = dya + cross(dnv, g.xa);", "dya = dya + cross(g.xa, dnv);"),
     "rect_too_small": ("rx = rx + 0.25f;", "rx = rx - 1.5f;"),
+    "sh_basis_component": ("Y[1] = T(kSh.c1) * y;", "Y[1] = T(kSh.c1) * x;"),
+    "sh_tangent_projection": ("(1.0 / rn) * (dd - dot(d, dd) * d)", "(1.0 / rn) * (dd + dot(d, dd) * d)"),
+    "sh_grad_factor": ("G[6][2] = kSh.c2b * 6.0 * z;", "G[6][2] = kSh.c2b * 3.0 * z;"),
     "depth_order": ("return bins[(size_t)view * F + i].depth_bits < bins[(size_t)view * F + j].depth_bits;",
                     "return bins[(size_t)view * F + i].depth_bits > bins[(size_t)view * F + j].depth_bits;"),
 }
