@@ -55,9 +55,10 @@ FLOPS_EVAL = 13
 FLOPS_FWD_CONTRIB = 10
 FLOPS_BWD_CONTRIB = 59
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that
-# one ncu capture measured for the dominant kernel, per workload; an entry is
-# removed when the kernel changes after its capture.
-NCU_TRAFFIC = {}
+# one ncu capture measured for the dominant kernel, per workload and launch
+# shape (tile, backward threads, batch, persistent); an entry is removed when
+# the kernel changes after its capture.
+NCU_TRAFFIC = {("raster_bwd", "icosphere6_noise_64xuneven", (16, 128, 256, 0)): 1950448128}
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -201,16 +202,19 @@ def cpu_baseline(scene, target_seconds, gpu_check=None):
 
     cores = oracle.set_threads(0)
     # calibration on all cores: one pixel (the per-call conversion,
-    # projection and depth sort of every record dominate) and 16 per core
+    # projection and depth sort of every record dominate) and 64 per core
     t_a, n_a = oracle_sample_time(scene, 1)
-    t_b, n_b = oracle_sample_time(scene, 16 * cores)
+    t_b, n_b = oracle_sample_time(scene, 64 * cores)
     per_px = max((t_b - t_a) / max(n_b - n_a, 1), 1e-7)
     fixed = max(t_a - n_a * per_px, 0.0)
     n = int(max(64, min(400000, (target_seconds - fixed) / per_px)))
     t, n, kept = oracle_sample_time(scene, n, seed=1, keep=True)
-    # one thread, on 1/cores of that many pixels
+    # one thread: its per-pixel and fixed costs are at most `cores` times the
+    # all-core ones (the parallel loops scale at best linearly), so this many
+    # pixels take at most about target_seconds
+    per_px = max((t - fixed) / n, per_px)
     oracle.set_threads(1)
-    n1_req = max(8, n // cores)
+    n1_req = int(max(8, min(n, (target_seconds - fixed * cores) / (per_px * cores))))
     t1, n1 = oracle_sample_time(scene, n1_req, seed=2)
     out = {"value": n / t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
@@ -593,7 +597,8 @@ def run_gmr(args, ws, rank, local):
         log(f"note: the largest stage is {max(kern, key=kern.get)}, not {DOMINANT}")
     if stage_acc.get(DOMINANT):
         # duration of the dominant kernel inside the timed steps themselves
-        roof = roofline_for(DOMINANT, statistics.mean(stage_acc[DOMINANT]), stats, scene, peaks, peak_kind, args)
+        roof = roofline_for(DOMINANT, statistics.mean(stage_acc[DOMINANT]), stats, scene, peaks, peak_kind, args,
+                            shape=(tile, threads_bwd, batch, int(persistent)))
     else:
         roof = None
         log("no stage times were recorded")
@@ -648,15 +653,17 @@ def run_gmr(args, ws, rank, local):
 DOMINANT = "raster_bwd"  # the step's largest kernel (compositing backward)
 
 
-def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
-    """Roofline entry of the dominant kernel from its live event time."""
+def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args, shape=None):
+    """Roofline entry of the dominant kernel from its live event time
+    (shape: the launch shape (tile, backward threads, batch, persistent),
+    which selects the recorded DRAM traffic)."""
     E_f, E_b, K = stats["evals_fwd"], stats["evals_bwd"], stats["contribs"]
     if stage in ("raster_fwd", "raster_bwd"):
         flops = (FLOPS_EVAL * E_f + FLOPS_FWD_CONTRIB * K) if stage == "raster_fwd" else \
                 (FLOPS_EVAL * E_b + FLOPS_BWD_CONTRIB * K)
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((stage, args.workload)),
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((stage, args.workload, shape)),
                 "peak_source": "FP32 CUDA-core peak from unit counts and max clock (148 SM x 128 x 2 x 2.032 GHz)",
                 "ms": ms}
     # memory-type stages: algorithmic bytes per record, pair, tile and face
@@ -669,7 +676,7 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args):
     ach = byts / (ms / 1e3) / 1e9
     pk = peaks["hbm_gbs"]
     return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-            "traffic": NCU_TRAFFIC.get((stage, args.workload)), "peak_source": peak_kind, "ms": ms}
+            "traffic": NCU_TRAFFIC.get((stage, args.workload, shape)), "peak_source": peak_kind, "ms": ms}
 
 
 def main():

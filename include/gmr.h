@@ -70,8 +70,15 @@ typedef enum {
 
 /* Sec. 2.2, colour assignment. */
 typedef enum {
-  GMR_COLOR_PER_FACE = 0,  /* rgb is F x 3 */
-  GMR_COLOR_PER_VERTEX = 1 /* rgb is V x 3; face colour = mean of its 3 vertices (Eq. 16) */
+  GMR_COLOR_PER_FACE = 0,   /* rgb is F x 3 */
+  GMR_COLOR_PER_VERTEX = 1, /* rgb is V x 3; face colour = mean of its 3 vertices (Eq. 16) */
+  GMR_COLOR_SH = 2          /* view-dependent colour, the extension the colour assignment of
+                               Sec. 2.2 names: rgb is F x K x 3 (K = (L + 1)^2, L =
+                               gmr_config.sh_degree <= 3) coefficients of the real spherical
+                               harmonics Y_k (no Condon-Shortley phase, order (l, m) = (0, 0),
+                               (1, -1), (1, 0), (1, 1), (2, -2), ...); the colour of a facet in a
+                               view is max(0, sum_k a_k Y_k(d) + 1/2) per channel, d the unit
+                               vector from the camera centre to the facet's centroid */
 } gmr_color_mode;
 
 /* Pinhole camera (76 bytes, no padding). World-to-camera rotation R
@@ -104,6 +111,7 @@ typedef struct {
   int32_t flags;      /* GMR_FLAG_* */
   uint32_t profile_stages; /* under GMR_FLAG_PROFILE: bit s set = time gmr_stage s;
                               0 = time every stage */
+  int32_t sh_degree;  /* GMR_COLOR_SH: degree L of the spherical harmonics, 0..3 */
 } gmr_config;
 
 /* With this flag the forward reads the pair count back to the host once
@@ -209,7 +217,8 @@ GMR_API gmr_status gmr_set_workspace_limit(gmr_ctx* ctx, int64_t max_bytes);
  * Outputs (any may be NULL): means F x 3 (centroid, Eq. 3-4), cov F x 6
  * (xx, xy, xz, yy, yz, zz of Eq. 13 or Eq. 15 per cov_mode), face_rgb F x 3
  * (Eq. 16), face_opacity F. Faces with an index outside [0, V) set
- * GMR_DEV_BAD_FACE_INDEX and get zero outputs. */
+ * GMR_DEV_BAD_FACE_INDEX and get zero outputs. With GMR_COLOR_SH the colour
+ * depends on the view: face_rgb must then be NULL (GMR_ERR_INVALID_ARG). */
 GMR_API gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t* faces, int32_t F,
                        const float* rgb, const float* opacity, float* means, float* cov, float* face_rgb,
                        float* face_opacity, gmr_stream stream);
@@ -248,7 +257,8 @@ GMR_API gmr_status gmr_render_fwd_l2(gmr_ctx* ctx, const float* verts, int32_t V
  * contributor; no per-pixel lists are kept.
  *  dL_dimages    packed, same layout as images.
  *  dL_dverts     V x 3 (may be NULL).
- *  dL_drgb       shape of rgb (may be NULL).
+ *  dL_drgb       shape of rgb (may be NULL; with GMR_COLOR_SH the
+ *                coefficients' gradient, F x K x 3).
  *  dL_dopacity   F (may be NULL; ignored when the forward had opacity NULL).
  *  accumulate    0: outputs are overwritten; 1: gradients are added to them.
  */

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "GMR_OK", 1: "GMR_ERR_INVALID_ARG", 2: "GMR_ERR_CUDA", 3: "GM
 GMR_DEV_BAD_FACE_INDEX = 1
 GMR_DEV_PAIR_OVERFLOW = 2
 GMR_COV_AREA, GMR_COV_EMBED_RAW = 0, 1
-GMR_COLOR_PER_FACE, GMR_COLOR_PER_VERTEX = 0, 1
+GMR_COLOR_PER_FACE, GMR_COLOR_PER_VERTEX, GMR_COLOR_SH = 0, 1, 2
 GMR_FLAG_SYNC_CHECK = 1
 GMR_FLAG_PROFILE = 2
 GMR_FLAG_DEBUG_COUNTS = 4
@@ -43,7 +43,7 @@ class GmrConfig(ctypes.Structure):
                 ("batch", ctypes.c_int32),
                 ("cov_mode", ctypes.c_int32),
                 ("color_mode", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32),
-                ("profile_stages", ctypes.c_uint32)]
+                ("profile_stages", ctypes.c_uint32), ("sh_degree", ctypes.c_int32)]
 
 
 class GmrCamera(ctypes.Structure):

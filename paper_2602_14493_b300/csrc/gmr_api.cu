@@ -118,8 +118,12 @@ bool valid_config(const gmr_config* c, std::string* why) {
   }
   if (c->batch != 64 && c->batch != 128 && c->batch != 256) { *why = "batch must be 64, 128 or 256"; return false; }
   if (c->cov_mode != GMR_COV_AREA && c->cov_mode != GMR_COV_EMBED_RAW) { *why = "bad cov_mode"; return false; }
-  if (c->color_mode != GMR_COLOR_PER_FACE && c->color_mode != GMR_COLOR_PER_VERTEX) {
+  if (c->color_mode != GMR_COLOR_PER_FACE && c->color_mode != GMR_COLOR_PER_VERTEX && c->color_mode != GMR_COLOR_SH) {
     *why = "bad color_mode";
+    return false;
+  }
+  if (c->color_mode == GMR_COLOR_SH && (c->sh_degree < 0 || c->sh_degree > 3)) {
+    *why = "sh_degree must be 0..3";
     return false;
   }
   for (int k = 0; k < 3; ++k)
@@ -188,6 +192,19 @@ gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
   if ((s = realloc_exact(ctx, &w.rec_key, cap, "rec_key")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_grad, 2 * cap, "rec_grad")) != GMR_OK) return s;
   w.cap_records = cap;
+  return GMR_OK;
+}
+
+// Per-record colours and colour gradient sums of the view-dependent colour.
+gmr_status ensure_sh(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_sh_records) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "colour workspace must grow during stream capture; call gmr_reserve");
+  const int64_t cap = n + n / 4 + 1024;
+  gmr_status s;
+  if ((s = realloc_exact(ctx, &w.rec_col, cap, "rec_col")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_cgrad, cap, "rec_cgrad")) != GMR_OK) return s;
+  w.cap_sh_records = cap;
   return GMR_OK;
 }
 
@@ -346,6 +363,8 @@ void build_views(gmr_ctx* ctx, const gmr_camera* cams, int32_t C, int64_t* n_til
     std::memcpy(v.R, cams[c].R, sizeof(v.R));
     std::memcpy(v.t, cams[c].t, sizeof(v.t));
     v.fx = cams[c].fx; v.fy = cams[c].fy; v.cx = cams[c].cx; v.cy = cams[c].cy; v.znear = cams[c].znear;
+    for (int q = 0; q < 3; ++q)  // camera centre -R^T t
+      v.o[q] = (float)-((double)v.R[q] * v.t[0] + (double)v.R[3 + q] * v.t[1] + (double)v.R[6 + q] * v.t[2]);
     v.W = cams[c].width; v.H = cams[c].height;
     v.tiles_x = (v.W + ts - 1) / ts;
     v.tiles_y = (v.H + ts - 1) / ts;
@@ -415,7 +434,8 @@ gmr_status gmr_create(const gmr_config* cfg, gmr_ctx** out) {
 gmr_status gmr_destroy(gmr_ctx* ctx) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   Workspace& w = ctx->ws;
-  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.face_col,
+  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.rec_col, w.rec_cgrad,
+                  w.face_col,
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
                   w.tile_order, w.tile_desc,
                   w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch};
@@ -476,6 +496,8 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   } inval{ctx, ctx->dev_bytes};
   gmr_status s;
   if ((s = ensure_records(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK) return s;
+  if (ctx->cfg.color_mode == GMR_COLOR_SH && (s = ensure_sh(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK)
+    return s;
   if ((s = ensure_faces(ctx, max_faces, false)) != GMR_OK) return s;
   if ((s = ensure_pixels(ctx, max_pixels, false)) != GMR_OK) return s;
   // tiles: at most one per 16x16 block plus one ragged tile per row/column and view
@@ -493,6 +515,8 @@ gmr_status gmr_convert(gmr_ctx* ctx, const float* verts, int32_t V, const int32_
   if (V < 0 || F < 0) return fail(ctx, GMR_ERR_INVALID_ARG, "negative size");
   if (F > 0 && (!verts || !faces || V == 0)) return fail(ctx, GMR_ERR_INVALID_ARG, "null verts/faces");
   if (face_rgb && !rgb && F > 0) return fail(ctx, GMR_ERR_INVALID_ARG, "face_rgb requested without rgb");
+  if (face_rgb && ctx->cfg.color_mode == GMR_COLOR_SH)
+    return fail(ctx, GMR_ERR_INVALID_ARG, "face_rgb: with GMR_COLOR_SH the colour depends on the view");
   cudaStream_t s = (cudaStream_t)stream;
   GMR_CUDA(ctx, gmr::launch_convert(verts, V, faces, F, rgb, opacity, ctx->cfg.cov_mode, ctx->cfg.color_mode, means,
                                     cov, face_rgb, face_opacity, ctx->ws.counters, s, &ctx->launches));
@@ -537,6 +561,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   if ((st = ensure_faces(ctx, F, capturing)) != GMR_OK) return st;
   if ((st = ensure_pixels(ctx, n_pixels, capturing)) != GMR_OK) return st;
   if ((st = ensure_tiles(ctx, n_tiles, capturing)) != GMR_OK) return st;
+  if (cfg.color_mode == GMR_COLOR_SH && (st = ensure_sh(ctx, n_rec, capturing)) != GMR_OK) return st;
   if (fl.target) {
     // one float per forward warp after slot 0 (gmr_l2_loss's ticket counter)
     const int64_t n_warp_sums = n_tiles * (ctx->cfg.threads / 32);
@@ -562,7 +587,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
     GMR_CUDA(ctx, cudaMemsetAsync(w.counters, 0, gmr::kStepCountersBytes, s));
     {
       StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
-      GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, w.views, C, cfg.tile,
+      GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, cfg.sh_degree, w.views, C,
+                                        cfg.tile,
                                         cfg.cov_mode, w, s, &ctx->launches));
     }
     {
@@ -589,7 +615,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
     uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
-    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0, w,
+    GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
+                                         cfg.color_mode == GMR_COLOR_SH, w,
                                          w.pair_face, w.views, C, F, n_tiles, cfg.bg, images, t_final, nc, fl, s,
                                          &ctx->launches));
   }
@@ -684,7 +711,11 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   ctx->grads_zero = false;
   if (!zeroed) {
     if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_grad, 0, sizeof(float4) * 2 * (size_t)n_rec, s));
-    if (F > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
+    if (cfg.color_mode == GMR_COLOR_SH) {
+      if (n_rec > 0) GMR_CUDA(ctx, cudaMemsetAsync(w.rec_cgrad, 0, sizeof(float4) * (size_t)n_rec, s));
+    } else if (F > 0) {
+      GMR_CUDA(ctx, cudaMemsetAsync(w.face_grad, 0, sizeof(float4) * (size_t)F, s));
+    }
     GMR_CUDA(ctx, cudaMemsetAsync(&w.counters->evals_bwd, 0, gmr::kBwdCountersBytes, s));
   }
   // outputs the projection backward accumulates into: zeroed by the
@@ -703,6 +734,7 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
+                                         cfg.color_mode == GMR_COLOR_SH,
                                          w, w.pair_face, w.views, C, F, ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal,
                                          bl, bz, s, &ctx->launches));
   }
@@ -718,6 +750,7 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   {
     StageTimer t(ctx, GMR_STAGE_PROJECT_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_project_bwd(ctx->verts, V, ctx->faces, F, w.views, C, cfg.cov_mode, cfg.color_mode,
+                                          cfg.sh_degree, ctx->rgb,
                                           ctx->opacity, w, dL_dverts, dL_drgb, dL_dopacity, accumulate, s,
                                           &ctx->launches));
   }

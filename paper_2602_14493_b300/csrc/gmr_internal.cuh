@@ -82,6 +82,7 @@ struct ViewInfo {
   float R[9];
   float t[3];
   float fx, fy, cx, cy, znear;
+  float o[3];  // camera centre in world coordinates, -R^T t
   int32_t W, H, tiles_x, tiles_y;
   int32_t tile_base;  // first global tile id of this view
   int64_t pix_base;   // first packed pixel of this view
@@ -314,6 +315,75 @@ __device__ __forceinline__ float gauss_alpha(float p2, float o, float& graw) {
 // log2(255)
 constexpr float kLog2_255 = 7.99435343685886f;
 
+// ---------------------------------------------------------------- view-dependent colour
+// Real spherical harmonics (no Condon-Shortley phase) of degree <= L at the
+// unit vector (x, y, z), ordered (l, m) = (0, 0), (1, -1), (1, 0), (1, 1),
+// (2, -2), ..., (3, 3), as polynomials in x, y, z; the FP32 constants are the
+// normalisations written next to them. The colour of a facet seen along d is
+// max(0, sum_k a_k Y_k(d) + 1/2) per channel (the 3DGS offset and clamp).
+constexpr int kShMaxCoeffs = 16;
+namespace sh {
+constexpr float c0 = 0.282094791773878f;   // (1/2) sqrt(1/pi)
+constexpr float c1 = 0.488602511902920f;   // sqrt(3/(4 pi))
+constexpr float c2a = 1.092548430592079f;  // (1/2) sqrt(15/pi): xy, yz, xz
+constexpr float c2b = 0.315391565252520f;  // (1/4) sqrt(5/pi): 3 z^2 - 1
+constexpr float c2c = 0.546274215296040f;  // (1/4) sqrt(15/pi): x^2 - y^2
+constexpr float c3a = 0.590043589926644f;  // (1/4) sqrt(35/(2 pi)): y (3x^2 - y^2), x (x^2 - 3y^2)
+constexpr float c3b = 2.890611442640554f;  // (1/2) sqrt(105/pi): xyz
+constexpr float c3c = 0.457045799464466f;  // (1/4) sqrt(21/(2 pi)): y (5z^2 - 1), x (5z^2 - 1)
+constexpr float c3d = 0.373176332590115f;  // (1/4) sqrt(7/pi): z (5z^2 - 3)
+constexpr float c3e = 1.445305721320277f;  // (1/4) sqrt(105/pi): z (x^2 - y^2)
+}  // namespace sh
+
+template <int L>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
+  Y[0] = sh::c0;
+  if (L < 1) return;
+  Y[1] = sh::c1 * y;
+  Y[2] = sh::c1 * z;
+  Y[3] = sh::c1 * x;
+  if (L < 2) return;
+  Y[4] = sh::c2a * x * y;
+  Y[5] = sh::c2a * y * z;
+  Y[6] = sh::c2b * (3.0f * z * z - 1.0f);
+  Y[7] = sh::c2a * x * z;
+  Y[8] = sh::c2c * (x * x - y * y);
+  if (L < 3) return;
+  Y[9] = sh::c3a * y * (3.0f * x * x - y * y);
+  Y[10] = sh::c3b * x * y * z;
+  Y[11] = sh::c3c * y * (5.0f * z * z - 1.0f);
+  Y[12] = sh::c3d * z * (5.0f * z * z - 3.0f);
+  Y[13] = sh::c3c * x * (5.0f * z * z - 1.0f);
+  Y[14] = sh::c3e * z * (x * x - y * y);
+  Y[15] = sh::c3a * x * (x * x - 3.0f * y * y);
+}
+
+// sum_k s_k grad Y_k at (x, y, z): the gradient of the polynomials above
+// (off the sphere as written; callers project onto the tangent plane).
+template <int L>
+__device__ __forceinline__ float3 sh_grad_dot(float x, float y, float z, const float* s) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (L >= 1) {
+    gy += sh::c1 * s[1];
+    gz += sh::c1 * s[2];
+    gx += sh::c1 * s[3];
+  }
+  if (L >= 2) {
+    gx += sh::c2a * (y * s[4] + z * s[7]) + 2.0f * sh::c2c * x * s[8];
+    gy += sh::c2a * (x * s[4] + z * s[5]) - 2.0f * sh::c2c * y * s[8];
+    gz += sh::c2a * (y * s[5] + x * s[7]) + 6.0f * sh::c2b * z * s[6];
+  }
+  if (L >= 3) {
+    gx += sh::c3a * (6.0f * x * y * s[9] + (3.0f * x * x - 3.0f * y * y) * s[15]) + sh::c3b * y * z * s[10] +
+          sh::c3c * (5.0f * z * z - 1.0f) * s[13] + 2.0f * sh::c3e * x * z * s[14];
+    gy += sh::c3a * ((3.0f * x * x - 3.0f * y * y) * s[9] - 6.0f * x * y * s[15]) + sh::c3b * x * z * s[10] +
+          sh::c3c * (5.0f * z * z - 1.0f) * s[11] - 2.0f * sh::c3e * y * z * s[14];
+    gz += sh::c3b * x * y * s[10] + 10.0f * sh::c3c * z * (y * s[11] + x * s[13]) +
+          sh::c3d * (15.0f * z * z - 3.0f) * s[12] + sh::c3e * (x * x - y * y) * s[14];
+  }
+  return make_float3(gx, gy, gz);
+}
+
 // ---------------------------------------------------------------- workspace
 struct Workspace {
   // records: one per (view, face)
@@ -326,6 +396,11 @@ struct Workspace {
   // 2 float4 per record: (sum q dx, sum q dy, sum q dx^2, sum q dx dy),
   // (sum q dy^2, 0, 0, 0) with q = alpha dL/dalpha over the record's pixels
   float4* rec_grad = nullptr;
+  // view-dependent colour (GMR_COLOR_SH), one per record: colour and
+  // opacity (r, g, b, o), and its gradient sums (dr, dg, db, sum dq)
+  int64_t cap_sh_records = 0;
+  float4* rec_col = nullptr;
+  float4* rec_cgrad = nullptr;
   // faces
   int64_t cap_faces = 0;
   float4* face_col = nullptr;    // (r, g, b, o)
@@ -380,13 +455,15 @@ int64_t scan_block_sums_needed(int64_t n);
 // per-face colour/opacity and counts the pairs of every tile.
 // Projection (S1-S2); it also zeroes the record and face gradient sums
 // (ws.rec_grad for all C x F records, ws.face_grad for all F faces).
+// With color_mode GMR_COLOR_SH (degree sh_degree) it writes ws.rec_col and
+// zeroes ws.rec_cgrad for every record instead of ws.face_col / face_grad.
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
-                           const float* opacity, int color_mode, const ViewInfo* views, int32_t C, int tile,
-                           int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);
+                           const float* opacity, int color_mode, int sh_degree, const ViewInfo* views, int32_t C,
+                           int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);
 cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
-                               const ViewInfo* views, int32_t C, int cov_mode, int color_mode, const float* opacity,
-                               const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
-                               cudaStream_t s, int64_t* launches);
+                               const ViewInfo* views, int32_t C, int cov_mode, int color_mode, int sh_degree,
+                               const float* rgb, const float* opacity, const Workspace& ws, float* dverts,
+                               float* drgb, float* dop, int accumulate, cudaStream_t s, int64_t* launches);
 cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int cov_mode, int color_mode, float* means, float* cov,
                            float* face_rgb, float* face_o, Counters* counters, cudaStream_t s, int64_t* launches);
@@ -415,7 +492,11 @@ struct FwdLoss {
 // persistent: a grid of resident CTAs taking compositing positions from a
 // cursor (Counters::raster_next_fwd / _bwd, zero at launch) instead of one
 // CTA per tile.
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+// Both compositing kernels read the colour of a record from ws.rec_col when
+// col_by_record (GMR_COLOR_SH), else from ws.face_col by face; the backward
+// adds colour gradients to ws.rec_cgrad or ws.face_grad likewise.
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, bool col_by_record,
+                              const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
                               uint32_t* ncontrib_out, const FwdLoss& fl, cudaStream_t s, int64_t* launches);
@@ -437,7 +518,8 @@ struct BwdZero {
   float* p[2] = {nullptr, nullptr};
   int64_t n[2] = {0, 0};
 };
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, bool col_by_record,
+                              const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
                               const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches);

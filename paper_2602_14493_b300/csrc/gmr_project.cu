@@ -201,9 +201,44 @@ __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, int lane) {
   return v;
 }
 
+// View-dependent colour of the facet with vertices a, b, c in view v
+// (GMR_COLOR_SH, degree L): max(0, sum_k a_k Y_k(d) + 1/2), d the unit vector
+// from the camera centre to the centroid; coef holds the facet's K x 3
+// coefficients.
+template <int L>
+__device__ __forceinline__ float3 sh_colour(const float* __restrict__ coef, float3 a, float3 b, float3 c,
+                                            const ViewInfo& v) {
+  constexpr int K = (L + 1) * (L + 1);
+  const float wx = (a.x + b.x + c.x) * (1.0f / 3.0f) - v.o[0];
+  const float wy = (a.y + b.y + c.y) * (1.0f / 3.0f) - v.o[1];
+  const float wz = (a.z + b.z + c.z) * (1.0f / 3.0f) - v.o[2];
+  const float rinv = 1.0f / sqrtf(wx * wx + wy * wy + wz * wz);
+  float Y[K];
+  sh_eval<L>(wx * rinv, wy * rinv, wz * rinv, Y);
+  float r = 0.5f, g = 0.5f, bl = 0.5f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    r += __ldg(coef + 3 * k) * Y[k];
+    g += __ldg(coef + 3 * k + 1) * Y[k];
+    bl += __ldg(coef + 3 * k + 2) * Y[k];
+  }
+  return make_float3(fmaxf(r, 0.0f), fmaxf(g, 0.0f), fmaxf(bl, 0.0f));
+}
+
+__device__ __forceinline__ float3 sh_colour_any(int L, const float* __restrict__ coef, float3 a, float3 b, float3 c,
+                                                const ViewInfo& v) {
+  switch (L) {
+    case 0: return sh_colour<0>(coef, a, b, c, v);
+    case 1: return sh_colour<1>(coef, a, b, c, v);
+    case 2: return sh_colour<2>(coef, a, b, c, v);
+    default: return sh_colour<3>(coef, a, b, c, v);
+  }
+}
+
 __global__ void __launch_bounds__(kProjThreads) k_project(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F,
-    const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode,
+    const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode, int sh_degree,
+    float4* __restrict__ rec_col, float4* __restrict__ rec_cgrad,
     const ViewInfo* __restrict__ views, int tile, float inv_tile, int cov_mode, float4* __restrict__ rec_u,
     float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
@@ -221,13 +256,15 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   const uint32_t rid = (uint32_t)c * (uint32_t)F + (uint32_t)f;
   int i0 = 0, i1 = 0, i2 = 0;
   const bool ok = live && load_face(faces, f, V, i0, i1, i2);
+  const bool sh_col = color_mode == GMR_COLOR_SH;
   if (live) {  // the backward's gradient sums of every record and face start at zero
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     rec_grad[2 * (size_t)rid] = z;
     rec_grad[2 * (size_t)rid + 1] = z;
-    if (c == 0) face_grad[f] = z;
+    if (sh_col) rec_cgrad[rid] = z;
+    else if (c == 0) face_grad[f] = z;
   }
-  if (live && c == 0) {
+  if (live && c == 0 && !sh_col) {
     float r = 0.f, g = 0.f, b = 0.f;
     if (color_mode == GMR_COLOR_PER_FACE) {
       r = __ldg(rgb + 3 * f); g = __ldg(rgb + 3 * f + 1); b = __ldg(rgb + 3 * f + 2);
@@ -339,6 +376,10 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   // log2 G < t2; +inf for o = 0)
   const float o = fminf(fmaxf(opacity ? __ldg(opacity + f) : 1.0f, 0.0f), 1.0f);
   rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, -(kLog2_255 + log2f(o)));
+  if (sh_col) {
+    const float3 col = sh_colour_any(sh_degree, rgb + (size_t)f * 3 * (sh_degree + 1) * (sh_degree + 1), a, b, cc, sv);
+    rec_col[rid] = make_float4(col.x, col.y, col.z, o);
+  }
 }
 
 // Backward of conversion + projection. A face's gradient sums over its
@@ -440,13 +481,59 @@ __device__ __forceinline__ float group_sum(float x) {
 // memory.
 constexpr int kProjBwdThreads = 64;  // swept 64, 128, 256: 64 is best (13% faster than 128 on the ring workload)
 
-template <int G>
+// Colour chain of one record (GMR_COLOR_SH, degree L): colour = max(0, raw),
+// raw = sum_k a_k Y_k(d) + 1/2 per channel, d = w / |w|, w = centroid - o.
+// Adds g_ch Y_k to dcoef[k][ch] for the unclamped channels, and the
+// direction's share (dL/dd projected on the tangent plane, over |w|) to
+// dL/dmu.
+template <int L>
+__device__ __forceinline__ void sh_colour_bwd(const float* __restrict__ coef, const FaceGeom& g, const ViewInfo& v,
+                                              float3 gc, float* dcoef, float3& dmu) {
+  constexpr int K = (L + 1) * (L + 1);
+  const float wx = g.mx - v.o[0], wy = g.my - v.o[1], wz = g.mz - v.o[2];
+  const float rinv = 1.0f / sqrtf(wx * wx + wy * wy + wz * wz);
+  const float dx = wx * rinv, dy = wy * rinv, dz = wz * rinv;
+  float Y[K];
+  sh_eval<L>(dx, dy, dz, Y);
+  float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) raw[ch] += __ldg(coef + 3 * k + ch) * Y[k];
+  const float gch[3] = {raw[0] > 0.0f ? gc.x : 0.0f, raw[1] > 0.0f ? gc.y : 0.0f, raw[2] > 0.0f ? gc.z : 0.0f};
+  float sY[K];  // dL/dY_k
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    sY[k] = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      dcoef[3 * k + ch] += gch[ch] * Y[k];
+      sY[k] += gch[ch] * __ldg(coef + 3 * k + ch);
+    }
+  }
+  if (L == 0) return;
+  const float3 dd = sh_grad_dot<L>(dx, dy, dz, sY);
+  const float dot = dd.x * dx + dd.y * dy + dd.z * dz;
+  dmu.x += (dd.x - dot * dx) * rinv;
+  dmu.y += (dd.y - dot * dy) * rinv;
+  dmu.z += (dd.z - dot * dz) * rinv;
+}
+
+// L: degree of the view-dependent colour (GMR_COLOR_SH), or -1 for a colour
+// per face or per vertex.
+template <int G, int L>
 __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
-    const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ opacity,
-    const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q, const float4* __restrict__ face_grad,
-    float* __restrict__ dverts, float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
+    const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ rgb,
+    const float* __restrict__ opacity, const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q,
+    const float4* __restrict__ face_grad, const float4* __restrict__ rec_cgrad, float* __restrict__ dverts,
+    float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
   pdl_enter();
+  constexpr int K = L >= 0 ? (L + 1) * (L + 1) : 1;
+  float dcoef[L >= 0 ? 3 * K : 1];
+#pragma unroll
+  for (int k = 0; k < (L >= 0 ? 3 * K : 1); ++k) dcoef[k] = 0.0f;
+  float dq_sum = 0.0f;  // view-dependent colour: sum over the views of sum dq
   const int64_t gid = (int64_t)blockIdx.x * kProjBwdThreads + threadIdx.x;
   const int f = (int)(gid / G);
   const int sub = (int)(gid % G);
@@ -479,8 +566,15 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
         r0n = rec_grad[2 * (rid + (size_t)G * F)];
         r4n = rec_grad[2 * (rid + (size_t)G * F) + 1].x;
       }
-      if (r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f) continue;
-      record_bwd(g, views[c], r0, r4, rec_q[rid], acc);
+      const bool geo = !(r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f);
+      if (L >= 0) {
+        const float4 cg = rec_cgrad[rid];
+        dq_sum += cg.w;
+        if (cg.x != 0.f || cg.y != 0.f || cg.z != 0.f)
+          sh_colour_bwd<L >= 0 ? L : 0>(rgb + (size_t)f * 3 * K, g, views[c], make_float3(cg.x, cg.y, cg.z), dcoef,
+                                        acc.dmu);
+      }
+      if (geo) record_bwd(g, views[c], r0, r4, rec_q[rid], acc);
     }
   }
   if (G > 1) {  // every lane of the warp takes part in the shuffles
@@ -490,6 +584,11 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
       acc.dd[k] = make_float3(group_sum<G>(acc.dd[k].x), group_sum<G>(acc.dd[k].y), group_sum<G>(acc.dd[k].z));
     acc.dn = make_float3(group_sum<G>(acc.dn.x), group_sum<G>(acc.dn.y), group_sum<G>(acc.dn.z));
     acc.dw = group_sum<G>(acc.dw);
+    if (L >= 0) {
+#pragma unroll
+      for (int k = 0; k < 3 * K; ++k) dcoef[k] = group_sum<G>(dcoef[k]);
+      dq_sum = group_sum<G>(dq_sum);
+    }
   }
   if (!ok || sub != 0) return;
   // to vertices: d_a = v_a - mu (mu = mean of v), n from e1 x e2
@@ -519,8 +618,12 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
       atomicAdd(dverts + 3 * idx[k] + 2, dv[k].z);
     }
   }
-  const float4 fg = face_grad[f];
-  if (drgb) {
+  const float4 fg = L >= 0 ? make_float4(0.f, 0.f, 0.f, dq_sum) : face_grad[f];
+  if (drgb && L >= 0) {  // the coefficients' gradient, summed over the views (no atomics)
+    float* dst = drgb + (size_t)f * 3 * K;
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dst[k] = accumulate ? dst[k] + dcoef[k] : dcoef[k];
+  } else if (drgb) {
     if (color_mode == GMR_COLOR_PER_FACE) {
       if (accumulate) {
         drgb[3 * f] += fg.x; drgb[3 * f + 1] += fg.y; drgb[3 * f + 2] += fg.z;
@@ -601,12 +704,13 @@ __global__ void k_convert(const float* __restrict__ verts, int32_t V, const int3
 }  // namespace
 
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
-                           const float* opacity, int color_mode, const ViewInfo* views, int32_t C, int tile,
-                           int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
+                           const float* opacity, int color_mode, int sh_degree, const ViewInfo* views, int32_t C,
+                           int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
   if (F <= 0 || C <= 0) return cudaSuccess;
   dim3 grid((F + kProjThreads - 1) / kProjThreads, C);
   cudaError_t e = launch_chained(k_project, true, grid, dim3(kProjThreads), 0, s, verts, V, faces, F, rgb, opacity,
-                                 color_mode, views, tile, 1.0f / (float)tile, cov_mode, ws.rec_u, ws.rec_q,
+                                 color_mode, sh_degree, ws.rec_col, ws.rec_cgrad, views, tile, 1.0f / (float)tile,
+                                 cov_mode, ws.rec_u, ws.rec_q,
                                  ws.rec_rect, ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
                                  ws.pair_key[1], ws.pair_face, ws.rec_grad, ws.face_grad, ws.counters);
   *launches += 1;
@@ -614,9 +718,9 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
 }
 
 cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
-                               const ViewInfo* views, int32_t C, int cov_mode, int color_mode, const float* opacity,
-                               const Workspace& ws, float* dverts, float* drgb, float* dop, int accumulate,
-                               cudaStream_t s, int64_t* launches) {
+                               const ViewInfo* views, int32_t C, int cov_mode, int color_mode, int sh_degree,
+                               const float* rgb, const float* opacity, const Workspace& ws, float* dverts,
+                               float* drgb, float* dop, int accumulate, cudaStream_t s, int64_t* launches) {
   if (F <= 0) return cudaSuccess;
   // lanes per face: enough threads to fill the GPU when faces are few, no
   // more lanes than views (more lanes than that repeat the per-face work and
@@ -625,10 +729,15 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
   while (G < 8 && G < C && (int64_t)F * G < 148 * 2048) G <<= 1;
   const int64_t threads = (int64_t)F * G;
   const unsigned blocks = (unsigned)((threads + kProjBwdThreads - 1) / kProjBwdThreads);
-  auto kern = G == 1 ? k_proj_bwd<1> : G == 2 ? k_proj_bwd<2> : G == 4 ? k_proj_bwd<4> : k_proj_bwd<8>;
+  const int L = color_mode == GMR_COLOR_SH ? sh_degree : -1;
+#define GMR_PB(G_) (L < 0 ? k_proj_bwd<G_, -1> : L == 0 ? k_proj_bwd<G_, 0> : L == 1 ? k_proj_bwd<G_, 1> \
+                    : L == 2 ? k_proj_bwd<G_, 2> : k_proj_bwd<G_, 3>)
+  auto kern = G == 1 ? GMR_PB(1) : G == 2 ? GMR_PB(2) : G == 4 ? GMR_PB(4) : GMR_PB(8);
+#undef GMR_PB
   cudaError_t e = launch_chained(kern, true, dim3(blocks), dim3(kProjBwdThreads), 0, s, verts, V, faces, F, C, views,
-                                 cov_mode, color_mode, opacity, (const float4*)ws.rec_grad, (const float4*)ws.rec_q,
-                                 (const float4*)ws.face_grad, dverts, drgb, dop, accumulate);
+                                 cov_mode, color_mode, rgb, opacity, (const float4*)ws.rec_grad,
+                                 (const float4*)ws.rec_q, (const float4*)ws.face_grad, (const float4*)ws.rec_cgrad,
+                                 dverts, drgb, dop, accumulate);
   *launches += 1;
   return e;
 }

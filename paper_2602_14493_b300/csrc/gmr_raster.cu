@@ -151,14 +151,15 @@ __device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, flo
 template <int TS, int NT, int BATCH>
 __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
                                             int count, uint32_t rec_base, const float4* __restrict__ rec_u,
-                                            const float4* __restrict__ rec_q, const float4* __restrict__ face_col,
-                                            float ax, float ay, float tox, float toy, bool want_ids) {
+                                            const float4* __restrict__ rec_q, const float4* __restrict__ col_src,
+                                            bool col_by_rec, float ax, float ay, float tox, float toy,
+                                            bool want_ids) {
   for (int i = threadIdx.x; i < count; i += NT) {
     uint32_t f = __ldg(pair_face + lo + i);
     uint32_t rid = rec_base + f;
     float4 u = __ldg(rec_u + rid);
     float4 q = __ldg(rec_q + rid);
-    float4 col = __ldg(face_col + f);
+    float4 col = __ldg(col_src + (col_by_rec ? rid : f));
     float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
     const uint32_t m = block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy);
@@ -256,7 +257,8 @@ struct RasterArgs {
   const uint32_t* pair_face;
   const float4* rec_u;
   const float4* rec_q;
-  const float4* face_col;
+  const float4* col;  // (r, g, b, o) per face, or per record when col_by_rec
+  int col_by_rec;     // view-dependent colour: colours and their gradients per record
   const ViewInfo* views;
   int32_t F;
   float bg0, bg1, bg2;
@@ -343,8 +345,8 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
     for (int k = 0; k < PPT; ++k) tdone &= done[k];
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
-    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.face_col, ax, ay,
-                               tox, toy, MODE == kFwdDebug);
+    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.col,
+                               a.col_by_rec != 0, ax, ay, tox, toy, MODE == kFwdDebug);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, cnt, 0, cnt, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
@@ -633,7 +635,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
     const int start = max(0, end - BATCH);
     __syncthreads();
     stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
-                               a.face_col, ax, ay, tox, toy, true);
+                               a.col, a.col_by_rec != 0, ax, ay, tox, toy, true);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, end - start, start, (int)wmax, PixMap<TS, NT>::warp_bits());
     const int warp = threadIdx.x >> 5;
@@ -684,6 +686,8 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
       }
       const uint32_t cm = __ballot_sync(kFull, any);
       if (cm == 0u) continue;
+      // colour gradient sums: per face, or per record (view-dependent colour)
+      const uint32_t ci = a.col_by_rec ? st.rid[j] : st.face[j];
       if (__popc(cm) <= kBwdDirectLanes) {
         // few contributing lanes: their own atomics cost fewer instructions
         // than the warp reduction
@@ -691,7 +695,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
           float4* rg = rec_grad + 2 * (size_t)st.rid[j];
           atomicAdd(rg, make_float4(acc[0], acc[1], acc[2], acc[3]));
           atomicAdd(reinterpret_cast<float*>(rg + 1), acc[4]);
-          atomicAdd(face_grad + st.face[j], make_float4(acc[6], acc[7], acc[8], acc[5]));
+          atomicAdd(face_grad + ci, make_float4(acc[6], acc[7], acc[8], acc[5]));
         }
         continue;
       }
@@ -703,11 +707,11 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
         int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
         float* dst;
         if (vi < 5) dst = reinterpret_cast<float*>(rec_grad + 2 * (size_t)st.rid[j]) + vi;
-        else if (vi == 5) dst = reinterpret_cast<float*>(face_grad + st.face[j]) + 3;
-        else dst = reinterpret_cast<float*>(face_grad + st.face[j]) + (vi - 6);
+        else if (vi == 5) dst = reinterpret_cast<float*>(face_grad + ci) + 3;
+        else dst = reinterpret_cast<float*>(face_grad + ci) + (vi - 6);
         atomicAdd(dst, s);
       }
-      if (lane == 0) atomicAdd(reinterpret_cast<float*>(face_grad + st.face[j]) + 2, s8);
+      if (lane == 0) atomicAdd(reinterpret_cast<float*>(face_grad + ci) + 2, s8);
     }
   }
 #pragma unroll
@@ -861,12 +865,13 @@ int resident_grid(K kern, int threads) {
 }
 
 RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t F,
-                       const float* bg, int64_t n_tiles) {
+                       const float* bg, int64_t n_tiles, bool col_by_record) {
   RasterArgs a;
   a.pair_face = pair_face;
   a.rec_u = ws.rec_u;
   a.rec_q = ws.rec_q;
-  a.face_col = ws.face_col;
+  a.col = col_by_record ? ws.rec_col : ws.face_col;
+  a.col_by_rec = col_by_record ? 1 : 0;
   a.views = views;
   a.F = F;
   a.bg0 = bg[0];
@@ -879,7 +884,8 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t fwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, const uint32_t* pair_face,
+cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, const Workspace& ws,
+                       const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, float* images, float* t_out,
                        uint32_t* nc_out, const FwdLoss& fl, cudaStream_t s) {
   auto kern = persistent ? (fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, true>
@@ -891,7 +897,7 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, co
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
   cudaError_t e = launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
-                                 raster_args(ws, pair_face, views, F, bg, n_tiles), images, ws.pix_T,
+                                 raster_args(ws, pair_face, views, F, bg, n_tiles, col_by_record), images, ws.pix_T,
                                  ws.pix_last, t_out, nc_out, ws.cap_pixels, fl);
   if (e == cudaSuccess && fl.target)
     e = launch_chained(k_sum_partials, true, dim3(1), dim3(1024), 0, s, (const float*)fl.part, n_tiles * (NT / 32), 1.0,
@@ -900,7 +906,8 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, co
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t bwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, const uint32_t* pair_face,
+cudaError_t bwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, const Workspace& ws,
+                       const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
                        const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
   auto kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true> : k_raster_bwd<TS, NT, BATCH, false, true>)
@@ -908,13 +915,15 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, const Workspace& ws, co
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
   return launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
-                        raster_args(ws, pair_face, views, F, bg, n_tiles), dL, dLdT,
-                        (const float*)ws.pix_T, (const uint32_t*)ws.pix_last, ws.rec_grad, ws.face_grad, bl, bz);
+                        raster_args(ws, pair_face, views, F, bg, n_tiles, col_by_record), dL, dLdT,
+                        (const float*)ws.pix_T, (const uint32_t*)ws.pix_last, ws.rec_grad,
+                        col_by_record ? ws.rec_cgrad : ws.face_grad, bl, bz);
 }
 
 }  // namespace
 
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, bool col_by_record,
+                              const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
                               uint32_t* ncontrib_out, const FwdLoss& fl, cudaStream_t s, int64_t* launches) {
@@ -923,7 +932,8 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_FWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, ws, pair_face, views, C, F, bg, images, t_final_out,          \
+  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, col_by_record, ws, pair_face, views, C, F, bg, images,         \
+                               t_final_out,                                                                      \
                                ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
   else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
@@ -935,7 +945,8 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   return e;
 }
 
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, const Workspace& ws,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, bool col_by_record,
+                              const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
                               const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches) {
@@ -943,7 +954,8 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, ws, pair_face, views, C, F, bg, dL_dimages, dL_dT, bl, bz, s)
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, col_by_record, ws, pair_face, views, C, F, bg, dL_dimages,  \
+                               dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);

@@ -18,7 +18,7 @@ import torch
 from . import _lib
 
 _COV = {"area": _lib.GMR_COV_AREA, "embed_raw": _lib.GMR_COV_EMBED_RAW}
-_COLOR = {"face": _lib.GMR_COLOR_PER_FACE, "vertex": _lib.GMR_COLOR_PER_VERTEX}
+_COLOR = {"face": _lib.GMR_COLOR_PER_FACE, "vertex": _lib.GMR_COLOR_PER_VERTEX, "sh": _lib.GMR_COLOR_SH}
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -74,7 +74,9 @@ class Renderer:
     backward (64/128/256 for 16x16 tiles, 256 for 32x32; None: 128 for 16x16
     tiles, 256 for 32x32); batch: Gaussians per shared-memory batch (64/128/256);
     cov_mode: "area" (Eq. 13) or "embed_raw" (Eq. 15 literally);
-    color_mode: "face" (F x 3 colours) or "vertex" (V x 3, Eq. 16);
+    color_mode: "face" (F x 3 colours), "vertex" (V x 3, Eq. 16) or "sh"
+    (view-dependent: F x (sh_degree + 1)^2 x 3 spherical-harmonic
+    coefficients, sh_degree 0..3);
     sync_check: read the pair count back once per forward and grow buffers
     (False: never synchronise; pre-size with ``reserve`` for graph capture).
     profile: time the stages with CUDA events (True: all of them; or a list
@@ -85,7 +87,7 @@ class Renderer:
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
                  sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None,
-                 persistent=False):
+                 persistent=False, sh_degree=0):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -98,6 +100,7 @@ class Renderer:
         self.cfg.batch = batch
         self.cfg.cov_mode = _COV[cov_mode]
         self.cfg.color_mode = _COLOR[color_mode]
+        self.cfg.sh_degree = int(sh_degree)
         self.cfg.bg[:] = [float(x) for x in bg]
         self.cfg.flags = ((_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
                           | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0)

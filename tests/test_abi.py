@@ -35,7 +35,7 @@ def test_struct_layouts_match_header():
     from paper_2602_14493_b300 import _lib
 
     assert ctypes.sizeof(_lib.GmrCamera) == 76 == gi.CAMERA_DTYPE.itemsize
-    assert ctypes.sizeof(_lib.GmrConfig) == 44
+    assert ctypes.sizeof(_lib.GmrConfig) == 48
     assert ctypes.sizeof(_lib.GmrStats) == 80
     cam = gi.look_at((0.0, -3.0, 1.0), 32, 16)
     arr = np.array([cam], dtype=gi.CAMERA_DTYPE)
