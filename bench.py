@@ -56,9 +56,10 @@ FLOPS_FWD_CONTRIB = 10
 FLOPS_BWD_CONTRIB = 59
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that
 # one ncu capture measured for the dominant kernel, per workload and launch
-# shape (tile, backward threads, batch, persistent); an entry is removed when
+# shape (tile, backward threads, batch, persistent, half-warp backward); an
+# entry is removed when
 # the kernel changes after its capture.
-NCU_TRAFFIC = {("raster_bwd", "icosphere6_noise_64xuneven", (16, 128, 256, 0)): 1950448128}
+NCU_TRAFFIC = {("raster_bwd", "icosphere6_noise_64xuneven", (16, 128, 256, 0, 0)): 1950448128}
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -395,18 +396,22 @@ def run_gmr(args, ws, rank, local):
     if args.tile == "auto":
         from paper_2602_14493_b300.autotune import shape_name, tune
 
-        (tile, threads, threads_bwd, batch, persistent), tuned = tune(r, v, f, c, o, cams, target, use_cache=False)
+        (tile, threads, threads_bwd, batch, persistent, half_fwd, half_bwd), tuned = tune(r, v, f, c, o, cams, target,
+                                                                                          use_cache=False)
         log("autotune:", {shape_name(k): round(t, 4) for k, t in sorted(tuned.items(), key=lambda kv: kv[1])[:8]})
-        # the best shape with one CTA per tile and as a persistent grid
-        scheduler = {"per_tile_grid_ms": tuned.get((tile, threads, threads_bwd, batch, 0)),
-                     "persistent_ms": tuned.get((tile, threads, threads_bwd, batch, 1)),
+        # the fastest full-warp shape with one CTA per tile and as a persistent
+        # grid, and the half-warp layouts the tuner tried
+        full = min((k for k in tuned if k[4:] == (0, 0, 0)), key=tuned.get)
+        scheduler = {"per_tile_grid_ms": tuned.get(full), "persistent_ms": tuned.get(full[:4] + (1, 0, 0)),
+                     "half_warp_ms": {shape_name(k): round(t, 4) for k, t in tuned.items() if k[5] or k[6]},
                      "source": "autotuner, eager fwd + loss + bwd step, median of 15"}
     else:
         tile, threads, batch = int(args.tile), args.threads, args.batch
         threads_bwd = args.threads_bwd or threads
-        persistent = int(args.persistent)
+        persistent, half_fwd, half_bwd = int(args.persistent), int(args.half_fwd), int(args.half_bwd)
         scheduler = None
-        r.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent))
+        r.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent),
+                     half_fwd=bool(half_fwd), half_bwd=bool(half_bwd))
     img, _ = r.forward(v, f, c, o, cams, want_t=False)
     torch.cuda.synchronize()
     P = r.stats()["n_pairs"]
@@ -598,7 +603,7 @@ def run_gmr(args, ws, rank, local):
     if stage_acc.get(DOMINANT):
         # duration of the dominant kernel inside the timed steps themselves
         roof = roofline_for(DOMINANT, statistics.mean(stage_acc[DOMINANT]), stats, scene, peaks, peak_kind, args,
-                            shape=(tile, threads_bwd, batch, int(persistent)))
+                            shape=(tile, threads_bwd, batch, int(persistent), int(half_bwd)))
     else:
         roof = None
         log("no stage times were recorded")
@@ -622,7 +627,8 @@ def run_gmr(args, ws, rank, local):
         "dtype": "fp32", "data": "synthetic",
         "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
                    "form": "batched, one call for all views, CUDA graph", "tile": tile, "threads": threads, "threads_bwd": threads_bwd,
-                   "batch": batch, "persistent": bool(persistent),
+                   "batch": batch, "persistent": bool(persistent), "half_warp_fwd": bool(half_fwd),
+                   "half_warp_bwd": bool(half_bwd),
                    "shape_choice": "autotuned" if args.tile == "auto" else "fixed",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -655,8 +661,8 @@ DOMINANT = "raster_bwd"  # the step's largest kernel (compositing backward)
 
 def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args, shape=None):
     """Roofline entry of the dominant kernel from its live event time
-    (shape: the launch shape (tile, backward threads, batch, persistent),
-    which selects the recorded DRAM traffic)."""
+    (shape: the launch shape (tile, backward threads, batch, persistent,
+    half-warp backward), which selects the recorded DRAM traffic)."""
     E_f, E_b, K = stats["evals_fwd"], stats["evals_bwd"], stats["contribs"]
     if stage in ("raster_fwd", "raster_bwd"):
         flops = (FLOPS_EVAL * E_f + FLOPS_FWD_CONTRIB * K) if stage == "raster_fwd" else \
@@ -691,6 +697,8 @@ def main():
     ap.add_argument("--threads-bwd", type=int, default=0, help="backward threads per tile (0: as --threads)")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--persistent", type=int, default=0, help="with a fixed shape: 1 = persistent compositing grids")
+    ap.add_argument("--half-fwd", type=int, default=0, help="with a fixed shape: 1 = half-warp layout, forward")
+    ap.add_argument("--half-bwd", type=int, default=0, help="with a fixed shape: 1 = half-warp layout, backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-pixels", type=int, default=128)

@@ -138,6 +138,16 @@ typedef struct {
  * left, instead of one CTA per tile. Results are identical either way. */
 #define GMR_FLAG_PERSISTENT 8
 
+/* With these flags the forward / backward compositing kernel uses the
+ * half-warp layout: each 16-lane half of a warp composites its own 4x4-pixel
+ * units and walks its own list of the Gaussians that can reach them, so a
+ * warp serves two Gaussians per step where they cover few pixels (dense
+ * meshes). 16x16 tiles with 128 or 256 threads only, not with
+ * GMR_FLAG_PERSISTENT (GMR_ERR_INVALID_ARG otherwise). Images are identical
+ * bit for bit; gradients agree up to the order of the float atomics. */
+#define GMR_FLAG_HALF_WARP_FWD 16
+#define GMR_FLAG_HALF_WARP_BWD 32
+
 /* Stages timed under GMR_FLAG_PROFILE. */
 typedef enum {
   GMR_STAGE_PROJECT = 0,      /* conversion fused with EWA projection, tile counts (Sec. 2.2, 2.1) */

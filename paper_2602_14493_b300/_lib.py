@@ -24,6 +24,8 @@ GMR_FLAG_SYNC_CHECK = 1
 GMR_FLAG_PROFILE = 2
 GMR_FLAG_DEBUG_COUNTS = 4
 GMR_FLAG_PERSISTENT = 8
+GMR_FLAG_HALF_WARP_FWD = 16
+GMR_FLAG_HALF_WARP_BWD = 32
 GMR_L2_NOALLOC_MAX_ELEMS = 67108864
 STAGES = ["project", "scan", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
 

@@ -18,16 +18,23 @@ import statistics
 
 import torch
 
-# (tile, forward threads per tile, backward threads per tile, batch)
+# (tile, forward threads per tile, backward threads per tile, batch), full-warp
+# layout, one CTA per tile
 CANDIDATES = [(16, tf, tb, b) for tf in (256, 128, 64) for tb in (256, 128, 64) for b in (256, 128, 64)] + [
     (32, 256, 256, 256), (32, 256, 256, 128),
 ]
 
 
+# A shape is (tile, forward threads, backward threads, batch, persistent,
+# half-warp forward, half-warp backward).
+def _full(shape):
+    return tuple(shape) + (0,) * (7 - len(shape))
+
+
 def _apply(renderer, shape):
-    tile, threads, threads_bwd, batch = shape[:4]
-    persistent = bool(shape[4]) if len(shape) > 4 else False
-    renderer.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=persistent)
+    tile, threads, threads_bwd, batch, persistent, half_fwd, half_bwd = _full(shape)
+    renderer.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent),
+                        half_fwd=bool(half_fwd), half_bwd=bool(half_bwd))
 
 
 def shape_name(shape) -> str:
@@ -67,13 +74,15 @@ def _store(d):
 
 
 def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates=CANDIDATES, use_cache=True):
-    """Times each candidate shape on this workload with one CTA per tile,
-    then the fastest also as a persistent grid, and configures ``renderer``
+    """Times each candidate shape on this workload with one CTA per tile;
+    then, from the fastest, the half-warp layout in the forward and in the
+    backward (128 and 256 threads each, separately, then together), and the
+    fastest full-warp shape as a persistent grid; configures ``renderer``
     with the fastest of all. Returns (best (tile, threads, threads_bwd,
-    batch, persistent), {shape: median ms})."""
+    batch, persistent, half_fwd, half_bwd), {shape: median ms})."""
     sig = signature(faces.shape[0], cams)
     cache = _load() if use_cache else {}
-    if use_cache and sig in cache and len(cache[sig]["best"]) == 5:
+    if use_cache and sig in cache and len(cache[sig]["best"]) == 7:
         best = tuple(cache[sig]["best"])
         _apply(renderer, best)
         return best, {}
@@ -99,9 +108,19 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
         results[shape] = statistics.median(ts)
 
     for shape in candidates:
-        time_shape(tuple(shape[:4]) + (0,))
+        time_shape(_full(shape[:4]))
     best = min(results, key=results.get)
-    time_shape(best[:4] + (1,))
+    tile, tf, tb, batch = best[:4]
+    if tile == 16:
+        fwd = [(16, t, tb, batch, 0, 1, 0) for t in (128, 256)]
+        bwd = [(16, tf, t, batch, 0, 0, 1) for t in (128, 256)]
+        for shape in fwd + bwd:
+            time_shape(shape)
+        bf = min(fwd + [best], key=results.get)
+        bb = min(bwd + [best], key=results.get)
+        if bf != best and bb != best:
+            time_shape((16, bf[1], bb[2], batch, 0, 1, 1))
+    time_shape(tuple(best[:4]) + (1, 0, 0))
     best = min(results, key=results.get)
     _apply(renderer, best)
     if use_cache:

@@ -112,18 +112,19 @@ __device__ __forceinline__ int warp_list(Stage<BATCH, NW>& st, int count, int fi
   return n;
 }
 
-// Bit mask of the tile's 8x4-pixel warp blocks that the Gaussian's region
-// alpha >= 1/255 can reach. In log2 units that region is
+// Bit mask of the tile's blocks of BW x BH pixels (NCB per row, NRB rows)
+// that the Gaussian's region alpha >= 1/255 can reach. In log2 units that
+// region is
 // A dx^2 + B dx dy + C dy^2 <= log2(255 o) with (A, B, C) = -(a2, b2, c2);
 // its bounding box has half-widths sqrt(k C / (AC - B^2/4)) and
 // sqrt(k A / (AC - B^2/4)). The box is widened (k by 1e-4 relative, 1e-3 px)
 // so that every skipped Gaussian has alpha below 1/255 by a margin (at least
 // 1e-4 in log2 units) far above
 // the rounding of the alpha evaluation: culling never changes a result.
-template <int TS>
-__device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, float b2, float c2, float k2, float tox,
-                                               float toy) {
-  constexpr int NC = TS / 8, NR = TS / 4;
+template <int NCB, int NRB, int BW, int BH>
+__device__ __forceinline__ uint32_t region_mask(float gx, float gy, float a2, float b2, float c2, float k2, float tox,
+                                                float toy) {
+  static_assert(NCB * NRB <= 32, "one bit per block");
   const float A = -a2, B = -b2, Cq = -c2;
   const float det = A * Cq - 0.25f * B * B;
   if (!(k2 > 0.0f) || !(det > 0.0f)) return 0u;  // k2 = log2(255 o)
@@ -131,29 +132,43 @@ __device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, flo
   const float hx = sqrtf(kk * Cq) + 1e-3f, hy = sqrtf(kk * A) + 1e-3f;
   uint32_t cols = 0;
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    float lo = tox + (float)(8 * c) + 0.5f;
-    if (gx + hx >= lo && gx - hx <= lo + 7.0f) cols |= 1u << c;
+  for (int c = 0; c < NCB; ++c) {
+    float lo = tox + (float)(BW * c) + 0.5f;
+    if (gx + hx >= lo && gx - hx <= lo + (float)(BW - 1)) cols |= 1u << c;
   }
   uint32_t m = 0;
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    float lo = toy + (float)(4 * r) + 0.5f;
-    if (gy + hy >= lo && gy - hy <= lo + 3.0f) m |= cols << (r * NC);
+  for (int r = 0; r < NRB; ++r) {
+    float lo = toy + (float)(BH * r) + 0.5f;
+    if (gy + hy >= lo && gy - hy <= lo + (float)(BH - 1)) m |= cols << (r * NCB);
   }
   return m;
+}
+
+// The tile's 8x4-pixel warp blocks (row-major, TS/8 per row)...
+template <int TS>
+__device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, float b2, float c2, float k2, float tox,
+                                               float toy) {
+  return region_mask<TS / 8, TS / 4, 8, 4>(gx, gy, a2, b2, c2, k2, tox, toy);
+}
+
+// ... and the 4x4-pixel half-warp units of a 16x16 tile (row-major, 4 per
+// row), for the half-warp layout.
+__device__ __forceinline__ uint32_t unit_mask(float gx, float gy, float a2, float b2, float c2, float k2, float tox,
+                                              float toy) {
+  return region_mask<4, 4, 4, 4>(gx, gy, a2, b2, c2, k2, tox, toy);
 }
 
 // Staging of one batch: records and colours of the listed Gaussians, the
 // mean relative to the anchor, and the block mask (the conservative
 // bounding-box test above). The record's w holds the skip threshold
 // t2 = -log2(255 o).
-template <int TS, int NT, int BATCH>
-__device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
+template <int TS, int NT, int BATCH, int NL = NT / 32>
+__device__ __forceinline__ void stage_batch(Stage<BATCH, NL>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
                                             int count, uint32_t rec_base, const float4* __restrict__ rec_u,
                                             const float4* __restrict__ rec_q, const float4* __restrict__ col_src,
                                             bool col_by_rec, float ax, float ay, float tox, float toy,
-                                            bool want_ids) {
+                                            bool want_ids, bool units = false) {
   for (int i = threadIdx.x; i < count; i += NT) {
     uint32_t f = __ldg(pair_face + lo + i);
     uint32_t rid = rec_base + f;
@@ -162,7 +177,8 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH, NT / 32>& st, const uin
     float4 col = __ldg(col_src + (col_by_rec ? rid : f));
     float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
-    const uint32_t m = block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy);
+    const uint32_t m = units ? unit_mask(ux, uy, q.x, q.y, q.z, -q.w, tox, toy)
+                             : block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy);
     st.g[i] = make_float4(ux, uy, q.x, q.y);
     st.h[i] = make_float4(q.z, q.w, col.w, 0.0f);
     st.mask[i] = m;
@@ -444,14 +460,238 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
   }
 }
 
+// ---------------------------------------------------------------- half-warp layout
+// Layout for Gaussians that cover few pixels: a 16x16 tile is cut into 16
+// units of 4x4 pixels (row-major, 4 per row), and each 16-lane half of a
+// warp composites PPT units (one pixel of each per lane) and walks its own
+// compacted list of the batch's Gaussians that can reach them. The two halves
+// of a warp step through their lists together, each on its own entry, so a
+// warp-step serves two Gaussians where the full-warp layout serves one when
+// the Gaussians are smaller than a warp block (the lists of a 4x4 unit are
+// shorter than those of an 8x4 block).
+template <int NT>
+struct HalfMap {
+  static constexpr int PPT = 256 / NT;  // 16x16 tiles: 128 or 256 threads
+  static_assert(PPT == 1 || PPT == 2, "half-warp layout: 16x16 tiles, 128 or 256 threads");
+  // half h owns the units in column h % 4, rows (h / 4) PPT + k
+  __device__ __forceinline__ static int unit_of(int h, int k) { return ((h / 4) * PPT + k) * 4 + (h % 4); }
+  __device__ __forceinline__ static int half() { return threadIdx.x >> 4; }
+  __device__ __forceinline__ static uint32_t bits_of(int h) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) b |= 1u << unit_of(h, k);
+    return b;
+  }
+  __device__ __forceinline__ static void local(int k, int& lx, int& ly) {
+    const int l = threadIdx.x & 15, u = unit_of(half(), k);
+    lx = (u % 4) * 4 + (l & 3);
+    ly = (u / 4) * 4 + (l >> 2);
+  }
+};
+
+// Both halves of each warp compact, in order, the batch entries whose unit
+// mask reaches their units and whose list position is below their limit;
+// returns this lane's half's count (and, in n_max, the larger of the two).
+template <int BATCH>
+__device__ __forceinline__ int half_lists(uint8_t (*list)[BATCH], const uint32_t* mask, int count, int first_pos,
+                                          int limit_lo, int limit_hi, uint32_t bits_lo, uint32_t bits_hi,
+                                          int& n_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  int n0 = 0, n1 = 0;
+  for (int c = 0; c < count; c += 32) {
+    const int i = c + lane;
+    const uint32_t m = i < count ? mask[i] : 0u;
+    const bool r0 = (m & bits_lo) && (first_pos + i) < limit_lo;
+    const bool r1 = (m & bits_hi) && (first_pos + i) < limit_hi;
+    const uint32_t b0 = __ballot_sync(0xffffffffu, r0), b1 = __ballot_sync(0xffffffffu, r1);
+    if (r0) list[2 * warp][n0 + __popc(b0 & lt)] = (uint8_t)i;
+    if (r1) list[2 * warp + 1][n1 + __popc(b1 & lt)] = (uint8_t)i;
+    n0 += __popc(b0);
+    n1 += __popc(b1);
+  }
+  __syncwarp();
+  n_max = max(n0, n1);
+  return (lane & 16) ? n1 : n0;
+}
+
+// The forward of one tile in the half-warp layout: the same arithmetic and
+// decisions per pixel as fwd_tile (so the same image bit for bit), only the
+// assignment of pixels to lanes and the list each lane walks differ.
+template <int NT, int BATCH, int MODE>
+__device__ __forceinline__ void fwd_tile_half(const RasterArgs& a, uint32_t pos, float* __restrict__ images,
+                                              float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
+                                              float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
+                                              int64_t n_pix_total, const FwdLoss& fl) {
+  constexpr int TS = 16;
+  using HM = HalfMap<NT>;
+  constexpr int PPT = HM::PPT;
+  constexpr int NW = NT / 32;
+  __shared__ Stage<BATCH, 2 * NW> st;  // list[h]: half h's entries
+  const uint4 desc = __ldg(a.tile_desc + pos);
+  const int g = (int)desc.x;
+  const int c = (int)desc.y;
+  const ViewInfo& v = a.views[c];
+  const int lt = g - v.tile_base;
+  const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
+  const int ox = txi * TS, oy = tyi * TS;
+  const int axi = ox & ~31, ayi = oy & ~31;
+  const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
+  const int lane = threadIdx.x & 31;
+  const int hl = HM::half();  // this lane's half (list index)
+
+  float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+  __shared__ float s_tgt[MODE == kFwdLoss ? 3 * PPT * NT : 1];
+  uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
+  bool done[PPT], inside[PPT];
+  int px[PPT], py[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    int lx, ly;
+    HM::local(k, lx, ly);
+    px[k] = ox + lx;
+    py[k] = oy + ly;
+    pcx[k] = (float)(px[k] - axi) + 0.5f;
+    pcy[k] = (float)(py[k] - ayi) + 0.5f;
+    inside[k] = px[k] < v.W && py[k] < v.H;
+    done[k] = !inside[k];
+    T[k] = 1.0f;
+    Cr[k] = Cg[k] = Cb[k] = 0.0f;
+    last[k] = 0;
+    term[k] = 0;
+    ncontrib[k] = 0;
+    chash[k] = 0;
+    if (MODE == kFwdLoss && inside[k]) {
+      const float* tp = fl.target + 3 * (v.pix_base + (int64_t)py[k] * v.W + px[k]);
+      const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&s_tgt[3 * (k * NT + threadIdx.x)]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + 4u * q), "l"(tp + q) : "memory");
+    }
+  }
+  if (MODE == kFwdLoss) asm volatile("cp.async.commit_group;" ::: "memory");
+  const uint2 range = make_uint2(desc.z, desc.w);
+  const int n = (int)(range.y - range.x);
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t bits_lo = HM::bits_of(2 * warp), bits_hi = HM::bits_of(2 * warp + 1);
+
+  for (int base = 0; base < n; base += BATCH) {
+    bool tdone = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) tdone &= done[k];
+    if (__syncthreads_and(tdone)) break;
+    int cnt = min(BATCH, n - base);
+    stage_batch<TS, NT, BATCH, 2 * NW>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.col,
+                                       a.col_by_rec != 0, ax, ay, tox, toy, MODE == kFwdDebug, true);
+    __syncthreads();
+    int n_max;
+    const int nl = half_lists<BATCH>(st.list, st.mask, cnt, 0, cnt, cnt, bits_lo, bits_hi, n_max);
+    for (int jj = 0; jj < n_max; ++jj) {
+      const bool act = jj < nl;
+      if ((jj & 3) == 0) {  // the warp's early exit, checked every 4 entries
+        bool wd = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) wd &= done[k];
+        if (__all_sync(kFull, wd || !act)) break;
+      }
+      const int j = act ? st.list[hl][jj] : 0;
+      const float4 hh = st.h[j];
+      const float4 gg = st.g[j];
+      float p2[PPT];
+      bool con[PPT];
+      bool anyc = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        float dx, dy;
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dx, dy);
+        con[k] = act && !done[k] && !(p2[k] < hh.y);
+        anyc |= con[k];
+      }
+      if (!anyc) continue;
+      const float4 col = st.col[j];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (!con[k]) continue;
+        float graw;
+        float alpha = gauss_alpha(p2[k], hh.z, graw);
+        float test = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+        if (test < kTMin) {
+          done[k] = true;
+          term[k] = (uint32_t)(base + j + 1);
+          continue;
+        }
+        float w = __fmul_rn(alpha, T[k]);
+        Cr[k] = __fmaf_rn(col.x, w, Cr[k]);
+        Cg[k] = __fmaf_rn(col.y, w, Cg[k]);
+        Cb[k] = __fmaf_rn(col.z, w, Cb[k]);
+        T[k] = test;
+        last[k] = (uint32_t)(base + j + 1);
+        ++ncontrib[k];
+        if (MODE == kFwdDebug) chash[k] = chash[k] * 0x9E3779B1u + st.face[j] + 1u;
+      }
+    }
+  }
+  unsigned long long evals = 0, ncon = 0;
+  float lsum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (!inside[k]) continue;
+    ncon += ncontrib[k];
+    int64_t pid = v.pix_base + (int64_t)py[k] * v.W + px[k];
+    const float i0 = Cr[k] + T[k] * a.bg0, i1 = Cg[k] + T[k] * a.bg1, i2 = Cb[k] + T[k] * a.bg2;
+    images[3 * pid] = i0;
+    images[3 * pid + 1] = i1;
+    images[3 * pid + 2] = i2;
+    if (MODE == kFwdLoss) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      const float* tg = &s_tgt[3 * (k * NT + threadIdx.x)];
+      const float d0 = i0 - tg[0], d1 = i1 - tg[1], d2 = i2 - tg[2];
+      fl.grad[3 * pid] = 2.0f * d0;
+      fl.grad[3 * pid + 1] = 2.0f * d1;
+      fl.grad[3 * pid + 2] = 2.0f * d2;
+      lsum = fmaf(d0, d0, lsum);
+      lsum = fmaf(d1, d1, lsum);
+      lsum = fmaf(d2, d2, lsum);
+    }
+    pix_T[pid] = T[k];
+    pix_last[pid] = last[k];
+    if (t_out) t_out[pid] = T[k];
+    if (MODE == kFwdDebug) {
+      nc_out[pid] = ncontrib[k];
+      nc_out[n_pix_total + pid] = chash[k];
+    }
+    evals += term[k] ? term[k] : (uint32_t)n;
+  }
+  if (MODE == kFwdLoss) asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(kFull, evals, o);
+    ncon += __shfl_xor_sync(kFull, ncon, o);
+  }
+  if (lane == 0 && evals) atomicAdd(&a.counters->evals_fwd, evals);
+  if (lane == 0 && ncon) atomicAdd(&a.counters->contribs, ncon);
+  if (MODE == kFwdLoss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
+    if (lane == 0) fl.part[(int64_t)g * NW + warp] = lsum;
+  }
+}
+
 // PERSIST: a persistent grid of resident CTAs taking positions from the
 // cursor; otherwise one CTA per position (the default: measured faster).
-template <int TS, int NT, int BATCH, int MODE, bool PERSIST>
+// HALF: the half-warp layout (16x16 tiles, 128 or 256 threads, one CTA per
+// tile).
+template <int TS, int NT, int BATCH, int MODE, bool PERSIST, bool HALF = false>
 __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value)
     k_raster_fwd(RasterArgs a, float* __restrict__ images, float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
                  float* __restrict__ t_out, uint32_t* __restrict__ nc_out, int64_t n_pix_total, FwdLoss fl) {
   pdl_enter();
-  if (!PERSIST) {
+  if constexpr (HALF) {
+    static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
+    fwd_tile_half<NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
+  } else if (!PERSIST) {
     fwd_tile<TS, NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
   } else {
     uint32_t pos;
@@ -719,13 +959,227 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
   if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
 }
 
-template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST>
+// Sum of v[0..7] over each 16-lane half of the warp, transposed: on return
+// lane L of a half (L = lane % 16, L even) holds the half's total of value
+// index ((L >> 3) & 1) * 4 + ((L >> 2) & 1) * 2 + ((L >> 1) & 1).
+__device__ __forceinline__ float half_reduce8_transposed(const float v[8], int lane) {
+  const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float k0 = (b3 ? v[4] : v[0]) + __shfl_xor_sync(kFull, b3 ? v[0] : v[4], 8);
+  float k1 = (b3 ? v[5] : v[1]) + __shfl_xor_sync(kFull, b3 ? v[1] : v[5], 8);
+  float k2 = (b3 ? v[6] : v[2]) + __shfl_xor_sync(kFull, b3 ? v[2] : v[6], 8);
+  float k3 = (b3 ? v[7] : v[3]) + __shfl_xor_sync(kFull, b3 ? v[3] : v[7], 8);
+  float m0 = (b2 ? k2 : k0) + __shfl_xor_sync(kFull, b2 ? k0 : k2, 4);
+  float m1 = (b2 ? k3 : k1) + __shfl_xor_sync(kFull, b2 ? k1 : k3, 4);
+  float s = (b1 ? m1 : m0) + __shfl_xor_sync(kFull, b1 ? m0 : m1, 2);
+  s += __shfl_xor_sync(kFull, s, 1);
+  return s;
+}
+
+// The backward of one tile in the half-warp layout (same per-pixel
+// arithmetic as bwd_tile): each half walks its own list back to front from
+// its own last contributor, and a half's contributions to one Gaussian are
+// reduced over its 16 lanes (or added by its few contributing lanes).
+template <int NT, int BATCH, bool LOSS>
+__device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos, const float* __restrict__ dL_dimg,
+                                              const float* __restrict__ dL_dT, const float* __restrict__ pix_T,
+                                              const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
+                                              float4* __restrict__ face_grad, const BwdLoss& bl) {
+  constexpr int TS = 16;
+  using HM = HalfMap<NT>;
+  constexpr int PPT = HM::PPT;
+  constexpr int NW = NT / 32;
+  __shared__ Stage<BATCH, 2 * NW> st;
+  __shared__ uint32_t s_maxlast;
+  const uint4 desc = __ldg(a.tile_desc + pos);
+  const int g = (int)desc.x;
+  const int c = (int)desc.y;
+  if (threadIdx.x == 0) s_maxlast = 0;
+  __syncthreads();
+  const ViewInfo& v = a.views[c];
+  const int lt = g - v.tile_base;
+  const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
+  const int ox = txi * TS, oy = tyi * TS;
+  const int axi = ox & ~31, ayi = oy & ~31;
+  const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
+  const int lane = threadIdx.x & 31;
+  const int hl = HM::half();
+
+  float pcx[PPT], pcy[PPT], T[PPT], SG[PPT], G0[PPT], G1[PPT], G2[PPT];
+  uint32_t last[PPT];
+  uint32_t tmax = 0;
+  float lsum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    int lx, ly;
+    HM::local(k, lx, ly);
+    int px = ox + lx, py = oy + ly;
+    pcx[k] = (float)(px - axi) + 0.5f;
+    pcy[k] = (float)(py - ayi) + 0.5f;
+    bool inside = px < v.W && py < v.H;
+    float gT;
+    if (inside) {
+      int64_t pid = v.pix_base + (int64_t)py * v.W + px;
+      T[k] = pix_T[pid];
+      last[k] = pix_last[pid];
+      if (LOSS) {
+        const float d0 = bl.img[3 * pid] - bl.target[3 * pid];
+        const float d1 = bl.img[3 * pid + 1] - bl.target[3 * pid + 1];
+        const float d2 = bl.img[3 * pid + 2] - bl.target[3 * pid + 2];
+        G0[k] = 2.0f * d0;
+        G1[k] = 2.0f * d1;
+        G2[k] = 2.0f * d2;
+        lsum = fmaf(d0, d0, lsum);
+        lsum = fmaf(d1, d1, lsum);
+        lsum = fmaf(d2, d2, lsum);
+      } else if (dL_dimg) {
+        G0[k] = dL_dimg[3 * pid];
+        G1[k] = dL_dimg[3 * pid + 1];
+        G2[k] = dL_dimg[3 * pid + 2];
+      } else {
+        G0[k] = G1[k] = G2[k] = 0.0f;
+      }
+      gT = dL_dT ? dL_dT[pid] : 0.0f;
+    } else {
+      T[k] = 1.0f;
+      last[k] = 0;
+      G0[k] = G1[k] = G2[k] = 0.0f;
+      gT = 0.0f;
+    }
+    SG[k] = T[k] * (a.bg0 * G0[k] + a.bg1 * G1[k] + a.bg2 * G2[k] + gT);
+    tmax = max(tmax, last[k]);
+  }
+  // last contributors: per half (the list limits) and over the CTA
+  uint32_t hmax = tmax;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) hmax = max(hmax, __shfl_xor_sync(kFull, hmax, o));
+  const int limit_lo = (int)__shfl_sync(kFull, hmax, 0), limit_hi = (int)__shfl_sync(kFull, hmax, 16);
+  if (lane == 0) atomicMax(&s_maxlast, (uint32_t)max(limit_lo, limit_hi));
+  __shared__ float s_lsum[LOSS ? NW : 1];
+  if (LOSS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
+    if (lane == 0) s_lsum[threadIdx.x >> 5] = lsum;
+  }
+  __syncthreads();
+  if (LOSS && threadIdx.x == 0) {
+    float b[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) b[w] = s_lsum[w];
+#pragma unroll
+    for (int h = 1; h < NW; h <<= 1)
+#pragma unroll
+      for (int w = 0; w + h < NW; w += 2 * h) b[w] += b[w + h];
+    bl.part[g] = b[0];
+  }
+  const int end_all = (int)s_maxlast;
+  const uint2 range = make_uint2(desc.z, desc.w);
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t bits_lo = HM::bits_of(2 * warp), bits_hi = HM::bits_of(2 * warp + 1);
+  unsigned long long evals = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) evals += last[k];
+
+  for (int end = end_all; end > 0; end -= BATCH) {
+    const int start = max(0, end - BATCH);
+    __syncthreads();
+    stage_batch<TS, NT, BATCH, 2 * NW>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
+                                       a.col, a.col_by_rec != 0, ax, ay, tox, toy, true, true);
+    __syncthreads();
+    int n_max;
+    const int nl = half_lists<BATCH>(st.list, st.mask, end - start, start, limit_lo, limit_hi, bits_lo, bits_hi,
+                                     n_max);
+    for (int jj = n_max - 1; jj >= 0; --jj) {
+      const bool act = jj < nl;
+      const int j = act ? st.list[hl][jj] : 0;
+      const int pos_j = start + j;
+      const float4 hh = st.h[j];
+      const float4 gg = st.g[j];
+      float p2[PPT], dxs[PPT], dys[PPT];
+      bool con[PPT];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
+        con[k] = act && ((uint32_t)pos_j < last[k]) && !(p2[k] < hh.y);
+        any |= con[k];
+      }
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (any) {
+        const float4 col = st.col[j];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (!con[k]) continue;
+          float graw;
+          float alpha = gauss_alpha(p2[k], hh.z, graw);
+          float om = __fsub_rn(1.0f, alpha);
+          float inv = rcp_refined(om);
+          float Tb = T[k] * inv;
+          float w = alpha * Tb;
+          float cg = col.x * G0[k] + col.y * G1[k] + col.z * G2[k];
+          float dalpha = inv * __fmaf_rn(T[k], cg, -SG[k]);
+          SG[k] += w * cg;
+          T[k] = Tb;
+          float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
+          float qx = dq * dxs[k], qy = dq * dys[k];
+          acc[0] += qx;
+          acc[1] += qy;
+          acc[2] += qx * dxs[k];
+          acc[3] += qx * dys[k];
+          acc[4] += qy * dys[k];
+          acc[5] += dq;
+          acc[6] += w * G0[k];
+          acc[7] += w * G1[k];
+          acc[8] += w * G2[k];
+        }
+      }
+      const uint32_t cm = __ballot_sync(kFull, any);
+      if (cm == 0u) continue;
+      const uint32_t cm_half = (lane & 16) ? (cm >> 16) : (cm & 0xffffu);
+      const uint32_t ci = a.col_by_rec ? st.rid[j] : st.face[j];
+      if (__popc(cm & 0xffffu) <= kBwdDirectLanes / 2 && __popc(cm >> 16) <= kBwdDirectLanes / 2) {
+        if (any) {
+          float4* rg = rec_grad + 2 * (size_t)st.rid[j];
+          atomicAdd(rg, make_float4(acc[0], acc[1], acc[2], acc[3]));
+          atomicAdd(reinterpret_cast<float*>(rg + 1), acc[4]);
+          atomicAdd(face_grad + ci, make_float4(acc[6], acc[7], acc[8], acc[5]));
+        }
+        continue;
+      }
+      float s8 = acc[8];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) s8 += __shfl_xor_sync(kFull, s8, o);
+      const float sv = half_reduce8_transposed(acc, lane);
+      if (cm_half != 0u) {  // this half's entry received contributions
+        const int l16 = lane & 15;
+        if ((l16 & 1) == 0) {
+          const int vi = ((l16 >> 3) & 1) * 4 + ((l16 >> 2) & 1) * 2 + ((l16 >> 1) & 1);
+          float* dst;
+          if (vi < 5) dst = reinterpret_cast<float*>(rec_grad + 2 * (size_t)st.rid[j]) + vi;
+          else if (vi == 5) dst = reinterpret_cast<float*>(face_grad + ci) + 3;
+          else dst = reinterpret_cast<float*>(face_grad + ci) + (vi - 6);
+          atomicAdd(dst, sv);
+        }
+        if (l16 == 0) atomicAdd(reinterpret_cast<float*>(face_grad + ci) + 2, s8);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(kFull, evals, o);
+  if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
+}
+
+template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST, bool HALF = false>
 __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
     k_raster_bwd(RasterArgs a, const float* __restrict__ dL_dimg, const float* __restrict__ dL_dT,
                  const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
                  float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz) {
   pdl_enter();
-  if (!PERSIST) {
+  if constexpr (HALF) {
+    static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
+    bwd_tile_half<NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+  } else if (!PERSIST) {
     bwd_tile<TS, NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   } else {
     uint32_t pos;
@@ -884,7 +1338,7 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, const Workspace& ws,
+cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_record, const Workspace& ws,
                        const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, float* images, float* t_out,
                        uint32_t* nc_out, const FwdLoss& fl, cudaStream_t s) {
@@ -894,6 +1348,14 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, con
                         : (fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false>
                            : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false>
                                      : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false>);
+  if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
+    if (half)
+      kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false, true>
+             : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false, true>
+                       : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false, true>;
+  } else {
+    if (half) return cudaErrorInvalidValue;
+  }
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
   cudaError_t e = launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
@@ -906,12 +1368,18 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, con
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t bwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, const Workspace& ws,
+cudaError_t bwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_record, const Workspace& ws,
                        const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
                        const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
   auto kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true> : k_raster_bwd<TS, NT, BATCH, false, true>)
                         : (bl.img ? k_raster_bwd<TS, NT, BATCH, true, false> : k_raster_bwd<TS, NT, BATCH, false, false>);
+  if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
+    if (half)
+      kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, true> : k_raster_bwd<TS, NT, BATCH, false, false, true>;
+  } else {
+    if (half) return cudaErrorInvalidValue;
+  }
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
   return launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
@@ -922,7 +1390,7 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, bool col_by_record, con
 
 }  // namespace
 
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, bool col_by_record,
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, bool half, bool col_by_record,
                               const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
@@ -932,7 +1400,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_FWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, col_by_record, ws, pair_face, views, C, F, bg, images,         \
+  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, half, col_by_record, ws, pair_face, views, C, F, bg, images,   \
                                t_final_out,                                                                      \
                                ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
@@ -945,7 +1413,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   return e;
 }
 
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, bool col_by_record,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, bool half, bool col_by_record,
                               const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
@@ -954,7 +1422,8 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, col_by_record, ws, pair_face, views, C, F, bg, dL_dimages,  \
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, half, col_by_record, ws, pair_face, views, C, F, bg,         \
+                               dL_dimages,                                                                       \
                                dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);

@@ -83,11 +83,14 @@ class Renderer:
     of stage names from ``STAGES``).
     persistent: run the compositing kernels as persistent grids (resident
     CTAs taking tiles from a counter) instead of one CTA per tile.
+    half_fwd / half_bwd: the half-warp layout in the forward / backward
+    compositing kernel (16-lane halves with their own 4x4-pixel units and
+    lists; 16x16 tiles with 128 or 256 threads).
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
                  sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None,
-                 persistent=False, sh_degree=0):
+                 persistent=False, sh_degree=0, half_fwd=False, half_bwd=False):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -104,7 +107,9 @@ class Renderer:
         self.cfg.bg[:] = [float(x) for x in bg]
         self.cfg.flags = ((_lib.GMR_FLAG_SYNC_CHECK if sync_check else 0) | (_lib.GMR_FLAG_PROFILE if profile else 0)
                           | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0)
-                          | (_lib.GMR_FLAG_PERSISTENT if persistent else 0))
+                          | (_lib.GMR_FLAG_PERSISTENT if persistent else 0)
+                          | (_lib.GMR_FLAG_HALF_WARP_FWD if half_fwd else 0)
+                          | (_lib.GMR_FLAG_HALF_WARP_BWD if half_bwd else 0))
         self.cfg.profile_stages = _stage_mask(profile)
         self.color_mode = color_mode
         self._ctx = ctypes.c_void_p()
@@ -149,8 +154,10 @@ class Renderer:
             if k == "sync_check":
                 self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_SYNC_CHECK) | (_lib.GMR_FLAG_SYNC_CHECK if v else 0)
                 continue
-            if k == "persistent":
-                self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_PERSISTENT) | (_lib.GMR_FLAG_PERSISTENT if v else 0)
+            flag = {"persistent": _lib.GMR_FLAG_PERSISTENT, "half_fwd": _lib.GMR_FLAG_HALF_WARP_FWD,
+                    "half_bwd": _lib.GMR_FLAG_HALF_WARP_BWD}.get(k)
+            if flag is not None:
+                self.cfg.flags = (self.cfg.flags & ~flag) | (flag if v else 0)
                 continue
             if k == "profile":
                 self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_PROFILE) | (_lib.GMR_FLAG_PROFILE if v else 0)
