@@ -42,6 +42,9 @@ WORKLOADS = {
     "icosphere6_noise_64xuneven": gi.scene_fibonacci_uneven,
     "icosphere8_perlin_16x1024": gi.scene_large,
     "icosphere7_fit_4x512": gi.scene_fit,
+    # the level-8 mesh in 2 views: a dense case small enough (about 2 GB on
+    # the device) for multi-pass profiler captures of the dense-mesh kernels
+    "icosphere8_perlin_2x1024": lambda: gi.scene_large(n_views=2),
 }
 # the optimisation-loop workload: a step is one Adam step of the fit (render
 # 4 views of 512^2, loss, backward, parameter update)
@@ -56,7 +59,7 @@ FLOPS_FWD_CONTRIB = 10
 FLOPS_BWD_CONTRIB = 59
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that
 # one ncu capture measured for the dominant kernel, per workload and launch
-# shape (tile, backward threads, batch, persistent, half-warp backward); an
+# shape (tile, backward threads, batch, persistent, backward layout); an
 # entry is removed when
 # the kernel changes after its capture.
 NCU_TRAFFIC = {("raster_bwd", "icosphere6_noise_64xuneven", (16, 128, 256, 0, 0)): 1950448128}
@@ -396,22 +399,25 @@ def run_gmr(args, ws, rank, local):
     if args.tile == "auto":
         from paper_2602_14493_b300.autotune import shape_name, tune
 
-        (tile, threads, threads_bwd, batch, persistent, half_fwd, half_bwd), tuned = tune(r, v, f, c, o, cams, target,
-                                                                                          use_cache=False)
+        (tile, threads, threads_bwd, batch, persistent, layout_fwd, layout_bwd), tuned = tune(r, v, f, c, o, cams,
+                                                                                              target, use_cache=False)
         log("autotune:", {shape_name(k): round(t, 4) for k, t in sorted(tuned.items(), key=lambda kv: kv[1])[:8]})
         # the fastest full-warp shape with one CTA per tile and as a persistent
         # grid, and the half-warp layouts the tuner tried
         full = min((k for k in tuned if k[4:] == (0, 0, 0)), key=tuned.get)
         scheduler = {"per_tile_grid_ms": tuned.get(full), "persistent_ms": tuned.get(full[:4] + (1, 0, 0)),
-                     "half_warp_ms": {shape_name(k): round(t, 4) for k, t in tuned.items() if k[5] or k[6]},
+                     "layouts_ms": {shape_name(k): round(t, 4) for k, t in tuned.items() if k[5] or k[6]},
+                     "layout_codes": "last two fields: forward, backward layout; 0 block-staged, 1 half-warp, "
+                                     "2 warp-staged",
                      "source": "autotuner, eager fwd + loss + bwd step, median of 15"}
     else:
         tile, threads, batch = int(args.tile), args.threads, args.batch
         threads_bwd = args.threads_bwd or threads
-        persistent, half_fwd, half_bwd = int(args.persistent), int(args.half_fwd), int(args.half_bwd)
+        persistent, layout_fwd, layout_bwd = int(args.persistent), int(args.layout_fwd), int(args.layout_bwd)
         scheduler = None
         r.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent),
-                     half_fwd=bool(half_fwd), half_bwd=bool(half_bwd))
+                     half_fwd=layout_fwd == 1, half_bwd=layout_bwd == 1, warp_fwd=layout_fwd == 2,
+                     warp_bwd=layout_bwd == 2)
     img, _ = r.forward(v, f, c, o, cams, want_t=False)
     torch.cuda.synchronize()
     P = r.stats()["n_pairs"]
@@ -603,7 +609,7 @@ def run_gmr(args, ws, rank, local):
     if stage_acc.get(DOMINANT):
         # duration of the dominant kernel inside the timed steps themselves
         roof = roofline_for(DOMINANT, statistics.mean(stage_acc[DOMINANT]), stats, scene, peaks, peak_kind, args,
-                            shape=(tile, threads_bwd, batch, int(persistent), int(half_bwd)))
+                            shape=(tile, threads_bwd, batch, int(persistent), int(layout_bwd)))
     else:
         roof = None
         log("no stage times were recorded")
@@ -627,8 +633,9 @@ def run_gmr(args, ws, rank, local):
         "dtype": "fp32", "data": "synthetic",
         "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
                    "form": "batched, one call for all views, CUDA graph", "tile": tile, "threads": threads, "threads_bwd": threads_bwd,
-                   "batch": batch, "persistent": bool(persistent), "half_warp_fwd": bool(half_fwd),
-                   "half_warp_bwd": bool(half_bwd),
+                   "batch": batch, "persistent": bool(persistent),
+                   "layout_fwd": ["block-staged", "half-warp", "warp-staged"][layout_fwd],
+                   "layout_bwd": ["block-staged", "half-warp", "warp-staged"][layout_bwd],
                    "shape_choice": "autotuned" if args.tile == "auto" else "fixed",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -662,7 +669,7 @@ DOMINANT = "raster_bwd"  # the step's largest kernel (compositing backward)
 def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args, shape=None):
     """Roofline entry of the dominant kernel from its live event time
     (shape: the launch shape (tile, backward threads, batch, persistent,
-    half-warp backward), which selects the recorded DRAM traffic)."""
+    backward layout), which selects the recorded DRAM traffic)."""
     E_f, E_b, K = stats["evals_fwd"], stats["evals_bwd"], stats["contribs"]
     if stage in ("raster_fwd", "raster_bwd"):
         flops = (FLOPS_EVAL * E_f + FLOPS_FWD_CONTRIB * K) if stage == "raster_fwd" else \
@@ -697,8 +704,9 @@ def main():
     ap.add_argument("--threads-bwd", type=int, default=0, help="backward threads per tile (0: as --threads)")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--persistent", type=int, default=0, help="with a fixed shape: 1 = persistent compositing grids")
-    ap.add_argument("--half-fwd", type=int, default=0, help="with a fixed shape: 1 = half-warp layout, forward")
-    ap.add_argument("--half-bwd", type=int, default=0, help="with a fixed shape: 1 = half-warp layout, backward")
+    ap.add_argument("--layout-fwd", type=int, default=0,
+                    help="with a fixed shape, forward layout: 0 block-staged, 1 half-warp, 2 warp-staged")
+    ap.add_argument("--layout-bwd", type=int, default=0, help="with a fixed shape, backward layout (as --layout-fwd)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-pixels", type=int, default=128)

@@ -148,6 +148,17 @@ typedef struct {
 #define GMR_FLAG_HALF_WARP_FWD 16
 #define GMR_FLAG_HALF_WARP_BWD 32
 
+/* With these flags the forward / backward compositing kernel uses the
+ * warp-staged layout: each warp loads the tile's list of Gaussians itself, 32
+ * at a time, keeps those that can reach its pixels and composites them, with
+ * no barrier of the thread block inside the tile (the batch size is unused).
+ * Any tile size and thread count; not with GMR_FLAG_PERSISTENT, and not
+ * together with the half-warp flag of the same direction
+ * (GMR_ERR_INVALID_ARG otherwise). Images are identical bit for bit;
+ * gradients agree up to the order of the float atomics. */
+#define GMR_FLAG_WARP_STAGE_FWD 64
+#define GMR_FLAG_WARP_STAGE_BWD 128
+
 /* Stages timed under GMR_FLAG_PROFILE. */
 typedef enum {
   GMR_STAGE_PROJECT = 0,      /* conversion fused with EWA projection, tile counts (Sec. 2.2, 2.1) */

@@ -26,15 +26,20 @@ CANDIDATES = [(16, tf, tb, b) for tf in (256, 128, 64) for tb in (256, 128, 64) 
 
 
 # A shape is (tile, forward threads, backward threads, batch, persistent,
-# half-warp forward, half-warp backward).
+# forward layout, backward layout); layouts: 0 staging by the thread block,
+# 1 half-warp, 2 staging by each warp.
+LAYOUT_CTA, LAYOUT_HALF, LAYOUT_WARP = 0, 1, 2
+
+
 def _full(shape):
     return tuple(shape) + (0,) * (7 - len(shape))
 
 
 def _apply(renderer, shape):
-    tile, threads, threads_bwd, batch, persistent, half_fwd, half_bwd = _full(shape)
+    tile, threads, threads_bwd, batch, persistent, lf, lb = _full(shape)
     renderer.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent),
-                        half_fwd=bool(half_fwd), half_bwd=bool(half_bwd))
+                        half_fwd=lf == LAYOUT_HALF, half_bwd=lb == LAYOUT_HALF, warp_fwd=lf == LAYOUT_WARP,
+                        warp_bwd=lb == LAYOUT_WARP)
 
 
 def shape_name(shape) -> str:
@@ -75,11 +80,12 @@ def _store(d):
 
 def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates=CANDIDATES, use_cache=True):
     """Times each candidate shape on this workload with one CTA per tile;
-    then, from the fastest, the half-warp layout in the forward and in the
-    backward (128 and 256 threads each, separately, then together), and the
-    fastest full-warp shape as a persistent grid; configures ``renderer``
-    with the fastest of all. Returns (best (tile, threads, threads_bwd,
-    batch, persistent, half_fwd, half_bwd), {shape: median ms})."""
+    then, from the fastest, the half-warp and the warp-staged layouts in the
+    forward and in the backward (128 and 256 threads each, separately, then
+    the best of each direction together), and the fastest block-staged shape
+    as a persistent grid; configures ``renderer`` with the fastest of all.
+    Returns (best (tile, threads, threads_bwd, batch, persistent,
+    forward layout, backward layout), {shape: median ms})."""
     sig = signature(faces.shape[0], cams)
     cache = _load() if use_cache else {}
     if use_cache and sig in cache and len(cache[sig]["best"]) == 7:
@@ -111,15 +117,16 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
         time_shape(_full(shape[:4]))
     best = min(results, key=results.get)
     tile, tf, tb, batch = best[:4]
-    if tile == 16:
-        fwd = [(16, t, tb, batch, 0, 1, 0) for t in (128, 256)]
-        bwd = [(16, tf, t, batch, 0, 0, 1) for t in (128, 256)]
-        for shape in fwd + bwd:
-            time_shape(shape)
-        bf = min(fwd + [best], key=results.get)
-        bb = min(bwd + [best], key=results.get)
-        if bf != best and bb != best:
-            time_shape((16, bf[1], bb[2], batch, 0, 1, 1))
+    layouts = [LAYOUT_HALF, LAYOUT_WARP] if tile == 16 else [LAYOUT_WARP]
+    threads = (128, 256) if tile == 16 else (256,)
+    fwd = [(tile, t, tb, batch, 0, lay, 0) for lay in layouts for t in threads]
+    bwd = [(tile, tf, t, batch, 0, 0, lay) for lay in layouts for t in threads]
+    for shape in fwd + bwd:
+        time_shape(shape)
+    bf = min(fwd + [best], key=results.get)
+    bb = min(bwd + [best], key=results.get)
+    if bf != best and bb != best:
+        time_shape((tile, bf[1], bb[2], batch, 0, bf[5], bb[6]))
     time_shape(tuple(best[:4]) + (1, 0, 0))
     best = min(results, key=results.get)
     _apply(renderer, best)

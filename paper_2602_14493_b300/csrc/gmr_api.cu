@@ -117,6 +117,15 @@ bool valid_config(const gmr_config* c, std::string* why) {
     if (c->tile == 32 && th != 256) { *why = "threads must be 256 with 32x32 tiles"; return false; }
   }
   if (c->batch != 64 && c->batch != 128 && c->batch != 256) { *why = "batch must be 64, 128 or 256"; return false; }
+  if (((c->flags & GMR_FLAG_HALF_WARP_FWD) && (c->flags & GMR_FLAG_WARP_STAGE_FWD)) ||
+      ((c->flags & GMR_FLAG_HALF_WARP_BWD) && (c->flags & GMR_FLAG_WARP_STAGE_BWD))) {
+    *why = "one compositing layout per direction";
+    return false;
+  }
+  if ((c->flags & (GMR_FLAG_WARP_STAGE_FWD | GMR_FLAG_WARP_STAGE_BWD)) && (c->flags & GMR_FLAG_PERSISTENT)) {
+    *why = "the warp-staged layout runs one CTA per tile (no persistent grid)";
+    return false;
+  }
   if (c->flags & (GMR_FLAG_HALF_WARP_FWD | GMR_FLAG_HALF_WARP_BWD)) {
     if (c->tile != 16 || (c->flags & GMR_FLAG_PERSISTENT)) {
       *why = "the half-warp layout needs 16x16 tiles and no persistent grid";
@@ -627,7 +636,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
     StageTimer t(ctx, GMR_STAGE_RASTER_FWD, s, cfg);
     uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
     GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
-                                         (cfg.flags & GMR_FLAG_HALF_WARP_FWD) != 0, cfg.color_mode == GMR_COLOR_SH, w,
+                                         (cfg.flags & GMR_FLAG_HALF_WARP_FWD) ? 1 : (cfg.flags & GMR_FLAG_WARP_STAGE_FWD) ? 2 : 0,
+                                         cfg.color_mode == GMR_COLOR_SH, w,
                                          w.pair_face, w.views, C, F, n_tiles, cfg.bg, images, t_final, nc, fl, s,
                                          &ctx->launches));
   }
@@ -745,7 +755,8 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   {
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
-                                         (cfg.flags & GMR_FLAG_HALF_WARP_BWD) != 0, cfg.color_mode == GMR_COLOR_SH,
+                                         (cfg.flags & GMR_FLAG_HALF_WARP_BWD) ? 1 : (cfg.flags & GMR_FLAG_WARP_STAGE_BWD) ? 2 : 0,
+                                         cfg.color_mode == GMR_COLOR_SH,
                                          w, w.pair_face, w.views, C, F, ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal,
                                          bl, bz, s, &ctx->launches));
   }

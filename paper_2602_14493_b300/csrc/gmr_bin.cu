@@ -44,8 +44,15 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 }
 
 constexpr int kPlaceThreads = 256;
+constexpr int kPlaceUnroll = 4;  // pair slots per thread and round, their loads issued together
+constexpr int kPlaceBlocksPerSm = 6;  // resident at 40 registers per thread
 
-// One thread per pair slot of the projection: key to segment start + rank.
+// Key of each pair slot of the projection to segment start + rank. The pair
+// count is known only on the device, so the grid is one wave (sized by the
+// device, not by the pair capacity: a workspace grown by a larger earlier
+// forward would otherwise launch many blocks with nothing to do) striding over
+// rounds of kPlaceUnroll slots per thread; the slot loads of a round, then
+// their gathers, are issued together, so the dependent gathers overlap.
 __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
     const unsigned long long* __restrict__ pair_tr, const uint32_t* __restrict__ pair_rec,
     const uint32_t* __restrict__ rec_key, int32_t F, const uint32_t* __restrict__ tile_start, int64_t cap,
@@ -53,13 +60,30 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
   pdl_enter();
   const int64_t n = counters->n_pairs;
   if (n > cap) return;  // overflow: the pair scratch is incomplete
-  for (int64_t i = (int64_t)blockIdx.x * kPlaceThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kPlaceThreads) {
-    const unsigned long long tr = pair_tr[i];
-    const uint32_t rid = pair_rec[i];
-    const uint32_t c = rid / (uint32_t)F;
-    const uint32_t f = rid - c * (uint32_t)F;
-    keys[tile_start[(uint32_t)(tr >> 32)] + (uint32_t)tr] = ((unsigned long long)rec_key[rid] << 32) | f;
+  constexpr int64_t kRound = (int64_t)kPlaceThreads * kPlaceUnroll;
+  for (int64_t base = (int64_t)blockIdx.x * kRound; base < n; base += (int64_t)gridDim.x * kRound) {
+    unsigned long long tr[kPlaceUnroll];
+    uint32_t rid[kPlaceUnroll], key[kPlaceUnroll], start[kPlaceUnroll];
+#pragma unroll
+    for (int u = 0; u < kPlaceUnroll; ++u) {
+      const int64_t i = base + u * kPlaceThreads + threadIdx.x;
+      tr[u] = i < n ? pair_tr[i] : 0ull;
+      rid[u] = i < n ? pair_rec[i] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kPlaceUnroll; ++u) {
+      const int64_t i = base + u * kPlaceThreads + threadIdx.x;
+      key[u] = i < n ? rec_key[rid[u]] : 0u;
+      start[u] = i < n ? tile_start[(uint32_t)(tr[u] >> 32)] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kPlaceUnroll; ++u) {
+      const int64_t i = base + u * kPlaceThreads + threadIdx.x;
+      if (i < n) {
+        const uint32_t c = rid[u] / (uint32_t)F;
+        keys[start[u] + (uint32_t)tr[u]] = ((unsigned long long)key[u] << 32) | (rid[u] - c * (uint32_t)F);
+      }
+    }
   }
 }
 
@@ -460,9 +484,11 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
                              int64_t n_tiles, cudaStream_t s, int64_t* launches) {
   if (n_rec > 0 && ws.cap_pairs > 0) {
-    // one thread per pair slot (a grid-stride loop over 148 x 8 blocks left
-    // each thread's dependent gathers in series: 13% slower on 38M pairs)
-    const int64_t blocks = (ws.cap_pairs + kPlaceThreads - 1) / kPlaceThreads;
+    // one wave: kPlaceBlocksPerSm blocks per SM (148 SMs), or fewer for a
+    // small pair capacity
+    const int64_t blocks = std::min<int64_t>((ws.cap_pairs + kPlaceThreads * kPlaceUnroll - 1) /
+                                                 (kPlaceThreads * kPlaceUnroll),
+                                             148 * kPlaceBlocksPerSm);
     cudaError_t e = launch_chained(k_place_keys, true, dim3((unsigned)blocks), dim3(kPlaceThreads), 0, s,
                                    (const unsigned long long*)ws.pair_key[1], (const uint32_t*)ws.pair_face,
                                    (const uint32_t*)ws.rec_key, F, (const uint32_t*)ws.tile_start, ws.cap_pairs,

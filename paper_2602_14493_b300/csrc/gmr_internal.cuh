@@ -495,9 +495,10 @@ struct FwdLoss {
 // Both compositing kernels read the colour of a record from ws.rec_col when
 // col_by_record (GMR_COLOR_SH), else from ws.face_col by face; the backward
 // adds colour gradients to ws.rec_cgrad or ws.face_grad likewise.
-// half: the half-warp layout (16x16 tiles, 128 or 256 threads, not with
-// persistent).
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, bool half, bool col_by_record,
+// layout: 0 staging by the CTA (full warps), 1 the half-warp layout (16x16
+// tiles, 128 or 256 threads), 2 staging by each warp; 1 and 2 not with
+// persistent.
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
                               const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
@@ -520,7 +521,7 @@ struct BwdZero {
   float* p[2] = {nullptr, nullptr};
   int64_t n[2] = {0, 0};
 };
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, bool half, bool col_by_record,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
                               const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,

@@ -268,6 +268,9 @@ __device__ __forceinline__ void loss_partial_and_finish(float v, double* __restr
 // against fl.target in the epilogue.
 constexpr int kFwdPlain = 0, kFwdDebug = 1, kFwdLoss = 2;
 
+// Compositing layouts (see the kernels).
+constexpr int kLayoutCta = 0, kLayoutHalf = 1, kLayoutWarp = 2;
+
 // Per-tile arguments of the compositing kernels.
 struct RasterArgs {
   const uint32_t* pair_face;
@@ -681,16 +684,230 @@ __device__ __forceinline__ void fwd_tile_half(const RasterArgs& a, uint32_t pos,
 
 // PERSIST: a persistent grid of resident CTAs taking positions from the
 // cursor; otherwise one CTA per position (the default: measured faster).
-// HALF: the half-warp layout (16x16 tiles, 128 or 256 threads, one CTA per
-// tile).
-template <int TS, int NT, int BATCH, int MODE, bool PERSIST, bool HALF = false>
+// ---------------------------------------------------------------- warp-staged layout
+// Each warp stages the tile's list itself, 32 entries at a time (lane l loads
+// entry c + l: face, record, colour), keeps those whose block mask reaches
+// its own blocks in warp-private shared memory, and composites them; no
+// barrier of the CTA sits inside the tile's loop, so a warp whose pixels
+// finish (or whose list is short) does not wait for the others, and the
+// backward starts each warp at its own last contributor. Same per-pixel
+// arithmetic and decisions as fwd_tile / bwd_tile. The CTA's warps load the
+// same records (mostly from L1).
+struct WarpSlots {
+  float4 g[32];   // (ux, uy, a2, b2)
+  float4 h[32];   // (c2, t2, o, 0)
+  float4 col[32]; // (r, g, b, 0)
+  uint32_t pos[32];
+  uint32_t rid[32];
+  uint32_t face[32];
+};
+
+// Stages entries [c, c + 32) of the tile's list that reach the warp's blocks
+// (and lie below `limit`) into the warp's slots, in order; returns their count.
+template <int TS>
+__device__ __forceinline__ int warp_stage(WarpSlots& ws, const RasterArgs& a, uint32_t lo, int c, int limit,
+                                          uint32_t rec_base, float ax, float ay, float tox, float toy,
+                                          uint32_t wbits) {
+  const int lane = threadIdx.x & 31;
+  const int i = c + lane;
+  bool rel = false;
+  float4 g4, h4, c4;
+  uint32_t f = 0, rid = 0;
+  if (i < limit) {
+    f = __ldg(a.pair_face + lo + i);
+    rid = rec_base + f;
+    const float4 u = __ldg(a.rec_u + rid);
+    const float4 q = __ldg(a.rec_q + rid);
+    const float4 col = __ldg(a.col + (a.col_by_rec ? rid : f));
+    const float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
+    const float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
+    rel = (block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy) & wbits) != 0u;
+    g4 = make_float4(ux, uy, q.x, q.y);
+    h4 = make_float4(q.z, q.w, col.w, 0.0f);
+    c4 = make_float4(col.x, col.y, col.z, 0.0f);
+  }
+  const uint32_t bal = __ballot_sync(kFull, rel);
+  if (rel) {
+    const int r = __popc(bal & ((1u << lane) - 1u));
+    ws.g[r] = g4;
+    ws.h[r] = h4;
+    ws.col[r] = c4;
+    ws.pos[r] = (uint32_t)i;
+    ws.rid[r] = rid;
+    ws.face[r] = f;
+  }
+  __syncwarp();
+  return __popc(bal);
+}
+
+template <int TS, int NT, int MODE>
+__device__ __forceinline__ void fwd_tile_ws(const RasterArgs& a, uint32_t pos, float* __restrict__ images,
+                                            float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
+                                            float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
+                                            int64_t n_pix_total, const FwdLoss& fl) {
+  constexpr int PPT = PixMap<TS, NT>::PPT;
+  constexpr int NW = NT / 32;
+  __shared__ WarpSlots slots[NW];
+  const uint4 desc = __ldg(a.tile_desc + pos);
+  const int g = (int)desc.x;
+  const int c = (int)desc.y;
+  const ViewInfo& v = a.views[c];
+  const int lt = g - v.tile_base;
+  const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
+  const int ox = txi * TS, oy = tyi * TS;
+  const int axi = ox & ~31, ayi = oy & ~31;
+  const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  WarpSlots& ws = slots[warp];
+
+  float pcx[PPT], pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+  __shared__ float s_tgt[MODE == kFwdLoss ? 3 * PPT * NT : 1];
+  uint32_t last[PPT], term[PPT], ncontrib[PPT], chash[PPT];
+  bool done[PPT], inside[PPT];
+  int px[PPT], py[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    int lx, ly;
+    PixMap<TS, NT>::local(k, lx, ly);
+    px[k] = ox + lx;
+    py[k] = oy + ly;
+    pcx[k] = (float)(px[k] - axi) + 0.5f;
+    pcy[k] = (float)(py[k] - ayi) + 0.5f;
+    inside[k] = px[k] < v.W && py[k] < v.H;
+    done[k] = !inside[k];
+    T[k] = 1.0f;
+    Cr[k] = Cg[k] = Cb[k] = 0.0f;
+    last[k] = 0;
+    term[k] = 0;
+    ncontrib[k] = 0;
+    chash[k] = 0;
+    if (MODE == kFwdLoss && inside[k]) {
+      const float* tp = fl.target + 3 * (v.pix_base + (int64_t)py[k] * v.W + px[k]);
+      const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&s_tgt[3 * (k * NT + threadIdx.x)]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + 4u * q), "l"(tp + q) : "memory");
+    }
+  }
+  if (MODE == kFwdLoss) asm volatile("cp.async.commit_group;" ::: "memory");
+  const uint2 range = make_uint2(desc.z, desc.w);
+  const int n = (int)(range.y - range.x);
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
+  const uint32_t wbits = PixMap<TS, NT>::warp_bits();
+
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    bool wd = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) wd &= done[k];
+    if (__all_sync(kFull, wd)) break;
+    const int nl = warp_stage<TS>(ws, a, range.x, c0, n, rec_base, ax, ay, tox, toy, wbits);
+    for (int jj = 0; jj < nl; ++jj) {
+      if ((jj & 3) == 3) {  // the warp's early exit, checked every 4 entries
+        bool wd2 = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) wd2 &= done[k];
+        if (__all_sync(kFull, wd2)) break;
+      }
+      const float4 hh = ws.h[jj];
+      const float4 gg = ws.g[jj];
+      float p2[PPT];
+      bool con[PPT];
+      bool anyc = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        float dx, dy;
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dx, dy);
+        con[k] = !done[k] && !(p2[k] < hh.y);
+        anyc |= con[k];
+      }
+      if (!anyc) continue;
+      const float4 col = ws.col[jj];
+      const uint32_t p1 = ws.pos[jj] + 1u;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (!con[k]) continue;
+        float graw;
+        float alpha = gauss_alpha(p2[k], hh.z, graw);
+        float test = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+        if (test < kTMin) {
+          done[k] = true;
+          term[k] = p1;
+          continue;
+        }
+        float w = __fmul_rn(alpha, T[k]);
+        Cr[k] = __fmaf_rn(col.x, w, Cr[k]);
+        Cg[k] = __fmaf_rn(col.y, w, Cg[k]);
+        Cb[k] = __fmaf_rn(col.z, w, Cb[k]);
+        T[k] = test;
+        last[k] = p1;
+        ++ncontrib[k];
+        if (MODE == kFwdDebug) chash[k] = chash[k] * 0x9E3779B1u + ws.face[jj] + 1u;
+      }
+    }
+    __syncwarp();  // the slots are refilled by the next chunk
+  }
+  unsigned long long evals = 0, ncon = 0;
+  float lsum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (!inside[k]) continue;
+    ncon += ncontrib[k];
+    int64_t pid = v.pix_base + (int64_t)py[k] * v.W + px[k];
+    const float i0 = Cr[k] + T[k] * a.bg0, i1 = Cg[k] + T[k] * a.bg1, i2 = Cb[k] + T[k] * a.bg2;
+    images[3 * pid] = i0;
+    images[3 * pid + 1] = i1;
+    images[3 * pid + 2] = i2;
+    if (MODE == kFwdLoss) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      const float* tg = &s_tgt[3 * (k * NT + threadIdx.x)];
+      const float d0 = i0 - tg[0], d1 = i1 - tg[1], d2 = i2 - tg[2];
+      fl.grad[3 * pid] = 2.0f * d0;
+      fl.grad[3 * pid + 1] = 2.0f * d1;
+      fl.grad[3 * pid + 2] = 2.0f * d2;
+      lsum = fmaf(d0, d0, lsum);
+      lsum = fmaf(d1, d1, lsum);
+      lsum = fmaf(d2, d2, lsum);
+    }
+    pix_T[pid] = T[k];
+    pix_last[pid] = last[k];
+    if (t_out) t_out[pid] = T[k];
+    if (MODE == kFwdDebug) {
+      nc_out[pid] = ncontrib[k];
+      nc_out[n_pix_total + pid] = chash[k];
+    }
+    evals += term[k] ? term[k] : (uint32_t)n;
+  }
+  if (MODE == kFwdLoss) asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(kFull, evals, o);
+    ncon += __shfl_xor_sync(kFull, ncon, o);
+  }
+  if (lane == 0 && evals) atomicAdd(&a.counters->evals_fwd, evals);
+  if (lane == 0 && ncon) atomicAdd(&a.counters->contribs, ncon);
+  if (MODE == kFwdLoss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
+    if (lane == 0) fl.part[(int64_t)g * NW + warp] = lsum;
+  }
+}
+
+// LAYOUT: kLayoutCta (staging by the CTA, full warps), kLayoutHalf (the
+// half-warp layout: 16x16 tiles, 128 or 256 threads) or kLayoutWarp (staging
+// by each warp); the last two with one CTA per tile.
+template <int TS, int NT, int BATCH, int MODE, bool PERSIST, int LAYOUT = kLayoutCta>
 __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value)
     k_raster_fwd(RasterArgs a, float* __restrict__ images, float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
                  float* __restrict__ t_out, uint32_t* __restrict__ nc_out, int64_t n_pix_total, FwdLoss fl) {
   pdl_enter();
-  if constexpr (HALF) {
+  if constexpr (LAYOUT == kLayoutHalf) {
     static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
     fwd_tile_half<NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
+  } else if constexpr (LAYOUT == kLayoutWarp) {
+    static_assert(!PERSIST, "warp-staged layout: one CTA per tile");
+    fwd_tile_ws<TS, NT, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
   } else if (!PERSIST) {
     fwd_tile<TS, NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
   } else {
@@ -1170,15 +1387,190 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
   if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
 }
 
-template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST, bool HALF = false>
+template <int TS, int NT, bool LOSS>
+__device__ __forceinline__ void bwd_tile_ws(const RasterArgs& a, uint32_t pos, const float* __restrict__ dL_dimg,
+                                            const float* __restrict__ dL_dT, const float* __restrict__ pix_T,
+                                            const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
+                                            float4* __restrict__ face_grad, const BwdLoss& bl) {
+  constexpr int PPT = PixMap<TS, NT>::PPT;
+  constexpr int NW = NT / 32;
+  __shared__ WarpSlots slots[NW];
+  const uint4 desc = __ldg(a.tile_desc + pos);
+  const int g = (int)desc.x;
+  const int c = (int)desc.y;
+  const ViewInfo& v = a.views[c];
+  const int lt = g - v.tile_base;
+  const int tyi = lt / v.tiles_x, txi = lt - tyi * v.tiles_x;
+  const int ox = txi * TS, oy = tyi * TS;
+  const int axi = ox & ~31, ayi = oy & ~31;
+  const float ax = (float)axi, ay = (float)ayi;
+  const float tox = (float)(ox - axi), toy = (float)(oy - ayi);
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  WarpSlots& ws = slots[warp];
+
+  float pcx[PPT], pcy[PPT], T[PPT], SG[PPT], G0[PPT], G1[PPT], G2[PPT];
+  uint32_t last[PPT];
+  uint32_t tmax = 0;
+  float lsum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    int lx, ly;
+    PixMap<TS, NT>::local(k, lx, ly);
+    int px = ox + lx, py = oy + ly;
+    pcx[k] = (float)(px - axi) + 0.5f;
+    pcy[k] = (float)(py - ayi) + 0.5f;
+    bool inside = px < v.W && py < v.H;
+    float gT;
+    if (inside) {
+      int64_t pid = v.pix_base + (int64_t)py * v.W + px;
+      T[k] = pix_T[pid];
+      last[k] = pix_last[pid];
+      if (LOSS) {
+        const float d0 = bl.img[3 * pid] - bl.target[3 * pid];
+        const float d1 = bl.img[3 * pid + 1] - bl.target[3 * pid + 1];
+        const float d2 = bl.img[3 * pid + 2] - bl.target[3 * pid + 2];
+        G0[k] = 2.0f * d0;
+        G1[k] = 2.0f * d1;
+        G2[k] = 2.0f * d2;
+        lsum = fmaf(d0, d0, lsum);
+        lsum = fmaf(d1, d1, lsum);
+        lsum = fmaf(d2, d2, lsum);
+      } else if (dL_dimg) {
+        G0[k] = dL_dimg[3 * pid];
+        G1[k] = dL_dimg[3 * pid + 1];
+        G2[k] = dL_dimg[3 * pid + 2];
+      } else {
+        G0[k] = G1[k] = G2[k] = 0.0f;
+      }
+      gT = dL_dT ? dL_dT[pid] : 0.0f;
+    } else {
+      T[k] = 1.0f;
+      last[k] = 0;
+      G0[k] = G1[k] = G2[k] = 0.0f;
+      gT = 0.0f;
+    }
+    SG[k] = T[k] * (a.bg0 * G0[k] + a.bg1 * G1[k] + a.bg2 * G2[k] + gT);
+    tmax = max(tmax, last[k]);
+  }
+  uint32_t wmax = tmax;  // the warp walks its list from its own last contributor
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
+  if (LOSS) {  // one FP32 partial per tile: warp sums, then thread 0 over the warps
+    __shared__ float s_lsum[NW];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(kFull, lsum, o);
+    if (lane == 0) s_lsum[warp] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) b[w] = s_lsum[w];
+#pragma unroll
+      for (int h = 1; h < NW; h <<= 1)
+#pragma unroll
+        for (int w = 0; w + h < NW; w += 2 * h) b[w] += b[w + h];
+      bl.part[g] = b[0];
+    }
+  }
+  const uint2 range = make_uint2(desc.z, desc.w);
+  const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
+  const uint32_t wbits = PixMap<TS, NT>::warp_bits();
+  unsigned long long evals = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) evals += last[k];
+
+  for (int end = (int)wmax; end > 0; end -= 32) {
+    const int c0 = max(0, end - 32);
+    const int nl = warp_stage<TS>(ws, a, range.x, c0, end, rec_base, ax, ay, tox, toy, wbits);
+    for (int jj = nl - 1; jj >= 0; --jj) {
+      const uint32_t pos_j = ws.pos[jj];
+      const float4 hh = ws.h[jj];
+      const float4 gg = ws.g[jj];
+      float p2[PPT], dxs[PPT], dys[PPT];
+      bool con[PPT];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        p2[k] = gauss_p2(gg, hh.x, pcx[k], pcy[k], dxs[k], dys[k]);
+        con[k] = (pos_j < last[k]) && !(p2[k] < hh.y);
+        any |= con[k];
+      }
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (any) {
+        const float4 col = ws.col[jj];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (!con[k]) continue;
+          float graw;
+          float alpha = gauss_alpha(p2[k], hh.z, graw);
+          float om = __fsub_rn(1.0f, alpha);
+          float inv = rcp_refined(om);
+          float Tb = T[k] * inv;
+          float w = alpha * Tb;
+          float cg = col.x * G0[k] + col.y * G1[k] + col.z * G2[k];
+          float dalpha = inv * __fmaf_rn(T[k], cg, -SG[k]);
+          SG[k] += w * cg;
+          T[k] = Tb;
+          float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
+          float qx = dq * dxs[k], qy = dq * dys[k];
+          acc[0] += qx;
+          acc[1] += qy;
+          acc[2] += qx * dxs[k];
+          acc[3] += qx * dys[k];
+          acc[4] += qy * dys[k];
+          acc[5] += dq;
+          acc[6] += w * G0[k];
+          acc[7] += w * G1[k];
+          acc[8] += w * G2[k];
+        }
+      }
+      const uint32_t cm = __ballot_sync(kFull, any);
+      if (cm == 0u) continue;
+      const uint32_t rid = ws.rid[jj];
+      const uint32_t ci = a.col_by_rec ? rid : ws.face[jj];
+      if (__popc(cm) <= kBwdDirectLanes) {
+        if (any) {
+          float4* rg = rec_grad + 2 * (size_t)rid;
+          atomicAdd(rg, make_float4(acc[0], acc[1], acc[2], acc[3]));
+          atomicAdd(reinterpret_cast<float*>(rg + 1), acc[4]);
+          atomicAdd(face_grad + ci, make_float4(acc[6], acc[7], acc[8], acc[5]));
+        }
+        continue;
+      }
+      float s8 = acc[8];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(kFull, s8, o);
+      float sv = warp_reduce8_transposed(acc, lane);
+      if ((lane & 3) == 0) {
+        int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        float* dst;
+        if (vi < 5) dst = reinterpret_cast<float*>(rec_grad + 2 * (size_t)rid) + vi;
+        else if (vi == 5) dst = reinterpret_cast<float*>(face_grad + ci) + 3;
+        else dst = reinterpret_cast<float*>(face_grad + ci) + (vi - 6);
+        atomicAdd(dst, sv);
+      }
+      if (lane == 0) atomicAdd(reinterpret_cast<float*>(face_grad + ci) + 2, s8);
+    }
+    __syncwarp();  // the slots are refilled by the next chunk
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(kFull, evals, o);
+  if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
+}
+
+template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST, int LAYOUT = kLayoutCta>
 __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
     k_raster_bwd(RasterArgs a, const float* __restrict__ dL_dimg, const float* __restrict__ dL_dT,
                  const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
                  float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz) {
   pdl_enter();
-  if constexpr (HALF) {
+  if constexpr (LAYOUT == kLayoutHalf) {
     static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
     bwd_tile_half<NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+  } else if constexpr (LAYOUT == kLayoutWarp) {
+    static_assert(!PERSIST, "warp-staged layout: one CTA per tile");
+    bwd_tile_ws<TS, NT, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   } else if (!PERSIST) {
     bwd_tile<TS, NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   } else {
@@ -1338,7 +1730,7 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_record, const Workspace& ws,
+cudaError_t fwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by_record, const Workspace& ws,
                        const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, float* images, float* t_out,
                        uint32_t* nc_out, const FwdLoss& fl, cudaStream_t s) {
@@ -1349,12 +1741,21 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_
                            : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false>
                                      : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false>);
   if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
-    if (half)
-      kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false, true>
-             : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false, true>
-                       : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false, true>;
+    if (layout == kLayoutHalf)
+      kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false, kLayoutHalf>
+             : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false, kLayoutHalf>
+                       : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false, kLayoutHalf>;
   } else {
-    if (half) return cudaErrorInvalidValue;
+    if (layout == kLayoutHalf) return cudaErrorInvalidValue;
+  }
+  if constexpr (BATCH == 256) {  // (the warp-staged layout has no batch)
+    if (layout == kLayoutWarp)
+      kern = fl.target ? k_raster_fwd<TS, NT, 256, kFwdLoss, false, kLayoutWarp>
+             : nc_out  ? k_raster_fwd<TS, NT, 256, kFwdDebug, false, kLayoutWarp>
+                       : k_raster_fwd<TS, NT, 256, kFwdPlain, false, kLayoutWarp>;
+  } else {
+    if (layout == kLayoutWarp) return fwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, ws, pair_face,
+                                                              views, C, F, bg, images, t_out, nc_out, fl, s);
   }
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
@@ -1368,17 +1769,26 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t bwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_record, const Workspace& ws,
+cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by_record, const Workspace& ws,
                        const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
                        const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
   auto kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true> : k_raster_bwd<TS, NT, BATCH, false, true>)
                         : (bl.img ? k_raster_bwd<TS, NT, BATCH, true, false> : k_raster_bwd<TS, NT, BATCH, false, false>);
   if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
-    if (half)
-      kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, true> : k_raster_bwd<TS, NT, BATCH, false, false, true>;
+    if (layout == kLayoutHalf)
+      kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, kLayoutHalf>
+                    : k_raster_bwd<TS, NT, BATCH, false, false, kLayoutHalf>;
   } else {
-    if (half) return cudaErrorInvalidValue;
+    if (layout == kLayoutHalf) return cudaErrorInvalidValue;
+  }
+  if constexpr (BATCH == 256) {  // (the warp-staged layout has no batch)
+    if (layout == kLayoutWarp)
+      kern = bl.img ? k_raster_bwd<TS, NT, 256, true, false, kLayoutWarp>
+                    : k_raster_bwd<TS, NT, 256, false, false, kLayoutWarp>;
+  } else {
+    if (layout == kLayoutWarp) return bwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, ws, pair_face,
+                                                              views, C, F, bg, dL, dLdT, bl, bz, s);
   }
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
@@ -1390,7 +1800,7 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, bool half, bool col_by_
 
 }  // namespace
 
-cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, bool half, bool col_by_record,
+cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
                               const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
@@ -1400,7 +1810,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_FWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, half, col_by_record, ws, pair_face, views, C, F, bg, images,   \
+  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, ws, pair_face, views, C, F, bg, images, \
                                t_final_out,                                                                      \
                                ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
@@ -1413,7 +1823,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   return e;
 }
 
-cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, bool half, bool col_by_record,
+cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
                               const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
@@ -1422,7 +1832,7 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, half, col_by_record, ws, pair_face, views, C, F, bg,         \
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, ws, pair_face, views, C, F, bg,       \
                                dL_dimages,                                                                       \
                                dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);

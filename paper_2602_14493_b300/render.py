@@ -86,11 +86,14 @@ class Renderer:
     half_fwd / half_bwd: the half-warp layout in the forward / backward
     compositing kernel (16-lane halves with their own 4x4-pixel units and
     lists; 16x16 tiles with 128 or 256 threads).
+    warp_fwd / warp_bwd: the warp-staged layout (each warp stages the
+    tile's list itself, no block-wide barrier inside a tile).
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
                  sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None,
-                 persistent=False, sh_degree=0, half_fwd=False, half_bwd=False):
+                 persistent=False, sh_degree=0, half_fwd=False, half_bwd=False, warp_fwd=False,
+                 warp_bwd=False):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -109,7 +112,9 @@ class Renderer:
                           | (_lib.GMR_FLAG_DEBUG_COUNTS if debug_counts else 0)
                           | (_lib.GMR_FLAG_PERSISTENT if persistent else 0)
                           | (_lib.GMR_FLAG_HALF_WARP_FWD if half_fwd else 0)
-                          | (_lib.GMR_FLAG_HALF_WARP_BWD if half_bwd else 0))
+                          | (_lib.GMR_FLAG_HALF_WARP_BWD if half_bwd else 0)
+                          | (_lib.GMR_FLAG_WARP_STAGE_FWD if warp_fwd else 0)
+                          | (_lib.GMR_FLAG_WARP_STAGE_BWD if warp_bwd else 0))
         self.cfg.profile_stages = _stage_mask(profile)
         self.color_mode = color_mode
         self._ctx = ctypes.c_void_p()
@@ -155,7 +160,8 @@ class Renderer:
                 self.cfg.flags = (self.cfg.flags & ~_lib.GMR_FLAG_SYNC_CHECK) | (_lib.GMR_FLAG_SYNC_CHECK if v else 0)
                 continue
             flag = {"persistent": _lib.GMR_FLAG_PERSISTENT, "half_fwd": _lib.GMR_FLAG_HALF_WARP_FWD,
-                    "half_bwd": _lib.GMR_FLAG_HALF_WARP_BWD}.get(k)
+                    "half_bwd": _lib.GMR_FLAG_HALF_WARP_BWD, "warp_fwd": _lib.GMR_FLAG_WARP_STAGE_FWD,
+                    "warp_bwd": _lib.GMR_FLAG_WARP_STAGE_BWD}.get(k)
             if flag is not None:
                 self.cfg.flags = (self.cfg.flags & ~flag) | (flag if v else 0)
                 continue

@@ -30,11 +30,14 @@ def _uneven():
 
 
 def test_image_invariant_to_tile_and_batch_size():
+    """Every launch shape, the half-warp layout included, takes the same
+    decisions with the same arithmetic per pixel: identical images."""
     s = _uneven()
     ref = None
-    for tile, threads in ((16, 256), (16, 128), (16, 64), (32, 256)):
+    for tile, threads, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (16, 256, 1), (16, 128, 1),
+                               (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2)):
         for batch in (64, 128, 256):
-            r = _renderer(tile=tile, batch=batch, threads=threads)
+            r = _renderer(tile=tile, batch=batch, threads=threads, half_fwd=lay == 1, warp_fwd=lay == 2)
             _, img, T = render_gpu(r, s)
             a = img.cpu().numpy()
             if ref is None:
@@ -45,13 +48,16 @@ def test_image_invariant_to_tile_and_batch_size():
 
 
 def test_gradients_invariant_to_backward_shape():
-    """The backward's launch shape changes only the order of the float
-    atomics, so gradients agree to rounding across all shapes."""
+    """The backward's launch shape (the half-warp layout included) changes
+    only the order of the float atomics, so gradients agree to rounding
+    across all shapes."""
     s = _uneven()
     ref = None
-    for tile, threads_bwd in ((16, 256), (16, 128), (16, 64), (32, 256)):
+    for tile, threads_bwd, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (16, 256, 1),
+                                   (16, 128, 1), (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2)):
         for batch in (64, 256):
-            r = _renderer(tile=tile, batch=batch, threads=256, threads_bwd=threads_bwd)
+            r = _renderer(tile=tile, batch=batch, threads=256, threads_bwd=threads_bwd, half_bwd=lay == 1,
+                          warp_bwd=lay == 2)
             _, img, T = render_gpu(r, s)
             g = torch.sin(torch.arange(img.numel(), device=DEV, dtype=torch.float32)).reshape(img.shape)
             got = [x.cpu().numpy().copy() for x in r.backward(g.contiguous())]
@@ -295,6 +301,13 @@ def test_host_side_argument_errors():
     from paper_2602_14493_b300 import GmrError, _lib
 
     r = _renderer()
+    for bad in (dict(tile=32, threads=256, threads_bwd=256, half_fwd=True), dict(threads=64, half_fwd=True),
+                dict(threads_bwd=64, half_bwd=True), dict(persistent=True, half_bwd=True),
+                dict(persistent=True, warp_fwd=True), dict(half_fwd=True, warp_fwd=True)):
+        with pytest.raises(GmrError):
+            r.set_config(**bad)
+        r.set_config(tile=16, threads=128, threads_bwd=128, half_fwd=False, half_bwd=False, warp_fwd=False,
+                     warp_bwd=False, persistent=False)
     s = gi.scene_single_view(level=1, width=16, height=16)
     v, f, c, o = to_dev(s)
     # backward before any forward

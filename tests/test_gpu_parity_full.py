@@ -8,7 +8,8 @@ the FP64 oracle computes one by one:
 * 16 views of 1024^2 of a level-8 icosphere (1.31M faces) with Perlin
   displacement, in one batched call, in the benchmark's launch shape;
 
-each also with the compositing kernels as persistent grids.
+each also with the compositing kernels as persistent grids, in the
+half-warp layout and in the warp-staged layout.
 
 Images: max abs error 1e-5 on pixels whose discrete decisions are not in the
 ambiguity bands. Gradients: dL/dI is non-zero on the sampled pixels only, so
@@ -49,7 +50,9 @@ def _check(scene, shapes, n_random, window, seed):
     for shape in shapes:
         tile, threads, threads_bwd = shape[:3]
         persistent = len(shape) > 3 and bool(shape[3])
-        r = Renderer(tile=tile, threads=threads, threads_bwd=threads_bwd, persistent=persistent)
+        lay = shape[4] if len(shape) > 4 else 0
+        r = Renderer(tile=tile, threads=threads, threads_bwd=threads_bwd, persistent=persistent, half_fwd=lay == 1,
+                     half_bwd=lay == 1, warp_fwd=lay == 2, warp_bwd=lay == 2)
         img, T = r.forward(v, f, c, o, scene.cams)
         dv, dc, do = r.backward(g)
         torch.cuda.synchronize()
@@ -66,10 +69,12 @@ def _check(scene, shapes, n_random, window, seed):
 def test_fibonacci_64_uneven_views_full_size():
     s = gi.scene_fibonacci_uneven()
     assert len(s.cams) == 64 and s.n_pixels > 20_000_000
-    _check(s, ((16, 128, 128), BENCH_SHAPE, (32, 256, 256), BENCH_SHAPE + (1,)), n_random=256, window=4, seed=301)
+    _check(s, ((16, 128, 128), BENCH_SHAPE, (32, 256, 256), BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1),
+               BENCH_SHAPE + (0, 2)), n_random=256, window=4, seed=301)
 
 
 def test_large_mesh_16_views_1024_full_size():
     s = gi.scene_large()
     assert len(s.faces) == 1_310_720 and s.n_pixels == 16 * 1024 * 1024
-    _check(s, (BENCH_SHAPE, BENCH_SHAPE + (1,)), n_random=128, window=4, seed=401)
+    _check(s, (BENCH_SHAPE, BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1), BENCH_SHAPE + (0, 2)), n_random=128, window=4,
+           seed=401)
