@@ -243,12 +243,26 @@ __device__ __forceinline__ float dot3_rn(const float* r, float x, float y, float
   return __fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)), __fmul_rn(r[2], z));
 }
 
-__device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, const ViewInfo& v, int tile,
-                                              float inv_tile) {
+// The view-independent part of the specification: centroid and edges.
+struct BinFace {
+  float mx, my, mz;
+  float e1x, e1y, e1z, e2x, e2y, e2z;
+};
+__device__ __forceinline__ BinFace bin_face(float3 a, float3 b, float3 c) {
+  BinFace q;
+  q.mx = __fdiv_rn(__fadd_rn(__fadd_rn(a.x, b.x), c.x), 3.0f);
+  q.my = __fdiv_rn(__fadd_rn(__fadd_rn(a.y, b.y), c.y), 3.0f);
+  q.mz = __fdiv_rn(__fadd_rn(__fadd_rn(a.z, b.z), c.z), 3.0f);
+  q.e1x = __fsub_rn(b.x, a.x); q.e1y = __fsub_rn(b.y, a.y); q.e1z = __fsub_rn(b.z, a.z);
+  q.e2x = __fsub_rn(c.x, a.x); q.e2y = __fsub_rn(c.y, a.y); q.e2z = __fsub_rn(c.z, a.z);
+  return q;
+}
+
+// The per-view part, from bin_face's result (the same operations in the same
+// order as if computed from the vertices here).
+__device__ __forceinline__ BinResult bin_view(const BinFace& q, const ViewInfo& v, int tile, float inv_tile) {
   BinResult r;
-  float mx = __fdiv_rn(__fadd_rn(__fadd_rn(a.x, b.x), c.x), 3.0f);
-  float my = __fdiv_rn(__fadd_rn(__fadd_rn(a.y, b.y), c.y), 3.0f);
-  float mz = __fdiv_rn(__fadd_rn(__fadd_rn(a.z, b.z), c.z), 3.0f);
+  const float mx = q.mx, my = q.my, mz = q.mz;
   float tx = __fadd_rn(dot3_rn(v.R + 0, mx, my, mz), v.t[0]);
   float ty = __fadd_rn(dot3_rn(v.R + 3, mx, my, mz), v.t[1]);
   float tz = __fadd_rn(dot3_rn(v.R + 6, mx, my, mz), v.t[2]);
@@ -257,12 +271,10 @@ __device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, cons
   float fyy = __fmul_rn(v.fy, ty);
   float ux = __fadd_rn(__fdiv_rn(fxx, tz), v.cx);
   float uy = __fadd_rn(__fdiv_rn(fyy, tz), v.cy);
-  float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
-  float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
-  float q1x = dot3_rn(v.R + 0, e1x, e1y, e1z), q1y = dot3_rn(v.R + 3, e1x, e1y, e1z),
-        q1z = dot3_rn(v.R + 6, e1x, e1y, e1z);
-  float q2x = dot3_rn(v.R + 0, e2x, e2y, e2z), q2y = dot3_rn(v.R + 3, e2x, e2y, e2z),
-        q2z = dot3_rn(v.R + 6, e2x, e2y, e2z);
+  float q1x = dot3_rn(v.R + 0, q.e1x, q.e1y, q.e1z), q1y = dot3_rn(v.R + 3, q.e1x, q.e1y, q.e1z),
+        q1z = dot3_rn(v.R + 6, q.e1x, q.e1y, q.e1z);
+  float q2x = dot3_rn(v.R + 0, q.e2x, q.e2y, q.e2z), q2y = dot3_rn(v.R + 3, q.e2x, q.e2y, q.e2z),
+        q2z = dot3_rn(v.R + 6, q.e2x, q.e2y, q.e2z);
   float zz = __fmul_rn(tz, tz);
   float j00 = __fdiv_rn(v.fx, tz);
   float j11 = __fdiv_rn(v.fy, tz);
@@ -290,6 +302,11 @@ __device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, cons
   if (bx0 > bx1 || by0 > by1) return r;
   r.x0 = (int)bx0; r.x1 = (int)bx1; r.y0 = (int)by0; r.y1 = (int)by1;
   return r;
+}
+
+__device__ __forceinline__ BinResult bin_spec(float3 a, float3 b, float3 c, const ViewInfo& v, int tile,
+                                              float inv_tile) {
+  return bin_view(bin_face(a, b, c), v, tile, inv_tile);
 }
 
 // Exponent of one staged Gaussian at one pixel, in log2 units:
