@@ -79,6 +79,15 @@ struct PixMap {
     lx = (b % NC) * 8 + (lane & 7);
     ly = (b / NC) * 4 + (lane >> 3);
   }
+  // The warp's rectangle of pixel centres, [x0, x1] x [y0, y1], relative to
+  // the anchor (the tile's offset from it is (tox, toy)).
+  __device__ __forceinline__ static void region(float tox, float toy, float& x0, float& x1, float& y0, float& y1) {
+    const int b0 = block(0), bc = b0 % NC, br = b0 / NC;
+    x0 = tox + (float)(8 * bc) + 0.5f;
+    x1 = tox + (float)(8 * (bc + RW)) - 0.5f;
+    y0 = toy + (float)(4 * br) + 0.5f;
+    y1 = toy + (float)(4 * (br + RH)) - 0.5f;
+  }
 };
 
 // ---------------------------------------------------------------- staging
@@ -686,8 +695,11 @@ __device__ __forceinline__ void fwd_tile_half(const RasterArgs& a, uint32_t pos,
 // cursor; otherwise one CTA per position (the default: measured faster).
 // ---------------------------------------------------------------- warp-staged layout
 // Each warp stages the tile's list itself, 32 entries at a time (lane l loads
-// entry c + l: face, record, colour), keeps those whose block mask reaches
-// its own blocks in warp-private shared memory, and composites them; no
+// entry c + l: face, record, colour), keeps those whose alpha >= 1/255
+// region reaches its own pixel rectangle (an exact test of the ellipse
+// against the rectangle, cheap here because each lane tests one entry
+// against one rectangle) in warp-private shared memory, and composites
+// them; no
 // barrier of the CTA sits inside the tile's loop, so a warp whose pixels
 // finish (or whose list is short) does not wait for the others, and the
 // backward starts each warp at its own last contributor. Same per-pixel
@@ -702,12 +714,41 @@ struct WarpSlots {
   uint32_t face[32];
 };
 
-// Stages entries [c, c + 32) of the tile's list that reach the warp's blocks
-// (and lie below `limit`) into the warp's slots, in order; returns their count.
-template <int TS>
+// Whether a Gaussian can reach alpha >= 1/255 at some point of the box
+// [x0, x1] x [y0, y1] of pixel centres (anchor-relative): the exponent
+// p2(d) = a2 dx^2 + b2 dx dy + c2 dy^2, d = mean - point, is concave, so its
+// maximum over the box is 0 at the mean when the mean lies inside, else on an
+// edge, where it is a concave parabola maximised at its clamped vertex. The
+// test passes when that maximum reaches t2 = -log2(255 o) within a margin
+// (1e-4 in log2 units plus 1e-5 of the magnitude of the exponent's terms,
+// far above the FP32 rounding of this test and of the per-pixel evaluation),
+// so culling never changes a result.
+__device__ __forceinline__ bool reaches_box(float ux, float uy, float a2, float b2, float c2, float t2, float x0,
+                                            float x1, float y0, float y1) {
+  if (!(t2 <= 0.0f)) return false;  // o < 1/255: reaches nothing
+  const float dxl = ux - x1, dxh = ux - x0, dyl = uy - y1, dyh = uy - y0;
+  if (dxl <= 0.0f && dxh >= 0.0f && dyl <= 0.0f && dyh >= 0.0f) return true;
+  bool hit = false;
+  auto test = [&](float dx, float dy) {
+    const float xx = a2 * dx * dx, xy = b2 * dx * dy, yy = c2 * dy * dy;
+    const float mag = fabsf(xx) + fabsf(xy) + fabsf(yy);
+    hit |= (xx + xy + yy) + (1e-4f + 1e-5f * mag) >= t2;
+  };
+  // edges dx = const: vertex at dy = -b2 dx / (2 c2); edges dy = const alike
+  const float ky = -0.5f * b2 / c2, kx = -0.5f * b2 / a2;
+  test(dxl, fminf(fmaxf(ky * dxl, dyl), dyh));
+  test(dxh, fminf(fmaxf(ky * dxh, dyl), dyh));
+  test(fminf(fmaxf(kx * dyl, dxl), dxh), dyl);
+  test(fminf(fmaxf(kx * dyh, dxl), dxh), dyh);
+  return hit;
+}
+
+// Stages entries [c, c + 32) of the tile's list that reach the warp's pixel
+// rectangle (and lie below `limit`) into the warp's slots, in order; returns
+// their count.
 __device__ __forceinline__ int warp_stage(WarpSlots& ws, const RasterArgs& a, uint32_t lo, int c, int limit,
-                                          uint32_t rec_base, float ax, float ay, float tox, float toy,
-                                          uint32_t wbits) {
+                                          uint32_t rec_base, float ax, float ay, float rx0, float rx1, float ry0,
+                                          float ry1) {
   const int lane = threadIdx.x & 31;
   const int i = c + lane;
   bool rel = false;
@@ -721,7 +762,7 @@ __device__ __forceinline__ int warp_stage(WarpSlots& ws, const RasterArgs& a, ui
     const float4 col = __ldg(a.col + (a.col_by_rec ? rid : f));
     const float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     const float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
-    rel = (block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy) & wbits) != 0u;
+    rel = reaches_box(ux, uy, q.x, q.y, q.z, q.w, rx0, rx1, ry0, ry1);
     g4 = make_float4(ux, uy, q.x, q.y);
     h4 = make_float4(q.z, q.w, col.w, 0.0f);
     c4 = make_float4(col.x, col.y, col.z, 0.0f);
@@ -795,14 +836,15 @@ __device__ __forceinline__ void fwd_tile_ws(const RasterArgs& a, uint32_t pos, f
   const uint2 range = make_uint2(desc.z, desc.w);
   const int n = (int)(range.y - range.x);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
-  const uint32_t wbits = PixMap<TS, NT>::warp_bits();
+  float rx0, rx1, ry0, ry1;
+  PixMap<TS, NT>::region(tox, toy, rx0, rx1, ry0, ry1);
 
   for (int c0 = 0; c0 < n; c0 += 32) {
     bool wd = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) wd &= done[k];
     if (__all_sync(kFull, wd)) break;
-    const int nl = warp_stage<TS>(ws, a, range.x, c0, n, rec_base, ax, ay, tox, toy, wbits);
+    const int nl = warp_stage(ws, a, range.x, c0, n, rec_base, ax, ay, rx0, rx1, ry0, ry1);
     for (int jj = 0; jj < nl; ++jj) {
       if ((jj & 3) == 3) {  // the warp's early exit, checked every 4 entries
         bool wd2 = true;
@@ -1475,14 +1517,15 @@ __device__ __forceinline__ void bwd_tile_ws(const RasterArgs& a, uint32_t pos, c
   }
   const uint2 range = make_uint2(desc.z, desc.w);
   const uint32_t rec_base = (uint32_t)c * (uint32_t)a.F;
-  const uint32_t wbits = PixMap<TS, NT>::warp_bits();
+  float rx0, rx1, ry0, ry1;
+  PixMap<TS, NT>::region(tox, toy, rx0, rx1, ry0, ry1);
   unsigned long long evals = 0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) evals += last[k];
 
   for (int end = (int)wmax; end > 0; end -= 32) {
     const int c0 = max(0, end - 32);
-    const int nl = warp_stage<TS>(ws, a, range.x, c0, end, rec_base, ax, ay, tox, toy, wbits);
+    const int nl = warp_stage(ws, a, range.x, c0, end, rec_base, ax, ay, rx0, rx1, ry0, ry1);
     for (int jj = nl - 1; jj >= 0; --jj) {
       const uint32_t pos_j = ws.pos[jj];
       const float4 hh = ws.h[jj];
