@@ -45,6 +45,9 @@ WORKLOADS = {
     # the level-8 mesh in 2 views: a dense case small enough (about 2 GB on
     # the device) for multi-pass profiler captures of the dense-mesh kernels
     "icosphere8_perlin_2x1024": lambda: gi.scene_large(n_views=2),
+    # the first 16 of the 64 uneven views' resolution draws: the 64-view
+    # workload's kernels at about a quarter of its size, for full captures
+    "icosphere6_noise_16xuneven": lambda: gi.scene_fibonacci_uneven(n_views=16),
 }
 # the optimisation-loop workload: a step is one Adam step of the fit (render
 # 4 views of 512^2, loss, backward, parameter update)
@@ -409,6 +412,8 @@ def run_gmr(args, ws, rank, local):
                      "layouts_ms": {shape_name(k): round(t, 4) for k, t in tuned.items() if k[5] or k[6]},
                      "layout_codes": "last two fields: forward, backward layout; 0 block-staged, 1 half-warp, "
                                      "2 warp-staged",
+                     "best_ms_per_tile": {str(t): round(min(v for k, v in tuned.items() if k[0] == t), 4)
+                                          for t in sorted({k[0] for k in tuned})},
                      "source": "autotuner, eager fwd + loss + bwd step, median of 15"}
     else:
         tile, threads, batch = int(args.tile), args.threads, args.batch
@@ -699,7 +704,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gmr", choices=["gmr", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--tile", default="auto", help="16, 32 or auto (autotuner)")
+    ap.add_argument("--tile", default="auto", help="8, 16, 32 or auto (autotuner)")
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--threads-bwd", type=int, default=0, help="backward threads per tile (0: as --threads)")
     ap.add_argument("--batch", type=int, default=256)

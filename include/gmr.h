@@ -100,9 +100,11 @@ typedef struct {
  * Gaussian that would take its transmittance below 1e-4, and a 0.3 px^2
  * low-pass term is added to every projected covariance. */
 typedef struct {
-  int32_t tile;       /* tile edge in pixels: 16 or 32 */
-  int32_t threads;    /* forward threads per tile: 64, 128 or 256 (16x16 tiles), 256
-                         (32x32); each thread composites tile^2 / threads pixels */
+  int32_t tile;       /* tile edge in pixels: 8, 16 or 32 (finer tiles give
+                         shorter lists where Gaussians cover few pixels) */
+  int32_t threads;    /* forward threads per tile: 32 or 64 (8x8 tiles), 64, 128
+                         or 256 (16x16), 256 (32x32); each thread composites
+                         tile^2 / threads pixels */
   int32_t threads_bwd; /* backward threads per tile, same choices */
   int32_t batch;      /* Gaussians staged per shared-memory batch: 64, 128 or 256 */
   int32_t cov_mode;   /* gmr_cov_mode */
@@ -217,9 +219,10 @@ GMR_API gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t*
 /* Pre-sizes the workspace for up to max_faces faces, max_views views,
  * max_pixels total pixels and max_pairs (tile, Gaussian) pairs, so that
  * later calls within these limits allocate nothing (needed before stream
- * capture). If it has to grow the workspace, the last forward's state is
- * dropped: gmr_render_bwd then returns GMR_ERR_STATE until the next
- * forward. */
+ * capture; the tile count is bounded for the configured tile size and
+ * views of sides up to 16384 px). If it has to grow the workspace, the last
+ * forward's state is dropped: gmr_render_bwd then returns GMR_ERR_STATE
+ * until the next forward. */
 GMR_API gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels,
                        int64_t max_pairs);
 

@@ -1,6 +1,7 @@
-"""Autotuner for the rasterizer's launch shape: tile size, threads per tile
-(forward and backward separately), Gaussians per shared-memory batch, and
-whether the compositing kernels run as persistent grids.
+"""Autotuner for the rasterizer's launch shape: tile size (8, 16 or 32),
+threads per tile (forward and backward separately), Gaussians per
+shared-memory batch, the compositing layout per direction, and whether the
+compositing kernels run as persistent grids.
 
 Every candidate renders the same forward + L2 loss + backward step; the
 fastest (median of CUDA-event timings after warm-up) wins. Images do not
@@ -22,7 +23,9 @@ import torch
 # layout, one CTA per tile
 CANDIDATES = [(16, tf, tb, b) for tf in (256, 128, 64) for tb in (256, 128, 64) for b in (256, 128, 64)] + [
     (32, 256, 256, 256), (32, 256, 256, 128),
-]
+] + [(8, tf, tb, b) for tf in (64, 32) for tb in (64, 32) for b in (256, 128, 64)]
+# threads per tile tried with the half-warp and warp-staged layouts
+LAYOUT_THREADS = {8: (64, 32), 16: (128, 256), 32: (256,)}
 
 
 # A shape is (tile, forward threads, backward threads, batch, persistent,
@@ -80,10 +83,11 @@ def _store(d):
 
 def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates=CANDIDATES, use_cache=True):
     """Times each candidate shape on this workload with one CTA per tile;
-    then, from the fastest, the half-warp and the warp-staged layouts in the
-    forward and in the backward (128 and 256 threads each, separately, then
-    the best of each direction together), and the fastest block-staged shape
-    as a persistent grid; configures ``renderer`` with the fastest of all.
+    then, from the fastest of each tile size among 8 and 16, the half-warp
+    (16x16 tiles) and the warp-staged layouts in the forward and in the
+    backward (each thread count of ``LAYOUT_THREADS``, separately, then the
+    best of each direction together), and the fastest block-staged shape as a
+    persistent grid; configures ``renderer`` with the fastest of all.
     Returns (best (tile, threads, threads_bwd, batch, persistent,
     forward layout, backward layout), {shape: median ms})."""
     sig = signature(faces.shape[0], cams)
@@ -115,19 +119,24 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
 
     for shape in candidates:
         time_shape(_full(shape[:4]))
-    best = min(results, key=results.get)
-    tile, tf, tb, batch = best[:4]
-    layouts = [LAYOUT_HALF, LAYOUT_WARP] if tile == 16 else [LAYOUT_WARP]
-    threads = (128, 256) if tile == 16 else (256,)
-    fwd = [(tile, t, tb, batch, 0, lay, 0) for lay in layouts for t in threads]
-    bwd = [(tile, tf, t, batch, 0, 0, lay) for lay in layouts for t in threads]
-    for shape in fwd + bwd:
-        time_shape(shape)
-    bf = min(fwd + [best], key=results.get)
-    bb = min(bwd + [best], key=results.get)
-    if bf != best and bb != best:
-        time_shape((tile, bf[1], bb[2], batch, 0, bf[5], bb[6]))
-    time_shape(tuple(best[:4]) + (1, 0, 0))
+    best_cta = min(results, key=results.get)
+    for tile in (16, 8):
+        of_tile = [k for k in results if k[0] == tile]
+        if not of_tile:
+            continue
+        base = min(of_tile, key=results.get)
+        _, tf, tb, batch = base[:4]
+        layouts = [LAYOUT_HALF, LAYOUT_WARP] if tile == 16 else [LAYOUT_WARP]
+        threads = LAYOUT_THREADS[tile]
+        fwd = [(tile, t, tb, batch, 0, lay, 0) for lay in layouts for t in threads]
+        bwd = [(tile, tf, t, batch, 0, 0, lay) for lay in layouts for t in threads]
+        for shape in fwd + bwd:
+            time_shape(shape)
+        bf = min(fwd + [base], key=results.get)
+        bb = min(bwd + [base], key=results.get)
+        if bf != base and bb != base:
+            time_shape((tile, bf[1], bb[2], batch, 0, bf[5], bb[6]))
+    time_shape(tuple(best_cta[:4]) + (1, 0, 0))
     best = min(results, key=results.get)
     _apply(renderer, best)
     if use_cache:

@@ -104,7 +104,7 @@ gmr_status cuda_fail(gmr_ctx* ctx, cudaError_t e, const char* where) {
   } while (0)
 
 bool valid_config(const gmr_config* c, std::string* why) {
-  if (c->tile != 16 && c->tile != 32) { *why = "tile must be 16 or 32"; return false; }
+  if (c->tile != 8 && c->tile != 16 && c->tile != 32) { *why = "tile must be 8, 16 or 32"; return false; }
   if (c->profile_stages >> GMR_NUM_STAGES) {
     *why = "profile_stages has bits beyond the last stage";
     return false;
@@ -115,6 +115,7 @@ bool valid_config(const gmr_config* c, std::string* why) {
       return false;
     }
     if (c->tile == 32 && th != 256) { *why = "threads must be 256 with 32x32 tiles"; return false; }
+    if (c->tile == 8 && th != 32 && th != 64) { *why = "threads must be 32 or 64 with 8x8 tiles"; return false; }
   }
   if (c->batch != 64 && c->batch != 128 && c->batch != 256) { *why = "batch must be 64, 128 or 256"; return false; }
   if (((c->flags & GMR_FLAG_HALF_WARP_FWD) && (c->flags & GMR_FLAG_WARP_STAGE_FWD)) ||
@@ -365,6 +366,10 @@ gmr_status check_cams(gmr_ctx* ctx, const gmr_camera* cams, int32_t C) {
     const gmr_camera& k = cams[c];
     if (k.width <= 0 || k.height <= 0 || k.width > (1 << 20) || k.height > (1 << 20))
       return fail(ctx, GMR_ERR_INVALID_ARG, "camera " + std::to_string(c) + ": bad image size");
+    // tile coordinates are packed in 16 bits in the projection's records
+    const int64_t ts = ctx->cfg.tile;
+    if ((k.width + ts - 1) / ts > 65536 || (k.height + ts - 1) / ts > 65536)
+      return fail(ctx, GMR_ERR_INVALID_ARG, "camera " + std::to_string(c) + ": more than 65536 tiles per side");
     const float* f = &k.R[0];
     for (int q = 0; q < 16; ++q)
       if (!std::isfinite(f[q])) return fail(ctx, GMR_ERR_INVALID_ARG, "camera " + std::to_string(c) + ": non-finite");
@@ -520,8 +525,11 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
     return s;
   if ((s = ensure_faces(ctx, max_faces, false)) != GMR_OK) return s;
   if ((s = ensure_pixels(ctx, max_pixels, false)) != GMR_OK) return s;
-  // tiles: at most one per 16x16 block plus one ragged tile per row/column and view
-  int64_t mt = max_pixels / 256 + 2 * (int64_t)max_views * 1024 + 16;
+  // tiles: at most one per tile-sized block plus one ragged tile per row and
+  // column of each view (sides up to 16384 px; a larger view grows the
+  // buffers in its forward)
+  const int64_t ts = ctx->cfg.tile;
+  int64_t mt = max_pixels / (ts * ts) + 2 * (int64_t)max_views * (16384 / ts) + 16;
   if ((s = ensure_tiles(ctx, mt, false)) != GMR_OK) return s;
   if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
   if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;

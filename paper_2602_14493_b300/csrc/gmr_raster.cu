@@ -1860,6 +1860,8 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   else GMR_FWD(16, 128, 64); else GMR_FWD(16, 128, 128); else GMR_FWD(16, 128, 256);
   else GMR_FWD(16, 64, 64); else GMR_FWD(16, 64, 128); else GMR_FWD(16, 64, 256);
   else GMR_FWD(32, 256, 64); else GMR_FWD(32, 256, 128); else GMR_FWD(32, 256, 256);
+  else GMR_FWD(8, 64, 64); else GMR_FWD(8, 64, 128); else GMR_FWD(8, 64, 256);
+  else GMR_FWD(8, 32, 64); else GMR_FWD(8, 32, 128); else GMR_FWD(8, 32, 256);
   else return cudaErrorInvalidValue;
 #undef GMR_FWD
   *launches += 1;
@@ -1882,6 +1884,8 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
   else GMR_BWD(16, 128, 64); else GMR_BWD(16, 128, 128); else GMR_BWD(16, 128, 256);
   else GMR_BWD(16, 64, 64); else GMR_BWD(16, 64, 128); else GMR_BWD(16, 64, 256);
   else GMR_BWD(32, 256, 64); else GMR_BWD(32, 256, 128); else GMR_BWD(32, 256, 256);
+  else GMR_BWD(8, 64, 64); else GMR_BWD(8, 64, 128); else GMR_BWD(8, 64, 256);
+  else GMR_BWD(8, 32, 64); else GMR_BWD(8, 32, 128); else GMR_BWD(8, 32, 256);
   else return cudaErrorInvalidValue;
 #undef GMR_BWD
   *launches += 1;

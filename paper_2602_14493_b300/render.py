@@ -64,15 +64,16 @@ def _stage_mask(profile):
 
 
 def _default_threads(tile):
-    return 256 if tile == 32 else 128
+    return {8: 64, 32: 256}.get(tile, 128)
 
 
 class Renderer:
     """One library context on the current CUDA device.
 
-    tile: 16 or 32; threads / threads_bwd: threads per tile in the forward /
-    backward (64/128/256 for 16x16 tiles, 256 for 32x32; None: 128 for 16x16
-    tiles, 256 for 32x32); batch: Gaussians per shared-memory batch (64/128/256);
+    tile: 8, 16 or 32; threads / threads_bwd: threads per tile in the forward
+    / backward (32/64 for 8x8 tiles, 64/128/256 for 16x16, 256 for 32x32;
+    None: 64, 128 and 256 respectively); batch: Gaussians per shared-memory
+    batch (64/128/256);
     cov_mode: "area" (Eq. 13) or "embed_raw" (Eq. 15 literally);
     color_mode: "face" (F x 3 colours), "vertex" (V x 3, Eq. 16) or "sh"
     (view-dependent: F x (sh_degree + 1)^2 x 3 spherical-harmonic

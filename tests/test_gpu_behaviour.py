@@ -34,8 +34,9 @@ def test_image_invariant_to_tile_and_batch_size():
     decisions with the same arithmetic per pixel: identical images."""
     s = _uneven()
     ref = None
-    for tile, threads, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (16, 256, 1), (16, 128, 1),
-                               (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2)):
+    for tile, threads, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (8, 64, 0), (8, 32, 0),
+                               (16, 256, 1), (16, 128, 1), (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2),
+                               (8, 64, 2), (8, 32, 2)):
         for batch in (64, 128, 256):
             r = _renderer(tile=tile, batch=batch, threads=threads, half_fwd=lay == 1, warp_fwd=lay == 2)
             _, img, T = render_gpu(r, s)
@@ -53,11 +54,12 @@ def test_gradients_invariant_to_backward_shape():
     across all shapes."""
     s = _uneven()
     ref = None
-    for tile, threads_bwd, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (16, 256, 1),
-                                   (16, 128, 1), (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2)):
+    for tile, threads_bwd, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (8, 64, 0), (8, 32, 0),
+                                   (16, 256, 1), (16, 128, 1), (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2),
+                                   (8, 64, 2), (8, 32, 2)):
         for batch in (64, 256):
-            r = _renderer(tile=tile, batch=batch, threads=256, threads_bwd=threads_bwd, half_bwd=lay == 1,
-                          warp_bwd=lay == 2)
+            r = _renderer(tile=tile, batch=batch, threads=64 if tile == 8 else 256, threads_bwd=threads_bwd,
+                          half_bwd=lay == 1, warp_bwd=lay == 2)
             _, img, T = render_gpu(r, s)
             g = torch.sin(torch.arange(img.numel(), device=DEV, dtype=torch.float32)).reshape(img.shape)
             got = [x.cpu().numpy().copy() for x in r.backward(g.contiguous())]
@@ -94,7 +96,7 @@ def test_fused_forward_loss_matches_separate():
     gmr_render_fwd + gmr_l2_loss; twice in a row, on views of uneven
     sizes."""
     s = _uneven()
-    for tile, threads in ((16, 256), (16, 128), (32, 256)):
+    for tile, threads in ((16, 256), (16, 128), (32, 256), (8, 64), (8, 32)):
         r = _renderer(tile=tile, threads=threads)
         (v, f, c, o), img, T = render_gpu(r, s)
         img = img.clone()
@@ -123,7 +125,7 @@ def test_backward_with_fused_loss_matches_separate():
     float atomics, the same loss up to the FP32 partial sums, on views of
     uneven sizes, for every backward shape, also with dL/dT_final."""
     s = _uneven()
-    for tile, threads in ((16, 128), (16, 256), (16, 64), (32, 256)):
+    for tile, threads in ((16, 128), (16, 256), (16, 64), (32, 256), (8, 64), (8, 32)):
         r = _renderer(tile=tile, threads=threads)
         (v, f, c, o), img, T = render_gpu(r, s)
         img, T = img.clone(), T.clone()
@@ -314,7 +316,10 @@ def test_host_side_argument_errors():
     st = r._L.gmr_render_bwd(r._ctx, ctypes.c_void_p(torch.zeros(3, device=DEV).data_ptr()), None, None, None, 0, None)
     assert st == 6  # GMR_ERR_STATE
     with pytest.raises(GmrError):
-        r.set_config(tile=8)
+        r.set_config(tile=12)
+    with pytest.raises(GmrError):
+        r.set_config(tile=8, threads=128, threads_bwd=64)
+    r.set_config(tile=16, threads=128, threads_bwd=128)
     with pytest.raises(GmrError):
         r.set_config(batch=100)
     bad = s.cams.copy()
@@ -394,7 +399,7 @@ def test_copy_h2d_kernel_copy():
     assert st == 1  # GMR_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("shape", [(16, 128, 128), (16, 256, 128), (16, 64, 256), (32, 256, 256)])
+@pytest.mark.parametrize("shape", [(16, 128, 128), (16, 256, 128), (16, 64, 256), (32, 256, 256), (8, 64, 32)])
 def test_persistent_grid_matches_per_tile_grid(shape):
     """The compositing kernels as persistent grids (resident CTAs taking
     tiles from a counter) give the same images and final T bit for bit and

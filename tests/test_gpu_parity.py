@@ -86,7 +86,7 @@ def _dense_scene():
 SORT_CLASSES = [(0, 256), (256, 512), (512, 1024), (1024, 4096), (4096, 1 << 30)]
 
 
-@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("tile", [8, 16, 32])
 @pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven", "dense6_128_256"])
 def test_binning_bit_exact(renderer, tile, name):
     s = _dense_scene() if name == "dense6_128_256" else _scenes()[name]
@@ -136,7 +136,7 @@ def test_records_match_oracle_projection(renderer):
 
 # ------------------------------------------------------------------ images
 @pytest.mark.parametrize("name", ["icosphere3_1x128", "soup", "uneven"])
-@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("tile", [8, 16, 32])
 def test_image_matches_oracle(renderer, name, tile):
     s = _scenes()[name]
     renderer.set_config(tile=tile, bg=(0.1, 0.2, 0.3))

@@ -3,13 +3,13 @@ the FP64 oracle computes one by one:
 
 * 64 views of uneven resolution (256^2 ... 1024^2, 27.4 Mpixel) of a
   level-6 icosphere with value-noise face colours, in one batched call, with
-  16x16 and 32x32 tiles (the autotuner's two tile sizes) and the launch
-  shape the benchmark times;
+  8x8, 16x16 and 32x32 tiles and the launch shapes the autotuner picks;
 * 16 views of 1024^2 of a level-8 icosphere (1.31M faces) with Perlin
-  displacement, in one batched call, in the benchmark's launch shape;
+  displacement, in one batched call, with 16x16 and 8x8 tiles;
 
 each also with the compositing kernels as persistent grids, in the
-half-warp layout and in the warp-staged layout.
+half-warp layout, in the warp-staged layout and in the autotuner's mix of
+the two (warp-staged forward, half-warp backward).
 
 Images: max abs error 1e-5 on pixels whose discrete decisions are not in the
 ambiguity bands. Gradients: dL/dI is non-zero on the sampled pixels only, so
@@ -27,9 +27,11 @@ from gpu_util import DEV, GRAD_TOL, IMG_TOL, rel_l2, sample_pixels, to_dev
 pytestmark = pytest.mark.gpu
 
 
-# launch shapes (tile, forward threads, backward threads): the default and
-# the one the autotuner picks for these workloads (the benchmark's)
+# launch shapes (tile, forward threads, backward threads[, persistent[,
+# layout of both directions | forward layout, backward layout]]); layouts:
+# 0 staging by the thread block, 1 half-warp, 2 staging by each warp
 BENCH_SHAPE = (16, 256, 128)
+TUNED_SHAPE = (16, 128, 128, 0, 2, 1)
 
 
 def _check(scene, shapes, n_random, window, seed):
@@ -50,9 +52,10 @@ def _check(scene, shapes, n_random, window, seed):
     for shape in shapes:
         tile, threads, threads_bwd = shape[:3]
         persistent = len(shape) > 3 and bool(shape[3])
-        lay = shape[4] if len(shape) > 4 else 0
-        r = Renderer(tile=tile, threads=threads, threads_bwd=threads_bwd, persistent=persistent, half_fwd=lay == 1,
-                     half_bwd=lay == 1, warp_fwd=lay == 2, warp_bwd=lay == 2)
+        lf = shape[4] if len(shape) > 4 else 0
+        lb = shape[5] if len(shape) > 5 else lf
+        r = Renderer(tile=tile, threads=threads, threads_bwd=threads_bwd, persistent=persistent, half_fwd=lf == 1,
+                     half_bwd=lb == 1, warp_fwd=lf == 2, warp_bwd=lb == 2)
         img, T = r.forward(v, f, c, o, scene.cams)
         dv, dc, do = r.backward(g)
         torch.cuda.synchronize()
@@ -70,11 +73,12 @@ def test_fibonacci_64_uneven_views_full_size():
     s = gi.scene_fibonacci_uneven()
     assert len(s.cams) == 64 and s.n_pixels > 20_000_000
     _check(s, ((16, 128, 128), BENCH_SHAPE, (32, 256, 256), BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1),
-               BENCH_SHAPE + (0, 2)), n_random=256, window=4, seed=301)
+               BENCH_SHAPE + (0, 2), TUNED_SHAPE, (8, 64, 64), (8, 32, 64, 0, 2)), n_random=256, window=4,
+           seed=301)
 
 
 def test_large_mesh_16_views_1024_full_size():
     s = gi.scene_large()
     assert len(s.faces) == 1_310_720 and s.n_pixels == 16 * 1024 * 1024
-    _check(s, (BENCH_SHAPE, BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1), BENCH_SHAPE + (0, 2)), n_random=128, window=4,
-           seed=401)
+    _check(s, (BENCH_SHAPE, BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1), BENCH_SHAPE + (0, 2), TUNED_SHAPE, (8, 64, 64),
+               (8, 64, 64, 0, 2), (8, 64, 32, 1)), n_random=128, window=4, seed=401)
