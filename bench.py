@@ -422,7 +422,7 @@ def run_gmr(args, ws, rank, local):
         scheduler = None
         r.set_config(tile=tile, threads=threads, threads_bwd=threads_bwd, batch=batch, persistent=bool(persistent),
                      half_fwd=layout_fwd == 1, half_bwd=layout_bwd == 1, warp_fwd=layout_fwd == 2,
-                     warp_bwd=layout_bwd == 2)
+                     warp_bwd=layout_bwd == 2, deterministic=bool(args.deterministic))
     img, _ = r.forward(v, f, c, o, cams, want_t=False)
     torch.cuda.synchronize()
     P = r.stats()["n_pairs"]
@@ -638,7 +638,7 @@ def run_gmr(args, ws, rank, local):
         "dtype": "fp32", "data": "synthetic",
         "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
                    "form": "batched, one call for all views, CUDA graph", "tile": tile, "threads": threads, "threads_bwd": threads_bwd,
-                   "batch": batch, "persistent": bool(persistent),
+                   "batch": batch, "persistent": bool(persistent), "deterministic": bool(args.deterministic),
                    "layout_fwd": ["block-staged", "half-warp", "warp-staged"][layout_fwd],
                    "layout_bwd": ["block-staged", "half-warp", "warp-staged"][layout_bwd],
                    "shape_choice": "autotuned" if args.tile == "auto" else "fixed",
@@ -681,7 +681,7 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args, shape=None):
                 (FLOPS_EVAL * E_b + FLOPS_BWD_CONTRIB * K)
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((stage, args.workload, shape)),
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None if args.deterministic else NCU_TRAFFIC.get((stage, args.workload, shape)),
                 "peak_source": "FP32 CUDA-core peak from unit counts and max clock (148 SM x 128 x 2 x 2.032 GHz)",
                 "ms": ms}
     # memory-type stages: algorithmic bytes per record, pair, tile and face
@@ -694,7 +694,7 @@ def roofline_for(stage, ms, stats, scene, peaks, peak_kind, args, shape=None):
     ach = byts / (ms / 1e3) / 1e9
     pk = peaks["hbm_gbs"]
     return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-            "traffic": NCU_TRAFFIC.get((stage, args.workload, shape)), "peak_source": peak_kind, "ms": ms}
+            "traffic": None if args.deterministic else NCU_TRAFFIC.get((stage, args.workload, shape)), "peak_source": peak_kind, "ms": ms}
 
 
 def main():
@@ -712,6 +712,8 @@ def main():
     ap.add_argument("--layout-fwd", type=int, default=0,
                     help="with a fixed shape, forward layout: 0 block-staged, 1 half-warp, 2 warp-staged")
     ap.add_argument("--layout-bwd", type=int, default=0, help="with a fixed shape, backward layout (as --layout-fwd)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="with a fixed shape (block-staged backward): the fixed-order backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-pixels", type=int, default=128)

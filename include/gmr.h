@@ -161,6 +161,26 @@ typedef struct {
 #define GMR_FLAG_WARP_STAGE_FWD 64
 #define GMR_FLAG_WARP_STAGE_BWD 128
 
+/* With this flag (set for the forward: the backward follows the forward's
+ * configuration) every gradient sum of the backward is formed in a fixed
+ * order, so identical inputs give bit-identical gradients (same launch
+ * shape, same device): the compositing backward writes the sums of each
+ * (tile, Gaussian) pair to the pair's own slot, adding the shares of the
+ * thread block's warps in warp order (no float atomics); the projection
+ * backward adds a record's slots in the order of its tiles and a face's
+ * records in view order; each vertex's gradient (and, with per-vertex
+ * colours, its colour gradient) is gathered over its incident faces in
+ * face order through a vertex-to-face incidence list that the backward
+ * builds. The backward then runs block-staged with at most 128 Gaussians
+ * per batch (a larger batch is taken as 128; the flag is refused together
+ * with GMR_FLAG_HALF_WARP_BWD or GMR_FLAG_WARP_STAGE_BWD) and is slower; the
+ * workspace grows by 4 bytes per record, 48 bytes per pair and 4 + 12 +
+ * 64 bytes per vertex / face. Graph capture of such a backward needs
+ * gmr_reserve (which sizes the vertex buffers for up to 3 max_faces
+ * vertices) or an earlier uncaptured backward of at least the same sizes.
+ * Images do not change. */
+#define GMR_FLAG_DETERMINISTIC 256
+
 /* Stages timed under GMR_FLAG_PROFILE. */
 typedef enum {
   GMR_STAGE_PROJECT = 0,      /* conversion fused with EWA projection, tile counts (Sec. 2.2, 2.1) */

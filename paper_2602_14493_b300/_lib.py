@@ -28,6 +28,7 @@ GMR_FLAG_HALF_WARP_FWD = 16
 GMR_FLAG_HALF_WARP_BWD = 32
 GMR_FLAG_WARP_STAGE_FWD = 64
 GMR_FLAG_WARP_STAGE_BWD = 128
+GMR_FLAG_DETERMINISTIC = 256
 GMR_L2_NOALLOC_MAX_ELEMS = 67108864
 STAGES = ["project", "scan", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
 

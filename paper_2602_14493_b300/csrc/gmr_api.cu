@@ -123,6 +123,10 @@ bool valid_config(const gmr_config* c, std::string* why) {
     *why = "one compositing layout per direction";
     return false;
   }
+  if ((c->flags & GMR_FLAG_DETERMINISTIC) && (c->flags & (GMR_FLAG_HALF_WARP_BWD | GMR_FLAG_WARP_STAGE_BWD))) {
+    *why = "the deterministic backward runs in the block-staged layout";
+    return false;
+  }
   if ((c->flags & (GMR_FLAG_WARP_STAGE_FWD | GMR_FLAG_WARP_STAGE_BWD)) && (c->flags & GMR_FLAG_PERSISTENT)) {
     *why = "the warp-staged layout runs one CTA per tile (no persistent grid)";
     return false;
@@ -283,6 +287,50 @@ gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
     if ((s = realloc_exact(ctx, &w.pair_key[b], cap, "pair_key")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.pair_face, cap, "pair_face")) != GMR_OK) return s;
   w.cap_pairs = cap;
+  return GMR_OK;
+}
+
+// GMR_FLAG_DETERMINISTIC: the records' first pair slots.
+gmr_status ensure_det_records(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_det_records) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "slot workspace must grow during stream capture; call gmr_reserve");
+  const int64_t cap = n + n / 4 + 1024;
+  gmr_status s = realloc_exact(ctx, &w.rec_slot, cap, "rec_slot");
+  if (s == GMR_OK) w.cap_det_records = cap;
+  return s;
+}
+
+// GMR_FLAG_DETERMINISTIC: the pair slots' sums (3 float4 per slot, as many
+// slots as the pair buffers hold).
+gmr_status ensure_det_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_det_pairs) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "pair-sum workspace must grow during stream capture; call gmr_reserve");
+  gmr_status s = realloc_exact(ctx, &w.pair_grad, 3 * n, "pair_grad");
+  if (s == GMR_OK) w.cap_det_pairs = n;
+  return s;
+}
+
+// GMR_FLAG_DETERMINISTIC: the vertex-to-face incidence list and the faces'
+// corner shares.
+gmr_status ensure_det_mesh(gmr_ctx* ctx, int64_t V, int64_t F, bool capturing) {
+  Workspace& w = ctx->ws;
+  gmr_status s;
+  if (V > w.cap_det_verts) {
+    if (capturing) return fail(ctx, GMR_ERR_STATE, "vertex workspace must grow during stream capture; call gmr_reserve");
+    const int64_t cap = V + V / 4 + 1024;
+    if ((s = realloc_exact(ctx, &w.v_off, cap + 1, "v_off")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.v_cur, cap, "v_cur")) != GMR_OK) return s;
+    w.cap_det_verts = cap;
+  }
+  if (F > w.cap_det_faces) {
+    if (capturing) return fail(ctx, GMR_ERR_STATE, "face workspace must grow during stream capture; call gmr_reserve");
+    const int64_t cap = F + F / 4 + 1024;
+    if ((s = realloc_exact(ctx, &w.v_inc, 3 * cap, "v_inc")) != GMR_OK) return s;
+    if ((s = realloc_exact(ctx, &w.corner_grad, 4 * cap, "corner_grad")) != GMR_OK) return s;
+    w.cap_det_faces = cap;
+  }
   return GMR_OK;
 }
 
@@ -463,7 +511,8 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
                   w.face_col,
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
                   w.tile_order, w.tile_desc,
-                  w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch};
+                  w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch,
+                  w.rec_slot, w.pair_grad, w.v_off, w.v_cur, w.v_inc, w.corner_grad};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
@@ -533,6 +582,11 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   if ((s = ensure_tiles(ctx, mt, false)) != GMR_OK) return s;
   if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
   if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;
+  if (ctx->cfg.flags & GMR_FLAG_DETERMINISTIC) {
+    if ((s = ensure_det_records(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK) return s;
+    if ((s = ensure_det_pairs(ctx, ctx->ws.cap_pairs, false)) != GMR_OK) return s;
+    if ((s = ensure_det_mesh(ctx, 3 * max_faces, max_faces, false)) != GMR_OK) return s;
+  }
   return ensure_loss(ctx, std::max<int64_t>(gmr::l2_loss_partials_needed(3 * max_pixels), 1 + mt * 4), false);
 }
 
@@ -590,6 +644,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   if ((st = ensure_pixels(ctx, n_pixels, capturing)) != GMR_OK) return st;
   if ((st = ensure_tiles(ctx, n_tiles, capturing)) != GMR_OK) return st;
   if (cfg.color_mode == GMR_COLOR_SH && (st = ensure_sh(ctx, n_rec, capturing)) != GMR_OK) return st;
+  if ((cfg.flags & GMR_FLAG_DETERMINISTIC) && (st = ensure_det_records(ctx, n_rec, capturing)) != GMR_OK) return st;
   if (fl.target) {
     // one float per forward warp after slot 0 (gmr_l2_loss's ticket counter)
     const int64_t n_warp_sums = n_tiles * (ctx->cfg.threads / 32);
@@ -616,8 +671,8 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
     {
       StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
       GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, cfg.sh_degree, w.views, C,
-                                        cfg.tile,
-                                        cfg.cov_mode, w, s, &ctx->launches));
+                                        cfg.tile, cfg.cov_mode, (cfg.flags & GMR_FLAG_DETERMINISTIC) != 0, w, s,
+                                        &ctx->launches));
     }
     {
       StageTimer t(ctx, GMR_STAGE_SCAN, s, cfg);
@@ -728,6 +783,15 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
     bl.part = reinterpret_cast<float*>(w.loss_part + 1);
   }
   const int64_t n_rec = (int64_t)F * C;
+  const bool det = (cfg.flags & GMR_FLAG_DETERMINISTIC) != 0;
+  if (det) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GMR_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
+    const bool capt = cs != cudaStreamCaptureStatusNone;
+    gmr_status st;
+    if ((st = ensure_det_pairs(ctx, w.cap_pairs, capt)) != GMR_OK) return st;
+    if ((st = ensure_det_mesh(ctx, V, F, capt)) != GMR_OK) return st;
+  }
   // The record and face gradient sums, the evaluation counter and the
   // persistent grid's cursor start at
   // zero: the forward's projection zeroed them if this backward follows it
@@ -750,7 +814,7 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   // outputs the projection backward accumulates into: zeroed by the
   // compositing backward's CTAs (or here, when it has no tiles)
   gmr::BwdZero bz;
-  if (!accumulate) {
+  if (!accumulate && !det) {  // (the deterministic gather writes every vertex)
     int k = 0;
     if (dL_dverts && V > 0) { bz.p[k] = dL_dverts; bz.n[k++] = 3 * (int64_t)V; }
     if (dL_drgb && cfg.color_mode == GMR_COLOR_PER_VERTEX && V > 0) { bz.p[k] = dL_drgb; bz.n[k++] = 3 * (int64_t)V; }
@@ -764,7 +828,7 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
                                          (cfg.flags & GMR_FLAG_HALF_WARP_BWD) ? 1 : (cfg.flags & GMR_FLAG_WARP_STAGE_BWD) ? 2 : 0,
-                                         cfg.color_mode == GMR_COLOR_SH,
+                                         cfg.color_mode == GMR_COLOR_SH, det,
                                          w, w.pair_face, w.views, C, F, ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal,
                                          bl, bz, s, &ctx->launches));
   }
@@ -780,9 +844,8 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
   {
     StageTimer t(ctx, GMR_STAGE_PROJECT_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_project_bwd(ctx->verts, V, ctx->faces, F, w.views, C, cfg.cov_mode, cfg.color_mode,
-                                          cfg.sh_degree, ctx->rgb,
-                                          ctx->opacity, w, dL_dverts, dL_drgb, dL_dopacity, accumulate, s,
-                                          &ctx->launches));
+                                          cfg.sh_degree, ctx->rgb, ctx->opacity, det, w, dL_dverts, dL_drgb,
+                                          dL_dopacity, accumulate, s, &ctx->launches));
   }
   return GMR_OK;
 }

@@ -456,6 +456,25 @@ struct Workspace {
   int32_t cap_views = 0;
   ViewInfo* views = nullptr;
   Counters* counters = nullptr;
+  // GMR_FLAG_DETERMINISTIC: per record, the first of its pair slots (the
+  // projection deals a record's pairs to consecutive slots, in the order of
+  // its tiles in its rectangle, row by row); per pair slot, the compositing
+  // backward's sums (3 float4: (sum q dx, sum q dy, sum q dx^2,
+  // sum q dx dy), (sum q dy^2, sum dq, dr, dg), (db, 0, 0, 0))
+  int64_t cap_det_records = 0;
+  uint32_t* rec_slot = nullptr;
+  int64_t cap_det_pairs = 0;
+  float4* pair_grad = nullptr;
+  // the vertex-to-face incidence list: per vertex its count, then (after the
+  // scan) its first entry (cap_det_verts + 1), a fill cursor per vertex, the
+  // entries 3 f + corner (3 per face), and per face the three corners'
+  // vertex gradients and its colour gradient share (4 float4)
+  int64_t cap_det_verts = 0;
+  uint32_t* v_off = nullptr;
+  uint32_t* v_cur = nullptr;
+  int64_t cap_det_faces = 0;
+  uint32_t* v_inc = nullptr;
+  float4* corner_grad = nullptr;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -474,13 +493,26 @@ int64_t scan_block_sums_needed(int64_t n);
 // (ws.rec_grad for all C x F records, ws.face_grad for all F faces).
 // With color_mode GMR_COLOR_SH (degree sh_degree) it writes ws.rec_col and
 // zeroes ws.rec_cgrad for every record instead of ws.face_col / face_grad.
+// det (GMR_FLAG_DETERMINISTIC): it also writes ws.rec_slot.
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int color_mode, int sh_degree, const ViewInfo* views, int32_t C,
-                           int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches);
+                           int tile, int cov_mode, bool det, Workspace& ws, cudaStream_t s, int64_t* launches);
+// det: the record sums come from the pair slots (ws.pair_grad, ws.rec_slot,
+// ws.rec_ntiles) instead of ws.rec_grad / face_grad / rec_cgrad, and the
+// vertex (and per-vertex colour) gradients are gathered over the
+// vertex-to-face incidence list (built here, in ws.v_off / v_cur / v_inc)
+// from ws.corner_grad instead of added by atomics.
 cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
                                const ViewInfo* views, int32_t C, int cov_mode, int color_mode, int sh_degree,
-                               const float* rgb, const float* opacity, const Workspace& ws, float* dverts,
+                               const float* rgb, const float* opacity, bool det, const Workspace& ws, float* dverts,
                                float* drgb, float* dop, int accumulate, cudaStream_t s, int64_t* launches);
+// gmr_det.cu: dverts (V x 3) and dcol (V x 3, per-vertex colours; either
+// may be null) from ws.corner_grad, each vertex's incident faces' shares
+// added in (face, corner) order over the incidence list built here
+// (ws.v_off, v_cur, v_inc: cap_det_verts >= V, cap_det_faces >= F);
+// accumulate: add to the outputs instead of writing them.
+cudaError_t launch_vertex_gather(const int32_t* faces, int32_t F, int32_t V, const Workspace& ws, float* dverts,
+                                 float* dcol, int accumulate, cudaStream_t s, int64_t* launches);
 cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int cov_mode, int color_mode, float* means, float* cov,
                            float* face_rgb, float* face_o, Counters* counters, cudaStream_t s, int64_t* launches);
@@ -538,8 +570,12 @@ struct BwdZero {
   float* p[2] = {nullptr, nullptr};
   int64_t n[2] = {0, 0};
 };
+// det (GMR_FLAG_DETERMINISTIC, layout 0 only; batch capped at 128): every
+// pair's sums go to its slot in ws.pair_grad (zeros for the pairs behind the
+// tile's last contributor) instead of atomics into rec_grad / face_grad /
+// rec_cgrad.
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
-                              const Workspace& ws,
+                              bool det, const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
                               const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches);

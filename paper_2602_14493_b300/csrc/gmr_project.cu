@@ -43,6 +43,40 @@ __device__ __forceinline__ float3 f3sub(float3 a, float3 b) { return make_float3
 __device__ __forceinline__ float3 f3add(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 f3scale(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ float f3dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// GMR_FLAG_DETERMINISTIC: the compositing backward's sums of each pair are
+// in the pair's slot, and a record's pairs sit in consecutive slots from
+// rec_slot[rid], in the order of its tiles; record_sums adds them in that
+// order. pair_grad == nullptr: not in this mode.
+struct DetSums {
+  const float4* pair_grad = nullptr;
+  const uint32_t* rec_slot = nullptr;
+  const uint32_t* rec_ntiles = nullptr;
+  int64_t cap_pairs = 0;
+  float4* corner_grad = nullptr;  // out: 4 per face (three corners' dL/dv, colour share)
+  // r0 = (sum q dx, sum q dy, sum q dx^2, sum q dx dy), r4 = sum q dy^2,
+  // cg = (dr, dg, db, sum dq) of record rid
+  __device__ __forceinline__ void record_sums(size_t rid, float4& r0, float& r4, float4& cg) const {
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    cg = r0;
+    r4 = 0.f;
+    const uint32_t n = __ldg(rec_ntiles + rid);
+    if (n == 0) return;
+    const int64_t s0 = __ldg(rec_slot + rid);
+    if (s0 + n > cap_pairs) return;  // pair overflow (reported by the forward): no sums
+    for (uint32_t k = 0; k < n; ++k) {
+      const float4 a = __ldg(pair_grad + 3 * (s0 + k));
+      const float4 b = __ldg(pair_grad + 3 * (s0 + k) + 1);
+      const float c = __ldg(pair_grad + 3 * (s0 + k) + 2).x;
+      r0 = f4add(r0, a);
+      r4 += b.x;
+      cg = f4add(cg, make_float4(b.z, b.w, c, b.y));
+    }
+  }
+};
 __device__ __forceinline__ float3 f3cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
@@ -257,7 +291,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
     int64_t cap_pairs, unsigned long long* __restrict__ pair_tr, uint32_t* __restrict__ pair_rec,
-    float4* __restrict__ rec_grad, float4* __restrict__ face_grad, Counters* __restrict__ counters) {
+    uint32_t* __restrict__ rec_slot, float4* __restrict__ rec_grad, float4* __restrict__ face_grad,
+    Counters* __restrict__ counters) {
   pdl_enter();
   __shared__ ViewInfo sv[kProjMaxVpt];
   __shared__ uint32_t s_off[kProjThreads / 32][32];
@@ -344,6 +379,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&counters->pair_alloc, total);
         base = __shfl_sync(0xffffffffu, base, 0);
+        if (rec_slot && live && nt > 0) rec_slot[rid] = base + (incl - nt);  // this record's first slot
         __syncwarp();
         const uint32_t tx = (uint32_t)v.tiles_x;
         const uint32_t rid0 = rid - (uint32_t)lane;
@@ -560,20 +596,21 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ rgb,
     const float* __restrict__ opacity, const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q,
     const float4* __restrict__ face_grad, const float4* __restrict__ rec_cgrad, float* __restrict__ dverts,
-    float* __restrict__ drgb, float* __restrict__ dop, int accumulate) {
+    float* __restrict__ drgb, float* __restrict__ dop, int accumulate, DetSums det) {
   pdl_enter();
   constexpr int K = L >= 0 ? (L + 1) * (L + 1) : 1;
   float dcoef[L >= 0 ? 3 * K : 1];
 #pragma unroll
   for (int k = 0; k < (L >= 0 ? 3 * K : 1); ++k) dcoef[k] = 0.0f;
   float dq_sum = 0.0f;  // view-dependent colour: sum over the views of sum dq
+  float4 fg_det = make_float4(0.f, 0.f, 0.f, 0.f);  // det: this lane's views' colour sums (dr, dg, db, dq)
   const int64_t gid = (int64_t)blockIdx.x * kProjBwdThreads + threadIdx.x;
   const int f = (int)(gid / G);
   const int sub = (int)(gid % G);
   // the first view's sums are loaded before the face and its vertices
   float4 r0n = make_float4(0.f, 0.f, 0.f, 0.f);
   float r4n = 0.f;
-  if (f < F && sub < C) {
+  if (!det.pair_grad && f < F && sub < C) {
     r0n = rec_grad[2 * ((size_t)sub * F + f)];
     r4n = rec_grad[2 * ((size_t)sub * F + f) + 1].x;
   }
@@ -593,15 +630,19 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     // the next view's sums are loaded before this view's arithmetic
     for (int c = sub; c < C; c += G) {
       const size_t rid = (size_t)c * F + f;
-      const float4 r0 = r0n;
-      const float r4 = r4n;
-      if (c + G < C) {
+      float4 r0 = r0n;
+      float r4 = r4n;
+      float4 cgd;  // det: the record's colour sums
+      if (det.pair_grad) {
+        det.record_sums(rid, r0, r4, cgd);
+        fg_det = f4add(fg_det, cgd);
+      } else if (c + G < C) {
         r0n = rec_grad[2 * (rid + (size_t)G * F)];
         r4n = rec_grad[2 * (rid + (size_t)G * F) + 1].x;
       }
       const bool geo = !(r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r4 == 0.f);
       if (L >= 0) {
-        const float4 cg = rec_cgrad[rid];
+        const float4 cg = det.pair_grad ? cgd : rec_cgrad[rid];
         dq_sum += cg.w;
         if (cg.x != 0.f || cg.y != 0.f || cg.z != 0.f)
           sh_colour_bwd<L >= 0 ? L : 0>(rgb + (size_t)f * 3 * K, g, views[c], make_float3(cg.x, cg.y, cg.z), dcoef,
@@ -621,9 +662,22 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
 #pragma unroll
       for (int k = 0; k < 3 * K; ++k) dcoef[k] = group_sum<G>(dcoef[k]);
       dq_sum = group_sum<G>(dq_sum);
+    } else if (det.pair_grad) {
+      fg_det = make_float4(group_sum<G>(fg_det.x), group_sum<G>(fg_det.y), group_sum<G>(fg_det.z),
+                           group_sum<G>(fg_det.w));
     }
   }
-  if (!ok || sub != 0) return;
+  if (f >= F || sub != 0) return;
+  if (!ok) {  // a face with an index outside [0, V): no gradient (written, unless accumulating)
+    if (!accumulate) {
+      if (drgb && L >= 0)
+        for (int k = 0; k < 3 * K; ++k) drgb[(size_t)f * 3 * K + k] = 0.0f;
+      else if (drgb && color_mode == GMR_COLOR_PER_FACE)
+        drgb[3 * f] = drgb[3 * f + 1] = drgb[3 * f + 2] = 0.0f;
+      if (dop && opacity) dop[f] = 0.0f;
+    }
+    return;
+  }
   // to vertices: d_a = v_a - mu (mu = mean of v), n from e1 x e2
   const float3 sdd = f3add(f3add(acc.dd[0], acc.dd[1]), acc.dd[2]);
   float3 dv[3];
@@ -643,7 +697,14 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     dv[2] = f3add(dv[2], de2);
   }
   const int idx[3] = {i0, i1, i2};
-  if (dverts) {
+  const float4 fg = L >= 0 ? make_float4(0.f, 0.f, 0.f, dq_sum) : det.pair_grad ? fg_det : face_grad[f];
+  if (det.pair_grad) {
+    // the vertices' shares, gathered per vertex in face order afterwards
+#pragma unroll
+    for (int k = 0; k < 3; ++k) det.corner_grad[4 * (size_t)f + k] = make_float4(dv[k].x, dv[k].y, dv[k].z, 0.f);
+    det.corner_grad[4 * (size_t)f + 3] =
+        make_float4(fg.x * (1.0f / 3.0f), fg.y * (1.0f / 3.0f), fg.z * (1.0f / 3.0f), 0.f);
+  } else if (dverts) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       atomicAdd(dverts + 3 * idx[k], dv[k].x);
@@ -651,7 +712,6 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
       atomicAdd(dverts + 3 * idx[k] + 2, dv[k].z);
     }
   }
-  const float4 fg = L >= 0 ? make_float4(0.f, 0.f, 0.f, dq_sum) : face_grad[f];
   if (drgb && L >= 0) {  // the coefficients' gradient, summed over the views (no atomics)
     float* dst = drgb + (size_t)f * 3 * K;
 #pragma unroll
@@ -663,7 +723,7 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
       } else {
         drgb[3 * f] = fg.x; drgb[3 * f + 1] = fg.y; drgb[3 * f + 2] = fg.z;
       }
-    } else {
+    } else if (!det.pair_grad) {  // (det: gathered per vertex afterwards)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         atomicAdd(drgb + 3 * idx[k], fg.x * (1.0f / 3.0f));
@@ -738,7 +798,7 @@ __global__ void k_convert(const float* __restrict__ verts, int32_t V, const int3
 
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int color_mode, int sh_degree, const ViewInfo* views, int32_t C,
-                           int tile, int cov_mode, Workspace& ws, cudaStream_t s, int64_t* launches) {
+                           int tile, int cov_mode, bool det, Workspace& ws, cudaStream_t s, int64_t* launches) {
   if (F <= 0 || C <= 0) return cudaSuccess;
   // views per thread: as many as keep about two threads per SM slot (148 SMs
   // x 2048) busy, at most kProjMaxVpt, spread evenly over the view blocks
@@ -751,15 +811,17 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
                                  color_mode, sh_degree, ws.rec_col, ws.rec_cgrad, views, tile, 1.0f / (float)tile,
                                  cov_mode, ws.rec_u, ws.rec_q,
                                  ws.rec_rect, ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
-                                 ws.pair_key[1], ws.pair_face, ws.rec_grad, ws.face_grad, ws.counters);
+                                 ws.pair_key[1], ws.pair_face, det ? ws.rec_slot : nullptr, ws.rec_grad,
+                                 ws.face_grad, ws.counters);
   *launches += 1;
   return e;
 }
 
 cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* faces, int32_t F,
                                const ViewInfo* views, int32_t C, int cov_mode, int color_mode, int sh_degree,
-                               const float* rgb, const float* opacity, const Workspace& ws, float* dverts,
-                               float* drgb, float* dop, int accumulate, cudaStream_t s, int64_t* launches) {
+                               const float* rgb, const float* opacity, bool det, const Workspace& ws,
+                               float* dverts, float* drgb, float* dop, int accumulate, cudaStream_t s,
+                               int64_t* launches) {
   if (F <= 0) return cudaSuccess;
   // lanes per face: enough threads to fill the GPU when faces are few, no
   // more lanes than views (more lanes than that repeat the per-face work and
@@ -773,12 +835,24 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
                     : L == 2 ? k_proj_bwd<G_, 2> : k_proj_bwd<G_, 3>)
   auto kern = G == 1 ? GMR_PB(1) : G == 2 ? GMR_PB(2) : G == 4 ? GMR_PB(4) : GMR_PB(8);
 #undef GMR_PB
+  DetSums ds;
+  if (det) {
+    ds.pair_grad = ws.pair_grad;
+    ds.rec_slot = ws.rec_slot;
+    ds.rec_ntiles = ws.rec_ntiles;
+    ds.cap_pairs = std::min(ws.cap_pairs, ws.cap_det_pairs);
+    ds.corner_grad = ws.corner_grad;
+  }
   cudaError_t e = launch_chained(kern, true, dim3(blocks), dim3(kProjBwdThreads), 0, s, verts, V, faces, F, C, views,
                                  cov_mode, color_mode, rgb, opacity, (const float4*)ws.rec_grad,
                                  (const float4*)ws.rec_q, (const float4*)ws.face_grad, (const float4*)ws.rec_cgrad,
-                                 dverts, drgb, dop, accumulate);
+                                 dverts, drgb, dop, accumulate, ds);
   *launches += 1;
-  return e;
+  if (e != cudaSuccess || !det) return e;
+  // per-vertex sums over the incidence list (vertex gradients, and colour
+  // gradients of a per-vertex colour)
+  return launch_vertex_gather(faces, F, V, ws, dverts, color_mode == GMR_COLOR_PER_VERTEX ? drgb : nullptr,
+                              accumulate, s, launches);
 }
 
 cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,

@@ -68,12 +68,13 @@ struct PixMap {
   }
   __device__ __forceinline__ static int block(int k) { return block_of(threadIdx.x >> 5, k); }
 
-  __device__ __forceinline__ static uint32_t warp_bits() {
+  __device__ __forceinline__ static uint32_t warp_bits_of(int warp) {
     uint32_t b = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) b |= 1u << block(k);
+    for (int k = 0; k < PPT; ++k) b |= 1u << block_of(warp, k);
     return b;
   }
+  __device__ __forceinline__ static uint32_t warp_bits() { return warp_bits_of(threadIdx.x >> 5); }
   __device__ __forceinline__ static void local(int k, int& lx, int& ly) {
     int lane = threadIdx.x & 31, b = block(k);
     lx = (b % NC) * 8 + (lane & 7);
@@ -293,6 +294,12 @@ struct RasterArgs {
   const uint4* tile_desc;
   Counters* counters;
   uint32_t n_pos;   // compositing positions (tiles)
+  // deterministic backward: per pair slot its sums (3 float4), the records'
+  // tile rectangles and first slots, the slot capacity
+  float4* pair_grad;
+  const uint2* rec_rect;
+  const uint32_t* rec_slot;
+  int64_t cap_slots;
 };
 
 // The next compositing position of a persistent grid's CTA: one atomic on
@@ -1030,15 +1037,38 @@ struct BwdMinBlocks {
   static constexpr int value = NT == 128 ? 9 : 0;
 };
 
-template <int TS, int NT, int BATCH, bool LOSS>
+// Deterministic backward: the 9 sums of one (tile, Gaussian) pair into its
+// slot, the rec_slot of the record plus the rank of the tile (tx, ty) in the
+// record's rectangle, row by row (the order in which the projection dealt
+// the record's pairs to its slots).
+__device__ __forceinline__ void det_store(const RasterArgs& a, uint32_t rid, int tx, int ty, const float* sum) {
+  const uint2 rect = __ldg(a.rec_rect + rid);
+  const int x0 = (int)(rect.x & 0xffffu), x1 = (int)(rect.x >> 16), y0 = (int)(rect.y & 0xffffu);
+  const int64_t slot = (int64_t)__ldg(a.rec_slot + rid) + (int64_t)(ty - y0) * (x1 - x0 + 1) + (tx - x0);
+  if (slot >= a.cap_slots) return;  // pair overflow (reported by the forward)
+  float4* pg = a.pair_grad + 3 * slot;
+  pg[0] = make_float4(sum[0], sum[1], sum[2], sum[3]);
+  pg[1] = make_float4(sum[4], sum[5], sum[6], sum[7]);
+  pg[2] = make_float4(sum[8], 0.0f, 0.0f, 0.0f);
+}
+
+// DET: the deterministic backward (GMR_FLAG_DETERMINISTIC): each warp
+// reduces its share of every entry of its list over its lanes (a fixed
+// shuffle tree) into shared memory, and after each batch one thread per
+// entry adds the warps' shares in warp order and stores the pair's sums to
+// its slot; pairs behind the tile's last contributor get zeros.
+template <int TS, int NT, int BATCH, bool LOSS, bool DET = false>
 __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, const float* __restrict__ dL_dimg,
                                          const float* __restrict__ dL_dT, const float* __restrict__ pix_T,
                                          const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
                                          float4* __restrict__ face_grad, const BwdLoss& bl) {
   constexpr int PPT = PixMap<TS, NT>::PPT;
   constexpr int NW = NT / 32;
+  static_assert(!DET || BATCH <= 128, "deterministic backward: at most 128 Gaussians per batch");
   __shared__ Stage<BATCH, NW> st;
   __shared__ uint32_t s_maxlast;
+  __shared__ float s_acc[DET ? NW : 1][9][DET ? BATCH : 1];  // per warp, value and entry
+  __shared__ uint32_t s_wmax[DET ? NW : 1];
   // the tile at this compositing position, its view and its pair range
   const uint4 desc = __ldg(a.tile_desc + pos);
   const int g = (int)desc.x;
@@ -1106,6 +1136,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
   if (lane == 0) atomicMax(&s_maxlast, wmax);
+  if (DET && lane == 0) s_wmax[threadIdx.x >> 5] = wmax;
   __shared__ float s_lsum[LOSS ? NT / 32 : 1];
   if (LOSS) {  // warp sums now, the CTA's partial after the barrier
 #pragma unroll
@@ -1184,6 +1215,18 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
         }
       }
       const uint32_t cm = __ballot_sync(kFull, any);
+      if (DET) {  // this warp's share of entry j (zeros when it has none)
+        float sv = 0.0f, s8 = 0.0f;
+        if (cm != 0u) {
+          s8 = acc[8];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(kFull, s8, o);
+          sv = warp_reduce8_transposed(acc, lane);
+        }
+        if ((lane & 3) == 0) s_acc[warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)][j] = sv;
+        if (lane == 0) s_acc[warp][8][j] = s8;
+        continue;
+      }
       if (cm == 0u) continue;
       // colour gradient sums: per face, or per record (view-dependent colour)
       const uint32_t ci = a.col_by_rec ? st.rid[j] : st.face[j];
@@ -1212,6 +1255,27 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
       }
       if (lane == 0) atomicAdd(reinterpret_cast<float*>(face_grad + ci) + 2, s8);
     }
+    if (DET) {
+      __syncthreads();  // every warp's shares of this batch are in s_acc
+      for (int j = threadIdx.x; j < end - start; j += NT) {
+        // the warps whose list held entry j (the test of warp_list), in order
+        float sum[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const uint32_t m = st.mask[j];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          if ((m & PixMap<TS, NT>::warp_bits_of(w)) && start + j < (int)s_wmax[w]) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) sum[q] += s_acc[w][q][j];
+          }
+        }
+        det_store(a, st.rid[j], txi, tyi, sum);
+      }
+    }
+  }
+  if (DET) {  // the pairs behind the tile's last contributor: zeros
+    const float zero[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int j = end_all + (int)threadIdx.x; j < (int)(range.y - range.x); j += NT)
+      det_store(a, rec_base + __ldg(a.pair_face + range.x + j), txi, tyi, zero);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(kFull, evals, o);
@@ -1602,11 +1666,12 @@ __device__ __forceinline__ void bwd_tile_ws(const RasterArgs& a, uint32_t pos, c
   if (lane == 0 && evals) atomicAdd(&a.counters->evals_bwd, evals);
 }
 
-template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST, int LAYOUT = kLayoutCta>
+template <int TS, int NT, int BATCH, bool LOSS, bool PERSIST, int LAYOUT = kLayoutCta, bool DET = false>
 __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
     k_raster_bwd(RasterArgs a, const float* __restrict__ dL_dimg, const float* __restrict__ dL_dT,
                  const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
                  float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz) {
+  static_assert(!DET || LAYOUT == kLayoutCta, "deterministic backward: block-staged layout");
   pdl_enter();
   if constexpr (LAYOUT == kLayoutHalf) {
     static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
@@ -1615,11 +1680,11 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
     static_assert(!PERSIST, "warp-staged layout: one CTA per tile");
     bwd_tile_ws<TS, NT, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   } else if (!PERSIST) {
-    bwd_tile<TS, NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+    bwd_tile<TS, NT, BATCH, LOSS, DET>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   } else {
     uint32_t pos;
     while (next_position(&a.counters->raster_next_bwd, a.n_pos, pos))
-      bwd_tile<TS, NT, BATCH, LOSS>(a, pos, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+      bwd_tile<TS, NT, BATCH, LOSS, DET>(a, pos, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   }
 #pragma unroll
   for (int z = 0; z < 2; ++z)
@@ -1769,6 +1834,10 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
   a.tile_desc = ws.tile_desc;
   a.counters = ws.counters;
   a.n_pos = (uint32_t)n_tiles;
+  a.pair_grad = ws.pair_grad;
+  a.rec_rect = ws.rec_rect;
+  a.rec_slot = ws.rec_slot;
+  a.cap_slots = std::min(ws.cap_pairs, ws.cap_det_pairs);
   return a;
 }
 
@@ -1812,12 +1881,24 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
 }
 
 template <int TS, int NT, int BATCH>
-cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by_record, const Workspace& ws,
+cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by_record, bool det, const Workspace& ws,
                        const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
                        const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
   auto kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true> : k_raster_bwd<TS, NT, BATCH, false, true>)
                         : (bl.img ? k_raster_bwd<TS, NT, BATCH, true, false> : k_raster_bwd<TS, NT, BATCH, false, false>);
+  if (det) {
+    if (layout != kLayoutCta || !ws.pair_grad || !ws.rec_slot) return cudaErrorInvalidValue;
+    if constexpr (BATCH <= 128) {
+      kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true, kLayoutCta, true>
+                                  : k_raster_bwd<TS, NT, BATCH, false, true, kLayoutCta, true>)
+                        : (bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, kLayoutCta, true>
+                                  : k_raster_bwd<TS, NT, BATCH, false, false, kLayoutCta, true>);
+    } else {
+      return bwd_launch<TS, NT, 128>(n_tiles, persistent, layout, col_by_record, det, ws, pair_face, views, C, F, bg,
+                                     dL, dLdT, bl, bz, s);
+    }
+  }
   if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
     if (layout == kLayoutHalf)
       kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, kLayoutHalf>
@@ -1830,8 +1911,8 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
       kern = bl.img ? k_raster_bwd<TS, NT, 256, true, false, kLayoutWarp>
                     : k_raster_bwd<TS, NT, 256, false, false, kLayoutWarp>;
   } else {
-    if (layout == kLayoutWarp) return bwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, ws, pair_face,
-                                                              views, C, F, bg, dL, dLdT, bl, bz, s);
+    if (layout == kLayoutWarp) return bwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, det, ws,
+                                                              pair_face, views, C, F, bg, dL, dLdT, bl, bz, s);
   }
   const unsigned grid =
       persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
@@ -1869,7 +1950,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
 }
 
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
-                              const Workspace& ws,
+                              bool det, const Workspace& ws,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
                               const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches) {
@@ -1877,7 +1958,7 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, ws, pair_face, views, C, F, bg,       \
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, det, ws, pair_face, views, C, F, bg,  \
                                dL_dimages,                                                                       \
                                dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);

@@ -89,12 +89,16 @@ class Renderer:
     lists; 16x16 tiles with 128 or 256 threads).
     warp_fwd / warp_bwd: the warp-staged layout (each warp stages the
     tile's list itself, no block-wide barrier inside a tile).
+    deterministic: every gradient sum of the backward in a fixed order
+    (bit-identical gradients for identical inputs and launch shape; the
+    backward runs block-staged with at most 128 Gaussians per batch, so not
+    with half_bwd or warp_bwd).
     """
 
     def __init__(self, tile=16, batch=256, cov_mode="area", color_mode="face", bg=(0.0, 0.0, 0.0),
                  sync_check=True, profile=False, threads=None, debug_counts=False, threads_bwd=None,
                  persistent=False, sh_degree=0, half_fwd=False, half_bwd=False, warp_fwd=False,
-                 warp_bwd=False):
+                 warp_bwd=False, deterministic=False):
         if not torch.cuda.is_available():
             raise _lib.GmrError("the Gaussian Mesh Renderer needs a CUDA device")
         torch.cuda.init()
@@ -115,7 +119,8 @@ class Renderer:
                           | (_lib.GMR_FLAG_HALF_WARP_FWD if half_fwd else 0)
                           | (_lib.GMR_FLAG_HALF_WARP_BWD if half_bwd else 0)
                           | (_lib.GMR_FLAG_WARP_STAGE_FWD if warp_fwd else 0)
-                          | (_lib.GMR_FLAG_WARP_STAGE_BWD if warp_bwd else 0))
+                          | (_lib.GMR_FLAG_WARP_STAGE_BWD if warp_bwd else 0)
+                          | (_lib.GMR_FLAG_DETERMINISTIC if deterministic else 0))
         self.cfg.profile_stages = _stage_mask(profile)
         self.color_mode = color_mode
         self._ctx = ctypes.c_void_p()
@@ -162,7 +167,7 @@ class Renderer:
                 continue
             flag = {"persistent": _lib.GMR_FLAG_PERSISTENT, "half_fwd": _lib.GMR_FLAG_HALF_WARP_FWD,
                     "half_bwd": _lib.GMR_FLAG_HALF_WARP_BWD, "warp_fwd": _lib.GMR_FLAG_WARP_STAGE_FWD,
-                    "warp_bwd": _lib.GMR_FLAG_WARP_STAGE_BWD}.get(k)
+                    "warp_bwd": _lib.GMR_FLAG_WARP_STAGE_BWD, "deterministic": _lib.GMR_FLAG_DETERMINISTIC}.get(k)
             if flag is not None:
                 self.cfg.flags = (self.cfg.flags & ~flag) | (flag if v else 0)
                 continue
