@@ -1671,8 +1671,8 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
     k_raster_bwd(RasterArgs a, const float* __restrict__ dL_dimg, const float* __restrict__ dL_dT,
                  const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
                  float4* __restrict__ rec_grad, float4* __restrict__ face_grad, BwdLoss bl, BwdZero bz) {
-  static_assert(!DET || LAYOUT == kLayoutCta, "deterministic backward: block-staged layout");
   pdl_enter();
+  static_assert(!DET || LAYOUT == kLayoutCta, "deterministic backward: block-staged layout");
   if constexpr (LAYOUT == kLayoutHalf) {
     static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
     bwd_tile_half<NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
