@@ -128,14 +128,18 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
         _, tf, tb, batch = base[:4]
         layouts = [LAYOUT_HALF, LAYOUT_WARP] if tile == 16 else [LAYOUT_WARP]
         threads = LAYOUT_THREADS[tile]
-        fwd = [(tile, t, tb, batch, 0, lay, 0) for lay in layouts for t in threads]
-        bwd = [(tile, tf, t, batch, 0, 0, lay) for lay in layouts for t in threads]
+        # the half-warp layout stages per batch: both larger batch sizes (the
+        # warp-staged layout has no batch)
+        batches = lambda lay: sorted({batch, 128, 256}) if lay == LAYOUT_HALF else [batch]
+        fwd = [(tile, t, tb, b, 0, lay, 0) for lay in layouts for t in threads for b in batches(lay)]
+        bwd = [(tile, tf, t, b, 0, 0, lay) for lay in layouts for t in threads for b in batches(lay)]
         for shape in fwd + bwd:
             time_shape(shape)
         bf = min(fwd + [base], key=results.get)
         bb = min(bwd + [base], key=results.get)
         if bf != base and bb != base:
-            time_shape((tile, bf[1], bb[2], batch, 0, bf[5], bb[6]))
+            # one batch size for both directions: the backward's (it weighs more)
+            time_shape((tile, bf[1], bb[2], bb[3], 0, bf[5], bb[6]))
     time_shape(tuple(best_cta[:4]) + (1, 0, 0))
     best = min(results, key=results.get)
     _apply(renderer, best)

@@ -56,6 +56,8 @@ struct gmr_ctx {
   const float* opacity = nullptr;
   int32_t V = 0, F = 0, C = 0;
   int64_t n_tiles = 0, n_pixels = 0;
+  int64_t n_btiles = 0;  // binning tiles of the last forward (= n_tiles unless split)
+  bool split = false;    // the last forward binned 8x8 tiles as 16x16 and split the lists
   gmr_config fwd_cfg;
   // device bytes held by the workspace (per allocation, and the total), and
   // the most it may hold (0: no limit; gmr_set_workspace_limit)
@@ -286,8 +288,34 @@ gmr_status ensure_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
   for (int b = 0; b < 2; ++b)
     if ((s = realloc_exact(ctx, &w.pair_key[b], cap, "pair_key")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.pair_face, cap, "pair_face")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.pair_quad, cap, "pair_quad")) != GMR_OK) return s;
   w.cap_pairs = cap;
   return GMR_OK;
+}
+
+// Split binning: the 8x8 compositing descriptors (4 per binning tile) and
+// ranges (one per 8x8 tile).
+gmr_status ensure_split_tiles(gmr_ctx* ctx, int64_t n_btiles, int64_t n_tiles, bool capturing) {
+  Workspace& w = ctx->ws;
+  const int64_t need = std::max<int64_t>(4 * n_btiles, n_tiles);
+  if (need <= w.cap_split_tiles) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "tile workspace must grow during stream capture; call gmr_reserve");
+  const int64_t cap = need + need / 4 + 1024;
+  gmr_status s;
+  if ((s = realloc_exact(ctx, &w.tile_desc_c, cap, "tile_desc_c")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.tile_range_c, cap, "tile_range_c")) != GMR_OK) return s;
+  w.cap_split_tiles = cap;
+  return GMR_OK;
+}
+
+// Split binning: the quadrants' lists (4 face ids per pair slot).
+gmr_status ensure_split_pairs(gmr_ctx* ctx, int64_t n, bool capturing) {
+  Workspace& w = ctx->ws;
+  if (n <= w.cap_split_pairs) return GMR_OK;
+  if (capturing) return fail(ctx, GMR_ERR_STATE, "pair workspace must grow during stream capture; call gmr_reserve");
+  gmr_status s = realloc_exact(ctx, &w.pair_face_c, n, "pair_face_c");
+  if (s == GMR_OK) w.cap_split_pairs = n;
+  return s;
 }
 
 // GMR_FLAG_DETERMINISTIC: the records' first pair slots.
@@ -426,11 +454,21 @@ gmr_status check_cams(gmr_ctx* ctx, const gmr_camera* cams, int32_t C) {
   return GMR_OK;
 }
 
-// Builds the view table (tile and pixel bases) for the configured tile size.
-void build_views(gmr_ctx* ctx, const gmr_camera* cams, int32_t C, int64_t* n_tiles, int64_t* n_pixels) {
+// Split binning: 8x8 compositing tiles binned as 16x16 (then each sorted
+// list split into its quadrants), except for the deterministic backward,
+// whose pair slots follow the compositing tiles.
+bool split_binning(const gmr_config& c) { return c.tile == 8 && !(c.flags & GMR_FLAG_DETERMINISTIC); }
+// (the sort keys carry the quadrants below the face id: face << 4 | quadrants)
+constexpr int64_t kSplitMaxFaces = int64_t(1) << 28;
+
+// Builds the view table (tile and pixel bases) for the configured tile size
+// and the binning grid.
+void build_views(gmr_ctx* ctx, const gmr_camera* cams, int32_t C, int64_t* n_tiles, int64_t* n_pixels,
+                 int64_t* n_btiles) {
   ctx->views.resize(C);
-  int64_t tb = 0, pb = 0;
+  int64_t tb = 0, pb = 0, bb = 0;
   int ts = ctx->cfg.tile;
+  const int bs = split_binning(ctx->cfg) ? 2 * ts : ts;
   for (int32_t c = 0; c < C; ++c) {
     ViewInfo& v = ctx->views[c];
     std::memcpy(v.R, cams[c].R, sizeof(v.R));
@@ -442,12 +480,17 @@ void build_views(gmr_ctx* ctx, const gmr_camera* cams, int32_t C, int64_t* n_til
     v.tiles_x = (v.W + ts - 1) / ts;
     v.tiles_y = (v.H + ts - 1) / ts;
     v.tile_base = (int32_t)tb;
+    v.btiles_x = (v.W + bs - 1) / bs;
+    v.btiles_y = (v.H + bs - 1) / bs;
+    v.btile_base = (int32_t)bb;
     v.pix_base = pb;
     tb += (int64_t)v.tiles_x * v.tiles_y;
+    bb += (int64_t)v.btiles_x * v.btiles_y;
     pb += (int64_t)v.W * v.H;
   }
   *n_tiles = tb;
   *n_pixels = pb;
+  *n_btiles = bb;
 }
 
 }  // namespace
@@ -512,7 +555,8 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
                   w.tile_order, w.tile_desc,
                   w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch,
-                  w.rec_slot, w.pair_grad, w.v_off, w.v_cur, w.v_inc, w.corner_grad};
+                  w.rec_slot, w.pair_grad, w.v_off, w.v_cur, w.v_inc, w.corner_grad, w.pair_face_c, w.tile_desc_c,
+                  w.tile_range_c, w.pair_quad};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
@@ -582,6 +626,11 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   if ((s = ensure_tiles(ctx, mt, false)) != GMR_OK) return s;
   if ((s = ensure_views(ctx, max_views, false)) != GMR_OK) return s;
   if ((s = ensure_pairs(ctx, max_pairs, false)) != GMR_OK) return s;
+  if (split_binning(ctx->cfg)) {
+    // binning tiles of 16 px: fewer than the 8x8 tiles
+    if ((s = ensure_split_tiles(ctx, mt, mt, false)) != GMR_OK) return s;
+    if ((s = ensure_split_pairs(ctx, 4 * ctx->ws.cap_pairs, false)) != GMR_OK) return s;
+  }
   if (ctx->cfg.flags & GMR_FLAG_DETERMINISTIC) {
     if ((s = ensure_det_records(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK) return s;
     if ((s = ensure_det_pairs(ctx, ctx->ws.cap_pairs, false)) != GMR_OK) return s;
@@ -632,8 +681,10 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   const bool cams_same = same_cams(ctx->cams, cams, C);
   if (!cams_same && capturing)
     return fail(ctx, GMR_ERR_STATE, "cameras differ from the previous call during stream capture");
-  int64_t n_tiles, n_pixels;
-  build_views(ctx, cams, C, &n_tiles, &n_pixels);
+  int64_t n_tiles, n_pixels, n_btiles;
+  build_views(ctx, cams, C, &n_tiles, &n_pixels, &n_btiles);
+  const bool split = split_binning(cfg);
+  if (split && F >= kSplitMaxFaces) return fail(ctx, GMR_ERR_INVALID_ARG, "8x8 tiles need fewer than 2^28 faces");
   if (n_tiles >= (int64_t)0x7fffffff) return fail(ctx, GMR_ERR_INVALID_ARG, "too many tiles");
   const int64_t n_rec = (int64_t)F * C;
 
@@ -645,6 +696,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   if ((st = ensure_tiles(ctx, n_tiles, capturing)) != GMR_OK) return st;
   if (cfg.color_mode == GMR_COLOR_SH && (st = ensure_sh(ctx, n_rec, capturing)) != GMR_OK) return st;
   if ((cfg.flags & GMR_FLAG_DETERMINISTIC) && (st = ensure_det_records(ctx, n_rec, capturing)) != GMR_OK) return st;
+  if (split && (st = ensure_split_tiles(ctx, n_btiles, n_tiles, capturing)) != GMR_OK) return st;
   if (fl.target) {
     // one float per forward warp after slot 0 (gmr_l2_loss's ticket counter)
     const int64_t n_warp_sums = n_tiles * (ctx->cfg.threads / 32);
@@ -671,12 +723,12 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
     {
       StageTimer t(ctx, GMR_STAGE_PROJECT, s, cfg);
       GMR_CUDA(ctx, gmr::launch_project(verts, V, faces, F, rgb, opacity, cfg.color_mode, cfg.sh_degree, w.views, C,
-                                        cfg.tile, cfg.cov_mode, (cfg.flags & GMR_FLAG_DETERMINISTIC) != 0, w, s,
-                                        &ctx->launches));
+                                        cfg.tile, split ? 1 : 0, cfg.cov_mode,
+                                        (cfg.flags & GMR_FLAG_DETERMINISTIC) != 0, w, s, &ctx->launches));
     }
     {
       StageTimer t(ctx, GMR_STAGE_SCAN, s, cfg);
-      GMR_CUDA(ctx, gmr::scan_exclusive(w.tile_count, n_tiles, w.tile_start, &w.counters->n_pairs,
+      GMR_CUDA(ctx, gmr::scan_exclusive(w.tile_count, n_btiles, w.tile_start, &w.counters->n_pairs,
                                         w.scan_tmp, w.tile_order, w.counters->n_class, s, &ctx->launches));
     }
     if (!(cfg.flags & GMR_FLAG_SYNC_CHECK) || capturing) break;
@@ -690,9 +742,11 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   }
   // S4-S6: keys to segment start + rank, per-tile sort by (depth, face),
   // ranges
+  if (split && (st = ensure_split_pairs(ctx, 4 * w.cap_pairs, capturing)) != GMR_OK) return st;
   {
     StageTimer t(ctx, GMR_STAGE_BIN, s, cfg);
-    GMR_CUDA(ctx, gmr::launch_bin_pairs(w, n_rec, F, w.views, C, n_tiles, s, &ctx->launches));
+    GMR_CUDA(ctx, gmr::launch_bin_pairs(w, n_rec, F, w.views, C, n_btiles, split, s, &ctx->launches));
+    if (split) GMR_CUDA(ctx, gmr::launch_split_quads(w, w.views, n_btiles, s, &ctx->launches));
   }
   // S7: compositing
   {
@@ -700,8 +754,9 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
     uint32_t* nc = (cfg.flags & GMR_FLAG_DEBUG_COUNTS) ? w.pix_ncontrib : nullptr;
     GMR_CUDA(ctx, gmr::launch_raster_fwd(cfg.tile, cfg.threads, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
                                          (cfg.flags & GMR_FLAG_HALF_WARP_FWD) ? 1 : (cfg.flags & GMR_FLAG_WARP_STAGE_FWD) ? 2 : 0,
-                                         cfg.color_mode == GMR_COLOR_SH, w,
-                                         w.pair_face, w.views, C, F, n_tiles, cfg.bg, images, t_final, nc, fl, s,
+                                         cfg.color_mode == GMR_COLOR_SH, w, split ? w.tile_desc_c : w.tile_desc,
+                                         split ? 4 * n_btiles : n_tiles, split ? w.pair_face_c : w.pair_face,
+                                         w.views, C, F, n_tiles, cfg.bg, images, t_final, nc, fl, s,
                                          &ctx->launches));
   }
 
@@ -711,6 +766,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   ctx->verts = verts; ctx->faces = faces; ctx->rgb = rgb; ctx->opacity = opacity;
   ctx->V = V; ctx->F = F; ctx->C = C;
   ctx->n_tiles = n_tiles; ctx->n_pixels = n_pixels;
+  ctx->n_btiles = n_btiles; ctx->split = split;
   ctx->fwd_cfg = cfg;
   return GMR_OK;
 }
@@ -828,9 +884,11 @@ gmr_status render_bwd(gmr_ctx* ctx, const float* dL_dimages, const float* dL_dtf
     StageTimer t(ctx, GMR_STAGE_RASTER_BWD, s, cfg);
     GMR_CUDA(ctx, gmr::launch_raster_bwd(cfg.tile, cfg.threads_bwd, cfg.batch, (cfg.flags & GMR_FLAG_PERSISTENT) != 0,
                                          (cfg.flags & GMR_FLAG_HALF_WARP_BWD) ? 1 : (cfg.flags & GMR_FLAG_WARP_STAGE_BWD) ? 2 : 0,
-                                         cfg.color_mode == GMR_COLOR_SH, det,
-                                         w, w.pair_face, w.views, C, F, ctx->n_tiles, cfg.bg, dL_dimages, dL_dtfinal,
-                                         bl, bz, s, &ctx->launches));
+                                         cfg.color_mode == GMR_COLOR_SH, det, w,
+                                         ctx->split ? w.tile_desc_c : w.tile_desc,
+                                         ctx->split ? 4 * ctx->n_btiles : ctx->n_tiles,
+                                         ctx->split ? w.pair_face_c : w.pair_face, w.views, C, F, ctx->n_tiles, cfg.bg,
+                                         dL_dimages, dL_dtfinal, bl, bz, s, &ctx->launches));
   }
   if (images) {  // the loss: sum of the warps' partial sums
     StageTimer t(ctx, GMR_STAGE_LOSS, s, cfg);
@@ -993,8 +1051,42 @@ gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* 
                                   s));
   if (rec_u && n_rec > 0)
     GMR_CUDA(ctx, cudaMemcpyAsync(rec_u, w.rec_u, sizeof(float4) * (size_t)n_rec, cudaMemcpyDeviceToDevice, s));
-  if ((tile_ids || face_ids) && P > cap) return fail(ctx, GMR_ERR_CAPACITY, "cap smaller than the pair count");
   if (P > w.cap_pairs) return fail(ctx, GMR_ERR_CAPACITY, "pair buffer overflowed in the forward");
+  if (ctx->split) {
+    // the 8x8 tiles' lists sit at 4 start + q n of their binning tile's
+    // segment: gathered here, in tile order, into the packed form
+    const int64_t nt = ctx->n_tiles;
+    std::vector<uint2> rg((size_t)std::max<int64_t>(nt, 1));
+    std::vector<uint32_t> pf((size_t)std::max<int64_t>(4 * P, 1));
+    if (nt > 0)
+      GMR_CUDA(ctx, cudaMemcpyAsync(rg.data(), w.tile_range_c, sizeof(uint2) * (size_t)nt, cudaMemcpyDeviceToHost, s));
+    if (P > 0)
+      GMR_CUDA(ctx, cudaMemcpyAsync(pf.data(), w.pair_face_c, sizeof(uint32_t) * 4 * (size_t)P, cudaMemcpyDeviceToHost,
+                                    s));
+    GMR_CUDA(ctx, cudaStreamSynchronize(s));
+    std::vector<uint2> crg((size_t)std::max<int64_t>(nt, 1));
+    std::vector<uint32_t> tid, fid;
+    for (int64_t g = 0; g < nt; ++g) {
+      const uint32_t b = (uint32_t)fid.size();
+      for (uint32_t i = rg[g].x; i < rg[g].y; ++i) {
+        tid.push_back((uint32_t)g);
+        fid.push_back(pf[i]);
+      }
+      crg[g] = fid.size() > b ? make_uint2(b, (uint32_t)fid.size()) : make_uint2(0u, 0u);
+    }
+    const int64_t P8 = (int64_t)fid.size();
+    if (n_pairs) *n_pairs = P8;
+    if ((tile_ids || face_ids) && P8 > cap) return fail(ctx, GMR_ERR_CAPACITY, "cap smaller than the pair count");
+    if (tile_ids && P8 > 0)
+      GMR_CUDA(ctx, cudaMemcpyAsync(tile_ids, tid.data(), sizeof(uint32_t) * (size_t)P8, cudaMemcpyHostToDevice, s));
+    if (face_ids && P8 > 0)
+      GMR_CUDA(ctx, cudaMemcpyAsync(face_ids, fid.data(), sizeof(uint32_t) * (size_t)P8, cudaMemcpyHostToDevice, s));
+    if (ranges && nt > 0)
+      GMR_CUDA(ctx, cudaMemcpyAsync(ranges, crg.data(), sizeof(uint2) * (size_t)nt, cudaMemcpyHostToDevice, s));
+    GMR_CUDA(ctx, cudaStreamSynchronize(s));  // (the host vectors go out of scope)
+    tile_ids = face_ids = ranges = nullptr;
+  }
+  if ((tile_ids || face_ids) && P > cap) return fail(ctx, GMR_ERR_CAPACITY, "cap smaller than the pair count");
   if (tile_ids && P > 0) GMR_CUDA(ctx, gmr::launch_expand_tiles(w.tile_range, ctx->n_tiles, tile_ids, s, &ctx->launches));
   if (face_ids && P > 0)
     GMR_CUDA(ctx, cudaMemcpyAsync(face_ids, w.pair_face, sizeof(uint32_t) * (size_t)P, cudaMemcpyDeviceToDevice, s));

@@ -53,22 +53,26 @@ constexpr int kPlaceBlocksPerSm = 6;  // resident at 40 registers per thread
 // forward would otherwise launch many blocks with nothing to do) striding over
 // rounds of kPlaceUnroll slots per thread; the slot loads of a round, then
 // their gathers, are issued together, so the dependent gathers overlap.
+// With split binning (pair_quad) the key's low word is face << 4 | the
+// pair's quadrants: the order by (depth, face) is unchanged.
 __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
     const unsigned long long* __restrict__ pair_tr, const uint32_t* __restrict__ pair_rec,
-    const uint32_t* __restrict__ rec_key, int32_t F, const uint32_t* __restrict__ tile_start, int64_t cap,
-    unsigned long long* __restrict__ keys, const Counters* __restrict__ counters) {
+    const uint8_t* __restrict__ pair_quad, const uint32_t* __restrict__ rec_key, int32_t F,
+    const uint32_t* __restrict__ tile_start, int64_t cap, unsigned long long* __restrict__ keys,
+    const Counters* __restrict__ counters) {
   pdl_enter();
   const int64_t n = counters->n_pairs;
   if (n > cap) return;  // overflow: the pair scratch is incomplete
   constexpr int64_t kRound = (int64_t)kPlaceThreads * kPlaceUnroll;
   for (int64_t base = (int64_t)blockIdx.x * kRound; base < n; base += (int64_t)gridDim.x * kRound) {
     unsigned long long tr[kPlaceUnroll];
-    uint32_t rid[kPlaceUnroll], key[kPlaceUnroll], start[kPlaceUnroll];
+    uint32_t rid[kPlaceUnroll], key[kPlaceUnroll], start[kPlaceUnroll], quad[kPlaceUnroll];
 #pragma unroll
     for (int u = 0; u < kPlaceUnroll; ++u) {
       const int64_t i = base + u * kPlaceThreads + threadIdx.x;
       tr[u] = i < n ? pair_tr[i] : 0ull;
       rid[u] = i < n ? pair_rec[i] : 0u;
+      quad[u] = (pair_quad && i < n) ? pair_quad[i] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kPlaceUnroll; ++u) {
@@ -81,7 +85,9 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
       const int64_t i = base + u * kPlaceThreads + threadIdx.x;
       if (i < n) {
         const uint32_t c = rid[u] / (uint32_t)F;
-        keys[start[u] + (uint32_t)tr[u]] = ((unsigned long long)key[u] << 32) | (rid[u] - c * (uint32_t)F);
+        const uint32_t face = rid[u] - c * (uint32_t)F;
+        keys[start[u] + (uint32_t)tr[u]] =
+            ((unsigned long long)key[u] << 32) | (pair_quad ? (face << 4 | quad[u]) : face);
       }
     }
   }
@@ -471,6 +477,67 @@ __global__ void __launch_bounds__(kSegThreads) k_long_sort(const uint32_t* __res
 
 constexpr size_t kLongSortSmem = (2 * kSegSmem) * sizeof(unsigned long long) + kSegWarps * kRadix * sizeof(uint32_t);
 
+// Split binning: one warp per binning (16x16) tile, at its compositing
+// position w: the tile's sorted list, 32 entries at a time (lane l takes
+// entry c + l: face << 4 | the quadrants its record's 8x8 rectangle holds,
+// from the projection), is dealt to the lists of those quadrants (a ballot
+// per quadrant keeps the order), quadrant q's list from 4 start + q n; lanes
+// 0-3 then write the quadrants' descriptors at positions 4 w + q (kNoTile
+// for a quadrant beyond the image) and their ranges. A record is in the 8x8
+// tile (X, Y) exactly when its rectangle holds it, and then also in the
+// binning tile (X / 2, Y / 2), so the quadrant lists are the 8x8 binning's,
+// in its order.
+constexpr int kSplitThreads = 128;
+__global__ void __launch_bounds__(kSplitThreads) k_split_quads(const uint4* __restrict__ desc_b, int64_t n_btiles,
+                                                               const uint32_t* __restrict__ pair_face,
+                                                               const ViewInfo* __restrict__ views,
+                                                               uint32_t* __restrict__ pair_face_c,
+                                                               uint4* __restrict__ desc_c, uint2* __restrict__ range_c) {
+  pdl_enter();
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * (kSplitThreads / 32) + (threadIdx.x >> 5);
+  if (w >= n_btiles) return;
+  const uint4 d = desc_b[w];  // (binning tile, view, start, end)
+  const ViewInfo& v = views[d.y];
+  const int lt = (int)d.x - v.btile_base;
+  const int by = lt / v.btiles_x, bx = lt - by * v.btiles_x;
+  const uint32_t n = d.w - d.z;
+  const uint32_t base = 4u * d.z;
+  const uint32_t below = (1u << lane) - 1u;
+  bool valid[4];
+  uint32_t cnt[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    valid[q] = 2 * bx + (q & 1) < v.tiles_x && 2 * by + (q >> 1) < v.tiles_y;
+    cnt[q] = 0;
+  }
+  for (uint32_t c = 0; c < n; c += 32) {
+    const uint32_t i = c + lane;
+    const uint32_t e = i < n ? __ldg(pair_face + d.z + i) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool in = valid[q] && ((e >> q) & 1u);
+      const uint32_t bal = __ballot_sync(0xffffffffu, in);
+      if (in) pair_face_c[base + (uint32_t)q * n + cnt[q] + __popc(bal & below)] = e >> 4;
+      cnt[q] += __popc(bal);
+    }
+  }
+  if (lane < 4) {
+    const int q = lane;
+    const uint32_t cq = q == 0 ? cnt[0] : q == 1 ? cnt[1] : q == 2 ? cnt[2] : cnt[3];
+    const int Xq = 2 * bx + (q & 1), Yq = 2 * by + (q >> 1);
+    if (Xq < v.tiles_x && Yq < v.tiles_y) {
+      const uint32_t g = (uint32_t)v.tile_base + (uint32_t)Yq * (uint32_t)v.tiles_x + (uint32_t)Xq;
+      const uint32_t lo = base + (uint32_t)q * n;
+      const uint2 rg = cq > 0 ? make_uint2(lo, lo + cq) : make_uint2(0u, 0u);
+      desc_c[4 * w + q] = make_uint4(g, d.y, rg.x, rg.y);
+      range_c[g] = rg;
+    } else {
+      desc_c[4 * w + q] = make_uint4(kNoTile, d.y, 0u, 0u);
+    }
+  }
+}
+
 // Debug: global tile id of every sorted pair, from the ranges.
 __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* __restrict__ tile_ids) {
   const int64_t t = blockIdx.x;
@@ -482,7 +549,7 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 }  // namespace
 
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
-                             int64_t n_tiles, cudaStream_t s, int64_t* launches) {
+                             int64_t n_tiles, bool split, cudaStream_t s, int64_t* launches) {
   if (n_rec > 0 && ws.cap_pairs > 0) {
     // one wave: kPlaceBlocksPerSm blocks per SM (148 SMs), or fewer for a
     // small pair capacity
@@ -491,8 +558,9 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
                                              148 * kPlaceBlocksPerSm);
     cudaError_t e = launch_chained(k_place_keys, true, dim3((unsigned)blocks), dim3(kPlaceThreads), 0, s,
                                    (const unsigned long long*)ws.pair_key[1], (const uint32_t*)ws.pair_face,
-                                   (const uint32_t*)ws.rec_key, F, (const uint32_t*)ws.tile_start, ws.cap_pairs,
-                                   ws.pair_key[0], (const Counters*)ws.counters);
+                                   split ? (const uint8_t*)ws.pair_quad : nullptr, (const uint32_t*)ws.rec_key, F,
+                                   (const uint32_t*)ws.tile_start, ws.cap_pairs, ws.pair_key[0],
+                                   (const Counters*)ws.counters);
     *launches += 1;
     if (e != cudaSuccess) return e;
   }
@@ -519,6 +587,19 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_split_quads(const Workspace& ws, const ViewInfo* views, int64_t n_btiles, cudaStream_t s,
+                               int64_t* launches) {
+  if (n_btiles <= 0) return cudaSuccess;
+  if (ws.cap_split_pairs < 4 * ws.cap_pairs || ws.cap_split_tiles < 4 * n_btiles) return cudaErrorInvalidValue;
+  constexpr int kPerCta = kSplitThreads / 32;
+  cudaError_t e = launch_chained(k_split_quads, true, dim3((unsigned)((n_btiles + kPerCta - 1) / kPerCta)),
+                                 dim3(kSplitThreads), 0, s, (const uint4*)ws.tile_desc, n_btiles,
+                                 (const uint32_t*)ws.pair_face, views, ws.pair_face_c, ws.tile_desc_c,
+                                 ws.tile_range_c);
+  *launches += 1;
+  return e;
 }
 
 cudaError_t launch_expand_tiles(const uint2* ranges, int64_t n_tiles, uint32_t* tile_ids, cudaStream_t s,

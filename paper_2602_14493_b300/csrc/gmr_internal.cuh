@@ -85,8 +85,15 @@ struct ViewInfo {
   float o[3];  // camera centre in world coordinates, -R^T t
   int32_t W, H, tiles_x, tiles_y;
   int32_t tile_base;  // first global tile id of this view
+  // the binning grid: the compositing tiles themselves, or (8x8 compositing
+  // tiles, split binning) 16x16 tiles whose sorted lists are split into
+  // their four 8x8 quadrants
+  int32_t btiles_x, btiles_y, btile_base;
   int64_t pix_base;   // first packed pixel of this view
 };
+// Descriptor of a compositing position with no tile (a quadrant of a 16x16
+// binning tile beyond the image's last 8x8 tile).
+constexpr uint32_t kNoTile = 0xffffffffu;
 
 // Device status bits (mirrors GMR_DEV_*).
 constexpr uint32_t kDevBadFace = GMR_DEV_BAD_FACE_INDEX;
@@ -134,11 +141,12 @@ __device__ __forceinline__ int tile_class(uint32_t L) {
   return kTileClasses - 1 - min(bits, kTileClasses - 1);
 }
 // Binary search of the view owning global tile g.
+// The view of binning tile g.
 __device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
   int lo = 0, hi = C - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (views[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+    if (views[mid].btile_base <= g) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -444,6 +452,10 @@ struct Workspace {
   // face ids in (tile, depth, face) order; before the sort, per pair slot of
   // the projection, the pair's record id
   uint32_t* pair_face = nullptr;
+  // split binning: per pair slot of the projection, the quadrants of its
+  // 16x16 binning tile that the record's 8x8 rectangle holds (bit 2 qy + qx);
+  // the keys then carry them below the face id (face << 4 | quadrants)
+  uint8_t* pair_quad = nullptr;
   // scratch for scans
   int64_t cap_scan = 0;
   uint32_t* scan_tmp = nullptr;     // block sums
@@ -456,6 +468,15 @@ struct Workspace {
   int32_t cap_views = 0;
   ViewInfo* views = nullptr;
   Counters* counters = nullptr;
+  // split binning (8x8 compositing tiles binned as 16x16): per binning
+  // tile of n sorted pairs from `start`, its quadrants' lists at 4 start +
+  // q n (4 x cap_pairs face ids), the compositing positions' descriptors
+  // (4 per binning tile) and the 8x8 tiles' ranges (debug)
+  int64_t cap_split_pairs = 0;
+  uint32_t* pair_face_c = nullptr;
+  int64_t cap_split_tiles = 0;
+  uint4* tile_desc_c = nullptr;
+  uint2* tile_range_c = nullptr;
   // GMR_FLAG_DETERMINISTIC: per record, the first of its pair slots (the
   // projection deals a record's pairs to consecutive slots, in the order of
   // its tiles in its rectangle, row by row); per pair slot, the compositing
@@ -494,9 +515,13 @@ int64_t scan_block_sums_needed(int64_t n);
 // With color_mode GMR_COLOR_SH (degree sh_degree) it writes ws.rec_col and
 // zeroes ws.rec_cgrad for every record instead of ws.face_col / face_grad.
 // det (GMR_FLAG_DETERMINISTIC): it also writes ws.rec_slot.
+// tile: the compositing tile (the records' rectangles are in its units);
+// bshift: log2 of binning tile / compositing tile (1 with split binning),
+// the pairs are counted and emitted per binning tile.
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int color_mode, int sh_degree, const ViewInfo* views, int32_t C,
-                           int tile, int cov_mode, bool det, Workspace& ws, cudaStream_t s, int64_t* launches);
+                           int tile, int bshift, int cov_mode, bool det, Workspace& ws, cudaStream_t s,
+                           int64_t* launches);
 // det: the record sums come from the pair slots (ws.pair_grad, ws.rec_slot,
 // ws.rec_ntiles) instead of ws.rec_grad / face_grad / rec_cgrad, and the
 // vertex (and per-vertex colour) gradients are gathered over the
@@ -519,11 +544,18 @@ cudaError_t launch_convert(const float* verts, int32_t V, const int32_t* faces, 
 
 // raster.cu
 // bin.cu: scatter keys into tile segments, sort each segment, write ranges.
+// split: the keys carry the pairs' quadrants (ws.pair_quad) below the face.
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
-                             int64_t n_tiles,
-                             cudaStream_t s, int64_t* launches);
+                             int64_t n_tiles, bool split, cudaStream_t s, int64_t* launches);
 cudaError_t launch_expand_tiles(const uint2* ranges, int64_t n_tiles, uint32_t* tile_ids, cudaStream_t s,
                                 int64_t* launches);
+// Split binning: the sorted list of every 16x16 binning tile (ws.tile_desc,
+// n_btiles positions; entries face << 4 | quadrants) into the lists of its
+// four 8x8 quadrants (the order kept) in ws.pair_face_c, with the
+// compositing descriptors ws.tile_desc_c (position 4 w + q; kNoTile beyond
+// the image) and the 8x8 ranges ws.tile_range_c.
+cudaError_t launch_split_quads(const Workspace& ws, const ViewInfo* views, int64_t n_btiles, cudaStream_t s,
+                               int64_t* launches);
 // Debug copies of the forward's per-record data: tile rectangle and the
 // unscaled conic.
 cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* rects, float* conic, cudaStream_t s,
@@ -547,8 +579,11 @@ struct FwdLoss {
 // layout: 0 staging by the CTA (full warps), 1 the half-warp layout (16x16
 // tiles, 128 or 256 threads), 2 staging by each warp; 1 and 2 not with
 // persistent.
+// n_pos compositing positions (descriptors tile_desc, lists in pair_face:
+// ws.tile_desc / ws.pair_face, or the split binning's); n_tiles compositing
+// tiles (the loss partials are per tile).
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
-                              const Workspace& ws,
+                              const Workspace& ws, const uint4* tile_desc, int64_t n_pos,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
                               uint32_t* ncontrib_out, const FwdLoss& fl, cudaStream_t s, int64_t* launches);
@@ -575,7 +610,7 @@ struct BwdZero {
 // tile's last contributor) instead of atomics into rec_grad / face_grad /
 // rec_cgrad.
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
-                              bool det, const Workspace& ws,
+                              bool det, const Workspace& ws, const uint4* tile_desc, int64_t n_pos,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
                               const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches);

@@ -287,16 +287,17 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C, int vpt,
     const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode, int sh_degree,
     float4* __restrict__ rec_col, float4* __restrict__ rec_cgrad,
-    const ViewInfo* __restrict__ views, int tile, float inv_tile, int cov_mode, float4* __restrict__ rec_u,
+    const ViewInfo* __restrict__ views, int tile, float inv_tile, int bshift, int cov_mode, float4* __restrict__ rec_u,
     float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
     int64_t cap_pairs, unsigned long long* __restrict__ pair_tr, uint32_t* __restrict__ pair_rec,
-    uint32_t* __restrict__ rec_slot, float4* __restrict__ rec_grad, float4* __restrict__ face_grad,
-    Counters* __restrict__ counters) {
+    uint8_t* __restrict__ pair_quad, uint32_t* __restrict__ rec_slot, float4* __restrict__ rec_grad,
+    float4* __restrict__ face_grad, Counters* __restrict__ counters) {
   pdl_enter();
   __shared__ ViewInfo sv[kProjMaxVpt];
   __shared__ uint32_t s_off[kProjThreads / 32][32];
   __shared__ uint2 s_first[kProjThreads / 32][32];  // (first tile, rectangle width)
+  __shared__ uint2 s_rect[kProjThreads / 32][32];   // split binning: the rectangle on the 8x8 grid
   const int c0 = blockIdx.y * vpt;
   const int nv = min(vpt, C - c0);
   for (int i = threadIdx.x; i < nv; i += kProjThreads) sv[i] = views[c0 + i];
@@ -355,9 +356,15 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     if (ok) br = bin_view(bf, v, tile, inv_tile);
     uint32_t nt = 0;
     uint2 rect = make_uint2(1u, 1u);  // x0 = 1 > x1 = 0: empty
+    int bx0 = 0, bx1 = 0, by0 = 0;  // the rectangle on the binning grid
     if (br.visible && br.x0 <= br.x1) {
-      nt = (uint32_t)(br.x1 - br.x0 + 1) * (uint32_t)(br.y1 - br.y0 + 1);
       rect = make_uint2((uint32_t)br.x0 | ((uint32_t)br.x1 << 16), (uint32_t)br.y0 | ((uint32_t)br.y1 << 16));
+      // (floor(a / 2t) = floor(floor(a / t) / 2), also clamped: the binning
+      // tiles hold every compositing tile of the rectangle)
+      bx0 = br.x0 >> bshift;
+      bx1 = br.x1 >> bshift;
+      by0 = br.y0 >> bshift;
+      nt = (uint32_t)(bx1 - bx0 + 1) * (uint32_t)((br.y1 >> bshift) - by0 + 1);
     }
     // (record, tile) pairs: the warp takes a run of pair slots from a global
     // counter and deals its records' pairs out evenly over its lanes (pair p
@@ -373,23 +380,24 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
       if (total > 0) {
         s_off[warp][lane] = incl - nt;
-        s_first[warp][lane] = make_uint2((uint32_t)v.tile_base + (uint32_t)br.y0 * (uint32_t)v.tiles_x +
-                                             (uint32_t)br.x0,
-                                         (uint32_t)(br.x1 - br.x0 + 1));
+        s_first[warp][lane] = make_uint2((uint32_t)v.btile_base + (uint32_t)by0 * (uint32_t)v.btiles_x + (uint32_t)bx0,
+                                         (uint32_t)(bx1 - bx0 + 1));
+        if (pair_quad) s_rect[warp][lane] = rect;
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&counters->pair_alloc, total);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (rec_slot && live && nt > 0) rec_slot[rid] = base + (incl - nt);  // this record's first slot
         __syncwarp();
-        const uint32_t tx = (uint32_t)v.tiles_x;
+        const uint32_t tx = (uint32_t)v.btiles_x;
         const uint32_t rid0 = rid - (uint32_t)lane;
         for (uint32_t p0 = 0; p0 < total; p0 += 32 * kPairUnroll) {
-          uint32_t t[kPairUnroll], peers[kPairUnroll], old[kPairUnroll], own[kPairUnroll];
+          uint32_t t[kPairUnroll], peers[kPairUnroll], old[kPairUnroll], own[kPairUnroll], quad[kPairUnroll];
 #pragma unroll
           for (int u = 0; u < kPairUnroll; ++u) {
             const uint32_t p = p0 + 32u * u + lane;
             t[u] = 0xffffffffu - (uint32_t)lane;  // distinct dummies for idle lanes
             own[u] = 0;
+            quad[u] = 0;
             if (p < total) {
               int q = 0;
 #pragma unroll
@@ -400,6 +408,18 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
               const uint32_t row = k / fr.y;
               t[u] = fr.x + row * tx + (k - row * fr.y);
               own[u] = (uint32_t)q;
+              if (pair_quad) {
+                // which quadrants (8x8 tiles) of this binning tile the
+                // record's 8x8 rectangle holds: bit qy * 2 + qx
+                const uint2 r = s_rect[warp][q];
+                const int x0 = (int)(r.x & 0xffffu), x1 = (int)(r.x >> 16);
+                const int y0 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
+                const int X = 2 * ((x0 >> 1) + (int)(k - row * fr.y)), Y = 2 * ((y0 >> 1) + (int)row);
+                const bool cx0 = X >= x0 && X <= x1, cx1 = X + 1 >= x0 && X + 1 <= x1;
+                const bool cy0 = Y >= y0 && Y <= y1, cy1 = Y + 1 >= y0 && Y + 1 <= y1;
+                quad[u] = (uint32_t)(cx0 && cy0) | (uint32_t)(cx1 && cy0) << 1 | (uint32_t)(cx0 && cy1) << 2 |
+                          (uint32_t)(cx1 && cy1) << 3;
+              }
             }
             peers[u] = __match_any_sync(0xffffffffu, t[u]);
           }
@@ -417,6 +437,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
             if (p < total && slot < cap_pairs) {
               pair_tr[slot] = ((unsigned long long)t[u] << 32) | rank;
               pair_rec[slot] = rid0 + own[u];
+              if (pair_quad) pair_quad[slot] = (uint8_t)quad[u];
             }
           }
         }
@@ -798,7 +819,8 @@ __global__ void k_convert(const float* __restrict__ verts, int32_t V, const int3
 
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
                            const float* opacity, int color_mode, int sh_degree, const ViewInfo* views, int32_t C,
-                           int tile, int cov_mode, bool det, Workspace& ws, cudaStream_t s, int64_t* launches) {
+                           int tile, int bshift, int cov_mode, bool det, Workspace& ws, cudaStream_t s,
+                           int64_t* launches) {
   if (F <= 0 || C <= 0) return cudaSuccess;
   // views per thread: as many as keep about two threads per SM slot (148 SMs
   // x 2048) busy, at most kProjMaxVpt, spread evenly over the view blocks
@@ -809,10 +831,10 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
   cudaError_t e = launch_chained(k_project, true, grid, dim3(kProjThreads), 0, s, verts, V, faces, F, C, vpt, rgb,
                                  opacity,
                                  color_mode, sh_degree, ws.rec_col, ws.rec_cgrad, views, tile, 1.0f / (float)tile,
-                                 cov_mode, ws.rec_u, ws.rec_q,
+                                 bshift, cov_mode, ws.rec_u, ws.rec_q,
                                  ws.rec_rect, ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
-                                 ws.pair_key[1], ws.pair_face, det ? ws.rec_slot : nullptr, ws.rec_grad,
-                                 ws.face_grad, ws.counters);
+                                 ws.pair_key[1], ws.pair_face, bshift ? ws.pair_quad : nullptr,
+                                 det ? ws.rec_slot : nullptr, ws.rec_grad, ws.face_grad, ws.counters);
   *launches += 1;
   return e;
 }

@@ -327,6 +327,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
   __shared__ Stage<BATCH, NW> st;
   // the tile at this compositing position, its view and its pair range
   const uint4 desc = __ldg(a.tile_desc + pos);
+  if (desc.x == kNoTile) return;  // a quadrant beyond the image (split binning)
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   const ViewInfo& v = a.views[c];
@@ -548,6 +549,7 @@ __device__ __forceinline__ void fwd_tile_half(const RasterArgs& a, uint32_t pos,
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, 2 * NW> st;  // list[h]: half h's entries
   const uint4 desc = __ldg(a.tile_desc + pos);
+  if (desc.x == kNoTile) return;  // a quadrant beyond the image (split binning)
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   const ViewInfo& v = a.views[c];
@@ -797,6 +799,7 @@ __device__ __forceinline__ void fwd_tile_ws(const RasterArgs& a, uint32_t pos, f
   constexpr int NW = NT / 32;
   __shared__ WarpSlots slots[NW];
   const uint4 desc = __ldg(a.tile_desc + pos);
+  if (desc.x == kNoTile) return;  // a quadrant beyond the image (split binning)
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   const ViewInfo& v = a.views[c];
@@ -1071,6 +1074,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
   __shared__ uint32_t s_wmax[DET ? NW : 1];
   // the tile at this compositing position, its view and its pair range
   const uint4 desc = __ldg(a.tile_desc + pos);
+  if (desc.x == kNoTile) return;  // a quadrant beyond the image (split binning)
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   if (threadIdx.x == 0) s_maxlast = 0;
@@ -1314,6 +1318,7 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
   __shared__ Stage<BATCH, 2 * NW> st;
   __shared__ uint32_t s_maxlast;
   const uint4 desc = __ldg(a.tile_desc + pos);
+  if (desc.x == kNoTile) return;  // a quadrant beyond the image (split binning)
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   if (threadIdx.x == 0) s_maxlast = 0;
@@ -1502,6 +1507,7 @@ __device__ __forceinline__ void bwd_tile_ws(const RasterArgs& a, uint32_t pos, c
   constexpr int NW = NT / 32;
   __shared__ WarpSlots slots[NW];
   const uint4 desc = __ldg(a.tile_desc + pos);
+  if (desc.x == kNoTile) return;  // a quadrant beyond the image (split binning)
   const int g = (int)desc.x;
   const int c = (int)desc.y;
   const ViewInfo& v = a.views[c];
@@ -1818,8 +1824,8 @@ int resident_grid(K kern, int threads) {
   return n;
 }
 
-RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const ViewInfo* views, int32_t F,
-                       const float* bg, int64_t n_tiles, bool col_by_record) {
+RasterArgs raster_args(const Workspace& ws, const uint4* tile_desc, int64_t n_pos, const uint32_t* pair_face,
+                       const ViewInfo* views, int32_t F, const float* bg, bool col_by_record) {
   RasterArgs a;
   a.pair_face = pair_face;
   a.rec_u = ws.rec_u;
@@ -1831,9 +1837,9 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
   a.bg0 = bg[0];
   a.bg1 = bg[1];
   a.bg2 = bg[2];
-  a.tile_desc = ws.tile_desc;
+  a.tile_desc = tile_desc;
   a.counters = ws.counters;
-  a.n_pos = (uint32_t)n_tiles;
+  a.n_pos = (uint32_t)n_pos;
   a.pair_grad = ws.pair_grad;
   a.rec_rect = ws.rec_rect;
   a.rec_slot = ws.rec_slot;
@@ -1843,7 +1849,7 @@ RasterArgs raster_args(const Workspace& ws, const uint32_t* pair_face, const Vie
 
 template <int TS, int NT, int BATCH>
 cudaError_t fwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by_record, const Workspace& ws,
-                       const uint32_t* pair_face,
+                       const uint4* tile_desc, int64_t n_pos, const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, float* images, float* t_out,
                        uint32_t* nc_out, const FwdLoss& fl, cudaStream_t s) {
   auto kern = persistent ? (fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, true>
@@ -1866,14 +1872,14 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
              : nc_out  ? k_raster_fwd<TS, NT, 256, kFwdDebug, false, kLayoutWarp>
                        : k_raster_fwd<TS, NT, 256, kFwdPlain, false, kLayoutWarp>;
   } else {
-    if (layout == kLayoutWarp) return fwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, ws, pair_face,
-                                                              views, C, F, bg, images, t_out, nc_out, fl, s);
+    if (layout == kLayoutWarp) return fwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, ws, tile_desc,
+                                                              n_pos, pair_face, views, C, F, bg, images, t_out, nc_out,
+                                                              fl, s);
   }
-  const unsigned grid =
-      persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
+  const unsigned grid = persistent ? (unsigned)std::min<int64_t>(n_pos, resident_grid(kern, NT)) : (unsigned)n_pos;
   cudaError_t e = launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
-                                 raster_args(ws, pair_face, views, F, bg, n_tiles, col_by_record), images, ws.pix_T,
-                                 ws.pix_last, t_out, nc_out, ws.cap_pixels, fl);
+                                 raster_args(ws, tile_desc, n_pos, pair_face, views, F, bg, col_by_record), images,
+                                 ws.pix_T, ws.pix_last, t_out, nc_out, ws.cap_pixels, fl);
   if (e == cudaSuccess && fl.target)
     e = launch_chained(k_sum_partials, true, dim3(1), dim3(1024), 0, s, (const float*)fl.part, n_tiles * (NT / 32), 1.0,
                        fl.loss);
@@ -1882,7 +1888,7 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
 
 template <int TS, int NT, int BATCH>
 cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by_record, bool det, const Workspace& ws,
-                       const uint32_t* pair_face,
+                       const uint4* tile_desc, int64_t n_pos, const uint32_t* pair_face,
                        const ViewInfo* views, int32_t C, int32_t F, const float* bg, const float* dL,
                        const float* dLdT, const BwdLoss& bl, const BwdZero& bz, cudaStream_t s) {
   auto kern = persistent ? (bl.img ? k_raster_bwd<TS, NT, BATCH, true, true> : k_raster_bwd<TS, NT, BATCH, false, true>)
@@ -1895,8 +1901,8 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
                         : (bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, kLayoutCta, true>
                                   : k_raster_bwd<TS, NT, BATCH, false, false, kLayoutCta, true>);
     } else {
-      return bwd_launch<TS, NT, 128>(n_tiles, persistent, layout, col_by_record, det, ws, pair_face, views, C, F, bg,
-                                     dL, dLdT, bl, bz, s);
+      return bwd_launch<TS, NT, 128>(n_tiles, persistent, layout, col_by_record, det, ws, tile_desc, n_pos, pair_face,
+                                     views, C, F, bg, dL, dLdT, bl, bz, s);
     }
   }
   if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
@@ -1912,12 +1918,12 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
                     : k_raster_bwd<TS, NT, 256, false, false, kLayoutWarp>;
   } else {
     if (layout == kLayoutWarp) return bwd_launch<TS, NT, 256>(n_tiles, persistent, layout, col_by_record, det, ws,
-                                                              pair_face, views, C, F, bg, dL, dLdT, bl, bz, s);
+                                                              tile_desc, n_pos, pair_face, views, C, F, bg, dL, dLdT,
+                                                              bl, bz, s);
   }
-  const unsigned grid =
-      persistent ? (unsigned)std::min<int64_t>(n_tiles, resident_grid(kern, NT)) : (unsigned)n_tiles;
+  const unsigned grid = persistent ? (unsigned)std::min<int64_t>(n_pos, resident_grid(kern, NT)) : (unsigned)n_pos;
   return launch_chained(kern, false, dim3(grid), dim3(NT), 0, s,
-                        raster_args(ws, pair_face, views, F, bg, n_tiles, col_by_record), dL, dLdT,
+                        raster_args(ws, tile_desc, n_pos, pair_face, views, F, bg, col_by_record), dL, dLdT,
                         (const float*)ws.pix_T, (const uint32_t*)ws.pix_last, ws.rec_grad,
                         col_by_record ? ws.rec_cgrad : ws.face_grad, bl, bz);
 }
@@ -1925,7 +1931,7 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
 }  // namespace
 
 cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
-                              const Workspace& ws,
+                              const Workspace& ws, const uint4* tile_desc, int64_t n_pos,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, float* images, float* t_final_out,
                               uint32_t* ncontrib_out, const FwdLoss& fl, cudaStream_t s, int64_t* launches) {
@@ -1934,7 +1940,8 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_FWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, ws, pair_face, views, C, F, bg, images, \
+  e = fwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, ws, tile_desc, n_pos, pair_face, views,  \
+                               C, F, bg, images,                                                                 \
                                t_final_out,                                                                      \
                                ncontrib_out, fl, s)
   GMR_FWD(16, 256, 64); else GMR_FWD(16, 256, 128); else GMR_FWD(16, 256, 256);
@@ -1950,7 +1957,7 @@ cudaError_t launch_raster_fwd(int tile, int threads, int batch, bool persistent,
 }
 
 cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent, int layout, bool col_by_record,
-                              bool det, const Workspace& ws,
+                              bool det, const Workspace& ws, const uint4* tile_desc, int64_t n_pos,
                               const uint32_t* pair_face, const ViewInfo* views, int32_t C, int32_t F,
                               int64_t n_tiles, const float* bg, const float* dL_dimages, const float* dL_dT,
                               const BwdLoss& bl, const BwdZero& bz, cudaStream_t s, int64_t* launches) {
@@ -1958,7 +1965,8 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
   cudaError_t e = cudaSuccess;
 #define GMR_BWD(TS_, NT_, B_)                                                                                    \
   if (tile == TS_ && threads == NT_ && batch == B_)                                                              \
-  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, det, ws, pair_face, views, C, F, bg,  \
+  e = bwd_launch<TS_, NT_, B_>(n_tiles, persistent, layout, col_by_record, det, ws, tile_desc, n_pos, pair_face,   \
+                               views, C, F, bg,                                                                  \
                                dL_dimages,                                                                       \
                                dL_dT, bl, bz, s)
   GMR_BWD(16, 256, 64); else GMR_BWD(16, 256, 128); else GMR_BWD(16, 256, 256);
