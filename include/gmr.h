@@ -144,7 +144,7 @@ typedef struct {
  * half-warp layout: each 16-lane half of a warp composites its own 4x4-pixel
  * units and walks its own list of the Gaussians that can reach them, so a
  * warp serves two Gaussians per step where they cover few pixels (dense
- * meshes). 16x16 tiles with 128 or 256 threads only, not with
+ * meshes). 16x16 tiles with 128 or 256 threads, or 8x8 tiles, not with
  * GMR_FLAG_PERSISTENT (GMR_ERR_INVALID_ARG otherwise). Images are identical
  * bit for bit; gradients agree up to the order of the float atomics. */
 #define GMR_FLAG_HALF_WARP_FWD 16

@@ -84,7 +84,7 @@ def _store(d):
 def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates=CANDIDATES, use_cache=True):
     """Times each candidate shape on this workload with one CTA per tile;
     then, from the fastest of each tile size among 8 and 16, the half-warp
-    (16x16 tiles) and the warp-staged layouts in the forward and in the
+    and the warp-staged layouts in the forward and in the
     backward (each thread count of ``LAYOUT_THREADS``, separately, then the
     best of each direction together), and the fastest block-staged shape as a
     persistent grid; configures ``renderer`` with the fastest of all.
@@ -126,7 +126,7 @@ def tune(renderer, verts, faces, rgb, opacity, cams, target, reps=15, candidates
             continue
         base = min(of_tile, key=results.get)
         _, tf, tb, batch = base[:4]
-        layouts = [LAYOUT_HALF, LAYOUT_WARP] if tile == 16 else [LAYOUT_WARP]
+        layouts = [LAYOUT_HALF, LAYOUT_WARP]
         threads = LAYOUT_THREADS[tile]
         # the half-warp layout stages per batch: both larger batch sizes (the
         # warp-staged layout has no batch)

@@ -134,13 +134,13 @@ bool valid_config(const gmr_config* c, std::string* why) {
     return false;
   }
   if (c->flags & (GMR_FLAG_HALF_WARP_FWD | GMR_FLAG_HALF_WARP_BWD)) {
-    if (c->tile != 16 || (c->flags & GMR_FLAG_PERSISTENT)) {
-      *why = "the half-warp layout needs 16x16 tiles and no persistent grid";
+    if (c->tile == 32 || (c->flags & GMR_FLAG_PERSISTENT)) {
+      *why = "the half-warp layout needs 8x8 or 16x16 tiles and no persistent grid";
       return false;
     }
-    if (((c->flags & GMR_FLAG_HALF_WARP_FWD) && c->threads == 64) ||
-        ((c->flags & GMR_FLAG_HALF_WARP_BWD) && c->threads_bwd == 64)) {
-      *why = "the half-warp layout needs 128 or 256 threads per tile";
+    if (c->tile == 16 && (((c->flags & GMR_FLAG_HALF_WARP_FWD) && c->threads == 64) ||
+                          ((c->flags & GMR_FLAG_HALF_WARP_BWD) && c->threads_bwd == 64))) {
+      *why = "the half-warp layout needs 128 or 256 threads per 16x16 tile";
       return false;
     }
   }

@@ -162,11 +162,12 @@ __device__ __forceinline__ uint32_t block_mask(float gx, float gy, float a2, flo
   return region_mask<TS / 8, TS / 4, 8, 4>(gx, gy, a2, b2, c2, k2, tox, toy);
 }
 
-// ... and the 4x4-pixel half-warp units of a 16x16 tile (row-major, 4 per
+// ... and the 4x4-pixel half-warp units of the tile (row-major, TS/4 per
 // row), for the half-warp layout.
+template <int TS>
 __device__ __forceinline__ uint32_t unit_mask(float gx, float gy, float a2, float b2, float c2, float k2, float tox,
                                               float toy) {
-  return region_mask<4, 4, 4, 4>(gx, gy, a2, b2, c2, k2, tox, toy);
+  return region_mask<TS / 4, TS / 4, 4, 4>(gx, gy, a2, b2, c2, k2, tox, toy);
 }
 
 // Staging of one batch: records and colours of the listed Gaussians, the
@@ -187,7 +188,7 @@ __device__ __forceinline__ void stage_batch(Stage<BATCH, NL>& st, const uint32_t
     float4 col = __ldg(col_src + (col_by_rec ? rid : f));
     float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
-    const uint32_t m = units ? unit_mask(ux, uy, q.x, q.y, q.z, -q.w, tox, toy)
+    const uint32_t m = units ? unit_mask<(TS <= 16 ? TS : 16)>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy)  // (no units at 32)
                              : block_mask<TS>(ux, uy, q.x, q.y, q.z, -q.w, tox, toy);
     st.g[i] = make_float4(ux, uy, q.x, q.y);
     st.h[i] = make_float4(q.z, q.w, col.w, 0.0f);
@@ -481,20 +482,22 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
 }
 
 // ---------------------------------------------------------------- half-warp layout
-// Layout for Gaussians that cover few pixels: a 16x16 tile is cut into 16
-// units of 4x4 pixels (row-major, 4 per row), and each 16-lane half of a
-// warp composites PPT units (one pixel of each per lane) and walks its own
-// compacted list of the batch's Gaussians that can reach them. The two halves
-// of a warp step through their lists together, each on its own entry, so a
-// warp-step serves two Gaussians where the full-warp layout serves one when
-// the Gaussians are smaller than a warp block (the lists of a 4x4 unit are
-// shorter than those of an 8x4 block).
-template <int NT>
+// Layout for Gaussians that cover few pixels: a TS x TS tile is cut into
+// units of 4x4 pixels (row-major, U = TS/4 per row), and each 16-lane half
+// of a warp composites PPT units (one pixel of each per lane) and walks its
+// own compacted list of the batch's Gaussians that can reach them. The two
+// halves of a warp step through their lists together, each on its own
+// entry, so a warp-step serves two Gaussians where the full-warp layout
+// serves one when the Gaussians are smaller than a warp block (the lists of
+// a 4x4 unit are shorter than those of an 8x4 block). 16x16 tiles with 128
+// or 256 threads, 8x8 tiles with 32 or 64.
+template <int TS, int NT>
 struct HalfMap {
-  static constexpr int PPT = 256 / NT;  // 16x16 tiles: 128 or 256 threads
-  static_assert(PPT == 1 || PPT == 2, "half-warp layout: 16x16 tiles, 128 or 256 threads");
-  // half h owns the units in column h % 4, rows (h / 4) PPT + k
-  __device__ __forceinline__ static int unit_of(int h, int k) { return ((h / 4) * PPT + k) * 4 + (h % 4); }
+  static constexpr int U = TS / 4;             // units per tile row
+  static constexpr int PPT = TS * TS / NT;      // units per half = pixels per lane
+  static_assert((TS == 16 || TS == 8) && (PPT == 1 || PPT == 2), "half-warp layout: 1 or 2 units per half");
+  // half h owns the units in column h % U, rows (h / U) PPT + k
+  __device__ __forceinline__ static int unit_of(int h, int k) { return ((h / U) * PPT + k) * U + (h % U); }
   __device__ __forceinline__ static int half() { return threadIdx.x >> 4; }
   __device__ __forceinline__ static uint32_t bits_of(int h) {
     uint32_t b = 0;
@@ -504,8 +507,8 @@ struct HalfMap {
   }
   __device__ __forceinline__ static void local(int k, int& lx, int& ly) {
     const int l = threadIdx.x & 15, u = unit_of(half(), k);
-    lx = (u % 4) * 4 + (l & 3);
-    ly = (u / 4) * 4 + (l >> 2);
+    lx = (u % U) * 4 + (l & 3);
+    ly = (u / U) * 4 + (l >> 2);
   }
 };
 
@@ -538,13 +541,12 @@ __device__ __forceinline__ int half_lists(uint8_t (*list)[BATCH], const uint32_t
 // The forward of one tile in the half-warp layout: the same arithmetic and
 // decisions per pixel as fwd_tile (so the same image bit for bit), only the
 // assignment of pixels to lanes and the list each lane walks differ.
-template <int NT, int BATCH, int MODE>
+template <int TS, int NT, int BATCH, int MODE>
 __device__ __forceinline__ void fwd_tile_half(const RasterArgs& a, uint32_t pos, float* __restrict__ images,
                                               float* __restrict__ pix_T, uint32_t* __restrict__ pix_last,
                                               float* __restrict__ t_out, uint32_t* __restrict__ nc_out,
                                               int64_t n_pix_total, const FwdLoss& fl) {
-  constexpr int TS = 16;
-  using HM = HalfMap<NT>;
+  using HM = HalfMap<TS, NT>;
   constexpr int PPT = HM::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, 2 * NW> st;  // list[h]: half h's entries
@@ -955,8 +957,8 @@ __global__ void __launch_bounds__(NT, FwdMinBlocks<TS, NT>::value)
                  float* __restrict__ t_out, uint32_t* __restrict__ nc_out, int64_t n_pix_total, FwdLoss fl) {
   pdl_enter();
   if constexpr (LAYOUT == kLayoutHalf) {
-    static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
-    fwd_tile_half<NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
+    static_assert(!PERSIST, "half-warp layout: one CTA per tile");
+    fwd_tile_half<TS, NT, BATCH, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
   } else if constexpr (LAYOUT == kLayoutWarp) {
     static_assert(!PERSIST, "warp-staged layout: one CTA per tile");
     fwd_tile_ws<TS, NT, MODE>(a, blockIdx.x, images, pix_T, pix_last, t_out, nc_out, n_pix_total, fl);
@@ -1306,13 +1308,12 @@ __device__ __forceinline__ float half_reduce8_transposed(const float v[8], int l
 // arithmetic as bwd_tile): each half walks its own list back to front from
 // its own last contributor, and a half's contributions to one Gaussian are
 // reduced over its 16 lanes (or added by its few contributing lanes).
-template <int NT, int BATCH, bool LOSS>
+template <int TS, int NT, int BATCH, bool LOSS>
 __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos, const float* __restrict__ dL_dimg,
                                               const float* __restrict__ dL_dT, const float* __restrict__ pix_T,
                                               const uint32_t* __restrict__ pix_last, float4* __restrict__ rec_grad,
                                               float4* __restrict__ face_grad, const BwdLoss& bl) {
-  constexpr int TS = 16;
-  using HM = HalfMap<NT>;
+  using HM = HalfMap<TS, NT>;
   constexpr int PPT = HM::PPT;
   constexpr int NW = NT / 32;
   __shared__ Stage<BATCH, 2 * NW> st;
@@ -1680,8 +1681,8 @@ __global__ void __launch_bounds__(NT, BwdMinBlocks<NT>::value)
   pdl_enter();
   static_assert(!DET || LAYOUT == kLayoutCta, "deterministic backward: block-staged layout");
   if constexpr (LAYOUT == kLayoutHalf) {
-    static_assert(TS == 16 && !PERSIST, "half-warp layout: 16x16 tiles, one CTA per tile");
-    bwd_tile_half<NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
+    static_assert(!PERSIST, "half-warp layout: one CTA per tile");
+    bwd_tile_half<TS, NT, BATCH, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
   } else if constexpr (LAYOUT == kLayoutWarp) {
     static_assert(!PERSIST, "warp-staged layout: one CTA per tile");
     bwd_tile_ws<TS, NT, LOSS>(a, blockIdx.x, dL_dimg, dL_dT, pix_T, pix_last, rec_grad, face_grad, bl);
@@ -1858,7 +1859,7 @@ cudaError_t fwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
                         : (fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false>
                            : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false>
                                      : k_raster_fwd<TS, NT, BATCH, kFwdPlain, false>);
-  if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
+  if constexpr ((TS == 16 && (NT == 128 || NT == 256)) || (TS == 8 && (NT == 32 || NT == 64))) {
     if (layout == kLayoutHalf)
       kern = fl.target ? k_raster_fwd<TS, NT, BATCH, kFwdLoss, false, kLayoutHalf>
              : nc_out  ? k_raster_fwd<TS, NT, BATCH, kFwdDebug, false, kLayoutHalf>
@@ -1905,7 +1906,7 @@ cudaError_t bwd_launch(int64_t n_tiles, bool persistent, int layout, bool col_by
                                      views, C, F, bg, dL, dLdT, bl, bz, s);
     }
   }
-  if constexpr (TS == 16 && (NT == 128 || NT == 256)) {
+  if constexpr ((TS == 16 && (NT == 128 || NT == 256)) || (TS == 8 && (NT == 32 || NT == 64))) {
     if (layout == kLayoutHalf)
       kern = bl.img ? k_raster_bwd<TS, NT, BATCH, true, false, kLayoutHalf>
                     : k_raster_bwd<TS, NT, BATCH, false, false, kLayoutHalf>;

@@ -86,7 +86,7 @@ class Renderer:
     CTAs taking tiles from a counter) instead of one CTA per tile.
     half_fwd / half_bwd: the half-warp layout in the forward / backward
     compositing kernel (16-lane halves with their own 4x4-pixel units and
-    lists; 16x16 tiles with 128 or 256 threads).
+    lists; 16x16 tiles with 128 or 256 threads, or 8x8 tiles).
     warp_fwd / warp_bwd: the warp-staged layout (each warp stages the
     tile's list itself, no block-wide barrier inside a tile).
     deterministic: every gradient sum of the backward in a fixed order

@@ -35,8 +35,8 @@ def test_image_invariant_to_tile_and_batch_size():
     s = _uneven()
     ref = None
     for tile, threads, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (8, 64, 0), (8, 32, 0),
-                               (16, 256, 1), (16, 128, 1), (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2),
-                               (8, 64, 2), (8, 32, 2)):
+                               (16, 256, 1), (16, 128, 1), (8, 64, 1), (8, 32, 1), (16, 256, 2), (16, 128, 2),
+                               (16, 64, 2), (32, 256, 2), (8, 64, 2), (8, 32, 2)):
         for batch in (64, 128, 256):
             r = _renderer(tile=tile, batch=batch, threads=threads, half_fwd=lay == 1, warp_fwd=lay == 2)
             _, img, T = render_gpu(r, s)
@@ -55,8 +55,8 @@ def test_gradients_invariant_to_backward_shape():
     s = _uneven()
     ref = None
     for tile, threads_bwd, lay in ((16, 256, 0), (16, 128, 0), (16, 64, 0), (32, 256, 0), (8, 64, 0), (8, 32, 0),
-                                   (16, 256, 1), (16, 128, 1), (16, 256, 2), (16, 128, 2), (16, 64, 2), (32, 256, 2),
-                                   (8, 64, 2), (8, 32, 2)):
+                                   (16, 256, 1), (16, 128, 1), (8, 64, 1), (8, 32, 1), (16, 256, 2), (16, 128, 2),
+                                   (16, 64, 2), (32, 256, 2), (8, 64, 2), (8, 32, 2)):
         for batch in (64, 256):
             r = _renderer(tile=tile, batch=batch, threads=64 if tile == 8 else 256, threads_bwd=threads_bwd,
                           half_bwd=lay == 1, warp_bwd=lay == 2)
@@ -304,6 +304,7 @@ def test_host_side_argument_errors():
 
     r = _renderer()
     for bad in (dict(tile=32, threads=256, threads_bwd=256, half_fwd=True), dict(threads=64, half_fwd=True),
+                dict(tile=8, threads=64, threads_bwd=32, half_bwd=True, persistent=True),
                 dict(threads_bwd=64, half_bwd=True), dict(persistent=True, half_bwd=True),
                 dict(persistent=True, warp_fwd=True), dict(half_fwd=True, warp_fwd=True)):
         with pytest.raises(GmrError):
