@@ -240,7 +240,8 @@ GMR_API gmr_status gmr_image_offsets(const gmr_camera* cams, int32_t C, int64_t*
  * max_pixels total pixels and max_pairs (tile, Gaussian) pairs, so that
  * later calls within these limits allocate nothing (needed before stream
  * capture; the tile count is bounded for the configured tile size and
- * views of sides up to 16384 px). If it has to grow the workspace, the last
+ * views of sides up to 16384 px, the vertex count by 3 max_faces). If it
+ * has to grow the workspace, the last
  * forward's state is dropped: gmr_render_bwd then returns GMR_ERR_STATE
  * until the next forward. */
 GMR_API gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64_t max_pixels,

@@ -556,7 +556,7 @@ gmr_status gmr_destroy(gmr_ctx* ctx) {
                   w.tile_order, w.tile_desc,
                   w.pair_key[0], w.pair_key[1], w.pair_face, w.scan_tmp, w.loss_part, w.views, w.counters, w.reg_scratch,
                   w.rec_slot, w.pair_grad, w.v_off, w.v_cur, w.v_inc, w.corner_grad, w.pair_face_c, w.tile_desc_c,
-                  w.tile_range_c, w.pair_quad};
+                  w.tile_range_c, w.pair_quad, w.verts4};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (ctx->views_pinned) cudaFreeHost(ctx->views_pinned);
@@ -617,6 +617,8 @@ gmr_status gmr_reserve(gmr_ctx* ctx, int64_t max_faces, int32_t max_views, int64
   if (ctx->cfg.color_mode == GMR_COLOR_SH && (s = ensure_sh(ctx, max_faces * (int64_t)max_views, false)) != GMR_OK)
     return s;
   if ((s = ensure_faces(ctx, max_faces, false)) != GMR_OK) return s;
+  if ((s = grow<float4>(ctx, &ctx->ws.verts4, &ctx->ws.cap_verts4, 3 * max_faces, false, "verts4")) != GMR_OK)
+    return s;
   if ((s = ensure_pixels(ctx, max_pixels, false)) != GMR_OK) return s;
   // tiles: at most one per tile-sized block plus one ragged tile per row and
   // column of each view (sides up to 16384 px; a larger view grows the
@@ -692,6 +694,7 @@ gmr_status render_fwd(gmr_ctx* ctx, const float* verts, int32_t V, const int32_t
   if ((st = ensure_views(ctx, C, capturing)) != GMR_OK) return st;
   if ((st = ensure_records(ctx, n_rec, capturing)) != GMR_OK) return st;
   if ((st = ensure_faces(ctx, F, capturing)) != GMR_OK) return st;
+  if ((st = grow<float4>(ctx, &w.verts4, &w.cap_verts4, V, capturing, "verts4")) != GMR_OK) return st;
   if ((st = ensure_pixels(ctx, n_pixels, capturing)) != GMR_OK) return st;
   if ((st = ensure_tiles(ctx, n_tiles, capturing)) != GMR_OK) return st;
   if (cfg.color_mode == GMR_COLOR_SH && (st = ensure_sh(ctx, n_rec, capturing)) != GMR_OK) return st;

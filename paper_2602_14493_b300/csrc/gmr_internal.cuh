@@ -231,6 +231,11 @@ __device__ __forceinline__ float rcp_refined(float a) {
 __device__ __forceinline__ float3 ld_vert(const float* v, int i) {
   return make_float3(__ldg(v + 3 * i), __ldg(v + 3 * i + 1), __ldg(v + 3 * i + 2));
 }
+// A vertex of the forward's padded copy (one 16-byte load).
+__device__ __forceinline__ float3 ld_vert4(const float4* v, int i) {
+  const float4 p = __ldg(v + i);
+  return make_float3(p.x, p.y, p.z);
+}
 
 // FP32 binning specification. Every operation is a separately rounded
 // IEEE-754 single operation in a fixed order (the _rn intrinsics are never
@@ -411,6 +416,11 @@ __device__ __forceinline__ float3 sh_grad_dot(float x, float y, float z, const f
 
 // ---------------------------------------------------------------- workspace
 struct Workspace {
+  // the vertices padded to 16 bytes (x, y, z, 0), written at the start of
+  // every forward: the projection and its backward gather one vector per
+  // vertex
+  int64_t cap_verts4 = 0;
+  float4* verts4 = nullptr;
   // records: one per (view, face)
   int64_t cap_records = 0;
   float4* rec_u = nullptr;       // (ux_hi, uy_hi, ux_lo, uy_lo)
@@ -514,7 +524,9 @@ int64_t scan_block_sums_needed(int64_t n);
 // (ws.rec_grad for all C x F records, ws.face_grad for all F faces).
 // With color_mode GMR_COLOR_SH (degree sh_degree) it writes ws.rec_col and
 // zeroes ws.rec_cgrad for every record instead of ws.face_col / face_grad.
-// det (GMR_FLAG_DETERMINISTIC): it also writes ws.rec_slot.
+// det (GMR_FLAG_DETERMINISTIC): it also writes ws.rec_slot. It first pads
+// the vertices into ws.verts4 (cap_verts4 >= V), which the projection
+// backward reads too.
 // tile: the compositing tile (the records' rectangles are in its units);
 // bshift: log2 of binning tile / compositing tile (1 with split binning),
 // the pairs are counted and emitted per binning tile.

@@ -284,7 +284,7 @@ __device__ __forceinline__ float3 sh_colour_any(int L, const float* __restrict__
 constexpr int kProjMaxVpt = 32;
 
 __global__ void __launch_bounds__(kProjThreads) k_project(
-    const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C, int vpt,
+    const float4* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C, int vpt,
     const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode, int sh_degree,
     float4* __restrict__ rec_col, float4* __restrict__ rec_cgrad,
     const ViewInfo* __restrict__ views, int tile, float inv_tile, int bshift, int cov_mode, float4* __restrict__ rec_u,
@@ -325,9 +325,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
   // the face's view-independent quantities, once for all views
   float3 a = make_float3(0.f, 0.f, 0.f), b = a, cc = a;
   if (ok) {
-    a = ld_vert(verts, i0);
-    b = ld_vert(verts, i1);
-    cc = ld_vert(verts, i2);
+    a = ld_vert4(verts, i0);
+    b = ld_vert4(verts, i1);
+    cc = ld_vert4(verts, i2);
   }
   const BinFace bf = bin_face(a, b, cc);
   const df m[3] = {df_mean3(a.x, b.x, cc.x), df_mean3(a.y, b.y, cc.y), df_mean3(a.z, b.z, cc.z)};
@@ -613,7 +613,7 @@ __device__ __forceinline__ void sh_colour_bwd(const float* __restrict__ coef, co
 // per face or per vertex.
 template <int G, int L>
 __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
-    const float* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
+    const float4* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
     const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ rgb,
     const float* __restrict__ opacity, const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q,
     const float4* __restrict__ face_grad, const float4* __restrict__ rec_cgrad, float* __restrict__ dverts,
@@ -644,9 +644,9 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
   float3 a = acc.dmu, b = acc.dmu, cc = acc.dmu;
   FaceGeom g;
   if (ok) {
-    a = ld_vert(verts, i0);
-    b = ld_vert(verts, i1);
-    cc = ld_vert(verts, i2);
+    a = ld_vert4(verts, i0);
+    b = ld_vert4(verts, i1);
+    cc = ld_vert4(verts, i2);
     g = face_geom(a, b, cc, cov_mode);
     // the next view's sums are loaded before this view's arithmetic
     for (int c = sub; c < C; c += G) {
@@ -815,6 +815,16 @@ __global__ void k_convert(const float* __restrict__ verts, int32_t V, const int3
   if (face_o) face_o[f] = fminf(fmaxf(opacity ? opacity[f] : 1.0f, 0.0f), 1.0f);
 }
 
+// The vertices padded to 16 bytes: one thread per vertex (a warp reads 384
+// contiguous bytes and writes 512).
+constexpr int kPadThreads = 256;
+__global__ void __launch_bounds__(kPadThreads) k_pad_verts(const float* __restrict__ verts, int32_t V,
+                                                           float4* __restrict__ verts4) {
+  pdl_enter();
+  const int64_t i = (int64_t)blockIdx.x * kPadThreads + threadIdx.x;
+  if (i < V) verts4[i] = make_float4(__ldg(verts + 3 * i), __ldg(verts + 3 * i + 1), __ldg(verts + 3 * i + 2), 0.0f);
+}
+
 }  // namespace
 
 cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, int32_t F, const float* rgb,
@@ -828,7 +838,15 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
   const int n_blocks_y = (int)((C + want - 1) / want);
   const int vpt = (C + n_blocks_y - 1) / n_blocks_y;
   dim3 grid((F + kProjThreads - 1) / kProjThreads, n_blocks_y);
-  cudaError_t e = launch_chained(k_project, true, grid, dim3(kProjThreads), 0, s, verts, V, faces, F, C, vpt, rgb,
+  if (ws.cap_verts4 < V) return cudaErrorInvalidValue;
+  if (V > 0) {
+    cudaError_t e = launch_chained(k_pad_verts, true, dim3((unsigned)((V + kPadThreads - 1) / kPadThreads)),
+                                   dim3(kPadThreads), 0, s, verts, V, ws.verts4);
+    *launches += 1;
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = launch_chained(k_project, true, grid, dim3(kProjThreads), 0, s, (const float4*)ws.verts4, V, faces,
+                                 F, C, vpt, rgb,
                                  opacity,
                                  color_mode, sh_degree, ws.rec_col, ws.rec_cgrad, views, tile, 1.0f / (float)tile,
                                  bshift, cov_mode, ws.rec_u, ws.rec_q,
@@ -865,7 +883,8 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
     ds.cap_pairs = std::min(ws.cap_pairs, ws.cap_det_pairs);
     ds.corner_grad = ws.corner_grad;
   }
-  cudaError_t e = launch_chained(kern, true, dim3(blocks), dim3(kProjBwdThreads), 0, s, verts, V, faces, F, C, views,
+  cudaError_t e = launch_chained(kern, true, dim3(blocks), dim3(kProjBwdThreads), 0, s, (const float4*)ws.verts4, V,
+                                 faces, F, C, views,
                                  cov_mode, color_mode, rgb, opacity, (const float4*)ws.rec_grad,
                                  (const float4*)ws.rec_q, (const float4*)ws.face_grad, (const float4*)ws.rec_cgrad,
                                  dverts, drgb, dop, accumulate, ds);

@@ -15,7 +15,7 @@ import pytest
 CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2602_14493_b300", "csrc")
 
 # the kernels of one forward + loss + backward step
-STEP_KERNELS = ["k_project", "k_scan_single", "k_scan_reduce", "k_scan_top", "k_scan_down", "k_place_keys",
+STEP_KERNELS = ["k_pad_verts", "k_project", "k_scan_single", "k_scan_reduce", "k_scan_top", "k_scan_down", "k_place_keys",
                 "k_tile_sort", "k_long_sort", "k_split_quads", "k_raster_fwd", "k_raster_bwd", "k_sum_partials",
                 "k_proj_bwd"]
 
