@@ -65,7 +65,8 @@ FLOPS_BWD_CONTRIB = 59
 # shape (tile, backward threads, batch, persistent, backward layout); an
 # entry is removed when
 # the kernel changes after its capture.
-NCU_TRAFFIC = {("raster_bwd", "icosphere6_noise_64xuneven", (16, 128, 256, 0, 1)): 1944362496}
+NCU_TRAFFIC = {("raster_bwd", "icosphere6_noise_64xuneven", (16, 128, 256, 0, 1)): 1946733824,
+               ("raster_bwd", "icosphere8_perlin_16x1024", (8, 32, 64, 0, 2)): 12668304896}
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -189,7 +190,7 @@ def oracle_sample_time(scene, n_pix, seed=0, keep=False):
         pix.append((c, int(rng.integers(int(scene.cams[c]["width"]))), int(rng.integers(int(scene.cams[c]["height"])))))
     pix = np.unique(np.array(pix, dtype=np.int32), axis=0)
     t0 = time.perf_counter()
-    r = oracle.render(scene, pixels=pix, bands=None)
+    r = oracle.render(scene, pixels=pix)  # with the ambiguity flags the parity check excludes
     g = 2.0 * (r["rgb"] - 0.5)
     g[r["flags"] != 0] = 0.0  # no gradient through pixels near a decision threshold
     b = oracle.backward(scene, g, pixels=pix)
