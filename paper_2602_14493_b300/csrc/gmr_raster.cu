@@ -754,19 +754,19 @@ __device__ __forceinline__ bool reaches_box(float ux, float uy, float a2, float 
   return hit;
 }
 
-// Stages entries [c, c + 32) of the tile's list that reach the warp's pixel
-// rectangle (and lie below `limit`) into the warp's slots, in order; returns
-// their count.
-__device__ __forceinline__ int warp_stage(WarpSlots& ws, const RasterArgs& a, uint32_t lo, int c, int limit,
+// Stages a chunk of 32 entries of the tile's list (lane l: list position i,
+// face f, already loaded; valid: i lies in the chunk's range) that reach the
+// warp's pixel rectangle into the warp's slots, in order; returns their
+// count. The callers load the next chunk's faces before compositing this
+// one, so that load overlaps the compositing.
+__device__ __forceinline__ int warp_stage(WarpSlots& ws, const RasterArgs& a, uint32_t f, int i, bool valid,
                                           uint32_t rec_base, float ax, float ay, float rx0, float rx1, float ry0,
                                           float ry1) {
   const int lane = threadIdx.x & 31;
-  const int i = c + lane;
   bool rel = false;
   float4 g4, h4, c4;
-  uint32_t f = 0, rid = 0;
-  if (i < limit) {
-    f = __ldg(a.pair_face + lo + i);
+  uint32_t rid = 0;
+  if (valid) {
     rid = rec_base + f;
     const float4 u = __ldg(a.rec_u + rid);
     const float4 q = __ldg(a.rec_q + rid);
@@ -851,12 +851,25 @@ __device__ __forceinline__ void fwd_tile_ws(const RasterArgs& a, uint32_t pos, f
   float rx0, rx1, ry0, ry1;
   PixMap<TS, NT>::region(tox, toy, rx0, rx1, ry0, ry1);
 
+  // 8x8 tiles: the next chunk's faces are loaded before this chunk is
+  // composited (1.6% faster there; at 16x16 the extra live register costs
+  // the 128-thread shape an occupancy step, 4% slower)
+  constexpr bool kPrefetch = TS == 8;
+  uint32_t f_next = (kPrefetch && lane < n) ? __ldg(a.pair_face + range.x + lane) : 0u;
   for (int c0 = 0; c0 < n; c0 += 32) {
     bool wd = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) wd &= done[k];
     if (__all_sync(kFull, wd)) break;
-    const int nl = warp_stage(ws, a, range.x, c0, n, rec_base, ax, ay, rx0, rx1, ry0, ry1);
+    const int i = c0 + lane;
+    uint32_t f;
+    if (kPrefetch) {
+      f = f_next;
+      f_next = i + 32 < n ? __ldg(a.pair_face + range.x + i + 32) : 0u;
+    } else {
+      f = i < n ? __ldg(a.pair_face + range.x + i) : 0u;
+    }
+    const int nl = warp_stage(ws, a, f, i, i < n, rec_base, ax, ay, rx0, rx1, ry0, ry1);
     for (int jj = 0; jj < nl; ++jj) {
       if ((jj & 3) == 3) {  // the warp's early exit, checked every 4 entries
         bool wd2 = true;
@@ -1613,9 +1626,27 @@ __device__ __forceinline__ void bwd_tile_ws(const RasterArgs& a, uint32_t pos, c
 #pragma unroll
   for (int k = 0; k < PPT; ++k) evals += last[k];
 
+  // chunks from the warp's last contributor back to the front; 8x8 tiles:
+  // the next chunk's faces loaded before this chunk is composited (1.4%
+  // faster there; at 16x16 more spills)
+  constexpr bool kPrefetch = TS == 8;
+  uint32_t f_next = 0u;
+  if (kPrefetch) {
+    const int end = (int)wmax, i = max(0, end - 32) + lane;
+    if (end > 0 && i < end) f_next = __ldg(a.pair_face + range.x + i);
+  }
   for (int end = (int)wmax; end > 0; end -= 32) {
     const int c0 = max(0, end - 32);
-    const int nl = warp_stage(ws, a, range.x, c0, end, rec_base, ax, ay, rx0, rx1, ry0, ry1);
+    const int i = c0 + lane;
+    uint32_t f;
+    if (kPrefetch) {
+      f = f_next;
+      const int end2 = end - 32, i2 = max(0, end2 - 32) + lane;
+      f_next = (end2 > 0 && i2 < end2) ? __ldg(a.pair_face + range.x + i2) : 0u;
+    } else {
+      f = i < end ? __ldg(a.pair_face + range.x + i) : 0u;
+    }
+    const int nl = warp_stage(ws, a, f, i, i < end, rec_base, ax, ay, rx0, rx1, ry0, ry1);
     for (int jj = nl - 1; jj >= 0; --jj) {
       const uint32_t pos_j = ws.pos[jj];
       const float4 hh = ws.h[jj];
