@@ -529,8 +529,10 @@ def run_gmr(args, ws, rank, local):
     # its results (loss and gradients) back; the copies of step k + 1 run on
     # a copy stream while step k computes (double-buffered inputs), and the
     # host waits for each step's results before it goes on. The inputs are
-    # copied by gmr_copy_h2d (a kernel reading the pinned host buffers over
-    # the bus: faster than the copy engine for these sizes on these hosts).
+    # copied by gmr_copy_h2d (below 64 MiB a kernel reading the pinned host
+    # buffers over the bus, faster than the copy engine for such sizes on
+    # these hosts; larger buffers, such as the 64-view targets, by the copy
+    # engine).
     h_v = torch.from_numpy(scene.verts).pin_memory()
     h_f = torch.from_numpy(scene.faces).pin_memory()
     h_c = torch.from_numpy(scene.rgb).pin_memory()
@@ -658,7 +660,8 @@ def run_gmr(args, ws, rank, local):
         "cpu_baseline": cpu,
         "e2e": {"value": ws * n_pix / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s,
-                "form": "public API, pinned host buffers copied by gmr_copy_h2d; step k+1's copies overlap "
+                "form": "public API, pinned host buffers copied by gmr_copy_h2d (kernel < 64 MiB, copy engine "
+                        "above); step k+1's copies overlap "
                         "step k's compute"},
         "gpu_launches": launches_per_step * args.steps,
         "launches_per_step": launches_per_step,

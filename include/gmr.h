@@ -382,8 +382,10 @@ GMR_API gmr_status gmr_l2_loss_noalloc(const float* img, const float* target, in
 
 /* Host-to-device copy of `bytes` bytes from page-locked host memory `src`
  * (allocated with cudaHostAlloc / cudaMallocHost, or registered) to device
- * memory `dst`, done by a kernel that reads the host buffer directly over the
- * bus (no copy engine), asynchronously on `stream`. No context: any device.
+ * memory `dst`, asynchronously on `stream`: below 64 MiB by a kernel that
+ * reads the host buffer directly over the bus (faster than the copy engine
+ * for such sizes on the hosts measured), from 64 MiB up by the copy engine
+ * (one cudaMemcpyAsync). No context: any device.
  * Returns GMR_ERR_INVALID_ARG when src is not page-locked memory mapped into
  * the device's address space (nothing is launched then), GMR_ERR_CUDA when
  * the launch fails. 16-byte aligned buffers take the vector path; the rest

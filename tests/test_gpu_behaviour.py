@@ -370,12 +370,13 @@ def test_stats_and_launch_count():
 
 def test_copy_h2d_kernel_copy():
     """gmr_copy_h2d: bytes equal after the copy for sizes with and without a
-    16-byte tail and for offset (unaligned) views; a pageable source is
-    refused before anything is launched."""
+    16-byte tail, for offset (unaligned) views and from 64 MiB up (the copy
+    engine's path); a pageable source is refused before anything is
+    launched."""
     from paper_2602_14493_b300 import GmrError, copy_h2d
 
     rng = np.random.default_rng(5)
-    for nbytes in (1, 15, 16, 17, 4096, 1 << 20, (25 << 20) + 12):
+    for nbytes in (1, 15, 16, 17, 4096, 1 << 20, (25 << 20) + 12, (64 << 20) + 5):
         src = torch.from_numpy(rng.integers(0, 256, nbytes, dtype=np.uint8)).pin_memory()
         dst = torch.zeros(nbytes, dtype=torch.uint8, device=DEV)
         copy_h2d(dst, src)
