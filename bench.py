@@ -640,6 +640,9 @@ def run_gmr(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "fp32", "data": "synthetic",
+        "step_ms_spread": {"median": float(np.median(step_ms)), "p10": float(np.percentile(step_ms, 10)),
+                           "p90": float(np.percentile(step_ms, 90)), "min": min(step_ms), "max": max(step_ms),
+                           "source": "CUDA events around each timed graph replay (this rank)"},
         "config": {"workload": args.workload, "views": C, "faces": F, "pixels_per_step": n_pix,
                    "form": "batched, one call for all views, CUDA graph", "tile": tile, "threads": threads, "threads_bwd": threads_bwd,
                    "batch": batch, "persistent": bool(persistent), "deterministic": bool(args.deterministic),

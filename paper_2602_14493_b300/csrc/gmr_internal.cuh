@@ -140,8 +140,7 @@ __device__ __forceinline__ int tile_class(uint32_t L) {
   const int bits = 32 - __clz((int)L);
   return kTileClasses - 1 - min(bits, kTileClasses - 1);
 }
-// Binary search of the view owning global tile g.
-// The view of binning tile g.
+// Binary search of the view owning binning tile g.
 __device__ __forceinline__ int find_view(const ViewInfo* views, int C, int g) {
   int lo = 0, hi = C - 1;
   while (lo < hi) {
