@@ -871,7 +871,7 @@ __device__ __forceinline__ void fwd_tile_ws(const RasterArgs& a, uint32_t pos, f
     }
     const int nl = warp_stage(ws, a, f, i, i < n, rec_base, ax, ay, rx0, rx1, ry0, ry1);
     for (int jj = 0; jj < nl; ++jj) {
-      if ((jj & 3) == 3) {  // the warp's early exit, checked every 4 entries
+      if ((jj & 7) == 7) {  // the warp's early exit, checked every 8 entries (every 2 or 4: 0.6-1.6% slower)
         bool wd2 = true;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) wd2 &= done[k];
