@@ -204,19 +204,21 @@ def oracle_sample_time(scene, n_pix, seed=0, keep=False):
 def cpu_baseline(scene, target_seconds, gpu_check=None):
     """The oracle timed on bounded samples of the workload's pixels, on every
     host core (OpenMP over pixels, records and faces; the headline value) and
-    on one thread. With gpu_check, the GPU's image at the all-cores sample's
-    pixels and its gradients for the same upstream gradient are compared with
-    the oracle's."""
+    on one thread, in its binned mode (each pixel walks the faces its 16x16
+    grid cell lists; bit-identical to its brute force). With gpu_check, the
+    GPU's image at the all-cores sample's pixels and its gradients for the
+    same upstream gradient are compared with the oracle's."""
     import oracle
 
     cores = oracle.set_threads(0)
+    was_binned = oracle.set_binned(True)
     # calibration on all cores: one pixel (the per-call conversion,
     # projection and depth sort of every record dominate) and 64 per core
     t_a, n_a = oracle_sample_time(scene, 1)
     t_b, n_b = oracle_sample_time(scene, 64 * cores)
     per_px = max((t_b - t_a) / max(n_b - n_a, 1), 1e-7)
     fixed = max(t_a - n_a * per_px, 0.0)
-    n = int(max(64, min(400000, (target_seconds - fixed) / per_px)))
+    n = int(max(64, min(4000000, (target_seconds - fixed) / per_px)))
     t, n, kept = oracle_sample_time(scene, n, seed=1, keep=True)
     # one thread: its per-pixel and fixed costs are at most `cores` times the
     # all-core ones (the parallel loops scale at best linearly), so this many
@@ -226,10 +228,11 @@ def cpu_baseline(scene, target_seconds, gpu_check=None):
     n1_req = int(max(8, min(n, (target_seconds - fixed * cores) / (per_px * cores))))
     t1, n1 = oracle_sample_time(scene, n1_req, seed=2)
     out = {"value": n / t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 brute-force fwd+bwd "
+           "sample": f"{n} random pixels of the {len(scene.cams)}-view workload, FP64 binned fwd+bwd "
                      f"on {cores} host threads (os.cpu_count() = {os.cpu_count()}), {t:.1f} s",
            "single_thread": {"value": n1 / t1 / 1e6, "unit": UNIT, "cores": 1,
                              "sample": f"{n1} random pixels, one thread, {t1:.1f} s"}}
+    oracle.set_binned(was_binned)
     if gpu_check is not None:
         out["parity"] = gpu_check(*kept)
     return out
@@ -266,12 +269,14 @@ def parity_with_oracle(r, v, f, c, o, cams, scene, pix, ref, g, bref):
 
 def run_reference(args, ws, rank):
     """The reference arm: the FP64 oracle (the paper publishes no code), fwd +
-    bwd of a bounded random pixel sample per step, on every host core."""
+    bwd of a bounded random pixel sample per step, on every host core, in
+    its binned mode."""
     if rank != 0:
         return
     import oracle
 
     cores = oracle.set_threads(0)
+    oracle.set_binned(True)
     scene = WORKLOADS[args.workload]()
     n_pix = args.ref_pixels
     for _ in range(args.warmup):
@@ -285,7 +290,7 @@ def run_reference(args, ws, rank):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "step": f"oracle fwd+bwd on {n_pix} random pixels"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{n_pix} random pixels per step, FP64 brute force, {cores} host threads"},
+                            "sample": f"{n_pix} random pixels per step, FP64 binned, {cores} host threads"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -724,7 +729,7 @@ def main():
                     help="with a fixed shape (block-staged backward): the fixed-order backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-pixels", type=int, default=128)
+    ap.add_argument("--ref-pixels", type=int, default=65536)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -53,6 +53,8 @@ def lib():
         L.gmr_oracle_sh_basis.argtypes = [i32, i64, P, P]
         L.gmr_oracle_set_threads.argtypes = [i32]
         L.gmr_oracle_set_threads.restype = i32
+        L.gmr_oracle_set_binned.argtypes = [i32]
+        L.gmr_oracle_set_binned.restype = i32
         _LIB = L
     return _LIB
 
@@ -61,6 +63,23 @@ def set_threads(n):
     """Host threads of the oracle's parallel loops (n < 1: every core).
     Returns the count in use. Results are bit-identical for every count."""
     return int(lib().gmr_oracle_set_threads(int(n)))
+
+
+_BINNED = False
+# The binned mode's grid lists every face whose o G can reach (1 - 1e-3)/255
+# at a pixel of the cell, which covers the flag bands up to this width.
+BINNED_MAX_ALPHA_BAND = 1e-3
+
+
+def set_binned(on):
+    """Binned compositing (each pixel walks the faces a 16 x 16-pixel grid
+    cell lists, built from each face's FP64 support, instead of every
+    visible face) for the calls that follow. Same decisions, order and
+    results as the brute force (tested); returns the previous setting."""
+    global _BINNED
+    prev = bool(lib().gmr_oracle_set_binned(1 if on else 0))
+    _BINNED = bool(on)
+    return prev
 
 
 def _p(a):
@@ -191,7 +210,8 @@ def _scene_args(scene, cov_mode, color_mode, bg, rgb=None):
 
 def render(scene, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, bands=DEFAULT_BANDS,
            opacity_scalar=1.0, sh_degree=0):
-    """Brute-force FP64 render of the given pixels (default: every pixel).
+    """FP64 render of the given pixels (default: every pixel), by brute
+    force over every visible face, or binned (set_binned).
     color_mode 0: per-face rgb [F,3]; 1: per-vertex rgb [V,3] (Eq. 16);
     2: spherical-harmonic coefficients [F,(sh_degree+1)^2,3]."""
     if pixels is None:
@@ -205,6 +225,8 @@ def render(scene, pixels=None, cov_mode=0, color_mode=0, bg=None, tile=16, bands
     nc = np.zeros(n, dtype=np.int32)
     fl = np.zeros(n, dtype=np.int32)
     bd = np.ascontiguousarray(np.asarray(bands, dtype=np.float64)) if bands is not None else None
+    if _BINNED and bd is not None and bd[0] > BINNED_MAX_ALPHA_BAND:
+        raise ValueError(f"binned mode covers alpha bands up to {BINNED_MAX_ALPHA_BAND}")
     rc = lib().gmr_oracle_render(len(v), _p(v), len(f), _p(f), _p(c), color_mode, _p(o), opacity_scalar,
                                  cov_mode, len(scene.cams), _p(cf), _p(ci), _p(b), tile, n, _p(pix), _p(out),
                                  _p(T), _p(last), _p(nc), _p(fl), _p(bd), sh_degree)
