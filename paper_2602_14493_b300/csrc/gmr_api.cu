@@ -212,8 +212,7 @@ gmr_status ensure_records(gmr_ctx* ctx, int64_t n, bool capturing) {
   if (capturing) return fail(ctx, GMR_ERR_STATE, "record workspace must grow during stream capture; call gmr_reserve");
   const int64_t cap = n + n / 4 + 1024;
   gmr_status s;
-  if ((s = realloc_exact(ctx, &w.rec_u, cap, "rec_u")) != GMR_OK) return s;
-  if ((s = realloc_exact(ctx, &w.rec_q, cap, "rec_q")) != GMR_OK) return s;
+  if ((s = realloc_exact(ctx, &w.rec_uq, 2 * cap, "rec_uq")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_rect, cap, "rec_rect")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_ntiles, cap, "rec_ntiles")) != GMR_OK) return s;
   if ((s = realloc_exact(ctx, &w.rec_key, cap, "rec_key")) != GMR_OK) return s;
@@ -550,7 +549,7 @@ gmr_status gmr_create(const gmr_config* cfg, gmr_ctx** out) {
 gmr_status gmr_destroy(gmr_ctx* ctx) {
   if (!ctx) return GMR_ERR_INVALID_ARG;
   Workspace& w = ctx->ws;
-  void* bufs[] = {w.rec_u, w.rec_q, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.rec_col, w.rec_cgrad,
+  void* bufs[] = {w.rec_uq, w.rec_rect, w.rec_ntiles, w.rec_key, w.rec_grad, w.rec_col, w.rec_cgrad,
                   w.face_col,
                   w.face_grad, w.pix_T, w.pix_last, w.pix_ncontrib, w.tile_count, w.tile_start, w.tile_range, w.long_tiles,
                   w.tile_order, w.tile_desc,
@@ -1053,7 +1052,8 @@ gmr_status gmr_debug_forward_state(gmr_ctx* ctx, uint32_t* depth_bits, int32_t* 
     GMR_CUDA(ctx, cudaMemcpyAsync(depth_bits, w.rec_key, sizeof(uint32_t) * (size_t)n_rec, cudaMemcpyDeviceToDevice,
                                   s));
   if (rec_u && n_rec > 0)
-    GMR_CUDA(ctx, cudaMemcpyAsync(rec_u, w.rec_u, sizeof(float4) * (size_t)n_rec, cudaMemcpyDeviceToDevice, s));
+    GMR_CUDA(ctx, cudaMemcpy2DAsync(rec_u, sizeof(float4), w.rec_uq, 2 * sizeof(float4), sizeof(float4), (size_t)n_rec,
+                                    cudaMemcpyDeviceToDevice, s));
   if (P > w.cap_pairs) return fail(ctx, GMR_ERR_CAPACITY, "pair buffer overflowed in the forward");
   if (ctx->split) {
     // the 8x8 tiles' lists sit at 4 start + q n of their binning tile's

@@ -422,8 +422,10 @@ struct Workspace {
   float4* verts4 = nullptr;
   // records: one per (view, face)
   int64_t cap_records = 0;
-  float4* rec_u = nullptr;       // (ux_hi, uy_hi, ux_lo, uy_lo)
-  float4* rec_q = nullptr;       // (a2, b2, c2, 0) pre-scaled conic
+  // one 32-byte record per (view, face), so that a gather touches one DRAM
+  // sector: [2 r] = (ux_hi, uy_hi, ux_lo, uy_lo) the image mean,
+  // [2 r + 1] = (a2, b2, c2, t2) the pre-scaled conic and skip threshold
+  float4* rec_uq = nullptr;
   uint2* rec_rect = nullptr;     // packed (x0 | x1 << 16, y0 | y1 << 16)
   uint32_t* rec_ntiles = nullptr;
   uint32_t* rec_key = nullptr;   // FP32 depth bits (0xffffffff when culled)

@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const float4* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C, int vpt,
     const float* __restrict__ rgb, const float* __restrict__ opacity, int color_mode, int sh_degree,
     float4* __restrict__ rec_col, float4* __restrict__ rec_cgrad,
-    const ViewInfo* __restrict__ views, int tile, float inv_tile, int bshift, int cov_mode, float4* __restrict__ rec_u,
-    float4* __restrict__ rec_q, uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
+    const ViewInfo* __restrict__ views, int tile, float inv_tile, int bshift, int cov_mode, float4* __restrict__ rec_uq,
+    uint2* __restrict__ rec_rect, uint32_t* __restrict__ rec_ntiles,
     uint32_t* __restrict__ rec_key, uint32_t* __restrict__ tile_count, float4* __restrict__ face_col,
     int64_t cap_pairs, unsigned long long* __restrict__ pair_tr, uint32_t* __restrict__ pair_rec,
     uint8_t* __restrict__ pair_quad, uint32_t* __restrict__ rec_slot, float4* __restrict__ rec_grad,
@@ -458,8 +458,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
           ProjRec p = project_rec(gm, v);
           df ux, uy;
           image_mean(m, v, ux, uy);
-          rec_u[rid] = make_float4(ux.hi, uy.hi, ux.lo, uy.lo);
-          rec_q[rid] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, t2);
+          rec_uq[2 * (size_t)rid] = make_float4(ux.hi, uy.hi, ux.lo, uy.lo);
+          rec_uq[2 * (size_t)rid + 1] = make_float4(p.qa * kNegHalfLog2e, p.qb * kNegLog2e, p.qc * kNegHalfLog2e, t2);
           if (sh_col) {
             const float3 col = sh_colour_any(sh_degree, rgb + (size_t)f * 3 * (sh_degree + 1) * (sh_degree + 1), a,
                                              b, cc, v);
@@ -615,7 +615,7 @@ template <int G, int L>
 __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
     const float4* __restrict__ verts, int32_t V, const int32_t* __restrict__ faces, int32_t F, int32_t C,
     const ViewInfo* __restrict__ views, int cov_mode, int color_mode, const float* __restrict__ rgb,
-    const float* __restrict__ opacity, const float4* __restrict__ rec_grad, const float4* __restrict__ rec_q,
+    const float* __restrict__ opacity, const float4* __restrict__ rec_grad, const float4* __restrict__ rec_uq,
     const float4* __restrict__ face_grad, const float4* __restrict__ rec_cgrad, float* __restrict__ dverts,
     float* __restrict__ drgb, float* __restrict__ dop, int accumulate, DetSums det) {
   pdl_enter();
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_proj_bwd(
           sh_colour_bwd<L >= 0 ? L : 0>(rgb + (size_t)f * 3 * K, g, views[c], make_float3(cg.x, cg.y, cg.z), dcoef,
                                         acc.dmu);
       }
-      if (geo) record_bwd(g, views[c], r0, r4, rec_q[rid], acc);
+      if (geo) record_bwd(g, views[c], r0, r4, rec_uq[2 * (size_t)rid + 1], acc);
     }
   }
   if (G > 1) {  // every lane of the warp takes part in the shuffles
@@ -849,7 +849,7 @@ cudaError_t launch_project(const float* verts, int32_t V, const int32_t* faces, 
                                  F, C, vpt, rgb,
                                  opacity,
                                  color_mode, sh_degree, ws.rec_col, ws.rec_cgrad, views, tile, 1.0f / (float)tile,
-                                 bshift, cov_mode, ws.rec_u, ws.rec_q,
+                                 bshift, cov_mode, ws.rec_uq,
                                  ws.rec_rect, ws.rec_ntiles, ws.rec_key, ws.tile_count, ws.face_col, ws.cap_pairs,
                                  ws.pair_key[1], ws.pair_face, bshift ? ws.pair_quad : nullptr,
                                  det ? ws.rec_slot : nullptr, ws.rec_grad, ws.face_grad, ws.counters);
@@ -886,7 +886,7 @@ cudaError_t launch_project_bwd(const float* verts, int32_t V, const int32_t* fac
   cudaError_t e = launch_chained(kern, true, dim3(blocks), dim3(kProjBwdThreads), 0, s, (const float4*)ws.verts4, V,
                                  faces, F, C, views,
                                  cov_mode, color_mode, rgb, opacity, (const float4*)ws.rec_grad,
-                                 (const float4*)ws.rec_q, (const float4*)ws.face_grad, (const float4*)ws.rec_cgrad,
+                                 (const float4*)ws.rec_uq, (const float4*)ws.face_grad, (const float4*)ws.rec_cgrad,
                                  dverts, drgb, dop, accumulate, ds);
   *launches += 1;
   if (e != cudaSuccess || !det) return e;

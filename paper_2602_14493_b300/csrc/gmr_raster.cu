@@ -176,15 +176,15 @@ __device__ __forceinline__ uint32_t unit_mask(float gx, float gy, float a2, floa
 // t2 = -log2(255 o).
 template <int TS, int NT, int BATCH, int NL = NT / 32>
 __device__ __forceinline__ void stage_batch(Stage<BATCH, NL>& st, const uint32_t* __restrict__ pair_face, uint32_t lo,
-                                            int count, uint32_t rec_base, const float4* __restrict__ rec_u,
-                                            const float4* __restrict__ rec_q, const float4* __restrict__ col_src,
+                                            int count, uint32_t rec_base, const float4* __restrict__ rec_uq,
+                                            const float4* __restrict__ col_src,
                                             bool col_by_rec, float ax, float ay, float tox, float toy,
                                             bool want_ids, bool units = false) {
   for (int i = threadIdx.x; i < count; i += NT) {
     uint32_t f = __ldg(pair_face + lo + i);
     uint32_t rid = rec_base + f;
-    float4 u = __ldg(rec_u + rid);
-    float4 q = __ldg(rec_q + rid);
+    float4 u = __ldg(rec_uq + 2 * (size_t)rid);
+    float4 q = __ldg(rec_uq + 2 * (size_t)rid + 1);
     float4 col = __ldg(col_src + (col_by_rec ? rid : f));
     float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
@@ -285,8 +285,7 @@ constexpr int kLayoutCta = 0, kLayoutHalf = 1, kLayoutWarp = 2;
 // Per-tile arguments of the compositing kernels.
 struct RasterArgs {
   const uint32_t* pair_face;
-  const float4* rec_u;
-  const float4* rec_q;
+  const float4* rec_uq;  // 32-byte records: [2 r] image mean, [2 r + 1] conic and threshold
   const float4* col;  // (r, g, b, o) per face, or per record when col_by_rec
   int col_by_rec;     // view-dependent colour: colours and their gradients per record
   const ViewInfo* views;
@@ -382,7 +381,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs& a, uint32_t pos, floa
     for (int k = 0; k < PPT; ++k) tdone &= done[k];
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
-    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.col,
+    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_uq, a.col,
                                a.col_by_rec != 0, ax, ay, tox, toy, MODE == kFwdDebug);
     __syncthreads();
     const int nl = warp_list<BATCH, NW>(st, cnt, 0, cnt, PixMap<TS, NT>::warp_bits());
@@ -606,7 +605,7 @@ __device__ __forceinline__ void fwd_tile_half(const RasterArgs& a, uint32_t pos,
     for (int k = 0; k < PPT; ++k) tdone &= done[k];
     if (__syncthreads_and(tdone)) break;
     int cnt = min(BATCH, n - base);
-    stage_batch<TS, NT, BATCH, 2 * NW>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_u, a.rec_q, a.col,
+    stage_batch<TS, NT, BATCH, 2 * NW>(st, a.pair_face, range.x + base, cnt, rec_base, a.rec_uq, a.col,
                                        a.col_by_rec != 0, ax, ay, tox, toy, MODE == kFwdDebug, true);
     __syncthreads();
     int n_max;
@@ -768,8 +767,8 @@ __device__ __forceinline__ int warp_stage(WarpSlots& ws, const RasterArgs& a, ui
   uint32_t rid = 0;
   if (valid) {
     rid = rec_base + f;
-    const float4 u = __ldg(a.rec_u + rid);
-    const float4 q = __ldg(a.rec_q + rid);
+    const float4 u = __ldg(a.rec_uq + 2 * (size_t)rid);
+    const float4 q = __ldg(a.rec_uq + 2 * (size_t)rid + 1);
     const float4 col = __ldg(a.col + (a.col_by_rec ? rid : f));
     const float ux = __fadd_rn(__fsub_rn(u.x, ax), u.z);
     const float uy = __fadd_rn(__fsub_rn(u.y, ay), u.w);
@@ -1117,7 +1116,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
   const int n_all = (int)(range.y - range.x);
   const bool one = n_all <= BATCH;
   if (one && n_all > 0)
-    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x, n_all, rec_base, a.rec_u, a.rec_q, a.col,
+    stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x, n_all, rec_base, a.rec_uq, a.col,
                                a.col_by_rec != 0, ax, ay, tox, toy, true);
 
   // SG = (colour composited behind the current Gaussian, plus T_final bg) . g
@@ -1199,7 +1198,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
     const int start = max(0, end - BATCH);
     if (!one) {
       __syncthreads();
-      stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
+      stage_batch<TS, NT, BATCH>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_uq,
                                  a.col, a.col_by_rec != 0, ax, ay, tox, toy, true);
       __syncthreads();
     }
@@ -1445,7 +1444,7 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
   for (int end = end_all; end > 0; end -= BATCH) {
     const int start = max(0, end - BATCH);
     __syncthreads();
-    stage_batch<TS, NT, BATCH, 2 * NW>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_u, a.rec_q,
+    stage_batch<TS, NT, BATCH, 2 * NW>(st, a.pair_face, range.x + start, end - start, rec_base, a.rec_uq,
                                        a.col, a.col_by_rec != 0, ax, ay, tox, toy, true, true);
     __syncthreads();
     int n_max;
@@ -1829,7 +1828,7 @@ __global__ void __launch_bounds__(kLossThreads) k_l2_loss(const float* __restric
   finish_loss_partial<kLossThreads>(bs, part, loss);
 }
 
-__global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_q, int64_t n_rec,
+__global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4* __restrict__ rec_uq, int64_t n_rec,
                                 int32_t* __restrict__ rects, float* __restrict__ conic) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_rec) return;
@@ -1841,7 +1840,7 @@ __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4
     rects[4 * k + 3] = (int32_t)(r.y >> 16);
   }
   if (conic) {
-    float4 q = rec_q[k];
+    float4 q = rec_uq[2 * k + 1];
     conic[4 * k] = q.x / kNegHalfLog2e;
     conic[4 * k + 1] = q.y / kNegLog2e;
     conic[4 * k + 2] = q.z / kNegHalfLog2e;
@@ -1879,8 +1878,7 @@ RasterArgs raster_args(const Workspace& ws, const uint4* tile_desc, int64_t n_po
                        const ViewInfo* views, int32_t F, const float* bg, bool col_by_record) {
   RasterArgs a;
   a.pair_face = pair_face;
-  a.rec_u = ws.rec_u;
-  a.rec_q = ws.rec_q;
+  a.rec_uq = ws.rec_uq;
   a.col = col_by_record ? ws.rec_col : ws.face_col;
   a.col_by_rec = col_by_record ? 1 : 0;
   a.views = views;
@@ -2035,7 +2033,7 @@ cudaError_t launch_raster_bwd(int tile, int threads, int batch, bool persistent,
 cudaError_t launch_debug_records(const Workspace& ws, int64_t n_rec, int32_t* rects, float* conic, cudaStream_t s,
                                  int64_t* launches) {
   if (n_rec <= 0) return cudaSuccess;
-  k_debug_records<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(ws.rec_rect, ws.rec_q, n_rec, rects, conic);
+  k_debug_records<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(ws.rec_rect, ws.rec_uq, n_rec, rects, conic);
   *launches += 1;
   return cudaGetLastError();
 }
