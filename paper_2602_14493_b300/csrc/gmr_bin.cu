@@ -8,9 +8,9 @@
 //     and k_place_keys writes each pair's 64-bit key (depth bits << 32 |
 //     face) to segment start + rank, with no atomics;
 //  2. the remaining digits, (depth bits, face), within each tile: segments
-//     of up to 512 keys (nearly all) are sorted by one warp each with a
-//     bitonic network, up to 256 keys in registers (shuffles only) and 257 to
-//     512 in shared memory; longer segments are listed and sorted by one CTA
+//     of up to 512 keys (nearly all) are sorted by one warp each: up to 256
+//     keys by a bitonic network in registers (shuffles only), 257 to 512 as
+//     two such halves merged through shared memory; longer segments are listed and sorted by one CTA
 //     each: up to 4096 keys by a merge sort in shared memory (register
 //     bitonic chunks, then merge-path rounds), beyond that by LSD radix
 //     passes through global memory on the 8-bit digits that differ within
@@ -45,7 +45,6 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 
 constexpr int kPlaceThreads = 256;
 constexpr int kPlaceUnroll = 4;  // pair slots per thread and round, their loads issued together
-constexpr int kPlaceBlocksPerSm = 6;  // resident at 40 registers per thread
 
 // Key of each pair slot of the projection to segment start + rank. The pair
 // count is known only on the device, so the grid is one wave (sized by the
@@ -227,7 +226,7 @@ __device__ __forceinline__ void warp_sort_segment(const unsigned long long* __re
   unsigned long long v[KPL];
 #pragma unroll
   for (int r = 0; r < KPL; ++r) {
-    const int e = lane * KPL + r;
+    const int e = r * 32 + lane;  // any input order suits a sort: the coalesced one
     v[r] = e < L ? gk[e] : ~0ull;
   }
   warp_bitonic<KPL>(v, lane);
@@ -238,32 +237,60 @@ __device__ __forceinline__ void warp_sort_segment(const unsigned long long* __re
   }
 }
 
-// Ascending bitonic sort of up to 512 64-bit keys by one warp in shared
-// memory (s holds 512 keys): each lane takes 8 of the 256 compare-exchange
-// pairs of every stage.
-__device__ __forceinline__ void warp_sort_smem512(const unsigned long long* __restrict__ gk, int L,
-                                                  uint32_t* __restrict__ out, unsigned long long* s, int lane) {
-  for (int i = lane; i < 512; i += 32) s[i] = i < L ? gk[i] : ~0ull;
-  __syncwarp();
+// Position of element e (0..255) of a sorted half in shared memory: e with
+// its low four bits XORed with the next four. For each register r, the 32
+// lanes' elements lane * 8 + r then fall on distinct 8-byte bank pairs two
+// by two (two wavefronts, the minimum for 256 bytes).
+__device__ __forceinline__ int swz16(int e) { return e ^ ((e >> 4) & 15); }
+
+// Ascending sort of 257 to 512 64-bit keys by one warp (s holds 512 keys):
+// each half of 256 is sorted in registers (the second padded with all-ones
+// keys) and stored to s in the swizzled order; then lane l merges outputs
+// 16 l .. 16 l + 15 of the two sorted halves (merge path: a binary search
+// for where that output diagonal crosses them, taking from the first half
+// on ties, then 16 sequential steps) and writes their face ids. (A bitonic
+// network over the 512 keys in shared memory took 45 exchange stages, each
+// lane 8 pairs of loads and stores per stage, and was bound by the
+// shared-memory instruction queue.)
+__device__ __forceinline__ void warp_sort_512(const unsigned long long* __restrict__ gk, int L,
+                                              uint32_t* __restrict__ out, unsigned long long* s, int lane) {
 #pragma unroll 1
-  for (int k = 2; k <= 512; k <<= 1) {
-#pragma unroll 1
-    for (int j = k >> 1; j > 0; j >>= 1) {
+  for (int h = 0; h < 2; ++h) {
+    unsigned long long v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int p = q * 32 + lane;                  // pair index 0..255
-        const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));  // lower element of the pair
-        const unsigned long long a = s[i], b = s[i + j];
-        const bool asc = (i & k) == 0;
-        if ((a > b) == asc) {
-          s[i] = b;
-          s[i + j] = a;
-        }
-      }
-      __syncwarp();
+    for (int r = 0; r < 8; ++r) {
+      const int e = h * 256 + r * 32 + lane;
+      v[r] = e < L ? gk[e] : ~0ull;
+    }
+    warp_bitonic<8>(v, lane);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[h * 256 + swz16(lane * 8 + r)] = v[r];
+  }
+  __syncwarp();
+  const unsigned long long* A = s;
+  const unsigned long long* B = s + 256;
+  const int d = lane * 16;
+  int lo = max(0, d - 256), hi = min(d, 256);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (A[swz16(mid)] <= B[swz16(d - 1 - mid)]) lo = mid + 1;
+    else hi = mid;
+  }
+  int i = lo, j = d - lo;
+  unsigned long long a = i < 256 ? A[swz16(i)] : ~0ull, b = j < 256 ? B[swz16(j)] : ~0ull;
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    const bool take_a = j >= 256 || (i < 256 && a <= b);
+    if (d + k < L) out[d + k] = (uint32_t)(take_a ? a : b);
+    if (take_a) {
+      ++i;
+      a = i < 256 ? A[swz16(i)] : ~0ull;
+    } else {
+      ++j;
+      b = j < 256 ? B[swz16(j)] : ~0ull;
     }
   }
-  for (int i = lane; i < L; i += 32) out[i] = (uint32_t)s[i];
+  __syncwarp();
 }
 
 constexpr int kWarpSortMax = 512;   // keys sorted by one warp
@@ -274,8 +301,9 @@ constexpr int kTilesPerCta = kTileSortThreads / 32;
 // order: write the range and, at position w, the tile's descriptor (tile,
 // view, range) for the compositing CTA w; sort segments of up to 256 keys
 // in registers (8 per lane at most, which keeps the register count and so
-// the occupancy at that of the common case) and of 257 to 512 keys in
-// shared memory; list longer segments for k_long_sort.
+// the occupancy at that of the common case) and of 257 to 512 keys as two
+// register-sorted halves merged through shared memory; list longer segments
+// for k_long_sort.
 __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
     const uint32_t* __restrict__ tile_start, int64_t n_tiles, const unsigned long long* __restrict__ keys,
     uint32_t* __restrict__ pair_face, uint2* __restrict__ ranges, uint32_t* __restrict__ long_list,
@@ -322,7 +350,7 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(
   } else if (L <= 256) {
     warp_sort_segment<8>(gk, L, out, lane);
   } else if (L <= kWarpSortMax) {
-    warp_sort_smem512(gk, L, out, s_keys[threadIdx.x >> 5], lane);
+    warp_sort_512(gk, L, out, s_keys[threadIdx.x >> 5], lane);
   } else if (lane == 0) {
     long_list[atomicAdd(&counters->n_long, 1u)] = (uint32_t)t;
   }
@@ -551,11 +579,12 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
                              int64_t n_tiles, bool split, cudaStream_t s, int64_t* launches) {
   if (n_rec > 0 && ws.cap_pairs > 0) {
-    // one wave: kPlaceBlocksPerSm blocks per SM (148 SMs), or fewer for a
-    // small pair capacity
+    // one wave (the blocks that are resident at once), or fewer for a small
+    // pair capacity: a grid sized for more blocks per SM than its registers
+    // allow runs the rest as a second wave as long as the first
     const int64_t blocks = std::min<int64_t>((ws.cap_pairs + kPlaceThreads * kPlaceUnroll - 1) /
                                                  (kPlaceThreads * kPlaceUnroll),
-                                             148 * kPlaceBlocksPerSm);
+                                             resident_grid(k_place_keys, kPlaceThreads));
     cudaError_t e = launch_chained(k_place_keys, true, dim3((unsigned)blocks), dim3(kPlaceThreads), 0, s,
                                    (const unsigned long long*)ws.pair_key[1], (const uint32_t*)ws.pair_face,
                                    split ? (const uint8_t*)ws.pair_quad : nullptr, (const uint32_t*)ws.rec_key, F,
@@ -580,7 +609,8 @@ cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, cons
                        (const unsigned long long*)ws.pair_key[0], ws.pair_face, ws.tile_range, ws.long_tiles,
                        (const uint32_t*)ws.tile_order, views, C, ws.tile_desc, ws.counters, ws.cap_pairs);
     if (e != cudaSuccess) return e;
-    e = launch_chained(k_long_sort, true, dim3(148 * 3), dim3(kSegThreads), kLongSortSmem, s,
+    e = launch_chained(k_long_sort, true, dim3((unsigned)resident_grid(k_long_sort, kSegThreads, kLongSortSmem)),
+                       dim3(kSegThreads), kLongSortSmem, s,
                        (const uint32_t*)ws.long_tiles, ws.counters, (const uint2*)ws.tile_range,
                        ws.pair_key[0], ws.pair_key[1], ws.pair_face);
     *launches += 2;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <utility>
 
 #include "gmr.h"
@@ -665,5 +667,30 @@ cudaError_t launch_regularizers(const float* verts, int32_t V, const int32_t* fa
 // out[0] = mean_a min_b |a - b|^2, out[1] = mean_b min_a |b - a|^2; scratch: na + nb floats
 cudaError_t launch_chamfer(const float* a, int64_t na, const float* b, int64_t nb, float* scratch, double* out,
                            cudaStream_t s, int64_t* launches);
+
+template <typename K>
+inline int resident_grid(K kern, int threads, size_t smem = 0) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 148;
+  }
+  const int n = std::max(1, per_sm) * std::max(1, sms);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = n;
+  return n;
+}
+
 
 }  // namespace gmr

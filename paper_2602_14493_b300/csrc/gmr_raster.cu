@@ -1848,32 +1848,6 @@ __global__ void k_debug_records(const uint2* __restrict__ rec_rect, const float4
   }
 }
 
-// Resident CTAs of a compositing kernel on the current device (a persistent
-// grid's size), looked up once per kernel and device.
-template <typename K>
-int resident_grid(K kern, int threads) {
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, int> cache;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-  const auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-  }
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return 148;
-  }
-  const int n = std::max(1, per_sm) * std::max(1, sms);
-  std::lock_guard<std::mutex> lock(mu);
-  cache[key] = n;
-  return n;
-}
-
 RasterArgs raster_args(const Workspace& ws, const uint4* tile_desc, int64_t n_pos, const uint32_t* pair_face,
                        const ViewInfo* views, int32_t F, const float* bg, bool col_by_record) {
   RasterArgs a;
