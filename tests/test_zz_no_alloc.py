@@ -38,7 +38,8 @@ def test_noalloc_loss_matches_context_loss_on_two_calls():
         assert abs(float(loss) - float(ref_loss)) <= 1e-12 * abs(float(ref_loss))
         expect = float(((img.double() - tgt.double()) ** 2).sum())
         assert abs(float(loss) - expect) <= 1e-6 * expect
-    # sizes beyond the fixed scratch array are rejected before anything runs
+    # sizes beyond the entry point's stated maximum (GMR_L2_NOALLOC_MAX_ELEMS)
+    # are rejected before anything runs
     st = L.gmr_l2_loss_noalloc(_p(img), _p(tgt), _lib.GMR_L2_NOALLOC_MAX_ELEMS + 1, _p(grad), _p(loss), stream)
     assert st == 4  # GMR_ERR_CAPACITY
     assert L.gmr_l2_loss_noalloc(_p(img), _p(tgt), -1, _p(grad), _p(loss), stream) == 1
