@@ -1219,11 +1219,16 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
         any |= con[k];
       }
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (any) {
+      const uint32_t cm = __ballot_sync(kFull, any);
+      if (cm != 0u) {
         const float4 col = st.col[j];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          if (!con[k]) continue;
+          // one vote per pixel slot: the lanes without a contribution
+          // compute along and keep their state (a divergent branch per
+          // slot measured 1.7% slower in the half-warp backward, 2.8% in
+          // the block-staged one)
+          if (!__any_sync(kFull, con[k])) continue;
           float graw;
           float alpha = gauss_alpha(p2[k], hh.z, graw);
           float om = __fsub_rn(1.0f, alpha);
@@ -1234,9 +1239,11 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
           // T_i (c.g) - S.g / (1 - alpha) = (T_(i+1) (c.g) - S.g) / (1 - alpha):
           // the difference of the two (often nearly equal) terms in one FMA
           float dalpha = inv * __fmaf_rn(T[k], cg, -SG[k]);
-          SG[k] += w * cg;
-          T[k] = Tb;
-          float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
+          const float sg_new = SG[k] + w * cg;
+          SG[k] = con[k] ? sg_new : SG[k];
+          T[k] = con[k] ? Tb : T[k];
+          w = con[k] ? w : 0.0f;
+          float dq = (con[k] && graw < kAlphaMax) ? dalpha * alpha : 0.0f;
           float qx = dq * dxs[k], qy = dq * dys[k];
           acc[0] += qx;
           acc[1] += qy;
@@ -1249,7 +1256,6 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs& a, uint32_t pos, cons
           acc[8] += w * G2[k];
         }
       }
-      const uint32_t cm = __ballot_sync(kFull, any);
       if (DET) {  // this warp's share of entry j (zeros when it has none)
         float sv = 0.0f, s8 = 0.0f;
         if (cm != 0u) {
@@ -1466,11 +1472,16 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
         any |= con[k];
       }
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (any) {
+      const uint32_t cm = __ballot_sync(kFull, any);
+      if (cm != 0u) {
         const float4 col = st.col[j];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          if (!con[k]) continue;
+          // one vote per pixel slot: the lanes without a contribution
+          // compute along and keep their state (a divergent branch per
+          // slot measured 1.7% slower in the half-warp backward, 2.8% in
+          // the block-staged one)
+          if (!__any_sync(kFull, con[k])) continue;
           float graw;
           float alpha = gauss_alpha(p2[k], hh.z, graw);
           float om = __fsub_rn(1.0f, alpha);
@@ -1479,9 +1490,11 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
           float w = alpha * Tb;
           float cg = col.x * G0[k] + col.y * G1[k] + col.z * G2[k];
           float dalpha = inv * __fmaf_rn(T[k], cg, -SG[k]);
-          SG[k] += w * cg;
-          T[k] = Tb;
-          float dq = (graw < kAlphaMax) ? dalpha * alpha : 0.0f;
+          const float sg_new = SG[k] + w * cg;
+          SG[k] = con[k] ? sg_new : SG[k];
+          T[k] = con[k] ? Tb : T[k];
+          w = con[k] ? w : 0.0f;
+          float dq = (con[k] && graw < kAlphaMax) ? dalpha * alpha : 0.0f;
           float qx = dq * dxs[k], qy = dq * dys[k];
           acc[0] += qx;
           acc[1] += qy;
@@ -1494,7 +1507,6 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
           acc[8] += w * G2[k];
         }
       }
-      const uint32_t cm = __ballot_sync(kFull, any);
       if (cm == 0u) continue;
       const uint32_t cm_half = (lane & 16) ? (cm >> 16) : (cm & 0xffffu);
       const uint32_t ci = a.col_by_rec ? st.rid[j] : st.face[j];
@@ -1664,6 +1676,9 @@ __device__ __forceinline__ void bwd_tile_ws(const RasterArgs& a, uint32_t pos, c
         const float4 col = ws.col[jj];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
+          // (a divergent branch per pixel slot: computing the chain on every
+          // lane after one vote per slot, as the other layouts do, was 3.5%
+          // slower here, where few lanes contribute per entry)
           if (!con[k]) continue;
           float graw;
           float alpha = gauss_alpha(p2[k], hh.z, graw);
