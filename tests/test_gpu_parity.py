@@ -68,11 +68,56 @@ def test_convert_matches_oracle(cov_mode, color_mode):
     r.close()
 
 
+@pytest.mark.parametrize("cov_mode", ["area", "embed_raw"])
+def test_convert_invariant_to_vertex_order_and_rigid_motion(cov_mode):
+    """The GPU conversion does not depend on which vertex of a face comes
+    first or on the face's orientation (the covariance is a symmetric
+    function of the three vertices and enters through n n^T), and it is
+    equivariant under rigid motions: mu(Q v + t) = Q mu(v) + t and
+    Sigma(Q v + t) = Q Sigma(v) Q^T (Sec. 2.2). Both FP32 results are within
+    1e-5 of the exact covariance (test above), so they agree to 2e-5."""
+    from paper_2602_14493_b300 import Renderer
+
+    r = Renderer(cov_mode=cov_mode)
+    s = gi.random_triangle_soup(7, 2000)
+    v, f, c, o = to_dev(s, s.rgb)
+
+    def conv(vv, ff):
+        out = r.convert(vv, ff, c, o)
+        torch.cuda.synchronize()
+        cv = out["cov"].cpu().numpy().astype(np.float64)
+        full = np.stack([cv[:, [0, 1, 2]], cv[:, [1, 3, 4]], cv[:, [2, 4, 5]]], 1)
+        return out["means"].cpu().numpy().astype(np.float64), full
+
+    m0, c0 = conv(v, f)
+    scale = np.abs(c0).reshape(len(c0), -1).max(1)[:, None, None]
+    mscale = np.abs(m0).max()
+    for perm in ([1, 2, 0], [2, 0, 1], [0, 2, 1]):
+        m1, c1 = conv(v, f[:, perm].contiguous())
+        assert np.abs(m1 - m0).max() <= 1e-6 * mscale
+        assert np.all(np.abs(c1 - c0) <= 2e-5 * scale + 1e-13)
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    t = rng.normal(size=3)
+    vq = (s.verts.astype(np.float64) @ Q.T + t).astype(np.float32)
+    m2, c2 = conv(torch.from_numpy(vq).to(v.device), f)
+    np.testing.assert_allclose(m2, m0 @ Q.T + t, atol=2e-6 * (mscale + np.abs(t).max()))
+    rot = np.einsum("ij,fjk,lk->fil", Q, c0, Q)
+    # the moved vertices are rounded to FP32 (relative 2^-24 of their
+    # magnitude), which moves a face's covariance by up to ~4 |edge| |dv|
+    vv = s.verts.astype(np.float64)[s.faces]
+    edge = np.linalg.norm(vv - vv.mean(1, keepdims=True), axis=2).max(1)[:, None, None]
+    dv = 2.0 ** -24 * max(np.abs(vq).max(), np.abs(s.verts).max())
+    assert np.all(np.abs(c2 - rot) <= 2e-5 * scale + 8.0 * edge * dv + 1e-13)
+    assert r.device_status() == 0
+    r.close()
+
+
 # ------------------------------------------------------------------ binning
 def _dense_scene():
     """A level-6 icosphere (81,920 faces) in a 128^2 and a 256^2 view: with
     16x16 tiles, segments of every length class of the per-tile sort (up to
-    256 keys in registers, 257-512 in shared memory, 513-1024 and 1025-4096
+    256 keys in registers, 257-512 as two register halves merged, 513-1024 and 1025-4096
     by the CTA merge sort, longer by radix passes: the longest holds 4,920
     keys)."""
     v, f = gi.icosphere(6)
