@@ -1068,11 +1068,18 @@ __device__ __forceinline__ float warp_reduce8_transposed(const float v[8], int l
 constexpr int kBwdDirectLanes = GMR_BWD_DIRECT_LANES;
 // The same for the warp-staged layout (swept 8, 12, 20, 32 on three
 // workloads: 12 is best there, 3-5% faster backward than 20; the block-staged
-// and half-warp layouts keep 20).
+// layout keeps 20).
 #ifndef GMR_BWD_DIRECT_LANES_WS
 #define GMR_BWD_DIRECT_LANES_WS 12
 #endif
 constexpr int kBwdDirectLanesWs = GMR_BWD_DIRECT_LANES_WS;
+// The same per 16-lane half in the half-warp layout (both halves under it;
+// swept 10-16 on the 64-view workload with the predicated chain: 12 and 14
+// 2% faster than 10, 16, never reducing, 33% slower).
+#ifndef GMR_BWD_DIRECT_LANES_HALF
+#define GMR_BWD_DIRECT_LANES_HALF 12
+#endif
+constexpr int kBwdDirectLanesHalf = GMR_BWD_DIRECT_LANES_HALF;
 
 // LOSS: dL/dimg = 2 (img - target) is formed from bl.img and bl.target (the
 // squared-error loss), and each warp writes its pixels' sum of squared
@@ -1534,7 +1541,7 @@ __device__ __forceinline__ void bwd_tile_half(const RasterArgs& a, uint32_t pos,
       if (cm == 0u) continue;
       const uint32_t cm_half = (lane & 16) ? (cm >> 16) : (cm & 0xffffu);
       const uint32_t ci = a.col_by_rec ? st.rid[j] : st.face[j];
-      if (__popc(cm & 0xffffu) <= kBwdDirectLanes / 2 && __popc(cm >> 16) <= kBwdDirectLanes / 2) {
+      if (__popc(cm & 0xffffu) <= kBwdDirectLanesHalf && __popc(cm >> 16) <= kBwdDirectLanesHalf) {
         if (any) {
           float4* rg = rec_grad + 2 * (size_t)st.rid[j];
           atomicAdd(rg, make_float4(acc[0], acc[1], acc[2], acc[3]));
