@@ -220,6 +220,14 @@ def cpu_baseline(scene, target_seconds, gpu_check=None):
     fixed = max(t_a - n_a * per_px, 0.0)
     n = int(max(64, min(4000000, (target_seconds - fixed) / per_px)))
     t, n, kept = oracle_sample_time(scene, n, seed=1, keep=True)
+    # the two calibration calls are single timings: when one was noisy and
+    # the sample ended well short of the target, size it again from its own
+    # rate (once)
+    if t < 0.5 * target_seconds and n < 4000000:
+        per_px_s = max((t - fixed) / n, 1e-7)
+        n2 = int(min(4000000, (target_seconds - fixed) / per_px_s))
+        if n2 > 1.5 * n:
+            t, n, kept = oracle_sample_time(scene, n2, seed=1, keep=True)
     # one thread: its per-pixel and fixed costs are at most `cores` times the
     # all-core ones (the parallel loops scale at best linearly), so this many
     # pixels take at most about target_seconds
