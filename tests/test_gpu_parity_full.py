@@ -29,7 +29,9 @@ pytestmark = pytest.mark.gpu
 
 # launch shapes (tile, forward threads, backward threads[, persistent[,
 # layout of both directions | forward layout, backward layout]]); layouts:
-# 0 staging by the thread block, 1 half-warp, 2 staging by each warp
+# 0 staging by the thread block, 1 half-warp, 2 staging by each warp. The
+# autotuner's shapes: (16, 128, 128, 0, 2, 1) on the 64-view workload,
+# (16, 128, 128, 0, 2, 0) on the ring, (8, 64, 32, 0, 2, 2) on the level-8 mesh.
 BENCH_SHAPE = (16, 256, 128)
 TUNED_SHAPE = (16, 128, 128, 0, 2, 1)
 
@@ -73,7 +75,8 @@ def test_fibonacci_64_uneven_views_full_size():
     s = gi.scene_fibonacci_uneven()
     assert len(s.cams) == 64 and s.n_pixels > 20_000_000
     _check(s, ((16, 128, 128), BENCH_SHAPE, (32, 256, 256), BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1),
-               BENCH_SHAPE + (0, 2), TUNED_SHAPE, (8, 64, 64), (8, 32, 64, 0, 2), (8, 64, 32, 0, 2, 1)),
+               BENCH_SHAPE + (0, 2), TUNED_SHAPE, (16, 128, 128, 0, 2, 0), (8, 64, 64), (8, 32, 64, 0, 2),
+               (8, 64, 32, 0, 2, 1)),
            n_random=256, window=4, seed=301)
 
 
@@ -81,5 +84,6 @@ def test_large_mesh_16_views_1024_full_size():
     s = gi.scene_large()
     assert len(s.faces) == 1_310_720 and s.n_pixels == 16 * 1024 * 1024
     _check(s, (BENCH_SHAPE, BENCH_SHAPE + (1,), BENCH_SHAPE + (0, 1), BENCH_SHAPE + (0, 2), TUNED_SHAPE, (8, 64, 64),
-               (8, 64, 64, 0, 2), (8, 64, 32, 1), (8, 64, 32, 0, 2, 1), (8, 32, 64, 0, 1, 2)), n_random=128,
+               (8, 64, 64, 0, 2), (8, 64, 32, 1), (8, 64, 32, 0, 2, 1), (8, 32, 64, 0, 1, 2), (8, 64, 32, 0, 2, 2)),
+           n_random=128,
            window=4, seed=401)
