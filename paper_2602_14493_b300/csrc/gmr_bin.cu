@@ -33,6 +33,8 @@ constexpr int kSegThreads = 256;
 constexpr int kSegWarps = kSegThreads / 32;
 constexpr int kSegSmem = 4096;  // keys of a long segment sorted in shared memory
 constexpr int kRadix = 256;
+// the radix pass gives each digit one thread of the CTA (its run offsets)
+static_assert(kSegThreads == kRadix, "cta_radix_pass: one thread per digit");
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
@@ -44,16 +46,18 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 }
 
 constexpr int kPlaceThreads = 256;
-constexpr int kPlaceUnroll = 4;  // pair slots per thread and round, their loads issued together
 
 // Key of each pair slot of the projection to segment start + rank. The pair
 // count is known only on the device, so the grid is one wave (sized by the
 // device, not by the pair capacity: a workspace grown by a larger earlier
 // forward would otherwise launch many blocks with nothing to do) striding over
-// rounds of kPlaceUnroll slots per thread; the slot loads of a round, then
-// their gathers, are issued together, so the dependent gathers overlap.
+// rounds of U slots per thread; the slot loads of a round, then their
+// gathers, are issued together, so the dependent gathers overlap (the
+// kernel waits on them: more in flight per thread pays once there are
+// enough pairs to fill the wave, see launch_bin_pairs).
 // With split binning (pair_quad) the key's low word is face << 4 | the
 // pair's quadrants: the order by (depth, face) is unchanged.
+template <int U>
 __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
     const unsigned long long* __restrict__ pair_tr, const uint32_t* __restrict__ pair_rec,
     const uint8_t* __restrict__ pair_quad, const uint32_t* __restrict__ rec_key, int32_t F,
@@ -62,25 +66,25 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place_keys(
   pdl_enter();
   const int64_t n = counters->n_pairs;
   if (n > cap) return;  // overflow: the pair scratch is incomplete
-  constexpr int64_t kRound = (int64_t)kPlaceThreads * kPlaceUnroll;
+  constexpr int64_t kRound = (int64_t)kPlaceThreads * U;
   for (int64_t base = (int64_t)blockIdx.x * kRound; base < n; base += (int64_t)gridDim.x * kRound) {
-    unsigned long long tr[kPlaceUnroll];
-    uint32_t rid[kPlaceUnroll], key[kPlaceUnroll], start[kPlaceUnroll], quad[kPlaceUnroll];
+    unsigned long long tr[U];
+    uint32_t rid[U], key[U], start[U], quad[U];
 #pragma unroll
-    for (int u = 0; u < kPlaceUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * kPlaceThreads + threadIdx.x;
       tr[u] = i < n ? pair_tr[i] : 0ull;
       rid[u] = i < n ? pair_rec[i] : 0u;
       quad[u] = (pair_quad && i < n) ? pair_quad[i] : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < kPlaceUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * kPlaceThreads + threadIdx.x;
       key[u] = i < n ? rec_key[rid[u]] : 0u;
       start[u] = i < n ? tile_start[(uint32_t)(tr[u] >> 32)] : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < kPlaceUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * kPlaceThreads + threadIdx.x;
       if (i < n) {
         const uint32_t c = rid[u] / (uint32_t)F;
@@ -579,13 +583,19 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
                              int64_t n_tiles, bool split, cudaStream_t s, int64_t* launches) {
   if (n_rec > 0 && ws.cap_pairs > 0) {
+    // slots per thread and round by the pair capacity (the pair count itself
+    // is on the device): 4 up to 4M pairs, 8 up to 32M, 12 beyond (swept 4-12:
+    // 8 took the 64-view workload's binning 0.509 -> 0.472 ms, 12 the level-8
+    // mesh's 2.06 -> 1.78 ms; on the 0.64M pairs of 8 views of a 20K-face mesh
+    // 4 is 7% faster than 8: fewer, longer threads leave SMs idle)
+    const int U = ws.cap_pairs <= (int64_t(4) << 20) ? 4 : ws.cap_pairs <= (int64_t(32) << 20) ? 8 : 12;
+    auto kern = U == 4 ? k_place_keys<4> : U == 8 ? k_place_keys<8> : k_place_keys<12>;
     // one wave (the blocks that are resident at once), or fewer for a small
     // pair capacity: a grid sized for more blocks per SM than its registers
     // allow runs the rest as a second wave as long as the first
-    const int64_t blocks = std::min<int64_t>((ws.cap_pairs + kPlaceThreads * kPlaceUnroll - 1) /
-                                                 (kPlaceThreads * kPlaceUnroll),
-                                             resident_grid(k_place_keys, kPlaceThreads));
-    cudaError_t e = launch_chained(k_place_keys, true, dim3((unsigned)blocks), dim3(kPlaceThreads), 0, s,
+    const int64_t blocks = std::min<int64_t>((ws.cap_pairs + kPlaceThreads * U - 1) / (kPlaceThreads * U),
+                                             resident_grid(kern, kPlaceThreads));
+    cudaError_t e = launch_chained(kern, true, dim3((unsigned)blocks), dim3(kPlaceThreads), 0, s,
                                    (const unsigned long long*)ws.pair_key[1], (const uint32_t*)ws.pair_face,
                                    split ? (const uint8_t*)ws.pair_quad : nullptr, (const uint32_t*)ws.rec_key, F,
                                    (const uint32_t*)ws.tile_start, ws.cap_pairs, ws.pair_key[0],
