@@ -583,12 +583,13 @@ __global__ void k_expand_tiles(const uint2* __restrict__ ranges, int64_t n_tiles
 cudaError_t launch_bin_pairs(const Workspace& ws, int64_t n_rec, int32_t F, const ViewInfo* views, int32_t C,
                              int64_t n_tiles, bool split, cudaStream_t s, int64_t* launches) {
   if (n_rec > 0 && ws.cap_pairs > 0) {
-    // slots per thread and round by the pair capacity (the pair count itself
-    // is on the device): 4 up to 4M pairs, 8 up to 32M, 12 beyond (swept 4-12:
-    // 8 took the 64-view workload's binning 0.509 -> 0.472 ms, 12 the level-8
-    // mesh's 2.06 -> 1.78 ms; on the 0.64M pairs of 8 views of a 20K-face mesh
+    // slots per thread and round by the workload's size (the pair count is
+    // on the device; the records, 1-3 pairs each, are known here): 4 up to
+    // 1M records, 8 up to 10M, 12 beyond (swept 4-12: 8 took the 64-view
+    // workload's binning, 5.2M records, 0.509 -> 0.472 ms, 12 the level-8
+    // mesh's, 21M records, 2.06 -> 1.78 ms; on 8 views of a 20K-face mesh
     // 4 is 7% faster than 8: fewer, longer threads leave SMs idle)
-    const int U = ws.cap_pairs <= (int64_t(4) << 20) ? 4 : ws.cap_pairs <= (int64_t(32) << 20) ? 8 : 12;
+    const int U = n_rec <= (int64_t(1) << 20) ? 4 : n_rec <= int64_t(10) * (1 << 20) ? 8 : 12;
     auto kern = U == 4 ? k_place_keys<4> : U == 8 ? k_place_keys<8> : k_place_keys<12>;
     // one wave (the blocks that are resident at once), or fewer for a small
     // pair capacity: a grid sized for more blocks per SM than its registers
