@@ -543,9 +543,12 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_quads(const uint4* __re
     valid[q] = 2 * bx + (q & 1) < v.tiles_x && 2 * by + (q >> 1) < v.tiles_y;
     cnt[q] = 0;
   }
+  // the next chunk's entries are loaded before this chunk is dealt
+  uint32_t e_next = lane < n ? __ldg(pair_face + d.z + lane) : 0u;
   for (uint32_t c = 0; c < n; c += 32) {
     const uint32_t i = c + lane;
-    const uint32_t e = i < n ? __ldg(pair_face + d.z + i) : 0u;
+    const uint32_t e = e_next;
+    e_next = i + 32 < n ? __ldg(pair_face + d.z + i + 32) : 0u;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool in = valid[q] && ((e >> q) & 1u);
