@@ -517,3 +517,55 @@ def test_nonfinite_vertices_are_culled_and_match_oracle():
     assert rel_l2(dvn, ob["dverts"]) <= GRAD_TOL
     assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
     r.close()
+
+
+def test_view_beyond_2_31_pixels_matches_oracle():
+    """A single 50,000 x 46,000 view (2.3G pixels: packed pixel indices past
+    2^31 in its bottom 3,050 rows, image element indices past 2^32), the
+    sphere placed low in the view so that those rows cover it: the image,
+    the final transmittance and the gradients match the oracle at sampled
+    pixels on both sides of 2^31, in the default and the benchmark's launch
+    shape. About 120 GB of device memory."""
+    from paper_2602_14493_b300 import Renderer
+
+    W, H = 50_000, 46_000
+    v, f = gi.icosphere(2)
+    rng = np.random.default_rng(231)
+    cam = gi.look_at((3.0, 0.0, 0.0), W, H, target=(0.0, 0.0, 0.8))
+    s = gi.Scene("sphere2_50000x46000", v.astype(np.float32), f, rng.random((len(f), 3)).astype(np.float32),
+                 np.full(len(f), 0.9, np.float32), np.array([cam]))
+    assert s.n_pixels > 2 ** 31
+    xs = rng.integers(0, W, 96)
+    ys = np.concatenate([rng.integers(0, H, 48), rng.integers(43_000, H, 48)])
+    win_y, win_x = np.meshgrid(np.arange(45_000, 45_008), np.arange(24_996, 25_004), indexing="ij")
+    pix = np.concatenate([np.stack([np.zeros(96, int), xs, ys], 1),
+                          np.stack([np.zeros(64, int), win_x.ravel(), win_y.ravel()], 1),
+                          [[0, W - 1, H - 1], [0, 0, H - 1]]]).astype(np.int32)
+    pix = np.unique(pix, axis=0)
+    lin = pix[:, 2].astype(np.int64) * W + pix[:, 1]
+    assert (lin >= 2 ** 31).sum() >= 60
+    ref = oracle.render(s, pixels=pix)
+    amb = (ref["flags"] & (oracle.FLAG_ALPHA_SKIP | oracle.FLAG_TERMINATE)) != 0
+    inside = ref["n_contrib"] > 0
+    assert inside[lin >= 2 ** 31].sum() >= 30  # the sphere covers pixels past 2^31
+    gs = rng.normal(size=(len(pix), 3))
+    gs[ref["flags"] != 0] = 0.0
+    ob = oracle.backward(s, gs.astype(np.float32).astype(np.float64), pixels=pix)
+    vd, fd, cd, od = to_dev(s)
+    lin_t = torch.from_numpy(lin).to(DEV)
+    for shape in ({}, dict(threads=128, threads_bwd=128, warp_fwd=True, half_bwd=True)):
+        r = Renderer(**shape)
+        img, T = r.forward(vd, fd, cd, od, s.cams)
+        g = torch.zeros_like(img)
+        g[lin_t] = torch.from_numpy(gs.astype(np.float32)).to(DEV)
+        dv, dc, do = r.backward(g)
+        torch.cuda.synchronize()
+        err = np.abs(img[lin_t].cpu().numpy() - ref["rgb"]).max(1)
+        assert err[~amb].max() <= IMG_TOL, (shape, float(err[~amb].max()))
+        assert np.abs(T[lin_t].cpu().numpy() - ref["T"])[~amb].max() <= IMG_TOL
+        assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+        assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+        assert r.device_status() == 0
+        del img, T, g
+        r.close()
+        torch.cuda.empty_cache()
