@@ -439,6 +439,53 @@ def test_final_transmittance_gradients_match_oracle(name, with_image):
     r.close()
 
 
+BWD_LAYOUTS = [
+    dict(threads_bwd=128, half_bwd=True),
+    dict(threads_bwd=256, half_bwd=True),
+    dict(threads_bwd=128, warp_bwd=True),
+    dict(threads_bwd=128, persistent=True),
+    dict(tile=8, threads=64, threads_bwd=32, warp_fwd=True, warp_bwd=True),
+    dict(tile=8, threads=64, threads_bwd=32, half_bwd=True),
+    dict(tile=8, threads=64, threads_bwd=64, persistent=True),
+    dict(tile=32, threads=256, threads_bwd=256),
+    dict(threads_bwd=128, deterministic=True),
+]
+
+
+@functools.lru_cache(maxsize=1)
+def _silhouette_reference():
+    s = _scenes()["uneven"]
+    bg = (0.2, 0.1, 0.4)
+    ref = oracle.render(s, bg=bg)
+    rng = np.random.default_rng(23)
+    gT = rng.normal(size=ref["T"].shape).astype(np.float32)
+    g = rng.normal(size=ref["rgb"].shape).astype(np.float32)
+    gT[ref["flags"] != 0] = 0.0
+    g[ref["flags"] != 0] = 0.0
+    ob = oracle.backward(s, g.astype(np.float64), bg=bg, dLdT=gT.astype(np.float64))
+    return s, bg, g, gT, ob
+
+
+@pytest.mark.parametrize("shape", range(len(BWD_LAYOUTS)))
+def test_final_transmittance_gradients_in_every_backward_layout(shape):
+    """dL/dT_final together with dL/dI through each backward layout (half-warp
+    at 128 and 256 threads, warp-staged, block-staged as a persistent grid,
+    8x8 tiles with split binning, 32x32 tiles, the deterministic backward)
+    against the oracle's reverse pass."""
+    from paper_2602_14493_b300 import Renderer
+
+    s, bg, g, gT, ob = _silhouette_reference()
+    r = Renderer(bg=bg, **BWD_LAYOUTS[shape])
+    render_gpu(r, s)
+    dv, dc, do = r.backward(torch.from_numpy(g).to(DEV), dL_dtfinal=torch.from_numpy(gT).to(DEV))
+    torch.cuda.synchronize()
+    assert rel_l2(dv.cpu().numpy(), ob["dverts"]) <= GRAD_TOL
+    assert rel_l2(dc.cpu().numpy(), ob["drgb"]) <= GRAD_TOL
+    assert rel_l2(do.cpu().numpy(), ob["dopacity"]) <= GRAD_TOL
+    assert r.device_status() == 0
+    r.close()
+
+
 def test_silhouette_bce_against_fp64():
     """The loss and dL/dT_final of gmr_silhouette_bce against the FP64
     oracle on random transmittances (including clamped ends) and binary and
