@@ -94,10 +94,13 @@ def test_fused_forward_loss_matches_separate():
     """gmr_render_fwd_l2: same image, the same dL/dI bit for bit, and the
     same loss up to the FP32 rounding of the per-thread partial sums as
     gmr_render_fwd + gmr_l2_loss; twice in a row, on views of uneven
-    sizes."""
+    sizes, in the block-staged, warp-staged and half-warp forward layouts."""
     s = _uneven()
-    for tile, threads in ((16, 256), (16, 128), (32, 256), (8, 64), (8, 32)):
-        r = _renderer(tile=tile, threads=threads)
+    shapes = [dict(tile=t, threads=n) for t, n in ((16, 256), (16, 128), (32, 256), (8, 64), (8, 32))]
+    shapes += [dict(tile=16, threads=128, warp_fwd=True), dict(tile=16, threads=256, half_fwd=True),
+               dict(tile=8, threads=64, warp_fwd=True), dict(tile=8, threads=32, half_fwd=True)]
+    for kw in shapes:
+        r = _renderer(**kw)
         (v, f, c, o), img, T = render_gpu(r, s)
         img = img.clone()
         target = torch.rand_like(img)
@@ -123,10 +126,15 @@ def test_backward_with_fused_loss_matches_separate():
     """gmr_render_bwd_l2 (the loss formed in the compositing backward): the
     same gradients as gmr_l2_loss + gmr_render_bwd up to the order of the
     float atomics, the same loss up to the FP32 partial sums, on views of
-    uneven sizes, for every backward shape, also with dL/dT_final."""
+    uneven sizes, for every backward shape and layout, also with
+    dL/dT_final."""
     s = _uneven()
-    for tile, threads in ((16, 128), (16, 256), (16, 64), (32, 256), (8, 64), (8, 32)):
-        r = _renderer(tile=tile, threads=threads)
+    shapes = [dict(tile=t, threads=n) for t, n in ((16, 128), (16, 256), (16, 64), (32, 256), (8, 64), (8, 32))]
+    shapes += [dict(tile=16, threads_bwd=128, half_bwd=True), dict(tile=16, threads_bwd=256, half_bwd=True),
+               dict(tile=16, threads_bwd=128, warp_bwd=True), dict(tile=8, threads_bwd=32, warp_bwd=True),
+               dict(tile=8, threads_bwd=32, half_bwd=True), dict(tile=8, threads_bwd=64, half_bwd=True)]
+    for kw in shapes:
+        r = _renderer(**kw)
         (v, f, c, o), img, T = render_gpu(r, s)
         img, T = img.clone(), T.clone()
         target = torch.rand_like(img)
