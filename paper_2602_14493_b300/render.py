@@ -149,7 +149,10 @@ class Renderer:
 
     def set_config(self, **kw):
         """Changes configuration fields; a new tile size without thread
-        counts takes that size's default thread counts."""
+        counts takes that size's default thread counts. A refused change
+        (GmrError) leaves the configuration as it was."""
+        saved_cfg = type(self.cfg).from_buffer_copy(self.cfg)
+        saved_color_mode = self.color_mode
         if "tile" in kw:
             kw.setdefault("threads", _default_threads(kw["tile"]))
             kw.setdefault("threads_bwd", _default_threads(kw["tile"]))
@@ -176,7 +179,12 @@ class Renderer:
                 self.cfg.profile_stages = _stage_mask(v)
                 continue
             setattr(self.cfg, k, v)
-        self._check(self._L.gmr_set_config(self._ctx, ctypes.byref(self.cfg)), "gmr_set_config")
+        try:
+            self._check(self._L.gmr_set_config(self._ctx, ctypes.byref(self.cfg)), "gmr_set_config")
+        except _lib.GmrError:
+            self.cfg = saved_cfg
+            self.color_mode = saved_color_mode
+            raise
 
     def set_workspace_limit(self, max_bytes):
         """Caps the device bytes of the workspace (0: no cap); a call that

@@ -331,12 +331,39 @@ def test_host_side_argument_errors():
     r.set_config(tile=16, threads=128, threads_bwd=128)
     with pytest.raises(GmrError):
         r.set_config(batch=100)
+    assert r.cfg.batch == 256  # a refused change leaves the configuration as it was
     bad = s.cams.copy()
     bad[0]["width"] = 0
     with pytest.raises(GmrError):
         r.forward(v, f, c, o, bad)
     L = r._L
     assert L.gmr_render_fwd(r._ctx, None, 5, None, 3, None, None, None, 1, None, None, None) == 1
+    # size limits of the packed formats, refused on the host before any
+    # device work (the device pointers below are never read)
+    from paper_2602_14493_b300 import camera_array
+
+    img = torch.zeros(16 * 16 * 3, device=DEV)
+    p = [ctypes.c_void_p(t.data_ptr()) for t in (v, f, c, img)]
+
+    def fwd(cams, F=len(s.faces), C=None):
+        C = len(cams) if C is None else C
+        return L.gmr_render_fwd(r._ctx, p[0], len(s.verts), p[1], F, p[2], None, camera_array(cams), C, p[3], None,
+                                None)
+
+    assert fwd(s.cams) == 0
+    cams8 = np.repeat(s.cams, 8)
+    assert fwd(cams8, F=1 << 28) == 1                    # views x faces >= 2^31
+    assert fwd(s.cams, C=70000) == 1                     # more than 65535 views
+    wide = s.cams.copy()
+    wide[0]["width"] = (1 << 20) + 1                     # a side beyond 2^20 pixels
+    assert fwd(wide) == 1
+    r.set_config(tile=8, threads=64, threads_bwd=64)
+    wide[0]["width"] = 1 << 20                           # 131,072 tiles of 8 px across
+    assert fwd(wide) == 1
+    nan = s.cams.copy()
+    nan["R"][0, 4] = np.nan                              # a non-finite camera
+    assert fwd(nan) == 1
+    torch.cuda.synchronize()
     r.close()
 
 
